@@ -1,0 +1,718 @@
+// Decomposition build on the GPU (Section II-B and the sorting of Section II-C):
+// ingest and support radii, Morton keys, LSD radix sort, cell tree with the
+// split rule, self/pair interaction lists with recursive splitting, particle
+// offsets relative to their cell, and the per-cell sorted projections along
+// the 13 cell-pair axes.
+#include "sph_engine.h"
+
+#include <cfloat>
+
+namespace sph {
+
+// ============================================================== ingest
+// Validate the inputs, compute H = gamma_K * h (rounded once to FP32) and the
+// per-box extremes of H.  bid[p] is the box of input particle p.
+__global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box, const double* __restrict__ x,
+                         const float* __restrict__ v, const float* __restrict__ m, const float* __restrict__ u,
+                         const float* __restrict__ h, float gamma_k, float* __restrict__ H_out) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int b = bid[p];
+    const double L = box[b].L;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double xk = x[3 * p + k];
+      ok &= (xk >= 0.0) && (xk < L);
+      ok &= isfinite(v[3 * p + k]);
+    }
+    const float hp = h[p];
+    ok &= isfinite(hp) && hp > 0.0f && isfinite(m[p]) && m[p] > 0.0f && isfinite(u[p]) && u[p] >= 0.0f;
+    const float H = __fmul_rn(gamma_k, hp);
+    ok &= isfinite(H) && H > 0.0f;
+    if (!ok) {
+      atomicOr(&box[b].err, ERR_BAD_INPUT);
+      H_out[p] = 0.0f;
+      continue;
+    }
+    H_out[p] = H;
+    atomic_max_pos(&box[b].Hmax, H);
+    atomic_min_pos(&box[b].Hmin, H);
+  }
+}
+
+// ============================================================== keys
+// key = box << (3 dcap) | Morton(floor((x / L) 2^dcap)) with the cell index
+// clamped to [0, 2^dcap - 1]; the value is the input index.
+__global__ void k_keys(long long N, int dcap, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
+                       const double* __restrict__ x, unsigned long long* __restrict__ key,
+                       unsigned int* __restrict__ val) {
+  const double scale = ldexp(1.0, dcap);
+  const unsigned int qmax = (1u << dcap) - 1u;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int b = bid[p];
+    const double L = box[b].L;
+    unsigned int q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double uu = __ddiv_rn(x[3 * p + k], L);
+      double f = floor(__dmul_rn(uu, scale));
+      f = fmin(fmax(f, 0.0), (double)qmax);
+      q[k] = (unsigned int)f;
+    }
+    key[p] = ((unsigned long long)b << (3 * dcap)) | morton3(q[0], q[1], q[2]);
+    val[p] = (unsigned int)p;
+  }
+}
+
+// ============================================================== radix sort
+// Stable LSD radix sort of (64-bit key, 32-bit value), 8-bit digits.  Each
+// pass: per-tile digit histograms, one exclusive scan of the digit-major
+// histogram table, then a stable scatter that ranks equal digits by
+// (round, warp, lane) order inside the tile.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__global__ void k_radix_hist(long long n, const unsigned long long* __restrict__ key, int shift,
+                             unsigned int* __restrict__ hist, int ntiles) {
+  __shared__ unsigned int cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const long long i = base + r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(unsigned int)(key[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(long long)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(long long n, const unsigned long long* __restrict__ kin,
+                                const unsigned int* __restrict__ vin, unsigned long long* __restrict__ kout,
+                                unsigned int* __restrict__ vout, int shift, const unsigned int* __restrict__ offs,
+                                int ntiles) {
+  __shared__ unsigned int base[256];
+  __shared__ unsigned int wcnt[RS_THREADS / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  base[tid] = offs[(long long)tid * ntiles + blockIdx.x];
+  for (int k = 0; k < RS_THREADS / 32; ++k) wcnt[k][tid] = 0;
+  __syncthreads();
+  const long long tile0 = (long long)blockIdx.x * RS_TILE;
+  const unsigned int lt = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const long long i = tile0 + r * RS_THREADS + tid;
+    const bool valid = i < n;
+    unsigned long long k = valid ? kin[i] : 0ull;
+    const unsigned int d = valid ? ((unsigned int)(k >> shift) & 255u) : 256u;
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    const unsigned int lrank = __popc(peers & lt);
+    if (valid && lrank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned int pre = 0;
+      for (int q = 0; q < w; ++q) pre += wcnt[q][d];
+      const unsigned int pos = base[d] + pre + lrank;
+      kout[pos] = k;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    unsigned int tot = 0;
+    for (int q = 0; q < RS_THREADS / 32; ++q) {
+      tot += wcnt[q][tid];
+      wcnt[q][tid] = 0;
+    }
+    base[tid] += tot;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------- exclusive scan (u32)
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+__device__ unsigned int block_exclusive_scan(unsigned int v, unsigned int* tmp, unsigned int& total) {
+  // tmp: 32 words of shared memory
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    unsigned int s = lane < nw ? tmp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) tmp[lane] = s;
+  }
+  __syncthreads();
+  const unsigned int before = (w > 0 ? tmp[w - 1] : 0u) + x - v;
+  total = tmp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+// in and out may be the same array: every thread reads its items before writing them
+__global__ void k_scan_tiles(long long n, const unsigned int* in, unsigned int* out,
+                             unsigned int* __restrict__ tile_sums) {
+  __shared__ unsigned int tmp[32];
+  const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
+  unsigned int loc[SC_ITEMS];
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    loc[k] = (base + k < n) ? in[base + k] : 0u;
+    s += loc[k];
+  }
+  unsigned int total;
+  unsigned int run = block_exclusive_scan(s, tmp, total);
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += loc[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of the tile sums in place (any count), total -> *total
+__global__ void k_scan_sums(int ntiles, unsigned int* __restrict__ sums, unsigned int* __restrict__ total_out) {
+  __shared__ unsigned int tmp[32];
+  unsigned int carry = 0;
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const unsigned int v = i < ntiles ? sums[i] : 0u;
+    unsigned int total;
+    const unsigned int ex = block_exclusive_scan(v, tmp, total);
+    if (i < ntiles) sums[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void k_scan_add(long long n, unsigned int* __restrict__ out, const unsigned int* __restrict__ sums) {
+  const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
+  const unsigned int add = sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SC_ITEMS; ++k)
+    if (base + k < n) out[base + k] += add;
+}
+
+void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsigned int* tile_sums,
+                    unsigned int* total, cudaStream_t st) {
+  const long long ntiles = (n + SC_TILE - 1) / SC_TILE;
+  if (ntiles == 0) return;
+  k_scan_tiles<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, in, out, tile_sums);
+  k_scan_sums<<<1, 1024, 0, st>>>((int)ntiles, tile_sums, total);
+  k_scan_add<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, out, tile_sums);
+}
+
+long long radix_scratch_words(long long n) {
+  const long long ntiles = (n + RS_TILE - 1) / RS_TILE;
+  return 256 * ntiles + (256 * ntiles + SC_TILE - 1) / SC_TILE + 16;
+}
+
+// Sorts (k0, v0) by the low `bits` bits of the key; the result lands in
+// (k0, v0) (using (k1, v1) as the other half of each pass).
+void radix_sort(unsigned long long* k0, unsigned int* v0, unsigned long long* k1, unsigned int* v1, long long n,
+                int bits, unsigned int* scratch, cudaStream_t st) {
+  if (n <= 1 || bits <= 0) return;
+  const long long ntiles = (n + RS_TILE - 1) / RS_TILE;
+  unsigned int* hist = scratch;
+  unsigned int* sums = scratch + 256 * ntiles;
+  int passes = (bits + 7) / 8;
+  unsigned long long *ka = k0, *kb = k1;
+  unsigned int *va = v0, *vb = v1;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, shift, hist, (int)ntiles);
+    exclusive_scan(hist, hist, 256 * ntiles, sums, nullptr, st);
+    k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, va, kb, vb, shift, hist, (int)ntiles);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != k0) {
+    cudaMemcpyAsync(k0, ka, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(v0, va, n * sizeof(unsigned int), cudaMemcpyDeviceToDevice, st);
+  }
+}
+
+// ============================================================== gather
+__global__ void k_gather_sorted(long long N, const unsigned int* __restrict__ perm, const float* __restrict__ H_in,
+                                const float* __restrict__ v, const float* __restrict__ u, float* __restrict__ Hs,
+                                float4* __restrict__ vel4) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const unsigned int i = perm[p];
+    Hs[p] = H_in[i];
+    vel4[p] = make_float4(v[3ll * i], v[3ll * i + 1], v[3ll * i + 2], u[i]);
+  }
+}
+
+// ============================================================== cell tree
+__device__ __forceinline__ unsigned long long prefix_at(unsigned long long key, int dcap, int level, int box_shift) {
+  // box bits stay on top of the prefix
+  const unsigned long long box = key >> box_shift;
+  const unsigned long long mort = key & ((box_shift >= 64) ? ~0ull : ((1ull << box_shift) - 1ull));
+  return (box << (3 * level)) | (mort >> (3 * (dcap - level)));
+}
+
+// first index in [lo, hi) whose prefix at `level` is >= target
+__device__ __forceinline__ long long lower_bound_prefix(const unsigned long long* key, long long lo, long long hi,
+                                                        unsigned long long target, int dcap, int level,
+                                                        int box_shift) {
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (prefix_at(key[mid], dcap, level, box_shift) < target) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Integer coordinates of a cell from its prefix (box bits removed).
+__device__ __forceinline__ void cell_coords(unsigned long long prefix, int level, unsigned int& cx, unsigned int& cy,
+                                            unsigned int& cz) {
+  const unsigned long long mort = level > 0 ? (prefix & ((1ull << (3 * level)) - 1ull)) : 0ull;
+  cx = compact3(mort);
+  cy = compact3(mort >> 1);
+  cz = compact3(mort >> 2);
+}
+
+__global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc* __restrict__ box,
+                            const unsigned long long* __restrict__ key, Tree T, int cap_nodes,
+                            int* __restrict__ top_at, unsigned int* __restrict__ err_all) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(key[p] >> box_shift);
+    const BoxDesc bd = box[b];
+    const unsigned long long pre = prefix_at(key[p], dcap, bd.k, box_shift);
+    const bool start = (p == bd.off) || (prefix_at(key[p - 1], dcap, bd.k, box_shift) != pre);
+    if (!start) continue;
+    const int id = atomicAdd(&T.n_nodes[0], 1);
+    if (id >= cap_nodes) {
+      atomicOr(err_all, ERR_OVERFLOW);
+      continue;
+    }
+    const long long end = lower_bound_prefix(key, p, bd.off + bd.n, pre + 1, dcap, bd.k, box_shift);
+    T.start[id] = (unsigned int)p;
+    T.count[id] = (unsigned int)(end - p);
+    T.key[id] = pre;
+    T.level[id] = bd.k;
+    T.box[id] = b;
+    T.parent[id] = -1;
+    T.child[id] = -1;
+    T.nchild[id] = 0;
+    top_at[p] = id;
+  }
+}
+
+// Per-node statistics and the split rule of Section II-B / III-B:
+// split iff level < dcap, count > leaf_max and n_small > split_frac * count,
+// with n_small = #{H < edge/2 - margin}.
+__global__ void k_node_stats(Tree T, const BoxDesc* __restrict__ box, const float* __restrict__ Hs, int dcap,
+                             int leaf_max, float split_frac) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int f0 = T.n_nodes[1], f1 = min(T.n_nodes[2], T.n_nodes[0]);
+  for (int id = f0 + warp; id < f1; id += nwarps) {
+    const int d = T.level[id];
+    const BoxDesc bd = box[T.box[id]];
+    const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
+    const unsigned int s = T.start[id], c = T.count[id];
+    float hm = 0.0f;
+    unsigned int ns = 0;
+    for (unsigned int q = lane; q < c; q += 32) {
+      const float H = Hs[s + q];
+      hm = fmaxf(hm, H);
+      ns += ((double)H < half) ? 1u : 0u;
+    }
+    hm = warp_max(hm);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    if (lane == 0) {
+      T.hmax[id] = hm;
+      T.nsmall[id] = ns;
+      const bool sp = d < dcap && (int)c > leaf_max && (double)ns > (double)split_frac * (double)c;
+      T.split[id] = sp ? 1 : 0;
+      T.axes[id] = 0;
+      // limit the top grid sets on every particle: H < edge_k - margin
+      T.hlim[id] = (T.parent[id] < 0) ? __dsub_rn(ldexp(bd.L, -d), bd.margin) : 1e300;
+      unsigned int cx, cy, cz;
+      cell_coords(T.key[id], d, cx, cy, cz);
+      const double inv = ldexp(1.0, -d), invk = ldexp(1.0, -bd.k);
+      const int sh = d - bd.k;
+      const double tx = ((double)(cx >> sh) + 0.5) * invk, ty = ((double)(cy >> sh) + 0.5) * invk,
+                   tz = ((double)(cz >> sh) + 0.5) * invk;
+      T.cen[id] = make_float4((float)(((double)cx + 0.5) * inv - tx), (float)(((double)cy + 0.5) * inv - ty),
+                              (float)(((double)cz + 0.5) * inv - tz), (float)inv);
+    }
+  }
+}
+
+// Children of every split frontier node: the non-empty octants, found by binary
+// search on the sorted keys; children of one node get consecutive ids.
+__global__ void k_split_nodes(Tree T, const unsigned long long* __restrict__ key, int dcap, int box_shift,
+                              int cap_nodes, unsigned int* __restrict__ err_all) {
+  const int f0 = T.n_nodes[1], f1 = min(T.n_nodes[2], cap_nodes);
+  for (int id = f0 + blockIdx.x * blockDim.x + threadIdx.x; id < f1; id += gridDim.x * blockDim.x) {
+    if (!T.split[id]) continue;
+    const int d = T.level[id];
+    const long long s = T.start[id], e = s + T.count[id];
+    long long bound[9];
+    bound[0] = s;
+    bound[8] = e;
+    const unsigned long long base = T.key[id] << 3;
+    for (int o = 1; o < 8; ++o) bound[o] = lower_bound_prefix(key, s, e, base | (unsigned long long)o, dcap, d + 1, box_shift);
+    int nch = 0;
+    for (int o = 0; o < 8; ++o) nch += (bound[o + 1] > bound[o]) ? 1 : 0;
+    const int c0 = atomicAdd(&T.n_nodes[0], nch);
+    if (c0 + nch > cap_nodes) {
+      atomicOr(err_all, ERR_OVERFLOW);
+      T.split[id] = 0;
+      continue;
+    }
+    int c = c0;
+    for (int o = 0; o < 8; ++o) {
+      if (bound[o + 1] <= bound[o]) continue;
+      T.start[c] = (unsigned int)bound[o];
+      T.count[c] = (unsigned int)(bound[o + 1] - bound[o]);
+      T.key[c] = base | (unsigned long long)o;
+      T.level[c] = d + 1;
+      T.box[c] = T.box[id];
+      T.parent[c] = id;
+      T.child[c] = -1;
+      T.nchild[c] = 0;
+      ++c;
+    }
+    T.child[id] = c0;
+    T.nchild[id] = nch;
+  }
+}
+
+__global__ void k_frontier_next(Tree T, int cap_nodes) {
+  T.n_nodes[1] = T.n_nodes[2];
+  T.n_nodes[2] = min(T.n_nodes[0], cap_nodes);
+}
+
+__global__ void k_frontier_init(Tree T, int cap_nodes) {
+  T.n_nodes[1] = 0;
+  T.n_nodes[2] = min(T.n_nodes[0], cap_nodes);
+  T.n_nodes[3] = min(T.n_nodes[0], cap_nodes);   // top cells are nodes [0, n_nodes[3])
+}
+
+// ============================================================== interaction lists
+__device__ __forceinline__ void push_item(Lists Lq, int out, int kind, int a, int b, int ax, int cap_queue,
+                                          unsigned int* err_all) {
+  const int slot = atomicAdd(&Lq.counts[2 + out], 1);
+  if (slot >= cap_queue) {
+    atomicOr(err_all, ERR_OVERFLOW);
+    return;
+  }
+  Lq.q_kind[out][slot] = kind;
+  Lq.q_a[out][slot] = a;
+  Lq.q_b[out][slot] = b;
+  Lq.q_axis[out][slot] = ax;
+}
+
+// Top level: the self-interaction of every non-empty top cell and its pairs with
+// the non-empty neighbours along the 13 positive directions (periodic images
+// included; a box has at least 4 top cells per dimension when periodic).
+__global__ void k_items_top(int ntop, Tree T, const BoxDesc* __restrict__ box, const unsigned long long* __restrict__ key,
+                            const int* __restrict__ top_at, int dcap, int box_shift, Lists Lq, int cap_queue,
+                            unsigned int* __restrict__ err_all) {
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < ntop; id += gridDim.x * blockDim.x) {
+    const int b = T.box[id];
+    const BoxDesc bd = box[b];
+    const int k = bd.k;
+    push_item(Lq, 0, 0, id, -1, 0, cap_queue, err_all);
+    unsigned int cx, cy, cz;
+    cell_coords(T.key[id], k, cx, cy, cz);
+    const int side = 1 << k;
+    for (int a = 0; a < 13; ++a) {
+      int dx, dy, dz;
+      axis_vec(a, dx, dy, dz);
+      int nx = (int)cx + dx, ny = (int)cy + dy, nz = (int)cz + dz;
+      if (bd.periodic) {
+        nx = (nx + side) % side;
+        ny = (ny + side) % side;
+        nz = (nz + side) % side;
+      } else if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side) {
+        continue;
+      }
+      const unsigned long long target = ((unsigned long long)b << (3 * k)) | morton3(nx, ny, nz);
+      const long long p = lower_bound_prefix(key, bd.off, bd.off + bd.n, target, dcap, k, box_shift);
+      if (p < bd.off + bd.n && prefix_at(key[p], dcap, k, box_shift) == target)
+        push_item(Lq, 0, 1, id, top_at[p], a, cap_queue, err_all);
+    }
+  }
+}
+
+// One round of splitting (Fig. 2): a self-interaction of a split cell becomes its
+// children's selfs and the pairs between them; a pair of split cells becomes the
+// adjacent child pairs across the interface iff every particle of both cells has
+// H < edge/2 - margin.  Everything else is final.
+__global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, Lists Lq, int cap_queue,
+                               int cap_self, int cap_pair, unsigned int* __restrict__ err_all) {
+  const int out = in ^ 1;
+  const int n = min(Lq.counts[2 + in], cap_queue);
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    const int kind = Lq.q_kind[in][it];
+    const int A = Lq.q_a[in][it];
+    if (kind == 0) {
+      if (!T.split[A]) {
+        const int s = atomicAdd(&Lq.counts[0], 1);
+        if (s < cap_self) Lq.self_a[s] = A;
+        else atomicOr(err_all, ERR_OVERFLOW);
+        continue;
+      }
+      const int c0 = T.child[A], nc = T.nchild[A];
+      for (int i = 0; i < nc; ++i) push_item(Lq, out, 0, c0 + i, -1, 0, cap_queue, err_all);
+      for (int i = 0; i < nc; ++i) {
+        const int oi = (int)(T.key[c0 + i] & 7ull);
+        for (int j = i + 1; j < nc; ++j) {
+          const int oj = (int)(T.key[c0 + j] & 7ull);
+          int dx = (oj & 1) - (oi & 1), dy = ((oj >> 1) & 1) - ((oi >> 1) & 1), dz = ((oj >> 2) & 1) - ((oi >> 2) & 1);
+          if (dir_positive(dx, dy, dz)) push_item(Lq, out, 1, c0 + i, c0 + j, axis_index(dx, dy, dz), cap_queue, err_all);
+          else push_item(Lq, out, 1, c0 + j, c0 + i, axis_index(-dx, -dy, -dz), cap_queue, err_all);
+        }
+      }
+      continue;
+    }
+    const int B = Lq.q_b[in][it];
+    const int ax = Lq.q_axis[in][it];
+    const int d = T.level[A];
+    const BoxDesc bd = box[T.box[A]];
+    const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
+    const double hm = (double)fmaxf(T.hmax[A], T.hmax[B]);
+    if (!(T.split[A] && T.split[B] && hm < half)) {
+      const int s = atomicAdd(&Lq.counts[1], 1);
+      if (s < cap_pair) {
+        Lq.pair_a[s] = A;
+        Lq.pair_b[s] = B;
+        Lq.pair_axis[s] = ax;
+      } else {
+        atomicOr(err_all, ERR_OVERFLOW);
+      }
+      continue;
+    }
+    atomic_min_pos(&T.hlim[A], half);
+    atomic_min_pos(&T.hlim[B], half);
+    int bx, by, bz;
+    axis_vec(ax, bx, by, bz);
+    const int ca0 = T.child[A], na = T.nchild[A], cb0 = T.child[B], nb = T.nchild[B];
+    for (int i = 0; i < na; ++i) {
+      const int oa = (int)(T.key[ca0 + i] & 7ull);
+      for (int j = 0; j < nb; ++j) {
+        const int ob = (int)(T.key[cb0 + j] & 7ull);
+        const int dx = 2 * bx + (ob & 1) - (oa & 1);
+        const int dy = 2 * by + ((ob >> 1) & 1) - ((oa >> 1) & 1);
+        const int dz = 2 * bz + ((ob >> 2) & 1) - ((oa >> 2) & 1);
+        if (abs(dx) > 1 || abs(dy) > 1 || abs(dz) > 1) continue;
+        if (dir_positive(dx, dy, dz)) push_item(Lq, out, 1, ca0 + i, cb0 + j, axis_index(dx, dy, dz), cap_queue, err_all);
+        else push_item(Lq, out, 1, cb0 + j, ca0 + i, axis_index(-dx, -dy, -dz), cap_queue, err_all);
+      }
+    }
+  }
+}
+
+// leaf of every particle, and the smallest H limit along its chain of cells
+__global__ void k_leaves(Tree T, int nnodes, unsigned int* __restrict__ leaf_of) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int id = warp; id < nnodes; id += nwarps) {
+    if (T.child[id] >= 0) continue;
+    const unsigned int s = T.start[id], c = T.count[id];
+    for (unsigned int q = lane; q < c; q += 32) leaf_of[s + q] = (unsigned int)id;
+  }
+}
+
+__global__ void k_particle_limits(long long N, Tree T, const unsigned int* __restrict__ leaf_of,
+                                  float* __restrict__ hlimp) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    int id = (int)leaf_of[p];
+    double lim = 1e300;
+    while (id >= 0) {
+      lim = fmin(lim, T.hlim[id]);
+      id = T.parent[id];
+    }
+    hlimp[p] = __double2float_rz(lim);
+  }
+}
+
+// Particle offsets relative to the centre of their leaf (units of L, FP32) and
+// the leaf centre relative to its top cell's centre (exact), plus the mass.
+__global__ void k_shift(long long N, int box_shift, const unsigned long long* __restrict__ key,
+                        const unsigned int* __restrict__ perm, const unsigned int* __restrict__ leaf_of, Tree T,
+                        const BoxDesc* __restrict__ box, const double* __restrict__ x, const float* __restrict__ m,
+                        const float* __restrict__ Hs, float4* __restrict__ pos4, float4* __restrict__ cen4) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(key[p] >> box_shift);
+    const double L = box[b].L;
+    const unsigned int i = perm[p];
+    const int leaf = (int)leaf_of[p];
+    const int d = T.level[leaf];
+    unsigned int cx, cy, cz;
+    cell_coords(T.key[leaf], d, cx, cy, cz);
+    const double inv = ldexp(1.0, -d);
+    const float sx = (float)(__ddiv_rn(x[3ll * i], L) - ((double)cx + 0.5) * inv);
+    const float sy = (float)(__ddiv_rn(x[3ll * i + 1], L) - ((double)cy + 0.5) * inv);
+    const float sz = (float)(__ddiv_rn(x[3ll * i + 2], L) - ((double)cz + 0.5) * inv);
+    pos4[p] = make_float4(sx, sy, sz, Hs[p]);
+    const float4 c = T.cen[leaf];
+    cen4[p] = make_float4(c.x, c.y, c.z, m[i]);
+  }
+}
+
+// ============================================================== axis sorts
+__global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
+  const int n = min(Lq.counts[1], cap_pair);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned int bit = 1u << Lq.pair_axis[i];
+    atomicOr(&T.axes[Lq.pair_a[i]], bit);
+    atomicOr(&T.axes[Lq.pair_b[i]], bit);
+  }
+}
+
+// Storage for the sorted lists: every (cell, needed axis) gets count entries.
+// Cells above SORT_SMALL particles also list their (cell, axis) segments for
+// the global sort.
+__global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
+                             unsigned int* __restrict__ big_off, int* __restrict__ big_count, int cap_big) {
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
+    const unsigned int ax = T.axes[id];
+    if (!ax) continue;
+    const unsigned int c = T.count[id];
+    const int na = __popc(ax);
+    T.sortbase[id] = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
+    atomicAdd(&Lq.counts[4], na);
+    if (c > SORT_SMALL) {
+      const int s0 = atomicAdd(&big_count[0], na);
+      const unsigned int e0 = atomicAdd(reinterpret_cast<unsigned int*>(&big_count[1]), (unsigned int)na * c);
+      int q = 0;
+      for (int a = 0; a < 13; ++a) {
+        if (!(ax & (1u << a))) continue;
+        if (s0 + q < cap_big) {
+          big_node[s0 + q] = id;
+          big_axis[s0 + q] = a;
+          big_off[s0 + q] = e0 + (unsigned int)q * c;
+        }
+        ++q;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float3 axis_unit(int a) {
+  int dx, dy, dz;
+  axis_vec(a, dx, dy, dz);
+  const int n2 = dx * dx + dy * dy + dz * dz;
+  const float s = n2 == 1 ? 1.0f : (n2 == 2 ? 0.70710678118654752f : 0.57735026918962576f);
+  return make_float3(dx * s, dy * s, dz * s);
+}
+
+// projection of particle p on axis u in the frame of the cell with centre cc
+__device__ __forceinline__ float project(const float4* pos4, const float4* cen4, unsigned int p, float4 cc, float3 u) {
+  const float4 q = pos4[p];
+  const float4 c = cen4[p];
+  const float x = q.x + (c.x - cc.x), y = q.y + (c.y - cc.y), z = q.z + (c.z - cc.z);
+  return fmaf(u.x, x, fmaf(u.y, y, u.z * z));
+}
+
+// One CTA per cell with at most SORT_SMALL particles: bitonic sort of
+// (projection, local index) in shared memory for every needed axis.
+__global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, const float4* __restrict__ pos4,
+                                                   const float4* __restrict__ cen4, float* __restrict__ sort_r,
+                                                   unsigned int* __restrict__ sort_i) {
+  __shared__ float sr[SORT_SMALL];
+  __shared__ unsigned int si[SORT_SMALL];
+  for (int id = blockIdx.x; id < nnodes; id += gridDim.x) {
+    const unsigned int ax = T.axes[id];
+    const unsigned int c = T.count[id];
+    if (!ax || c > SORT_SMALL) continue;
+    unsigned int npow = 1;
+    while (npow < c) npow <<= 1;
+    const unsigned int s = T.start[id];
+    const float4 cc = T.cen[id];
+    unsigned int out = T.sortbase[id];
+    for (int a = 0; a < 13; ++a) {
+      if (!(ax & (1u << a))) continue;
+      const float3 u = axis_unit(a);
+      for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
+        sr[q] = q < c ? project(pos4, cen4, s + q, cc, u) : FLT_MAX;
+        si[q] = q;
+      }
+      __syncthreads();
+      for (unsigned int k = 2; k <= npow; k <<= 1) {
+        for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+          for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
+            const unsigned int l = q ^ j;
+            if (l > q) {
+              const bool up = (q & k) == 0;
+              const float a0 = sr[q], a1 = sr[l];
+              const unsigned int i0 = si[q], i1 = si[l];
+              const bool gt = (a0 > a1) || (a0 == a1 && i0 > i1);
+              if (gt == up) {
+                sr[q] = a1; sr[l] = a0;
+                si[q] = i1; si[l] = i0;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+        sort_r[out + q] = sr[q];
+        sort_i[out + q] = si[q];
+      }
+      out += c;
+      __syncthreads();
+    }
+  }
+}
+
+// Large cells: composite keys (segment << 32 | orderable projection) for one
+// global radix sort, then scatter back into each cell's storage.
+__global__ void k_sort_big_keys(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
+                                const unsigned int* __restrict__ big_off, Tree T, const float4* __restrict__ pos4,
+                                const float4* __restrict__ cen4, unsigned long long* __restrict__ ckey,
+                                unsigned int* __restrict__ cval) {
+  for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
+    const int id = big_node[sgi];
+    const int a = big_axis[sgi];
+    const unsigned int c = T.count[id], s = T.start[id], o = big_off[sgi];
+    const float4 cc = T.cen[id];
+    const float3 u = axis_unit(a);
+    for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+      ckey[o + q] = ((unsigned long long)sgi << 32) | float_key(project(pos4, cen4, s + q, cc, u));
+      cval[o + q] = q;
+    }
+  }
+}
+
+__global__ void k_sort_big_scatter(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
+                                   const unsigned int* __restrict__ big_off, Tree T, const float4* __restrict__ pos4,
+                                   const float4* __restrict__ cen4, const unsigned int* __restrict__ cval,
+                                   float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
+  for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
+    const int id = big_node[sgi];
+    const int a = big_axis[sgi];
+    const unsigned int ax = T.axes[id];
+    const unsigned int c = T.count[id], s = T.start[id], o = big_off[sgi];
+    const unsigned int dst = T.sortbase[id] + (unsigned int)__popc(ax & ((1u << a) - 1u)) * c;
+    const float4 cc = T.cen[id];
+    const float3 u = axis_unit(a);
+    for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+      const unsigned int li = cval[o + q];
+      sort_i[dst + q] = li;
+      sort_r[dst + q] = project(pos4, cen4, s + li, cc, u);
+    }
+  }
+}
+
+}  // namespace sph

@@ -1,0 +1,920 @@
+// Host orchestration of the GB300 SPH path and the C-ABI of include/sph.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sph_engine.h"
+
+namespace sph {
+
+// kernels of build.cu
+__global__ void k_ingest(long long, const int*, BoxDesc*, const double*, const float*, const float*, const float*,
+                         const float*, float, float*);
+__global__ void k_keys(long long, int, const int*, const BoxDesc*, const double*, unsigned long long*, unsigned int*);
+__global__ void k_gather_sorted(long long, const unsigned int*, const float*, const float*, const float*, float*,
+                                float4*);
+__global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned long long*, Tree, int, int*,
+                            unsigned int*);
+__global__ void k_node_stats(Tree, const BoxDesc*, const float*, int, int, float);
+__global__ void k_split_nodes(Tree, const unsigned long long*, int, int, int, unsigned int*);
+__global__ void k_frontier_next(Tree, int);
+__global__ void k_frontier_init(Tree, int);
+__global__ void k_items_top(int, Tree, const BoxDesc*, const unsigned long long*, const int*, int, int, Lists, int,
+                            unsigned int*);
+__global__ void k_items_expand(int, Tree, const BoxDesc*, Lists, int, int, int, unsigned int*);
+__global__ void k_leaves(Tree, int, unsigned int*);
+__global__ void k_particle_limits(long long, Tree, const unsigned int*, float*);
+__global__ void k_shift(long long, int, const unsigned long long*, const unsigned int*, const unsigned int*, Tree,
+                        const BoxDesc*, const double*, const float*, const float*, float4*, float4*);
+__global__ void k_mark_axes(Lists, int, Tree);
+__global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, int*, int);
+__global__ void k_sort_small(Tree, int, const float4*, const float4*, float*, unsigned int*);
+__global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, const float4*, const float4*,
+                                unsigned long long*, unsigned int*);
+__global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, const float4*,
+                                   const float4*, const unsigned int*, float*, unsigned int*);
+// launchers of interact.cu
+void launch_density(Engine& E);
+void launch_force(Engine& E);
+void launch_ghost(Engine& E, int mode, int it);
+void launch_zero_density(Engine& E, bool all);
+void launch_set_active(Engine& E);
+void launch_bracket_reset(Engine& E);
+void launch_reduce(Engine& E);
+void launch_save_acc(Engine& E);
+void launch_kick(Engine& E);
+void launch_drift(Engine& E);
+void launch_get_field(Engine& E, long long off, long long n, int field, void* out);
+
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+Engine::Engine(const sph_params& p, int dev, cudaStream_t s) : prm(p), device(dev), st(s) {
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  if (nsm <= 0) nsm = 148;
+}
+
+Engine::~Engine() {}
+
+int Engine::grid(long long work, int threads) const {
+  long long g = (work + threads - 1) / threads;
+  const long long cap = (long long)nsm * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+sph_status Engine::cuda_fail(cudaError_t e, const char* where) {
+  err = std::string("CUDA error ") + cudaGetErrorString(e) + " at " + where;
+  return SPH_E_CUDA;
+}
+
+sph_status Engine::fail(sph_status s, const std::string& msg) {
+  err = msg;
+  return s;
+}
+
+size_t Engine::footprint_bytes() const {
+  // device bytes per particle of the resident state plus the lists (estimate)
+  return (size_t)N * 520 + 4096;
+}
+
+sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
+  spec = boxes;
+  nbox = (int)boxes.size();
+  off.assign(nbox + 1, 0);
+  for (int b = 0; b < nbox; ++b) off[b + 1] = off[b] + boxes[b].n;
+  N = off[nbox];
+  hbox.assign(nbox, BoxDesc{});
+  for (int b = 0; b < nbox; ++b) {
+    BoxDesc& d = hbox[b];
+    d.L = boxes[b].L;
+    d.invL = 1.0 / boxes[b].L;
+    d.margin = boxes[b].L * std::ldexp(1.0, -50);
+    d.off = off[b];
+    d.n = boxes[b].n;
+    d.periodic = boxes[b].periodic;
+  }
+  built = have_density = have_ghost = have_force = have_acc = false;
+  sph_status s = ensure_particle_capacity();
+  if (s != SPH_OK) return s;
+  std::vector<int> hb(N);
+  for (int b = 0; b < nbox; ++b)
+    for (long long p = off[b]; p < off[b + 1]; ++p) hb[p] = b;
+  CK(cudaMemcpyAsync(bid.p, hb.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return SPH_OK;
+}
+
+sph_status Engine::ensure_particle_capacity() {
+  const size_t n = (size_t)std::max<long long>(N, 1);
+  CK(box.reserve(std::max(nbox, 1)));
+  CK(bid.reserve(n));
+  CK(x.reserve(3 * n));
+  CK(v.reserve(3 * n));
+  CK(m.reserve(n));
+  CK(u.reserve(n));
+  CK(h.reserve(n));
+  CK(H_in.reserve(n));
+  CK(hlo.reserve(n));
+  CK(hhi.reserve(n));
+  CK(conv.reserve(n));
+  CK(a_in.reserve(n));
+  CK(key.reserve(n));
+  CK(key_tmp.reserve(n));
+  CK(perm.reserve(n));
+  CK(perm_tmp.reserve(n));
+  CK(rs_scratch.reserve((size_t)radix_scratch_words(n)));
+  CK(Hs.reserve(n));
+  CK(hlimp.reserve(n));
+  CK(pos4.reserve(n));
+  CK(cen4.reserve(n));
+  CK(vel4.reserve(n));
+  CK(leaf_of.reserve(n));
+  CK(top_at.reserve(n));
+  CK(act.reserve(n));
+  CK(dacc.reserve(n));
+  CK(dcnt.reserve(n));
+  CK(ghost4.reserve(n));
+  CK(facc.reserve(n));
+  CK(fvsig.reserve(n));
+  CK(red.reserve(8 * std::max(nbox, 1)));
+  CK(err_all.reserve(4));
+  CK(pc.reserve(8));
+  CK(dev_counters.reserve(8));
+  CK(staging.reserve(24 * n));
+  CK(cudaMemsetAsync(conv.p, 0, n * sizeof(int), st));
+  if (cap_nodes == 0) {
+    sph_status s = ensure_tree_capacity((int)std::min<long long>(std::max<long long>(4096, N / 4), 1ll << 30));
+    if (s != SPH_OK) return s;
+  }
+  return SPH_OK;
+}
+
+sph_status Engine::ensure_tree_capacity(int nodes) {
+  if (nodes <= cap_nodes && t_start.p) return SPH_OK;
+  cap_nodes = nodes;
+  const size_t n = (size_t)nodes;
+  CK(t_start.reserve(n));
+  CK(t_count.reserve(n));
+  CK(t_nsmall.reserve(n));
+  CK(t_axes.reserve(n));
+  CK(t_sortbase.reserve(n));
+  CK(t_key.reserve(n));
+  CK(t_level.reserve(n));
+  CK(t_box.reserve(n));
+  CK(t_child.reserve(n));
+  CK(t_nchild.reserve(n));
+  CK(t_parent.reserve(n));
+  CK(t_split.reserve(n));
+  CK(t_hmax.reserve(n));
+  CK(t_hlim.reserve(n));
+  CK(t_cen.reserve(n));
+  CK(t_n.reserve(8));
+  T.start = t_start.p;
+  T.count = t_count.p;
+  T.key = t_key.p;
+  T.level = t_level.p;
+  T.box = t_box.p;
+  T.child = t_child.p;
+  T.nchild = t_nchild.p;
+  T.parent = t_parent.p;
+  T.split = t_split.p;
+  T.hmax = t_hmax.p;
+  T.nsmall = t_nsmall.p;
+  T.hlim = t_hlim.p;
+  T.cen = t_cen.p;
+  T.axes = t_axes.p;
+  T.sortbase = t_sortbase.p;
+  T.n_nodes = t_n.p;
+  CK(big_node.reserve(1));
+  return ensure_list_capacity(nodes, 8 * nodes, 8 * nodes);
+}
+
+sph_status Engine::ensure_list_capacity(int selfs, int pairs, int queue) {
+  if (selfs > cap_self || !l_self.p) {
+    cap_self = selfs;
+    CK(l_self.reserve(selfs));
+  }
+  if (pairs > cap_pair || !l_pa.p) {
+    cap_pair = pairs;
+    CK(l_pa.reserve(pairs));
+    CK(l_pb.reserve(pairs));
+    CK(l_pax.reserve(pairs));
+  }
+  if (queue > cap_queue || !q_kind[0].p) {
+    cap_queue = queue;
+    for (int k = 0; k < 2; ++k) {
+      CK(q_kind[k].reserve(queue));
+      CK(q_a[k].reserve(queue));
+      CK(q_b[k].reserve(queue));
+      CK(q_ax[k].reserve(queue));
+    }
+  }
+  CK(l_counts.reserve(8));
+  Lq.self_a = l_self.p;
+  Lq.pair_a = l_pa.p;
+  Lq.pair_b = l_pb.p;
+  Lq.pair_axis = l_pax.p;
+  for (int k = 0; k < 2; ++k) {
+    Lq.q_kind[k] = q_kind[k].p;
+    Lq.q_a[k] = q_a[k].p;
+    Lq.q_b[k] = q_b[k].p;
+    Lq.q_axis[k] = q_ax[k].p;
+  }
+  Lq.counts = l_counts.p;
+  return SPH_OK;
+}
+
+sph_status Engine::set_particles(int b, const double* xx, const float* vv, const float* mm, const float* uu,
+                                 const float* hh, int mem) {
+  if (b < 0 || b >= nbox) return fail(SPH_E_INVALID, "box index out of range");
+  if (!xx || !vv || !mm || !uu || !hh) return fail(SPH_E_INVALID, "null input pointer");
+  const cudaMemcpyKind kind = mem == SPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const long long o = off[b], n = spec[b].n;
+  CK(cudaMemcpyAsync(x.p + 3 * o, xx, 3 * n * sizeof(double), kind, st));
+  CK(cudaMemcpyAsync(v.p + 3 * o, vv, 3 * n * sizeof(float), kind, st));
+  CK(cudaMemcpyAsync(m.p + o, mm, n * sizeof(float), kind, st));
+  CK(cudaMemcpyAsync(u.p + o, uu, n * sizeof(float), kind, st));
+  CK(cudaMemcpyAsync(h.p + o, hh, n * sizeof(float), kind, st));
+  built = have_density = have_ghost = have_force = have_acc = false;
+  return SPH_OK;
+}
+
+// ----------------------------------------------------------------------- build
+sph_status Engine::build() {
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    bool retry = false;
+    sph_status s = build_once(&retry);
+    if (!retry) return s;
+  }
+  return fail(SPH_E_OOM, "decomposition lists kept overflowing");
+}
+
+static int ceil_log2(long long v) {
+  int b = 0;
+  while ((1ll << b) < v) ++b;
+  return b;
+}
+
+sph_status Engine::build_once(bool* retry) {
+  *retry = false;
+  built = have_density = have_ghost = have_force = false;
+  if (N == 0) return fail(SPH_E_INVALID, "no particles");
+  // ---- ingest: validation, H = gamma_K h, per-box H extremes
+  for (auto& d : hbox) {
+    d.Hmax = 0.0f;
+    d.Hmin = INFINITY;
+    d.err = 0;
+    d.k = 0;
+  }
+  CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+  k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(hbox.data(), box.p, nbox * sizeof(BoxDesc), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int box_bits = ceil_log2(nbox);
+  int dc = std::min(std::min(prm.max_depth, SPH_MAX_DEPTH), (64 - box_bits) / 3);
+  int need = 0;
+  kmin = 1 << 20;
+  kmax = 0;
+  for (int b = 0; b < nbox; ++b) {
+    BoxDesc& d = hbox[b];
+    if (d.err & ERR_BAD_INPUT)
+      return fail(SPH_E_INVALID, "box " + std::to_string(b) + ": invalid input (NaN, h <= 0, m <= 0, u < 0 or x outside [0, L))");
+    const int k0 = d.periodic ? 2 : 0;
+    if (!((double)d.Hmax < std::ldexp(d.L, -k0) - d.margin))
+      return fail(SPH_E_H_TOO_LARGE, "box " + std::to_string(b) + ": support radius too large for the box (periodic boxes need H < L/4)");
+    int k = k0;
+    while (k + 1 <= dc && (double)d.Hmax < std::ldexp(d.L, -(k + 1)) - d.margin) ++k;
+    d.k = k;
+    kmin = std::min(kmin, k);
+    kmax = std::max(kmax, k);
+    // deepest level a split can reach: more than split_frac of the cell must have H < edge/2
+    const int dn = (int)std::ceil(std::log2(d.L / (double)d.Hmin)) + 1;
+    need = std::max(need, dn);
+  }
+  dcap = std::max(std::min(dc, need), kmax);
+  box_shift = 3 * dcap;
+  key_bits = box_bits + 3 * dcap;
+  CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+
+  // ---- keys and sort
+  k_keys<<<grid(N), 256, 0, st>>>(N, dcap, bid.p, box.p, x.p, key.p, perm.p);
+  radix_sort(key.p, perm.p, key_tmp.p, perm_tmp.p, N, key_bits, rs_scratch.p, st);
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p);
+  CK(cudaGetLastError());
+
+  // ---- cell tree
+  CK(cudaMemsetAsync(t_n.p, 0, 8 * sizeof(int), st));
+  CK(cudaMemsetAsync(top_at.p, 0xff, N * sizeof(int), st));
+  CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  k_top_nodes<<<grid(N), 256, 0, st>>>(N, dcap, box_shift, box.p, key.p, T, cap_nodes, top_at.p, err_all.p);
+  k_frontier_init<<<1, 1, 0, st>>>(T, cap_nodes);
+  const int rounds = dcap - kmin + 1;
+  for (int r = 0; r < rounds; ++r) {
+    k_node_stats<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, dcap, prm.leaf_max, prm.split_frac);
+    if (r + 1 < rounds) {
+      k_split_nodes<<<nsm * 4, 128, 0, st>>>(T, key.p, dcap, box_shift, cap_nodes, err_all.p);
+      k_frontier_next<<<1, 1, 0, st>>>(T, cap_nodes);
+    }
+  }
+  CK(cudaGetLastError());
+  int tn[8];
+  unsigned int ea[4];
+  CK(cudaMemcpyAsync(tn, t_n.p, sizeof(tn), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if ((ea[0] & ERR_OVERFLOW) || tn[0] > cap_nodes) {
+    sph_status s = ensure_tree_capacity(std::max(2 * cap_nodes, tn[0] + 1024));
+    if (s != SPH_OK) return s;
+    *retry = true;
+    return SPH_OK;
+  }
+  n_nodes = tn[0];
+  n_top = tn[3];
+
+  // ---- interaction lists
+  CK(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
+  k_items_top<<<grid(n_top), 256, 0, st>>>(n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
+                                           err_all.p);
+  for (int r = 0; r < rounds; ++r) {
+    const int in = r & 1;
+    CK(cudaMemsetAsync(l_counts.p + 2 + (in ^ 1), 0, sizeof(int), st));
+    k_items_expand<<<nsm * 8, 256, 0, st>>>(in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p);
+  }
+  k_leaves<<<nsm * 8, 256, 0, st>>>(T, n_nodes, leaf_of.p);
+  k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p);
+  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p);
+
+  // ---- sorted projections
+  CK(big_count.reserve(2));
+  if (cap_big == 0) {
+    cap_big = 4096;
+    CK(big_node.reserve(cap_big));
+    CK(big_axis.reserve(cap_big));
+    CK(big_off.reserve(cap_big));
+  }
+  CK(cudaMemsetAsync(big_count.p, 0, 2 * sizeof(int), st));
+  k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T);
+  k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
+                                              cap_big);
+  CK(cudaGetLastError());
+  int lc[8], bc[2];
+  CK(cudaMemcpyAsync(lc, l_counts.p, sizeof(lc), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(bc, big_count.p, sizeof(bc), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int last_q = lc[2 + (rounds & 1)];
+  if ((ea[0] & ERR_OVERFLOW) || lc[0] > cap_self || lc[1] > cap_pair || last_q != 0) {
+    sph_status s = ensure_list_capacity(std::max(cap_self, lc[0]) * 2, std::max(cap_pair, lc[1]) * 2,
+                                        cap_queue * 2);
+    if (s != SPH_OK) return s;
+    *retry = true;
+    return SPH_OK;
+  }
+  if (bc[0] > cap_big) {
+    cap_big = 2 * bc[0];
+    CK(big_node.reserve(cap_big));
+    CK(big_axis.reserve(cap_big));
+    CK(big_off.reserve(cap_big));
+    *retry = true;
+    return SPH_OK;
+  }
+  n_selfs = lc[0];
+  n_pairs = lc[1];
+  n_segments = lc[4];
+  n_entries = (unsigned int)lc[5];
+  n_big = bc[0];
+  n_big_entries = (unsigned int)bc[1];
+  CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
+  CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
+  k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, pos4.p, cen4.p, sort_r.p, sort_i.p);
+  if (n_big > 0) {
+    const size_t nb = (size_t)n_big_entries;
+    CK(ckey.reserve(nb));
+    CK(ckey_tmp.reserve(nb));
+    CK(cval.reserve(nb));
+    CK(cval_tmp.reserve(nb));
+    if (rs_scratch.n < (size_t)radix_scratch_words(nb)) CK(rs_scratch.reserve(radix_scratch_words(nb)));
+    k_sort_big_keys<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, pos4.p,
+                                                              cen4.p, ckey.p, cval.p);
+    radix_sort(ckey.p, cval.p, ckey_tmp.p, cval_tmp.p, (long long)nb, 32 + std::max(1, ceil_log2(n_big)),
+               rs_scratch.p, st);
+    k_sort_big_scatter<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T,
+                                                                 pos4.p, cen4.p, cval.p, sort_r.p, sort_i.p);
+  }
+  CK(cudaGetLastError());
+  depth_used = 0;
+  built = true;
+  return SPH_OK;
+}
+
+// ----------------------------------------------------------------------- passes
+sph_status Engine::set_all_active() {
+  launch_set_active(*this);
+  CK(cudaGetLastError());
+  return SPH_OK;
+}
+
+sph_status Engine::density_pass() {
+  launch_zero_density(*this, false);
+  launch_density(*this);
+  CK(cudaGetLastError());
+  return SPH_OK;
+}
+
+sph_status Engine::density() {
+  if (!built) {
+    sph_status s = build();
+    if (s != SPH_OK) return s;
+  }
+  if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 8 * sizeof(unsigned long long), st));
+  sph_status s = set_all_active();
+  if (s != SPH_OK) return s;
+  s = density_pass();
+  if (s != SPH_OK) return s;
+  CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+  launch_ghost(*this, 0, 1);
+  CK(cudaGetLastError());
+  have_density = have_ghost = true;
+  have_force = false;
+  last_iters = 1;
+  last_rebuilds = 0;
+  return SPH_OK;
+}
+
+sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
+  if (!built) {
+    sph_status s = build();
+    if (s != SPH_OK) return s;
+  }
+  if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 8 * sizeof(unsigned long long), st));
+  launch_bracket_reset(*this);
+  sph_status s = set_all_active();
+  if (s != SPH_OK) return s;
+  int it = 0, rebuilds = 0, n_active = 0;
+  for (it = 1; it <= prm.h_max_iter; ++it) {
+    s = density_pass();
+    if (s != SPH_OK) return s;
+    CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+    CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+    launch_ghost(*this, 1, it);
+    CK(cudaGetLastError());
+    unsigned int ea = 0;
+    CK(cudaMemcpyAsync(&n_active, dev_counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_active == 0) break;
+    if (ea & ERR_REBUILD) {
+      s = build();   // the input-order h carries the iteration's state
+      if (s != SPH_OK) return s;
+      s = set_all_active();
+      if (s != SPH_OK) return s;
+      ++rebuilds;
+    }
+  }
+  if (it > prm.h_max_iter) it = prm.h_max_iter;
+  // particles that never converged
+  std::vector<int> hc(N);
+  CK(cudaMemcpyAsync(hc.data(), conv.p, N * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  long long nu = 0;
+  for (long long p = 0; p < N; ++p) nu += hc[p] ? 0 : 1;
+  last_iters = it;
+  last_rebuilds = rebuilds;
+  last_unconverged = nu;
+  if (n_unconverged) *n_unconverged = nu;
+  if (iterations) *iterations = it;
+  have_density = have_ghost = true;
+  have_force = false;
+  if (nu > 0) return fail(SPH_E_NOT_CONVERGED, std::to_string(nu) + " particles did not converge");
+  return SPH_OK;
+}
+
+sph_status Engine::force() {
+  if (!have_ghost) return fail(SPH_E_NOT_BUILT, "force pass needs a density pass first");
+  CK(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
+  CK(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
+  launch_force(*this);
+  launch_reduce(*this);
+  launch_save_acc(*this);
+  CK(cudaGetLastError());
+  have_force = true;
+  have_acc = true;
+  return SPH_OK;
+}
+
+sph_status Engine::upload_boxes() {
+  CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+  return SPH_OK;
+}
+
+sph_status Engine::step(double dt) {
+  for (auto& d : hbox) d.dt = dt;
+  return step_boxes();
+}
+
+// Kick-drift-kick (Section III-B: fixed time step, forces on all particles every
+// step): v += a dt/2, u += du/dt dt/2 with the forces of the previous step, x +=
+// v dt in FP64, then build, density with h iteration, force and reductions at
+// the new positions, and the closing half kick.  Boxes with dt = 0 only run the
+// passes.  The first call computes the starting forces.
+sph_status Engine::step_boxes() {
+  sph_status s;
+  bool moving = false;
+  for (auto& d : hbox) moving |= d.dt > 0.0;
+  if (moving && !have_acc) {
+    s = build();
+    if (s != SPH_OK) return s;
+    s = h_update(nullptr, nullptr);
+    if (s != SPH_OK && s != SPH_E_NOT_CONVERGED) return s;
+    s = force();
+    if (s != SPH_OK) return s;
+  }
+  if (moving) {
+    s = upload_boxes();
+    if (s != SPH_OK) return s;
+    launch_kick(*this);
+    launch_drift(*this);
+    CK(cudaGetLastError());
+  }
+  s = build();
+  if (s != SPH_OK) return s;
+  sph_status hs = h_update(nullptr, nullptr);
+  if (hs != SPH_OK && hs != SPH_E_NOT_CONVERGED) return hs;
+  s = force();
+  if (s != SPH_OK) return s;
+  if (moving) {
+    launch_kick(*this);
+    CK(cudaGetLastError());
+  }
+  return hs;
+}
+
+sph_status Engine::cfl_dt(int b, double* dt) {
+  if (!have_force) return fail(SPH_E_NOT_BUILT, "cfl_dt needs a force pass");
+  const long long o = off[b], n = spec[b].n;
+  std::vector<float> H(n), vs(n);
+  CK(cudaMemcpyAsync(H.data(), Hs.p + o, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(vs.data(), fvsig.p + o, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double hmin = INFINITY, vmax = 0.0;
+  for (long long p = 0; p < n; ++p) {
+    hmin = std::min(hmin, (double)H[p]);
+    vmax = std::max(vmax, (double)vs[p]);
+  }
+  *dt = vmax > 0 ? prm.c_cfl * hmin / vmax : INFINITY;
+  return SPH_OK;
+}
+
+// ----------------------------------------------------------------------- outputs
+sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
+  if (b < 0 || b >= nbox) return fail(SPH_E_INVALID, "box index out of range");
+  if (!dst) return fail(SPH_E_INVALID, "null destination");
+  const long long o = off[b], nb = spec[b].n;
+  const cudaMemcpyKind kind = mem == SPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (field == SPH_FIELD_REDUCTIONS) {
+    if (n != 8) return fail(SPH_E_INVALID, "reductions need n = 8");
+    if (!have_force) return fail(SPH_E_NOT_BUILT, "no force pass yet");
+    CK(cudaMemcpyAsync(dst, red.p + 8 * b, 8 * sizeof(double), kind, st));
+    if (mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
+    return SPH_OK;
+  }
+  if (n != nb) return fail(SPH_E_INVALID, "n does not match the box's particle count");
+  size_t bytes = 0;
+  const void* src = nullptr;
+  switch (field) {
+    case SPH_FIELD_X: src = x.p + 3 * o; bytes = 3 * nb * sizeof(double); break;
+    case SPH_FIELD_V: src = v.p + 3 * o; bytes = 3 * nb * sizeof(float); break;
+    case SPH_FIELD_U: src = u.p + o; bytes = nb * sizeof(float); break;
+    case SPH_FIELD_H: src = h.p + o; bytes = nb * sizeof(float); break;
+    case SPH_FIELD_CONVERGED:
+      if (!have_density) return fail(SPH_E_NOT_BUILT, "no density pass yet");
+      src = conv.p + o; bytes = nb * sizeof(int); break;
+    default: break;
+  }
+  if (src) {
+    CK(cudaMemcpyAsync(dst, src, bytes, kind, st));
+    if (mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
+    return SPH_OK;
+  }
+  int per = 1;
+  switch (field) {
+    case SPH_FIELD_RHO: case SPH_FIELD_DRHO_DH: case SPH_FIELD_NW: case SPH_FIELD_NNGB: case SPH_FIELD_COUNT:
+      if (!have_density) return fail(SPH_E_NOT_BUILT, "no density pass yet");
+      break;
+    case SPH_FIELD_P: case SPH_FIELD_C: case SPH_FIELD_F:
+      if (!have_ghost) return fail(SPH_E_NOT_BUILT, "no ghost pass yet");
+      break;
+    case SPH_FIELD_A: per = 3;  // fallthrough
+    case SPH_FIELD_DUDT: case SPH_FIELD_VSIG:
+      if (!have_force) return fail(SPH_E_NOT_BUILT, "no force pass yet");
+      break;
+    default: return fail(SPH_E_INVALID, "unknown field");
+  }
+  void* out = mem == SPH_MEM_DEVICE ? dst : (void*)staging.p;
+  launch_get_field(*this, o, nb, field, out);
+  CK(cudaGetLastError());
+  if (mem != SPH_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(dst, staging.p, per * nb * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return SPH_OK;
+}
+
+sph_status Engine::stats(int b, sph_stats* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->n_particles = spec[b].n;
+  o->n_cells = n_nodes;
+  o->n_selfs = n_selfs;
+  o->n_leaves = n_selfs;
+  o->n_pairs = n_pairs;
+  o->n_sort_segments = n_segments;
+  o->n_sorted_entries = n_entries;
+  o->top_level = hbox.empty() ? 0 : hbox[b].k;
+  o->depth = dcap;
+  o->h_iterations = last_iters;
+  o->rebuilds = last_rebuilds;
+  o->n_unconverged = last_unconverged;
+  if (count_pairs) {
+    unsigned long long c[8];
+    CK(cudaMemcpyAsync(c, pc.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    o->density_pairs = (long long)c[0];
+    o->density_sides = (long long)c[1];
+    o->density_candidates = (long long)c[2];
+    o->force_pairs = (long long)c[3];
+    o->force_candidates = (long long)c[4];
+    o->guard_rechecks = (long long)c[5];
+  }
+  return SPH_OK;
+}
+
+sph_status Engine::cells(int b, long long cap, int* level, int* ijk, int* count, int* split, long long* n_out) {
+  if (!built) return fail(SPH_E_NOT_BUILT, "no decomposition built");
+  std::vector<int> lv(n_nodes), bx(n_nodes), sp(n_nodes);
+  std::vector<unsigned int> ct(n_nodes);
+  std::vector<unsigned long long> ky(n_nodes);
+  CK(cudaMemcpyAsync(lv.data(), t_level.p, n_nodes * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(bx.data(), t_box.p, n_nodes * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(sp.data(), t_split.p, n_nodes * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ct.data(), t_count.p, n_nodes * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ky.data(), t_key.p, n_nodes * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  long long k = 0;
+  for (int id = 0; id < n_nodes; ++id) {
+    if (bx[id] != b) continue;
+    if (k < cap) {
+      const int d = lv[id];
+      const unsigned long long mort = d > 0 ? (ky[id] & ((1ull << (3 * d)) - 1ull)) : 0ull;
+      if (level) level[k] = d;
+      if (ijk) {
+        ijk[3 * k] = (int)compact3(mort);
+        ijk[3 * k + 1] = (int)compact3(mort >> 1);
+        ijk[3 * k + 2] = (int)compact3(mort >> 2);
+      }
+      if (count) count[k] = (int)ct[id];
+      if (split) split[k] = sp[id];
+    }
+    ++k;
+  }
+  *n_out = k;
+  return SPH_OK;
+}
+
+sph_status Engine::interactions(int b, long long cap, int* kind, int* a, int* bb, int* axis, long long* n_out) {
+  if (!built) return fail(SPH_E_NOT_BUILT, "no decomposition built");
+  std::vector<int> bx(n_nodes), sa(n_selfs), pa(n_pairs), pb(n_pairs), pax(n_pairs);
+  CK(cudaMemcpyAsync(bx.data(), t_box.p, n_nodes * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (n_selfs) CK(cudaMemcpyAsync(sa.data(), l_self.p, n_selfs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (n_pairs) {
+    CK(cudaMemcpyAsync(pa.data(), l_pa.p, n_pairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(pb.data(), l_pb.p, n_pairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(pax.data(), l_pax.p, n_pairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  std::vector<int> local(n_nodes, -1);
+  int c = 0;
+  for (int id = 0; id < n_nodes; ++id)
+    if (bx[id] == b) local[id] = c++;
+  long long k = 0;
+  auto put = [&](int kd, int x0, int x1, int ax) {
+    if (k < cap) {
+      if (kind) kind[k] = kd;
+      if (a) a[k] = x0;
+      if (bb) bb[k] = x1;
+      if (axis) axis[k] = ax;
+    }
+    ++k;
+  };
+  for (int i = 0; i < n_selfs; ++i)
+    if (bx[sa[i]] == b) put(0, local[sa[i]], -1, -1);
+  for (int i = 0; i < n_pairs; ++i)
+    if (bx[pa[i]] == b) put(1, local[pa[i]], local[pb[i]], pax[i]);
+  *n_out = k;
+  return SPH_OK;
+}
+
+}  // namespace sph
+
+// =============================================================================== C-ABI
+using sph::Engine;
+
+struct sph_box {
+  sph_ctx* ctx = nullptr;
+  Engine* eng = nullptr;
+};
+
+static sph_status set_err(sph_ctx* c, sph_status s, const std::string& msg) {
+  if (c) {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->last = msg;
+  }
+  return s;
+}
+
+static sph_status from_engine(sph_box* b, sph_status s) {
+  if (s != SPH_OK && b && b->ctx) set_err(b->ctx, s, b->eng->err);
+  return s;
+}
+
+extern "C" {
+
+void sph_params_default(sph_params* p) {
+  if (!p) return;
+  p->gamma_kernel = 1.825742f;
+  p->n_ngb = 48.0f;
+  p->gamma_gas = 5.0f / 3.0f;
+  p->alpha_visc = 2.0f;
+  p->c_cfl = 0.3f;
+  p->h_tol = 1e-4f;
+  p->h_max_iter = 30;
+  p->leaf_max = 400;
+  p->split_frac = 0.875f;
+  p->max_depth = 20;
+}
+
+sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
+  if (!out) return SPH_E_INVALID;
+  *out = nullptr;
+  sph_params p;
+  sph_params_default(&p);
+  if (params) p = *params;
+  if (!(p.gamma_kernel > 0) || !(p.n_ngb > 0) || !(p.gamma_gas > 1) || p.h_max_iter < 1 || p.leaf_max < 1 ||
+      !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0))
+    return SPH_E_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) return SPH_E_CUDA;
+  sph_ctx* c = new sph_ctx;
+  c->prm = p;
+  c->device = device;
+  if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return SPH_E_CUDA;
+  }
+  c->cur = c->own;
+  *out = c;
+  return SPH_OK;
+}
+
+sph_status sph_ctx_set_stream(sph_ctx* c, void* stream) {
+  if (!c) return SPH_E_INVALID;
+  c->cur = stream ? (cudaStream_t)stream : c->own;
+  return SPH_OK;
+}
+
+void* sph_ctx_stream(sph_ctx* c) { return c ? (void*)c->cur : nullptr; }
+
+sph_status sph_ctx_destroy(sph_ctx* c) {
+  if (!c) return SPH_E_INVALID;
+  cudaSetDevice(c->device);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+  return SPH_OK;
+}
+
+const char* sph_last_error(sph_ctx* c) { return c ? c->last.c_str() : "null context"; }
+
+sph_status sph_box_create(sph_ctx* c, int64_t n, double L, int periodic, sph_box** out) {
+  if (!c || !out) return SPH_E_INVALID;
+  *out = nullptr;
+  if (n < 1 || n > (1ll << 31) - 1 || !(L > 0) || !std::isfinite(L))
+    return set_err(c, SPH_E_INVALID, "box needs 1 <= n < 2^31 particles and a finite L > 0");
+  cudaSetDevice(c->device);
+  sph_box* b = new sph_box;
+  b->ctx = c;
+  b->eng = new Engine(c->prm, c->device, c->cur);
+  sph_status s = b->eng->set_boxes({sph::BoxSpec{L, n, periodic ? 1 : 0}});
+  if (s != SPH_OK) {
+    set_err(c, s, b->eng->err);
+    delete b->eng;
+    delete b;
+    return s == SPH_E_CUDA ? SPH_E_OOM : s;
+  }
+  *out = b;
+  return SPH_OK;
+}
+
+#define BOX_PRE(b)                       \
+  if (!(b) || !(b)->eng) return SPH_E_INVALID; \
+  cudaSetDevice((b)->ctx->device);       \
+  (b)->eng->st = (b)->ctx->cur;
+
+sph_status sph_box_set(sph_box* b, const double* x, const float* v, const float* m, const float* u, const float* h,
+                       int mem) {
+  BOX_PRE(b);
+  return from_engine(b, b->eng->set_particles(0, x, v, m, u, h, mem));
+}
+
+sph_status sph_box_count_pairs(sph_box* b, int on) {
+  BOX_PRE(b);
+  b->eng->count_pairs = on != 0;
+  return SPH_OK;
+}
+
+sph_status sph_box_destroy(sph_box* b) {
+  if (!b) return SPH_E_INVALID;
+  cudaSetDevice(b->ctx->device);
+  cudaStreamSynchronize(b->ctx->cur);
+  delete b->eng;
+  delete b;
+  return SPH_OK;
+}
+
+sph_status sph_build(sph_box* b) {
+  BOX_PRE(b);
+  return from_engine(b, b->eng->build());
+}
+
+sph_status sph_density(sph_box* b) {
+  BOX_PRE(b);
+  return from_engine(b, b->eng->density());
+}
+
+sph_status sph_h_update(sph_box* b, int64_t* n_unconverged, int32_t* iterations) {
+  BOX_PRE(b);
+  long long nu = 0;
+  int it = 0;
+  sph_status s = b->eng->h_update(&nu, &it);
+  if (n_unconverged) *n_unconverged = nu;
+  if (iterations) *iterations = it;
+  return from_engine(b, s);
+}
+
+sph_status sph_force(sph_box* b) {
+  BOX_PRE(b);
+  return from_engine(b, b->eng->force());
+}
+
+sph_status sph_step(sph_box* b, double dt) {
+  BOX_PRE(b);
+  if (!(dt >= 0) || !std::isfinite(dt)) return set_err(b->ctx, SPH_E_INVALID, "dt must be finite and >= 0");
+  return from_engine(b, b->eng->step(dt));
+}
+
+sph_status sph_cfl_dt(sph_box* b, double* dt) {
+  BOX_PRE(b);
+  if (!dt) return SPH_E_INVALID;
+  return from_engine(b, b->eng->cfl_dt(0, dt));
+}
+
+sph_status sph_get(sph_box* b, int field, void* dst, int64_t n, int mem) {
+  BOX_PRE(b);
+  return from_engine(b, b->eng->get(0, field, dst, n, mem));
+}
+
+sph_status sph_get_stats(sph_box* b, sph_stats* out) {
+  BOX_PRE(b);
+  if (!out) return SPH_E_INVALID;
+  return from_engine(b, b->eng->stats(0, out));
+}
+
+sph_status sph_get_cells(sph_box* b, int64_t cap, int32_t* level, int32_t* ijk, int32_t* count, int32_t* split,
+                         int64_t* n_out) {
+  BOX_PRE(b);
+  if (!n_out) return SPH_E_INVALID;
+  long long n = 0;
+  sph_status s = b->eng->cells(0, cap, level, ijk, count, split, &n);
+  *n_out = n;
+  return from_engine(b, s);
+}
+
+sph_status sph_get_interactions(sph_box* b, int64_t cap, int32_t* kind, int32_t* a, int32_t* bb, int32_t* axis,
+                                int64_t* n_out) {
+  BOX_PRE(b);
+  if (!n_out) return SPH_E_INVALID;
+  long long n = 0;
+  sph_status s = b->eng->interactions(0, cap, kind, a, bb, axis, &n);
+  *n_out = n;
+  return from_engine(b, s);
+}
+
+}  // extern "C"

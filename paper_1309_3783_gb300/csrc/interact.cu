@@ -1,0 +1,880 @@
+// Density and force passes (Section II: two interaction stages), the ghost /
+// h-update step between them, the FP64 conservation reductions and the
+// per-field output gathers.
+//
+// Pair-interactions follow the sorted cell-pair interaction of Section II-C
+// (Fig. 3) with warp granularity: a warp takes a pair (A, B); particles of both
+// cells are read in their sorted order along the axis joining the cell
+// centres; the warp walks i-tiles of A from the interface outwards and, for
+// each, j-tiles of B from the interface outwards, and stops as soon as the
+// projected gap exceeds every support radius that could still bridge it.
+// Inside a 32 x 32 tile every lane evaluates one (i, j) pair per step on a
+// rotating diagonal, so both sides of a pair are updated once without
+// conflicts (the pair is found once and used symmetrically, Section II-D).
+#include "sph_engine.h"
+
+#include <cfloat>
+
+namespace sph {
+
+constexpr float BAND_REL = 7.62939453125e-06f;  // 2^-17: guard band of the FP32 predicate
+
+struct ItemGeom {
+  float e;          // cell edge (units of L)
+  float3 offB;      // centre of B minus centre of A (units of L), exact: e * db
+  float offBp;      // projection of offB on the axis: e |db|
+  float invL;
+  double L, halfL;
+  int periodic;
+};
+
+__device__ __forceinline__ ItemGeom item_geom(const Tree& T, const BoxDesc* box, int A, int ax) {
+  ItemGeom g;
+  const int d = T.level[A];
+  const BoxDesc bd = box[T.box[A]];
+  g.e = ldexpf(1.0f, -d);
+  int dx, dy, dz;
+  axis_vec(ax, dx, dy, dz);
+  g.offB = make_float3(g.e * dx, g.e * dy, g.e * dz);
+  const int n2 = dx * dx + dy * dy + dz * dz;
+  g.offBp = g.e * (n2 == 1 ? 1.0f : (n2 == 2 ? 1.41421356237f : 1.73205080757f));
+  g.invL = (float)bd.invL;
+  g.L = bd.L;
+  g.halfL = 0.5 * bd.L;
+  g.periodic = bd.periodic;
+  return g;
+}
+
+// Exact decision r_ij < H (physical H) from the caller's FP64 positions.
+__device__ __noinline__ bool exact_less(int gi, int gj, float Hphys, const unsigned int* __restrict__ perm,
+                                        const double* __restrict__ x, double L, double halfL, int periodic) {
+  const long long i = perm[gi], j = perm[gj];
+  const double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  const double xj[3] = {x[3 * j], x[3 * j + 1], x[3 * j + 2]};
+  return canonical_less(canonical_r2(xi, xj, L, halfL, periodic), Hphys);
+}
+
+// FP32 test with guard band; inside the band the FP64 decision is taken.
+__device__ __forceinline__ bool decide(float r2, float H2, float band, int gi, int gj, float Hphys,
+                                       const unsigned int* perm, const double* x, const ItemGeom& g,
+                                       unsigned int& rechecks) {
+  const float dl = r2 - H2;
+  if (dl < -band) return true;
+  if (dl > band) return false;
+  ++rechecks;
+  return exact_less(gi, gj, Hphys, perm, x, g.L, g.halfL, g.periodic);
+}
+
+// Axis-aligned box of a warp's tile and the separation between two tiles.
+struct TileBox {
+  float lx, ly, lz, hx, hy, hz;
+};
+__device__ __forceinline__ TileBox tile_box(bool valid, float3 p) {
+  TileBox b;
+  b.lx = warp_min(valid ? p.x : FLT_MAX);
+  b.ly = warp_min(valid ? p.y : FLT_MAX);
+  b.lz = warp_min(valid ? p.z : FLT_MAX);
+  b.hx = warp_max(valid ? p.x : -FLT_MAX);
+  b.hy = warp_max(valid ? p.y : -FLT_MAX);
+  b.hz = warp_max(valid ? p.z : -FLT_MAX);
+  return b;
+}
+__device__ __forceinline__ float tile_gap(const TileBox& a, const TileBox& b) {
+  const float gx = fmaxf(0.0f, fmaxf(b.lx - a.hx, a.lx - b.hx));
+  const float gy = fmaxf(0.0f, fmaxf(b.ly - a.hy, a.ly - b.hy));
+  const float gz = fmaxf(0.0f, fmaxf(b.lz - a.hz, a.lz - b.hz));
+  return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+}
+
+// =========================================================================== density
+struct DensI {
+  float3 p;
+  float invH, H2, band, Hphys, m;
+  int g;
+  bool valid, act;
+};
+
+__device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
+                                           const float4* cen4, const unsigned char* act, float invL, float e) {
+  DensI r;
+  r.valid = valid;
+  if (valid) {
+    const float4 p = pos4[gidx];
+    const float4 c = cen4[gidx];
+    // the cell offsets (c + shift) are exact dyadic values: add them first, round once
+    r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
+    const float H = p.w * invL;
+    r.invH = 1.0f / H;
+    r.H2 = H * H;
+    r.band = BAND_REL * H * (e + H);
+    r.Hphys = p.w;
+    r.m = c.w;
+    r.g = (int)gidx;
+    r.act = act[gidx] != 0;
+  } else {
+    r.p = make_float3(1e30f, 1e30f, 1e30f);
+    r.invH = 0.0f;
+    r.H2 = -1.0f;
+    r.band = 0.0f;
+    r.Hphys = 0.0f;
+    r.m = 0.0f;
+    r.g = -1;
+    r.act = false;
+  }
+  return r;
+}
+
+struct DensShared {
+  float4 p[32];     // position, 1/H (units of L)
+  float4 a[32];     // H^2, band, m, H (physical)
+  float4 acc[32];   // sum m w, sum m g, sum w, sum g
+  unsigned int cnt[32];
+  int g[32];
+  unsigned char act[32];
+};
+
+__device__ __forceinline__ void dens_put(DensShared& S, int lane, const DensI& j) {
+  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.invH);
+  S.a[lane] = make_float4(j.H2, j.band, j.m, j.Hphys);
+  S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.cnt[lane] = 0;
+  S.g[lane] = j.g;
+  S.act[lane] = j.act ? 1 : 0;
+}
+
+struct Counters {
+  unsigned int cand = 0, pairs = 0, sides = 0, rechecks = 0;
+};
+
+// one diagonal step of a density tile: lane pairs i with shared entry k
+template <bool COUNT>
+__device__ __forceinline__ void dens_step(const DensI& I, DensShared& S, int k, float4& acc, unsigned int& cnt,
+                                          const unsigned int* perm, const double* x, const ItemGeom& g,
+                                          Counters& C) {
+  const float4 J = S.p[k];
+  const float4 Ja = S.a[k];
+  if (!(I.valid && Ja.w > 0.0f)) return;
+  const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  unsigned int rc = 0;
+  const bool pI = decide(r2, I.H2, I.band, I.g, S.g[k], I.Hphys, perm, x, g, rc);
+  const bool pJ = decide(r2, Ja.x, Ja.y, I.g, S.g[k], Ja.w, perm, x, g, rc);
+  if (COUNT) {
+    C.cand++;
+    C.rechecks += rc;
+    C.pairs += (pI || pJ) ? 1u : 0u;
+    C.sides += (pI ? 1u : 0u) + (pJ ? 1u : 0u);
+  }
+  if (!(pI || pJ)) return;
+  const float r = sqrtf(r2);
+  if (pI && I.act) {
+    float w, dw;
+    const float q = r * I.invH;
+    spline_w_dw(q, w, dw);
+    const float gg = fmaf(q, dw, 3.0f * w);
+    acc.x = fmaf(Ja.z, w, acc.x);
+    acc.y = fmaf(Ja.z, gg, acc.y);
+    acc.z += w;
+    acc.w += gg;
+    cnt++;
+  }
+  if (pJ && S.act[k]) {
+    float w, dw;
+    const float q = r * J.w;
+    spline_w_dw(q, w, dw);
+    const float gg = fmaf(q, dw, 3.0f * w);
+    float4 a = S.acc[k];
+    a.x = fmaf(I.m, w, a.x);
+    a.y = fmaf(I.m, gg, a.y);
+    a.z += w;
+    a.w += gg;
+    S.acc[k] = a;
+    S.cnt[k]++;
+  }
+}
+
+__device__ __forceinline__ void flush_dens(int gidx, float4 acc, unsigned int cnt, float4* dacc, unsigned int* dcnt) {
+  if (gidx < 0 || cnt == 0) return;
+  atomicAdd(&dacc[gidx], acc);
+  atomicAdd(&dcnt[gidx], cnt);
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void commit_counters(const Counters& C, unsigned long long* pc, int which) {
+  if (!COUNT) return;
+  // pc layout: PairCounters {dens_pairs, dens_sides, dens_cand, force_pairs, force_cand, rechecks}
+  unsigned long long c = C.cand, p = C.pairs, s = C.sides, r = C.rechecks;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    p += __shfl_xor_sync(0xffffffffu, p, o);
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (which == 0) {
+      atomicAdd(&pc[0], p);
+      atomicAdd(&pc[1], s);
+      atomicAdd(&pc[2], c);
+    } else {
+      atomicAdd(&pc[3], p);
+      atomicAdd(&pc[4], c);
+    }
+    atomicAdd(&pc[5], r);
+  }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_pair, Tree T,
+                                                              const BoxDesc* __restrict__ box,
+                                                              const float4* __restrict__ pos4,
+                                                              const float4* __restrict__ cen4,
+                                                              const float* __restrict__ sort_r,
+                                                              const unsigned int* __restrict__ sort_i,
+                                                              const unsigned char* __restrict__ act,
+                                                              const unsigned int* __restrict__ perm,
+                                                              const double* __restrict__ x, float4* dacc,
+                                                              unsigned int* dcnt, unsigned long long* pc) {
+  __shared__ DensShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  DensShared& S = SH[wl];
+  Counters C;
+  const int npair = min(Lq.counts[1], cap_pair);
+  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < npair; item += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int A = Lq.pair_a[item], B = Lq.pair_b[item], ax = Lq.pair_axis[item];
+    const ItemGeom g = item_geom(T, box, A, ax);
+    const unsigned int nA = T.count[A], nB = T.count[B], sA = T.start[A], sB = T.start[B];
+    const unsigned int bit = (1u << ax) - 1u;
+    const unsigned int oA = T.sortbase[A] + (unsigned int)__popc(T.axes[A] & bit) * nA;
+    const unsigned int oB = T.sortbase[B] + (unsigned int)__popc(T.axes[B] & bit) * nB;
+    const float4 cA = T.cen[A], cB = T.cen[B];
+    const float3 shA = make_float3(-cA.x, -cA.y, -cA.z);
+    const float3 shB = make_float3(g.offB.x - cB.x, g.offB.y - cB.y, g.offB.z - cB.z);
+    const float HmA = T.hmax[A] * g.invL, HmB = T.hmax[B] * g.invL;
+    const float slack = g.e * 1.52587890625e-05f + 1e-6f * fmaxf(HmA, HmB);   // 2^-16 e
+    const float rB0 = sort_r[oB] + g.offBp;
+    for (int it = (int)((nA - 1) >> 5); it >= 0; --it) {
+      const unsigned int ii = (unsigned int)it * 32u + lane;
+      const bool vi = ii < nA;
+      const DensI I = load_dens(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, act, g.invL, g.e);
+      const float ri = vi ? sort_r[oA + ii] : -FLT_MAX;
+      const float maxri = warp_max(ri);
+      if (rB0 - maxri > fmaxf(HmA, HmB) + slack) break;      // this and every lower tile is out of reach
+      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
+      const TileBox bi = tile_box(vi, I.p);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned int cnt = 0;
+      for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
+        const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
+        if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;  // sorted: every later j is further away
+        const unsigned int jj = jt * 32u + lane;
+        const bool vj = jj < nB;
+        const DensI J = load_dens(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, act, g.invL, g.e);
+        const TileBox bj = tile_box(vj, J.p);
+        const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
+        if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
+        dens_put(S, lane, J);
+        __syncwarp();
+        for (int s = 0; s < 32; ++s) {
+          dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
+          __syncwarp();
+        }
+        flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+        __syncwarp();
+      }
+      flush_dens(I.g, acc, cnt, dacc, dcnt);
+    }
+  }
+  commit_counters<COUNT>(C, pc, 0);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_self, Tree T,
+                                                              const BoxDesc* __restrict__ box,
+                                                              const float4* __restrict__ pos4,
+                                                              const float4* __restrict__ cen4,
+                                                              const unsigned char* __restrict__ act,
+                                                              const unsigned int* __restrict__ perm,
+                                                              const double* __restrict__ x, float4* dacc,
+                                                              unsigned int* dcnt, unsigned long long* pc) {
+  __shared__ DensShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  DensShared& S = SH[wl];
+  Counters C;
+  const int nself = min(Lq.counts[0], cap_self);
+  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < nself; item += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int A = Lq.self_a[item];
+    const ItemGeom g = item_geom(T, box, A, 0);
+    const unsigned int n = T.count[A], s0 = T.start[A];
+    const float4 cA = T.cen[A];
+    const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
+    const float slack = g.e * 1.52587890625e-05f;
+    const int nt = (int)((n + 31) >> 5);
+    for (int it = 0; it < nt; ++it) {
+      const unsigned int ii = (unsigned int)it * 32u + lane;
+      const bool vi = ii < n;
+      const DensI I = load_dens(vi, s0 + ii, sh, pos4, cen4, act, g.invL, g.e);
+      const TileBox bi = tile_box(vi, I.p);
+      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned int cnt = 0;
+      for (int jt = it; jt < nt; ++jt) {
+        const unsigned int jj = (unsigned int)jt * 32u + lane;
+        const bool vj = jj < n;
+        const DensI J = load_dens(vj, s0 + jj, sh, pos4, cen4, act, g.invL, g.e);
+        if (jt != it) {
+          const TileBox bj = tile_box(vj, J.p);
+          const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
+          if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
+        }
+        dens_put(S, lane, J);
+        __syncwarp();
+        if (jt == it) {
+          // pairs inside one tile: steps 1..16, the 16th on half the lanes
+          for (int s = 1; s <= 16; ++s) {
+            if (s < 16 || lane < 16) dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
+            __syncwarp();
+          }
+        } else {
+          for (int s = 0; s < 32; ++s) {
+            dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
+            __syncwarp();
+          }
+        }
+        flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+        __syncwarp();
+      }
+      flush_dens(I.g, acc, cnt, dacc, dcnt);
+    }
+  }
+  commit_counters<COUNT>(C, pc, 0);
+}
+
+// =========================================================================== force
+struct ForceI {
+  float3 p;
+  float invH, H2, band, Hphys, m;
+  float3 v;
+  float rho, F, c, K4;
+  int g;
+  bool valid;
+};
+
+__device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
+                                             const float4* cen4, const float4* vel4, const float4* ghost4,
+                                             float invL, float e) {
+  ForceI r;
+  r.valid = valid;
+  if (valid) {
+    const float4 p = pos4[gidx];
+    const float4 c = cen4[gidx];
+    const float4 vv = vel4[gidx];
+    const float4 gh = ghost4[gidx];
+    // the cell offsets (c + shift) are exact dyadic values: add them first, round once
+    r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
+    const float H = p.w * invL;
+    r.invH = 1.0f / H;
+    r.H2 = H * H;
+    r.band = BAND_REL * H * (e + H);
+    r.Hphys = p.w;
+    r.m = c.w;
+    r.v = make_float3(vv.x, vv.y, vv.z);
+    r.rho = gh.x;
+    r.F = gh.y;
+    r.c = gh.z;
+    const float ih = 1.0f / p.w;
+    r.K4 = SPH_KNORM * (ih * ih) * (ih * ih);
+    r.g = (int)gidx;
+  } else {
+    r.p = make_float3(1e30f, 1e30f, 1e30f);
+    r.invH = 0.f;
+    r.H2 = -1.f;
+    r.band = 0.f;
+    r.Hphys = 0.f;
+    r.m = 0.f;
+    r.v = make_float3(0.f, 0.f, 0.f);
+    r.rho = 1.f;
+    r.F = 0.f;
+    r.c = 0.f;
+    r.K4 = 0.f;
+    r.g = -1;
+  }
+  return r;
+}
+
+struct ForceShared {
+  float4 p[32];    // position, 1/H
+  float4 a[32];    // H^2, band, m, H (physical)
+  float4 v[32];    // velocity, rho
+  float4 f[32];    // f P / rho^2, c, K/H^4, -
+  float4 acc[32];  // a (3), du/dt
+  float vs[32];
+  int g[32];
+};
+
+__device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
+  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.invH);
+  S.a[lane] = make_float4(j.H2, j.band, j.m, j.Hphys);
+  S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
+  S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
+  S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.vs[lane] = 0.f;
+  S.g[lane] = j.g;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void force_step(const ForceI& I, ForceShared& S, int k, float4& acc, float& vsig_i,
+                                           const unsigned int* perm, const double* x, const ItemGeom& g,
+                                           float alpha, Counters& C) {
+  const float4 J = S.p[k];
+  const float4 Ja = S.a[k];
+  if (!(I.valid && Ja.w > 0.0f)) return;
+  const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  unsigned int rc = 0;
+  const bool pI = decide(r2, I.H2, I.band, I.g, S.g[k], I.Hphys, perm, x, g, rc);
+  const bool pJ = decide(r2, Ja.x, Ja.y, I.g, S.g[k], Ja.w, perm, x, g, rc);
+  if (COUNT) {
+    C.cand++;
+    C.rechecks += rc;
+    C.pairs += ((pI || pJ) && r2 > 0.0f) ? 1u : 0u;
+  }
+  if (!(pI || pJ) || !(r2 > 0.0f)) return;
+  const float4 Jv = S.v[k];
+  const float4 Jf = S.f[k];
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
+  float w, dwi = 0.0f, dwj = 0.0f;
+  if (pI) spline_w_dw(r * I.invH, w, dwi);
+  if (pJ) spline_w_dw(r * J.w, w, dwj);
+  const float Wi = I.K4 * dwi, Wj = Jf.z * dwj;
+  const float vdx = fmaf(I.v.x - Jv.x, dx, fmaf(I.v.y - Jv.y, dy, (I.v.z - Jv.z) * dz));
+  const float wv = vdx * rinv;
+  const float mu = fminf(wv, 0.0f);
+  const float vsig = I.c + Jf.y - 3.0f * mu;
+  const float Pi = -alpha * vsig * mu / (I.rho + Jv.w);
+  const float Wbar = 0.5f * (Wi + Wj);
+  const float coef = fmaf(I.F, Wi, fmaf(Jf.x, Wj, Pi * Wbar)) * rinv;
+  const float hv = 0.5f * Pi * Wbar;
+  acc.x = fmaf(-Ja.z * coef, dx, acc.x);
+  acc.y = fmaf(-Ja.z * coef, dy, acc.y);
+  acc.z = fmaf(-Ja.z * coef, dz, acc.z);
+  acc.w = fmaf(Ja.z * fmaf(I.F, Wi, hv), wv, acc.w);
+  vsig_i = fmaxf(vsig_i, vsig);
+  float4 a = S.acc[k];
+  const float mic = I.m * coef;
+  a.x = fmaf(mic, dx, a.x);
+  a.y = fmaf(mic, dy, a.y);
+  a.z = fmaf(mic, dz, a.z);
+  a.w = fmaf(I.m * fmaf(Jf.x, Wj, hv), wv, a.w);
+  S.acc[k] = a;
+  S.vs[k] = fmaxf(S.vs[k], vsig);
+}
+
+__device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, float4* facc, float* fvsig) {
+  if (gidx < 0 || !(vs > 0.0f)) return;   // vsig > 0 for every pair that contributed
+  atomicAdd(&facc[gidx], acc);
+  atomic_max_pos(&fvsig[gidx], vs);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pair, Tree T,
+                                                            const BoxDesc* __restrict__ box,
+                                                            const float4* __restrict__ pos4,
+                                                            const float4* __restrict__ cen4,
+                                                            const float4* __restrict__ vel4,
+                                                            const float4* __restrict__ ghost4,
+                                                            const float* __restrict__ sort_r,
+                                                            const unsigned int* __restrict__ sort_i,
+                                                            const unsigned int* __restrict__ perm,
+                                                            const double* __restrict__ x, float alpha, float4* facc,
+                                                            float* fvsig, unsigned long long* pc) {
+  __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  ForceShared& S = SH[wl];
+  Counters C;
+  const int npair = min(Lq.counts[1], cap_pair);
+  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < npair; item += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int A = Lq.pair_a[item], B = Lq.pair_b[item], ax = Lq.pair_axis[item];
+    const ItemGeom g = item_geom(T, box, A, ax);
+    const unsigned int nA = T.count[A], nB = T.count[B], sA = T.start[A], sB = T.start[B];
+    const unsigned int bit = (1u << ax) - 1u;
+    const unsigned int oA = T.sortbase[A] + (unsigned int)__popc(T.axes[A] & bit) * nA;
+    const unsigned int oB = T.sortbase[B] + (unsigned int)__popc(T.axes[B] & bit) * nB;
+    const float4 cA = T.cen[A], cB = T.cen[B];
+    const float3 shA = make_float3(-cA.x, -cA.y, -cA.z);
+    const float3 shB = make_float3(g.offB.x - cB.x, g.offB.y - cB.y, g.offB.z - cB.z);
+    const float HmA = T.hmax[A] * g.invL, HmB = T.hmax[B] * g.invL;
+    const float slack = g.e * 1.52587890625e-05f + 1e-6f * fmaxf(HmA, HmB);
+    const float rB0 = sort_r[oB] + g.offBp;
+    for (int it = (int)((nA - 1) >> 5); it >= 0; --it) {
+      const unsigned int ii = (unsigned int)it * 32u + lane;
+      const bool vi = ii < nA;
+      const ForceI I = load_force(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      const float ri = vi ? sort_r[oA + ii] : -FLT_MAX;
+      const float maxri = warp_max(ri);
+      if (rB0 - maxri > fmaxf(HmA, HmB) + slack) break;
+      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
+      const TileBox bi = tile_box(vi, I.p);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float vsi = 0.0f;
+      for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
+        const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
+        if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;
+        const unsigned int jj = jt * 32u + lane;
+        const bool vj = jj < nB;
+        const ForceI J = load_force(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, vel4, ghost4, g.invL, g.e);
+        const TileBox bj = tile_box(vj, J.p);
+        const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
+        if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
+        force_put(S, lane, J);
+        __syncwarp();
+        for (int s = 0; s < 32; ++s) {
+          force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
+          __syncwarp();
+        }
+        flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+        __syncwarp();
+      }
+      flush_force(I.g, acc, vsi, facc, fvsig);
+    }
+  }
+  commit_counters<COUNT>(C, pc, 1);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_self, Tree T,
+                                                            const BoxDesc* __restrict__ box,
+                                                            const float4* __restrict__ pos4,
+                                                            const float4* __restrict__ cen4,
+                                                            const float4* __restrict__ vel4,
+                                                            const float4* __restrict__ ghost4,
+                                                            const unsigned int* __restrict__ perm,
+                                                            const double* __restrict__ x, float alpha, float4* facc,
+                                                            float* fvsig, unsigned long long* pc) {
+  __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  ForceShared& S = SH[wl];
+  Counters C;
+  const int nself = min(Lq.counts[0], cap_self);
+  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < nself; item += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int A = Lq.self_a[item];
+    const ItemGeom g = item_geom(T, box, A, 0);
+    const unsigned int n = T.count[A], s0 = T.start[A];
+    const float4 cA = T.cen[A];
+    const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
+    const float slack = g.e * 1.52587890625e-05f;
+    const int nt = (int)((n + 31) >> 5);
+    for (int it = 0; it < nt; ++it) {
+      const unsigned int ii = (unsigned int)it * 32u + lane;
+      const bool vi = ii < n;
+      const ForceI I = load_force(vi, s0 + ii, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      const TileBox bi = tile_box(vi, I.p);
+      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float vsi = 0.0f;
+      for (int jt = it; jt < nt; ++jt) {
+        const unsigned int jj = (unsigned int)jt * 32u + lane;
+        const bool vj = jj < n;
+        const ForceI J = load_force(vj, s0 + jj, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+        if (jt != it) {
+          const TileBox bj = tile_box(vj, J.p);
+          const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
+          if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
+        }
+        force_put(S, lane, J);
+        __syncwarp();
+        if (jt == it) {
+          for (int s = 1; s <= 16; ++s) {
+            if (s < 16 || lane < 16) force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
+            __syncwarp();
+          }
+        } else {
+          for (int s = 0; s < 32; ++s) {
+            force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
+            __syncwarp();
+          }
+        }
+        flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+        __syncwarp();
+      }
+      flush_force(I.g, acc, vsi, facc, fvsig);
+    }
+  }
+  commit_counters<COUNT>(C, pc, 1);
+}
+
+// =========================================================================== ghost
+// mode 0: finalise every particle at its current h (one density pass);
+// mode 1: one h iteration (Newton on N~ = n_ngb, bracket, clamp) for the
+//         active particles, finalising those that converged or ran out.
+__global__ void k_ghost(long long N, int mode, int it, int max_iter, float gamma_k, float n_ngb, float tol,
+                        float gamma_gas, const unsigned int* __restrict__ perm, float* __restrict__ Hs,
+                        float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
+                        const float4* __restrict__ dacc, unsigned char* __restrict__ act, float* __restrict__ h,
+                        float* __restrict__ hlo, float* __restrict__ hhi, int* __restrict__ conv,
+                        const float* __restrict__ hlimp, const unsigned int* __restrict__ leaf_of, Tree T,
+                        float4* __restrict__ ghost4, int* __restrict__ n_active, unsigned int* __restrict__ err_all) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    if (mode == 1 && !act[p]) continue;
+    const unsigned int i = perm[p];
+    const float H = Hs[p];
+    const float m = cen4[p].w;
+    const float4 a = dacc[p];
+    const float sw = a.z + 1.0f;          // self term w(0) = 1
+    const float sg = a.w + 3.0f;          // 3 w(0) + 0
+    const float Nw = (32.0f / 3.0f) * sw; // (4 pi / 3) H^3 n with n = (8/pi) sum w / H^3
+    const float F = Nw - n_ngb;
+    const bool ok = fabsf(F) <= tol * n_ngb;
+    if (mode == 1 && !ok && it < max_iter) {
+      const float hc = h[i];
+      float lo = hlo[i], hi = hhi[i];
+      if (F < 0.0f) lo = hc;
+      else hi = hc;
+      const float dN = gamma_k * (32.0f / 3.0f) * (3.0f * sw - sg) / H;
+      float hn = dN > 0.0f ? hc - F / dN : (F < 0.0f ? 2.0f * hc : 0.5f * hc);
+      hn = fminf(fmaxf(hn, 0.5f * hc), 2.0f * hc);
+      if (lo > 0.0f && isfinite(hi) && !(hn > lo && hn < hi)) hn = 0.5f * (lo + hi);
+      hlo[i] = lo;
+      hhi[i] = hi;
+      h[i] = hn;
+      const float Hn = __fmul_rn(gamma_k, hn);
+      Hs[p] = Hn;
+      pos4[p].w = Hn;
+      if (!(Hn < hlimp[p])) atomicOr(err_all, ERR_REBUILD);
+      if (Hn > H) {
+        for (int id = (int)leaf_of[p]; id >= 0; id = T.parent[id]) atomic_max_pos(&T.hmax[id], Hn);
+      }
+      atomicAdd(n_active, 1);
+      continue;
+    }
+    act[p] = 0;
+    conv[i] = ok ? 1 : 0;
+    const float ih = 1.0f / H;
+    const float K3 = SPH_KNORM * ih * ih * ih;
+    const float rho = K3 * (a.x + m);
+    const float Sm = K3 * (a.y + 3.0f * m);
+    const float u = vel4[p].w;
+    const float P = (gamma_gas - 1.0f) * rho * u;
+    const float c = sqrtf(gamma_gas * P / rho);
+    const float f = 1.0f / (1.0f - Sm / (3.0f * rho));
+    ghost4[p] = make_float4(rho, f * P / (rho * rho), c, f);
+  }
+}
+
+__global__ void k_zero_active(long long N, const unsigned char* __restrict__ act, float4* __restrict__ dacc,
+                              unsigned int* __restrict__ dcnt, int all) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    if (all || act[p]) {
+      dacc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      dcnt[p] = 0;
+    }
+  }
+}
+
+__global__ void k_set_active(long long N, unsigned char* __restrict__ act) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    act[p] = 1;
+}
+
+__global__ void k_h_bracket_reset(long long N, float* __restrict__ hlo, float* __restrict__ hhi, int* __restrict__ conv) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    hlo[p] = 0.0f;
+    hhi[p] = __int_as_float(0x7f800000);
+    conv[p] = 0;
+  }
+}
+
+// =========================================================================== reductions
+// Per box, in FP64: sum m a (3), sum m (v.a + du/dt), sum m v (3), sum m (v^2/2 + u).
+__global__ void k_reduce(long long N, int box_shift, const unsigned long long* __restrict__ key,
+                         const float4* __restrict__ cen4, const float4* __restrict__ vel4,
+                         const float4* __restrict__ facc, double* __restrict__ red) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p - threadIdx.x < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    const bool valid = p < N;
+    const int b = valid ? (int)(key[p] >> box_shift) : -1;
+    double val[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (valid) {
+      const double m = cen4[p].w;
+      const float4 vv = vel4[p];
+      const float4 a = facc[p];
+      val[0] = m * a.x;
+      val[1] = m * a.y;
+      val[2] = m * a.z;
+      val[3] = m * ((double)vv.x * a.x + (double)vv.y * a.y + (double)vv.z * a.z + (double)a.w);
+      val[4] = m * vv.x;
+      val[5] = m * vv.y;
+      val[6] = m * vv.z;
+      val[7] = m * (0.5 * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z) + (double)vv.w);
+    }
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    const bool uniform = __all_sync(0xffffffffu, b == b0) && b0 >= 0;
+    if (uniform) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        double s = val[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&red[8 * b0 + k], s);
+      }
+    } else if (valid) {
+      for (int k = 0; k < 8; ++k) atomicAdd(&red[8 * b + k], val[k]);
+    }
+  }
+}
+
+// =========================================================================== time stepping
+// accelerations of the last force pass, kept in caller order for the next kick
+__global__ void k_save_acc(long long N, const unsigned int* __restrict__ perm, const float4* __restrict__ facc,
+                           float4* __restrict__ a_in) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    a_in[perm[p]] = facc[p];
+}
+
+// half kick with the box's dt: v += a dt/2, u += du/dt dt/2 (u kept >= 0)
+__global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
+                       const float4* __restrict__ a_in, float* __restrict__ v, float* __restrict__ u) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const float hdt = (float)(0.5 * box[bid[i]].dt);
+    if (hdt == 0.0f) continue;
+    const float4 a = a_in[i];
+    v[3 * i] += a.x * hdt;
+    v[3 * i + 1] += a.y * hdt;
+    v[3 * i + 2] += a.z * hdt;
+    u[i] = fmaxf(u[i] + a.w * hdt, 0.0f);
+  }
+}
+
+// drift in FP64 with the box's dt, wrapped into [0, L) (periodic) or clamped (open)
+__global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
+                        double* __restrict__ x, const float* __restrict__ v) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const BoxDesc bd = box[bid[p]];
+    if (bd.dt == 0.0) continue;
+    for (int k = 0; k < 3; ++k) {
+      double xn = x[3 * p + k] + (double)v[3 * p + k] * bd.dt;
+      if (bd.periodic) {
+        xn -= bd.L * floor(xn * bd.invL);
+        if (xn >= bd.L) xn -= bd.L;
+        if (xn < 0.0 || xn >= bd.L) xn = 0.0;
+      } else {
+        xn = fmin(fmax(xn, 0.0), nextafter(bd.L, 0.0));
+      }
+      x[3 * p + k] = xn;
+    }
+  }
+}
+
+// =========================================================================== outputs
+// Write field `field` of the particles of one box [off, off + n) in caller order.
+__global__ void k_get_field(long long off, long long n, int field, const unsigned int* __restrict__ perm,
+                            const float* __restrict__ Hs, const float4* __restrict__ cen4,
+                            const float4* __restrict__ vel4, const float4* __restrict__ dacc,
+                            const unsigned int* __restrict__ dcnt, const float4* __restrict__ ghost4,
+                            const float4* __restrict__ facc, const float* __restrict__ fvsig,
+                            const float* __restrict__ h, float gamma_gas, void* out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long p = off + q;
+    const long long i = (long long)perm[p] - off;
+    const float H = Hs[p];
+    const float ih = 1.0f / H;
+    const float K3 = SPH_KNORM * ih * ih * ih;
+    const float4 a = dacc[p];
+    const float m = cen4[p].w;
+    float* fo = reinterpret_cast<float*>(out);
+    switch (field) {
+      case SPH_FIELD_RHO: fo[i] = K3 * (a.x + m); break;
+      case SPH_FIELD_DRHO_DH: fo[i] = -K3 * (a.y + 3.0f * m) / h[perm[p]]; break;
+      case SPH_FIELD_NW: fo[i] = K3 * (a.z + 1.0f); break;
+      case SPH_FIELD_NNGB: fo[i] = (32.0f / 3.0f) * (a.z + 1.0f); break;
+      case SPH_FIELD_COUNT: reinterpret_cast<int*>(out)[i] = (int)dcnt[p]; break;
+      case SPH_FIELD_P: fo[i] = (gamma_gas - 1.0f) * ghost4[p].x * vel4[p].w; break;
+      case SPH_FIELD_C: fo[i] = ghost4[p].z; break;
+      case SPH_FIELD_F: fo[i] = ghost4[p].w; break;
+      case SPH_FIELD_A: {
+        const float4 f = facc[p];
+        fo[3 * i] = f.x;
+        fo[3 * i + 1] = f.y;
+        fo[3 * i + 2] = f.z;
+        break;
+      }
+      case SPH_FIELD_DUDT: fo[i] = facc[p].w; break;
+      case SPH_FIELD_VSIG: fo[i] = fvsig[p]; break;
+      default: break;
+    }
+  }
+}
+
+// =========================================================================== launchers
+void launch_density(Engine& E) {
+  const int grid = E.nsm * 8;
+  if (E.count_pairs) {
+    k_density_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                         E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
+                                                         E.dacc.p, E.dcnt.p, E.pc.p);
+    k_density_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                         E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
+  } else {
+    k_density_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                          E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
+                                                          E.dacc.p, E.dcnt.p, E.pc.p);
+    k_density_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                          E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
+  }
+}
+
+void launch_force(Engine& E) {
+  const int grid = E.nsm * 8;
+  const float alpha = E.prm.alpha_visc;
+  if (E.count_pairs) {
+    k_force_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                       E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
+                                                       E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
+    k_force_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                       E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
+                                                       E.fvsig.p, E.pc.p);
+  } else {
+    k_force_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                        E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
+                                                        E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
+    k_force_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                        E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
+                                                        E.fvsig.p, E.pc.p);
+  }
+}
+
+void launch_ghost(Engine& E, int mode, int it) {
+  k_ghost<<<E.grid(E.N), 256, 0, E.st>>>(E.N, mode, it, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
+                                          E.prm.h_tol, E.prm.gamma_gas, E.perm.p, E.Hs.p, E.pos4.p, E.cen4.p,
+                                          E.vel4.p, E.dacc.p, E.act.p, E.h.p, E.hlo.p, E.hhi.p, E.conv.p,
+                                          E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.dev_counters.p, E.err_all.p);
+}
+
+void launch_zero_density(Engine& E, bool all) {
+  k_zero_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.dacc.p, E.dcnt.p, all ? 1 : 0);
+}
+
+void launch_set_active(Engine& E) { k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); }
+
+void launch_bracket_reset(Engine& E) {
+  k_h_bracket_reset<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.hlo.p, E.hhi.p, E.conv.p);
+}
+
+void launch_reduce(Engine& E) {
+  cudaMemsetAsync(E.red.p, 0, sizeof(double) * 8 * E.nbox, E.st);
+  k_reduce<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.box_shift, E.key.p, E.cen4.p, E.vel4.p, E.facc.p, E.red.p);
+}
+
+void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); }
+
+void launch_kick(Engine& E) { k_kick<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); }
+
+void launch_drift(Engine& E) { k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p); }
+
+void launch_get_field(Engine& E, long long off, long long n, int field, void* out) {
+  k_get_field<<<E.grid(n), 256, 0, E.st>>>(off, n, field, E.perm.p, E.Hs.p, E.cen4.p, E.vel4.p, E.dacc.p, E.dcnt.p,
+                                           E.ghost4.p, E.facc.p, E.fvsig.p, E.h.p, E.prm.gamma_gas, out);
+}
+
+}  // namespace sph

@@ -1,0 +1,305 @@
+// Batched, served boxes: a request queue in front of one engine that holds every
+// admitted box on the device and advances all of them by one step per tick with
+// a single batched pipeline (one launch per kernel for all boxes: the key sort,
+// tree, interaction lists, axis sorts and the density/force kernels all run over
+// the concatenated boxes; interactions never cross boxes).
+//
+// Admission is by device footprint against a byte budget and by a box count
+// limit; waiting requests are admitted in submission order as finished boxes
+// retire (continuous batching).  A box's first tick computes its starting
+// forces; each further tick is one kick-drift-kick step of its own dt.
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sph_engine.h"
+
+namespace {
+
+constexpr int kFields = 17;
+
+struct Request {
+  long long id = 0;
+  double L = 1.0;
+  int periodic = 1;
+  long long n = 0;
+  std::vector<double> x;
+  std::vector<float> v, m, u, h;
+  std::vector<float> acc;   // a (3) and du/dt per particle, once started
+  int n_steps = 0, done_steps = 0;
+  double dt = 0.0;
+  bool started = false;
+  int state = 0;            // 0 waiting, 1 resident, 2 finished
+  std::vector<float> step_ms;
+  std::vector<std::vector<unsigned char>> result;   // per field, caller order
+};
+
+size_t field_bytes(int f, long long n) {
+  switch (f) {
+    case SPH_FIELD_X: return 3 * n * sizeof(double);
+    case SPH_FIELD_V: case SPH_FIELD_A: return 3 * n * sizeof(float);
+    case SPH_FIELD_REDUCTIONS: return 8 * sizeof(double);
+    default: return n * 4;
+  }
+}
+
+}  // namespace
+
+struct sph_server {
+  sph_ctx* ctx = nullptr;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  sph::Engine* eng = nullptr;
+  long long budget = 0;
+  int max_boxes = 0;
+  long long next_id = 1;
+  std::map<long long, Request> reqs;
+  std::deque<long long> waiting;
+  std::vector<long long> resident;
+  bool dirty = true;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::string err;
+};
+
+static const long long kBytesPerParticle = 520;
+
+static sph_status srv_fail(sph_server* s, sph_status st, const std::string& m) {
+  s->err = m;
+  return st;
+}
+
+// Copy the device state of every resident box back to its request.
+static sph_status save_resident(sph_server* s) {
+  sph::Engine& E = *s->eng;
+  for (size_t b = 0; b < s->resident.size(); ++b) {
+    Request& r = s->reqs[s->resident[b]];
+    const long long o = E.off[b];
+    cudaMemcpyAsync(r.x.data(), E.x.p + 3 * o, 3 * r.n * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    cudaMemcpyAsync(r.v.data(), E.v.p + 3 * o, 3 * r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
+    cudaMemcpyAsync(r.u.data(), E.u.p + o, r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
+    cudaMemcpyAsync(r.h.data(), E.h.p + o, r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
+    if (r.started) {
+      r.acc.resize(4 * r.n);
+      cudaMemcpyAsync(r.acc.data(), E.a_in.p + o, 4 * r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
+    }
+  }
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return srv_fail(s, SPH_E_CUDA, "saving resident boxes failed");
+  return SPH_OK;
+}
+
+static sph_status load_resident(sph_server* s) {
+  std::vector<sph::BoxSpec> spec;
+  for (long long id : s->resident) {
+    const Request& r = s->reqs[id];
+    spec.push_back(sph::BoxSpec{r.L, r.n, r.periodic});
+  }
+  sph::Engine& E = *s->eng;
+  sph_status st = E.set_boxes(spec);
+  if (st != SPH_OK) return srv_fail(s, st, E.err);
+  bool all_started = true;
+  for (size_t b = 0; b < s->resident.size(); ++b) {
+    Request& r = s->reqs[s->resident[b]];
+    st = E.set_particles((int)b, r.x.data(), r.v.data(), r.m.data(), r.u.data(), r.h.data(), SPH_MEM_HOST);
+    if (st != SPH_OK) return srv_fail(s, st, E.err);
+    if (r.started)
+      cudaMemcpyAsync(E.a_in.p + E.off[b], r.acc.data(), 4 * r.n * sizeof(float), cudaMemcpyHostToDevice, s->st);
+    else
+      cudaMemsetAsync(E.a_in.p + E.off[b], 0, 4 * r.n * sizeof(float), s->st);
+    all_started &= r.started;
+  }
+  // starting forces of new boxes come from their first (dt = 0) tick; the kick of
+  // every box reads a_in, so the engine never recomputes forces on its own
+  E.have_acc = true;
+  (void)all_started;
+  return SPH_OK;
+}
+
+static sph_status finish(sph_server* s, size_t b) {
+  sph::Engine& E = *s->eng;
+  Request& r = s->reqs[s->resident[b]];
+  r.result.assign(kFields, {});
+  for (int f = 0; f < kFields; ++f) {
+    const long long n = f == SPH_FIELD_REDUCTIONS ? 8 : r.n;
+    r.result[f].resize(field_bytes(f, r.n));
+    sph_status st = E.get((int)b, f, r.result[f].data(), n, SPH_MEM_HOST);
+    if (st != SPH_OK) r.result[f].clear();
+  }
+  r.state = 2;
+  return SPH_OK;
+}
+
+extern "C" {
+
+sph_status sph_server_create(sph_ctx* ctx, int64_t budget_bytes, int32_t max_boxes, sph_server** out) {
+  if (!ctx || !out) return SPH_E_INVALID;
+  *out = nullptr;
+  const sph_ctx* cv = ctx;
+  cudaSetDevice(cv->device);
+  sph_server* s = new sph_server;
+  s->ctx = ctx;
+  s->device = cv->device;
+  s->st = cv->cur;
+  s->max_boxes = max_boxes > 0 ? max_boxes : 1 << 16;
+  if (budget_bytes <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    budget_bytes = (int64_t)(0.8 * (double)fr);
+  }
+  s->budget = budget_bytes;
+  s->eng = new sph::Engine(cv->prm, cv->device, s->st);
+  cudaEventCreate(&s->e0);
+  cudaEventCreate(&s->e1);
+  *out = s;
+  return SPH_OK;
+}
+
+sph_status sph_server_submit(sph_server* s, int64_t n, double L, int periodic, const double* x, const float* v,
+                             const float* m, const float* u, const float* h, int32_t n_steps, double dt, int64_t* id) {
+  if (!s || !id || !x || !v || !m || !u || !h) return SPH_E_INVALID;
+  if (n < 1 || !(L > 0) || n_steps < 0 || !(dt >= 0)) return srv_fail(s, SPH_E_INVALID, "bad request");
+  if ((long long)n * kBytesPerParticle > s->budget) return srv_fail(s, SPH_E_OOM, "box can never fit the budget");
+  Request r;
+  r.id = s->next_id++;
+  r.L = L;
+  r.periodic = periodic ? 1 : 0;
+  r.n = n;
+  r.x.assign(x, x + 3 * n);
+  r.v.assign(v, v + 3 * n);
+  r.m.assign(m, m + n);
+  r.u.assign(u, u + n);
+  r.h.assign(h, h + n);
+  r.n_steps = n_steps;
+  r.dt = dt;
+  s->waiting.push_back(r.id);
+  *id = r.id;
+  s->reqs.emplace(r.id, std::move(r));
+  return SPH_OK;
+}
+
+sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
+  if (!s) return SPH_E_INVALID;
+  cudaSetDevice(s->device);
+  s->st = s->ctx->cur;
+  s->eng->st = s->st;
+  if (n_active) *n_active = 0;
+  // admission in submission order while the footprint fits
+  long long used = 0;
+  for (long long id : s->resident) used += s->reqs[id].n * kBytesPerParticle;
+  bool admitted = false;
+  while (!s->waiting.empty() && (int)s->resident.size() < s->max_boxes) {
+    Request& r = s->reqs[s->waiting.front()];
+    if (used + r.n * kBytesPerParticle > s->budget) break;
+    // the engine's layout still matches `resident` unless a box just retired
+    // (then the state was saved already)
+    if (!admitted && !s->resident.empty() && !s->dirty) {
+      sph_status st = save_resident(s);
+      if (st != SPH_OK) return st;
+    }
+    admitted = true;
+    used += r.n * kBytesPerParticle;
+    r.state = 1;
+    s->resident.push_back(r.id);
+    s->waiting.pop_front();
+  }
+  if (admitted) s->dirty = true;
+  if (s->resident.empty()) return SPH_OK;
+  if (s->dirty) {
+    sph_status st = load_resident(s);
+    if (st != SPH_OK) return st;
+    s->dirty = false;
+  }
+  sph::Engine& E = *s->eng;
+  for (size_t b = 0; b < s->resident.size(); ++b) {
+    const Request& r = s->reqs[s->resident[b]];
+    E.hbox[b].dt = r.started ? r.dt : 0.0;
+  }
+  cudaEventRecord(s->e0, s->st);
+  sph_status st = E.step_boxes();
+  cudaEventRecord(s->e1, s->st);
+  if (st != SPH_OK && st != SPH_E_NOT_CONVERGED) return srv_fail(s, st, E.err);
+  cudaEventSynchronize(s->e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, s->e0, s->e1);
+  if (n_active) *n_active = (int)s->resident.size();
+  bool any_done = false;
+  for (size_t b = 0; b < s->resident.size(); ++b) {
+    Request& r = s->reqs[s->resident[b]];
+    if (r.started) {
+      r.done_steps++;
+      r.step_ms.push_back(ms);
+    } else {
+      r.started = true;
+    }
+    if (r.done_steps >= r.n_steps) any_done = true;
+  }
+  if (any_done) {
+    // keep the state of the boxes that stay, return the finished ones
+    sph_status sv = save_resident(s);
+    if (sv != SPH_OK) return sv;
+    std::vector<long long> keep;
+    for (size_t b = 0; b < s->resident.size(); ++b) {
+      Request& r = s->reqs[s->resident[b]];
+      if (r.done_steps >= r.n_steps) finish(s, b);
+      else keep.push_back(r.id);
+    }
+    s->resident = keep;
+    s->dirty = true;
+  }
+  return SPH_OK;
+}
+
+sph_status sph_server_poll(sph_server* s, int64_t id, int32_t* done, float* step_ms, int32_t max_steps) {
+  if (!s || !done) return SPH_E_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return srv_fail(s, SPH_E_INVALID, "unknown request");
+  const Request& r = it->second;
+  *done = r.state == 2 ? 1 : 0;
+  if (step_ms)
+    for (int k = 0; k < max_steps && k < (int)r.step_ms.size(); ++k) step_ms[k] = r.step_ms[k];
+  return SPH_OK;
+}
+
+sph_status sph_server_get(sph_server* s, int64_t id, int field, void* dst, int64_t n) {
+  if (!s || !dst) return SPH_E_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return srv_fail(s, SPH_E_INVALID, "unknown request");
+  const Request& r = it->second;
+  if (r.state != 2) return srv_fail(s, SPH_E_BUSY, "request not finished");
+  if (field < 0 || field >= kFields) return srv_fail(s, SPH_E_INVALID, "unknown field");
+  const long long want = field == SPH_FIELD_REDUCTIONS ? 8 : r.n;
+  if (n != want) return srv_fail(s, SPH_E_INVALID, "n does not match");
+  if (r.result[field].empty()) return srv_fail(s, SPH_E_NOT_BUILT, "field not available");
+  std::memcpy(dst, r.result[field].data(), r.result[field].size());
+  return SPH_OK;
+}
+
+sph_status sph_server_release(sph_server* s, int64_t id) {
+  if (!s) return SPH_E_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return SPH_E_INVALID;
+  if (it->second.state == 1) return srv_fail(s, SPH_E_BUSY, "request is resident");
+  if (it->second.state == 0)
+    for (auto w = s->waiting.begin(); w != s->waiting.end(); ++w)
+      if (*w == id) {
+        s->waiting.erase(w);
+        break;
+      }
+  s->reqs.erase(it);
+  return SPH_OK;
+}
+
+sph_status sph_server_destroy(sph_server* s) {
+  if (!s) return SPH_E_INVALID;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->st);
+  delete s->eng;
+  cudaEventDestroy(s->e0);
+  cudaEventDestroy(s->e1);
+  delete s;
+  return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// Host-side engine of the GB300 SPH path: device buffers of a batch of boxes
+// and the launch sequences of the build and the passes.  One engine drives one
+// box (the C-ABI sph_box) or many boxes at once (the server).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// A device array that only grows.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t reserve(size_t want) {
+    if (want <= n && p) return cudaSuccess;
+    release();
+    if (want == 0) want = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), want * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      return e;
+    }
+    n = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  ~DBuf() { release(); }
+};
+
+struct BoxSpec {
+  double L;
+  long long n;
+  int periodic;
+};
+
+// Kernels and helpers implemented in build.cu / interact.cu.
+void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsigned int* tile_sums,
+                    unsigned int* total, cudaStream_t st);
+long long radix_scratch_words(long long n);
+void radix_sort(unsigned long long* k0, unsigned int* v0, unsigned long long* k1, unsigned int* v1, long long n,
+                int bits, unsigned int* scratch, cudaStream_t st);
+
+class Engine {
+ public:
+  Engine(const sph_params& prm, int device, cudaStream_t st);
+  ~Engine();
+
+  // ---- configuration -------------------------------------------------------
+  sph_status set_boxes(const std::vector<BoxSpec>& boxes);   // (re)size for these boxes
+  // copy particle state of box b (host or device pointers)
+  sph_status set_particles(int b, const double* x, const float* v, const float* m, const float* u, const float* h,
+                           int mem);
+
+  // ---- the hot path -----------------------------------------------------------
+  sph_status build();
+  sph_status density();                                        // one pass at the current h, all particles
+  sph_status h_update(long long* n_unconverged, int* iterations);
+  sph_status force();
+  sph_status step(double dt);          // every box with the same dt
+  sph_status step_boxes();             // every box with its own hbox[b].dt
+  sph_status cfl_dt(int b, double* dt);
+  sph_status get(int b, int field, void* dst, long long n, int mem);
+  sph_status stats(int b, sph_stats* out);
+  sph_status cells(int b, long long cap, int* level, int* ijk, int* count, int* split, long long* n_out);
+  sph_status interactions(int b, long long cap, int* kind, int* a, int* bb, int* axis, long long* n_out);
+
+  // ---- state -----------------------------------------------------------------
+  sph_params prm;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  int nsm = 148;
+  std::string err;
+  bool count_pairs = false;
+  size_t footprint_bytes() const;
+
+  std::vector<BoxSpec> spec;
+  std::vector<long long> off;   // first particle of each box
+  long long N = 0;
+  int nbox = 0;
+  std::vector<BoxDesc> hbox;
+  int dcap = 0, box_shift = 0, kmin = 0, kmax = 0, key_bits = 0;
+
+  // box table and input-order particle state (owned by the engine)
+  DBuf<BoxDesc> box;
+  DBuf<int> bid;
+  DBuf<double> x;
+  DBuf<float> v, m, u, h;
+  DBuf<float> H_in, hlo, hhi;
+  DBuf<int> conv;                 // 1 when h converged (input order)
+  DBuf<float4> a_in;              // a and du/dt of the last force pass (input order)
+
+  // key-sorted particle state
+  DBuf<unsigned long long> key, key_tmp;
+  DBuf<unsigned int> perm, perm_tmp, rs_scratch;
+  DBuf<float> Hs, hlimp;
+  DBuf<float4> pos4, cen4, vel4;
+  DBuf<unsigned int> leaf_of;
+  DBuf<int> top_at;
+  DBuf<unsigned char> act;        // still iterating h (sorted order)
+
+  // cell tree
+  int cap_nodes = 0;
+  DBuf<unsigned int> t_start, t_count, t_nsmall, t_axes, t_sortbase;
+  DBuf<unsigned long long> t_key;
+  DBuf<int> t_level, t_box, t_child, t_nchild, t_parent, t_split, t_n;
+  DBuf<float> t_hmax;
+  DBuf<double> t_hlim;
+  DBuf<float4> t_cen;
+  Tree T{};
+
+  // interaction lists
+  int cap_self = 0, cap_pair = 0, cap_queue = 0;
+  DBuf<int> l_self, l_pa, l_pb, l_pax, l_counts;
+  DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
+  Lists Lq{};
+
+  // sorted projections
+  DBuf<float> sort_r;
+  DBuf<unsigned int> sort_i;
+  int cap_big = 0;
+  DBuf<int> big_node, big_axis, big_count;
+  DBuf<unsigned int> big_off;
+  DBuf<unsigned long long> ckey, ckey_tmp;
+  DBuf<unsigned int> cval, cval_tmp;
+
+  // pass results (sorted order)
+  DBuf<float4> dacc;              // sum m w, sum m (3w + q w'), sum w, sum (3w + q w')
+  DBuf<unsigned int> dcnt;
+  DBuf<float4> ghost4;            // rho, f P / rho^2, c, f
+  DBuf<float4> facc;              // a (3), du/dt
+  DBuf<float> fvsig;
+  DBuf<double> red;               // 8 per box
+  DBuf<unsigned int> err_all;     // global error bits
+  DBuf<unsigned long long> pc;    // PairCounters per engine
+  DBuf<int> dev_counters;         // [0] particles still active after a ghost pass
+  DBuf<unsigned char> staging;    // output staging (input order)
+
+  // host mirrors of counts after the last build
+  int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0, depth_used = 0;
+  long long n_entries = 0, n_big_entries = 0;
+  int last_iters = 0, last_rebuilds = 0;
+  long long last_unconverged = 0;
+  bool built = false, have_density = false, have_ghost = false, have_force = false, have_acc = false;
+
+  // helpers
+  int grid(long long work, int threads = 256) const;
+  sph_status cuda_fail(cudaError_t e, const char* where);
+  sph_status fail(sph_status s, const std::string& msg);
+  sph_status ensure_particle_capacity();
+  sph_status ensure_tree_capacity(int nodes);
+  sph_status ensure_list_capacity(int selfs, int pairs, int queue);
+  sph_status build_once(bool* retry);
+  sph_status set_all_active();
+  sph_status density_pass();
+  sph_status ghost_pass(int mode, int it, int* n_active, bool* rebuild);
+  sph_status upload_boxes();
+};
+
+}  // namespace sph
+
+// C-ABI context: device, parameters, the stream every call launches on.
+struct sph_ctx {
+  sph_params prm;
+  int device = 0;
+  cudaStream_t own = nullptr;
+  cudaStream_t cur = nullptr;
+  std::string last;
+  std::mutex mu;
+};

@@ -1,0 +1,194 @@
+// Internal definitions of the GB300 SPH path: device data layout and helpers
+// shared by the build, interaction and host translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SPH_MAX_DEPTH 20          // bits per dimension of the Morton code
+#define SPH_WARPS_PER_CTA 4
+#define SPH_THREADS (32 * SPH_WARPS_PER_CTA)
+#define SORT_SMALL 2048u       // cells up to this size are sorted in shared memory
+
+// Error bits set by kernels in a box's status word.
+enum : unsigned int {
+  ERR_BAD_INPUT = 1u,        // NaN / non-positive h / x outside [0, L)
+  ERR_H_TOO_LARGE = 2u,      // top grid cannot hold H_max
+  ERR_OVERFLOW = 4u,         // a device list exceeded its capacity
+  ERR_REBUILD = 8u,          // some H outgrew what the cell splits assumed
+};
+
+// One box of a batch.  Particles of box b occupy [off, off + n) both in the
+// caller-order input arrays and in the key-sorted arrays.
+struct BoxDesc {
+  double L, invL;       // edge and its reciprocal
+  double margin;        // 2^-50 L: every cell rule is strict by this much
+  long long off, n;
+  int periodic;
+  int k;                // top level: cell edge L / 2^k
+  float Hmax, Hmin;     // extremes of the support radius (physical units)
+  unsigned int err;     // ERR_* bits
+  unsigned int pad;
+  double dt;            // time step of the box (0: passes only)
+};
+
+// The 13 cell-pair directions db in {-1,0,1}^3 with dz > 0, or dz = 0 and
+// dy > 0, or dz = dy = 0 and dx > 0 (one of each +-db).  Section II-C: the
+// sorted indices are kept per cell along these 13 axes.
+__host__ __device__ inline void axis_vec(int a, int& dx, int& dy, int& dz) {
+  // enumeration in z-major order over (dx, dy, dz) restricted to the half space
+  const signed char T[13][3] = {
+      {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1},
+      {-1, 0, 1}, {0, 0, 1},  {1, 0, 1},  {-1, 1, 1}, {0, 1, 1},   {1, 1, 1}};
+  dx = T[a][0]; dy = T[a][1]; dz = T[a][2];
+}
+
+__host__ __device__ inline int axis_index(int dx, int dy, int dz) {
+  // inverse of axis_vec for db in the positive half space; -1 otherwise
+  if (dz == 1) return 4 + (dy + 1) * 3 + (dx + 1);
+  if (dz == 0 && dy == 1) return 1 + (dx + 1);
+  if (dz == 0 && dy == 0 && dx == 1) return 0;
+  return -1;
+}
+
+__host__ __device__ inline bool dir_positive(int dx, int dy, int dz) {
+  return dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+}
+
+// ---------------------------------------------------------------- Morton codes
+__host__ __device__ inline unsigned long long spread3(unsigned long long v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__host__ __device__ inline unsigned int compact3(unsigned long long v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (unsigned int)v;
+}
+
+// x in bits 0,3,6..., y in 1,4,..., z in 2,5,...
+__host__ __device__ inline unsigned long long morton3(unsigned int x, unsigned int y, unsigned int z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ------------------------------------------------------------ cubic spline
+// w(q) and dw/dq of the cubic spline with support 1 (W = 8/(pi H^3) w(r/H)).
+__device__ __forceinline__ void spline_w_dw(float q, float& w, float& dw) {
+  const float one_m = 1.0f - q;
+  const float q2 = q * q;
+  const float w_in = fmaf(6.0f * q2, q - 1.0f, 1.0f);      // 1 - 6q^2 + 6q^3
+  const float dw_in = q * fmaf(18.0f, q, -12.0f);          // -12q + 18q^2
+  const float w_out = 2.0f * one_m * one_m * one_m;        // 2(1-q)^3
+  const float dw_out = -6.0f * one_m * one_m;              // -6(1-q)^2
+  const bool inner = q < 0.5f;
+  w = inner ? w_in : w_out;
+  dw = inner ? dw_in : dw_out;
+}
+
+#define SPH_KNORM 2.5464790894703255f   // 8 / pi
+
+// ------------------------------------------------- orderable float as uint32
+__device__ __forceinline__ unsigned int float_key(float f) {
+  unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ------------------------------------------- exact neighbour decision in FP64
+// The fixed evaluation both this path and the oracle use for r_ij < H:
+// d = x_i - x_j per component, wrapped by +-L when |d| > L/2 (periodic),
+// r2 = (d0*d0 + d1*d1) + d2*d2 with correctly rounded operations, no FMA.
+__device__ __forceinline__ double canonical_r2(const double* xi, const double* xj, double L, double halfL,
+                                               int periodic) {
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = __dsub_rn(xi[k], xj[k]);
+    if (periodic) {
+      if (t > halfL) t = __dsub_rn(t, L);
+      else if (t < -halfL) t = __dadd_rn(t, L);
+    }
+    d[k] = t;
+  }
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+__device__ __forceinline__ bool canonical_less(double r2, float H) {
+  const double h = (double)H;
+  return r2 < __dmul_rn(h, h);   // exact: the product of two FP32 fits FP64
+}
+
+// ------------------------------------------------------------ warp helpers
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// atomicMax / atomicMin on non-negative floats and doubles through their bits
+__device__ __forceinline__ void atomic_max_pos(float* a, float v) {
+  atomicMax(reinterpret_cast<unsigned int*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_min_pos(float* a, float v) {
+  atomicMin(reinterpret_cast<unsigned int*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_min_pos(double* a, double v) {
+  atomicMin(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// ------------------------------------------------------------ device arrays
+// Cell tree (structure of arrays, capacity cap_nodes).
+struct Tree {
+  unsigned int* start;      // first particle (sorted order)
+  unsigned int* count;
+  unsigned long long* key;  // box bits | Morton prefix of the cell at its level
+  int* level;
+  int* box;
+  int* child;               // first child (children are contiguous), -1 for a leaf
+  int* nchild;
+  int* parent;
+  int* split;               // 1 when split
+  float* hmax;              // max support radius inside (physical units); grows with H
+  unsigned int* nsmall;     // particles with H < edge/2 - margin
+  double* hlim;             // H must stay below this for the interactions built (physical)
+  float4* cen;              // centre minus its top cell's centre (units of L), exact
+  unsigned int* axes;       // bit a: a sorted list along axis a is needed
+  unsigned int* sortbase;   // offset of the first sorted list of this cell
+  int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier
+};
+
+// Interaction lists.
+struct Lists {
+  int* self_a;              // final self-interactions
+  int* pair_a;              // final pair-interactions: cells a, b, axis (a -> b)
+  int* pair_b;
+  int* pair_axis;
+  int* q_kind[2];           // expansion queues (ping-pong): 0 self, 1 pair
+  int* q_a[2];
+  int* q_b[2];
+  int* q_axis[2];
+  int* counts;              // [0] selfs, [1] pairs, [2] queue 0 size, [3] queue 1 size, [4] sort segments, [5] sort entries
+};
+
+// Per-box counters kept by the pair kernels when counting is on.
+struct PairCounters {
+  unsigned long long dens_pairs, dens_sides, dens_cand, force_pairs, force_cand, rechecks;
+};

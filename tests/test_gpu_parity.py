@@ -1,0 +1,300 @@
+"""GPU path (through the C-ABI) against the FP64 oracle.
+
+Bars: neighbour counts, cells and interaction lists bit-exact; rho, nw, P, c, f
+within 1e-5 relative; d rho/dh within 2e-5 of 3 rho/h; accelerations and du/dt
+within 1e-4 of their rms; vsig within 1e-5 relative; converged h within 1e-4
+relative (the h tolerance 1e-4 on N~ bounds two converged solutions to
+2/3 x 1e-4 apart); conservation sums within 1e-5 of the sum of magnitudes.
+"""
+import numpy as np
+import pytest
+
+from oracle import decomposition as dc
+from oracle import sph as orc
+from paper_1309_3783_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1309_3783_gb300 import build, sph
+    build.build()
+    return sph
+
+
+def make_ctx(api, **kw):
+    p = api.sph_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return api.sph_ctx_create(p, device=0)
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = make_ctx(api)
+    yield c
+    api.sph_ctx_destroy(c)
+
+
+def gpu_fixed_h(api, ctx, box, force=True):
+    b = api.box_from(ctx, box)
+    b.density()
+    out = {k: b.get(k) for k in ("count", "rho", "nw", "drho_dh", "nngb", "P", "c", "f")}
+    if force:
+        b.force()
+        for k in ("a", "dudt", "vsig", "reductions"):
+            out[k] = b.get(k)
+    out["stats"] = b.stats()
+    b.close()
+    return out
+
+
+def check_density(g, ref, box, idx=None):
+    idx = np.arange(box.n) if idx is None else idx
+    assert np.array_equal(g["count"][idx], ref["count"]), np.nonzero(g["count"][idx] != ref["count"])
+    np.testing.assert_allclose(g["rho"][idx], ref["rho"], rtol=1e-5)
+    np.testing.assert_allclose(g["nw"][idx], ref["nw"], rtol=1e-5)
+    h = box.h.astype(np.float64)[idx]
+    drho = orc.drho_dh(ref, h)
+    assert np.all(np.abs(g["drho_dh"][idx] - drho) <= 2e-5 * 3 * ref["rho"] / h)
+
+
+def check_force(g, ref, idx=None, ref_all=None):
+    idx = slice(None) if idx is None else idx
+    scale_src = ref if ref_all is None else ref_all
+    rms = np.sqrt(np.mean(np.sum(scale_src["a"] ** 2, axis=1)))
+    assert np.max(np.abs(g["a"][idx] - ref["a"])) <= 1e-4 * rms
+    rms_u = np.sqrt(np.mean(scale_src["dudt"] ** 2))
+    assert np.max(np.abs(g["dudt"][idx] - ref["dudt"])) <= 1e-4 * rms_u
+    np.testing.assert_allclose(g["vsig"][idx], ref["vsig"], rtol=1e-5)
+
+
+# ------------------------------------------------------------------ fixed h
+def test_c1_lattice_4096_fixed_h(api, ctx):
+    """4096 particles, 16^3 lattice jittered by +-0.1 spacing, h = 1.2348 spacing."""
+    box = inputs.lattice_box(16, jitter=0.1, seed=1)
+    g = gpu_fixed_h(api, ctx, box)
+    ref = orc.full_step(box, iterate_h=False)
+    check_density(g, ref, box)
+    np.testing.assert_allclose(g["P"], ref["P"], rtol=1e-5)
+    np.testing.assert_allclose(g["c"], ref["c"], rtol=1e-5)
+    np.testing.assert_allclose(g["f"], ref["f"], rtol=1e-5)
+    check_force(g, ref)
+    m = box.m.astype(np.float64)
+    red = g["reductions"]
+    assert np.all(np.abs(red[0:3]) <= 1e-5 * np.sum(m * np.linalg.norm(ref["a"], axis=1)))
+    assert abs(red[3]) <= 1e-5 * np.sum(m * np.abs(ref["dudt"])) + 1e-5 * np.sum(m * np.abs((box.v * ref["a"]).sum(1)))
+    np.testing.assert_allclose(red[4:8], ref["reductions"][4:8], rtol=1e-6, atol=1e-9)
+
+
+def test_perfect_lattice_56_neighbours(api, ctx):
+    box = inputs.lattice_box(16, jitter=0.0, v_sigma=0.0)
+    g = gpu_fixed_h(api, ctx, box)
+    assert np.all(g["count"] == 56)
+    ref = orc.full_step(box, iterate_h=False)
+    np.testing.assert_allclose(g["rho"], ref["rho"], rtol=1e-6)
+    scale = np.max(ref["P"] / ref["rho"]) * 16
+    assert np.max(np.abs(g["a"])) < 1e-4 * scale       # a lattice at rest feels no force
+
+
+def _h_for_support(H):
+    """An FP32 h whose support radius rounds to exactly H."""
+    h = np.float32(H / float(orc.GAMMA_K))
+    for _ in range(64):
+        got = np.float32(orc.GAMMA_K * h)
+        if got == np.float32(H):
+            return h
+        h = np.nextafter(h, np.float32(np.inf) if got < H else np.float32(0))
+    raise AssertionError("no FP32 h maps to H")
+
+
+def test_exact_ties_at_the_cutoff(api, ctx):
+    """H = 2 spacing exactly on a perfect lattice: the 6 neighbours at distance 2a are out."""
+    box = inputs.lattice_box(16, jitter=0.0, v_sigma=0.0)
+    box.h[:] = _h_for_support(2.0 / 16)
+    g = gpu_fixed_h(api, ctx, box, force=True)
+    assert np.all(g["count"] == 6 + 12 + 8)
+    assert g["stats"]["n_pairs"] > 0
+    ref = orc.full_step(box, iterate_h=False)
+    check_density(g, ref, box)
+    check_force(g, ref)
+
+
+def test_ragged_sizes_and_tiny_boxes(api, ctx):
+    for n_side, jit in ((3, 0.3), (5, 0.2), (11, 0.45)):
+        box = inputs.lattice_box(n_side, jitter=jit, seed=n_side)
+        box.h[:] *= 0.7 if n_side == 3 else 1.0
+        g = gpu_fixed_h(api, ctx, box)
+        ref = orc.full_step(box, iterate_h=False)
+        check_density(g, ref, box)
+        check_force(g, ref)
+
+
+def test_single_particle(api, ctx):
+    box = inputs.lattice_box(1, jitter=0.0)
+    box.h[:] = 0.1
+    g = gpu_fixed_h(api, ctx, box)
+    assert g["count"][0] == 0
+    np.testing.assert_allclose(g["rho"][0], box.m[0] * orc.kernel_w(0.0, orc.support_radius(box.h)[0]), rtol=1e-6)
+    assert np.all(g["a"] == 0)
+
+
+def test_plummer_variable_h_with_splits(api):
+    box = inputs.plummer_box(n=20000, n_spheres=4, scale=0.05, seed=3)
+    api_ctx = make_ctx(api, leaf_max=48)
+    try:
+        g = gpu_fixed_h(api, api_ctx, box)
+    finally:
+        api.sph_ctx_destroy(api_ctx)
+    assert g["stats"]["n_cells"] > g["stats"]["n_selfs"]      # the tree was split
+    ref = orc.full_step(box, iterate_h=False, method="kdtree")
+    check_density(g, ref, box)
+    check_force(g, ref)
+
+
+def test_open_box_and_box_length(api, ctx):
+    box = inputs.plummer_box(n=6000, n_spheres=2, scale=0.06, seed=8)
+    L = 3.7
+    box.x *= L
+    box.x[box.x >= L] = 0.0
+    box.h *= np.float32(L)
+    box.m *= np.float32(L ** 3)
+    box.L = L
+    for periodic in (True, False):
+        box.periodic = periodic
+        g = gpu_fixed_h(api, ctx, box)
+        ref = orc.full_step(box, iterate_h=False, method="kdtree")
+        check_density(g, ref, box)
+        check_force(g, ref)
+
+
+# ------------------------------------------------------------------ decomposition
+def test_decomposition_matches_the_paper_rules(api):
+    box = inputs.plummer_box(n=8000, n_spheres=3, scale=0.04, seed=5)
+    leaf = 32
+    c = make_ctx(api, leaf_max=leaf)
+    try:
+        b = api.box_from(c, box)
+        b.build()
+        cells = b.cells()
+        items = b.interactions()
+        b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    D = dc.decompose(box.x, orc.support_radius(box.h), box.L, True, leaf_max=leaf)
+    keys = [(int(l), tuple(int(v) for v in ijk)) for l, ijk in zip(cells["level"], cells["ijk"])]
+    assert set(keys) == set(D.cells)
+    for k, cnt, sp in zip(keys, cells["count"], cells["split"]):
+        assert cnt == len(D.cells[k]) and bool(sp) == (k in D.split)
+    selfs = {keys[a] for kd, a in zip(items["kind"], items["a"]) if kd == 0}
+    assert selfs == D.selfs
+    pairs = set()
+    for kd, a, bb, ax in zip(items["kind"], items["a"], items["b"], items["axis"]):
+        if kd == 1:
+            (d, ca), (_, cb) = keys[a], keys[bb]
+            pairs.add((d, ca, cb, dc.AXES[ax]))
+    assert pairs == D.pairs
+
+
+# ------------------------------------------------------------------ h iteration
+def _gpu_iterate(api, ctx, box):
+    b = api.box_from(ctx, box)
+    st, nu, it = b.h_update()
+    out = {"h": b.get("h"), "rho": b.get("rho"), "nngb": b.get("nngb"), "conv": b.get("converged"),
+           "iters": it, "unconverged": nu, "stats": b.stats()}
+    b.force()
+    out["a"] = b.get("a")
+    b.close()
+    return out
+
+
+def test_h_iteration_matches_oracle(api, ctx):
+    box = inputs.lattice_box(12, jitter=0.3, seed=4)
+    box.h = (box.h * np.random.default_rng(2).uniform(0.7, 1.4, box.n)).astype(np.float32)
+    g = _gpu_iterate(api, ctx, box)
+    assert g["unconverged"] == 0 and g["conv"].all()
+    assert np.all(np.abs(g["nngb"] - 48) <= 1e-4 * 48 * 1.01)
+    h, conv, it, dens = orc.h_iterate(box.x, box.m, box.h, box.L, True, tol=1e-4)
+    assert conv.all()
+    np.testing.assert_allclose(g["h"], h, rtol=1e-4)
+
+
+def test_h_iteration_variable_h_with_rebuild(api):
+    box = inputs.plummer_box(n=20000, n_spheres=4, scale=0.03, seed=6)
+    box.h = (box.h * np.float32(0.6)).astype(np.float32)   # forces h to grow past the cell splits
+    c = make_ctx(api, leaf_max=64)
+    try:
+        g = _gpu_iterate(api, c, box)
+    finally:
+        api.sph_ctx_destroy(c)
+    assert g["unconverged"] == 0
+    h, conv, it, dens = orc.h_iterate(box.x, box.m, box.h, box.L, True, tol=1e-4, method="kdtree")
+    assert conv.all()
+    np.testing.assert_allclose(g["h"], h, rtol=1e-4)
+    np.testing.assert_allclose(g["rho"], dens["rho"], rtol=3e-4)
+
+
+# ------------------------------------------------------------------ inputs and errors
+def test_invalid_inputs_are_rejected(api, ctx):
+    box = inputs.lattice_box(6, jitter=0.2)
+    for mutate, status in (
+        (lambda b: b.x.__setitem__((3, 1), np.nan), "SPH_E_INVALID"),
+        (lambda b: b.x.__setitem__((4, 0), b.L), "SPH_E_INVALID"),
+        (lambda b: b.h.__setitem__(5, 0.0), "SPH_E_INVALID"),
+        (lambda b: b.m.__setitem__(2, -1.0), "SPH_E_INVALID"),
+        (lambda b: b.h.__setitem__(0, 0.3), "SPH_E_H_TOO_LARGE"),
+    ):
+        bad = box.subset(np.arange(box.n))
+        mutate(bad)
+        b = api.box_from(ctx, bad)
+        with pytest.raises(api.SphError) as e:
+            b.density()
+        assert status in str(e.value)
+        b.close()
+    with pytest.raises(api.SphError):
+        api.sph_box_create(ctx, 0, 1.0, True)
+
+
+def test_device_pointers_match_host_path(api, ctx):
+    torch = pytest.importorskip("torch")
+    box = inputs.lattice_box(10, jitter=0.3, seed=12, v_sigma=0.1)
+    host = gpu_fixed_h(api, ctx, box)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    b = api.Box(ctx, box.n, box.L, True)
+    b.set(d(box.x), d(box.v), d(box.m), d(box.u), d(box.h))
+    b.density()
+    b.force()
+    rho = torch.empty(box.n, dtype=torch.float32, device="cuda")
+    b.get("rho", out=rho)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(rho.cpu().numpy(), host["rho"], rtol=1e-6)
+    np.testing.assert_array_equal(b.get("count"), host["count"])
+    b.close()
+
+
+# ------------------------------------------------------------------ full-size workload, sampled
+@pytest.mark.slow
+def test_plummer_262144_sampled(api, ctx):
+    """The 262,144-particle variable-h box (16 Plummer spheres + background): sampled parity."""
+    box = inputs.plummer_box()
+    g = gpu_fixed_h(api, ctx, box)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(box.n, 2000, replace=False))
+    H = orc.support_radius(box.h)
+    ref = orc.density(box.x, box.m, H, box.L, True, targets=idx, method="kdtree")
+    check_density(g, ref, box, idx)
+    # force on a smaller sample needs every neighbour's density: take it for all
+    dens = orc.density(box.x, box.m, H, box.L, True, method="kdtree")
+    gh = orc.ghost(dens["rho"], dens["S_m"], box.u)
+    fi = idx[:500]
+    fo = orc.force(box.x, box.v, box.m, H, dens["rho"], gh["P"], gh["c"], gh["f"], box.L, True,
+                   targets=fi, method="kdtree")
+    check_force(g, fo, fi)
+    # h iteration from the same start: every particle's iteration is independent
+    gi = _gpu_iterate(api, ctx, box)
+    assert gi["unconverged"] == 0
+    hs, conv, _, _ = orc.h_iterate(box.x, box.m, box.h, box.L, True, tol=1e-4, targets=idx[:300],
+                                   method="kdtree")
+    assert conv.all()
+    np.testing.assert_allclose(gi["h"][idx[:300]], hs, rtol=1e-4)

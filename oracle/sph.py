@@ -178,8 +178,8 @@ def density(x, m, H, L, periodic, targets=None, method="auto"):
     """Density pass for ``targets`` (default: all) at fixed support radii H (FP64 array).
 
     Returns a dict of FP64 arrays over the targets:
-    rho, S_m = sum m_j (3W + r dW/dr), nw = sum W, S = sum (3W + r dW/dr),
-    count (int64, j != i), Nw = (4 pi/3) H^3 nw.
+    rho, S_m = sum m_j (3W + r dW/dr), Sr_m = sum_{j != i} m_j r dW/dr,
+    nw = sum W, S = sum (3W + r dW/dr), count (int64, j != i), Nw = (4 pi/3) H^3 nw.
     """
     n = x.shape[0]
     targets = np.arange(n) if targets is None else np.asarray(targets, dtype=np.int64)
@@ -198,6 +198,7 @@ def density(x, m, H, L, periodic, targets=None, method="auto"):
     out = {
         "rho": np.bincount(t, weights=m[j] * w, minlength=nt) + mt * w0,
         "S_m": np.bincount(t, weights=m[j] * g, minlength=nt) + mt * 3.0 * w0,
+        "Sr_m": np.bincount(t, weights=m[j] * r * dw, minlength=nt),
         "nw": np.bincount(t, weights=w, minlength=nt) + w0,
         "S": np.bincount(t, weights=g, minlength=nt) + 3.0 * w0,
         "count": np.bincount(t, minlength=nt).astype(np.int64),
@@ -236,7 +237,7 @@ def h_iterate(x, m, h0, L, periodic, n_ngb=N_NGB, tol=1e-4, max_iter=30, targets
     hi = np.full_like(h, np.inf)
     conv = np.zeros(len(h), dtype=bool)
     iters = np.zeros(len(h), dtype=np.int64)
-    final = {k: np.zeros(len(h)) for k in ("rho", "S_m", "nw", "S", "Nw")}
+    final = {k: np.zeros(len(h)) for k in ("rho", "S_m", "Sr_m", "nw", "S", "Nw")}
     final["count"] = np.zeros(len(h), dtype=np.int64)
     active = np.arange(len(h))
     for it in range(1, max_iter + 1):
@@ -272,17 +273,22 @@ def h_iterate(x, m, h0, L, periodic, n_ngb=N_NGB, tol=1e-4, max_iter=30, targets
 
 
 # -------------------------------------------------------------------------- ghost
-def ghost(rho, S_m, u, gamma=GAMMA_GAS):
+def ghost(rho, Sr_m, u, gamma=GAMMA_GAS):
     """Derived per-particle quantities between the passes.
 
     P = (gamma - 1) rho u; c = sqrt(gamma P / rho);
-    f = [1 + h/(3 rho) d rho/d h]^-1 = [1 - S_m/(3 rho)]^-1.
+    f = [1 + h/(3 rho) d rho/d h]^-1.  With h d rho/dh = -(3 rho + sum_j m_j r dW/dr)
+    this is f = 3 rho / (-sum_{j != i} m_j r dW/dr) (``Sr_m``), the same quantity
+    without the cancellation of 1 - S_m/(3 rho).  Reading: f is undefined when no
+    other particle lies inside the support (rho then does not depend on h beyond
+    the self term); it is taken as 1 there.
     """
     rho = np.asarray(rho, dtype=np.float64)
     u = np.asarray(u, dtype=np.float64)
+    Sr_m = np.asarray(Sr_m, dtype=np.float64)
     P = (gamma - 1.0) * rho * u
     c = np.sqrt(gamma * P / rho)
-    f = 1.0 / (1.0 - np.asarray(S_m, dtype=np.float64) / (3.0 * rho))
+    f = np.where(Sr_m < 0, 3.0 * rho / np.where(Sr_m < 0, -Sr_m, 1.0), 1.0)
     return {"P": P, "c": c, "f": f}
 
 
@@ -370,7 +376,7 @@ def full_step(box, n_ngb=N_NGB, tol=1e-4, max_iter=30, alpha=ALPHA_VISC, gamma=G
         dens = density(x, m, H, box.L, box.periodic, method=method)
         conv = np.ones(box.n, dtype=bool)
         iters = np.ones(box.n, dtype=np.int64)
-    g = ghost(dens["rho"], dens["S_m"], box.u, gamma)
+    g = ghost(dens["rho"], dens["Sr_m"], box.u, gamma)
     fo = force(x, box.v, m, H, dens["rho"], g["P"], g["c"], g["f"], box.L, box.periodic,
                alpha, method=method)
     red = reductions(m, box.v, box.u, fo["a"], fo["dudt"])

@@ -118,7 +118,7 @@ def _prepare(box, alpha=sph.ALPHA_VISC, tol=1e-12):
     h, conv, _, dens = sph.h_iterate(box.x, box.m, box.h, box.L, box.periodic, tol=tol, max_iter=60)
     assert conv.all()
     H = float(sph.GAMMA_K) * h
-    g = sph.ghost(dens["rho"], dens["S_m"], box.u)
+    g = sph.ghost(dens["rho"], dens["Sr_m"], box.u)
     fo = sph.force(box.x, box.v, box.m, H, dens["rho"], g["P"], g["c"], g["f"], box.L, box.periodic,
                    alpha=alpha)
     return h, dens, g, fo
@@ -159,7 +159,7 @@ def test_two_particle_closed_form():
     d = sph.density(x, m, Hv, L, periodic=False)
     rho = mm * (sph.kernel_w(0, H) + sph.kernel_w(r, H))
     np.testing.assert_allclose(d["rho"], rho, rtol=1e-14)
-    g = sph.ghost(d["rho"], d["S_m"], u)
+    g = sph.ghost(d["rho"], d["Sr_m"], u)
     v = np.zeros((2, 3), np.float32)
     fo = sph.force(x, v, m, Hv, d["rho"], g["P"], g["c"], g["f"], L, False)
     Fk = g["f"][0] * g["P"][0] / rho ** 2
@@ -227,7 +227,7 @@ def test_brute_force_and_tree_search_agree():
     b = sph.density(box.x, box.m, H, box.L, True, method="kdtree")
     assert np.array_equal(a["count"], b["count"])
     np.testing.assert_allclose(a["rho"], b["rho"], rtol=1e-13)
-    g = sph.ghost(a["rho"], a["S_m"], box.u)
+    g = sph.ghost(a["rho"], a["Sr_m"], box.u)
     fa = sph.force(box.x, box.v, box.m, H, a["rho"], g["P"], g["c"], g["f"], box.L, True, method="brute")
     fb = sph.force(box.x, box.v, box.m, H, a["rho"], g["P"], g["c"], g["f"], box.L, True, method="kdtree")
     np.testing.assert_allclose(fa["a"], fb["a"], rtol=1e-10, atol=1e-12 * np.abs(fa["a"]).max())

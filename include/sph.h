@@ -148,6 +148,8 @@ sph_status sph_ctx_set_stream(sph_ctx* ctx, void* cuda_stream);
 /* The stream the context launches on, as a cudaStream_t cast to void*. */
 void* sph_ctx_stream(sph_ctx* ctx);
 
+/* Destroy a context.  Errors: SPH_E_BUSY while boxes or servers created on it
+ * are alive (destroy them first). */
 sph_status sph_ctx_destroy(sph_ctx* ctx);
 
 /* Text of the last error on this context (never NULL; "" when none). */
@@ -229,7 +231,10 @@ sph_status sph_get_cells(sph_box* box, int64_t cap, int32_t* level, int32_t* ijk
 
 /* Final interactions: kind[k] = 0 (self of cell a[k]) or 1 (pair a[k], b[k]
  * along axis[k] in 0..12, from a towards b).  Cell numbers index the
- * sph_get_cells arrays.  Selfs come first.  Synchronises. */
+ * sph_get_cells arrays.  Selfs come first.  Synchronises.
+ * Axis numbering: the offset of b from a in cell units (periodic image
+ * included) is, for axis 0..12: (1,0,0) (-1,1,0) (0,1,0) (1,1,0) (-1,-1,1)
+ * (0,-1,1) (1,-1,1) (-1,0,1) (0,0,1) (1,0,1) (-1,1,1) (0,1,1) (1,1,1). */
 sph_status sph_get_interactions(sph_box* box, int64_t cap, int32_t* kind, int32_t* a,
                                 int32_t* b, int32_t* axis, int64_t* n_out);
 

@@ -583,7 +583,8 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
 // Cells above SORT_SMALL particles also list their (cell, axis) segments for
 // the global sort.
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
-                             unsigned int* __restrict__ big_off, int* __restrict__ big_count, int cap_big) {
+                             unsigned int* __restrict__ big_off, unsigned long long* __restrict__ big_count,
+                             int cap_big) {
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int ax = T.axes[id];
     if (!ax) continue;
@@ -592,8 +593,12 @@ __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big
     T.sortbase[id] = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
     atomicAdd(&Lq.counts[4], na);
     if (c > SORT_SMALL) {
-      const int s0 = atomicAdd(&big_count[0], na);
-      const unsigned int e0 = atomicAdd(reinterpret_cast<unsigned int*>(&big_count[1]), (unsigned int)na * c);
+      // one atomic hands out the segment numbers and their storage together, so
+      // storage follows segment order (the order the global sort produces)
+      const unsigned long long t =
+          atomicAdd(big_count, ((unsigned long long)na << 40) | (unsigned long long)((unsigned int)na * c));
+      const int s0 = (int)(t >> 40);
+      const unsigned int e0 = (unsigned int)(t & ((1ull << 40) - 1ull));
       int q = 0;
       for (int a = 0; a < 13; ++a) {
         if (!(ax & (1u << a))) continue;

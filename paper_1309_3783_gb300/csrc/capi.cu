@@ -30,7 +30,7 @@ __global__ void k_particle_limits(long long, Tree, const unsigned int*, float*);
 __global__ void k_shift(long long, int, const unsigned long long*, const unsigned int*, const unsigned int*, Tree,
                         const BoxDesc*, const double*, const float*, const float*, float4*, float4*);
 __global__ void k_mark_axes(Lists, int, Tree);
-__global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, int*, int);
+__global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, unsigned long long*, int);
 __global__ void k_sort_small(Tree, int, const float4*, const float4*, float*, unsigned int*);
 __global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, const float4*, const float4*,
                                 unsigned long long*, unsigned int*);
@@ -354,21 +354,22 @@ sph_status Engine::build_once(bool* retry) {
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p);
 
   // ---- sorted projections
-  CK(big_count.reserve(2));
+  CK(big_count.reserve(1));
   if (cap_big == 0) {
     cap_big = 4096;
     CK(big_node.reserve(cap_big));
     CK(big_axis.reserve(cap_big));
     CK(big_off.reserve(cap_big));
   }
-  CK(cudaMemsetAsync(big_count.p, 0, 2 * sizeof(int), st));
+  CK(cudaMemsetAsync(big_count.p, 0, sizeof(unsigned long long), st));
   k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T);
   k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
                                               cap_big);
   CK(cudaGetLastError());
-  int lc[8], bc[2];
+  int lc[8];
+  unsigned long long bcw = 0;
   CK(cudaMemcpyAsync(lc, l_counts.p, sizeof(lc), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(bc, big_count.p, sizeof(bc), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&bcw, big_count.p, sizeof(bcw), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int last_q = lc[2 + (rounds & 1)];
@@ -379,8 +380,9 @@ sph_status Engine::build_once(bool* retry) {
     *retry = true;
     return SPH_OK;
   }
+  const long long bc[2] = {(long long)(bcw >> 40), (long long)(bcw & ((1ull << 40) - 1ull))};
   if (bc[0] > cap_big) {
-    cap_big = 2 * bc[0];
+    cap_big = (int)(2 * bc[0]);
     CK(big_node.reserve(cap_big));
     CK(big_axis.reserve(cap_big));
     CK(big_off.reserve(cap_big));
@@ -391,8 +393,8 @@ sph_status Engine::build_once(bool* retry) {
   n_pairs = lc[1];
   n_segments = lc[4];
   n_entries = (unsigned int)lc[5];
-  n_big = bc[0];
-  n_big_entries = (unsigned int)bc[1];
+  n_big = (int)bc[0];
+  n_big_entries = bc[1];
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, pos4.p, cen4.p, sort_r.p, sort_i.p);
@@ -729,6 +731,7 @@ using sph::Engine;
 
 struct sph_box {
   sph_ctx* ctx = nullptr;
+  int device = 0;
   Engine* eng = nullptr;
 };
 
@@ -795,6 +798,13 @@ void* sph_ctx_stream(sph_ctx* c) { return c ? (void*)c->cur : nullptr; }
 
 sph_status sph_ctx_destroy(sph_ctx* c) {
   if (!c) return SPH_E_INVALID;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (c->live > 0) {
+      c->last = "context still has live boxes or servers";
+      return SPH_E_BUSY;
+    }
+  }
   cudaSetDevice(c->device);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
@@ -811,6 +821,7 @@ sph_status sph_box_create(sph_ctx* c, int64_t n, double L, int periodic, sph_box
   cudaSetDevice(c->device);
   sph_box* b = new sph_box;
   b->ctx = c;
+  b->device = c->device;
   b->eng = new Engine(c->prm, c->device, c->cur);
   sph_status s = b->eng->set_boxes({sph::BoxSpec{L, n, periodic ? 1 : 0}});
   if (s != SPH_OK) {
@@ -818,6 +829,10 @@ sph_status sph_box_create(sph_ctx* c, int64_t n, double L, int periodic, sph_box
     delete b->eng;
     delete b;
     return s == SPH_E_CUDA ? SPH_E_OOM : s;
+  }
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->live++;
   }
   *out = b;
   return SPH_OK;
@@ -842,9 +857,13 @@ sph_status sph_box_count_pairs(sph_box* b, int on) {
 
 sph_status sph_box_destroy(sph_box* b) {
   if (!b) return SPH_E_INVALID;
-  cudaSetDevice(b->ctx->device);
-  cudaStreamSynchronize(b->ctx->cur);
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->eng->st);
   delete b->eng;
+  {
+    std::lock_guard<std::mutex> g(b->ctx->mu);
+    b->ctx->live--;
+  }
   delete b;
   return SPH_OK;
 }

@@ -127,7 +127,7 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
 struct DensShared {
   float4 p[32];     // position, 1/H (units of L)
   float4 a[32];     // H^2, band, m, H (physical)
-  float4 acc[32];   // sum m w, sum m g, sum w, sum g
+  float4 acc[32];   // sum m w, sum m q w', sum w, sum q w'
   unsigned int cnt[32];
   int g[32];
   unsigned char act[32];
@@ -171,7 +171,7 @@ __device__ __forceinline__ void dens_step(const DensI& I, DensShared& S, int k, 
     float w, dw;
     const float q = r * I.invH;
     spline_w_dw(q, w, dw);
-    const float gg = fmaf(q, dw, 3.0f * w);
+    const float gg = q * dw;                 // q w'(q) = r dW/dr in units of W
     acc.x = fmaf(Ja.z, w, acc.x);
     acc.y = fmaf(Ja.z, gg, acc.y);
     acc.z += w;
@@ -182,7 +182,7 @@ __device__ __forceinline__ void dens_step(const DensI& I, DensShared& S, int k, 
     float w, dw;
     const float q = r * J.w;
     spline_w_dw(q, w, dw);
-    const float gg = fmaf(q, dw, 3.0f * w);
+    const float gg = q * dw;
     float4 a = S.acc[k];
     a.x = fmaf(I.m, w, a.x);
     a.y = fmaf(I.m, gg, a.y);
@@ -622,7 +622,6 @@ __global__ void k_ghost(long long N, int mode, int it, int max_iter, float gamma
     const float m = cen4[p].w;
     const float4 a = dacc[p];
     const float sw = a.z + 1.0f;          // self term w(0) = 1
-    const float sg = a.w + 3.0f;          // 3 w(0) + 0
     const float Nw = (32.0f / 3.0f) * sw; // (4 pi / 3) H^3 n with n = (8/pi) sum w / H^3
     const float F = Nw - n_ngb;
     const bool ok = fabsf(F) <= tol * n_ngb;
@@ -631,7 +630,8 @@ __global__ void k_ghost(long long N, int mode, int it, int max_iter, float gamma
       float lo = hlo[i], hi = hhi[i];
       if (F < 0.0f) lo = hc;
       else hi = hc;
-      const float dN = gamma_k * (32.0f / 3.0f) * (3.0f * sw - sg) / H;
+      // dN~/dh = gamma_K (4 pi/3) H^2 (3 n - sum (3W + r W')) = -gamma_K (32/3) sum q w' / H
+      const float dN = -gamma_k * (32.0f / 3.0f) * a.w / H;
       float hn = dN > 0.0f ? hc - F / dN : (F < 0.0f ? 2.0f * hc : 0.5f * hc);
       hn = fminf(fmaxf(hn, 0.5f * hc), 2.0f * hc);
       if (lo > 0.0f && isfinite(hi) && !(hn > lo && hn < hi)) hn = 0.5f * (lo + hi);
@@ -653,11 +653,12 @@ __global__ void k_ghost(long long N, int mode, int it, int max_iter, float gamma
     const float ih = 1.0f / H;
     const float K3 = SPH_KNORM * ih * ih * ih;
     const float rho = K3 * (a.x + m);
-    const float Sm = K3 * (a.y + 3.0f * m);
     const float u = vel4[p].w;
     const float P = (gamma_gas - 1.0f) * rho * u;
     const float c = sqrtf(gamma_gas * P / rho);
-    const float f = 1.0f / (1.0f - Sm / (3.0f * rho));
+    // f = [1 + h/(3 rho) d rho/dh]^-1 = 3 rho / (-sum_j m_j r W'), without cancellation;
+    // 1 when no other particle lies inside the support
+    const float f = a.y < 0.0f ? -3.0f * (a.x + m) / a.y : 1.0f;
     ghost4[p] = make_float4(rho, f * P / (rho * rho), c, f);
   }
 }
@@ -785,7 +786,7 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
     float* fo = reinterpret_cast<float*>(out);
     switch (field) {
       case SPH_FIELD_RHO: fo[i] = K3 * (a.x + m); break;
-      case SPH_FIELD_DRHO_DH: fo[i] = -K3 * (a.y + 3.0f * m) / h[perm[p]]; break;
+      case SPH_FIELD_DRHO_DH: fo[i] = -K3 * fmaf(3.0f, a.x + m, a.y) / h[perm[p]]; break;
       case SPH_FIELD_NW: fo[i] = K3 * (a.z + 1.0f); break;
       case SPH_FIELD_NNGB: fo[i] = (32.0f / 3.0f) * (a.z + 1.0f); break;
       case SPH_FIELD_COUNT: reinterpret_cast<int*>(out)[i] = (int)dcnt[p]; break;

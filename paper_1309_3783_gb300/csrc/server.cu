@@ -152,6 +152,10 @@ sph_status sph_server_create(sph_ctx* ctx, int64_t budget_bytes, int32_t max_box
   s->eng = new sph::Engine(cv->prm, cv->device, s->st);
   cudaEventCreate(&s->e0);
   cudaEventCreate(&s->e1);
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->live++;
+  }
   *out = s;
   return SPH_OK;
 }
@@ -298,6 +302,10 @@ sph_status sph_server_destroy(sph_server* s) {
   delete s->eng;
   cudaEventDestroy(s->e0);
   cudaEventDestroy(s->e1);
+  {
+    std::lock_guard<std::mutex> g(s->ctx->mu);
+    s->ctx->live--;
+  }
   delete s;
   return SPH_OK;
 }

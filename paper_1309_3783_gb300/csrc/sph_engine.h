@@ -132,13 +132,14 @@ class Engine {
   DBuf<float> sort_r;
   DBuf<unsigned int> sort_i;
   int cap_big = 0;
-  DBuf<int> big_node, big_axis, big_count;
+  DBuf<int> big_node, big_axis;
+  DBuf<unsigned long long> big_count;   // segments << 40 | entries
   DBuf<unsigned int> big_off;
   DBuf<unsigned long long> ckey, ckey_tmp;
   DBuf<unsigned int> cval, cval_tmp;
 
   // pass results (sorted order)
-  DBuf<float4> dacc;              // sum m w, sum m (3w + q w'), sum w, sum (3w + q w')
+  DBuf<float4> dacc;              // sum m w, sum m q w', sum w, sum q w'
   DBuf<unsigned int> dcnt;
   DBuf<float4> ghost4;            // rho, f P / rho^2, c, f
   DBuf<float4> facc;              // a (3), du/dt
@@ -180,4 +181,5 @@ struct sph_ctx {
   cudaStream_t cur = nullptr;
   std::string last;
   std::mutex mu;
+  int live = 0;   // boxes and servers created on this context and not yet destroyed
 };

@@ -15,6 +15,10 @@ from paper_1309_3783_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
+# axis numbering of sph_get_interactions (include/sph.h): db from cell a to cell b
+GPU_AXES = [(1, 0, 0), (-1, 1, 0), (0, 1, 0), (1, 1, 0), (-1, -1, 1), (0, -1, 1), (1, -1, 1),
+            (-1, 0, 1), (0, 0, 1), (1, 0, 1), (-1, 1, 1), (0, 1, 1), (1, 1, 1)]
+
 
 @pytest.fixture(scope="module")
 def api():
@@ -39,14 +43,16 @@ def ctx(api):
 
 def gpu_fixed_h(api, ctx, box, force=True):
     b = api.box_from(ctx, box)
-    b.density()
-    out = {k: b.get(k) for k in ("count", "rho", "nw", "drho_dh", "nngb", "P", "c", "f")}
-    if force:
-        b.force()
-        for k in ("a", "dudt", "vsig", "reductions"):
-            out[k] = b.get(k)
-    out["stats"] = b.stats()
-    b.close()
+    try:
+        b.density()
+        out = {k: b.get(k) for k in ("count", "rho", "nw", "drho_dh", "nngb", "P", "c", "f")}
+        if force:
+            b.force()
+            for k in ("a", "dudt", "vsig", "reductions"):
+                out[k] = b.get(k)
+        out["stats"] = b.stats()
+    finally:
+        b.close()
     return out
 
 
@@ -60,12 +66,13 @@ def check_density(g, ref, box, idx=None):
     assert np.all(np.abs(g["drho_dh"][idx] - drho) <= 2e-5 * 3 * ref["rho"] / h)
 
 
-def check_force(g, ref, idx=None, ref_all=None):
+def check_force(g, ref, idx=None, ref_all=None, floor=0.0):
+    """floor: a force scale for configurations whose exact forces vanish (lattices at rest)."""
     idx = slice(None) if idx is None else idx
     scale_src = ref if ref_all is None else ref_all
-    rms = np.sqrt(np.mean(np.sum(scale_src["a"] ** 2, axis=1)))
+    rms = max(np.sqrt(np.mean(np.sum(scale_src["a"] ** 2, axis=1))), floor)
     assert np.max(np.abs(g["a"][idx] - ref["a"])) <= 1e-4 * rms
-    rms_u = np.sqrt(np.mean(scale_src["dudt"] ** 2))
+    rms_u = max(np.sqrt(np.mean(scale_src["dudt"] ** 2)), floor)
     assert np.max(np.abs(g["dudt"][idx] - ref["dudt"])) <= 1e-4 * rms_u
     np.testing.assert_allclose(g["vsig"][idx], ref["vsig"], rtol=1e-5)
 
@@ -118,13 +125,14 @@ def test_exact_ties_at_the_cutoff(api, ctx):
     assert g["stats"]["n_pairs"] > 0
     ref = orc.full_step(box, iterate_h=False)
     check_density(g, ref, box)
-    check_force(g, ref)
+    # the lattice is at rest: forces vanish; bound the error by the pressure force scale P / (rho H)
+    check_force(g, ref, floor=float(np.max(ref["P"] / ref["rho"] / ref["H"])))
 
 
 def test_ragged_sizes_and_tiny_boxes(api, ctx):
     for n_side, jit in ((3, 0.3), (5, 0.2), (11, 0.45)):
         box = inputs.lattice_box(n_side, jitter=jit, seed=n_side)
-        box.h[:] *= 0.7 if n_side == 3 else 1.0
+        box.h[:] = np.minimum(box.h, np.float32(0.12))    # periodic boxes need H < L/4
         g = gpu_fixed_h(api, ctx, box)
         ref = orc.full_step(box, iterate_h=False)
         check_density(g, ref, box)
@@ -193,7 +201,7 @@ def test_decomposition_matches_the_paper_rules(api):
     for kd, a, bb, ax in zip(items["kind"], items["a"], items["b"], items["axis"]):
         if kd == 1:
             (d, ca), (_, cb) = keys[a], keys[bb]
-            pairs.add((d, ca, cb, dc.AXES[ax]))
+            pairs.add((d, ca, cb, GPU_AXES[ax]))
     assert pairs == D.pairs
 
 
@@ -210,7 +218,7 @@ def _gpu_iterate(api, ctx, box):
 
 
 def test_h_iteration_matches_oracle(api, ctx):
-    box = inputs.lattice_box(12, jitter=0.3, seed=4)
+    box = inputs.lattice_box(16, jitter=0.3, seed=4)
     box.h = (box.h * np.random.default_rng(2).uniform(0.7, 1.4, box.n)).astype(np.float32)
     g = _gpu_iterate(api, ctx, box)
     assert g["unconverged"] == 0 and g["conv"].all()
@@ -286,7 +294,7 @@ def test_plummer_262144_sampled(api, ctx):
     check_density(g, ref, box, idx)
     # force on a smaller sample needs every neighbour's density: take it for all
     dens = orc.density(box.x, box.m, H, box.L, True, method="kdtree")
-    gh = orc.ghost(dens["rho"], dens["S_m"], box.u)
+    gh = orc.ghost(dens["rho"], dens["Sr_m"], box.u)
     fi = idx[:500]
     fo = orc.force(box.x, box.v, box.m, H, dens["rho"], gh["P"], gh["c"], gh["f"], box.L, True,
                    targets=fi, method="kdtree")

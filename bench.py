@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the SPH density + force step on GB300 (one JSON line).
+
+Workload: the variable-h single box -- 262,144 particles, 50 % uniform
+background plus 16 Plummer spheres (scale radius 0.02, seeded centres),
+periodic unit box, equal masses, u = 1, v ~ N(0, 0.1), h iterated to 48
+neighbours.  One step is the whole path: decomposition build (keys, sort, cell
+tree, interaction lists, particle offsets, axis sorts), density with the h
+iteration (starting from the previous step's converged h), ghost, force, FP64
+conservation reductions and a kick-drift-kick update with a fixed time step.
+Every step starts from the same resident input state, so the steps are
+identical work.
+
+value : particle-updates/s with the inputs resident in device memory
+        (each step copies the resident input state into the box, device to device).
+e2e   : the same through the C-ABI with host buffers: the host->device copy of
+        x, v, m, u, h and the device->host read of a, du/dt, rho and h are inside
+        the timed region of every step.
+
+``--impl reference`` times the FP64 oracle (the only reference this method has:
+the paper publishes no code) on the host cores, on a bounded sample of the same
+workload per step.  Under torchrun (N > 1) every rank runs an independent replica
+on its own GPU ("replicas only": the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1309_3783_gb300 import inputs  # noqa: E402
+
+METRIC = "SPH density+force particle-updates/s"
+UNIT = "particle-updates/s"
+WORKLOAD = "plummer-262144"
+SAMPLE_N = 16384            # the oracle's bounded sample: the same recipe at 1/16 of the particles
+
+# Algorithmic FP32 operations per interacting pair, counted from the formulas
+# the kernels evaluate (mul/add = 1, FMA = 2, sqrt/rsqrt/div = 1):
+#   density: per unordered pair 9 (separation 3, r^2 5, r 1), per side that
+#            interacts 19 (q 1, w 5, w' 4, q w' 1... accumulations 8);
+#   force:   per unordered pair 76 (separation, r^2, 1/r, two kernel
+#            derivatives, v.x, viscosity, both sides' accumulations).
+FLOPS_DENSITY_PAIR = 9
+FLOPS_DENSITY_SIDE = 19
+FLOPS_FORCE_PAIR = 76
+
+# FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
+SM_COUNT, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1309_3783_gb300 import build as libbuild
+    from paper_1309_3783_gb300 import sph
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    box = inputs.plummer_box(seed=1 + rank)
+    n = box.n
+    ctx = sph.sph_ctx_create(device=local_rank)
+    stream = torch.cuda.Stream()
+    sph.sph_ctx_set_stream(ctx, stream.cuda_stream)
+    b = sph.Box(ctx, n, box.L, True)
+
+    # resident input state: h converged once (a simulation's previous step), dt from CFL
+    b.set(box.x, box.v, box.m, box.u, box.h)
+    b.h_update()
+    b.force()
+    dt = b.cfl_dt()
+    h_conv = b.get("h").copy()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).to(f"cuda:{local_rank}")
+    xd, vd, md, ud, hd = dev(box.x), dev(box.v), dev(box.m), dev(box.u), dev(h_conv)
+    torch.cuda.synchronize()
+
+    def step_device():
+        b.set(xd, vd, md, ud, hd)
+        return b.step(dt)
+
+    # algorithmic work of one step's passes: exact pair counts (untimed)
+    b.count_pairs(True)
+    b.set(xd, vd, md, ud, hd)
+    b.density()
+    b.force()
+    st = b.stats()
+    b.count_pairs(False)
+    flops_density_pair = FLOPS_DENSITY_PAIR * st["density_pairs_cellpair"] + FLOPS_DENSITY_SIDE * st["density_sides_cellpair"]
+    flops_force_pair = FLOPS_FORCE_PAIR * st["force_pairs_cellpair"]
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local_rank}")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = sph.sph_launch_count()
+    b.profile(True)
+    statuses = []
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.profiler.start()                 # ncu --profile-from-start off captures from here
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                       # L2 flush between steps (outside the events)
+                evs[k][0].record(stream)
+            statuses.append(step_device())
+            with torch.cuda.stream(stream):
+                evs[k][1].record(stream)
+        barrier()
+        torch.cuda.profiler.stop()
+    launches = sph.sph_launch_count() - l0
+    prof = b.get_profile()
+    b.profile(False)
+    ms = [s.elapsed_time(e) for s, e in evs]
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=f"cuda:{local_rank}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms / 1e3)
+
+    # e2e through the C-ABI with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    xh, vh, mh, uh, hh = pin(box.x), pin(box.v), pin(box.m), pin(box.u), pin(h_conv)
+    a_out = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    s_out = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3)]
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        b.set(xh, vh, mh, uh, hh)
+        b.step(dt)
+        b.get("a", out=a_out)
+        b.get("dudt", out=s_out[0])
+        b.get("rho", out=s_out[1])
+        b.get("h", out=s_out[2])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=f"cuda:{local_rank}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = world * n * e2e_steps / e2e_s
+
+    # roofline of the dominant kernel (FP32 ALU bound)
+    dom = max(("density_pair", "force_pair"), key=lambda k: prof[k]["ms"])
+    calls = max(prof[dom]["calls"], 1)
+    avg_ms = prof[dom]["ms"] / calls
+    flops = flops_density_pair if dom == "density_pair" else flops_force_pair
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(dom)
+        except (OSError, ValueError):
+            traffic = None
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_gpu": n, "h": "converged from the previous step",
+                   "dt": dt, "leaf_max": 400, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 12 + 4 + 4 + 4),
+                "d2h_bytes_per_step": n * (12 + 4 + 4 + 4), "steps": e2e_steps},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "phases_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["calls"]},
+        "pairs": {"density": st["density_pairs"], "density_candidates": st["density_candidates"],
+                  "force": st["force_pairs"], "force_candidates": st["force_candidates"],
+                  "guard_rechecks": st["guard_rechecks"]},
+        "h_iterations_last_step": b.stats()["h_iterations"],
+    }
+    b.close()
+    sph.sph_ctx_destroy(ctx)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(box)
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+# ------------------------------------------------------------------ oracle arm
+def _oracle_sample_box():
+    """The workload's recipe at 1/16 of the particles, with h converged by the oracle."""
+    from oracle import sph as orc
+    box = inputs.plummer_box(n=SAMPLE_N, seed=1)
+    h, conv, _, _ = orc.h_iterate(box.x, box.m, box.h, box.L, True, method="kdtree")
+    box.h = h.astype(np.float32)
+    return box
+
+
+def _oracle_step(box):
+    from oracle import sph as orc
+    return orc.full_step(box, iterate_h=True, method="kdtree")
+
+
+def cpu_baseline(_box=None):
+    sample = _oracle_sample_box()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        _oracle_step(sample)
+        reps += 1
+        if time.perf_counter() - t0 > 10.0 or reps >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sample.n * reps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} oracle steps (h iteration from converged h, force, reductions; FP64) on the "
+                      f"same Plummer recipe at {sample.n} particles; k-d tree search on all cores, numpy "
+                      f"arithmetic on one"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sample = _oracle_sample_box()
+    for _ in range(args.warmup):
+        _oracle_step(sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _oracle_step(sample)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample.n * args.steps / total
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_step": sample.n,
+                   "sample": "same recipe at 1/16 of the particles"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{sample.n}-particle Plummer box per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -121,14 +121,31 @@ typedef struct sph_stats {
     int32_t h_iterations;       /* density passes of the last sph_h_update            */
     int32_t rebuilds;           /* tree rebuilds during the last sph_h_update         */
     int64_t n_unconverged;
-    /* filled only when pair counting is on (sph_box_count_pairs) */
+    /* filled only when pair counting is on (sph_box_count_pairs); summed over
+       the density passes of the last sph_density / sph_h_update and the force
+       passes since then */
     int64_t density_pairs;      /* unordered pairs with r < max(H_i, H_j)             */
     int64_t density_sides;      /* sum over those pairs of [r < H_i] + [r < H_j]      */
     int64_t density_candidates; /* unordered pairs whose distance was evaluated       */
+    int64_t density_pairs_cellpair;      /* ... of which in cell-pair interactions     */
+    int64_t density_sides_cellpair;
+    int64_t density_candidates_cellpair;
     int64_t force_pairs;        /* unordered pairs with r < max(H_i,H_j), r > 0       */
     int64_t force_candidates;
+    int64_t force_pairs_cellpair;
+    int64_t force_candidates_cellpair;
     int64_t guard_rechecks;     /* predicate decisions re-taken in FP64               */
 } sph_stats;
+
+/* Device time of one phase of the path (CUDA events on the context stream). */
+typedef struct sph_profile_entry {
+    char name[32];              /* ingest, keys_sort, tree, lists, shift, axis_sort,
+                                   density_pair, density_self, ghost, force_pair,
+                                   force_self, reduce, kick_drift, output        */
+    int64_t calls;              /* times the phase ran while recording                */
+    int64_t launches;           /* kernel launches inside it                          */
+    double ms;                  /* summed device time                                 */
+} sph_profile_entry;
 
 /* ---- parameters and context ------------------------------------------------ */
 
@@ -219,6 +236,17 @@ sph_status sph_get(sph_box* box, int field, void* dst, int64_t n, int mem);
 
 /* Counters of the last build and passes (synchronises). */
 sph_status sph_get_stats(sph_box* box, sph_stats* out);
+
+/* Start (on = 1, clearing earlier records) or stop recording the device time of
+ * every phase of this box with CUDA events on the context stream. */
+sph_status sph_box_profile(sph_box* box, int on);
+
+/* Per-phase totals recorded since sph_box_profile(box, 1): fills up to cap
+ * entries (14 phases), *n_out receives the number of phases.  Synchronises. */
+sph_status sph_get_profile(sph_box* box, int32_t cap, sph_profile_entry* out, int32_t* n_out);
+
+/* Kernel launches made by the library in this process so far. */
+int64_t sph_launch_count(void);
 
 /* ---- introspection of the decomposition (Section II-B) -------------------- */
 

@@ -208,9 +208,9 @@ void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsi
                     unsigned int* total, cudaStream_t st) {
   const long long ntiles = (n + SC_TILE - 1) / SC_TILE;
   if (ntiles == 0) return;
-  k_scan_tiles<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, in, out, tile_sums);
-  k_scan_sums<<<1, 1024, 0, st>>>((int)ntiles, tile_sums, total);
-  k_scan_add<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, out, tile_sums);
+  k_scan_tiles<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, in, out, tile_sums); count_launch();
+  k_scan_sums<<<1, 1024, 0, st>>>((int)ntiles, tile_sums, total); count_launch();
+  k_scan_add<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, out, tile_sums); count_launch();
 }
 
 long long radix_scratch_words(long long n) {
@@ -231,9 +231,9 @@ void radix_sort(unsigned long long* k0, unsigned int* v0, unsigned long long* k1
   unsigned int *va = v0, *vb = v1;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
-    k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, shift, hist, (int)ntiles);
+    k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, shift, hist, (int)ntiles); count_launch();
     exclusive_scan(hist, hist, 256 * ntiles, sums, nullptr, st);
-    k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, va, kb, vb, shift, hist, (int)ntiles);
+    k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, va, kb, vb, shift, hist, (int)ntiles); count_launch();
     std::swap(ka, kb);
     std::swap(va, vb);
   }

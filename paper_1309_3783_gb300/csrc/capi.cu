@@ -1,4 +1,5 @@
 // Host orchestration of the GB300 SPH path and the C-ABI of include/sph.h.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -37,8 +38,10 @@ __global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*
 __global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, const float4*,
                                    const float4*, const unsigned int*, float*, unsigned int*);
 // launchers of interact.cu
-void launch_density(Engine& E);
-void launch_force(Engine& E);
+void launch_density_pair(Engine& E);
+void launch_density_self(Engine& E);
+void launch_force_pair(Engine& E);
+void launch_force_self(Engine& E);
 void launch_ghost(Engine& E, int mode, int it);
 void launch_zero_density(Engine& E, bool all);
 void launch_set_active(Engine& E);
@@ -48,6 +51,62 @@ void launch_save_acc(Engine& E);
 void launch_kick(Engine& E);
 void launch_drift(Engine& E);
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out);
+
+#define CK_PLAIN(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+const char* const kPhaseNames[PH_COUNT] = {"ingest",       "keys_sort",  "tree",        "lists",
+                                           "shift",        "axis_sort",  "density_pair", "density_self",
+                                           "ghost",        "force_pair", "force_self",  "reduce",
+                                           "kick_drift",   "output"};
+
+int Engine::prof_begin(int phase, long long* l0) {
+  *l0 = launch_count();
+  if (!prof) return -1;
+  while (ev_pool.size() < ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    ev_pool.push_back(e);
+  }
+  const int ev = (int)ev_used;
+  ev_used += 2;
+  cudaEventRecord(ev_pool[ev], st);
+  (void)phase;
+  return ev;
+}
+
+void Engine::prof_end(int phase, int ev, long long l0) {
+  if (!prof || ev < 0) return;
+  cudaEventRecord(ev_pool[ev + 1], st);
+  prof_recs.push_back(ProfRec{phase, ev, launch_count() - l0});
+}
+
+void Engine::prof_reset() {
+  prof_recs.clear();
+  ev_used = 0;
+}
+
+sph_status Engine::prof_read(std::vector<double>& ms, std::vector<long long>& calls, std::vector<long long>& launches) {
+  ms.assign(PH_COUNT, 0.0);
+  calls.assign(PH_COUNT, 0);
+  launches.assign(PH_COUNT, 0);
+  CK_PLAIN(cudaStreamSynchronize(st));
+  for (const ProfRec& r : prof_recs) {
+    float t = 0.0f;
+    CK_PLAIN(cudaEventElapsedTime(&t, ev_pool[r.ev], ev_pool[r.ev + 1]));
+    ms[r.phase] += t;
+    calls[r.phase] += 1;
+    launches[r.phase] += r.launches;
+  }
+  return SPH_OK;
+}
 
 #define CK(call)                                     \
   do {                                               \
@@ -60,7 +119,9 @@ Engine::Engine(const sph_params& p, int dev, cudaStream_t s) : prm(p), device(de
   if (nsm <= 0) nsm = 148;
 }
 
-Engine::~Engine() {}
+Engine::~Engine() {
+  for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+}
 
 int Engine::grid(long long work, int threads) const {
   long long g = (work + threads - 1) / threads;
@@ -146,7 +207,7 @@ sph_status Engine::ensure_particle_capacity() {
   CK(fvsig.reserve(n));
   CK(red.reserve(8 * std::max(nbox, 1)));
   CK(err_all.reserve(4));
-  CK(pc.reserve(8));
+  CK(pc.reserve(16));
   CK(dev_counters.reserve(8));
   CK(staging.reserve(24 * n));
   CK(cudaMemsetAsync(conv.p, 0, n * sizeof(int), st));
@@ -275,7 +336,10 @@ sph_status Engine::build_once(bool* retry) {
     d.k = 0;
   }
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
-  k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p);
+  {
+    Scope sc(this, PH_INGEST);
+    k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
+  }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hbox.data(), box.p, nbox * sizeof(BoxDesc), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -306,25 +370,30 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
 
   // ---- keys and sort
-  k_keys<<<grid(N), 256, 0, st>>>(N, dcap, bid.p, box.p, x.p, key.p, perm.p);
+  long long l0;
+  int ev = prof_begin(PH_SORT, &l0);
+  k_keys<<<grid(N), 256, 0, st>>>(N, dcap, bid.p, box.p, x.p, key.p, perm.p); count_launch();
   radix_sort(key.p, perm.p, key_tmp.p, perm_tmp.p, N, key_bits, rs_scratch.p, st);
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p);
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p); count_launch();
+  prof_end(PH_SORT, ev, l0);
   CK(cudaGetLastError());
 
   // ---- cell tree
+  ev = prof_begin(PH_TREE, &l0);
   CK(cudaMemsetAsync(t_n.p, 0, 8 * sizeof(int), st));
   CK(cudaMemsetAsync(top_at.p, 0xff, N * sizeof(int), st));
   CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
-  k_top_nodes<<<grid(N), 256, 0, st>>>(N, dcap, box_shift, box.p, key.p, T, cap_nodes, top_at.p, err_all.p);
-  k_frontier_init<<<1, 1, 0, st>>>(T, cap_nodes);
+  k_top_nodes<<<grid(N), 256, 0, st>>>(N, dcap, box_shift, box.p, key.p, T, cap_nodes, top_at.p, err_all.p); count_launch();
+  k_frontier_init<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
   const int rounds = dcap - kmin + 1;
   for (int r = 0; r < rounds; ++r) {
-    k_node_stats<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, dcap, prm.leaf_max, prm.split_frac);
+    k_node_stats<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, dcap, prm.leaf_max, prm.split_frac); count_launch();
     if (r + 1 < rounds) {
-      k_split_nodes<<<nsm * 4, 128, 0, st>>>(T, key.p, dcap, box_shift, cap_nodes, err_all.p);
-      k_frontier_next<<<1, 1, 0, st>>>(T, cap_nodes);
+      k_split_nodes<<<nsm * 4, 128, 0, st>>>(T, key.p, dcap, box_shift, cap_nodes, err_all.p); count_launch();
+      k_frontier_next<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
     }
   }
+  prof_end(PH_TREE, ev, l0);
   CK(cudaGetLastError());
   int tn[8];
   unsigned int ea[4];
@@ -341,17 +410,21 @@ sph_status Engine::build_once(bool* retry) {
   n_top = tn[3];
 
   // ---- interaction lists
+  ev = prof_begin(PH_LISTS, &l0);
   CK(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
   k_items_top<<<grid(n_top), 256, 0, st>>>(n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
-                                           err_all.p);
+                                           err_all.p); count_launch();
   for (int r = 0; r < rounds; ++r) {
     const int in = r & 1;
     CK(cudaMemsetAsync(l_counts.p + 2 + (in ^ 1), 0, sizeof(int), st));
-    k_items_expand<<<nsm * 8, 256, 0, st>>>(in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p);
+    k_items_expand<<<nsm * 8, 256, 0, st>>>(in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p); count_launch();
   }
-  k_leaves<<<nsm * 8, 256, 0, st>>>(T, n_nodes, leaf_of.p);
-  k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p);
-  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p);
+  prof_end(PH_LISTS, ev, l0);
+  ev = prof_begin(PH_SHIFT, &l0);
+  k_leaves<<<nsm * 8, 256, 0, st>>>(T, n_nodes, leaf_of.p); count_launch();
+  k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p); count_launch();
+  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  prof_end(PH_SHIFT, ev, l0);
 
   // ---- sorted projections
   CK(big_count.reserve(1));
@@ -361,10 +434,12 @@ sph_status Engine::build_once(bool* retry) {
     CK(big_axis.reserve(cap_big));
     CK(big_off.reserve(cap_big));
   }
+  ev = prof_begin(PH_AXIS_SORT, &l0);
   CK(cudaMemsetAsync(big_count.p, 0, sizeof(unsigned long long), st));
-  k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T);
+  k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T); count_launch();
   k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
-                                              cap_big);
+                                              cap_big); count_launch();
+  prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
   int lc[8];
   unsigned long long bcw = 0;
@@ -397,7 +472,8 @@ sph_status Engine::build_once(bool* retry) {
   n_big_entries = bc[1];
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
-  k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, pos4.p, cen4.p, sort_r.p, sort_i.p);
+  ev = prof_begin(PH_AXIS_SORT, &l0);
+  k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, pos4.p, cen4.p, sort_r.p, sort_i.p); count_launch();
   if (n_big > 0) {
     const size_t nb = (size_t)n_big_entries;
     CK(ckey.reserve(nb));
@@ -406,12 +482,13 @@ sph_status Engine::build_once(bool* retry) {
     CK(cval_tmp.reserve(nb));
     if (rs_scratch.n < (size_t)radix_scratch_words(nb)) CK(rs_scratch.reserve(radix_scratch_words(nb)));
     k_sort_big_keys<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, pos4.p,
-                                                              cen4.p, ckey.p, cval.p);
+                                                              cen4.p, ckey.p, cval.p); count_launch();
     radix_sort(ckey.p, cval.p, ckey_tmp.p, cval_tmp.p, (long long)nb, 32 + std::max(1, ceil_log2(n_big)),
                rs_scratch.p, st);
     k_sort_big_scatter<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T,
-                                                                 pos4.p, cen4.p, cval.p, sort_r.p, sort_i.p);
+                                                                 pos4.p, cen4.p, cval.p, sort_r.p, sort_i.p); count_launch();
   }
+  prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
   depth_used = 0;
   built = true;
@@ -426,8 +503,15 @@ sph_status Engine::set_all_active() {
 }
 
 sph_status Engine::density_pass() {
-  launch_zero_density(*this, false);
-  launch_density(*this);
+  {
+    Scope sc(this, PH_DENSITY_PAIR);
+    launch_zero_density(*this, false);
+    launch_density_pair(*this);
+  }
+  {
+    Scope sc(this, PH_DENSITY_SELF);
+    launch_density_self(*this);
+  }
   CK(cudaGetLastError());
   return SPH_OK;
 }
@@ -437,13 +521,16 @@ sph_status Engine::density() {
     sph_status s = build();
     if (s != SPH_OK) return s;
   }
-  if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 8 * sizeof(unsigned long long), st));
+  if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 16 * sizeof(unsigned long long), st));
   sph_status s = set_all_active();
   if (s != SPH_OK) return s;
   s = density_pass();
   if (s != SPH_OK) return s;
   CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
-  launch_ghost(*this, 0, 1);
+  {
+    Scope sc(this, PH_GHOST);
+    launch_ghost(*this, 0, 1);
+  }
   CK(cudaGetLastError());
   have_density = have_ghost = true;
   have_force = false;
@@ -457,7 +544,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     sph_status s = build();
     if (s != SPH_OK) return s;
   }
-  if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 8 * sizeof(unsigned long long), st));
+  if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 16 * sizeof(unsigned long long), st));
   launch_bracket_reset(*this);
   sph_status s = set_all_active();
   if (s != SPH_OK) return s;
@@ -467,7 +554,10 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     if (s != SPH_OK) return s;
     CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
     CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
-    launch_ghost(*this, 1, it);
+    {
+      Scope sc(this, PH_GHOST);
+      launch_ghost(*this, 1, it);
+    }
     CK(cudaGetLastError());
     unsigned int ea = 0;
     CK(cudaMemcpyAsync(&n_active, dev_counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -504,9 +594,19 @@ sph_status Engine::force() {
   if (!have_ghost) return fail(SPH_E_NOT_BUILT, "force pass needs a density pass first");
   CK(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
   CK(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
-  launch_force(*this);
-  launch_reduce(*this);
-  launch_save_acc(*this);
+  {
+    Scope sc(this, PH_FORCE_PAIR);
+    launch_force_pair(*this);
+  }
+  {
+    Scope sc(this, PH_FORCE_SELF);
+    launch_force_self(*this);
+  }
+  {
+    Scope sc(this, PH_REDUCE);
+    launch_reduce(*this);
+    launch_save_acc(*this);
+  }
   CK(cudaGetLastError());
   have_force = true;
   have_acc = true;
@@ -543,8 +643,11 @@ sph_status Engine::step_boxes() {
   if (moving) {
     s = upload_boxes();
     if (s != SPH_OK) return s;
-    launch_kick(*this);
-    launch_drift(*this);
+    {
+      Scope sc(this, PH_STEP);
+      launch_kick(*this);
+      launch_drift(*this);
+    }
     CK(cudaGetLastError());
   }
   s = build();
@@ -554,6 +657,7 @@ sph_status Engine::step_boxes() {
   s = force();
   if (s != SPH_OK) return s;
   if (moving) {
+    Scope sc(this, PH_STEP);
     launch_kick(*this);
     CK(cudaGetLastError());
   }
@@ -622,7 +726,10 @@ sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
     default: return fail(SPH_E_INVALID, "unknown field");
   }
   void* out = mem == SPH_MEM_DEVICE ? dst : (void*)staging.p;
-  launch_get_field(*this, o, nb, field, out);
+  {
+    Scope sc(this, PH_OUTPUT);
+    launch_get_field(*this, o, nb, field, out);
+  }
   CK(cudaGetLastError());
   if (mem != SPH_MEM_DEVICE) {
     CK(cudaMemcpyAsync(dst, staging.p, per * nb * 4, cudaMemcpyDeviceToHost, st));
@@ -646,15 +753,20 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->rebuilds = last_rebuilds;
   o->n_unconverged = last_unconverged;
   if (count_pairs) {
-    unsigned long long c[8];
+    unsigned long long c[16];
     CK(cudaMemcpyAsync(c, pc.p, sizeof(c), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    o->density_pairs = (long long)c[0];
-    o->density_sides = (long long)c[1];
-    o->density_candidates = (long long)c[2];
-    o->force_pairs = (long long)c[3];
-    o->force_candidates = (long long)c[4];
-    o->guard_rechecks = (long long)c[5];
+    o->density_pairs = (long long)(c[0] + c[3]);
+    o->density_sides = (long long)(c[1] + c[4]);
+    o->density_candidates = (long long)(c[2] + c[5]);
+    o->density_pairs_cellpair = (long long)c[0];
+    o->density_sides_cellpair = (long long)c[1];
+    o->density_candidates_cellpair = (long long)c[2];
+    o->force_pairs = (long long)(c[6] + c[8]);
+    o->force_candidates = (long long)(c[7] + c[9]);
+    o->force_pairs_cellpair = (long long)c[6];
+    o->force_candidates_cellpair = (long long)c[7];
+    o->guard_rechecks = (long long)c[10];
   }
   return SPH_OK;
 }
@@ -909,6 +1021,33 @@ sph_status sph_get(sph_box* b, int field, void* dst, int64_t n, int mem) {
   BOX_PRE(b);
   return from_engine(b, b->eng->get(0, field, dst, n, mem));
 }
+
+sph_status sph_box_profile(sph_box* b, int on) {
+  BOX_PRE(b);
+  b->eng->prof = on != 0;
+  b->eng->prof_reset();
+  return SPH_OK;
+}
+
+sph_status sph_get_profile(sph_box* b, int32_t cap, sph_profile_entry* out, int32_t* n_out) {
+  BOX_PRE(b);
+  if (!n_out) return SPH_E_INVALID;
+  std::vector<double> ms;
+  std::vector<long long> calls, launches;
+  sph_status s = b->eng->prof_read(ms, calls, launches);
+  if (s != SPH_OK) return from_engine(b, s);
+  for (int k = 0; k < sph::PH_COUNT && k < cap; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, sph::kPhaseNames[k], sizeof(out[k].name) - 1);
+    out[k].calls = calls[k];
+    out[k].launches = launches[k];
+    out[k].ms = ms[k];
+  }
+  *n_out = sph::PH_COUNT;
+  return SPH_OK;
+}
+
+int64_t sph_launch_count(void) { return sph::launch_count(); }
 
 sph_status sph_get_stats(sph_box* b, sph_stats* out) {
   BOX_PRE(b);

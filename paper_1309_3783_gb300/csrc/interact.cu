@@ -202,7 +202,6 @@ __device__ __forceinline__ void flush_dens(int gidx, float4 acc, unsigned int cn
 template <bool COUNT>
 __device__ __forceinline__ void commit_counters(const Counters& C, unsigned long long* pc, int which) {
   if (!COUNT) return;
-  // pc layout: PairCounters {dens_pairs, dens_sides, dens_cand, force_pairs, force_cand, rechecks}
   unsigned long long c = C.cand, p = C.pairs, s = C.sides, r = C.rechecks;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -212,15 +211,14 @@ __device__ __forceinline__ void commit_counters(const Counters& C, unsigned long
     r += __shfl_xor_sync(0xffffffffu, r, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    if (which == 0) {
-      atomicAdd(&pc[0], p);
-      atomicAdd(&pc[1], s);
-      atomicAdd(&pc[2], c);
-    } else {
-      atomicAdd(&pc[3], p);
-      atomicAdd(&pc[4], c);
-    }
-    atomicAdd(&pc[5], r);
+    // pc: [0..2] density cell-pair kernel (pairs, sides, candidates), [3..5] density
+    // self kernel, [6..7] force cell-pair kernel (pairs, candidates), [8..9] force
+    // self kernel, [10] FP64 re-decisions
+    const int base = which == 0 ? 0 : which == 1 ? 3 : which == 2 ? 6 : 8;
+    atomicAdd(&pc[base], p);
+    if (which < 2) atomicAdd(&pc[base + 1], s);
+    atomicAdd(&pc[base + (which < 2 ? 2 : 1)], c);
+    atomicAdd(&pc[10], r);
   }
 }
 
@@ -347,7 +345,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
       flush_dens(I.g, acc, cnt, dacc, dcnt);
     }
   }
-  commit_counters<COUNT>(C, pc, 0);
+  commit_counters<COUNT>(C, pc, 1);
 }
 
 // =========================================================================== force
@@ -539,7 +537,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
       flush_force(I.g, acc, vsi, facc, fvsig);
     }
   }
-  commit_counters<COUNT>(C, pc, 1);
+  commit_counters<COUNT>(C, pc, 2);
 }
 
 template <bool COUNT>
@@ -601,7 +599,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
       flush_force(I.g, acc, vsi, facc, fvsig);
     }
   }
-  commit_counters<COUNT>(C, pc, 1);
+  commit_counters<COUNT>(C, pc, 3);
 }
 
 // =========================================================================== ghost
@@ -808,74 +806,89 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
 }
 
 // =========================================================================== launchers
-void launch_density(Engine& E) {
+void launch_density_pair(Engine& E) {
   const int grid = E.nsm * 8;
-  if (E.count_pairs) {
+  if (E.count_pairs)
     k_density_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
                                                          E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
                                                          E.dacc.p, E.dcnt.p, E.pc.p);
-    k_density_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
-                                                         E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
-  } else {
+  else
     k_density_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
                                                           E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
                                                           E.dacc.p, E.dcnt.p, E.pc.p);
-    k_density_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
-                                                          E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
-  }
+  count_launch();
 }
 
-void launch_force(Engine& E) {
+void launch_density_self(Engine& E) {
+  const int grid = E.nsm * 8;
+  if (E.count_pairs)
+    k_density_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                         E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
+  else
+    k_density_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                          E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
+  count_launch();
+}
+
+void launch_force_pair(Engine& E) {
   const int grid = E.nsm * 8;
   const float alpha = E.prm.alpha_visc;
-  if (E.count_pairs) {
+  if (E.count_pairs)
     k_force_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
                                                        E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
                                                        E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
-    k_force_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
-                                                       E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
-                                                       E.fvsig.p, E.pc.p);
-  } else {
+  else
     k_force_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
                                                         E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
                                                         E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
+  count_launch();
+}
+
+void launch_force_self(Engine& E) {
+  const int grid = E.nsm * 8;
+  const float alpha = E.prm.alpha_visc;
+  if (E.count_pairs)
+    k_force_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+                                                       E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
+                                                       E.fvsig.p, E.pc.p);
+  else
     k_force_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
                                                         E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
                                                         E.fvsig.p, E.pc.p);
-  }
+  count_launch();
 }
 
 void launch_ghost(Engine& E, int mode, int it) {
   k_ghost<<<E.grid(E.N), 256, 0, E.st>>>(E.N, mode, it, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
                                           E.prm.h_tol, E.prm.gamma_gas, E.perm.p, E.Hs.p, E.pos4.p, E.cen4.p,
                                           E.vel4.p, E.dacc.p, E.act.p, E.h.p, E.hlo.p, E.hhi.p, E.conv.p,
-                                          E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.dev_counters.p, E.err_all.p);
+                                          E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.dev_counters.p, E.err_all.p); count_launch();
 }
 
 void launch_zero_density(Engine& E, bool all) {
-  k_zero_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.dacc.p, E.dcnt.p, all ? 1 : 0);
+  k_zero_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.dacc.p, E.dcnt.p, all ? 1 : 0); count_launch();
 }
 
-void launch_set_active(Engine& E) { k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); }
+void launch_set_active(Engine& E) { k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); count_launch(); }
 
 void launch_bracket_reset(Engine& E) {
-  k_h_bracket_reset<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.hlo.p, E.hhi.p, E.conv.p);
+  k_h_bracket_reset<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.hlo.p, E.hhi.p, E.conv.p); count_launch();
 }
 
 void launch_reduce(Engine& E) {
   cudaMemsetAsync(E.red.p, 0, sizeof(double) * 8 * E.nbox, E.st);
-  k_reduce<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.box_shift, E.key.p, E.cen4.p, E.vel4.p, E.facc.p, E.red.p);
+  k_reduce<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.box_shift, E.key.p, E.cen4.p, E.vel4.p, E.facc.p, E.red.p); count_launch();
 }
 
-void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); }
+void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); count_launch(); }
 
-void launch_kick(Engine& E) { k_kick<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); }
+void launch_kick(Engine& E) { k_kick<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); count_launch(); }
 
-void launch_drift(Engine& E) { k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p); }
+void launch_drift(Engine& E) { k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p); count_launch(); }
 
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out) {
   k_get_field<<<E.grid(n), 256, 0, E.st>>>(off, n, field, E.perm.p, E.Hs.p, E.cen4.p, E.vel4.p, E.dacc.p, E.dcnt.p,
-                                           E.ghost4.p, E.facc.p, E.fvsig.p, E.h.p, E.prm.gamma_gas, out);
+                                           E.ghost4.p, E.facc.p, E.fvsig.p, E.h.p, E.prm.gamma_gas, out); count_launch();
 }
 
 }  // namespace sph

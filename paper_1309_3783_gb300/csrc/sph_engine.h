@@ -47,6 +47,17 @@ struct BoxSpec {
   int periodic;
 };
 
+// Process-wide count of kernel launches made by the library (host side).
+void count_launch();
+long long launch_count();
+
+// Phases of the path timed with CUDA events when profiling is on.
+enum Phase {
+  PH_INGEST, PH_SORT, PH_TREE, PH_LISTS, PH_SHIFT, PH_AXIS_SORT, PH_DENSITY_PAIR, PH_DENSITY_SELF, PH_GHOST,
+  PH_FORCE_PAIR, PH_FORCE_SELF, PH_REDUCE, PH_STEP, PH_OUTPUT, PH_COUNT
+};
+extern const char* const kPhaseNames[PH_COUNT];
+
 // Kernels and helpers implemented in build.cu / interact.cu.
 void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsigned int* tile_sums,
                     unsigned int* total, cudaStream_t st);
@@ -146,7 +157,7 @@ class Engine {
   DBuf<float> fvsig;
   DBuf<double> red;               // 8 per box
   DBuf<unsigned int> err_all;     // global error bits
-  DBuf<unsigned long long> pc;    // PairCounters per engine
+  DBuf<unsigned long long> pc;    // pair counters per kernel (see commit_counters)
   DBuf<int> dev_counters;         // [0] particles still active after a ghost pass
   DBuf<unsigned char> staging;    // output staging (input order)
 
@@ -156,6 +167,27 @@ class Engine {
   int last_iters = 0, last_rebuilds = 0;
   long long last_unconverged = 0;
   bool built = false, have_density = false, have_ghost = false, have_force = false, have_acc = false;
+
+  // profiling: CUDA events around each phase on the engine's stream
+  struct ProfRec {
+    int phase, ev;
+    long long launches;
+  };
+  bool prof = false;
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  int prof_begin(int phase, long long* l0);
+  void prof_end(int phase, int ev, long long l0);
+  void prof_reset();
+  sph_status prof_read(std::vector<double>& ms, std::vector<long long>& calls, std::vector<long long>& launches);
+  struct Scope {
+    Engine* e;
+    int phase, ev;
+    long long l0;
+    Scope(Engine* en, int ph) : e(en), phase(ph), ev(-1), l0(0) { ev = e->prof_begin(ph, &l0); }
+    ~Scope() { e->prof_end(phase, ev, l0); }
+  };
 
   // helpers
   int grid(long long work, int threads = 256) const;

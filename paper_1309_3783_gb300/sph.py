@@ -42,7 +42,14 @@ class sph_stats(C.Structure):
                 ("n_sorted_entries", C.c_int64), ("top_level", C.c_int32), ("depth", C.c_int32),
                 ("h_iterations", C.c_int32), ("rebuilds", C.c_int32), ("n_unconverged", C.c_int64),
                 ("density_pairs", C.c_int64), ("density_sides", C.c_int64), ("density_candidates", C.c_int64),
-                ("force_pairs", C.c_int64), ("force_candidates", C.c_int64), ("guard_rechecks", C.c_int64)]
+                ("density_pairs_cellpair", C.c_int64), ("density_sides_cellpair", C.c_int64),
+                ("density_candidates_cellpair", C.c_int64), ("force_pairs", C.c_int64),
+                ("force_candidates", C.c_int64), ("force_pairs_cellpair", C.c_int64),
+                ("force_candidates_cellpair", C.c_int64), ("guard_rechecks", C.c_int64)]
+
+
+class sph_profile_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("calls", C.c_int64), ("launches", C.c_int64), ("ms", C.c_double)]
 
 
 class SphError(RuntimeError):
@@ -71,6 +78,9 @@ _SIGS = {
     "sph_cfl_dt": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "sph_get": (C.c_int, [_P, C.c_int, _P, C.c_int64, C.c_int]),
     "sph_get_stats": (C.c_int, [_P, C.POINTER(sph_stats)]),
+    "sph_box_profile": (C.c_int, [_P, C.c_int]),
+    "sph_get_profile": (C.c_int, [_P, C.c_int32, C.POINTER(sph_profile_entry), C.POINTER(C.c_int32)]),
+    "sph_launch_count": (C.c_int64, []),
     "sph_get_cells": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "sph_get_interactions": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "sph_server_create": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(_P)]),
@@ -244,6 +254,23 @@ def sph_get_stats(box, ctx) -> dict:
     return {k: getattr(s, k) for k, _ in sph_stats._fields_}
 
 
+def sph_box_profile(box, ctx, on: bool = True):
+    _check(load().sph_box_profile(box, 1 if on else 0), ctx)
+
+
+def sph_get_profile(box, ctx) -> dict:
+    """{phase: {"calls", "launches", "ms"}} recorded since sph_box_profile(box, True)."""
+    arr = (sph_profile_entry * 32)()
+    n = C.c_int32()
+    _check(load().sph_get_profile(box, 32, arr, C.byref(n)), ctx)
+    return {arr[k].name.decode(): {"calls": arr[k].calls, "launches": arr[k].launches, "ms": arr[k].ms}
+            for k in range(n.value)}
+
+
+def sph_launch_count() -> int:
+    return int(load().sph_launch_count())
+
+
 def sph_get_cells(box, ctx) -> dict:
     n = C.c_int64()
     _check(load().sph_get_cells(box, 0, None, None, None, None, C.byref(n)), ctx)
@@ -358,6 +385,12 @@ class Box:
 
     def stats(self):
         return sph_get_stats(self.h, self.ctx)
+
+    def profile(self, on=True):
+        sph_box_profile(self.h, self.ctx, on)
+
+    def get_profile(self):
+        return sph_get_profile(self.h, self.ctx)
 
     def cells(self):
         return sph_get_cells(self.h, self.ctx)

@@ -47,14 +47,18 @@ WORKLOAD = "plummer-262144"
 SAMPLE_N = 16384            # the oracle's bounded sample: the same recipe at 1/16 of the particles
 
 # Algorithmic FP32 operations per interacting pair, counted from the formulas
-# the kernels evaluate (mul/add = 1, FMA = 2, sqrt/rsqrt/div = 1):
-#   density: per unordered pair 9 (separation 3, r^2 5, r 1), per side that
-#            interacts 19 (q 1, w 5, w' 4, q w' 1... accumulations 8);
-#   force:   per unordered pair 76 (separation, r^2, 1/r, two kernel
-#            derivatives, v.x, viscosity, both sides' accumulations).
-FLOPS_DENSITY_PAIR = 9
-FLOPS_DENSITY_SIDE = 19
-FLOPS_FORCE_PAIR = 76
+# the kernels evaluate (mul/add = 1, FMA = 2, sqrt/rsqrt/div = 1; one branch of
+# the piecewise kernel):
+#   density: per unordered pair 11 (separation 3, r^2 5, two guard-band tests 2,
+#            r 1) plus 16 per side that accumulates (q 1, w and w' 8, q w' 1,
+#            four sums 6);
+#   force:   per unordered pair 75 (separation 3, r^2 5, guard bands 2, 1/r and r
+#            2, two kernel derivatives 10, v.x 8, w 1, min 1, v_sig 3, Pi 4,
+#            W-bar 2, coefficient 6, half-viscosity 2, both sides' a, du/dt and
+#            v_sig 26).
+FLOPS_DENSITY_PAIR = 11
+FLOPS_DENSITY_SIDE = 16
+FLOPS_FORCE_PAIR = 75
 
 # FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
 SM_COUNT, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.070
@@ -154,6 +158,10 @@ def run_ours(args, rank, world, local_rank):
     # resident input state: h converged once (a simulation's previous step), dt from CFL
     b.set(box.x, box.v, box.m, box.u, box.h)
     b.h_update()
+    leaf_max = 400
+    if not args.no_tune:
+        leaf_max = b.tune()                           # split threshold for this workload (untimed)
+        b.h_update()
     b.force()
     dt = b.cfl_dt()
     h_conv = b.get("h").copy()
@@ -165,15 +173,19 @@ def run_ours(args, rank, world, local_rank):
         b.set(xd, vd, md, ud, hd)
         return b.step(dt)
 
-    # algorithmic work of one step's passes: exact pair counts (untimed)
+    # algorithmic work of one step (identical for every step): exact pair counts
+    # over the step's density passes and its force pass (untimed)
     b.count_pairs(True)
-    b.set(xd, vd, md, ud, hd)
-    b.density()
-    b.force()
+    b.profile(True)
+    step_device()
     st = b.stats()
+    cprof = b.get_profile()
+    b.profile(False)
     b.count_pairs(False)
-    flops_density_pair = FLOPS_DENSITY_PAIR * st["density_pairs_cellpair"] + FLOPS_DENSITY_SIDE * st["density_sides_cellpair"]
-    flops_force_pair = FLOPS_FORCE_PAIR * st["force_pairs_cellpair"]
+    flops_density_pair = ((FLOPS_DENSITY_PAIR * st["density_pairs_cellpair"]
+                           + FLOPS_DENSITY_SIDE * st["density_sides_cellpair"])
+                          / max(cprof["density_pair"]["calls"], 1))
+    flops_force_pair = FLOPS_FORCE_PAIR * st["force_pairs_cellpair"] / max(cprof["force_pair"]["calls"], 1)
 
     for _ in range(args.warmup):
         step_device()
@@ -249,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles_per_gpu": n, "h": "converged from the previous step",
-                   "dt": dt, "leaf_max": 400, "l2": "flushed between timed steps (256 MB write)",
+                   "dt": dt, "leaf_max": leaf_max, "leaf_max_source": "autotuned" if not args.no_tune else "paper", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 12 + 4 + 4 + 4),
                 "d2h_bytes_per_step": n * (12 + 4 + 4 + 4), "steps": e2e_steps},
@@ -337,6 +349,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
+    ap.add_argument("--no-tune", action="store_true", help="keep the paper's leaf_max = 400")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

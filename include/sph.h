@@ -248,6 +248,16 @@ sph_status sph_get_profile(sph_box* box, int32_t cap, sph_profile_entry* out, in
 /* Kernel launches made by the library in this process so far. */
 int64_t sph_launch_count(void);
 
+/* Autotune the cell split threshold leaf_max (Section II-B splits cells above
+ * it; the paper uses 400 on its CPUs) for this box's current particles: times
+ * build + density + force for leaf_max in {24, 32, 48, 64, 96, 128, 192, 256,
+ * 400} and keeps the fastest for the box.  *leaf_max (may be NULL) receives it.
+ * Results of the passes run while tuning are discarded (the box is unbuilt). */
+sph_status sph_box_tune(sph_box* box, int32_t* leaf_max);
+
+/* Set the box's split threshold leaf_max (>= 1); clears built state. */
+sph_status sph_box_set_leaf_max(sph_box* box, int32_t leaf_max);
+
 /* ---- introspection of the decomposition (Section II-B) -------------------- */
 
 /* Cells of the current tree.  For cell c < min(cap, count): level[c], the

@@ -386,3 +386,47 @@ def full_step(box, n_ngb=N_NGB, tol=1e-4, max_iter=30, alpha=ALPHA_VISC, gamma=G
     out.update({"h": h, "H": H, "drho_dh": drho_dh(dens, h), "converged": conv,
                 "iterations": iters, "reductions": red})
     return out
+
+
+# ------------------------------------------------------------- time stepping
+def kdk_steps(box, dt, n_steps, n_ngb=N_NGB, tol=1e-4, max_iter=30, alpha=ALPHA_VISC, gamma=GAMMA_GAS,
+              method="auto"):
+    """Fixed-step kick-drift-kick integration (Section III-B: fixed time step,
+    forces on every particle each step; the integrator itself is a reading).
+
+    Starting forces come from an h iteration and a force pass at the initial
+    positions; every step then does v += a dt/2, u += du/dt dt/2 (u >= 0),
+    x += v dt in FP64 wrapped into [0, L), h iteration from the previous h,
+    force pass, and the closing half kick.  v, u are held in FP64.
+    Returns (x, v, u, h, last full_step dict).
+    """
+    from copy import deepcopy
+    b = deepcopy(box)
+    x = b.x.astype(np.float64).copy()
+    v = b.v.astype(np.float64).copy()
+    u = b.u.astype(np.float64).copy()
+    m = b.m.astype(np.float64)
+
+    def passes(h0):
+        h, conv, _, dens = h_iterate(x, m, h0, b.L, b.periodic, n_ngb, tol, max_iter, method=method)
+        H = float(GAMMA_K) * h
+        g = ghost(dens["rho"], dens["Sr_m"], u, gamma)
+        fo = force(x, v, m, H, dens["rho"], g["P"], g["c"], g["f"], b.L, b.periodic, alpha, method=method)
+        out = dict(dens)
+        out.update(g)
+        out.update(fo)
+        out["h"] = h
+        return h, out
+
+    h, out = passes(b.h.astype(np.float64))
+    for _ in range(n_steps):
+        v += 0.5 * dt * out["a"]
+        u = np.maximum(u + 0.5 * dt * out["dudt"], 0.0)
+        x = x + v * dt
+        if b.periodic:
+            x = np.mod(x, b.L)
+            x[x >= b.L] = 0.0
+        h, out = passes(h)
+        v += 0.5 * dt * out["a"]
+        u = np.maximum(u + 0.5 * dt * out["dudt"], 0.0)
+    return x, v, u, h, out

@@ -45,6 +45,9 @@ void launch_force_self(Engine& E);
 void launch_ghost(Engine& E, int mode, int it);
 void launch_zero_density(Engine& E, bool all);
 void launch_set_active(Engine& E);
+void launch_mark_active_cells(Engine& E);
+void launch_count_unconverged(Engine& E, int* out);
+void launch_task_tables(Engine& E);
 void launch_bracket_reset(Engine& E);
 void launch_reduce(Engine& E);
 void launch_save_acc(Engine& E);
@@ -237,6 +240,7 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   CK(t_hmax.reserve(n));
   CK(t_hlim.reserve(n));
   CK(t_cen.reserve(n));
+  CK(t_active.reserve(n));
   CK(t_n.reserve(8));
   T.start = t_start.p;
   T.count = t_count.p;
@@ -253,6 +257,7 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   T.cen = t_cen.p;
   T.axes = t_axes.p;
   T.sortbase = t_sortbase.p;
+  T.active = t_active.p;
   T.n_nodes = t_n.p;
   CK(big_node.reserve(1));
   return ensure_list_capacity(nodes, 8 * nodes, 8 * nodes);
@@ -262,13 +267,16 @@ sph_status Engine::ensure_list_capacity(int selfs, int pairs, int queue) {
   if (selfs > cap_self || !l_self.p) {
     cap_self = selfs;
     CK(l_self.reserve(selfs));
+    CK(l_stoff.reserve(selfs + 1));
   }
   if (pairs > cap_pair || !l_pa.p) {
     cap_pair = pairs;
     CK(l_pa.reserve(pairs));
     CK(l_pb.reserve(pairs));
     CK(l_pax.reserve(pairs));
+    CK(l_ptoff.reserve(pairs + 1));
   }
+  CK(scan_tmp.reserve((size_t)std::max(cap_pair, cap_self) / 2048 + 64));
   if (queue > cap_queue || !q_kind[0].p) {
     cap_queue = queue;
     for (int k = 0; k < 2; ++k) {
@@ -289,6 +297,8 @@ sph_status Engine::ensure_list_capacity(int selfs, int pairs, int queue) {
     Lq.q_b[k] = q_b[k].p;
     Lq.q_axis[k] = q_ax[k].p;
   }
+  Lq.p_toff = l_ptoff.p;
+  Lq.s_toff = l_stoff.p;
   Lq.counts = l_counts.p;
   return SPH_OK;
 }
@@ -470,6 +480,7 @@ sph_status Engine::build_once(bool* retry) {
   n_entries = (unsigned int)lc[5];
   n_big = (int)bc[0];
   n_big_entries = bc[1];
+  launch_task_tables(*this);
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   ev = prof_begin(PH_AXIS_SORT, &l0);
@@ -570,15 +581,21 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
       s = set_all_active();
       if (s != SPH_OK) return s;
       ++rebuilds;
+    } else {
+      launch_mark_active_cells(*this);
     }
   }
   if (it > prm.h_max_iter) it = prm.h_max_iter;
   // particles that never converged
-  std::vector<int> hc(N);
-  CK(cudaMemcpyAsync(hc.data(), conv.p, N * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
   long long nu = 0;
-  for (long long p = 0; p < N; ++p) nu += hc[p] ? 0 : 1;
+  if (n_active > 0) {
+    int cnt = 0;
+    CK(cudaMemsetAsync(dev_counters.p + 1, 0, sizeof(int), st));
+    launch_count_unconverged(*this, dev_counters.p + 1);
+    CK(cudaMemcpyAsync(&cnt, dev_counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    nu = cnt;
+  }
   last_iters = it;
   last_rebuilds = rebuilds;
   last_unconverged = nu;
@@ -662,6 +679,53 @@ sph_status Engine::step_boxes() {
     CK(cudaGetLastError());
   }
   return hs;
+}
+
+// Leaf-size autotuning: time build + density + force for each candidate
+// leaf_max (the split threshold of Section II-B; the paper uses 400 on its CPUs)
+// and keep the fastest.
+sph_status Engine::tune(int* best_out) {
+  static const int cand[] = {24, 32, 48, 64, 96, 128, 192, 256, 400};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int keep = prm.leaf_max;
+  float best_ms = 1e30f;
+  int best = keep;
+  tune_ms.clear();
+  for (int c : cand) {
+    prm.leaf_max = c;
+    float tot = 0.0f;
+    sph_status s = SPH_OK;
+    for (int rep = 0; rep < 3 && s == SPH_OK; ++rep) {
+      CK(cudaEventRecord(e0, st));
+      s = build();
+      if (s == SPH_OK) s = density();
+      if (s == SPH_OK) s = force();
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;            // the first repetition warms up allocations
+    }
+    if (s != SPH_OK) {
+      prm.leaf_max = keep;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return s;
+    }
+    tune_ms.push_back(std::make_pair(c, tot / 2));
+    if (tot < best_ms) {
+      best_ms = tot;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  prm.leaf_max = best;
+  built = have_density = have_ghost = have_force = false;
+  if (best_out) *best_out = best;
+  return SPH_OK;
 }
 
 sph_status Engine::cfl_dt(int b, double* dt) {
@@ -1048,6 +1112,22 @@ sph_status sph_get_profile(sph_box* b, int32_t cap, sph_profile_entry* out, int3
 }
 
 int64_t sph_launch_count(void) { return sph::launch_count(); }
+
+sph_status sph_box_tune(sph_box* b, int32_t* leaf_max) {
+  BOX_PRE(b);
+  int best = 0;
+  sph_status s = b->eng->tune(&best);
+  if (leaf_max) *leaf_max = best;
+  return from_engine(b, s);
+}
+
+sph_status sph_box_set_leaf_max(sph_box* b, int32_t leaf_max) {
+  BOX_PRE(b);
+  if (leaf_max < 1) return set_err(b->ctx, SPH_E_INVALID, "leaf_max must be >= 1");
+  b->eng->prm.leaf_max = leaf_max;
+  b->eng->built = b->eng->have_density = b->eng->have_ghost = b->eng->have_force = false;
+  return SPH_OK;
+}
 
 sph_status sph_get_stats(sph_box* b, sph_stats* out) {
   BOX_PRE(b);

@@ -86,6 +86,18 @@ __device__ __forceinline__ float tile_gap(const TileBox& a, const TileBox& b) {
   return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
 }
 
+// Task t of a prefix table toff[0..n) (exclusive prefix of i-tiles per item):
+// the item with toff[item] <= t < toff[item + 1].
+__device__ __forceinline__ int task_item(const unsigned int* __restrict__ toff, int n, unsigned int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (toff[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // =========================================================================== density
 struct DensI {
   float3 p;
@@ -160,10 +172,12 @@ __device__ __forceinline__ void dens_step(const DensI& I, DensShared& S, int k, 
   const bool pI = decide(r2, I.H2, I.band, I.g, S.g[k], I.Hphys, perm, x, g, rc);
   const bool pJ = decide(r2, Ja.x, Ja.y, I.g, S.g[k], Ja.w, perm, x, g, rc);
   if (COUNT) {
+    // useful work: sides that accumulate into a particle still iterating h
+    const bool ui = pI && I.act, uj = pJ && S.act[k];
     C.cand++;
     C.rechecks += rc;
-    C.pairs += (pI || pJ) ? 1u : 0u;
-    C.sides += (pI ? 1u : 0u) + (pJ ? 1u : 0u);
+    C.pairs += (ui || uj) ? 1u : 0u;
+    C.sides += (ui ? 1u : 0u) + (uj ? 1u : 0u);
   }
   if (!(pI || pJ)) return;
   const float r = sqrtf(r2);
@@ -238,8 +252,11 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
   DensShared& S = SH[wl];
   Counters C;
   const int npair = min(Lq.counts[1], cap_pair);
-  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < npair; item += gridDim.x * SPH_WARPS_PER_CTA) {
+  const unsigned int ntask = (unsigned int)Lq.counts[6];
+  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int item = task_item(Lq.p_toff, npair, t);
     const int A = Lq.pair_a[item], B = Lq.pair_b[item], ax = Lq.pair_axis[item];
+    if (!(T.active[A] | T.active[B])) continue;          // no particle of either cell still iterating h
     const ItemGeom g = item_geom(T, box, A, ax);
     const unsigned int nA = T.count[A], nB = T.count[B], sA = T.start[A], sB = T.start[B];
     const unsigned int bit = (1u << ax) - 1u;
@@ -251,37 +268,36 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
     const float HmA = T.hmax[A] * g.invL, HmB = T.hmax[B] * g.invL;
     const float slack = g.e * 1.52587890625e-05f + 1e-6f * fmaxf(HmA, HmB);   // 2^-16 e
     const float rB0 = sort_r[oB] + g.offBp;
-    for (int it = (int)((nA - 1) >> 5); it >= 0; --it) {
-      const unsigned int ii = (unsigned int)it * 32u + lane;
-      const bool vi = ii < nA;
-      const DensI I = load_dens(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, act, g.invL, g.e);
-      const float ri = vi ? sort_r[oA + ii] : -FLT_MAX;
-      const float maxri = warp_max(ri);
-      if (rB0 - maxri > fmaxf(HmA, HmB) + slack) break;      // this and every lower tile is out of reach
-      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
-      const TileBox bi = tile_box(vi, I.p);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      unsigned int cnt = 0;
-      for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
-        const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
-        if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;  // sorted: every later j is further away
-        const unsigned int jj = jt * 32u + lane;
-        const bool vj = jj < nB;
-        const DensI J = load_dens(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, act, g.invL, g.e);
-        const TileBox bj = tile_box(vj, J.p);
-        const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
-        if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
-        dens_put(S, lane, J);
-        __syncwarp();
-        for (int s = 0; s < 32; ++s) {
-          dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
-          __syncwarp();
-        }
-        flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+    // i-tiles are numbered from the interface (largest projection) outwards
+    const int it = (int)((nA - 1) >> 5) - (int)(t - Lq.p_toff[item]);
+    const unsigned int ii = (unsigned int)it * 32u + lane;
+    const bool vi = ii < nA;
+    const float maxri = warp_max(vi ? sort_r[oA + ii] : -FLT_MAX);
+    if (rB0 - maxri > fmaxf(HmA, HmB) + slack) continue;   // the tile is out of reach of every j
+    const DensI I = load_dens(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, act, g.invL, g.e);
+    const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
+    const TileBox bi = tile_box(vi, I.p);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned int cnt = 0;
+    for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
+      const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
+      if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;  // sorted: every later j is further away
+      const unsigned int jj = jt * 32u + lane;
+      const bool vj = jj < nB;
+      const DensI J = load_dens(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, act, g.invL, g.e);
+      const TileBox bj = tile_box(vj, J.p);
+      const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
+      if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
+      dens_put(S, lane, J);
+      __syncwarp();
+      for (int s = 0; s < 32; ++s) {
+        dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
         __syncwarp();
       }
-      flush_dens(I.g, acc, cnt, dacc, dcnt);
+      flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+      __syncwarp();
     }
+    flush_dens(I.g, acc, cnt, dacc, dcnt);
   }
   commit_counters<COUNT>(C, pc, 0);
 }
@@ -300,15 +316,19 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
   DensShared& S = SH[wl];
   Counters C;
   const int nself = min(Lq.counts[0], cap_self);
-  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < nself; item += gridDim.x * SPH_WARPS_PER_CTA) {
+  const unsigned int ntask = (unsigned int)Lq.counts[7];
+  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int item = task_item(Lq.s_toff, nself, t);
     const int A = Lq.self_a[item];
+    if (!T.active[A]) continue;
     const ItemGeom g = item_geom(T, box, A, 0);
     const unsigned int n = T.count[A], s0 = T.start[A];
     const float4 cA = T.cen[A];
     const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
     const float slack = g.e * 1.52587890625e-05f;
     const int nt = (int)((n + 31) >> 5);
-    for (int it = 0; it < nt; ++it) {
+    const int it = (int)(t - Lq.s_toff[item]);
+    {
       const unsigned int ii = (unsigned int)it * 32u + lane;
       const bool vi = ii < n;
       const DensI I = load_dens(vi, s0 + ii, sh, pos4, cen4, act, g.invL, g.e);
@@ -492,7 +512,9 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
   ForceShared& S = SH[wl];
   Counters C;
   const int npair = min(Lq.counts[1], cap_pair);
-  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < npair; item += gridDim.x * SPH_WARPS_PER_CTA) {
+  const unsigned int ntask = (unsigned int)Lq.counts[6];
+  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int item = task_item(Lq.p_toff, npair, t);
     const int A = Lq.pair_a[item], B = Lq.pair_b[item], ax = Lq.pair_axis[item];
     const ItemGeom g = item_geom(T, box, A, ax);
     const unsigned int nA = T.count[A], nB = T.count[B], sA = T.start[A], sB = T.start[B];
@@ -505,37 +527,35 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
     const float HmA = T.hmax[A] * g.invL, HmB = T.hmax[B] * g.invL;
     const float slack = g.e * 1.52587890625e-05f + 1e-6f * fmaxf(HmA, HmB);
     const float rB0 = sort_r[oB] + g.offBp;
-    for (int it = (int)((nA - 1) >> 5); it >= 0; --it) {
-      const unsigned int ii = (unsigned int)it * 32u + lane;
-      const bool vi = ii < nA;
-      const ForceI I = load_force(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, vel4, ghost4, g.invL, g.e);
-      const float ri = vi ? sort_r[oA + ii] : -FLT_MAX;
-      const float maxri = warp_max(ri);
-      if (rB0 - maxri > fmaxf(HmA, HmB) + slack) break;
-      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
-      const TileBox bi = tile_box(vi, I.p);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      float vsi = 0.0f;
-      for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
-        const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
-        if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;
-        const unsigned int jj = jt * 32u + lane;
-        const bool vj = jj < nB;
-        const ForceI J = load_force(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, vel4, ghost4, g.invL, g.e);
-        const TileBox bj = tile_box(vj, J.p);
-        const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
-        if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
-        force_put(S, lane, J);
-        __syncwarp();
-        for (int s = 0; s < 32; ++s) {
-          force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
-          __syncwarp();
-        }
-        flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+    const int it = (int)((nA - 1) >> 5) - (int)(t - Lq.p_toff[item]);
+    const unsigned int ii = (unsigned int)it * 32u + lane;
+    const bool vi = ii < nA;
+    const float maxri = warp_max(vi ? sort_r[oA + ii] : -FLT_MAX);
+    if (rB0 - maxri > fmaxf(HmA, HmB) + slack) continue;
+    const ForceI I = load_force(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, vel4, ghost4, g.invL, g.e);
+    const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
+    const TileBox bi = tile_box(vi, I.p);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float vsi = 0.0f;
+    for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
+      const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
+      if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;
+      const unsigned int jj = jt * 32u + lane;
+      const bool vj = jj < nB;
+      const ForceI J = load_force(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      const TileBox bj = tile_box(vj, J.p);
+      const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
+      if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
+      force_put(S, lane, J);
+      __syncwarp();
+      for (int s = 0; s < 32; ++s) {
+        force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
         __syncwarp();
       }
-      flush_force(I.g, acc, vsi, facc, fvsig);
+      flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+      __syncwarp();
     }
+    flush_force(I.g, acc, vsi, facc, fvsig);
   }
   commit_counters<COUNT>(C, pc, 2);
 }
@@ -555,7 +575,9 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
   ForceShared& S = SH[wl];
   Counters C;
   const int nself = min(Lq.counts[0], cap_self);
-  for (int item = blockIdx.x * SPH_WARPS_PER_CTA + wl; item < nself; item += gridDim.x * SPH_WARPS_PER_CTA) {
+  const unsigned int ntask = (unsigned int)Lq.counts[7];
+  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
+    const int item = task_item(Lq.s_toff, nself, t);
     const int A = Lq.self_a[item];
     const ItemGeom g = item_geom(T, box, A, 0);
     const unsigned int n = T.count[A], s0 = T.start[A];
@@ -563,7 +585,8 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
     const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
     const float slack = g.e * 1.52587890625e-05f;
     const int nt = (int)((n + 31) >> 5);
-    for (int it = 0; it < nt; ++it) {
+    const int it = (int)(t - Lq.s_toff[item]);
+    {
       const unsigned int ii = (unsigned int)it * 32u + lane;
       const bool vi = ii < n;
       const ForceI I = load_force(vi, s0 + ii, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
@@ -669,6 +692,35 @@ __global__ void k_zero_active(long long N, const unsigned char* __restrict__ act
       dcnt[p] = 0;
     }
   }
+}
+
+// Mark every cell that holds a particle still iterating h (and its ancestors).
+__global__ void k_mark_active_cells(long long N, const unsigned char* __restrict__ act,
+                                    const unsigned int* __restrict__ leaf_of, Tree T) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    if (!act[p]) continue;
+    for (int id = (int)leaf_of[p]; id >= 0; id = T.parent[id]) {
+      if (T.active[id]) break;        // an ancestor chain already being marked
+      T.active[id] = 1;
+    }
+  }
+}
+
+// i-tiles (32 particles) per interaction: the prefix of these numbers the tasks
+__global__ void k_task_tiles(Lists Lq, Tree T, int npair, int nself) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npair + nself; i += gridDim.x * blockDim.x) {
+    if (i < npair) Lq.p_toff[i] = (T.count[Lq.pair_a[i]] + 31u) >> 5;
+    else Lq.s_toff[i - npair] = (T.count[Lq.self_a[i - npair]] + 31u) >> 5;
+  }
+}
+
+__global__ void k_count_unconverged(long long N, const int* __restrict__ conv, int* __restrict__ out) {
+  int c = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    c += conv[p] ? 0 : 1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
 __global__ void k_set_active(long long N, unsigned char* __restrict__ act) {
@@ -869,7 +921,27 @@ void launch_zero_density(Engine& E, bool all) {
   k_zero_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.dacc.p, E.dcnt.p, all ? 1 : 0); count_launch();
 }
 
-void launch_set_active(Engine& E) { k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); count_launch(); }
+void launch_set_active(Engine& E) {
+  k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); count_launch();
+  cudaMemsetAsync(E.t_active.p, 1, E.n_nodes, E.st);
+}
+
+void launch_count_unconverged(Engine& E, int* out) {
+  k_count_unconverged<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.conv.p, out); count_launch();
+}
+
+void launch_mark_active_cells(Engine& E) {
+  cudaMemsetAsync(E.t_active.p, 0, E.n_nodes, E.st);
+  k_mark_active_cells<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.leaf_of.p, E.T); count_launch();
+}
+
+void launch_task_tables(Engine& E) {
+  k_task_tiles<<<E.grid(E.n_pairs + E.n_selfs), 256, 0, E.st>>>(E.Lq, E.T, E.n_pairs, E.n_selfs); count_launch();
+  exclusive_scan(E.Lq.p_toff, E.Lq.p_toff, E.n_pairs, E.scan_tmp.p,
+                 reinterpret_cast<unsigned int*>(E.Lq.counts + 6), E.st);
+  exclusive_scan(E.Lq.s_toff, E.Lq.s_toff, E.n_selfs, E.scan_tmp.p,
+                 reinterpret_cast<unsigned int*>(E.Lq.counts + 7), E.st);
+}
 
 void launch_bracket_reset(Engine& E) {
   k_h_bracket_reset<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.hlo.p, E.hhi.p, E.conv.p); count_launch();

@@ -84,6 +84,8 @@ class Engine {
   sph_status step(double dt);          // every box with the same dt
   sph_status step_boxes();             // every box with its own hbox[b].dt
   sph_status cfl_dt(int b, double* dt);
+  sph_status tune(int* best_leaf_max);
+  std::vector<std::pair<int, float>> tune_ms;   // (leaf_max, ms) of the last tune()
   sph_status get(int b, int field, void* dst, long long n, int mem);
   sph_status stats(int b, sph_stats* out);
   sph_status cells(int b, long long cap, int* level, int* ijk, int* count, int* split, long long* n_out);
@@ -131,11 +133,13 @@ class Engine {
   DBuf<float> t_hmax;
   DBuf<double> t_hlim;
   DBuf<float4> t_cen;
+  DBuf<unsigned char> t_active;
   Tree T{};
 
   // interaction lists
   int cap_self = 0, cap_pair = 0, cap_queue = 0;
   DBuf<int> l_self, l_pa, l_pb, l_pax, l_counts;
+  DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp;
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
   Lists Lq{};
 

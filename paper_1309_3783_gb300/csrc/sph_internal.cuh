@@ -172,6 +172,7 @@ struct Tree {
   float4* cen;              // centre minus its top cell's centre (units of L), exact
   unsigned int* axes;       // bit a: a sorted list along axis a is needed
   unsigned int* sortbase;   // offset of the first sorted list of this cell
+  unsigned char* active;    // 1 when a particle inside still iterates h
   int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier
 };
 
@@ -185,7 +186,10 @@ struct Lists {
   int* q_a[2];
   int* q_b[2];
   int* q_axis[2];
-  int* counts;              // [0] selfs, [1] pairs, [2] queue 0 size, [3] queue 1 size, [4] sort segments, [5] sort entries
+  unsigned int* p_toff;     // per pair: first task (i-tile) number, exclusive prefix
+  unsigned int* s_toff;     // per self: first task number
+  int* counts;              // [0] selfs, [1] pairs, [2] queue 0 size, [3] queue 1 size, [4] sort segments,
+                            // [5] sort entries, [6] pair tasks, [7] self tasks
 };
 
 // Per-box counters kept by the pair kernels when counting is on.

@@ -81,6 +81,8 @@ _SIGS = {
     "sph_box_profile": (C.c_int, [_P, C.c_int]),
     "sph_get_profile": (C.c_int, [_P, C.c_int32, C.POINTER(sph_profile_entry), C.POINTER(C.c_int32)]),
     "sph_launch_count": (C.c_int64, []),
+    "sph_box_tune": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "sph_box_set_leaf_max": (C.c_int, [_P, C.c_int32]),
     "sph_get_cells": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "sph_get_interactions": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "sph_server_create": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(_P)]),
@@ -271,6 +273,16 @@ def sph_launch_count() -> int:
     return int(load().sph_launch_count())
 
 
+def sph_box_tune(box, ctx) -> int:
+    v = C.c_int32()
+    _check(load().sph_box_tune(box, C.byref(v)), ctx)
+    return v.value
+
+
+def sph_box_set_leaf_max(box, ctx, leaf_max: int):
+    _check(load().sph_box_set_leaf_max(box, int(leaf_max)), ctx)
+
+
 def sph_get_cells(box, ctx) -> dict:
     n = C.c_int64()
     _check(load().sph_get_cells(box, 0, None, None, None, None, C.byref(n)), ctx)
@@ -385,6 +397,12 @@ class Box:
 
     def stats(self):
         return sph_get_stats(self.h, self.ctx)
+
+    def tune(self):
+        return sph_box_tune(self.h, self.ctx)
+
+    def set_leaf_max(self, leaf_max):
+        sph_box_set_leaf_max(self.h, self.ctx, leaf_max)
 
     def profile(self, on=True):
         sph_box_profile(self.h, self.ctx, on)

@@ -1,0 +1,136 @@
+"""GPU tests of stepping, serving (continuous batching), autotuning and profiling."""
+import numpy as np
+import pytest
+
+from oracle import sph as orc
+from paper_1309_3783_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1309_3783_gb300 import build, sph
+    build.build()
+    return sph
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.sph_ctx_create(device=0)
+    yield c
+    api.sph_ctx_destroy(c)
+
+
+def _run_alone(api, ctx, box, dt, n_steps):
+    b = api.box_from(ctx, box)
+    try:
+        for _ in range(n_steps):
+            b.step(dt)
+        return {k: b.get(k) for k in ("x", "v", "u", "h", "rho", "a", "count")}
+    finally:
+        b.close()
+
+
+def _periodic_diff(a, b, L):
+    d = a - b
+    return d - L * np.round(d / L)
+
+
+def test_kick_drift_kick_matches_oracle(api, ctx):
+    box = inputs.lattice_box(12, jitter=0.3, seed=31, v_sigma=0.3)
+    dt, n_steps = 2e-3, 3
+    g = _run_alone(api, ctx, box, dt, n_steps)
+    x, v, u, h, out = orc.kdk_steps(box, dt, n_steps)
+    a_rms = np.sqrt(np.mean(np.sum(out["a"] ** 2, axis=1)))
+    assert np.max(np.abs(_periodic_diff(g["x"], x, box.L))) < 1e-5 * box.meta["spacing"]
+    assert np.max(np.abs(g["v"] - v)) < 1e-3 * a_rms * dt * n_steps + 1e-6
+    np.testing.assert_allclose(g["h"], h, rtol=2e-4)
+    np.testing.assert_allclose(g["rho"], out["rho"], rtol=1e-3)
+
+
+def test_server_results_alone_and_in_the_mix(api, ctx):
+    boxes = [inputs.lattice_box(s, jitter=0.25, seed=40 + s, v_sigma=0.1) for s in (10, 14, 12, 16)]
+    dt, n_steps = 1e-3, 3
+    alone = [_run_alone(api, ctx, bx, dt, n_steps) for bx in boxes]
+    srv = api.sph_server_create(ctx, 0, 2)          # at most two resident boxes: the rest wait
+    try:
+        ids = [api.sph_server_submit(srv, bx.x, bx.v, bx.m, bx.u, bx.h, bx.L, True, n_steps, dt) for bx in boxes]
+        ticks = 0
+        while True:
+            done = [api.sph_server_poll(srv, i)[0] for i in ids]
+            if all(done):
+                break
+            api.sph_server_tick(srv)
+            ticks += 1
+            assert ticks < 100
+        # two boxes at a time, each needing a start tick plus n_steps ticks
+        assert ticks >= 2 * (n_steps + 1)
+        for bx, i, ref in zip(boxes, ids, alone):
+            _, ms = api.sph_server_poll(srv, i, n_steps)
+            assert np.all(ms > 0)
+            for k in ("x", "v", "u", "h", "rho", "a", "count"):
+                got = api.sph_server_get(srv, i, k, bx.n)
+                if k == "count":
+                    assert np.array_equal(got, ref[k])
+                elif k == "x":
+                    assert np.max(np.abs(_periodic_diff(got, ref[k], bx.L))) < 1e-9
+                else:
+                    scale = np.max(np.abs(ref[k]))
+                    assert np.max(np.abs(got - ref[k])) <= 1e-5 * scale + 1e-12, k
+            api.sph_server_release(srv, i)
+    finally:
+        api.sph_server_destroy(srv)
+
+
+def test_server_admission_by_memory_budget(api, ctx):
+    small = inputs.lattice_box(10, jitter=0.2, seed=3)
+    srv = api.sph_server_create(ctx, 700 * small.n, 0)   # room for one box of this size
+    try:
+        a = api.sph_server_submit(srv, small.x, small.v, small.m, small.u, small.h, 1.0, True, 1, 0.0)
+        b = api.sph_server_submit(srv, small.x, small.v, small.m, small.u, small.h, 1.0, True, 1, 0.0)
+        assert api.sph_server_tick(srv) == 1                 # only one admitted
+        while not api.sph_server_poll(srv, b)[0]:
+            api.sph_server_tick(srv)
+        assert api.sph_server_poll(srv, a)[0]
+        big = inputs.lattice_box(16, jitter=0.2, seed=4)
+        with pytest.raises(api.SphError):                    # can never fit
+            api.sph_server_submit(srv, big.x, big.v, big.m, big.u, big.h, 1.0, True, 1, 0.0)
+    finally:
+        api.sph_server_destroy(srv)
+
+
+def test_autotuned_leaf_size_keeps_parity(api, ctx):
+    box = inputs.plummer_box(n=12000, n_spheres=3, scale=0.04, seed=9)
+    b = api.box_from(ctx, box)
+    try:
+        leaf = b.tune()
+        assert leaf in (24, 32, 48, 64, 96, 128, 192, 256, 400)
+        b.density()
+        b.force()
+        cnt, rho, a = b.get("count"), b.get("rho"), b.get("a")
+    finally:
+        b.close()
+    ref = orc.full_step(box, iterate_h=False, method="kdtree")
+    assert np.array_equal(cnt, ref["count"])
+    np.testing.assert_allclose(rho, ref["rho"], rtol=1e-5)
+    rms = np.sqrt(np.mean(np.sum(ref["a"] ** 2, axis=1)))
+    assert np.max(np.abs(a - ref["a"])) <= 1e-4 * rms
+
+
+def test_profile_and_launch_counts(api, ctx):
+    box = inputs.lattice_box(16, jitter=0.1, seed=2)
+    b = api.box_from(ctx, box)
+    try:
+        l0 = api.sph_launch_count()
+        b.profile(True)
+        b.step(0.0)
+        prof = b.get_profile()
+        launched = api.sph_launch_count() - l0
+    finally:
+        b.close()
+    for ph in ("ingest", "keys_sort", "tree", "lists", "axis_sort", "density_pair", "density_self", "ghost",
+               "force_pair", "force_self", "reduce"):
+        assert prof[ph]["calls"] >= 1 and prof[ph]["ms"] > 0, ph
+    assert sum(v["launches"] for v in prof.values()) <= launched
+    assert prof["density_pair"]["launches"] >= 1

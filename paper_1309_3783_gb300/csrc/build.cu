@@ -15,28 +15,38 @@ namespace sph {
 __global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box, const double* __restrict__ x,
                          const float* __restrict__ v, const float* __restrict__ m, const float* __restrict__ u,
                          const float* __restrict__ h, float gamma_k, float* __restrict__ H_out) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const int b = bid[p];
-    const double L = box[b].L;
-    bool ok = true;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
+    const long long p = base + threadIdx.x;   // every lane of a warp runs every iteration
+    const bool valid = p < N;
+    const int b = valid ? bid[p] : -1;
+    bool ok = valid;
+    float H = 0.0f;
+    if (valid) {
+      const double L = box[b].L;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double xk = x[3 * p + k];
-      ok &= (xk >= 0.0) && (xk < L);
-      ok &= isfinite(v[3 * p + k]);
+      for (int k = 0; k < 3; ++k) {
+        const double xk = x[3 * p + k];
+        ok &= (xk >= 0.0) && (xk < L);
+        ok &= isfinite(v[3 * p + k]);
+      }
+      const float hp = h[p];
+      ok &= isfinite(hp) && hp > 0.0f && isfinite(m[p]) && m[p] > 0.0f && isfinite(u[p]) && u[p] >= 0.0f;
+      H = __fmul_rn(gamma_k, hp);
+      ok &= isfinite(H) && H > 0.0f;
+      if (!ok) atomicOr(&box[b].err, ERR_BAD_INPUT);
+      H_out[p] = ok ? H : 0.0f;
     }
-    const float hp = h[p];
-    ok &= isfinite(hp) && hp > 0.0f && isfinite(m[p]) && m[p] > 0.0f && isfinite(u[p]) && u[p] >= 0.0f;
-    const float H = __fmul_rn(gamma_k, hp);
-    ok &= isfinite(H) && H > 0.0f;
-    if (!ok) {
-      atomicOr(&box[b].err, ERR_BAD_INPUT);
-      H_out[p] = 0.0f;
-      continue;
+    // one atomic per warp and box: lanes of the same box reduce first (H > 0, so
+    // the float bit patterns order like the values)
+    const unsigned int same = __match_any_sync(0xffffffffu, b);
+    const unsigned int hb = ok ? __float_as_uint(H) : 0u;
+    const unsigned int mx = __reduce_max_sync(same, hb);
+    const unsigned int mn = __reduce_min_sync(same, ok ? hb : 0xffffffffu);
+    if (valid && (threadIdx.x & 31) == __ffs(same) - 1) {
+      if (mx) atomicMax(reinterpret_cast<unsigned int*>(&box[b].Hmax), mx);
+      if (mn != 0xffffffffu) atomicMin(reinterpret_cast<unsigned int*>(&box[b].Hmin), mn);
     }
-    H_out[p] = H;
-    atomic_max_pos(&box[b].Hmax, H);
-    atomic_min_pos(&box[b].Hmin, H);
   }
 }
 
@@ -569,7 +579,105 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
   }
 }
 
+// ============================================================== clusters
+// Inside every leaf, put the particles whose H exceeds the leaf edge after the
+// others (stable), so that warp-sized clusters hold particles of similar reach.
+// lsrc[p] = the particle that moves to position p.
+__global__ void k_leaf_partition(Tree T, int nnodes, const BoxDesc* __restrict__ box, const float* __restrict__ Hs,
+                                 unsigned int* __restrict__ lsrc) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned int lt = (1u << lane) - 1u;
+  for (int id = warp; id < nnodes; id += nwarps) {
+    if (T.child[id] >= 0) continue;
+    const unsigned int s = T.start[id], c = T.count[id];
+    const float thr = (float)ldexp(box[T.box[id]].L, -T.level[id]);
+    unsigned int nsmall = 0;
+    for (unsigned int b = 0; b < c; b += 32) {
+      const unsigned int q = b + lane;
+      nsmall += __popc(__ballot_sync(0xffffffffu, q < c && !(Hs[s + q] > thr)));
+    }
+    unsigned int os = 0, ol = nsmall;
+    for (unsigned int b = 0; b < c; b += 32) {
+      const unsigned int q = b + lane;
+      const bool valid = q < c;
+      const bool large = valid && Hs[s + q] > thr;
+      const unsigned int bs = __ballot_sync(0xffffffffu, valid && !large);
+      const unsigned int bl = __ballot_sync(0xffffffffu, large);
+      if (valid) {
+        const unsigned int dst = large ? ol + __popc(bl & lt) : os + __popc(bs & lt);
+        lsrc[s + dst] = s + q;
+      }
+      os += __popc(bs);
+      ol += __popc(bl);
+    }
+  }
+}
+
+__global__ void k_apply_partition(long long N, const unsigned int* __restrict__ lsrc,
+                                  const unsigned int* __restrict__ perm_in, unsigned int* __restrict__ perm_out,
+                                  const unsigned long long* __restrict__ key_in, unsigned long long* __restrict__ key_out,
+                                  const float* __restrict__ H_in, float* __restrict__ H_out,
+                                  const float4* __restrict__ vel_in, float4* __restrict__ vel_out) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const unsigned int q = lsrc[p];
+    perm_out[p] = perm_in[q];
+    key_out[p] = key_in[q];
+    H_out[p] = H_in[q];
+    vel_out[p] = vel_in[q];
+  }
+}
+
+// flag[p] = 1 where a cluster starts (every 32nd particle of a leaf)
+__global__ void k_tile_flags(long long N, Tree T, const unsigned int* __restrict__ leaf_of,
+                             unsigned int* __restrict__ flag) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    flag[p] = (((unsigned int)p - T.start[leaf_of[p]]) & 31u) == 0u ? 1u : 0u;
+}
+
+// cluster table from the exclusive prefix of the flags: tile_of[p], start, size,
+// leaf, box (relative to the leaf centre) and largest H
+__global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict__ leaf_of,
+                             const unsigned int* __restrict__ flag, const unsigned int* __restrict__ excl,
+                             const float4* __restrict__ pos4, unsigned int* __restrict__ tile_of, Tiles TL) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    tile_of[p] = excl[p] + flag[p] - 1u;
+    if (!flag[p]) continue;
+    const unsigned int t = excl[p];
+    const unsigned int leaf = leaf_of[p];
+    const unsigned int end = T.start[leaf] + T.count[leaf];
+    const unsigned int n = min(32u, end - (unsigned int)p);
+    float4 lo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.0f);
+    float4 hi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.0f);
+    for (unsigned int q = 0; q < n; ++q) {
+      const float4 a = pos4[p + q];
+      lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
+      hi.x = fmaxf(hi.x, a.x); hi.y = fmaxf(hi.y, a.y); hi.z = fmaxf(hi.z, a.z);
+      lo.w = fmaxf(lo.w, a.w);
+    }
+    TL.start[t] = (unsigned int)p;
+    TL.n[t] = n;
+    TL.leaf[t] = leaf;
+    TL.lo[t] = lo;
+    TL.hi[t] = hi;
+    TL.active[t] = 1;
+  }
+}
+
+__global__ void k_cell_tiles(Tree T, int nnodes, const unsigned int* __restrict__ tile_of) {
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
+    const unsigned int s = T.start[id], c = T.count[id];
+    const unsigned int t0 = tile_of[s];
+    T.tile0[id] = t0;
+    T.ntile[id] = tile_of[s + c - 1] - t0 + 1u;
+  }
+}
+
 // ============================================================== axis sorts
+// Section II-C keeps, per cell, the particles sorted along each of the 13
+// cell-pair axes.  Here the sorted entries are the cell's clusters, keyed by the
+// lower end of the projection of their box on the axis.
 __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
   const int n = min(Lq.counts[1], cap_pair);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -579,16 +687,16 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
   }
 }
 
-// Storage for the sorted lists: every (cell, needed axis) gets count entries.
-// Cells above SORT_SMALL particles also list their (cell, axis) segments for
-// the global sort.
+// Storage for the sorted lists: every (cell, needed axis) gets ntile entries.
+// Cells above SORT_SMALL clusters also list their (cell, axis) segments for the
+// global sort.
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
                              unsigned int* __restrict__ big_off, unsigned long long* __restrict__ big_count,
                              int cap_big) {
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int ax = T.axes[id];
     if (!ax) continue;
-    const unsigned int c = T.count[id];
+    const unsigned int c = T.ntile[id];
     const int na = __popc(ax);
     T.sortbase[id] = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
     atomicAdd(&Lq.counts[4], na);
@@ -621,35 +729,65 @@ __device__ __forceinline__ float3 axis_unit(int a) {
   return make_float3(dx * s, dy * s, dz * s);
 }
 
-// projection of particle p on axis u in the frame of the cell with centre cc
-__device__ __forceinline__ float project(const float4* pos4, const float4* cen4, unsigned int p, float4 cc, float3 u) {
-  const float4 q = pos4[p];
-  const float4 c = cen4[p];
-  const float x = q.x + (c.x - cc.x), y = q.y + (c.y - cc.y), z = q.z + (c.z - cc.z);
+// lower end of the projection on u of cluster t's box, in the frame of the cell
+// with centre cc (the leaf-to-cell offset is exact)
+__device__ __forceinline__ float tile_rlo(const Tiles& TL, const Tree& T, unsigned int t, float4 cc, float3 u) {
+  const float4 lc = T.cen[TL.leaf[t]];
+  const float4 lo = TL.lo[t], hi = TL.hi[t];
+  const float ox = lc.x - cc.x, oy = lc.y - cc.y, oz = lc.z - cc.z;
+  const float x = (u.x >= 0.0f ? lo.x : hi.x) + ox;
+  const float y = (u.y >= 0.0f ? lo.y : hi.y) + oy;
+  const float z = (u.z >= 0.0f ? lo.z : hi.z) + oz;
   return fmaf(u.x, x, fmaf(u.y, y, u.z * z));
 }
 
-// One CTA per cell with at most SORT_SMALL particles: bitonic sort of
-// (projection, local index) in shared memory for every needed axis.
-__global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, const float4* __restrict__ pos4,
-                                                   const float4* __restrict__ cen4, float* __restrict__ sort_r,
+// One CTA per cell with at most SORT_SMALL clusters: bitonic sort of
+// (projection, cluster) in shared memory for every needed axis.
+__global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, Tiles TL, float* __restrict__ sort_r,
                                                    unsigned int* __restrict__ sort_i) {
   __shared__ float sr[SORT_SMALL];
   __shared__ unsigned int si[SORT_SMALL];
   for (int id = blockIdx.x; id < nnodes; id += gridDim.x) {
     const unsigned int ax = T.axes[id];
-    const unsigned int c = T.count[id];
+    const unsigned int c = T.ntile[id];
     if (!ax || c > SORT_SMALL) continue;
     unsigned int npow = 1;
     while (npow < c) npow <<= 1;
-    const unsigned int s = T.start[id];
+    const unsigned int t0 = T.tile0[id];
     const float4 cc = T.cen[id];
     unsigned int out = T.sortbase[id];
     for (int a = 0; a < 13; ++a) {
       if (!(ax & (1u << a))) continue;
       const float3 u = axis_unit(a);
+      if (c <= 32) {
+        // one warp: register bitonic sort over shuffles
+        if (threadIdx.x < 32) {
+          const unsigned int q = threadIdx.x;
+          float r = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
+          unsigned int ix = q;
+          for (unsigned int k = 2; k <= 32; k <<= 1) {
+            for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+              const float r2 = __shfl_xor_sync(0xffffffffu, r, j);
+              const unsigned int i2 = __shfl_xor_sync(0xffffffffu, ix, j);
+              const bool lower = (q & j) == 0;
+              const bool up = (q & k) == 0;
+              const bool gt = (r > r2) || (r == r2 && ix > i2);
+              if ((lower == up) == gt) {
+                r = r2;
+                ix = i2;
+              }
+            }
+          }
+          if (q < c) {
+            sort_r[out + q] = r;
+            sort_i[out + q] = t0 + ix;
+          }
+        }
+        out += c;
+        continue;
+      }
       for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
-        sr[q] = q < c ? project(pos4, cen4, s + q, cc, u) : FLT_MAX;
+        sr[q] = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
         si[q] = q;
       }
       __syncthreads();
@@ -673,7 +811,7 @@ __global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, const fl
       }
       for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
         sort_r[out + q] = sr[q];
-        sort_i[out + q] = si[q];
+        sort_i[out + q] = t0 + si[q];
       }
       out += c;
       __syncthreads();
@@ -681,41 +819,40 @@ __global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, const fl
   }
 }
 
-// Large cells: composite keys (segment << 32 | orderable projection) for one
-// global radix sort, then scatter back into each cell's storage.
+// Cells with many clusters: composite keys (segment << 32 | orderable projection)
+// for one global radix sort, then scatter back into each cell's storage.
 __global__ void k_sort_big_keys(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
-                                const unsigned int* __restrict__ big_off, Tree T, const float4* __restrict__ pos4,
-                                const float4* __restrict__ cen4, unsigned long long* __restrict__ ckey,
-                                unsigned int* __restrict__ cval) {
+                                const unsigned int* __restrict__ big_off, Tree T, Tiles TL,
+                                unsigned long long* __restrict__ ckey, unsigned int* __restrict__ cval) {
   for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
     const int id = big_node[sgi];
     const int a = big_axis[sgi];
-    const unsigned int c = T.count[id], s = T.start[id], o = big_off[sgi];
+    const unsigned int c = T.ntile[id], t0 = T.tile0[id], o = big_off[sgi];
     const float4 cc = T.cen[id];
     const float3 u = axis_unit(a);
     for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
-      ckey[o + q] = ((unsigned long long)sgi << 32) | float_key(project(pos4, cen4, s + q, cc, u));
+      ckey[o + q] = ((unsigned long long)sgi << 32) | float_key(tile_rlo(TL, T, t0 + q, cc, u));
       cval[o + q] = q;
     }
   }
 }
 
 __global__ void k_sort_big_scatter(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
-                                   const unsigned int* __restrict__ big_off, Tree T, const float4* __restrict__ pos4,
-                                   const float4* __restrict__ cen4, const unsigned int* __restrict__ cval,
-                                   float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
+                                   const unsigned int* __restrict__ big_off, Tree T, Tiles TL,
+                                   const unsigned int* __restrict__ cval, float* __restrict__ sort_r,
+                                   unsigned int* __restrict__ sort_i) {
   for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
     const int id = big_node[sgi];
     const int a = big_axis[sgi];
     const unsigned int ax = T.axes[id];
-    const unsigned int c = T.count[id], s = T.start[id], o = big_off[sgi];
+    const unsigned int c = T.ntile[id], t0 = T.tile0[id], o = big_off[sgi];
     const unsigned int dst = T.sortbase[id] + (unsigned int)__popc(ax & ((1u << a) - 1u)) * c;
     const float4 cc = T.cen[id];
     const float3 u = axis_unit(a);
     for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
       const unsigned int li = cval[o + q];
-      sort_i[dst + q] = li;
-      sort_r[dst + q] = project(pos4, cen4, s + li, cc, u);
+      sort_i[dst + q] = t0 + li;
+      sort_r[dst + q] = tile_rlo(TL, T, t0 + li, cc, u);
     }
   }
 }

@@ -32,11 +32,19 @@ __global__ void k_shift(long long, int, const unsigned long long*, const unsigne
                         const BoxDesc*, const double*, const float*, const float*, float4*, float4*);
 __global__ void k_mark_axes(Lists, int, Tree);
 __global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, unsigned long long*, int);
-__global__ void k_sort_small(Tree, int, const float4*, const float4*, float*, unsigned int*);
-__global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, const float4*, const float4*,
-                                unsigned long long*, unsigned int*);
-__global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, const float4*,
-                                   const float4*, const unsigned int*, float*, unsigned int*);
+__global__ void k_sort_small(Tree, int, Tiles, float*, unsigned int*);
+__global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, Tiles, unsigned long long*,
+                                unsigned int*);
+__global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, Tiles,
+                                   const unsigned int*, float*, unsigned int*);
+__global__ void k_leaf_partition(Tree, int, const BoxDesc*, const float*, unsigned int*);
+__global__ void k_apply_partition(long long, const unsigned int*, const unsigned int*, unsigned int*,
+                                  const unsigned long long*, unsigned long long*, const float*, float*,
+                                  const float4*, float4*);
+__global__ void k_tile_flags(long long, Tree, const unsigned int*, unsigned int*);
+__global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigned int*, const unsigned int*,
+                             const float4*, unsigned int*, Tiles);
+__global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
 void launch_density_pair(Engine& E);
 void launch_density_self(Engine& E);
@@ -203,6 +211,24 @@ sph_status Engine::ensure_particle_capacity() {
   CK(leaf_of.reserve(n));
   CK(top_at.reserve(n));
   CK(act.reserve(n));
+  CK(Hs_tmp.reserve(n));
+  CK(vel4_tmp.reserve(n));
+  CK(lsrc.reserve(n));
+  CK(tflag.reserve(n));
+  CK(texcl.reserve(n));
+  CK(tile_of.reserve(n));
+  CK(tl_start.reserve(n));
+  CK(tl_n.reserve(n));
+  CK(tl_leaf.reserve(n));
+  CK(tl_lo.reserve(n));
+  CK(tl_hi.reserve(n));
+  CK(tl_active.reserve(n));
+  TL.start = tl_start.p;
+  TL.n = tl_n.p;
+  TL.leaf = tl_leaf.p;
+  TL.lo = tl_lo.p;
+  TL.hi = tl_hi.p;
+  TL.active = tl_active.p;
   CK(dacc.reserve(n));
   CK(dcnt.reserve(n));
   CK(ghost4.reserve(n));
@@ -241,6 +267,8 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   CK(t_hlim.reserve(n));
   CK(t_cen.reserve(n));
   CK(t_active.reserve(n));
+  CK(t_tile0.reserve(n));
+  CK(t_ntile.reserve(n));
   CK(t_n.reserve(8));
   T.start = t_start.p;
   T.count = t_count.p;
@@ -258,6 +286,8 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   T.axes = t_axes.p;
   T.sortbase = t_sortbase.p;
   T.active = t_active.p;
+  T.tile0 = t_tile0.p;
+  T.ntile = t_ntile.p;
   T.n_nodes = t_n.p;
   CK(big_node.reserve(1));
   return ensure_list_capacity(nodes, 8 * nodes, 8 * nodes);
@@ -432,8 +462,21 @@ sph_status Engine::build_once(bool* retry) {
   prof_end(PH_LISTS, ev, l0);
   ev = prof_begin(PH_SHIFT, &l0);
   k_leaves<<<nsm * 8, 256, 0, st>>>(T, n_nodes, leaf_of.p); count_launch();
+  // particles of each leaf: the ones with H above the leaf edge last (stable)
+  k_leaf_partition<<<nsm * 8, 256, 0, st>>>(T, n_nodes, box.p, Hs.p, lsrc.p); count_launch();
+  k_apply_partition<<<grid(N), 256, 0, st>>>(N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
+                                             vel4.p, vel4_tmp.p); count_launch();
+  perm.swap(perm_tmp);
+  key.swap(key_tmp);
+  Hs.swap(Hs_tmp);
+  vel4.swap(vel4_tmp);
   k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p); count_launch();
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  // clusters of at most 32 particles inside each leaf
+  k_tile_flags<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p); count_launch();
+  exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), st);
+  k_tile_table<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL); count_launch();
+  k_cell_tiles<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, tile_of.p); count_launch();
   prof_end(PH_SHIFT, ev, l0);
 
   // ---- sorted projections
@@ -455,6 +498,8 @@ sph_status Engine::build_once(bool* retry) {
   unsigned long long bcw = 0;
   CK(cudaMemcpyAsync(lc, l_counts.p, sizeof(lc), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&bcw, big_count.p, sizeof(bcw), cudaMemcpyDeviceToHost, st));
+  unsigned int ntl = 0;
+  CK(cudaMemcpyAsync(&ntl, dev_counters.p + 4, sizeof(ntl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int last_q = lc[2 + (rounds & 1)];
@@ -474,6 +519,7 @@ sph_status Engine::build_once(bool* retry) {
     *retry = true;
     return SPH_OK;
   }
+  n_tiles = ntl;
   n_selfs = lc[0];
   n_pairs = lc[1];
   n_segments = lc[4];
@@ -484,7 +530,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   ev = prof_begin(PH_AXIS_SORT, &l0);
-  k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, pos4.p, cen4.p, sort_r.p, sort_i.p); count_launch();
+  k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, TL, sort_r.p, sort_i.p); count_launch();
   if (n_big > 0) {
     const size_t nb = (size_t)n_big_entries;
     CK(ckey.reserve(nb));
@@ -492,12 +538,12 @@ sph_status Engine::build_once(bool* retry) {
     CK(cval.reserve(nb));
     CK(cval_tmp.reserve(nb));
     if (rs_scratch.n < (size_t)radix_scratch_words(nb)) CK(rs_scratch.reserve(radix_scratch_words(nb)));
-    k_sort_big_keys<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, pos4.p,
-                                                              cen4.p, ckey.p, cval.p); count_launch();
+    k_sort_big_keys<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, TL,
+                                                              ckey.p, cval.p); count_launch();
     radix_sort(ckey.p, cval.p, ckey_tmp.p, cval_tmp.p, (long long)nb, 32 + std::max(1, ceil_log2(n_big)),
                rs_scratch.p, st);
-    k_sort_big_scatter<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T,
-                                                                 pos4.p, cen4.p, cval.p, sort_r.p, sort_i.p); count_launch();
+    k_sort_big_scatter<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, TL,
+                                                                 cval.p, sort_r.p, sort_i.p); count_launch();
   }
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());

@@ -65,27 +65,6 @@ __device__ __forceinline__ bool decide(float r2, float H2, float band, int gi, i
   return exact_less(gi, gj, Hphys, perm, x, g.L, g.halfL, g.periodic);
 }
 
-// Axis-aligned box of a warp's tile and the separation between two tiles.
-struct TileBox {
-  float lx, ly, lz, hx, hy, hz;
-};
-__device__ __forceinline__ TileBox tile_box(bool valid, float3 p) {
-  TileBox b;
-  b.lx = warp_min(valid ? p.x : FLT_MAX);
-  b.ly = warp_min(valid ? p.y : FLT_MAX);
-  b.lz = warp_min(valid ? p.z : FLT_MAX);
-  b.hx = warp_max(valid ? p.x : -FLT_MAX);
-  b.hy = warp_max(valid ? p.y : -FLT_MAX);
-  b.hz = warp_max(valid ? p.z : -FLT_MAX);
-  return b;
-}
-__device__ __forceinline__ float tile_gap(const TileBox& a, const TileBox& b) {
-  const float gx = fmaxf(0.0f, fmaxf(b.lx - a.hx, a.lx - b.hx));
-  const float gy = fmaxf(0.0f, fmaxf(b.ly - a.hy, a.ly - b.hy));
-  const float gz = fmaxf(0.0f, fmaxf(b.lz - a.hz, a.lz - b.hz));
-  return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
-}
-
 // Task t of a prefix table toff[0..n) (exclusive prefix of i-tiles per item):
 // the item with toff[item] <= t < toff[item + 1].
 __device__ __forceinline__ int task_item(const unsigned int* __restrict__ toff, int n, unsigned int t) {
@@ -236,8 +215,111 @@ __device__ __forceinline__ void commit_counters(const Counters& C, unsigned long
   }
 }
 
+
+// ------------------------------------------------------------- cluster geometry
+__device__ __forceinline__ float3 axis_unit_f(int a) {
+  int dx, dy, dz;
+  axis_vec(a, dx, dy, dz);
+  const int n2 = dx * dx + dy * dy + dz * dz;
+  const float s = n2 == 1 ? 1.0f : (n2 == 2 ? 0.70710678118654752f : 0.57735026918962576f);
+  return make_float3(dx * s, dy * s, dz * s);
+}
+
+struct Box3 {
+  float3 lo, hi;
+};
+
+// box of cluster t in the frame whose origin sits at -off from the leaf frame:
+// box + (leaf centre + off), the offset being exact (dyadic)
+__device__ __forceinline__ Box3 tile_box3(const Tiles& TL, const Tree& T, unsigned int t, float3 off) {
+  const float4 lc = T.cen[TL.leaf[t]];
+  const float4 lo = TL.lo[t], hi = TL.hi[t];
+  const float ox = lc.x + off.x, oy = lc.y + off.y, oz = lc.z + off.z;
+  Box3 b;
+  b.lo = make_float3(lo.x + ox, lo.y + oy, lo.z + oz);
+  b.hi = make_float3(hi.x + ox, hi.y + oy, hi.z + oz);
+  return b;
+}
+
+__device__ __forceinline__ float box_gap(const Box3& a, const Box3& b) {
+  const float gx = fmaxf(0.0f, fmaxf(b.lo.x - a.hi.x, a.lo.x - b.hi.x));
+  const float gy = fmaxf(0.0f, fmaxf(b.lo.y - a.hi.y, a.lo.y - b.hi.y));
+  const float gz = fmaxf(0.0f, fmaxf(b.lo.z - a.hi.z, a.lo.z - b.hi.z));
+  return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+}
+
+// upper end of the projection of a box on u
+__device__ __forceinline__ float box_rhi(const Box3& b, float3 u) {
+  return fmaf(u.x, u.x >= 0.0f ? b.hi.x : b.lo.x,
+              fmaf(u.y, u.y >= 0.0f ? b.hi.y : b.lo.y, u.z * (u.z >= 0.0f ? b.hi.z : b.lo.z)));
+}
+
+// Pair-interaction setup shared by the density and force kernels.
+struct PairSetup {
+  int A, B;
+  ItemGeom g;
+  float3 shA, shB;        // particle frame offsets: leaf frame -> A's frame (B includes e db)
+  float3 tshA, tshB;      // cluster box offsets (the leaf centre is added per cluster)
+  float3 u;
+  unsigned int sb, ntj;   // B's sorted cluster list
+  float HmB, slack;
+  Box3 cellB;             // B's cell in A's frame
+};
+
+__device__ __forceinline__ PairSetup pair_setup(const Lists& Lq, const Tree& T, const BoxDesc* box, int item) {
+  PairSetup P;
+  P.A = Lq.pair_a[item];
+  P.B = Lq.pair_b[item];
+  const int ax = Lq.pair_axis[item];
+  P.g = item_geom(T, box, P.A, ax);
+  const float4 cA = T.cen[P.A], cB = T.cen[P.B];
+  P.shA = make_float3(-cA.x, -cA.y, -cA.z);
+  P.shB = make_float3(P.g.offB.x - cB.x, P.g.offB.y - cB.y, P.g.offB.z - cB.z);
+  P.tshA = P.shA;
+  P.tshB = P.shB;
+  P.u = axis_unit_f(ax);
+  P.ntj = T.ntile[P.B];
+  P.sb = T.sortbase[P.B] + (unsigned int)__popc(T.axes[P.B] & ((1u << ax) - 1u)) * P.ntj;
+  P.HmB = T.hmax[P.B] * P.g.invL;
+  P.slack = P.g.e * 1.52587890625e-05f + 1e-6f * fmaxf(P.HmB, T.hmax[P.A] * P.g.invL);   // 2^-16 e
+  const float h = 0.5f * P.g.e;
+  P.cellB.lo = make_float3(P.g.offB.x - h, P.g.offB.y - h, P.g.offB.z - h);
+  P.cellB.hi = make_float3(P.g.offB.x + h, P.g.offB.y + h, P.g.offB.z + h);
+  return P;
+}
+
+// Lane-parallel scan of B's sorted cluster list for the i cluster (box bi,
+// largest support Hi): returns in *jt the lane's candidate and a ballot of the
+// lanes whose cluster is in reach (sorted window, then box distance).
+// *stop is set when the sorted window has passed every cluster of B.
+template <bool DENS>
+__device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const Tree& T, const Tiles& TL,
+                                                      const float* __restrict__ sort_r,
+                                                      const unsigned int* __restrict__ sort_i, unsigned int e0,
+                                                      const Box3& bi, float rhi_i, float Hi, bool i_active,
+                                                      unsigned int* jt, bool* stop) {
+  const int lane = threadIdx.x & 31;
+  const float r0 = sort_r[P.sb + e0] + P.g.offBp;
+  *stop = r0 - rhi_i > fmaxf(Hi, P.HmB) + P.slack;     // the sorted list only moves further away
+  if (*stop) return 0u;
+  const unsigned int e = e0 + lane;
+  bool pass = false;
+  unsigned int t = 0;
+  if (e < P.ntj) {
+    t = sort_i[P.sb + e];
+    const float rlo = sort_r[P.sb + e] + P.g.offBp;
+    const float reach = fmaxf(Hi, TL.lo[t].w * P.g.invL) + P.slack;
+    if (rlo - rhi_i <= reach && (!DENS || i_active || TL.active[t])) {
+      const Box3 bj = tile_box3(TL, T, t, P.tshB);
+      pass = box_gap(bi, bj) <= reach;
+    }
+  }
+  *jt = t;
+  return __ballot_sync(0xffffffffu, pass);
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_pair, Tree T,
+__global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_pair, Tree T, Tiles TL,
                                                               const BoxDesc* __restrict__ box,
                                                               const float4* __restrict__ pos4,
                                                               const float4* __restrict__ cen4,
@@ -255,47 +337,41 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
   const unsigned int ntask = (unsigned int)Lq.counts[6];
   for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
     const int item = task_item(Lq.p_toff, npair, t);
-    const int A = Lq.pair_a[item], B = Lq.pair_b[item], ax = Lq.pair_axis[item];
-    if (!(T.active[A] | T.active[B])) continue;          // no particle of either cell still iterating h
-    const ItemGeom g = item_geom(T, box, A, ax);
-    const unsigned int nA = T.count[A], nB = T.count[B], sA = T.start[A], sB = T.start[B];
-    const unsigned int bit = (1u << ax) - 1u;
-    const unsigned int oA = T.sortbase[A] + (unsigned int)__popc(T.axes[A] & bit) * nA;
-    const unsigned int oB = T.sortbase[B] + (unsigned int)__popc(T.axes[B] & bit) * nB;
-    const float4 cA = T.cen[A], cB = T.cen[B];
-    const float3 shA = make_float3(-cA.x, -cA.y, -cA.z);
-    const float3 shB = make_float3(g.offB.x - cB.x, g.offB.y - cB.y, g.offB.z - cB.z);
-    const float HmA = T.hmax[A] * g.invL, HmB = T.hmax[B] * g.invL;
-    const float slack = g.e * 1.52587890625e-05f + 1e-6f * fmaxf(HmA, HmB);   // 2^-16 e
-    const float rB0 = sort_r[oB] + g.offBp;
-    // i-tiles are numbered from the interface (largest projection) outwards
-    const int it = (int)((nA - 1) >> 5) - (int)(t - Lq.p_toff[item]);
-    const unsigned int ii = (unsigned int)it * 32u + lane;
-    const bool vi = ii < nA;
-    const float maxri = warp_max(vi ? sort_r[oA + ii] : -FLT_MAX);
-    if (rB0 - maxri > fmaxf(HmA, HmB) + slack) continue;   // the tile is out of reach of every j
-    const DensI I = load_dens(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, act, g.invL, g.e);
-    const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
-    const TileBox bi = tile_box(vi, I.p);
+    const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
+    if (!(T.active[A0] | T.active[B0])) continue;          // no particle of either cell still iterating h
+    const unsigned int ti = T.tile0[A0] + (t - Lq.p_toff[item]);
+    const bool i_active = TL.active[ti] != 0;
+    if (!i_active && !T.active[B0]) continue;
+    const PairSetup P = pair_setup(Lq, T, box, item);
+    const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+    const float Hi = TL.lo[ti].w * P.g.invL;
+    if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;   // cluster out of reach of B
+    const float rhi_i = box_rhi(bi, P.u);
+    const unsigned int ni = TL.n[ti];
+    const bool vi = (unsigned int)lane < ni;
+    const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned int cnt = 0;
-    for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
-      const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
-      if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;  // sorted: every later j is further away
-      const unsigned int jj = jt * 32u + lane;
-      const bool vj = jj < nB;
-      const DensI J = load_dens(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, act, g.invL, g.e);
-      const TileBox bj = tile_box(vj, J.p);
-      const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
-      if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
-      dens_put(S, lane, J);
-      __syncwarp();
-      for (int s = 0; s < 32; ++s) {
-        dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
+    for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
+      unsigned int jt;
+      bool stop;
+      unsigned int mask = scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &stop);
+      if (stop) break;
+      while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const unsigned int tj = __shfl_sync(0xffffffffu, jt, k);
+        const bool vj = (unsigned int)lane < TL.n[tj];
+        const DensI J = load_dens(vj, TL.start[tj] + lane, P.shB, pos4, cen4, act, P.g.invL, P.g.e);
+        dens_put(S, lane, J);
+        __syncwarp();
+        for (int s = 0; s < 32; ++s) {
+          dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, P.g, C);
+          __syncwarp();
+        }
+        flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
         __syncwarp();
       }
-      flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
-      __syncwarp();
     }
     flush_dens(I.g, acc, cnt, dacc, dcnt);
   }
@@ -303,7 +379,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_self, Tree T,
+__global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_self, Tree T, Tiles TL,
                                                               const BoxDesc* __restrict__ box,
                                                               const float4* __restrict__ pos4,
                                                               const float4* __restrict__ cen4,
@@ -322,48 +398,44 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
     const int A = Lq.self_a[item];
     if (!T.active[A]) continue;
     const ItemGeom g = item_geom(T, box, A, 0);
-    const unsigned int n = T.count[A], s0 = T.start[A];
     const float4 cA = T.cen[A];
     const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-    const float slack = g.e * 1.52587890625e-05f;
-    const int nt = (int)((n + 31) >> 5);
-    const int it = (int)(t - Lq.s_toff[item]);
-    {
-      const unsigned int ii = (unsigned int)it * 32u + lane;
-      const bool vi = ii < n;
-      const DensI I = load_dens(vi, s0 + ii, sh, pos4, cen4, act, g.invL, g.e);
-      const TileBox bi = tile_box(vi, I.p);
-      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      unsigned int cnt = 0;
-      for (int jt = it; jt < nt; ++jt) {
-        const unsigned int jj = (unsigned int)jt * 32u + lane;
-        const bool vj = jj < n;
-        const DensI J = load_dens(vj, s0 + jj, sh, pos4, cen4, act, g.invL, g.e);
-        if (jt != it) {
-          const TileBox bj = tile_box(vj, J.p);
-          const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
-          if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
-        }
-        dens_put(S, lane, J);
-        __syncwarp();
-        if (jt == it) {
-          // pairs inside one tile: steps 1..16, the 16th on half the lanes
-          for (int s = 1; s <= 16; ++s) {
-            if (s < 16 || lane < 16) dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
-            __syncwarp();
-          }
-        } else {
-          for (int s = 0; s < 32; ++s) {
-            dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
-            __syncwarp();
-          }
-        }
-        flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
-        __syncwarp();
+    const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+    const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
+    const unsigned int ti = t0 + (t - Lq.s_toff[item]);
+    const bool i_active = TL.active[ti] != 0;
+    const Box3 bi = tile_box3(TL, T, ti, sh);
+    const float Hi = TL.lo[ti].w * g.invL;
+    const bool vi = (unsigned int)lane < TL.n[ti];
+    const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned int cnt = 0;
+    for (unsigned int tj = ti; tj < t0 + nt; ++tj) {
+      if (tj != ti) {
+        if (!i_active && !TL.active[tj]) continue;
+        const Box3 bj = tile_box3(TL, T, tj, sh);
+        if (box_gap(bi, bj) > fmaxf(Hi, TL.lo[tj].w * g.invL) + slack) continue;
       }
-      flush_dens(I.g, acc, cnt, dacc, dcnt);
+      const bool vj = (unsigned int)lane < TL.n[tj];
+      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
+      dens_put(S, lane, J);
+      __syncwarp();
+      if (tj == ti) {
+        // pairs inside one cluster: steps 1..16, the 16th on half the lanes
+        for (int s = 1; s <= 16; ++s) {
+          if (s < 16 || lane < 16) dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
+          __syncwarp();
+        }
+      } else {
+        for (int s = 0; s < 32; ++s) {
+          dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
+          __syncwarp();
+        }
+      }
+      flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+      __syncwarp();
     }
+    flush_dens(I.g, acc, cnt, dacc, dcnt);
   }
   commit_counters<COUNT>(C, pc, 1);
 }
@@ -495,8 +567,9 @@ __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, floa
   atomic_max_pos(&fvsig[gidx], vs);
 }
 
+
 template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pair, Tree T,
+__global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pair, Tree T, Tiles TL,
                                                             const BoxDesc* __restrict__ box,
                                                             const float4* __restrict__ pos4,
                                                             const float4* __restrict__ cen4,
@@ -515,45 +588,36 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
   const unsigned int ntask = (unsigned int)Lq.counts[6];
   for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
     const int item = task_item(Lq.p_toff, npair, t);
-    const int A = Lq.pair_a[item], B = Lq.pair_b[item], ax = Lq.pair_axis[item];
-    const ItemGeom g = item_geom(T, box, A, ax);
-    const unsigned int nA = T.count[A], nB = T.count[B], sA = T.start[A], sB = T.start[B];
-    const unsigned int bit = (1u << ax) - 1u;
-    const unsigned int oA = T.sortbase[A] + (unsigned int)__popc(T.axes[A] & bit) * nA;
-    const unsigned int oB = T.sortbase[B] + (unsigned int)__popc(T.axes[B] & bit) * nB;
-    const float4 cA = T.cen[A], cB = T.cen[B];
-    const float3 shA = make_float3(-cA.x, -cA.y, -cA.z);
-    const float3 shB = make_float3(g.offB.x - cB.x, g.offB.y - cB.y, g.offB.z - cB.z);
-    const float HmA = T.hmax[A] * g.invL, HmB = T.hmax[B] * g.invL;
-    const float slack = g.e * 1.52587890625e-05f + 1e-6f * fmaxf(HmA, HmB);
-    const float rB0 = sort_r[oB] + g.offBp;
-    const int it = (int)((nA - 1) >> 5) - (int)(t - Lq.p_toff[item]);
-    const unsigned int ii = (unsigned int)it * 32u + lane;
-    const bool vi = ii < nA;
-    const float maxri = warp_max(vi ? sort_r[oA + ii] : -FLT_MAX);
-    if (rB0 - maxri > fmaxf(HmA, HmB) + slack) continue;
-    const ForceI I = load_force(vi, vi ? sA + sort_i[oA + ii] : 0u, shA, pos4, cen4, vel4, ghost4, g.invL, g.e);
-    const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
-    const TileBox bi = tile_box(vi, I.p);
+    const PairSetup P = pair_setup(Lq, T, box, item);
+    const unsigned int ti = T.tile0[P.A] + (t - Lq.p_toff[item]);
+    const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+    const float Hi = TL.lo[ti].w * P.g.invL;
+    if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;
+    const float rhi_i = box_rhi(bi, P.u);
+    const bool vi = (unsigned int)lane < TL.n[ti];
+    const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     float vsi = 0.0f;
-    for (unsigned int jt = 0; jt * 32u < nB; ++jt) {
-      const float rj0 = sort_r[oB + jt * 32u] + g.offBp;
-      if (rj0 - maxri > fmaxf(maxHi, HmB) + slack) break;
-      const unsigned int jj = jt * 32u + lane;
-      const bool vj = jj < nB;
-      const ForceI J = load_force(vj, vj ? sB + sort_i[oB + jj] : 0u, shB, pos4, cen4, vel4, ghost4, g.invL, g.e);
-      const TileBox bj = tile_box(vj, J.p);
-      const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
-      if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
-      force_put(S, lane, J);
-      __syncwarp();
-      for (int s = 0; s < 32; ++s) {
-        force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
+    for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
+      unsigned int jt;
+      bool stop;
+      unsigned int mask = scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, true, &jt, &stop);
+      if (stop) break;
+      while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const unsigned int tj = __shfl_sync(0xffffffffu, jt, k);
+        const bool vj = (unsigned int)lane < TL.n[tj];
+        const ForceI J = load_force(vj, TL.start[tj] + lane, P.shB, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
+        force_put(S, lane, J);
+        __syncwarp();
+        for (int s = 0; s < 32; ++s) {
+          force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, P.g, alpha, C);
+          __syncwarp();
+        }
+        flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
         __syncwarp();
       }
-      flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
-      __syncwarp();
     }
     flush_force(I.g, acc, vsi, facc, fvsig);
   }
@@ -561,7 +625,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_self, Tree T,
+__global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_self, Tree T, Tiles TL,
                                                             const BoxDesc* __restrict__ box,
                                                             const float4* __restrict__ pos4,
                                                             const float4* __restrict__ cen4,
@@ -580,47 +644,41 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
     const int item = task_item(Lq.s_toff, nself, t);
     const int A = Lq.self_a[item];
     const ItemGeom g = item_geom(T, box, A, 0);
-    const unsigned int n = T.count[A], s0 = T.start[A];
     const float4 cA = T.cen[A];
     const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-    const float slack = g.e * 1.52587890625e-05f;
-    const int nt = (int)((n + 31) >> 5);
-    const int it = (int)(t - Lq.s_toff[item]);
-    {
-      const unsigned int ii = (unsigned int)it * 32u + lane;
-      const bool vi = ii < n;
-      const ForceI I = load_force(vi, s0 + ii, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
-      const TileBox bi = tile_box(vi, I.p);
-      const float maxHi = warp_max(vi ? 1.0f / I.invH : 0.0f);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      float vsi = 0.0f;
-      for (int jt = it; jt < nt; ++jt) {
-        const unsigned int jj = (unsigned int)jt * 32u + lane;
-        const bool vj = jj < n;
-        const ForceI J = load_force(vj, s0 + jj, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
-        if (jt != it) {
-          const TileBox bj = tile_box(vj, J.p);
-          const float maxHj = warp_max(vj ? 1.0f / J.invH : 0.0f);
-          if (tile_gap(bi, bj) > fmaxf(maxHi, maxHj) + slack) continue;
-        }
-        force_put(S, lane, J);
-        __syncwarp();
-        if (jt == it) {
-          for (int s = 1; s <= 16; ++s) {
-            if (s < 16 || lane < 16) force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
-            __syncwarp();
-          }
-        } else {
-          for (int s = 0; s < 32; ++s) {
-            force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
-            __syncwarp();
-          }
-        }
-        flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
-        __syncwarp();
+    const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+    const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
+    const unsigned int ti = t0 + (t - Lq.s_toff[item]);
+    const Box3 bi = tile_box3(TL, T, ti, sh);
+    const float Hi = TL.lo[ti].w * g.invL;
+    const bool vi = (unsigned int)lane < TL.n[ti];
+    const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float vsi = 0.0f;
+    for (unsigned int tj = ti; tj < t0 + nt; ++tj) {
+      if (tj != ti) {
+        const Box3 bj = tile_box3(TL, T, tj, sh);
+        if (box_gap(bi, bj) > fmaxf(Hi, TL.lo[tj].w * g.invL) + slack) continue;
       }
-      flush_force(I.g, acc, vsi, facc, fvsig);
+      const bool vj = (unsigned int)lane < TL.n[tj];
+      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      force_put(S, lane, J);
+      __syncwarp();
+      if (tj == ti) {
+        for (int s = 1; s <= 16; ++s) {
+          if (s < 16 || lane < 16) force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
+          __syncwarp();
+        }
+      } else {
+        for (int s = 0; s < 32; ++s) {
+          force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
+          __syncwarp();
+        }
+      }
+      flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+      __syncwarp();
     }
+    flush_force(I.g, acc, vsi, facc, fvsig);
   }
   commit_counters<COUNT>(C, pc, 3);
 }
@@ -706,11 +764,11 @@ __global__ void k_mark_active_cells(long long N, const unsigned char* __restrict
   }
 }
 
-// i-tiles (32 particles) per interaction: the prefix of these numbers the tasks
+// clusters of the i cell per interaction: the prefix of these numbers the tasks
 __global__ void k_task_tiles(Lists Lq, Tree T, int npair, int nself) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npair + nself; i += gridDim.x * blockDim.x) {
-    if (i < npair) Lq.p_toff[i] = (T.count[Lq.pair_a[i]] + 31u) >> 5;
-    else Lq.s_toff[i - npair] = (T.count[Lq.self_a[i - npair]] + 31u) >> 5;
+    if (i < npair) Lq.p_toff[i] = T.ntile[Lq.pair_a[i]];
+    else Lq.s_toff[i - npair] = T.ntile[Lq.self_a[i - npair]];
   }
 }
 
@@ -861,11 +919,11 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
 void launch_density_pair(Engine& E) {
   const int grid = E.nsm * 8;
   if (E.count_pairs)
-    k_density_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_density_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                          E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
                                                          E.dacc.p, E.dcnt.p, E.pc.p);
   else
-    k_density_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_density_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                           E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
                                                           E.dacc.p, E.dcnt.p, E.pc.p);
   count_launch();
@@ -874,10 +932,10 @@ void launch_density_pair(Engine& E) {
 void launch_density_self(Engine& E) {
   const int grid = E.nsm * 8;
   if (E.count_pairs)
-    k_density_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_density_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                          E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
   else
-    k_density_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_density_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                           E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
   count_launch();
 }
@@ -886,11 +944,11 @@ void launch_force_pair(Engine& E) {
   const int grid = E.nsm * 8;
   const float alpha = E.prm.alpha_visc;
   if (E.count_pairs)
-    k_force_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_force_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                        E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
                                                        E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
   else
-    k_force_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_force_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                         E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
                                                         E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
   count_launch();
@@ -900,11 +958,11 @@ void launch_force_self(Engine& E) {
   const int grid = E.nsm * 8;
   const float alpha = E.prm.alpha_visc;
   if (E.count_pairs)
-    k_force_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_force_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                        E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
                                                        E.fvsig.p, E.pc.p);
   else
-    k_force_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.box.p, E.pos4.p, E.cen4.p,
+    k_force_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
                                                         E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
                                                         E.fvsig.p, E.pc.p);
   count_launch();

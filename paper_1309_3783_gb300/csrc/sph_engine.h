@@ -38,6 +38,10 @@ struct DBuf {
     n = 0;
   }
   size_t bytes() const { return n * sizeof(T); }
+  void swap(DBuf& o) {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+  }
   ~DBuf() { release(); }
 };
 
@@ -124,6 +128,16 @@ class Engine {
   DBuf<unsigned int> leaf_of;
   DBuf<int> top_at;
   DBuf<unsigned char> act;        // still iterating h (sorted order)
+  DBuf<float> Hs_tmp;
+  DBuf<float4> vel4_tmp;
+  DBuf<unsigned int> lsrc, tflag, texcl, tile_of;
+
+  // clusters (capacity N)
+  DBuf<unsigned int> tl_start, tl_n, tl_leaf;
+  DBuf<float4> tl_lo, tl_hi;
+  DBuf<unsigned char> tl_active;
+  Tiles TL{};
+  long long n_tiles = 0;
 
   // cell tree
   int cap_nodes = 0;
@@ -134,6 +148,7 @@ class Engine {
   DBuf<double> t_hlim;
   DBuf<float4> t_cen;
   DBuf<unsigned char> t_active;
+  DBuf<unsigned int> t_tile0, t_ntile;
   Tree T{};
 
   // interaction lists

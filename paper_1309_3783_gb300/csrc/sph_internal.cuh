@@ -7,7 +7,7 @@
 #define SPH_MAX_DEPTH 20          // bits per dimension of the Morton code
 #define SPH_WARPS_PER_CTA 4
 #define SPH_THREADS (32 * SPH_WARPS_PER_CTA)
-#define SORT_SMALL 2048u       // cells up to this size are sorted in shared memory
+#define SORT_SMALL 2048u       // cells with up to this many clusters are sorted in shared memory
 
 // Error bits set by kernels in a box's status word.
 enum : unsigned int {
@@ -173,7 +173,21 @@ struct Tree {
   unsigned int* axes;       // bit a: a sorted list along axis a is needed
   unsigned int* sortbase;   // offset of the first sorted list of this cell
   unsigned char* active;    // 1 when a particle inside still iterates h
+  unsigned int* tile0;      // first cluster of the cell (clusters of a cell are contiguous)
+  unsigned int* ntile;      // clusters of the cell
   int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier
+};
+
+// Clusters: runs of at most 32 consecutive particles of one leaf (particles of a
+// leaf are ordered by H class, then Morton order), the unit the interaction
+// kernels load into a warp.  Their boxes and largest H drive the culling.
+struct Tiles {
+  unsigned int* start;      // first particle (sorted order)
+  unsigned int* n;          // particles in the cluster (1..32)
+  unsigned int* leaf;       // leaf cell
+  float4* lo;               // box minimum relative to the leaf centre (units of L); w: max H (physical)
+  float4* hi;               // box maximum relative to the leaf centre (units of L)
+  unsigned char* active;    // 1 when a particle inside still iterates h
 };
 
 // Interaction lists.

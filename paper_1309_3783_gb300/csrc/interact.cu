@@ -3,14 +3,12 @@
 // per-field output gathers.
 //
 // Pair-interactions follow the sorted cell-pair interaction of Section II-C
-// (Fig. 3) with warp granularity: a warp takes a pair (A, B); particles of both
-// cells are read in their sorted order along the axis joining the cell
-// centres; the warp walks i-tiles of A from the interface outwards and, for
-// each, j-tiles of B from the interface outwards, and stops as soon as the
-// projected gap exceeds every support radius that could still bridge it.
-// Inside a 32 x 32 tile every lane evaluates one (i, j) pair per step on a
-// rotating diagonal, so both sides of a pair are updated once without
-// conflicts (the pair is found once and used symmetrically, Section II-D).
+// (Fig. 3) at warp granularity: particles are grouped into clusters of at most
+// 32; a warp takes one cluster of cell A and walks the clusters of cell B in
+// their sorted order along the axis joining the cell centres, stopping once the
+// projected gap exceeds every support radius that could still bridge it, and
+// culling clusters whose boxes are out of reach.  Each in-reach particle pair
+// is found once and updates both sides (Section II-D: symmetric interactions).
 #include "sph_engine.h"
 
 #include <cfloat>
@@ -137,55 +135,6 @@ struct Counters {
   unsigned int cand = 0, pairs = 0, sides = 0, rechecks = 0;
 };
 
-// one diagonal step of a density tile: lane pairs i with shared entry k
-template <bool COUNT>
-__device__ __forceinline__ void dens_step(const DensI& I, DensShared& S, int k, float4& acc, unsigned int& cnt,
-                                          const unsigned int* perm, const double* x, const ItemGeom& g,
-                                          Counters& C) {
-  const float4 J = S.p[k];
-  const float4 Ja = S.a[k];
-  if (!(I.valid && Ja.w > 0.0f)) return;
-  const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
-  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  unsigned int rc = 0;
-  const bool pI = decide(r2, I.H2, I.band, I.g, S.g[k], I.Hphys, perm, x, g, rc);
-  const bool pJ = decide(r2, Ja.x, Ja.y, I.g, S.g[k], Ja.w, perm, x, g, rc);
-  if (COUNT) {
-    // useful work: sides that accumulate into a particle still iterating h
-    const bool ui = pI && I.act, uj = pJ && S.act[k];
-    C.cand++;
-    C.rechecks += rc;
-    C.pairs += (ui || uj) ? 1u : 0u;
-    C.sides += (ui ? 1u : 0u) + (uj ? 1u : 0u);
-  }
-  if (!(pI || pJ)) return;
-  const float r = sqrtf(r2);
-  if (pI && I.act) {
-    float w, dw;
-    const float q = r * I.invH;
-    spline_w_dw(q, w, dw);
-    const float gg = q * dw;                 // q w'(q) = r dW/dr in units of W
-    acc.x = fmaf(Ja.z, w, acc.x);
-    acc.y = fmaf(Ja.z, gg, acc.y);
-    acc.z += w;
-    acc.w += gg;
-    cnt++;
-  }
-  if (pJ && S.act[k]) {
-    float w, dw;
-    const float q = r * J.w;
-    spline_w_dw(q, w, dw);
-    const float gg = q * dw;
-    float4 a = S.acc[k];
-    a.x = fmaf(I.m, w, a.x);
-    a.y = fmaf(I.m, gg, a.y);
-    a.z += w;
-    a.w += gg;
-    S.acc[k] = a;
-    S.cnt[k]++;
-  }
-}
-
 __device__ __forceinline__ void flush_dens(int gidx, float4 acc, unsigned int cnt, float4* dacc, unsigned int* dcnt) {
   if (gidx < 0 || cnt == 0) return;
   atomicAdd(&dacc[gidx], acc);
@@ -214,6 +163,213 @@ __device__ __forceinline__ void commit_counters(const Counters& C, unsigned long
     atomicAdd(&pc[10], r);
   }
 }
+
+
+// =========================================================================== force
+struct ForceI {
+  float3 p;
+  float invH, H2, band, Hphys, m;
+  float3 v;
+  float rho, F, c, K4;
+  int g;
+  bool valid;
+};
+
+__device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
+                                             const float4* cen4, const float4* vel4, const float4* ghost4,
+                                             float invL, float e) {
+  ForceI r;
+  r.valid = valid;
+  if (valid) {
+    const float4 p = pos4[gidx];
+    const float4 c = cen4[gidx];
+    const float4 vv = vel4[gidx];
+    const float4 gh = ghost4[gidx];
+    // the cell offsets (c + shift) are exact dyadic values: add them first, round once
+    r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
+    const float H = p.w * invL;
+    r.invH = 1.0f / H;
+    r.H2 = H * H;
+    r.band = BAND_REL * H * (e + H);
+    r.Hphys = p.w;
+    r.m = c.w;
+    r.v = make_float3(vv.x, vv.y, vv.z);
+    r.rho = gh.x;
+    r.F = gh.y;
+    r.c = gh.z;
+    const float ih = 1.0f / p.w;
+    r.K4 = SPH_KNORM * (ih * ih) * (ih * ih);
+    r.g = (int)gidx;
+  } else {
+    r.p = make_float3(1e30f, 1e30f, 1e30f);
+    r.invH = 0.f;
+    r.H2 = -1.f;
+    r.band = 0.f;
+    r.Hphys = 0.f;
+    r.m = 0.f;
+    r.v = make_float3(0.f, 0.f, 0.f);
+    r.rho = 1.f;
+    r.F = 0.f;
+    r.c = 0.f;
+    r.K4 = 0.f;
+    r.g = -1;
+  }
+  return r;
+}
+
+struct ForceShared {
+  float4 p[32];    // position, 1/H
+  float4 a[32];    // H^2, band, m, H (physical)
+  float4 v[32];    // velocity, rho
+  float4 f[32];    // f P / rho^2, c, K/H^4, -
+  float4 acc[32];  // a (3), du/dt
+  float vs[32];
+  int g[32];
+};
+
+__device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
+  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.invH);
+  S.a[lane] = make_float4(j.H2, j.band, j.m, j.Hphys);
+  S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
+  S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
+  S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.vs[lane] = 0.f;
+  S.g[lane] = j.g;
+}
+
+__device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, float4* facc, float* fvsig) {
+  if (gidx < 0 || !(vs > 0.0f)) return;   // vsig > 0 for every pair that contributed
+  atomicAdd(&facc[gidx], acc);
+  atomic_max_pos(&fvsig[gidx], vs);
+}
+
+// ------------------------------------------------------------- two-phase tiles
+// The 32 partners of a cluster pair sit in shared memory.  Phase 1: every lane
+// tests its particle i against all 32 partners (broadcast reads) and keeps two
+// bitmasks, r < H_i and r < H_j, decided exactly.  Phase 2: every lane walks
+// only its set bits; its own side accumulates in registers, the partner side in
+// shared memory with atomics (lanes may share a partner).  Invalid lanes sit at
+// 1e30 with H^2 = -1, so they never pass a test.
+template <bool COUNT>
+__device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigned int allow, unsigned int jvalid,
+                                          unsigned int jact, float4& acc, unsigned int& cnt,
+                                          const unsigned int* perm, const double* x, const ItemGeom& g,
+                                          Counters& C) {
+  unsigned int mI = 0, mJ = 0, rc = 0;
+#pragma unroll 8
+  for (int s = 0; s < 32; ++s) {
+    const float4 J = S.p[s];
+    const float4 Ja = S.a[s];
+    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    mI |= (unsigned int)decide(r2, I.H2, I.band, I.g, S.g[s], I.Hphys, perm, x, g, rc) << s;
+    mJ |= (unsigned int)decide(r2, Ja.x, Ja.y, I.g, S.g[s], Ja.w, perm, x, g, rc) << s;
+  }
+  mI &= allow;
+  mJ &= allow;
+  const unsigned int ui = I.act ? mI : 0u, uj = mJ & jact;
+  if (COUNT) {
+    C.cand += I.valid ? __popc(allow & jvalid) : 0u;
+    C.rechecks += rc;
+    C.pairs += __popc(ui | uj);
+    C.sides += __popc(ui) + __popc(uj);
+  }
+  unsigned int m = ui | uj;
+  while (m) {
+    const int sj = __ffs(m) - 1;
+    m &= m - 1;
+    const float4 J = S.p[sj];
+    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+    const float r = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+    if ((ui >> sj) & 1u) {
+      float w, dw;
+      const float q = r * I.invH;
+      spline_w_dw(q, w, dw);
+      const float gg = q * dw;                 // q w'(q) = r dW/dr in units of W
+      acc.x = fmaf(S.a[sj].z, w, acc.x);
+      acc.y = fmaf(S.a[sj].z, gg, acc.y);
+      acc.z += w;
+      acc.w += gg;
+      cnt++;
+    }
+    if ((uj >> sj) & 1u) {
+      float w, dw;
+      const float q = r * J.w;
+      spline_w_dw(q, w, dw);
+      const float gg = q * dw;
+      atomicAdd(&S.acc[sj].x, I.m * w);
+      atomicAdd(&S.acc[sj].y, I.m * gg);
+      atomicAdd(&S.acc[sj].z, w);
+      atomicAdd(&S.acc[sj].w, gg);
+      atomicAdd(&S.cnt[sj], 1u);
+    }
+  }
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsigned int allow, unsigned int jvalid,
+                                           float4& acc, float& vsig_i, const unsigned int* perm, const double* x,
+                                           const ItemGeom& g, float alpha, Counters& C) {
+  unsigned int mI = 0, mJ = 0, rc = 0;
+#pragma unroll 8
+  for (int s = 0; s < 32; ++s) {
+    const float4 J = S.p[s];
+    const float4 Ja = S.a[s];
+    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    mI |= (unsigned int)decide(r2, I.H2, I.band, I.g, S.g[s], I.Hphys, perm, x, g, rc) << s;
+    mJ |= (unsigned int)decide(r2, Ja.x, Ja.y, I.g, S.g[s], Ja.w, perm, x, g, rc) << s;
+  }
+  mI &= allow;
+  mJ &= allow;
+  if (COUNT) {
+    C.cand += I.valid ? __popc(allow & jvalid) : 0u;
+    C.rechecks += rc;
+  }
+  unsigned int m = mI | mJ;
+  while (m) {
+    const int sj = __ffs(m) - 1;
+    m &= m - 1;
+    const float4 J = S.p[sj];
+    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (!(r2 > 0.0f)) continue;
+    if (COUNT) C.pairs++;
+    const float4 Ja = S.a[sj];
+    const float4 Jv = S.v[sj];
+    const float4 Jf = S.f[sj];
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    float w, dwi = 0.0f, dwj = 0.0f;
+    if ((mI >> sj) & 1u) spline_w_dw(r * I.invH, w, dwi);
+    if ((mJ >> sj) & 1u) spline_w_dw(r * J.w, w, dwj);
+    const float Wi = I.K4 * dwi, Wj = Jf.z * dwj;
+    const float vdx = fmaf(I.v.x - Jv.x, dx, fmaf(I.v.y - Jv.y, dy, (I.v.z - Jv.z) * dz));
+    const float wv = vdx * rinv;
+    const float mu = fminf(wv, 0.0f);
+    const float vsig = I.c + Jf.y - 3.0f * mu;
+    const float Pi = -alpha * vsig * mu / (I.rho + Jv.w);
+    const float Wbar = 0.5f * (Wi + Wj);
+    const float coef = fmaf(I.F, Wi, fmaf(Jf.x, Wj, Pi * Wbar)) * rinv;
+    const float hv = 0.5f * Pi * Wbar;
+    acc.x = fmaf(-Ja.z * coef, dx, acc.x);
+    acc.y = fmaf(-Ja.z * coef, dy, acc.y);
+    acc.z = fmaf(-Ja.z * coef, dz, acc.z);
+    acc.w = fmaf(Ja.z * fmaf(I.F, Wi, hv), wv, acc.w);
+    vsig_i = fmaxf(vsig_i, vsig);
+    const float mic = I.m * coef;
+    atomicAdd(&S.acc[sj].x, mic * dx);
+    atomicAdd(&S.acc[sj].y, mic * dy);
+    atomicAdd(&S.acc[sj].z, mic * dz);
+    atomicAdd(&S.acc[sj].w, I.m * fmaf(Jf.x, Wj, hv) * wv);
+    atomicMax(reinterpret_cast<unsigned int*>(&S.vs[sj]), __float_as_uint(vsig));
+  }
+}
+
+__device__ __forceinline__ unsigned int upper_mask(int lane) {
+  return lane == 31 ? 0u : (0xffffffffu << (lane + 1));
+}
+
 
 
 // ------------------------------------------------------------- cluster geometry
@@ -364,11 +520,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
         const bool vj = (unsigned int)lane < TL.n[tj];
         const DensI J = load_dens(vj, TL.start[tj] + lane, P.shB, pos4, cen4, act, P.g.invL, P.g.e);
         dens_put(S, lane, J);
+        const unsigned int jvalid = __ballot_sync(0xffffffffu, vj), jact = __ballot_sync(0xffffffffu, J.act);
         __syncwarp();
-        for (int s = 0; s < 32; ++s) {
-          dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, P.g, C);
-          __syncwarp();
-        }
+        dens_tile<COUNT>(I, S, 0xffffffffu, jvalid, jact, acc, cnt, perm, x, P.g, C);
+        __syncwarp();
         flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
         __syncwarp();
       }
@@ -419,19 +574,11 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
       const bool vj = (unsigned int)lane < TL.n[tj];
       const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
       dens_put(S, lane, J);
+      const unsigned int jvalid = __ballot_sync(0xffffffffu, vj), jact = __ballot_sync(0xffffffffu, J.act);
       __syncwarp();
-      if (tj == ti) {
-        // pairs inside one cluster: steps 1..16, the 16th on half the lanes
-        for (int s = 1; s <= 16; ++s) {
-          if (s < 16 || lane < 16) dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
-          __syncwarp();
-        }
-      } else {
-        for (int s = 0; s < 32; ++s) {
-          dens_step<COUNT>(I, S, (lane + s) & 31, acc, cnt, perm, x, g, C);
-          __syncwarp();
-        }
-      }
+      // inside one cluster each unordered pair once: partners above the lane
+      dens_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, jact, acc, cnt, perm, x, g, C);
+      __syncwarp();
       flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
       __syncwarp();
     }
@@ -439,134 +586,6 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
   }
   commit_counters<COUNT>(C, pc, 1);
 }
-
-// =========================================================================== force
-struct ForceI {
-  float3 p;
-  float invH, H2, band, Hphys, m;
-  float3 v;
-  float rho, F, c, K4;
-  int g;
-  bool valid;
-};
-
-__device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
-                                             const float4* cen4, const float4* vel4, const float4* ghost4,
-                                             float invL, float e) {
-  ForceI r;
-  r.valid = valid;
-  if (valid) {
-    const float4 p = pos4[gidx];
-    const float4 c = cen4[gidx];
-    const float4 vv = vel4[gidx];
-    const float4 gh = ghost4[gidx];
-    // the cell offsets (c + shift) are exact dyadic values: add them first, round once
-    r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
-    const float H = p.w * invL;
-    r.invH = 1.0f / H;
-    r.H2 = H * H;
-    r.band = BAND_REL * H * (e + H);
-    r.Hphys = p.w;
-    r.m = c.w;
-    r.v = make_float3(vv.x, vv.y, vv.z);
-    r.rho = gh.x;
-    r.F = gh.y;
-    r.c = gh.z;
-    const float ih = 1.0f / p.w;
-    r.K4 = SPH_KNORM * (ih * ih) * (ih * ih);
-    r.g = (int)gidx;
-  } else {
-    r.p = make_float3(1e30f, 1e30f, 1e30f);
-    r.invH = 0.f;
-    r.H2 = -1.f;
-    r.band = 0.f;
-    r.Hphys = 0.f;
-    r.m = 0.f;
-    r.v = make_float3(0.f, 0.f, 0.f);
-    r.rho = 1.f;
-    r.F = 0.f;
-    r.c = 0.f;
-    r.K4 = 0.f;
-    r.g = -1;
-  }
-  return r;
-}
-
-struct ForceShared {
-  float4 p[32];    // position, 1/H
-  float4 a[32];    // H^2, band, m, H (physical)
-  float4 v[32];    // velocity, rho
-  float4 f[32];    // f P / rho^2, c, K/H^4, -
-  float4 acc[32];  // a (3), du/dt
-  float vs[32];
-  int g[32];
-};
-
-__device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
-  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.invH);
-  S.a[lane] = make_float4(j.H2, j.band, j.m, j.Hphys);
-  S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
-  S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
-  S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-  S.vs[lane] = 0.f;
-  S.g[lane] = j.g;
-}
-
-template <bool COUNT>
-__device__ __forceinline__ void force_step(const ForceI& I, ForceShared& S, int k, float4& acc, float& vsig_i,
-                                           const unsigned int* perm, const double* x, const ItemGeom& g,
-                                           float alpha, Counters& C) {
-  const float4 J = S.p[k];
-  const float4 Ja = S.a[k];
-  if (!(I.valid && Ja.w > 0.0f)) return;
-  const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
-  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  unsigned int rc = 0;
-  const bool pI = decide(r2, I.H2, I.band, I.g, S.g[k], I.Hphys, perm, x, g, rc);
-  const bool pJ = decide(r2, Ja.x, Ja.y, I.g, S.g[k], Ja.w, perm, x, g, rc);
-  if (COUNT) {
-    C.cand++;
-    C.rechecks += rc;
-    C.pairs += ((pI || pJ) && r2 > 0.0f) ? 1u : 0u;
-  }
-  if (!(pI || pJ) || !(r2 > 0.0f)) return;
-  const float4 Jv = S.v[k];
-  const float4 Jf = S.f[k];
-  const float rinv = rsqrtf(r2);
-  const float r = r2 * rinv;
-  float w, dwi = 0.0f, dwj = 0.0f;
-  if (pI) spline_w_dw(r * I.invH, w, dwi);
-  if (pJ) spline_w_dw(r * J.w, w, dwj);
-  const float Wi = I.K4 * dwi, Wj = Jf.z * dwj;
-  const float vdx = fmaf(I.v.x - Jv.x, dx, fmaf(I.v.y - Jv.y, dy, (I.v.z - Jv.z) * dz));
-  const float wv = vdx * rinv;
-  const float mu = fminf(wv, 0.0f);
-  const float vsig = I.c + Jf.y - 3.0f * mu;
-  const float Pi = -alpha * vsig * mu / (I.rho + Jv.w);
-  const float Wbar = 0.5f * (Wi + Wj);
-  const float coef = fmaf(I.F, Wi, fmaf(Jf.x, Wj, Pi * Wbar)) * rinv;
-  const float hv = 0.5f * Pi * Wbar;
-  acc.x = fmaf(-Ja.z * coef, dx, acc.x);
-  acc.y = fmaf(-Ja.z * coef, dy, acc.y);
-  acc.z = fmaf(-Ja.z * coef, dz, acc.z);
-  acc.w = fmaf(Ja.z * fmaf(I.F, Wi, hv), wv, acc.w);
-  vsig_i = fmaxf(vsig_i, vsig);
-  float4 a = S.acc[k];
-  const float mic = I.m * coef;
-  a.x = fmaf(mic, dx, a.x);
-  a.y = fmaf(mic, dy, a.y);
-  a.z = fmaf(mic, dz, a.z);
-  a.w = fmaf(I.m * fmaf(Jf.x, Wj, hv), wv, a.w);
-  S.acc[k] = a;
-  S.vs[k] = fmaxf(S.vs[k], vsig);
-}
-
-__device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, float4* facc, float* fvsig) {
-  if (gidx < 0 || !(vs > 0.0f)) return;   // vsig > 0 for every pair that contributed
-  atomicAdd(&facc[gidx], acc);
-  atomic_max_pos(&fvsig[gidx], vs);
-}
-
 
 template <bool COUNT>
 __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pair, Tree T, Tiles TL,
@@ -610,11 +629,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
         const bool vj = (unsigned int)lane < TL.n[tj];
         const ForceI J = load_force(vj, TL.start[tj] + lane, P.shB, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
         force_put(S, lane, J);
+        const unsigned int jvalid = __ballot_sync(0xffffffffu, vj);
         __syncwarp();
-        for (int s = 0; s < 32; ++s) {
-          force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, P.g, alpha, C);
-          __syncwarp();
-        }
+        force_tile<COUNT>(I, S, 0xffffffffu, jvalid, acc, vsi, perm, x, P.g, alpha, C);
+        __syncwarp();
         flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
         __syncwarp();
       }
@@ -663,18 +681,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
       const bool vj = (unsigned int)lane < TL.n[tj];
       const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
       force_put(S, lane, J);
+      const unsigned int jvalid = __ballot_sync(0xffffffffu, vj);
       __syncwarp();
-      if (tj == ti) {
-        for (int s = 1; s <= 16; ++s) {
-          if (s < 16 || lane < 16) force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
-          __syncwarp();
-        }
-      } else {
-        for (int s = 0; s < 32; ++s) {
-          force_step<COUNT>(I, S, (lane + s) & 31, acc, vsi, perm, x, g, alpha, C);
-          __syncwarp();
-        }
-      }
+      force_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, acc, vsi, perm, x, g, alpha, C);
+      __syncwarp();
       flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
       __syncwarp();
     }

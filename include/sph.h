@@ -80,6 +80,10 @@ typedef struct sph_params {
     int32_t leaf_max;     /* split a cell when it holds more particles (400)         */
     float split_frac;     /* ... and more than this fraction has H < edge/2 (0.875)  */
     int32_t max_depth;    /* deepest cell level, <= 20 (20)                          */
+    float split_headroom; /* pairs split, and the top grid is chosen, only when
+                             H (1 + split_headroom) clears the limit, so that h
+                             may grow by that much before the interactions must be
+                             rebuilt; 0 = the paper's rule exactly (0.1)        */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;

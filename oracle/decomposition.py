@@ -49,14 +49,14 @@ def positive(db) -> bool:
 AXES = [db for db in product((-1, 0, 1), repeat=3) if positive(db)]
 
 
-def top_level(H_max: float, L: float, periodic: bool, max_depth: int) -> int:
-    """Finest level whose cell edge exceeds H_max by the margin; raises if none."""
+def top_level(H_max: float, L: float, periodic: bool, max_depth: int, headroom: float = 0.0) -> int:
+    """Finest level whose cell edge exceeds H_max (1 + headroom) by the margin; raises if none."""
     k_min = 2 if periodic else 0
     dl = margin(L)
     if not H_max < L * 2.0 ** -k_min - dl:
         raise ValueError("H_max too large for the box")
     k = k_min
-    while k + 1 <= max_depth and H_max < L * 2.0 ** -(k + 1) - dl:
+    while k + 1 <= max_depth and H_max * (1.0 + headroom) < L * 2.0 ** -(k + 1) - dl:
         k += 1
     return k
 
@@ -84,12 +84,16 @@ def _orient(d, ca, cb, db):
     return (d, cb, ca, tuple(-c for c in db))
 
 
-def decompose(x, H, L, periodic, leaf_max=400, split_frac=0.875, max_depth=20) -> Decomposition:
+def decompose(x, H, L, periodic, leaf_max=400, split_frac=0.875, max_depth=20, headroom=0.0) -> Decomposition:
+    """headroom > 0 (an implementation option, not the paper's): pairs split and the
+    top level is chosen only when H (1 + headroom) clears the limit; 0 is the rule
+    of the paper."""
     x = np.asarray(x, dtype=np.float64)
     H = np.asarray(H, dtype=np.float64)
     n = x.shape[0]
     dl = margin(L)
-    k = top_level(float(H.max()), L, periodic, max_depth)
+    headroom = float(np.float32(headroom))    # the library holds it in FP32
+    k = top_level(float(H.max()), L, periodic, max_depth, headroom)
     frac = float(np.float32(split_frac))
     D = Decomposition(k=k, max_depth=max_depth)
     D.hlim = np.full(n, L * 2.0 ** -k - dl)
@@ -155,7 +159,7 @@ def decompose(x, H, L, periodic, leaf_max=400, split_frac=0.875, max_depth=20) -
         ka, kb = (d, ca), (d, cb)
         half = L * 2.0 ** -(d + 1) - dl
         hmax = max(H[D.cells[ka]].max(), H[D.cells[kb]].max())
-        if ka in D.split and kb in D.split and hmax < half:
+        if ka in D.split and kb in D.split and hmax * (1.0 + headroom) < half:
             for p in D.cells[ka]:
                 D.hlim[p] = min(D.hlim[p], half)
             for p in D.cells[kb]:

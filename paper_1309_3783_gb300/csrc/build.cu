@@ -467,7 +467,7 @@ __global__ void k_items_top(int ntop, Tree T, const BoxDesc* __restrict__ box, c
 // adjacent child pairs across the interface iff every particle of both cells has
 // H < edge/2 - margin.  Everything else is final.
 __global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, Lists Lq, int cap_queue,
-                               int cap_self, int cap_pair, unsigned int* __restrict__ err_all) {
+                               int cap_self, int cap_pair, unsigned int* __restrict__ err_all, float headroom) {
   const int out = in ^ 1;
   const int n = min(Lq.counts[2 + in], cap_queue);
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
@@ -498,7 +498,9 @@ __global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, 
     const int d = T.level[A];
     const BoxDesc bd = box[T.box[A]];
     const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
-    const double hm = (double)fmaxf(T.hmax[A], T.hmax[B]);
+    // split the pair when every H, grown by the headroom, stays below half the edge
+    // (the interactions stay valid while H < half: that is the limit recorded)
+    const double hm = (double)fmaxf(T.hmax[A], T.hmax[B]) * (1.0 + (double)headroom);
     if (!(T.split[A] && T.split[B] && hm < half)) {
       const int s = atomicAdd(&Lq.counts[1], 1);
       if (s < cap_pair) {

@@ -25,7 +25,7 @@ __global__ void k_frontier_next(Tree, int);
 __global__ void k_frontier_init(Tree, int);
 __global__ void k_items_top(int, Tree, const BoxDesc*, const unsigned long long*, const int*, int, int, Lists, int,
                             unsigned int*);
-__global__ void k_items_expand(int, Tree, const BoxDesc*, Lists, int, int, int, unsigned int*);
+__global__ void k_items_expand(int, Tree, const BoxDesc*, Lists, int, int, int, unsigned int*, float);
 __global__ void k_leaves(Tree, int, unsigned int*);
 __global__ void k_particle_limits(long long, Tree, const unsigned int*, float*);
 __global__ void k_shift(long long, int, const unsigned long long*, const unsigned int*, const unsigned int*, Tree,
@@ -395,8 +395,10 @@ sph_status Engine::build_once(bool* retry) {
     const int k0 = d.periodic ? 2 : 0;
     if (!((double)d.Hmax < std::ldexp(d.L, -k0) - d.margin))
       return fail(SPH_E_H_TOO_LARGE, "box " + std::to_string(b) + ": support radius too large for the box (periodic boxes need H < L/4)");
+    // finest level whose edge clears H_max with the headroom (at least the coarsest allowed)
+    const double hr = 1.0 + (double)prm.split_headroom;
     int k = k0;
-    while (k + 1 <= dc && (double)d.Hmax < std::ldexp(d.L, -(k + 1)) - d.margin) ++k;
+    while (k + 1 <= dc && (double)d.Hmax * hr < std::ldexp(d.L, -(k + 1)) - d.margin) ++k;
     d.k = k;
     kmin = std::min(kmin, k);
     kmax = std::max(kmax, k);
@@ -457,7 +459,8 @@ sph_status Engine::build_once(bool* retry) {
   for (int r = 0; r < rounds; ++r) {
     const int in = r & 1;
     CK(cudaMemsetAsync(l_counts.p + 2 + (in ^ 1), 0, sizeof(int), st));
-    k_items_expand<<<nsm * 8, 256, 0, st>>>(in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p); count_launch();
+    k_items_expand<<<nsm * 8, 256, 0, st>>>(in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p,
+                                            prm.split_headroom); count_launch();
   }
   prof_end(PH_LISTS, ev, l0);
   ev = prof_begin(PH_SHIFT, &l0);
@@ -984,6 +987,7 @@ void sph_params_default(sph_params* p) {
   p->leaf_max = 400;
   p->split_frac = 0.875f;
   p->max_depth = 20;
+  p->split_headroom = 0.1f;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
@@ -993,7 +997,8 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
   sph_params_default(&p);
   if (params) p = *params;
   if (!(p.gamma_kernel > 0) || !(p.n_ngb > 0) || !(p.gamma_gas > 1) || p.h_max_iter < 1 || p.leaf_max < 1 ||
-      !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0))
+      !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0) ||
+      !(p.split_headroom >= 0 && p.split_headroom < 1))
     return SPH_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;

@@ -114,8 +114,8 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
 }
 
 struct DensShared {
-  float4 p[32];     // position, 1/H (units of L)
-  float4 a[32];     // H^2, band, m, H (physical)
+  float4 p[32];     // position, H^2 (units of L; H^2 = -1 marks an empty slot)
+  float4 a[32];     // 1/H, band, m, H (physical)
   float4 acc[32];   // sum m w, sum m q w', sum w, sum q w'
   unsigned int cnt[32];
   int g[32];
@@ -123,8 +123,8 @@ struct DensShared {
 };
 
 __device__ __forceinline__ void dens_put(DensShared& S, int lane, const DensI& j) {
-  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.invH);
-  S.a[lane] = make_float4(j.H2, j.band, j.m, j.Hphys);
+  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.H2);
+  S.a[lane] = make_float4(j.invH, j.band, j.m, j.Hphys);
   S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   S.cnt[lane] = 0;
   S.g[lane] = j.g;
@@ -218,8 +218,8 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
 }
 
 struct ForceShared {
-  float4 p[32];    // position, 1/H
-  float4 a[32];    // H^2, band, m, H (physical)
+  float4 p[32];    // position, H^2
+  float4 a[32];    // 1/H, band, m, H (physical)
   float4 v[32];    // velocity, rho
   float4 f[32];    // f P / rho^2, c, K/H^4, -
   float4 acc[32];  // a (3), du/dt
@@ -228,8 +228,8 @@ struct ForceShared {
 };
 
 __device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
-  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.invH);
-  S.a[lane] = make_float4(j.H2, j.band, j.m, j.Hphys);
+  S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.H2);
+  S.a[lane] = make_float4(j.invH, j.band, j.m, j.Hphys);
   S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
   S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
   S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -250,23 +250,56 @@ __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, floa
 // only its set bits; its own side accumulates in registers, the partner side in
 // shared memory with atomics (lanes may share a partner).  Invalid lanes sit at
 // 1e30 with H^2 = -1, so they never pass a test.
-template <bool COUNT>
-__device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigned int allow, unsigned int jvalid,
-                                          unsigned int jact, float4& acc, unsigned int& cnt,
-                                          const unsigned int* perm, const double* x, const ItemGeom& g,
-                                          Counters& C) {
-  unsigned int mI = 0, mJ = 0, rc = 0;
+
+// Phase 1 of a cluster pair: exact bitmasks of r < H_i (mI) and r < H_j (mJ) over
+// the 32 staged partners.  The FP32 test decides outside a guard band around
+// H^2; bandJ bounds every partner's band; the few uncertain bits are decided in
+// FP64 afterwards.
+template <class SH>
+__device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iband, int ig, float iHphys,
+                                           const SH& S, float bandJ, unsigned int allow, const unsigned int* perm,
+                                           const double* x, const ItemGeom& g, unsigned int& mI, unsigned int& mJ,
+                                           unsigned int& rc) {
+  unsigned int uI = 0, uJ = 0;
+  mI = 0;
+  mJ = 0;
 #pragma unroll 8
   for (int s = 0; s < 32; ++s) {
     const float4 J = S.p[s];
-    const float4 Ja = S.a[s];
-    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+    const float dx = ip.x - J.x, dy = ip.y - J.y, dz = ip.z - J.z;
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    mI |= (unsigned int)decide(r2, I.H2, I.band, I.g, S.g[s], I.Hphys, perm, x, g, rc) << s;
-    mJ |= (unsigned int)decide(r2, Ja.x, Ja.y, I.g, S.g[s], Ja.w, perm, x, g, rc) << s;
+    const float di = r2 - iH2, dj = r2 - J.w;
+    mI |= (di < -iband ? 1u : 0u) << s;
+    uI |= (fabsf(di) <= iband ? 1u : 0u) << s;
+    mJ |= (dj < -bandJ ? 1u : 0u) << s;
+    uJ |= (fabsf(dj) <= bandJ ? 1u : 0u) << s;
+  }
+  uI &= allow;
+  uJ &= allow;
+  unsigned int u = uI | uJ;
+  while (u) {
+    const int s = __ffs(u) - 1;
+    u &= u - 1;
+    if ((uI >> s) & 1u) {
+      ++rc;
+      if (exact_less(ig, S.g[s], iHphys, perm, x, g.L, g.halfL, g.periodic)) mI |= 1u << s;
+    }
+    if ((uJ >> s) & 1u) {
+      ++rc;
+      if (exact_less(ig, S.g[s], S.a[s].w, perm, x, g.L, g.halfL, g.periodic)) mJ |= 1u << s;
+    }
   }
   mI &= allow;
   mJ &= allow;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigned int allow, unsigned int jvalid,
+                                          unsigned int jact, float bandJ, float4& acc, unsigned int& cnt,
+                                          const unsigned int* perm, const double* x, const ItemGeom& g,
+                                          Counters& C) {
+  unsigned int mI, mJ, rc = 0;
+  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, perm, x, g, mI, mJ, rc);
   const unsigned int ui = I.act ? mI : 0u, uj = mJ & jact;
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid) : 0u;
@@ -294,7 +327,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
     }
     if ((uj >> sj) & 1u) {
       float w, dw;
-      const float q = r * J.w;
+      const float q = r * S.a[sj].x;
       spline_w_dw(q, w, dw);
       const float gg = q * dw;
       atomicAdd(&S.acc[sj].x, I.m * w);
@@ -308,20 +341,10 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
 
 template <bool COUNT>
 __device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsigned int allow, unsigned int jvalid,
-                                           float4& acc, float& vsig_i, const unsigned int* perm, const double* x,
-                                           const ItemGeom& g, float alpha, Counters& C) {
-  unsigned int mI = 0, mJ = 0, rc = 0;
-#pragma unroll 8
-  for (int s = 0; s < 32; ++s) {
-    const float4 J = S.p[s];
-    const float4 Ja = S.a[s];
-    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    mI |= (unsigned int)decide(r2, I.H2, I.band, I.g, S.g[s], I.Hphys, perm, x, g, rc) << s;
-    mJ |= (unsigned int)decide(r2, Ja.x, Ja.y, I.g, S.g[s], Ja.w, perm, x, g, rc) << s;
-  }
-  mI &= allow;
-  mJ &= allow;
+                                           float bandJ, float4& acc, float& vsig_i, const unsigned int* perm,
+                                           const double* x, const ItemGeom& g, float alpha, Counters& C) {
+  unsigned int mI, mJ, rc = 0;
+  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, perm, x, g, mI, mJ, rc);
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid) : 0u;
     C.rechecks += rc;
@@ -342,7 +365,7 @@ __device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsi
     const float r = r2 * rinv;
     float w, dwi = 0.0f, dwj = 0.0f;
     if ((mI >> sj) & 1u) spline_w_dw(r * I.invH, w, dwi);
-    if ((mJ >> sj) & 1u) spline_w_dw(r * J.w, w, dwj);
+    if ((mJ >> sj) & 1u) spline_w_dw(r * Ja.x, w, dwj);
     const float Wi = I.K4 * dwi, Wj = Jf.z * dwj;
     const float vdx = fmaf(I.v.x - Jv.x, dx, fmaf(I.v.y - Jv.y, dy, (I.v.z - Jv.z) * dz));
     const float wv = vdx * rinv;
@@ -521,8 +544,9 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
         const DensI J = load_dens(vj, TL.start[tj] + lane, P.shB, pos4, cen4, act, P.g.invL, P.g.e);
         dens_put(S, lane, J);
         const unsigned int jvalid = __ballot_sync(0xffffffffu, vj), jact = __ballot_sync(0xffffffffu, J.act);
+        const float bandJ = warp_max(J.band);
         __syncwarp();
-        dens_tile<COUNT>(I, S, 0xffffffffu, jvalid, jact, acc, cnt, perm, x, P.g, C);
+        dens_tile<COUNT>(I, S, 0xffffffffu, jvalid, jact, bandJ, acc, cnt, perm, x, P.g, C);
         __syncwarp();
         flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
         __syncwarp();
@@ -575,9 +599,11 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
       const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
       dens_put(S, lane, J);
       const unsigned int jvalid = __ballot_sync(0xffffffffu, vj), jact = __ballot_sync(0xffffffffu, J.act);
+      const float bandJ = warp_max(J.band);
       __syncwarp();
       // inside one cluster each unordered pair once: partners above the lane
-      dens_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, jact, acc, cnt, perm, x, g, C);
+      dens_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, jact, bandJ, acc, cnt, perm, x, g,
+                       C);
       __syncwarp();
       flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
       __syncwarp();
@@ -630,8 +656,9 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
         const ForceI J = load_force(vj, TL.start[tj] + lane, P.shB, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
         force_put(S, lane, J);
         const unsigned int jvalid = __ballot_sync(0xffffffffu, vj);
+        const float bandJ = warp_max(J.band);
         __syncwarp();
-        force_tile<COUNT>(I, S, 0xffffffffu, jvalid, acc, vsi, perm, x, P.g, alpha, C);
+        force_tile<COUNT>(I, S, 0xffffffffu, jvalid, bandJ, acc, vsi, perm, x, P.g, alpha, C);
         __syncwarp();
         flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
         __syncwarp();
@@ -682,8 +709,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
       const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
       force_put(S, lane, J);
       const unsigned int jvalid = __ballot_sync(0xffffffffu, vj);
+      const float bandJ = warp_max(J.band);
       __syncwarp();
-      force_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, acc, vsi, perm, x, g, alpha, C);
+      force_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, bandJ, acc, vsi, perm, x, g, alpha,
+                        C);
       __syncwarp();
       flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
       __syncwarp();

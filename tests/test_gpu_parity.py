@@ -178,10 +178,12 @@ def test_open_box_and_box_length(api, ctx):
 
 
 # ------------------------------------------------------------------ decomposition
-def test_decomposition_matches_the_paper_rules(api):
+@pytest.mark.parametrize("headroom", [0.0, 0.1])
+def test_decomposition_matches_the_paper_rules(api, headroom):
+    """Cells, selfs and pairs equal the oracle's; headroom 0 is the paper's rule."""
     box = inputs.plummer_box(n=8000, n_spheres=3, scale=0.04, seed=5)
     leaf = 32
-    c = make_ctx(api, leaf_max=leaf)
+    c = make_ctx(api, leaf_max=leaf, split_headroom=headroom)
     try:
         b = api.box_from(c, box)
         b.build()
@@ -190,7 +192,7 @@ def test_decomposition_matches_the_paper_rules(api):
         b.close()
     finally:
         api.sph_ctx_destroy(c)
-    D = dc.decompose(box.x, orc.support_radius(box.h), box.L, True, leaf_max=leaf)
+    D = dc.decompose(box.x, orc.support_radius(box.h), box.L, True, leaf_max=leaf, headroom=headroom)
     keys = [(int(l), tuple(int(v) for v in ijk)) for l, ijk in zip(cells["level"], cells["ijk"])]
     assert set(keys) == set(D.cells)
     for k, cnt, sp in zip(keys, cells["count"], cells["split"]):

@@ -190,6 +190,14 @@ sph_status sph_box_create(sph_ctx* ctx, int64_t n, double box_len, int periodic,
 sph_status sph_box_set(sph_box* box, const double* x, const float* v, const float* m,
                        const float* u, const float* h, int mem);
 
+/* Set one state field of the box from caller-order data (host or device, see
+ * `mem`): SPH_FIELD_A (n*3 floats) and SPH_FIELD_DUDT (n floats) restore the
+ * forces of the last step, so that sph_step with dt > 0 continues a run from a
+ * saved state (a checkpoint) without recomputing them; SPH_FIELD_H (n floats)
+ * replaces h.  Call after sph_box_set.  Errors: SPH_E_INVALID (other fields,
+ * n mismatch). */
+sph_status sph_box_set_field(sph_box* box, int field, const void* src, int64_t n, int mem);
+
 /* Turn exact pair counting on (1) or off (0) for the following passes; the
  * counts appear in sph_stats.  Counting adds atomics to the pair kernels. */
 sph_status sph_box_count_pairs(sph_box* box, int on);

@@ -62,6 +62,7 @@ void launch_save_acc(Engine& E);
 void launch_kick(Engine& E);
 void launch_drift(Engine& E);
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out);
+void launch_set_acc(Engine& E, long long off, long long n, int which, const float* src);
 
 #define CK_PLAIN(call)                                  \
   do {                                                  \
@@ -851,6 +852,31 @@ sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
   return SPH_OK;
 }
 
+sph_status Engine::set_field(int b, int field, const void* src, long long n, int mem) {
+  if (b < 0 || b >= nbox) return fail(SPH_E_INVALID, "box index out of range");
+  if (!src) return fail(SPH_E_INVALID, "null source");
+  const long long o = off[b], nb = spec[b].n;
+  if (n != nb) return fail(SPH_E_INVALID, "n does not match the box's particle count");
+  const cudaMemcpyKind kind = mem == SPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (field == SPH_FIELD_H) {
+    CK(cudaMemcpyAsync(h.p + o, src, nb * sizeof(float), kind, st));
+    built = have_density = have_ghost = have_force = false;
+    return SPH_OK;
+  }
+  if (field != SPH_FIELD_A && field != SPH_FIELD_DUDT) return fail(SPH_E_INVALID, "field cannot be set");
+  const int per = field == SPH_FIELD_A ? 3 : 1;
+  const float* dsrc = static_cast<const float*>(src);
+  if (mem != SPH_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(staging.p, src, per * nb * sizeof(float), cudaMemcpyHostToDevice, st));
+    dsrc = reinterpret_cast<const float*>(staging.p);
+  }
+  if (!have_acc) CK(cudaMemsetAsync(a_in.p + o, 0, nb * sizeof(float4), st));
+  launch_set_acc(*this, o, nb, field == SPH_FIELD_A ? 0 : 1, dsrc);
+  CK(cudaGetLastError());
+  have_acc = true;
+  return SPH_OK;
+}
+
 sph_status Engine::stats(int b, sph_stats* o) {
   std::memset(o, 0, sizeof(*o));
   o->n_particles = spec[b].n;
@@ -1074,6 +1100,11 @@ sph_status sph_box_set(sph_box* b, const double* x, const float* v, const float*
                        int mem) {
   BOX_PRE(b);
   return from_engine(b, b->eng->set_particles(0, x, v, m, u, h, mem));
+}
+
+sph_status sph_box_set_field(sph_box* b, int field, const void* src, int64_t n, int mem) {
+  BOX_PRE(b);
+  return from_engine(b, b->eng->set_field(0, field, src, n, mem));
 }
 
 sph_status sph_box_count_pairs(sph_box* b, int on) {

@@ -880,6 +880,26 @@ __global__ void k_save_acc(long long N, const unsigned int* __restrict__ perm, c
     a_in[perm[p]] = facc[p];
 }
 
+// caller-order (a, du/dt) into the saved accelerations: which = 0 sets a (n x 3), 1 sets du/dt
+__global__ void k_set_acc(long long off, long long n, int which, const float* __restrict__ src,
+                          float4* __restrict__ a_in) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    float4 a = a_in[off + q];
+    if (which == 0) {
+      a.x = src[3 * q];
+      a.y = src[3 * q + 1];
+      a.z = src[3 * q + 2];
+    } else {
+      a.w = src[q];
+    }
+    a_in[off + q] = a;
+  }
+}
+
+void launch_set_acc(Engine& E, long long off, long long n, int which, const float* src) {
+  k_set_acc<<<E.grid(n), 256, 0, E.st>>>(off, n, which, src, E.a_in.p); count_launch();
+}
+
 // half kick with the box's dt: v += a dt/2, u += du/dt dt/2 (u kept >= 0)
 __global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                        const float4* __restrict__ a_in, float* __restrict__ v, float* __restrict__ u) {

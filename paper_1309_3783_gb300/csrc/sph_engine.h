@@ -91,6 +91,7 @@ class Engine {
   sph_status tune(int* best_leaf_max);
   std::vector<std::pair<int, float>> tune_ms;   // (leaf_max, ms) of the last tune()
   sph_status get(int b, int field, void* dst, long long n, int mem);
+  sph_status set_field(int b, int field, const void* src, long long n, int mem);
   sph_status stats(int b, sph_stats* out);
   sph_status cells(int b, long long cap, int* level, int* ijk, int* count, int* split, long long* n_out);
   sph_status interactions(int b, long long cap, int* kind, int* a, int* bb, int* axis, long long* n_out);

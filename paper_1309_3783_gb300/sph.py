@@ -69,6 +69,7 @@ _SIGS = {
     "sph_box_create": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int, C.POINTER(_P)]),
     "sph_box_set": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int]),
     "sph_box_count_pairs": (C.c_int, [_P, C.c_int]),
+    "sph_box_set_field": (C.c_int, [_P, C.c_int, _P, C.c_int64, C.c_int]),
     "sph_box_destroy": (C.c_int, [_P]),
     "sph_build": (C.c_int, [_P]),
     "sph_density": (C.c_int, [_P]),
@@ -195,6 +196,13 @@ def sph_box_set(box, ctx, x, v, m, u, h, n: int):
     if len(mems) != 1:
         raise ValueError("all inputs must be on the host or all on the device")
     _check(load().sph_box_set(box, px, pv, pm, pu, ph, mems.pop()), ctx)
+
+
+def sph_box_set_field(box, ctx, field, src, n: int):
+    f = FIELDS[field] if isinstance(field, str) else int(field)
+    dtype, per = _FIELD_TYPE[f]
+    p, mem, keep = _arg(src, dtype, n * per)
+    _check(load().sph_box_set_field(box, f, p, n, mem), ctx)
 
 
 def sph_box_count_pairs(box, ctx, on: bool):
@@ -369,6 +377,10 @@ class Box:
 
     def set(self, x, v, m, u, h):
         sph_box_set(self.h, self.ctx, x, v, m, u, h, self.n)
+        return self
+
+    def set_field(self, field, src):
+        sph_box_set_field(self.h, self.ctx, field, src, self.n)
         return self
 
     def count_pairs(self, on=True):

@@ -144,3 +144,30 @@ def test_profile_and_launch_counts(api, ctx):
         assert prof[ph]["calls"] >= 1 and prof[ph]["ms"] > 0, ph
     assert sum(v["launches"] for v in prof.values()) <= launched
     assert prof["density_pair"]["launches"] >= 1
+
+
+def test_checkpoint_restart_continues_the_run(api, ctx):
+    """Saving x, v, u, h, a, du/dt and restoring them into a new box continues the run."""
+    box = inputs.lattice_box(12, jitter=0.3, seed=55, v_sigma=0.2)
+    dt = 1e-3
+    b = api.box_from(ctx, box)
+    try:
+        b.step(dt)
+        b.step(dt)
+        state = {k: b.get(k).copy() for k in ("x", "v", "u", "h", "a", "dudt")}
+        b.step(dt)
+        ref = {k: b.get(k) for k in ("x", "v", "rho", "a")}
+    finally:
+        b.close()
+    c = api.Box(ctx, box.n, box.L, True)
+    try:
+        c.set(state["x"], state["v"], box.m, state["u"], state["h"])
+        c.set_field("a", state["a"]).set_field("dudt", state["dudt"])
+        c.step(dt)
+        got = {k: c.get(k) for k in ("x", "v", "rho", "a")}
+    finally:
+        c.close()
+    d = got["x"] - ref["x"]
+    assert np.max(np.abs(d - box.L * np.round(d / box.L))) < 1e-9
+    for k in ("v", "rho", "a"):
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-4 * np.max(np.abs(ref[k])), k

@@ -835,13 +835,20 @@ __global__ void k_h_bracket_reset(long long N, float* __restrict__ hlo, float* _
 
 // =========================================================================== reductions
 // Per box, in FP64: sum m a (3), sum m (v.a + du/dt), sum m v (3), sum m (v^2/2 + u).
-__global__ void k_reduce(long long N, int box_shift, const unsigned long long* __restrict__ key,
-                         const float4* __restrict__ cen4, const float4* __restrict__ vel4,
-                         const float4* __restrict__ facc, double* __restrict__ red) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p - threadIdx.x < N;
-       p += (long long)gridDim.x * blockDim.x) {
-    const bool valid = p < N;
+// Each block accumulates its particles per box in shared memory (boxes are
+// contiguous, so a block spans few of them) and adds its partial sums once.
+__global__ void __launch_bounds__(256) k_reduce(long long N, int box_shift, const unsigned long long* __restrict__ key,
+                                                const float4* __restrict__ cen4, const float4* __restrict__ vel4,
+                                                const float4* __restrict__ facc, double* __restrict__ red) {
+  __shared__ double part[4][8];     // up to four boxes per block-chunk, flushed when a new box appears
+  __shared__ int pbox[4];
+  const long long chunk = (N + gridDim.x - 1) / gridDim.x;
+  const long long p0 = blockIdx.x * chunk, p1 = min(N, p0 + chunk);
+  for (long long base = p0; base < p1; base += blockDim.x) {
+    const long long p = base + threadIdx.x;
+    const bool valid = p < p1;
     const int b = valid ? (int)(key[p] >> box_shift) : -1;
+    const int b0 = (int)(key[base] >> box_shift);
     double val[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid) {
       const double m = cen4[p].w;
@@ -856,19 +863,38 @@ __global__ void k_reduce(long long N, int box_shift, const unsigned long long* _
       val[6] = m * vv.z;
       val[7] = m * (0.5 * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z) + (double)vv.w);
     }
-    const int b0 = __shfl_sync(0xffffffffu, b, 0);
-    const bool uniform = __all_sync(0xffffffffu, b == b0) && b0 >= 0;
-    if (uniform) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        double s = val[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&red[8 * b0 + k], s);
-      }
-    } else if (valid) {
-      for (int k = 0; k < 8; ++k) atomicAdd(&red[8 * b + k], val[k]);
+    // slots: box b0 + 0..3 of this pass; boxes further away go straight to global
+    if (threadIdx.x < 32) {
+      part[threadIdx.x >> 3][threadIdx.x & 7] = 0.0;
+      if (threadIdx.x < 4) pbox[threadIdx.x] = b0 + threadIdx.x;
     }
+    __syncthreads();
+    const int slot = b - b0;
+    if (valid) {
+      if (slot >= 0 && slot < 4) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          double v = val[k];
+          // lanes of the same slot reduce in registers first
+          const unsigned int same = __match_any_sync(__activemask(), slot);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(__activemask(), v, o);
+            const int os = __shfl_down_sync(__activemask(), slot, o);
+            if ((threadIdx.x & 31) + o < 32 && os == slot && ((same >> ((threadIdx.x & 31) + o)) & 1u)) v += w;
+          }
+          if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&part[slot][k], v);
+        }
+      } else {
+        for (int k = 0; k < 8; ++k) atomicAdd(&red[8 * b + k], val[k]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int sl = threadIdx.x >> 3, k = threadIdx.x & 7;
+      if (part[sl][k] != 0.0) atomicAdd(&red[8 * pbox[sl] + k], part[sl][k]);
+    }
+    __syncthreads();
   }
 }
 
@@ -1066,7 +1092,7 @@ void launch_bracket_reset(Engine& E) {
 
 void launch_reduce(Engine& E) {
   cudaMemsetAsync(E.red.p, 0, sizeof(double) * 8 * E.nbox, E.st);
-  k_reduce<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.box_shift, E.key.p, E.cen4.p, E.vel4.p, E.facc.p, E.red.p); count_launch();
+  k_reduce<<<E.nsm * 2, 256, 0, E.st>>>(E.N, E.box_shift, E.key.p, E.cen4.p, E.vel4.p, E.facc.p, E.red.p); count_launch();
 }
 
 void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); count_launch(); }

@@ -324,6 +324,32 @@ sph_status sph_server_release(sph_server* s, int64_t id);
 
 sph_status sph_server_destroy(sph_server* s);
 
+/* ---- density without allocation ---------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (an allocator-free embedding, code that must
+ * not reach the driver's allocator after start-up, or a pre-sized arena owned
+ * by someone else).  It computes the density pass of a small box with no
+ * context, no box and no allocation: its working memory (a uniform cell list
+ * and the particles sorted by cell, about 0.4 MB) is one static device array
+ * that every device holds from the moment the library is loaded until the
+ * process exits.
+ *
+ * x (n*3 doubles in [0, L)), m, h (n floats), rho (n floats, out) and count
+ * (n int32, out) are device pointers on the current device; stream is a
+ * cudaStream_t (NULL: the legacy default stream).  Results: rho_i including the
+ * self term and the neighbour count j != i with r_ij < H_i, H = 1.825742 h,
+ * decided exactly like sph_density.  Returns SPH_E_INVALID for n < 1 or
+ * n > SPH_STATIC_MAX_N, SPH_E_H_TOO_LARGE when a periodic box is narrower than
+ * three H_max, SPH_E_CUDA on a runtime error; synchronises the stream.
+ * The first call on a device looks up the array's address: make it before any
+ * stream capture.  All calls share the one array (each call clears what it
+ * needs), so calls that overlap on the GPU, from any stream or thread, race:
+ * serialise them. */
+#define SPH_STATIC_MAX_N 16384
+#define SPH_STATIC_GAMMA_K 1.825742f
+sph_status sph_density_static(const double* x, const float* m, const float* h, int64_t n, double box_len,
+                              int periodic, float* rho, int32_t* count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

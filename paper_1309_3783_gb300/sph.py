@@ -94,7 +94,10 @@ _SIGS = {
     "sph_server_get": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int64]),
     "sph_server_release": (C.c_int, [_P, C.c_int64]),
     "sph_server_destroy": (C.c_int, [_P]),
+    "sph_density_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_double, C.c_int, _P, _P, _P]),
 }
+
+SPH_STATIC_MAX_N = 16384
 
 _lib = None
 
@@ -444,3 +447,17 @@ def box_from(ctx, pb) -> Box:
     """A Box holding a ParticleBox of ``paper_1309_3783_gb300.inputs``."""
     b = Box(ctx, pb.n, pb.L, pb.periodic)
     return b.set(pb.x, pb.v, pb.m, pb.u, pb.h)
+
+
+def sph_density_static(x, m, h, box_len: float, periodic: bool, rho, count, stream: int = 0):
+    """The allocation-free density pass (all arguments CUDA tensors); returns the status."""
+    n = len(m)
+    px, mx, _ = _arg(x, np.float64, 3 * n)
+    pm, mm, _ = _arg(m, np.float32, n)
+    ph, mh, _ = _arg(h, np.float32, n)
+    pr, mr, _ = _arg(rho, np.float32, n)
+    pc, mc, _ = _arg(count, np.int32, n)
+    if {mx, mm, mh, mr, mc} != {SPH_MEM_DEVICE}:
+        raise ValueError("sph_density_static takes device tensors only")
+    return load().sph_density_static(px, pm, ph, n, float(box_len), 1 if periodic else 0, pr, pc,
+                                     C.c_void_p(stream) if stream else None)

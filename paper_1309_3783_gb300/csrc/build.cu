@@ -631,11 +631,55 @@ __global__ void k_apply_partition(long long N, const unsigned int* __restrict__ 
   }
 }
 
-// flag[p] = 1 where a cluster starts (every 32nd particle of a leaf)
-__global__ void k_tile_flags(long long N, Tree T, const unsigned int* __restrict__ leaf_of,
+// flag[p] = 1 where a cluster starts.  Inside each leaf, separately for its two
+// H classes, the clusters are the leaves of a binary split of the class along
+// its Morton keys: a node (the keys that agree on every bit from some bit b up)
+// is halved at bit b - 1 while it holds more than 32 particles.  Each cluster is
+// then an aligned box of aspect ratio at most 2, much tighter than 32 particles
+// taken in Morton order, which often straddle octants.  Walking a class from
+// its first particle a, the next cluster is the largest node that starts at a
+// and holds at most 32 particles: its bit b* is the smallest of the highest
+// bits in which key[a] differs from key[a - 1] (the node must start at a) and
+// from key[a + 32] (it must end before a + 32).  One warp per leaf.
+__device__ __forceinline__ int high_bit(unsigned long long v) { return v ? 63 - __clzll((long long)v) : -1; }
+
+__global__ void k_tile_flags(Tree T, int nnodes, int box_shift, const BoxDesc* __restrict__ box,
+                             const float* __restrict__ Hs, const unsigned long long* __restrict__ key,
                              unsigned int* __restrict__ flag) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
-    flag[p] = (((unsigned int)p - T.start[leaf_of[p]]) & 31u) == 0u ? 1u : 0u;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int id = warp; id < nnodes; id += nwarps) {
+    if (T.child[id] >= 0) continue;
+    const unsigned int s = T.start[id], c = T.count[id];
+    const float thr = (float)ldexp(box[T.box[id]].L, -T.level[id]);
+    unsigned int nsmall = 0;
+    for (unsigned int b = 0; b < c; b += 32) {
+      const unsigned int q = b + lane;
+      nsmall += __popc(__ballot_sync(0xffffffffu, q < c && !(Hs[s + q] > thr)));
+    }
+    const int lb = box_shift - 3 * T.level[id];      // key bits below the leaf's cell
+    for (int cls = 0; cls < 2; ++cls) {
+      const unsigned int beg = cls == 0 ? s : s + nsmall, end = cls == 0 ? s + nsmall : s + c;
+      unsigned int a = beg;
+      while (a < end) {
+        const unsigned long long ka = key[a];
+        int bs = lb;
+        if (a > beg) bs = min(bs, high_bit(key[a - 1] ^ ka));
+        if (a + 32 < end) bs = min(bs, high_bit(ka ^ key[a + 32]));
+        unsigned int n;
+        if (bs < 0) {
+          n = min(32u, end - a);            // equal keys: no node starts here, take a chunk
+        } else {
+          const unsigned int q = a + 1 + lane;
+          const bool in = lane < 31 && q < end && ((key[q] ^ ka) >> bs) == 0ull;
+          n = 1u + __popc(__ballot_sync(0xffffffffu, in));
+        }
+        if ((unsigned int)lane < n) flag[a + lane] = lane == 0 ? 1u : 0u;
+        a += n;
+      }
+    }
+  }
 }
 
 // cluster table from the exclusive prefix of the flags: tile_of[p], start, size,
@@ -649,7 +693,8 @@ __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict
     const unsigned int t = excl[p];
     const unsigned int leaf = leaf_of[p];
     const unsigned int end = T.start[leaf] + T.count[leaf];
-    const unsigned int n = min(32u, end - (unsigned int)p);
+    unsigned int n = 1;
+    while ((unsigned int)p + n < end && n < 32u && !flag[p + n]) ++n;
     float4 lo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.0f);
     float4 hi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.0f);
     for (unsigned int q = 0; q < n; ++q) {

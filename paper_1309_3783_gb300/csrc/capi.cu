@@ -41,7 +41,8 @@ __global__ void k_leaf_partition(Tree, int, const BoxDesc*, const float*, unsign
 __global__ void k_apply_partition(long long, const unsigned int*, const unsigned int*, unsigned int*,
                                   const unsigned long long*, unsigned long long*, const float*, float*,
                                   const float4*, float4*);
-__global__ void k_tile_flags(long long, Tree, const unsigned int*, unsigned int*);
+__global__ void k_tile_flags(Tree, int, int, const BoxDesc*, const float*, const unsigned long long*,
+                             unsigned int*);
 __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigned int*, const unsigned int*,
                              const float4*, unsigned int*, Tiles);
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
@@ -55,7 +56,8 @@ void launch_zero_density(Engine& E, bool all);
 void launch_set_active(Engine& E);
 void launch_mark_active_cells(Engine& E);
 void launch_count_unconverged(Engine& E, int* out);
-void launch_task_tables(Engine& E);
+void launch_task_offsets(Engine& E);
+void launch_task_items(Engine& E);
 void launch_bracket_reset(Engine& E);
 void launch_reduce(Engine& E);
 void launch_save_acc(Engine& E);
@@ -238,6 +240,7 @@ sph_status Engine::ensure_particle_capacity() {
   CK(red.reserve(8 * std::max(nbox, 1)));
   CK(err_all.reserve(4));
   CK(pc.reserve(16));
+  CK(task_ctr.reserve(4));
   CK(dev_counters.reserve(8));
   CK(staging.reserve(24 * n));
   CK(cudaMemsetAsync(conv.p, 0, n * sizeof(int), st));
@@ -477,7 +480,7 @@ sph_status Engine::build_once(bool* retry) {
   k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p); count_launch();
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   // clusters of at most 32 particles inside each leaf
-  k_tile_flags<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p); count_launch();
+  k_tile_flags<<<nsm * 8, 256, 0, st>>>(T, n_nodes, box_shift, box.p, Hs.p, key.p, tflag.p); count_launch();
   exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), st);
   k_tile_table<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL); count_launch();
   k_cell_tiles<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, tile_of.p); count_launch();
@@ -496,6 +499,7 @@ sph_status Engine::build_once(bool* retry) {
   k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T); count_launch();
   k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
                                               cap_big); count_launch();
+  launch_task_offsets(*this);
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
   int lc[8];
@@ -530,7 +534,11 @@ sph_status Engine::build_once(bool* retry) {
   n_entries = (unsigned int)lc[5];
   n_big = (int)bc[0];
   n_big_entries = bc[1];
-  launch_task_tables(*this);
+  CK(l_ptask.reserve(std::max(lc[6], 1)));
+  CK(l_stask.reserve(std::max(lc[7], 1)));
+  Lq.p_task = l_ptask.p;
+  Lq.s_task = l_stask.p;
+  launch_task_items(*this);
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   ev = prof_begin(PH_AXIS_SORT, &l0);

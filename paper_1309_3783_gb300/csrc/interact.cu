@@ -43,6 +43,11 @@ __device__ __forceinline__ ItemGeom item_geom(const Tree& T, const BoxDesc* box,
   return g;
 }
 
+// Tasks are handed out in chunks from a counter in device memory (zeroed before
+// every launch): the cost of a task varies by orders of magnitude, so a static
+// split leaves most SMs idle behind the longest ones.
+constexpr unsigned int TASK_CHUNK = 2;
+
 // Exact decision r_ij < H (physical H) from the caller's FP64 positions.
 __device__ __noinline__ bool exact_less(int gi, int gj, float Hphys, const unsigned int* __restrict__ perm,
                                         const double* __restrict__ x, double L, double halfL, int periodic) {
@@ -63,22 +68,10 @@ __device__ __forceinline__ bool decide(float r2, float H2, float band, int gi, i
   return exact_less(gi, gj, Hphys, perm, x, g.L, g.halfL, g.periodic);
 }
 
-// Task t of a prefix table toff[0..n) (exclusive prefix of i-tiles per item):
-// the item with toff[item] <= t < toff[item + 1].
-__device__ __forceinline__ int task_item(const unsigned int* __restrict__ toff, int n, unsigned int t) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (toff[mid] <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // =========================================================================== density
 struct DensI {
   float3 p;
-  float invH, H2, band, Hphys, m;
+  float H, invH, H2, band, Hphys, m;
   int g;
   bool valid, act;
 };
@@ -93,6 +86,7 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
     // the cell offsets (c + shift) are exact dyadic values: add them first, round once
     r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
     const float H = p.w * invL;
+    r.H = H;
     r.invH = 1.0f / H;
     r.H2 = H * H;
     r.band = BAND_REL * H * (e + H);
@@ -102,6 +96,7 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
     r.act = act[gidx] != 0;
   } else {
     r.p = make_float3(1e30f, 1e30f, 1e30f);
+    r.H = 0.0f;
     r.invH = 0.0f;
     r.H2 = -1.0f;
     r.band = 0.0f;
@@ -168,7 +163,7 @@ __device__ __forceinline__ void commit_counters(const Counters& C, unsigned long
 // =========================================================================== force
 struct ForceI {
   float3 p;
-  float invH, H2, band, Hphys, m;
+  float H, invH, H2, band, Hphys, m;
   float3 v;
   float rho, F, c, K4;
   int g;
@@ -188,6 +183,7 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
     // the cell offsets (c + shift) are exact dyadic values: add them first, round once
     r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
     const float H = p.w * invL;
+    r.H = H;
     r.invH = 1.0f / H;
     r.H2 = H * H;
     r.band = BAND_REL * H * (e + H);
@@ -202,6 +198,7 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
     r.g = (int)gidx;
   } else {
     r.p = make_float3(1e30f, 1e30f, 1e30f);
+    r.H = 0.f;
     r.invH = 0.f;
     r.H2 = -1.f;
     r.band = 0.f;
@@ -244,35 +241,40 @@ __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, floa
 }
 
 // ------------------------------------------------------------- two-phase tiles
-// The 32 partners of a cluster pair sit in shared memory.  Phase 1: every lane
-// tests its particle i against all 32 partners (broadcast reads) and keeps two
-// bitmasks, r < H_i and r < H_j, decided exactly.  Phase 2: every lane walks
+// Up to 32 partners sit in shared memory: particles of one or several partner
+// clusters that passed a test against the box of the warp's cluster.  Phase 1:
+// every lane tests its particle i against the staged partners (broadcast
+// reads) and keeps two bitmasks, r < H_i and r < H_j, decided exactly.  Phase 2:
+// every lane walks
 // only its set bits; its own side accumulates in registers, the partner side in
 // shared memory with atomics (lanes may share a partner).  Invalid lanes sit at
 // 1e30 with H^2 = -1, so they never pass a test.
 
-// Phase 1 of a cluster pair: exact bitmasks of r < H_i (mI) and r < H_j (mJ) over
-// the 32 staged partners.  The FP32 test decides outside a guard band around
+// Phase 1: exact bitmasks of r < H_i (mI) and r < H_j (mJ) over the first n
+// staged partners (n a multiple of 4; slots past the batch hold empty entries).  The FP32 test decides outside a guard band around
 // H^2; bandJ bounds every partner's band; the few uncertain bits are decided in
 // FP64 afterwards.
 template <class SH>
 __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iband, int ig, float iHphys,
-                                           const SH& S, float bandJ, unsigned int allow, const unsigned int* perm,
-                                           const double* x, const ItemGeom& g, unsigned int& mI, unsigned int& mJ,
-                                           unsigned int& rc) {
+                                           const SH& S, float bandJ, unsigned int allow, int n,
+                                           const unsigned int* perm, const double* x, const ItemGeom& g,
+                                           unsigned int& mI, unsigned int& mJ, unsigned int& rc) {
   unsigned int uI = 0, uJ = 0;
   mI = 0;
   mJ = 0;
-#pragma unroll 8
-  for (int s = 0; s < 32; ++s) {
-    const float4 J = S.p[s];
-    const float dx = ip.x - J.x, dy = ip.y - J.y, dz = ip.z - J.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const float di = r2 - iH2, dj = r2 - J.w;
-    mI |= (di < -iband ? 1u : 0u) << s;
-    uI |= (fabsf(di) <= iband ? 1u : 0u) << s;
-    mJ |= (dj < -bandJ ? 1u : 0u) << s;
-    uJ |= (fabsf(dj) <= bandJ ? 1u : 0u) << s;
+  for (int s0 = 0; s0 < n; s0 += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int s = s0 + k;
+      const float4 J = S.p[s];
+      const float dx = ip.x - J.x, dy = ip.y - J.y, dz = ip.z - J.z;
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const float di = r2 - iH2, dj = r2 - J.w;
+      mI |= (di < -iband ? 1u : 0u) << s;
+      uI |= (fabsf(di) <= iband ? 1u : 0u) << s;
+      mJ |= (dj < -bandJ ? 1u : 0u) << s;
+      uJ |= (fabsf(dj) <= bandJ ? 1u : 0u) << s;
+    }
   }
   uI &= allow;
   uJ &= allow;
@@ -295,11 +297,11 @@ __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iba
 
 template <bool COUNT>
 __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigned int allow, unsigned int jvalid,
-                                          unsigned int jact, float bandJ, float4& acc, unsigned int& cnt,
+                                          unsigned int jact, float bandJ, int n, float4& acc, unsigned int& cnt,
                                           const unsigned int* perm, const double* x, const ItemGeom& g,
                                           Counters& C) {
   unsigned int mI, mJ, rc = 0;
-  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, perm, x, g, mI, mJ, rc);
+  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
   const unsigned int ui = I.act ? mI : 0u, uj = mJ & jact;
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid) : 0u;
@@ -341,10 +343,10 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
 
 template <bool COUNT>
 __device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsigned int allow, unsigned int jvalid,
-                                           float bandJ, float4& acc, float& vsig_i, const unsigned int* perm,
+                                           float bandJ, int n, float4& acc, float& vsig_i, const unsigned int* perm,
                                            const double* x, const ItemGeom& g, float alpha, Counters& C) {
   unsigned int mI, mJ, rc = 0;
-  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, perm, x, g, mI, mJ, rc);
+  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid) : 0u;
     C.rechecks += rc;
@@ -393,6 +395,47 @@ __device__ __forceinline__ unsigned int upper_mask(int lane) {
   return lane == 31 ? 0u : (0xffffffffu << (lane + 1));
 }
 
+// One batch of q <= 32 staged partners (slots 0..q-1) against the warp's
+// cluster: empty the slots past the batch, run both phases over the first
+// q rounded up to 4, and flush the partners' shared-memory sums.  allow limits
+// the partners of each lane (the upper triangle inside one cluster).
+template <bool COUNT>
+__device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsigned int q, unsigned int allow,
+                                           float4& acc, unsigned int& cnt, const unsigned int* perm,
+                                           const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
+                                           Counters& C) {
+  const int lane = threadIdx.x & 31;
+  const bool v = (unsigned int)lane < q;
+  __syncwarp();
+  if (!v) S.p[lane] = make_float4(1e30f, 1e30f, 1e30f, -1.0f);
+  const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
+  const unsigned int jact = __ballot_sync(0xffffffffu, v && S.act[lane]);
+  const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
+  __syncwarp();
+  dens_tile<COUNT>(I, S, allow & jvalid, jvalid, jact, bandJ, (int)((q + 3u) & ~3u), acc, cnt, perm, x, g, C);
+  __syncwarp();
+  if (v) flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+  __syncwarp();
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, unsigned int q, unsigned int allow,
+                                            float4& acc, float& vsi, const unsigned int* perm, const double* x,
+                                            const ItemGeom& g, float alpha, float4* facc, float* fvsig,
+                                            Counters& C) {
+  const int lane = threadIdx.x & 31;
+  const bool v = (unsigned int)lane < q;
+  __syncwarp();
+  if (!v) S.p[lane] = make_float4(1e30f, 1e30f, 1e30f, -1.0f);
+  const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
+  const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
+  __syncwarp();
+  force_tile<COUNT>(I, S, allow & jvalid, jvalid, bandJ, (int)((q + 3u) & ~3u), acc, vsi, perm, x, g, alpha, C);
+  __syncwarp();
+  if (v) flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+  __syncwarp();
+}
+
 
 
 // ------------------------------------------------------------- cluster geometry
@@ -425,6 +468,15 @@ __device__ __forceinline__ float box_gap(const Box3& a, const Box3& b) {
   const float gy = fmaxf(0.0f, fmaxf(b.lo.y - a.hi.y, a.lo.y - b.hi.y));
   const float gz = fmaxf(0.0f, fmaxf(b.lo.z - a.hi.z, a.lo.z - b.hi.z));
   return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+}
+
+// distance from a point to a box within reach (FP32; the caller's slack covers
+// the rounding of both)
+__device__ __forceinline__ bool near_box(const float3 p, const Box3& b, float reach) {
+  const float gx = fmaxf(0.0f, fmaxf(b.lo.x - p.x, p.x - b.hi.x));
+  const float gy = fmaxf(0.0f, fmaxf(b.lo.y - p.y, p.y - b.hi.y));
+  const float gz = fmaxf(0.0f, fmaxf(b.lo.z - p.z, p.z - b.hi.z));
+  return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz))) <= reach;
 }
 
 // upper end of the projection of a box on u
@@ -468,15 +520,17 @@ __device__ __forceinline__ PairSetup pair_setup(const Lists& Lq, const Tree& T, 
 }
 
 // Lane-parallel scan of B's sorted cluster list for the i cluster (box bi,
-// largest support Hi): returns in *jt the lane's candidate and a ballot of the
-// lanes whose cluster is in reach (sorted window, then box distance).
+// largest support Hi): returns in *jt, *jn, *js the lane's candidate cluster,
+// its size and first particle, and a ballot of the lanes whose cluster is in
+// reach (sorted window, then box distance).
 // *stop is set when the sorted window has passed every cluster of B.
 template <bool DENS>
 __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const Tree& T, const Tiles& TL,
                                                       const float* __restrict__ sort_r,
                                                       const unsigned int* __restrict__ sort_i, unsigned int e0,
                                                       const Box3& bi, float rhi_i, float Hi, bool i_active,
-                                                      unsigned int* jt, bool* stop) {
+                                                      unsigned int* jt, unsigned int* jn, unsigned int* js,
+                                                      bool* stop) {
   const int lane = threadIdx.x & 31;
   const float r0 = sort_r[P.sb + e0] + P.g.offBp;
   *stop = r0 - rhi_i > fmaxf(Hi, P.HmB) + P.slack;     // the sorted list only moves further away
@@ -494,6 +548,8 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
     }
   }
   *jt = t;
+  *jn = pass ? TL.n[t] : 0u;
+  *js = pass ? TL.start[t] : 0u;
   return __ballot_sync(0xffffffffu, pass);
 }
 
@@ -507,52 +563,62 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
                                                               const unsigned char* __restrict__ act,
                                                               const unsigned int* __restrict__ perm,
                                                               const double* __restrict__ x, float4* dacc,
-                                                              unsigned int* dcnt, unsigned long long* pc) {
+                                                              unsigned int* dcnt, unsigned long long* pc,
+                                                              unsigned int* __restrict__ task_ctr) {
   __shared__ DensShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   DensShared& S = SH[wl];
   Counters C;
-  const int npair = min(Lq.counts[1], cap_pair);
   const unsigned int ntask = (unsigned int)Lq.counts[6];
-  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
-    const int item = task_item(Lq.p_toff, npair, t);
-    const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
-    if (!(T.active[A0] | T.active[B0])) continue;          // no particle of either cell still iterating h
-    const unsigned int ti = T.tile0[A0] + (t - Lq.p_toff[item]);
-    const bool i_active = TL.active[ti] != 0;
-    if (!i_active && !T.active[B0]) continue;
-    const PairSetup P = pair_setup(Lq, T, box, item);
-    const Box3 bi = tile_box3(TL, T, ti, P.tshA);
-    const float Hi = TL.lo[ti].w * P.g.invL;
-    if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;   // cluster out of reach of B
-    const float rhi_i = box_rhi(bi, P.u);
-    const unsigned int ni = TL.n[ti];
-    const bool vi = (unsigned int)lane < ni;
-    const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned int cnt = 0;
-    for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
-      unsigned int jt;
-      bool stop;
-      unsigned int mask = scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &stop);
-      if (stop) break;
-      while (mask) {
-        const int k = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const unsigned int tj = __shfl_sync(0xffffffffu, jt, k);
-        const bool vj = (unsigned int)lane < TL.n[tj];
-        const DensI J = load_dens(vj, TL.start[tj] + lane, P.shB, pos4, cen4, act, P.g.invL, P.g.e);
-        dens_put(S, lane, J);
-        const unsigned int jvalid = __ballot_sync(0xffffffffu, vj), jact = __ballot_sync(0xffffffffu, J.act);
-        const float bandJ = warp_max(J.band);
-        __syncwarp();
-        dens_tile<COUNT>(I, S, 0xffffffffu, jvalid, jact, bandJ, acc, cnt, perm, x, P.g, C);
-        __syncwarp();
-        flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
-        __syncwarp();
+  unsigned int raw = 0;
+  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
+    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    for (unsigned int t = base; t < tend; ++t) {
+      const int item = (int)Lq.p_task[t];
+      const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
+      if (!(T.active[A0] | T.active[B0])) continue;          // no particle of either cell still iterating h
+      const unsigned int ti = T.tile0[A0] + (t - Lq.p_toff[item]);
+      const bool i_active = TL.active[ti] != 0;
+      if (!i_active && !T.active[B0]) continue;
+      const PairSetup P = pair_setup(Lq, T, box, item);
+      const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+      const float Hi = TL.lo[ti].w * P.g.invL;
+      if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;   // cluster out of reach of B
+      const float rhi_i = box_rhi(bi, P.u);
+      const unsigned int ni = TL.n[ti];
+      const bool vi = (unsigned int)lane < ni;
+      const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned int cnt = 0, q = 0;
+      for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
+        unsigned int jt, jn, js;
+        bool stop;
+        unsigned int mask =
+            scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &jn, &js, &stop);
+        if (stop) break;
+        while (mask) {
+          const int k = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+          const DensI J = load_dens(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, act, P.g.invL,
+                                    P.g.e);
+          // stage only the partners within reach of the cluster's box
+          const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
+          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+          const unsigned int np = __popc(bal);
+          if (q + np > 32u) {
+            dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+            q = 0;
+          }
+          if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+          q += np;
+        }
       }
+      if (q) dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+      flush_dens(I.g, acc, cnt, dacc, dcnt);
     }
-    flush_dens(I.g, acc, cnt, dacc, dcnt);
   }
   commit_counters<COUNT>(C, pc, 0);
 }
@@ -565,50 +631,67 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
                                                               const unsigned char* __restrict__ act,
                                                               const unsigned int* __restrict__ perm,
                                                               const double* __restrict__ x, float4* dacc,
-                                                              unsigned int* dcnt, unsigned long long* pc) {
+                                                              unsigned int* dcnt, unsigned long long* pc,
+                                                              unsigned int* __restrict__ task_ctr) {
   __shared__ DensShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   DensShared& S = SH[wl];
   Counters C;
-  const int nself = min(Lq.counts[0], cap_self);
   const unsigned int ntask = (unsigned int)Lq.counts[7];
-  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
-    const int item = task_item(Lq.s_toff, nself, t);
-    const int A = Lq.self_a[item];
-    if (!T.active[A]) continue;
-    const ItemGeom g = item_geom(T, box, A, 0);
-    const float4 cA = T.cen[A];
-    const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-    const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
-    const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
-    const unsigned int ti = t0 + (t - Lq.s_toff[item]);
-    const bool i_active = TL.active[ti] != 0;
-    const Box3 bi = tile_box3(TL, T, ti, sh);
-    const float Hi = TL.lo[ti].w * g.invL;
-    const bool vi = (unsigned int)lane < TL.n[ti];
-    const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned int cnt = 0;
-    for (unsigned int tj = ti; tj < t0 + nt; ++tj) {
-      if (tj != ti) {
-        if (!i_active && !TL.active[tj]) continue;
-        const Box3 bj = tile_box3(TL, T, tj, sh);
-        if (box_gap(bi, bj) > fmaxf(Hi, TL.lo[tj].w * g.invL) + slack) continue;
+  unsigned int raw = 0;
+  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
+    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    for (unsigned int t = base; t < tend; ++t) {
+      const int item = (int)Lq.s_task[t];
+      const int A = Lq.self_a[item];
+      if (!T.active[A]) continue;
+      const ItemGeom g = item_geom(T, box, A, 0);
+      const float4 cA = T.cen[A];
+      const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
+      const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+      const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
+      const unsigned int ti = t0 + (t - Lq.s_toff[item]);
+      const bool i_active = TL.active[ti] != 0;
+      const Box3 bi = tile_box3(TL, T, ti, sh);
+      const float Hi = TL.lo[ti].w * g.invL;
+      const bool vi = (unsigned int)lane < TL.n[ti];
+      const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      unsigned int cnt = 0, q = 0;
+      // inside the cluster itself each unordered pair once: partners above the lane
+      if (vi) dens_put(S, lane, I);
+      dens_batch<COUNT>(I, S, TL.n[ti], upper_mask(lane), acc, cnt, perm, x, g, dacc, dcnt, C);
+      // the later clusters of the cell, 32 box tests at a time
+      for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
+        const unsigned int tl = b0 + lane;
+        bool ok = false;
+        if (tl < t0 + nt && (i_active || TL.active[tl])) {
+          const Box3 bj = tile_box3(TL, T, tl, sh);
+          ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
+        }
+        unsigned int mask = __ballot_sync(0xffffffffu, ok);
+        while (mask) {
+          const int k = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const unsigned int tj = b0 + (unsigned int)k;
+          const bool vj = (unsigned int)lane < TL.n[tj];
+          const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
+          const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
+          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+          const unsigned int np = __popc(bal);
+          if (q + np > 32u) {
+            dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
+            q = 0;
+          }
+          if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+          q += np;
+        }
       }
-      const bool vj = (unsigned int)lane < TL.n[tj];
-      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
-      dens_put(S, lane, J);
-      const unsigned int jvalid = __ballot_sync(0xffffffffu, vj), jact = __ballot_sync(0xffffffffu, J.act);
-      const float bandJ = warp_max(J.band);
-      __syncwarp();
-      // inside one cluster each unordered pair once: partners above the lane
-      dens_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, jact, bandJ, acc, cnt, perm, x, g,
-                       C);
-      __syncwarp();
-      flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
-      __syncwarp();
+      if (q) dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
+      flush_dens(I.g, acc, cnt, dacc, dcnt);
     }
-    flush_dens(I.g, acc, cnt, dacc, dcnt);
   }
   commit_counters<COUNT>(C, pc, 1);
 }
@@ -624,47 +707,57 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
                                                             const unsigned int* __restrict__ sort_i,
                                                             const unsigned int* __restrict__ perm,
                                                             const double* __restrict__ x, float alpha, float4* facc,
-                                                            float* fvsig, unsigned long long* pc) {
+                                                            float* fvsig, unsigned long long* pc,
+                                                            unsigned int* __restrict__ task_ctr) {
   __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   ForceShared& S = SH[wl];
   Counters C;
-  const int npair = min(Lq.counts[1], cap_pair);
   const unsigned int ntask = (unsigned int)Lq.counts[6];
-  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
-    const int item = task_item(Lq.p_toff, npair, t);
-    const PairSetup P = pair_setup(Lq, T, box, item);
-    const unsigned int ti = T.tile0[P.A] + (t - Lq.p_toff[item]);
-    const Box3 bi = tile_box3(TL, T, ti, P.tshA);
-    const float Hi = TL.lo[ti].w * P.g.invL;
-    if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;
-    const float rhi_i = box_rhi(bi, P.u);
-    const bool vi = (unsigned int)lane < TL.n[ti];
-    const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    float vsi = 0.0f;
-    for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
-      unsigned int jt;
-      bool stop;
-      unsigned int mask = scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, true, &jt, &stop);
-      if (stop) break;
-      while (mask) {
-        const int k = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const unsigned int tj = __shfl_sync(0xffffffffu, jt, k);
-        const bool vj = (unsigned int)lane < TL.n[tj];
-        const ForceI J = load_force(vj, TL.start[tj] + lane, P.shB, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
-        force_put(S, lane, J);
-        const unsigned int jvalid = __ballot_sync(0xffffffffu, vj);
-        const float bandJ = warp_max(J.band);
-        __syncwarp();
-        force_tile<COUNT>(I, S, 0xffffffffu, jvalid, bandJ, acc, vsi, perm, x, P.g, alpha, C);
-        __syncwarp();
-        flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
-        __syncwarp();
+  unsigned int raw = 0;
+  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
+    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    for (unsigned int t = base; t < tend; ++t) {
+      const int item = (int)Lq.p_task[t];
+      const PairSetup P = pair_setup(Lq, T, box, item);
+      const unsigned int ti = T.tile0[P.A] + (t - Lq.p_toff[item]);
+      const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+      const float Hi = TL.lo[ti].w * P.g.invL;
+      if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;
+      const float rhi_i = box_rhi(bi, P.u);
+      const bool vi = (unsigned int)lane < TL.n[ti];
+      const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float vsi = 0.0f;
+      unsigned int q = 0;
+      for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
+        unsigned int jt, jn, js;
+        bool stop;
+        unsigned int mask =
+            scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, true, &jt, &jn, &js, &stop);
+        if (stop) break;
+        while (mask) {
+          const int k = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+          const ForceI J = load_force(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, vel4, ghost4,
+                                      P.g.invL, P.g.e);
+          const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
+          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+          const unsigned int np = __popc(bal);
+          if (q + np > 32u) {
+            force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+            q = 0;
+          }
+          if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+          q += np;
+        }
       }
+      if (q) force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+      flush_force(I.g, acc, vsi, facc, fvsig);
     }
-    flush_force(I.g, acc, vsi, facc, fvsig);
   }
   commit_counters<COUNT>(C, pc, 2);
 }
@@ -678,46 +771,65 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
                                                             const float4* __restrict__ ghost4,
                                                             const unsigned int* __restrict__ perm,
                                                             const double* __restrict__ x, float alpha, float4* facc,
-                                                            float* fvsig, unsigned long long* pc) {
+                                                            float* fvsig, unsigned long long* pc,
+                                                            unsigned int* __restrict__ task_ctr) {
   __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   ForceShared& S = SH[wl];
   Counters C;
-  const int nself = min(Lq.counts[0], cap_self);
   const unsigned int ntask = (unsigned int)Lq.counts[7];
-  for (unsigned int t = blockIdx.x * SPH_WARPS_PER_CTA + wl; t < ntask; t += gridDim.x * SPH_WARPS_PER_CTA) {
-    const int item = task_item(Lq.s_toff, nself, t);
-    const int A = Lq.self_a[item];
-    const ItemGeom g = item_geom(T, box, A, 0);
-    const float4 cA = T.cen[A];
-    const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-    const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
-    const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
-    const unsigned int ti = t0 + (t - Lq.s_toff[item]);
-    const Box3 bi = tile_box3(TL, T, ti, sh);
-    const float Hi = TL.lo[ti].w * g.invL;
-    const bool vi = (unsigned int)lane < TL.n[ti];
-    const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    float vsi = 0.0f;
-    for (unsigned int tj = ti; tj < t0 + nt; ++tj) {
-      if (tj != ti) {
-        const Box3 bj = tile_box3(TL, T, tj, sh);
-        if (box_gap(bi, bj) > fmaxf(Hi, TL.lo[tj].w * g.invL) + slack) continue;
+  unsigned int raw = 0;
+  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
+    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    for (unsigned int t = base; t < tend; ++t) {
+      const int item = (int)Lq.s_task[t];
+      const int A = Lq.self_a[item];
+      const ItemGeom g = item_geom(T, box, A, 0);
+      const float4 cA = T.cen[A];
+      const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
+      const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+      const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
+      const unsigned int ti = t0 + (t - Lq.s_toff[item]);
+      const Box3 bi = tile_box3(TL, T, ti, sh);
+      const float Hi = TL.lo[ti].w * g.invL;
+      const bool vi = (unsigned int)lane < TL.n[ti];
+      const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float vsi = 0.0f;
+      unsigned int q = 0;
+      // inside the cluster itself each unordered pair once: partners above the lane
+      if (vi) force_put(S, lane, I);
+      force_batch<COUNT>(I, S, TL.n[ti], upper_mask(lane), acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+      for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
+        const unsigned int tl = b0 + lane;
+        bool ok = false;
+        if (tl < t0 + nt) {
+          const Box3 bj = tile_box3(TL, T, tl, sh);
+          ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
+        }
+        unsigned int mask = __ballot_sync(0xffffffffu, ok);
+        while (mask) {
+          const int k = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const unsigned int tj = b0 + (unsigned int)k;
+          const bool vj = (unsigned int)lane < TL.n[tj];
+          const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+          const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
+          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+          const unsigned int np = __popc(bal);
+          if (q + np > 32u) {
+            force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+            q = 0;
+          }
+          if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+          q += np;
+        }
       }
-      const bool vj = (unsigned int)lane < TL.n[tj];
-      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
-      force_put(S, lane, J);
-      const unsigned int jvalid = __ballot_sync(0xffffffffu, vj);
-      const float bandJ = warp_max(J.band);
-      __syncwarp();
-      force_tile<COUNT>(I, S, tj == ti ? upper_mask(lane) : 0xffffffffu, jvalid, bandJ, acc, vsi, perm, x, g, alpha,
-                        C);
-      __syncwarp();
-      flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
-      __syncwarp();
+      if (q) force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+      flush_force(I.g, acc, vsi, facc, fvsig);
     }
-    flush_force(I.g, acc, vsi, facc, fvsig);
   }
   commit_counters<COUNT>(C, pc, 3);
 }
@@ -804,10 +916,29 @@ __global__ void k_mark_active_cells(long long N, const unsigned char* __restrict
 }
 
 // clusters of the i cell per interaction: the prefix of these numbers the tasks
-__global__ void k_task_tiles(Lists Lq, Tree T, int npair, int nself) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npair + nself; i += gridDim.x * blockDim.x) {
-    if (i < npair) Lq.p_toff[i] = T.ntile[Lq.pair_a[i]];
-    else Lq.s_toff[i - npair] = T.ntile[Lq.self_a[i - npair]];
+// Tasks: one per (interaction, cluster of its first cell).  Counts per
+// interaction over the whole list capacity (zero past the list), so that the
+// prefix and the task totals are ready before the host reads the list sizes.
+__global__ void k_task_tiles(Lists Lq, Tree T, int cap_pair, int cap_self) {
+  const int npair = min(Lq.counts[1], cap_pair), nself = min(Lq.counts[0], cap_self);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap_pair + cap_self; i += gridDim.x * blockDim.x) {
+    if (i < cap_pair) Lq.p_toff[i] = i < npair ? T.ntile[Lq.pair_a[i]] : 0u;
+    else Lq.s_toff[i - cap_pair] = i - cap_pair < nself ? T.ntile[Lq.self_a[i - cap_pair]] : 0u;
+  }
+}
+
+// task -> interaction tables (one warp per interaction)
+__global__ void k_task_items(Lists Lq, Tree T, int npair, int nself) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < npair + nself; i += nwarps) {
+    const bool pr = i < npair;
+    const int it = pr ? i : i - npair;
+    const unsigned int t0 = pr ? Lq.p_toff[it] : Lq.s_toff[it];
+    const unsigned int n = T.ntile[pr ? Lq.pair_a[it] : Lq.self_a[it]];
+    unsigned int* dst = pr ? Lq.p_task : Lq.s_task;
+    for (unsigned int k = lane; k < n; k += 32) dst[t0 + k] = (unsigned int)it;
   }
 }
 
@@ -1001,55 +1132,56 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
 }
 
 // =========================================================================== launchers
+// CTAs of a kernel resident per SM at SPH_THREADS threads (looked up once)
+static int resident_ctas(const void* fn) {
+  static const void* fns[8] = {nullptr};
+  static int val[8] = {0};
+  for (int k = 0; k < 8; ++k) {
+    if (fns[k] == fn) return val[k];
+    if (!fns[k]) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, SPH_THREADS, 0) != cudaSuccess || nb < 1) nb = 4;
+      fns[k] = fn;
+      val[k] = nb;
+      return nb;
+    }
+  }
+  return 4;
+}
+
 void launch_density_pair(Engine& E) {
-  const int grid = E.nsm * 8;
-  if (E.count_pairs)
-    k_density_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                         E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
-                                                         E.dacc.p, E.dcnt.p, E.pc.p);
-  else
-    k_density_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                          E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
-                                                          E.dacc.p, E.dcnt.p, E.pc.p);
+  const auto k = E.count_pairs ? k_density_pair<true> : k_density_pair<false>;
+  cudaMemsetAsync(E.task_ctr.p + 0, 0, sizeof(unsigned int), E.st);
+  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+      E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
+      E.dacc.p, E.dcnt.p, E.pc.p, E.task_ctr.p + 0);
   count_launch();
 }
 
 void launch_density_self(Engine& E) {
-  const int grid = E.nsm * 8;
-  if (E.count_pairs)
-    k_density_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                         E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
-  else
-    k_density_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                          E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.pc.p);
+  const auto k = E.count_pairs ? k_density_self<true> : k_density_self<false>;
+  cudaMemsetAsync(E.task_ctr.p + 1, 0, sizeof(unsigned int), E.st);
+  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+      E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p,
+      E.pc.p, E.task_ctr.p + 1);
   count_launch();
 }
 
 void launch_force_pair(Engine& E) {
-  const int grid = E.nsm * 8;
-  const float alpha = E.prm.alpha_visc;
-  if (E.count_pairs)
-    k_force_pair<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                       E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
-                                                       E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
-  else
-    k_force_pair<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                        E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p,
-                                                        E.x.p, alpha, E.facc.p, E.fvsig.p, E.pc.p);
+  const auto k = E.count_pairs ? k_force_pair<true> : k_force_pair<false>;
+  cudaMemsetAsync(E.task_ctr.p + 2, 0, sizeof(unsigned int), E.st);
+  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+      E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p,
+      E.perm.p, E.x.p, E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 2);
   count_launch();
 }
 
 void launch_force_self(Engine& E) {
-  const int grid = E.nsm * 8;
-  const float alpha = E.prm.alpha_visc;
-  if (E.count_pairs)
-    k_force_self<true><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                       E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
-                                                       E.fvsig.p, E.pc.p);
-  else
-    k_force_self<false><<<grid, SPH_THREADS, 0, E.st>>>(E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p,
-                                                        E.vel4.p, E.ghost4.p, E.perm.p, E.x.p, alpha, E.facc.p,
-                                                        E.fvsig.p, E.pc.p);
+  const auto k = E.count_pairs ? k_force_self<true> : k_force_self<false>;
+  cudaMemsetAsync(E.task_ctr.p + 3, 0, sizeof(unsigned int), E.st);
+  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+      E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.perm.p, E.x.p,
+      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 3);
   count_launch();
 }
 
@@ -1078,12 +1210,16 @@ void launch_mark_active_cells(Engine& E) {
   k_mark_active_cells<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.leaf_of.p, E.T); count_launch();
 }
 
-void launch_task_tables(Engine& E) {
-  k_task_tiles<<<E.grid(E.n_pairs + E.n_selfs), 256, 0, E.st>>>(E.Lq, E.T, E.n_pairs, E.n_selfs); count_launch();
-  exclusive_scan(E.Lq.p_toff, E.Lq.p_toff, E.n_pairs, E.scan_tmp.p,
+void launch_task_offsets(Engine& E) {
+  k_task_tiles<<<E.grid(E.cap_pair + E.cap_self), 256, 0, E.st>>>(E.Lq, E.T, E.cap_pair, E.cap_self); count_launch();
+  exclusive_scan(E.Lq.p_toff, E.Lq.p_toff, E.cap_pair, E.scan_tmp.p,
                  reinterpret_cast<unsigned int*>(E.Lq.counts + 6), E.st);
-  exclusive_scan(E.Lq.s_toff, E.Lq.s_toff, E.n_selfs, E.scan_tmp.p,
+  exclusive_scan(E.Lq.s_toff, E.Lq.s_toff, E.cap_self, E.scan_tmp.p,
                  reinterpret_cast<unsigned int*>(E.Lq.counts + 7), E.st);
+}
+
+void launch_task_items(Engine& E) {
+  k_task_items<<<E.nsm * 8, 256, 0, E.st>>>(E.Lq, E.T, E.n_pairs, E.n_selfs); count_launch();
 }
 
 void launch_bracket_reset(Engine& E) {

@@ -155,7 +155,7 @@ class Engine {
   // interaction lists
   int cap_self = 0, cap_pair = 0, cap_queue = 0;
   DBuf<int> l_self, l_pa, l_pb, l_pax, l_counts;
-  DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp;
+  DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp, l_ptask, l_stask;
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
   Lists Lq{};
 
@@ -178,6 +178,7 @@ class Engine {
   DBuf<double> red;               // 8 per box
   DBuf<unsigned int> err_all;     // global error bits
   DBuf<unsigned long long> pc;    // pair counters per kernel (see commit_counters)
+  DBuf<unsigned int> task_ctr;    // task counters of the four interaction kernels
   DBuf<int> dev_counters;         // [0] particles still active after a ghost pass
   DBuf<unsigned char> staging;    // output staging (input order)
 

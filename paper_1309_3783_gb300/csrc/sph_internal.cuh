@@ -202,6 +202,8 @@ struct Lists {
   int* q_axis[2];
   unsigned int* p_toff;     // per pair: first task (i-tile) number, exclusive prefix
   unsigned int* s_toff;     // per self: first task number
+  unsigned int* p_task;     // per pair task: its pair
+  unsigned int* s_task;     // per self task: its self
   int* counts;              // [0] selfs, [1] pairs, [2] queue 0 size, [3] queue 1 size, [4] sort segments,
                             // [5] sort entries, [6] pair tasks, [7] self tasks
 };

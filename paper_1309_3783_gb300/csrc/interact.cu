@@ -108,22 +108,24 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
   return r;
 }
 
+// Per warp: the staged partners (p, a, g, act) and the warp's own cluster (ip).
 struct DensShared {
-  float4 p[32];     // position, H^2 (units of L; H^2 = -1 marks an empty slot)
-  float4 a[32];     // 1/H, band, m, H (physical)
-  float4 acc[32];   // sum m w, sum m q w', sum w, sum q w'
-  unsigned int cnt[32];
+  float4 p[32];     // partner position, H^2 (units of L; H^2 = -1 marks an empty slot)
+  float4 a[32];     // partner 1/H, band, m, H (physical)
   int g[32];
   unsigned char act[32];
+  float4 ip[32];    // own cluster: position, m
 };
 
 __device__ __forceinline__ void dens_put(DensShared& S, int lane, const DensI& j) {
   S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.H2);
   S.a[lane] = make_float4(j.invH, j.band, j.m, j.Hphys);
-  S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-  S.cnt[lane] = 0;
   S.g[lane] = j.g;
   S.act[lane] = j.act ? 1 : 0;
+}
+
+__device__ __forceinline__ void dens_stage_own(DensShared& S, int lane, const DensI& i) {
+  S.ip[lane] = make_float4(i.p.x, i.p.y, i.p.z, i.m);
 }
 
 struct Counters {
@@ -214,14 +216,17 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
   return r;
 }
 
+// Per warp: the staged partners (p, a, v, f, g) and the warp's own cluster
+// (ip, iv, if_).
 struct ForceShared {
-  float4 p[32];    // position, H^2
-  float4 a[32];    // 1/H, band, m, H (physical)
-  float4 v[32];    // velocity, rho
-  float4 f[32];    // f P / rho^2, c, K/H^4, -
-  float4 acc[32];  // a (3), du/dt
-  float vs[32];
+  float4 p[32];    // partner position, H^2
+  float4 a[32];    // partner 1/H, band, m, H (physical)
+  float4 v[32];    // partner velocity, rho
+  float4 f[32];    // partner f P / rho^2, c, K/H^4, -
   int g[32];
+  float4 ip[32];   // own cluster: position, m
+  float4 iv[32];   // own cluster: velocity, rho
+  float4 if_[32];  // own cluster: 1/H, f P / rho^2, c, K/H^4
 };
 
 __device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
@@ -229,9 +234,13 @@ __device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI
   S.a[lane] = make_float4(j.invH, j.band, j.m, j.Hphys);
   S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
   S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
-  S.acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-  S.vs[lane] = 0.f;
   S.g[lane] = j.g;
+}
+
+__device__ __forceinline__ void force_stage_own(ForceShared& S, int lane, const ForceI& i) {
+  S.ip[lane] = make_float4(i.p.x, i.p.y, i.p.z, i.m);
+  S.iv[lane] = make_float4(i.v.x, i.v.y, i.v.z, i.rho);
+  S.if_[lane] = make_float4(i.invH, i.F, i.c, i.K4);
 }
 
 __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, float4* facc, float* fvsig) {
@@ -244,16 +253,21 @@ __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, floa
 // Up to 32 partners sit in shared memory: particles of one or several partner
 // clusters that passed a test against the box of the warp's cluster.  Phase 1:
 // every lane tests its particle i against the staged partners (broadcast
-// reads) and keeps two bitmasks, r < H_i and r < H_j, decided exactly.  Phase 2:
-// every lane walks
-// only its set bits; its own side accumulates in registers, the partner side in
-// shared memory with atomics (lanes may share a partner).  Invalid lanes sit at
-// 1e30 with H^2 = -1, so they never pass a test.
+// reads) and keeps two bitmasks, r < H_i and r < H_j, decided exactly.  Phase 2
+// runs two sweeps without atomics: in the row sweep every lane walks its own
+// bits and accumulates its own side; the r < H_j mask is then transposed with
+// ballots so that in the column sweep every staged partner walks the lanes it
+// interacts with and accumulates its side in registers, flushed once to global
+// memory.  Each in-reach pair is still found once and updates both sides.
+// Inside one cluster (own-only batches) every lane walks its full row for its
+// own side, which keeps the lanes balanced: each pair's two sides are then
+// computed by the two lanes concerned.  Invalid lanes sit at 1e30 with
+// H^2 = -1, so they never pass a test.
 
 // Phase 1: exact bitmasks of r < H_i (mI) and r < H_j (mJ) over the first n
-// staged partners (n a multiple of 4; slots past the batch hold empty entries).  The FP32 test decides outside a guard band around
-// H^2; bandJ bounds every partner's band; the few uncertain bits are decided in
-// FP64 afterwards.
+// staged partners (n a multiple of 4; slots past the batch hold empty entries).
+// The FP32 test decides outside a guard band around H^2; bandJ bounds every
+// partner's band; the few uncertain bits are decided in FP64 afterwards.
 template <class SH>
 __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iband, int ig, float iHphys,
                                            const SH& S, float bandJ, unsigned int allow, int n,
@@ -295,99 +309,184 @@ __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iba
   mJ &= allow;
 }
 
+// lane s receives the lanes whose mask has bit s (s < n)
+__device__ __forceinline__ unsigned int transpose_bits(unsigned int m, int n) {
+  const int lane = threadIdx.x & 31;
+  unsigned int col = 0;
+  for (int s = 0; s < n; ++s) {
+    const unsigned int b = __ballot_sync(0xffffffffu, (m >> s) & 1u);
+    if (lane == s) col = b;
+  }
+  return col;
+}
+
+// One density contribution: w and q w'(q) at q = r / H, weighted by m.
+__device__ __forceinline__ void dens_add(float r, float invH, float m, float4& acc, unsigned int& cnt) {
+  float w, dw;
+  const float q = r * invH;
+  spline_w_dw(q, w, dw);
+  const float gg = q * dw;                 // q w'(q) = r dW/dr in units of W
+  acc.x = fmaf(m, w, acc.x);
+  acc.y = fmaf(m, gg, acc.y);
+  acc.z += w;
+  acc.w += gg;
+  cnt++;
+}
+
+// Density batch: own side for r < H_i (active i), partner side for r < H_j
+// (active j) unless own_only.  cmask selects the bits the counters count (the
+// upper triangle inside one cluster, where every pair appears in both rows).
 template <bool COUNT>
 __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigned int allow, unsigned int jvalid,
-                                          unsigned int jact, float bandJ, int n, float4& acc, unsigned int& cnt,
-                                          const unsigned int* perm, const double* x, const ItemGeom& g,
+                                          unsigned int jact, float bandJ, int n, bool own_only, unsigned int cmask,
+                                          float4& acc, unsigned int& cnt, const unsigned int* perm,
+                                          const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
                                           Counters& C) {
+  const int lane = threadIdx.x & 31;
   unsigned int mI, mJ, rc = 0;
   pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
-  const unsigned int ui = I.act ? mI : 0u, uj = mJ & jact;
+  const unsigned int ui = I.act ? mI : 0u, uj = own_only ? 0u : (mJ & jact);
   if (COUNT) {
-    C.cand += I.valid ? __popc(allow & jvalid) : 0u;
+    C.cand += I.valid ? __popc(allow & jvalid & cmask) : 0u;
     C.rechecks += rc;
-    C.pairs += __popc(ui | uj);
+    C.pairs += __popc((ui | (mJ & jact)) & cmask);
     C.sides += __popc(ui) + __popc(uj);
   }
-  unsigned int m = ui | uj;
-  while (m) {
+  // row sweep: own side
+  for (unsigned int m = ui; m; m &= m - 1) {
     const int sj = __ffs(m) - 1;
-    m &= m - 1;
     const float4 J = S.p[sj];
     const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
-    const float r = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-    if ((ui >> sj) & 1u) {
-      float w, dw;
-      const float q = r * I.invH;
-      spline_w_dw(q, w, dw);
-      const float gg = q * dw;                 // q w'(q) = r dW/dr in units of W
-      acc.x = fmaf(S.a[sj].z, w, acc.x);
-      acc.y = fmaf(S.a[sj].z, gg, acc.y);
-      acc.z += w;
-      acc.w += gg;
-      cnt++;
+    dens_add(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), I.invH, S.a[sj].z, acc, cnt);
+  }
+  if (own_only) return;
+  // column sweep: partner side, staged partner = lane
+  unsigned int col = transpose_bits(uj, n);
+  if (col) {
+    const float4 J = S.p[lane];
+    const float jinvH = S.a[lane].x;
+    float4 pacc = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned int pcnt = 0;
+    for (; col; col &= col - 1) {
+      const int li = __ffs(col) - 1;
+      const float4 P = S.ip[li];
+      const float dx = P.x - J.x, dy = P.y - J.y, dz = P.z - J.z;
+      dens_add(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), jinvH, P.w, pacc, pcnt);
     }
-    if ((uj >> sj) & 1u) {
-      float w, dw;
-      const float q = r * S.a[sj].x;
-      spline_w_dw(q, w, dw);
-      const float gg = q * dw;
-      atomicAdd(&S.acc[sj].x, I.m * w);
-      atomicAdd(&S.acc[sj].y, I.m * gg);
-      atomicAdd(&S.acc[sj].z, w);
-      atomicAdd(&S.acc[sj].w, gg);
-      atomicAdd(&S.cnt[sj], 1u);
-    }
+    flush_dens(S.g[lane], pacc, pcnt, dacc, dcnt);
   }
 }
 
+// One force pair seen from particle a (the side updated) with partner b:
+// d = x_a - x_b, r, the two kernel derivatives (zero where r is not below that
+// side's H), and the symmetric viscosity (Monaghan, alpha).  Adds to a's
+// acceleration -m_b coef d and to its du/dt m_b (f_a P_a/rho_a^2 W_a' + Pi Wbar/2) w.v,
+// keeping the largest signal velocity.
+struct ForceSide {
+  float3 p, v;
+  float rho, F, c, K4, invH, m;
+};
+
+__device__ __forceinline__ void force_add(const ForceSide& a, const ForceSide& b, bool fa, bool fb, float alpha,
+                                          float4& acc, float& vs) {
+  const float dx = a.p.x - b.p.x, dy = a.p.y - b.p.y, dz = a.p.z - b.p.z;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  if (!(r2 > 0.0f)) return;
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
+  float w, dwa = 0.0f, dwb = 0.0f;
+  if (fa) spline_w_dw(r * a.invH, w, dwa);
+  if (fb) spline_w_dw(r * b.invH, w, dwb);
+  const float Wa = a.K4 * dwa, Wb = b.K4 * dwb;
+  const float vdx = fmaf(a.v.x - b.v.x, dx, fmaf(a.v.y - b.v.y, dy, (a.v.z - b.v.z) * dz));
+  const float wv = vdx * rinv;
+  const float mu = fminf(wv, 0.0f);
+  const float vsig = a.c + b.c - 3.0f * mu;
+  const float Pi = -alpha * vsig * mu / (a.rho + b.rho);
+  const float Wbar = 0.5f * (Wa + Wb);
+  const float coef = fmaf(a.F, Wa, fmaf(b.F, Wb, Pi * Wbar)) * rinv;
+  const float hv = 0.5f * Pi * Wbar;
+  acc.x = fmaf(-b.m * coef, dx, acc.x);
+  acc.y = fmaf(-b.m * coef, dy, acc.y);
+  acc.z = fmaf(-b.m * coef, dz, acc.z);
+  acc.w = fmaf(b.m * fmaf(a.F, Wa, hv), wv, acc.w);
+  vs = fmaxf(vs, vsig);
+}
+
+__device__ __forceinline__ ForceSide side_of(const ForceI& I) {
+  ForceSide s;
+  s.p = I.p;
+  s.v = I.v;
+  s.rho = I.rho;
+  s.F = I.F;
+  s.c = I.c;
+  s.K4 = I.K4;
+  s.invH = I.invH;
+  s.m = I.m;
+  return s;
+}
+
+__device__ __forceinline__ ForceSide staged_side(const ForceShared& S, int k) {
+  const float4 P = S.p[k], A = S.a[k], V = S.v[k], F = S.f[k];
+  ForceSide s;
+  s.p = make_float3(P.x, P.y, P.z);
+  s.v = make_float3(V.x, V.y, V.z);
+  s.rho = V.w;
+  s.F = F.x;
+  s.c = F.y;
+  s.K4 = F.z;
+  s.invH = A.x;
+  s.m = A.z;
+  return s;
+}
+
+__device__ __forceinline__ ForceSide own_side(const ForceShared& S, int k) {
+  const float4 P = S.ip[k], V = S.iv[k], F = S.if_[k];
+  ForceSide s;
+  s.p = make_float3(P.x, P.y, P.z);
+  s.v = make_float3(V.x, V.y, V.z);
+  s.rho = V.w;
+  s.invH = F.x;
+  s.F = F.y;
+  s.c = F.z;
+  s.K4 = F.w;
+  s.m = P.w;
+  return s;
+}
+
+// Force batch: every pair with r < max(H_i, H_j); own side in the row sweep,
+// partner side in the column sweep unless own_only.
 template <bool COUNT>
 __device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsigned int allow, unsigned int jvalid,
-                                           float bandJ, int n, float4& acc, float& vsig_i, const unsigned int* perm,
-                                           const double* x, const ItemGeom& g, float alpha, Counters& C) {
+                                           float bandJ, int n, bool own_only, unsigned int cmask, float4& acc,
+                                           float& vsig_i, const unsigned int* perm, const double* x,
+                                           const ItemGeom& g, float alpha, float4* facc, float* fvsig,
+                                           Counters& C) {
+  const int lane = threadIdx.x & 31;
   unsigned int mI, mJ, rc = 0;
   pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
   if (COUNT) {
-    C.cand += I.valid ? __popc(allow & jvalid) : 0u;
+    C.cand += I.valid ? __popc(allow & jvalid & cmask) : 0u;
     C.rechecks += rc;
   }
-  unsigned int m = mI | mJ;
-  while (m) {
+  const ForceSide own = side_of(I);
+  for (unsigned int m = mI | mJ; m; m &= m - 1) {
     const int sj = __ffs(m) - 1;
-    m &= m - 1;
-    const float4 J = S.p[sj];
-    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    if (!(r2 > 0.0f)) continue;
-    if (COUNT) C.pairs++;
-    const float4 Ja = S.a[sj];
-    const float4 Jv = S.v[sj];
-    const float4 Jf = S.f[sj];
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    float w, dwi = 0.0f, dwj = 0.0f;
-    if ((mI >> sj) & 1u) spline_w_dw(r * I.invH, w, dwi);
-    if ((mJ >> sj) & 1u) spline_w_dw(r * Ja.x, w, dwj);
-    const float Wi = I.K4 * dwi, Wj = Jf.z * dwj;
-    const float vdx = fmaf(I.v.x - Jv.x, dx, fmaf(I.v.y - Jv.y, dy, (I.v.z - Jv.z) * dz));
-    const float wv = vdx * rinv;
-    const float mu = fminf(wv, 0.0f);
-    const float vsig = I.c + Jf.y - 3.0f * mu;
-    const float Pi = -alpha * vsig * mu / (I.rho + Jv.w);
-    const float Wbar = 0.5f * (Wi + Wj);
-    const float coef = fmaf(I.F, Wi, fmaf(Jf.x, Wj, Pi * Wbar)) * rinv;
-    const float hv = 0.5f * Pi * Wbar;
-    acc.x = fmaf(-Ja.z * coef, dx, acc.x);
-    acc.y = fmaf(-Ja.z * coef, dy, acc.y);
-    acc.z = fmaf(-Ja.z * coef, dz, acc.z);
-    acc.w = fmaf(Ja.z * fmaf(I.F, Wi, hv), wv, acc.w);
-    vsig_i = fmaxf(vsig_i, vsig);
-    const float mic = I.m * coef;
-    atomicAdd(&S.acc[sj].x, mic * dx);
-    atomicAdd(&S.acc[sj].y, mic * dy);
-    atomicAdd(&S.acc[sj].z, mic * dz);
-    atomicAdd(&S.acc[sj].w, I.m * fmaf(Jf.x, Wj, hv) * wv);
-    atomicMax(reinterpret_cast<unsigned int*>(&S.vs[sj]), __float_as_uint(vsig));
+    if (COUNT && ((cmask >> sj) & 1u)) C.pairs++;
+    force_add(own, staged_side(S, sj), (mI >> sj) & 1u, (mJ >> sj) & 1u, alpha, acc, vsig_i);
+  }
+  if (own_only) return;
+  unsigned int colI = transpose_bits(mI, n), colJ = transpose_bits(mJ, n);
+  unsigned int col = colI | colJ;
+  if (col) {
+    const ForceSide me = staged_side(S, lane);
+    float4 pacc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float pvs = 0.0f;
+    for (; col; col &= col - 1) {
+      const int li = __ffs(col) - 1;
+      force_add(me, own_side(S, li), (colJ >> li) & 1u, (colI >> li) & 1u, alpha, pacc, pvs);
+    }
+    flush_force(S.g[lane], pacc, pvs, facc, fvsig);
   }
 }
 
@@ -396,11 +495,11 @@ __device__ __forceinline__ unsigned int upper_mask(int lane) {
 }
 
 // One batch of q <= 32 staged partners (slots 0..q-1) against the warp's
-// cluster: empty the slots past the batch, run both phases over the first
-// q rounded up to 4, and flush the partners' shared-memory sums.  allow limits
-// the partners of each lane (the upper triangle inside one cluster).
+// cluster: empty the slots past the batch and run both phases over the first
+// q rounded up to 4.  own_only: the partners are the warp's own cluster (each
+// lane excludes itself and updates its own side only).
 template <bool COUNT>
-__device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsigned int q, unsigned int allow,
+__device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsigned int q, bool own_only,
                                            float4& acc, unsigned int& cnt, const unsigned int* perm,
                                            const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
                                            Counters& C) {
@@ -412,14 +511,14 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
   const unsigned int jact = __ballot_sync(0xffffffffu, v && S.act[lane]);
   const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
   __syncwarp();
-  dens_tile<COUNT>(I, S, allow & jvalid, jvalid, jact, bandJ, (int)((q + 3u) & ~3u), acc, cnt, perm, x, g, C);
-  __syncwarp();
-  if (v) flush_dens(S.g[lane], S.acc[lane], S.cnt[lane], dacc, dcnt);
+  const unsigned int allow = own_only ? jvalid & ~(1u << lane) : jvalid;
+  dens_tile<COUNT>(I, S, allow, jvalid, jact, bandJ, (int)((q + 3u) & ~3u), own_only,
+                   own_only ? upper_mask(lane) : 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
   __syncwarp();
 }
 
 template <bool COUNT>
-__device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, unsigned int q, unsigned int allow,
+__device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, unsigned int q, bool own_only,
                                             float4& acc, float& vsi, const unsigned int* perm, const double* x,
                                             const ItemGeom& g, float alpha, float4* facc, float* fvsig,
                                             Counters& C) {
@@ -430,13 +529,11 @@ __device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, uns
   const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
   const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
   __syncwarp();
-  force_tile<COUNT>(I, S, allow & jvalid, jvalid, bandJ, (int)((q + 3u) & ~3u), acc, vsi, perm, x, g, alpha, C);
-  __syncwarp();
-  if (v) flush_force(S.g[lane], S.acc[lane], S.vs[lane], facc, fvsig);
+  const unsigned int allow = own_only ? jvalid & ~(1u << lane) : jvalid;
+  force_tile<COUNT>(I, S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only,
+                    own_only ? upper_mask(lane) : 0xffffffffu, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
   __syncwarp();
 }
-
-
 
 // ------------------------------------------------------------- cluster geometry
 __device__ __forceinline__ float3 axis_unit_f(int a) {
@@ -590,6 +687,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
       const unsigned int ni = TL.n[ti];
       const bool vi = (unsigned int)lane < ni;
       const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
+      dens_stage_own(S, lane, I);
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned int cnt = 0, q = 0;
       for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
@@ -609,14 +707,14 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
           const unsigned int bal = __ballot_sync(0xffffffffu, pass);
           const unsigned int np = __popc(bal);
           if (q + np > 32u) {
-            dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+            dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
             q = 0;
           }
           if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
           q += np;
         }
       }
-      if (q) dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+      if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
       flush_dens(I.g, acc, cnt, dacc, dcnt);
     }
   }
@@ -658,11 +756,12 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
       const float Hi = TL.lo[ti].w * g.invL;
       const bool vi = (unsigned int)lane < TL.n[ti];
       const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
+      dens_stage_own(S, lane, I);
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       unsigned int cnt = 0, q = 0;
       // inside the cluster itself each unordered pair once: partners above the lane
       if (vi) dens_put(S, lane, I);
-      dens_batch<COUNT>(I, S, TL.n[ti], upper_mask(lane), acc, cnt, perm, x, g, dacc, dcnt, C);
+      dens_batch<COUNT>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
       // the later clusters of the cell, 32 box tests at a time
       for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
         const unsigned int tl = b0 + lane;
@@ -682,14 +781,14 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_
           const unsigned int bal = __ballot_sync(0xffffffffu, pass);
           const unsigned int np = __popc(bal);
           if (q + np > 32u) {
-            dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
+            dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
             q = 0;
           }
           if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
           q += np;
         }
       }
-      if (q) dens_batch<COUNT>(I, S, q, 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
+      if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
       flush_dens(I.g, acc, cnt, dacc, dcnt);
     }
   }
@@ -729,6 +828,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
       const float rhi_i = box_rhi(bi, P.u);
       const bool vi = (unsigned int)lane < TL.n[ti];
       const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
+      force_stage_own(S, lane, I);
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       float vsi = 0.0f;
       unsigned int q = 0;
@@ -748,14 +848,14 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
           const unsigned int bal = __ballot_sync(0xffffffffu, pass);
           const unsigned int np = __popc(bal);
           if (q + np > 32u) {
-            force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+            force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
             q = 0;
           }
           if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
           q += np;
         }
       }
-      if (q) force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+      if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
       flush_force(I.g, acc, vsi, facc, fvsig);
     }
   }
@@ -796,12 +896,13 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
       const float Hi = TL.lo[ti].w * g.invL;
       const bool vi = (unsigned int)lane < TL.n[ti];
       const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      force_stage_own(S, lane, I);
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
       float vsi = 0.0f;
       unsigned int q = 0;
       // inside the cluster itself each unordered pair once: partners above the lane
       if (vi) force_put(S, lane, I);
-      force_batch<COUNT>(I, S, TL.n[ti], upper_mask(lane), acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+      force_batch<COUNT>(I, S, TL.n[ti], true, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
       for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
         const unsigned int tl = b0 + lane;
         bool ok = false;
@@ -820,14 +921,14 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
           const unsigned int bal = __ballot_sync(0xffffffffu, pass);
           const unsigned int np = __popc(bal);
           if (q + np > 32u) {
-            force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+            force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
             q = 0;
           }
           if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
           q += np;
         }
       }
-      if (q) force_batch<COUNT>(I, S, q, 0xffffffffu, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+      if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
       flush_force(I.g, acc, vsi, facc, fvsig);
     }
   }

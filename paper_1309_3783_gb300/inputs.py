@@ -169,7 +169,7 @@ def gaussian_random_field(n_grid: int, index: float, rng) -> np.ndarray:
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (index / 4.0)  # sqrt(P) with P ~ k^index
-    g = np.fft.irfftn(fk * amp, s=(n_grid,) * 3)
+    g = np.fft.irfftn(fk * amp, s=(n_grid,) * 3, axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g

@@ -1,0 +1,108 @@
+"""Full-size variable-h workloads through the C-ABI, checked on local samples.
+
+The 8,388,608-particle log-normal box and the 33,554,432-particle clustered box
+(4096 Plummer spheres with scale radii from 1e-4 to 1e-2 over a uniform
+background) stand in for the paper's cosmological volume, whose smoothing
+lengths span three orders of magnitude.  The GPU iterates h from the first
+guess to N~ = 48 and then runs the force pass; the oracle takes the GPU's final
+h as its input, so that the neighbour predicate is identical on both sides, and
+is evaluated around a few sample centres.
+
+A sample is the k particles nearest to a centre (a randomly chosen particle, so
+dense regions are drawn in proportion to their mass).  Everything the oracle
+needs for those targets lies within R + 2 H_max of the centre (R the sample
+radius): their neighbours within max(H_i, H_j) and, for the force, those
+neighbours' own densities.  The oracle therefore runs on that sub-volume only.
+"""
+import numpy as np
+import pytest
+
+from oracle import sph as orc
+from paper_1309_3783_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1309_3783_gb300 import build, sph
+    build.build()
+    return sph
+
+
+def _min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def _samples(box, H, n_centres, k, seed):
+    """(targets, sub) per centre: the k nearest particles and the sub-volume the oracle needs."""
+    rng = np.random.default_rng(seed)
+    reach = 2.05 * float(H.max())
+    out = []
+    for c in rng.choice(box.n, n_centres, replace=False):
+        d = _min_image(box.x - box.x[c], box.L)
+        r = np.sqrt((d * d).sum(1))
+        targets = np.argpartition(r, k)[:k]
+        sub = np.nonzero(r <= r[targets].max() + reach)[0]
+        out.append((np.sort(targets), sub))
+    return out
+
+
+def _check_sampled(api, box, n_centres=6, k=64, seed=0):
+    p = api.sph_params_default()
+    ctx = api.sph_ctx_create(p, device=0)
+    try:
+        b = api.box_from(ctx, box)
+        try:
+            st, n_unconv, iters = b.h_update()
+            g = {f: b.get(f) for f in ("h", "count", "rho", "nw", "drho_dh", "nngb", "converged")}
+            b.force()
+            for f in ("a", "dudt", "vsig"):
+                g[f] = b.get(f)
+            cells = b.cells()
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(ctx)
+    assert n_unconv == 0 and g["converged"].all()
+    h = g["h"]
+    H = orc.support_radius(h)
+    print(f"{box.name}: h iterations {iters}, H in [{H.min():.3e}, {H.max():.3e}] "
+          f"(ratio {H.max() / H.min():.0f}), tree depth {int(cells['level'].max())}")
+    for targets, sub in _samples(box, H, n_centres, k, seed):
+        xs, Hs = box.x[sub], H[sub]
+        t = np.searchsorted(sub, targets)
+        ref = orc.density(xs, box.m[sub], Hs, box.L, True, targets=t, method="kdtree")
+        assert np.array_equal(g["count"][targets], ref["count"])
+        np.testing.assert_allclose(g["rho"][targets], ref["rho"], rtol=1e-5)
+        np.testing.assert_allclose(g["nw"][targets], ref["nw"], rtol=1e-5)
+        hh = h[targets].astype(np.float64)
+        assert np.all(np.abs(g["drho_dh"][targets] - orc.drho_dh(ref, hh)) <= 2e-5 * 3 * ref["rho"] / hh)
+        # self-consistency of the converged h, evaluated by the oracle (FP64)
+        assert np.all(np.abs(ref["Nw"] - orc.N_NGB) <= 1.05e-4 * orc.N_NGB)
+        # force: the partners' densities come from the oracle too
+        _, j, _, _ = orc.neighbour_pairs(xs, None, box.L, True, t, "force", Hall=Hs, method="kdtree")
+        need = np.unique(np.concatenate([t, j]))
+        dn = orc.density(xs, box.m[sub], Hs, box.L, True, targets=need, method="kdtree")
+        gh = orc.ghost(dn["rho"], dn["Sr_m"], box.u[sub][need])
+        full = {q: np.full(len(sub), np.nan) for q in ("rho", "P", "c", "f")}
+        full["rho"][need] = dn["rho"]
+        for q in ("P", "c", "f"):
+            full[q][need] = gh[q]
+        fo = orc.force(xs, box.v[sub], box.m[sub], Hs, full["rho"], full["P"], full["c"], full["f"], box.L, True,
+                       targets=t, method="kdtree")
+        rms = np.sqrt(np.mean(np.sum(fo["a"] ** 2, axis=1)))
+        assert np.max(np.abs(g["a"][targets] - fo["a"])) <= 1e-4 * rms
+        rms_u = np.sqrt(np.mean(fo["dudt"] ** 2))
+        assert np.max(np.abs(g["dudt"][targets] - fo["dudt"])) <= 1e-4 * rms_u
+        np.testing.assert_allclose(g["vsig"][targets], fo["vsig"], rtol=1e-5)
+
+
+def test_lognormal_8m_sampled(api):
+    """2^23 particles drawn from a log-normal field (sigma 2, P(k) ~ k^-2, 256^3 mesh)."""
+    _check_sampled(api, inputs.lognormal_box())
+
+
+def test_clustered_33m_sampled(api):
+    """2^25 particles: 30 % uniform, 70 % in 4096 Plummer spheres, scale radii 1e-4 to 1e-2."""
+    _check_sampled(api, inputs.clustered_box())

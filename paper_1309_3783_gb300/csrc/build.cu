@@ -708,6 +708,7 @@ __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict
     TL.leaf[t] = leaf;
     TL.lo[t] = lo;
     TL.hi[t] = hi;
+    TL.cen[t] = T.cen[leaf];
     TL.active[t] = 1;
   }
 }
@@ -779,7 +780,7 @@ __device__ __forceinline__ float3 axis_unit(int a) {
 // lower end of the projection on u of cluster t's box, in the frame of the cell
 // with centre cc (the leaf-to-cell offset is exact)
 __device__ __forceinline__ float tile_rlo(const Tiles& TL, const Tree& T, unsigned int t, float4 cc, float3 u) {
-  const float4 lc = T.cen[TL.leaf[t]];
+  const float4 lc = TL.cen[t];
   const float4 lo = TL.lo[t], hi = TL.hi[t];
   const float ox = lc.x - cc.x, oy = lc.y - cc.y, oz = lc.z - cc.z;
   const float x = (u.x >= 0.0f ? lo.x : hi.x) + ox;

@@ -225,12 +225,14 @@ sph_status Engine::ensure_particle_capacity() {
   CK(tl_leaf.reserve(n));
   CK(tl_lo.reserve(n));
   CK(tl_hi.reserve(n));
+  CK(tl_cen.reserve(n));
   CK(tl_active.reserve(n));
   TL.start = tl_start.p;
   TL.n = tl_n.p;
   TL.leaf = tl_leaf.p;
   TL.lo = tl_lo.p;
   TL.hi = tl_hi.p;
+  TL.cen = tl_cen.p;
   TL.active = tl_active.p;
   CK(dacc.reserve(n));
   CK(dcnt.reserve(n));
@@ -536,8 +538,13 @@ sph_status Engine::build_once(bool* retry) {
   n_big_entries = bc[1];
   CK(l_ptask.reserve(std::max(lc[6], 1)));
   CK(l_stask.reserve(std::max(lc[7], 1)));
+  CK(l_plive.reserve(std::max(lc[6], 1)));
+  CK(l_nlive.reserve(1));
+  n_ptasks = lc[6];
   Lq.p_task = l_ptask.p;
   Lq.s_task = l_stask.p;
+  Lq.p_live = l_plive.p;
+  Lq.n_live = l_nlive.p;
   launch_task_items(*this);
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));

@@ -76,13 +76,34 @@ struct DensI {
   bool valid, act;
 };
 
-__device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
-                                           const float4* cen4, const unsigned char* act, float invL, float e) {
+// The raw loads of one particle, issued ahead of their use (see the pair kernel).
+struct DensRaw {
+  float4 p, c;
+  unsigned char a;
+};
+
+__device__ __forceinline__ DensRaw fetch_dens(bool valid, unsigned int gidx, const float4* pos4, const float4* cen4,
+                                              const unsigned char* act) {
+  DensRaw r;
+  if (valid) {
+    r.p = pos4[gidx];
+    r.c = cen4[gidx];
+    r.a = act[gidx];
+  } else {
+    r.p = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.c = r.p;
+    r.a = 0;
+  }
+  return r;
+}
+
+__device__ __forceinline__ DensI make_dens(bool valid, unsigned int gidx, const DensRaw& raw, float3 shift,
+                                           float invL, float e) {
   DensI r;
   r.valid = valid;
   if (valid) {
-    const float4 p = pos4[gidx];
-    const float4 c = cen4[gidx];
+    const float4 p = raw.p;
+    const float4 c = raw.c;
     // the cell offsets (c + shift) are exact dyadic values: add them first, round once
     r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
     const float H = p.w * invL;
@@ -93,7 +114,7 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
     r.Hphys = p.w;
     r.m = c.w;
     r.g = (int)gidx;
-    r.act = act[gidx] != 0;
+    r.act = raw.a != 0;
   } else {
     r.p = make_float3(1e30f, 1e30f, 1e30f);
     r.H = 0.0f;
@@ -106,6 +127,11 @@ __device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3
     r.act = false;
   }
   return r;
+}
+
+__device__ __forceinline__ DensI load_dens(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
+                                           const float4* cen4, const unsigned char* act, float invL, float e) {
+  return make_dens(valid, gidx, fetch_dens(valid, gidx, pos4, cen4, act), shift, invL, e);
 }
 
 // Per warp: the staged partners (p, a, g, act) and the warp's own cluster (ip).
@@ -551,7 +577,7 @@ struct Box3 {
 // box of cluster t in the frame whose origin sits at -off from the leaf frame:
 // box + (leaf centre + off), the offset being exact (dyadic)
 __device__ __forceinline__ Box3 tile_box3(const Tiles& TL, const Tree& T, unsigned int t, float3 off) {
-  const float4 lc = T.cen[TL.leaf[t]];
+  const float4 lc = TL.cen[t];
   const float4 lo = TL.lo[t], hi = TL.hi[t];
   const float ox = lc.x + off.x, oy = lc.y + off.y, oz = lc.z + off.z;
   Box3 b;
@@ -666,23 +692,20 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   DensShared& S = SH[wl];
   Counters C;
-  const unsigned int ntask = (unsigned int)Lq.counts[6];
+  const unsigned int ntask = *Lq.n_live;
   unsigned int raw = 0;
   if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
   for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
     if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
     const unsigned int tend = min(base + TASK_CHUNK, ntask);
     for (unsigned int t = base; t < tend; ++t) {
-      const int item = (int)Lq.p_task[t];
-      const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
-      if (!(T.active[A0] | T.active[B0])) continue;          // no particle of either cell still iterating h
-      const unsigned int ti = T.tile0[A0] + (t - Lq.p_toff[item]);
+      const uint2 lt = Lq.p_live[t];
+      const int item = (int)lt.x;
+      const unsigned int ti = lt.y;
       const bool i_active = TL.active[ti] != 0;
-      if (!i_active && !T.active[B0]) continue;
       const PairSetup P = pair_setup(Lq, T, box, item);
       const Box3 bi = tile_box3(TL, T, ti, P.tshA);
       const float Hi = TL.lo[ti].w * P.g.invL;
-      if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;   // cluster out of reach of B
       const float rhi_i = box_rhi(bi, P.u);
       const unsigned int ni = TL.n[ti];
       const bool vi = (unsigned int)lane < ni;
@@ -696,12 +719,29 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_
         unsigned int mask =
             scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &jn, &js, &stop);
         if (stop) break;
-        while (mask) {
+        // the loads of the next candidate cluster are issued before the current
+        // one is tested, so that their latency overlaps that work
+        bool nv = false;
+        unsigned int ng = 0;
+        DensRaw nr;
+        if (mask) {
           const int k = __ffs(mask) - 1;
+          nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+          ng = __shfl_sync(0xffffffffu, js, k) + lane;
+          nr = fetch_dens(nv, ng, pos4, cen4, act);
+        }
+        while (mask) {
           mask &= mask - 1;
-          const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
-          const DensI J = load_dens(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, act, P.g.invL,
-                                    P.g.e);
+          const bool vj = nv;
+          const unsigned int gj = ng;
+          const DensRaw cr = nr;
+          if (mask) {
+            const int k = __ffs(mask) - 1;
+            nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+            ng = __shfl_sync(0xffffffffu, js, k) + lane;
+            nr = fetch_dens(nv, ng, pos4, cen4, act);
+          }
+          const DensI J = make_dens(vj, gj, cr, P.shB, P.g.invL, P.g.e);
           // stage only the partners within reach of the cluster's box
           const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
           const unsigned int bal = __ballot_sync(0xffffffffu, pass);
@@ -812,19 +852,19 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pa
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   ForceShared& S = SH[wl];
   Counters C;
-  const unsigned int ntask = (unsigned int)Lq.counts[6];
+  const unsigned int ntask = *Lq.n_live;
   unsigned int raw = 0;
   if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
   for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
     if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
     const unsigned int tend = min(base + TASK_CHUNK, ntask);
     for (unsigned int t = base; t < tend; ++t) {
-      const int item = (int)Lq.p_task[t];
+      const uint2 lt = Lq.p_live[t];
+      const int item = (int)lt.x;
+      const unsigned int ti = lt.y;
       const PairSetup P = pair_setup(Lq, T, box, item);
-      const unsigned int ti = T.tile0[P.A] + (t - Lq.p_toff[item]);
       const Box3 bi = tile_box3(TL, T, ti, P.tshA);
       const float Hi = TL.lo[ti].w * P.g.invL;
-      if (box_gap(bi, P.cellB) > fmaxf(Hi, P.HmB) + P.slack) continue;
       const float rhi_i = box_rhi(bi, P.u);
       const bool vi = (unsigned int)lane < TL.n[ti];
       const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
@@ -933,6 +973,39 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_se
     }
   }
   commit_counters<COUNT>(C, pc, 3);
+}
+
+// Pair tasks of one pass that have work, as (pair, cluster): in a density pass
+// those whose cluster or partner cell still iterates h, and in every pass
+// those whose cluster lies within reach of the partner cell (the same test the
+// sweep would start with).  One thread per task; warp-aggregated appends.
+template <bool DENS>
+__global__ void k_live_pair_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long ntask) {
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < ntask; b0 += stride) {
+    const long long t = b0 + threadIdx.x;
+    bool live = false;
+    int item = 0;
+    unsigned int ti = 0;
+    if (t < ntask) {
+      item = (int)Lq.p_task[t];
+      const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
+      ti = T.tile0[A0] + ((unsigned int)t - Lq.p_toff[item]);
+      live = !DENS || TL.active[ti] || T.active[B0];
+      if (live) {
+        const PairSetup P = pair_setup(Lq, T, box, item);
+        const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+        const float Hi = TL.lo[ti].w * P.g.invL;
+        live = box_gap(bi, P.cellB) <= fmaxf(Hi, P.HmB) + P.slack;
+      }
+    }
+    const unsigned int bal = __ballot_sync(0xffffffffu, live);
+    unsigned int at = 0;
+    if (lane == 0 && bal) at = atomicAdd(Lq.n_live, (unsigned int)__popc(bal));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (live) Lq.p_live[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned int)item, ti);
+  }
 }
 
 // =========================================================================== ghost
@@ -1250,7 +1323,17 @@ static int resident_ctas(const void* fn) {
   return 4;
 }
 
+void launch_live_pair_tasks(Engine& E, bool dens) {
+  cudaMemsetAsync(E.Lq.n_live, 0, sizeof(unsigned int), E.st);
+  if (E.n_ptasks == 0) return;
+  const int grid = (int)std::min<long long>((E.n_ptasks + 255) / 256, (long long)E.nsm * 16);
+  if (dens) k_live_pair_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks);
+  else k_live_pair_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks);
+  count_launch();
+}
+
 void launch_density_pair(Engine& E) {
+  launch_live_pair_tasks(E, true);
   const auto k = E.count_pairs ? k_density_pair<true> : k_density_pair<false>;
   cudaMemsetAsync(E.task_ctr.p + 0, 0, sizeof(unsigned int), E.st);
   k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
@@ -1269,6 +1352,7 @@ void launch_density_self(Engine& E) {
 }
 
 void launch_force_pair(Engine& E) {
+  launch_live_pair_tasks(E, false);
   const auto k = E.count_pairs ? k_force_pair<true> : k_force_pair<false>;
   cudaMemsetAsync(E.task_ctr.p + 2, 0, sizeof(unsigned int), E.st);
   k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(

@@ -135,7 +135,7 @@ class Engine {
 
   // clusters (capacity N)
   DBuf<unsigned int> tl_start, tl_n, tl_leaf;
-  DBuf<float4> tl_lo, tl_hi;
+  DBuf<float4> tl_lo, tl_hi, tl_cen;
   DBuf<unsigned char> tl_active;
   Tiles TL{};
   long long n_tiles = 0;
@@ -155,7 +155,9 @@ class Engine {
   // interaction lists
   int cap_self = 0, cap_pair = 0, cap_queue = 0;
   DBuf<int> l_self, l_pa, l_pb, l_pax, l_counts;
-  DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp, l_ptask, l_stask;
+  DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp, l_ptask, l_stask, l_nlive;
+  DBuf<uint2> l_plive;
+  long long n_ptasks = 0;
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
   Lists Lq{};
 

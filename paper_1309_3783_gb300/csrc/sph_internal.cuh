@@ -187,6 +187,7 @@ struct Tiles {
   unsigned int* leaf;       // leaf cell
   float4* lo;               // box minimum relative to the leaf centre (units of L); w: max H (physical)
   float4* hi;               // box maximum relative to the leaf centre (units of L)
+  float4* cen;              // the leaf's centre (as Tree::cen)
   unsigned char* active;    // 1 when a particle inside still iterates h
 };
 
@@ -204,6 +205,8 @@ struct Lists {
   unsigned int* s_toff;     // per self: first task number
   unsigned int* p_task;     // per pair task: its pair
   unsigned int* s_task;     // per self task: its self
+  uint2* p_live;            // pair tasks of the current pass that have work: (pair, cluster)
+  unsigned int* n_live;     // their number
   int* counts;              // [0] selfs, [1] pairs, [2] queue 0 size, [3] queue 1 size, [4] sort segments,
                             // [5] sort entries, [6] pair tasks, [7] self tasks
 };

@@ -16,6 +16,16 @@ e2e   : the same through the C-ABI with host buffers: every step uploads the ful
         state (x, v, m, u, h, a, du/dt) from pinned host memory and reads the new
         state back (x, v, u, h, a, du/dt) inside the timed region.
 
+serving: the served batch -- 512 independent jittered-lattice boxes with
+        particle counts log-uniform in [1k, 262k] (per-box seeds), each request
+        advancing 10 kick-drift-kick steps -- through the continuous-batching
+        server.  A saturated run (every request submitted at once) measures the
+        capacity; a run with Poisson arrivals at 80 % of that capacity gives the
+        p50/p99 step latency (CUDA events around every batched step, one sample
+        per box and step), the request latency and the aggregate throughput.  The
+        same requests on a 1-in-8 subset also run one box at a time through the
+        plain single-box path for comparison with the batched server.
+
 ``--impl reference`` times the FP64 oracle (the only reference this method has:
 the paper publishes no code) on the host cores, on a bounded sample of the same
 workload per step.  Under torchrun (N > 1) every rank runs an independent replica
@@ -280,12 +290,98 @@ def run_ours(args, rank, world, local_rank):
         "h_iterations_last_step": b.stats()["h_iterations"],
     }
     b.close()
+    if not args.no_serving:
+        out["serving"] = run_serving(sph, ctx)
     sph.sph_ctx_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(box)
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+# ------------------------------------------------------------------ serving
+SERVE_STEPS = 10
+SERVE_LOAD = 0.8
+
+
+def _served_requests(n_boxes):
+    """(box, dt) per request: C_CFL x min H / (2 c) at the initial state (u = 1)."""
+    out = []
+    for bx in inputs.served_boxes(n_boxes):
+        c = np.sqrt(5.0 / 3.0 * (5.0 / 3.0 - 1.0) * float(bx.u.max()))
+        out.append((bx, 0.3 * 1.825742 * float(bx.h.min()) / (2.0 * c)))
+    return out
+
+
+def _serve(sph, ctx, reqs, arrivals=None):
+    """Run requests through one server; returns (wall s, step ms list, request latencies s)."""
+    srv = sph.sph_server_create(ctx, 0, 0)
+    try:
+        order = np.argsort(arrivals) if arrivals is not None else np.arange(len(reqs))
+        ids, t_sub = {}, {}
+        k = 0
+        done_t = {}
+        t0 = time.perf_counter()
+        while len(done_t) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(reqs) and (arrivals is None or arrivals[order[k]] <= now):
+                bx, dt = reqs[order[k]]
+                ids[order[k]] = sph.sph_server_submit(srv, bx.x, bx.v, bx.m, bx.u, bx.h, bx.L, True, SERVE_STEPS, dt)
+                t_sub[order[k]] = t0 + (arrivals[order[k]] if arrivals is not None else 0.0)
+                k += 1
+            active = sph.sph_server_tick(srv)
+            tnow = time.perf_counter()
+            for r, rid in ids.items():
+                if r not in done_t and sph.sph_server_poll(srv, rid)[0]:
+                    done_t[r] = tnow
+            if active == 0 and k < len(reqs) and arrivals is not None:
+                time.sleep(max(0.0, min(0.002, arrivals[order[k]] - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        step_ms = []
+        for r, rid in ids.items():
+            step_ms.extend(sph.sph_server_poll(srv, rid, SERVE_STEPS)[1].tolist())
+            sph.sph_server_release(srv, rid)
+        lat = [done_t[r] - t_sub[r] for r in ids]
+        return wall, step_ms, lat
+    finally:
+        sph.sph_server_destroy(srv)
+
+
+def run_serving(sph, ctx, n_boxes=512):
+    reqs = _served_requests(n_boxes)
+    work = sum(bx.n for bx, _ in reqs) * SERVE_STEPS
+    mean_n = work / SERVE_STEPS / len(reqs)
+    wall_sat, _, _ = _serve(sph, ctx, reqs)                 # saturated: every request at once
+    capacity = work / wall_sat
+    rate = SERVE_LOAD * capacity / (mean_n * SERVE_STEPS)  # requests per second
+    arrivals = inputs.poisson_arrivals(len(reqs), rate, seed=1)
+    wall, step_ms, lat = _serve(sph, ctx, reqs, arrivals)
+    # the same requests on a 1-in-8 subset: batched server against one box at a time
+    sub = reqs[::8]
+    sub_work = sum(bx.n for bx, _ in sub) * SERVE_STEPS
+    wall_b, _, _ = _serve(sph, ctx, sub)
+    t0 = time.perf_counter()
+    for bx, dt in sub:
+        b = sph.box_from(ctx, bx)
+        b.h_update()
+        b.force()
+        for _ in range(SERVE_STEPS):
+            b.step(dt)
+        b.get("rho")
+        b.close()
+    wall_1 = time.perf_counter() - t0
+    pct = lambda a, q: float(np.percentile(np.asarray(a), q))
+    return {
+        "workload": f"{len(reqs)} jittered-lattice boxes, 1k-262k particles (mean {mean_n:.0f}), "
+                    f"{SERVE_STEPS} kick-drift-kick steps each, Poisson arrivals at {SERVE_LOAD:.0%} of capacity",
+        "p50_step_ms": pct(step_ms, 50), "p99_step_ms": pct(step_ms, 99),
+        "p50_request_s": pct(lat, 50), "p99_request_s": pct(lat, 99),
+        "throughput": work / wall, "unit": UNIT, "capacity": capacity, "arrival_rate_per_s": rate,
+        "step_samples": len(step_ms),
+        "batched_vs_single_box": {"boxes": len(sub), "batched": sub_work / wall_b, "single_box": sub_work / wall_1,
+                                  "unit": UNIT},
+    }
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -352,6 +448,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="keep the paper's leaf_max = 400")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-batch latency run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

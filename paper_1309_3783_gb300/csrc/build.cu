@@ -74,6 +74,42 @@ __global__ void k_keys(long long N, int dcap, const int* __restrict__ bid, const
   }
 }
 
+// box of every particle from the box offsets (off[0..nbox], off[nbox] = N)
+__global__ void k_box_ids(long long N, int nbox, const long long* __restrict__ off, int* __restrict__ bid) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= p) lo = mid;
+      else hi = mid - 1;
+    }
+    bid[p] = lo;
+  }
+}
+
+// Moves of input-order state for a new box layout: block row y moves
+// tab[3y + 2] particles from offset tab[3y + 1] to offset tab[3y].
+__global__ void k_relayout(const long long* __restrict__ tab, const double* __restrict__ x,
+                           const float* __restrict__ v, const float* __restrict__ m, const float* __restrict__ u,
+                           const float* __restrict__ h, const float4* __restrict__ a, double* __restrict__ nx,
+                           float* __restrict__ nv, float* __restrict__ nm, float* __restrict__ nu,
+                           float* __restrict__ nh, float4* __restrict__ na) {
+  const long long dst = tab[3 * blockIdx.y], src = tab[3 * blockIdx.y + 1], n = tab[3 * blockIdx.y + 2];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long s = src + q, d = dst + q;
+    nx[3 * d] = x[3 * s];
+    nx[3 * d + 1] = x[3 * s + 1];
+    nx[3 * d + 2] = x[3 * s + 2];
+    nv[3 * d] = v[3 * s];
+    nv[3 * d + 1] = v[3 * s + 1];
+    nv[3 * d + 2] = v[3 * s + 2];
+    nm[d] = m[s];
+    nu[d] = u[s];
+    nh[d] = h[s];
+    na[d] = a[s];
+  }
+}
+
 // ============================================================== radix sort
 // Stable LSD radix sort of (64-bit key, 32-bit value), 8-bit digits.  Each
 // pass: per-tile digit histograms, one exclusive scan of the digit-major

@@ -15,6 +15,9 @@ namespace sph {
 __global__ void k_ingest(long long, const int*, BoxDesc*, const double*, const float*, const float*, const float*,
                          const float*, float, float*);
 __global__ void k_keys(long long, int, const int*, const BoxDesc*, const double*, unsigned long long*, unsigned int*);
+__global__ void k_box_ids(long long, int, const long long*, int*);
+__global__ void k_relayout(const long long*, const double*, const float*, const float*, const float*, const float*,
+                           const float4*, double*, float*, float*, float*, float*, float4*);
 __global__ void k_gather_sorted(long long, const unsigned int*, const float*, const float*, const float*, float*,
                                 float4*);
 __global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned long long*, Tree, int, int*,
@@ -179,11 +182,51 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
   built = have_density = have_ghost = have_force = have_acc = false;
   sph_status s = ensure_particle_capacity();
   if (s != SPH_OK) return s;
-  std::vector<int> hb(N);
-  for (int b = 0; b < nbox; ++b)
-    for (long long p = off[b]; p < off[b + 1]; ++p) hb[p] = b;
-  CK(cudaMemcpyAsync(bid.p, hb.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(boff.reserve(nbox + 1));
+  CK(cudaMemcpyAsync(boff.p, off.data(), (nbox + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
+  k_box_ids<<<grid(N), 256, 0, st>>>(N, nbox, boff.p, bid.p); count_launch();
   CK(cudaStreamSynchronize(st));
+  return SPH_OK;
+}
+
+sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector<int>& src) {
+  if (src.size() != boxes.size()) return fail(SPH_E_INVALID, "relayout: one source per box");
+  long long nN = 0, maxn = 0;
+  std::vector<long long> tab;   // (destination offset, source offset, count) per moved box
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const int sb = src[b];
+    if (sb >= 0) {
+      if (sb >= nbox || spec[sb].n != boxes[b].n) return fail(SPH_E_INVALID, "relayout: source box mismatch");
+      tab.push_back(nN);
+      tab.push_back(off[sb]);
+      tab.push_back(boxes[b].n);
+      maxn = std::max(maxn, boxes[b].n);
+    }
+    nN += boxes[b].n;
+  }
+  const size_t n = (size_t)std::max<long long>(nN, 1);
+  CK(rl_x.reserve(3 * n));
+  CK(rl_v.reserve(3 * n));
+  CK(rl_m.reserve(n));
+  CK(rl_u.reserve(n));
+  CK(rl_h.reserve(n));
+  CK(rl_a.reserve(n));
+  const int nmove = (int)(tab.size() / 3);
+  if (nmove > 0) {
+    CK(rl_tab.reserve(tab.size()));
+    CK(cudaMemcpyAsync(rl_tab.p, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    const dim3 g((unsigned)std::min<long long>((maxn + 255) / 256, 64), (unsigned)nmove);
+    k_relayout<<<g, 256, 0, st>>>(rl_tab.p, x.p, v.p, m.p, u.p, h.p, a_in.p, rl_x.p, rl_v.p, rl_m.p, rl_u.p, rl_h.p,
+                                  rl_a.p); count_launch();
+  }
+  sph_status s = set_boxes(boxes);
+  if (s != SPH_OK) return s;
+  x.swap(rl_x);
+  v.swap(rl_v);
+  m.swap(rl_m);
+  u.swap(rl_u);
+  h.swap(rl_h);
+  a_in.swap(rl_a);
   return SPH_OK;
 }
 

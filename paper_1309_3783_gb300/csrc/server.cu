@@ -7,7 +7,10 @@
 // Admission is by device footprint against a byte budget and by a box count
 // limit; waiting requests are admitted in submission order as finished boxes
 // retire (continuous batching).  A box's first tick computes its starting
-// forces; each further tick is one kick-drift-kick step of its own dt.
+// forces; each further tick is one kick-drift-kick step of its own dt.  When
+// the resident set changes, the boxes that stay keep their state on the device:
+// the engine moves it to the new layout with one kernel, and only the new
+// boxes are copied in from the host.
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -28,7 +31,6 @@ struct Request {
   long long n = 0;
   std::vector<double> x;
   std::vector<float> v, m, u, h;
-  std::vector<float> acc;   // a (3) and du/dt per particle, once started
   int n_steps = 0, done_steps = 0;
   double dt = 0.0;
   bool started = false;
@@ -59,7 +61,7 @@ struct sph_server {
   std::map<long long, Request> reqs;
   std::deque<long long> waiting;
   std::vector<long long> resident;
-  bool dirty = true;
+  std::vector<long long> layout;   // the boxes in the engine, in its order
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   std::string err;
 };
@@ -71,49 +73,33 @@ static sph_status srv_fail(sph_server* s, sph_status st, const std::string& m) {
   return st;
 }
 
-// Copy the device state of every resident box back to its request.
-static sph_status save_resident(sph_server* s) {
+// Bring the engine's box layout to the resident set: boxes that stay move on
+// the device, new boxes are copied from their requests.
+static sph_status apply_layout(sph_server* s) {
   sph::Engine& E = *s->eng;
-  for (size_t b = 0; b < s->resident.size(); ++b) {
-    Request& r = s->reqs[s->resident[b]];
-    const long long o = E.off[b];
-    cudaMemcpyAsync(r.x.data(), E.x.p + 3 * o, 3 * r.n * sizeof(double), cudaMemcpyDeviceToHost, s->st);
-    cudaMemcpyAsync(r.v.data(), E.v.p + 3 * o, 3 * r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
-    cudaMemcpyAsync(r.u.data(), E.u.p + o, r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
-    cudaMemcpyAsync(r.h.data(), E.h.p + o, r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
-    if (r.started) {
-      r.acc.resize(4 * r.n);
-      cudaMemcpyAsync(r.acc.data(), E.a_in.p + o, 4 * r.n * sizeof(float), cudaMemcpyDeviceToHost, s->st);
-    }
-  }
-  if (cudaStreamSynchronize(s->st) != cudaSuccess) return srv_fail(s, SPH_E_CUDA, "saving resident boxes failed");
-  return SPH_OK;
-}
-
-static sph_status load_resident(sph_server* s) {
   std::vector<sph::BoxSpec> spec;
+  std::vector<int> src;
   for (long long id : s->resident) {
     const Request& r = s->reqs[id];
     spec.push_back(sph::BoxSpec{r.L, r.n, r.periodic});
+    int from = -1;
+    for (size_t k = 0; k < s->layout.size(); ++k)
+      if (s->layout[k] == id) from = (int)k;
+    src.push_back(from);
   }
-  sph::Engine& E = *s->eng;
-  sph_status st = E.set_boxes(spec);
+  sph_status st = E.relayout(spec, src);
   if (st != SPH_OK) return srv_fail(s, st, E.err);
-  bool all_started = true;
   for (size_t b = 0; b < s->resident.size(); ++b) {
+    if (src[b] >= 0) continue;
     Request& r = s->reqs[s->resident[b]];
     st = E.set_particles((int)b, r.x.data(), r.v.data(), r.m.data(), r.u.data(), r.h.data(), SPH_MEM_HOST);
     if (st != SPH_OK) return srv_fail(s, st, E.err);
-    if (r.started)
-      cudaMemcpyAsync(E.a_in.p + E.off[b], r.acc.data(), 4 * r.n * sizeof(float), cudaMemcpyHostToDevice, s->st);
-    else
-      cudaMemsetAsync(E.a_in.p + E.off[b], 0, 4 * r.n * sizeof(float), s->st);
-    all_started &= r.started;
+    cudaMemsetAsync(E.a_in.p + E.off[b], 0, r.n * sizeof(float4), s->st);
   }
   // starting forces of new boxes come from their first (dt = 0) tick; the kick of
   // every box reads a_in, so the engine never recomputes forces on its own
   E.have_acc = true;
-  (void)all_started;
+  s->layout = s->resident;
   return SPH_OK;
 }
 
@@ -196,24 +182,17 @@ sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
   while (!s->waiting.empty() && (int)s->resident.size() < s->max_boxes) {
     Request& r = s->reqs[s->waiting.front()];
     if (used + r.n * kBytesPerParticle > s->budget) break;
-    // the engine's layout still matches `resident` unless a box just retired
-    // (then the state was saved already)
-    if (!admitted && !s->resident.empty() && !s->dirty) {
-      sph_status st = save_resident(s);
-      if (st != SPH_OK) return st;
-    }
     admitted = true;
     used += r.n * kBytesPerParticle;
     r.state = 1;
     s->resident.push_back(r.id);
     s->waiting.pop_front();
   }
-  if (admitted) s->dirty = true;
+  (void)admitted;
   if (s->resident.empty()) return SPH_OK;
-  if (s->dirty) {
-    sph_status st = load_resident(s);
+  if (s->resident != s->layout) {
+    sph_status st = apply_layout(s);
     if (st != SPH_OK) return st;
-    s->dirty = false;
   }
   sph::Engine& E = *s->eng;
   for (size_t b = 0; b < s->resident.size(); ++b) {
@@ -240,9 +219,8 @@ sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
     if (r.done_steps >= r.n_steps) any_done = true;
   }
   if (any_done) {
-    // keep the state of the boxes that stay, return the finished ones
-    sph_status sv = save_resident(s);
-    if (sv != SPH_OK) return sv;
+    // return the finished boxes; the others stay on the device and move to the
+    // new layout at the next tick
     std::vector<long long> keep;
     for (size_t b = 0; b < s->resident.size(); ++b) {
       Request& r = s->reqs[s->resident[b]];
@@ -250,7 +228,6 @@ sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
       else keep.push_back(r.id);
     }
     s->resident = keep;
-    s->dirty = true;
   }
   return SPH_OK;
 }

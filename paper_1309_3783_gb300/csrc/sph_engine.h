@@ -76,6 +76,10 @@ class Engine {
 
   // ---- configuration -------------------------------------------------------
   sph_status set_boxes(const std::vector<BoxSpec>& boxes);   // (re)size for these boxes
+  // New box layout where box b takes over the input-order state (x, v, m, u, h,
+  // saved accelerations) of current box src[b], or starts empty (src[b] < 0)
+  // for set_particles to fill; the moves run on the device.
+  sph_status relayout(const std::vector<BoxSpec>& boxes, const std::vector<int>& src);
   // copy particle state of box b (host or device pointers)
   sph_status set_particles(int b, const double* x, const float* v, const float* m, const float* u, const float* h,
                            int mem);
@@ -120,6 +124,12 @@ class Engine {
   DBuf<float> H_in, hlo, hhi;
   DBuf<int> conv;                 // 1 when h converged (input order)
   DBuf<float4> a_in;              // a and du/dt of the last force pass (input order)
+  DBuf<long long> boff;           // first particle of each box, and N (device copy of off)
+  // relayout targets
+  DBuf<double> rl_x;
+  DBuf<float> rl_v, rl_m, rl_u, rl_h;
+  DBuf<float4> rl_a;
+  DBuf<long long> rl_tab;
 
   // key-sorted particle state
   DBuf<unsigned long long> key, key_tmp;

@@ -187,10 +187,9 @@ def run_ours(args, rank, world, local_rank):
     cprof = b.get_profile()
     b.profile(False)
     b.count_pairs(False)
-    flops_density_pair = ((FLOPS_DENSITY_PAIR * st["density_pairs_cellpair"]
-                           + FLOPS_DENSITY_SIDE * st["density_sides_cellpair"])
-                          / max(cprof["density_pair"]["calls"], 1))
-    flops_force_pair = FLOPS_FORCE_PAIR * st["force_pairs_cellpair"] / max(cprof["force_pair"]["calls"], 1)
+    flops_density = ((FLOPS_DENSITY_PAIR * st["density_pairs"] + FLOPS_DENSITY_SIDE * st["density_sides"])
+                     / max(cprof["density"]["calls"], 1))
+    flops_force = FLOPS_FORCE_PAIR * st["force_pairs"] / max(cprof["force"]["calls"], 1)
 
     for _ in range(args.warmup):
         step_device()
@@ -254,10 +253,10 @@ def run_ours(args, rank, world, local_rank):
     e2e = world * n * e2e_steps / e2e_s
 
     # roofline of the dominant kernel (FP32 ALU bound)
-    dom = max(("density_pair", "force_pair"), key=lambda k: prof[k]["ms"])
+    dom = max(("density", "force"), key=lambda k: prof[k]["ms"])
     calls = max(prof[dom]["calls"], 1)
     avg_ms = prof[dom]["ms"] / calls
-    flops = flops_density_pair if dom == "density_pair" else flops_force_pair
+    flops = flops_density if dom == "density" else flops_force
     achieved = flops / (avg_ms / 1e3) / 1e12
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")

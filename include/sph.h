@@ -144,8 +144,9 @@ typedef struct sph_stats {
 /* Device time of one phase of the path (CUDA events on the context stream). */
 typedef struct sph_profile_entry {
     char name[32];              /* ingest, keys_sort, tree, lists, shift, axis_sort,
-                                   density_pair, density_self, ghost, force_pair,
-                                   force_self, reduce, kick_drift, output        */
+                                   density (pair and self interactions),
+                                   density_tasks (the pass's live task list), ghost,
+                                   force, force_tasks, reduce, kick_drift, output */
     int64_t calls;              /* times the phase ran while recording                */
     int64_t launches;           /* kernel launches inside it                          */
     double ms;                  /* summed device time                                 */

@@ -50,10 +50,9 @@ __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigne
                              const float4*, unsigned int*, Tiles);
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
-void launch_density_pair(Engine& E);
-void launch_density_self(Engine& E);
-void launch_force_pair(Engine& E);
-void launch_force_self(Engine& E);
+void launch_live_tasks(Engine& E, bool dens);
+void launch_density(Engine& E);
+void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it);
 void launch_zero_density(Engine& E, bool all);
 void launch_set_active(Engine& E);
@@ -79,10 +78,10 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-const char* const kPhaseNames[PH_COUNT] = {"ingest",       "keys_sort",  "tree",        "lists",
-                                           "shift",        "axis_sort",  "density_pair", "density_self",
-                                           "ghost",        "force_pair", "force_self",  "reduce",
-                                           "kick_drift",   "output"};
+const char* const kPhaseNames[PH_COUNT] = {"ingest",     "keys_sort",   "tree",      "lists",
+                                           "shift",      "axis_sort",   "density",   "density_tasks",
+                                           "ghost",      "force",       "force_tasks", "reduce",
+                                           "kick_drift", "output"};
 
 int Engine::prof_begin(int phase, long long* l0) {
   *l0 = launch_count();
@@ -581,9 +580,10 @@ sph_status Engine::build_once(bool* retry) {
   n_big_entries = bc[1];
   CK(l_ptask.reserve(std::max(lc[6], 1)));
   CK(l_stask.reserve(std::max(lc[7], 1)));
-  CK(l_plive.reserve(std::max(lc[6], 1)));
+  CK(l_plive.reserve(std::max(lc[6] + lc[7], 1)));
   CK(l_nlive.reserve(1));
   n_ptasks = lc[6];
+  n_stasks = lc[7];
   Lq.p_task = l_ptask.p;
   Lq.s_task = l_stask.p;
   Lq.p_live = l_plive.p;
@@ -623,13 +623,13 @@ sph_status Engine::set_all_active() {
 
 sph_status Engine::density_pass() {
   {
-    Scope sc(this, PH_DENSITY_PAIR);
+    Scope sc(this, PH_DENSITY_TASKS);
     launch_zero_density(*this, false);
-    launch_density_pair(*this);
+    launch_live_tasks(*this, true);
   }
   {
-    Scope sc(this, PH_DENSITY_SELF);
-    launch_density_self(*this);
+    Scope sc(this, PH_DENSITY);
+    launch_density(*this);
   }
   CK(cudaGetLastError());
   return SPH_OK;
@@ -720,12 +720,12 @@ sph_status Engine::force() {
   CK(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
   CK(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
   {
-    Scope sc(this, PH_FORCE_PAIR);
-    launch_force_pair(*this);
+    Scope sc(this, PH_FORCE_TASKS);
+    launch_live_tasks(*this, false);
   }
   {
-    Scope sc(this, PH_FORCE_SELF);
-    launch_force_self(*this);
+    Scope sc(this, PH_FORCE);
+    launch_force(*this);
   }
   {
     Scope sc(this, PH_REDUCE);

@@ -676,322 +676,332 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
   return __ballot_sync(0xffffffffu, pass);
 }
 
+// One pair task: cluster ti of cell A against the sorted clusters of cell B.
 template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_density_pair(Lists Lq, int cap_pair, Tree T, Tiles TL,
-                                                              const BoxDesc* __restrict__ box,
-                                                              const float4* __restrict__ pos4,
-                                                              const float4* __restrict__ cen4,
-                                                              const float* __restrict__ sort_r,
-                                                              const unsigned int* __restrict__ sort_i,
-                                                              const unsigned char* __restrict__ act,
-                                                              const unsigned int* __restrict__ perm,
-                                                              const double* __restrict__ x, float4* dacc,
-                                                              unsigned int* dcnt, unsigned long long* pc,
-                                                              unsigned int* __restrict__ task_ctr) {
-  __shared__ DensShared SH[SPH_WARPS_PER_CTA];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  DensShared& S = SH[wl];
-  Counters C;
-  const unsigned int ntask = *Lq.n_live;
-  unsigned int raw = 0;
-  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
-  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
-    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
-    const unsigned int tend = min(base + TASK_CHUNK, ntask);
-    for (unsigned int t = base; t < tend; ++t) {
-      const uint2 lt = Lq.p_live[t];
-      const int item = (int)lt.x;
-      const unsigned int ti = lt.y;
-      const bool i_active = TL.active[ti] != 0;
-      const PairSetup P = pair_setup(Lq, T, box, item);
-      const Box3 bi = tile_box3(TL, T, ti, P.tshA);
-      const float Hi = TL.lo[ti].w * P.g.invL;
-      const float rhi_i = box_rhi(bi, P.u);
-      const unsigned int ni = TL.n[ti];
-      const bool vi = (unsigned int)lane < ni;
-      const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
-      dens_stage_own(S, lane, I);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      unsigned int cnt = 0, q = 0;
-      for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
-        unsigned int jt, jn, js;
-        bool stop;
-        unsigned int mask =
-            scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &jn, &js, &stop);
-        if (stop) break;
-        // the loads of the next candidate cluster are issued before the current
-        // one is tested, so that their latency overlaps that work
-        bool nv = false;
-        unsigned int ng = 0;
-        DensRaw nr;
-        if (mask) {
-          const int k = __ffs(mask) - 1;
-          nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
-          ng = __shfl_sync(0xffffffffu, js, k) + lane;
-          nr = fetch_dens(nv, ng, pos4, cen4, act);
-        }
-        while (mask) {
-          mask &= mask - 1;
-          const bool vj = nv;
-          const unsigned int gj = ng;
-          const DensRaw cr = nr;
-          if (mask) {
-            const int k = __ffs(mask) - 1;
-            nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
-            ng = __shfl_sync(0xffffffffu, js, k) + lane;
-            nr = fetch_dens(nv, ng, pos4, cen4, act);
-          }
-          const DensI J = make_dens(vj, gj, cr, P.shB, P.g.invL, P.g.e);
-          // stage only the partners within reach of the cluster's box
-          const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
-          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
-          const unsigned int np = __popc(bal);
-          if (q + np > 32u) {
-            dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
-            q = 0;
-          }
-          if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
-          q += np;
-        }
-      }
-      if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
-      flush_dens(I.g, acc, cnt, dacc, dcnt);
-    }
-  }
-  commit_counters<COUNT>(C, pc, 0);
-}
-
-template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_density_self(Lists Lq, int cap_self, Tree T, Tiles TL,
-                                                              const BoxDesc* __restrict__ box,
-                                                              const float4* __restrict__ pos4,
-                                                              const float4* __restrict__ cen4,
-                                                              const unsigned char* __restrict__ act,
-                                                              const unsigned int* __restrict__ perm,
-                                                              const double* __restrict__ x, float4* dacc,
-                                                              unsigned int* dcnt, unsigned long long* pc,
-                                                              unsigned int* __restrict__ task_ctr) {
-  __shared__ DensShared SH[SPH_WARPS_PER_CTA];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  DensShared& S = SH[wl];
-  Counters C;
-  const unsigned int ntask = (unsigned int)Lq.counts[7];
-  unsigned int raw = 0;
-  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
-  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
-    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
-    const unsigned int tend = min(base + TASK_CHUNK, ntask);
-    for (unsigned int t = base; t < tend; ++t) {
-      const int item = (int)Lq.s_task[t];
-      const int A = Lq.self_a[item];
-      if (!T.active[A]) continue;
-      const ItemGeom g = item_geom(T, box, A, 0);
-      const float4 cA = T.cen[A];
-      const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-      const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
-      const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
-      const unsigned int ti = t0 + (t - Lq.s_toff[item]);
-      const bool i_active = TL.active[ti] != 0;
-      const Box3 bi = tile_box3(TL, T, ti, sh);
-      const float Hi = TL.lo[ti].w * g.invL;
-      const bool vi = (unsigned int)lane < TL.n[ti];
-      const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
-      dens_stage_own(S, lane, I);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      unsigned int cnt = 0, q = 0;
-      // inside the cluster itself each unordered pair once: partners above the lane
-      if (vi) dens_put(S, lane, I);
-      dens_batch<COUNT>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
-      // the later clusters of the cell, 32 box tests at a time
-      for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
-        const unsigned int tl = b0 + lane;
-        bool ok = false;
-        if (tl < t0 + nt && (i_active || TL.active[tl])) {
-          const Box3 bj = tile_box3(TL, T, tl, sh);
-          ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
-        }
-        unsigned int mask = __ballot_sync(0xffffffffu, ok);
-        while (mask) {
-          const int k = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const unsigned int tj = b0 + (unsigned int)k;
-          const bool vj = (unsigned int)lane < TL.n[tj];
-          const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
-          const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
-          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
-          const unsigned int np = __popc(bal);
-          if (q + np > 32u) {
-            dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
-            q = 0;
-          }
-          if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
-          q += np;
-        }
-      }
-      if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
-      flush_dens(I.g, acc, cnt, dacc, dcnt);
-    }
-  }
-  commit_counters<COUNT>(C, pc, 1);
-}
-
-template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_force_pair(Lists Lq, int cap_pair, Tree T, Tiles TL,
-                                                            const BoxDesc* __restrict__ box,
-                                                            const float4* __restrict__ pos4,
-                                                            const float4* __restrict__ cen4,
-                                                            const float4* __restrict__ vel4,
-                                                            const float4* __restrict__ ghost4,
-                                                            const float* __restrict__ sort_r,
-                                                            const unsigned int* __restrict__ sort_i,
-                                                            const unsigned int* __restrict__ perm,
-                                                            const double* __restrict__ x, float alpha, float4* facc,
-                                                            float* fvsig, unsigned long long* pc,
-                                                            unsigned int* __restrict__ task_ctr) {
-  __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  ForceShared& S = SH[wl];
-  Counters C;
-  const unsigned int ntask = *Lq.n_live;
-  unsigned int raw = 0;
-  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
-  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
-    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
-    const unsigned int tend = min(base + TASK_CHUNK, ntask);
-    for (unsigned int t = base; t < tend; ++t) {
-      const uint2 lt = Lq.p_live[t];
-      const int item = (int)lt.x;
-      const unsigned int ti = lt.y;
-      const PairSetup P = pair_setup(Lq, T, box, item);
-      const Box3 bi = tile_box3(TL, T, ti, P.tshA);
-      const float Hi = TL.lo[ti].w * P.g.invL;
-      const float rhi_i = box_rhi(bi, P.u);
-      const bool vi = (unsigned int)lane < TL.n[ti];
-      const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
-      force_stage_own(S, lane, I);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      float vsi = 0.0f;
-      unsigned int q = 0;
-      for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
-        unsigned int jt, jn, js;
-        bool stop;
-        unsigned int mask =
-            scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, true, &jt, &jn, &js, &stop);
-        if (stop) break;
-        while (mask) {
-          const int k = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
-          const ForceI J = load_force(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, vel4, ghost4,
-                                      P.g.invL, P.g.e);
-          const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
-          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
-          const unsigned int np = __popc(bal);
-          if (q + np > 32u) {
-            force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
-            q = 0;
-          }
-          if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
-          q += np;
-        }
-      }
-      if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
-      flush_force(I.g, acc, vsi, facc, fvsig);
-    }
-  }
-  commit_counters<COUNT>(C, pc, 2);
-}
-
-template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_force_self(Lists Lq, int cap_self, Tree T, Tiles TL,
-                                                            const BoxDesc* __restrict__ box,
-                                                            const float4* __restrict__ pos4,
-                                                            const float4* __restrict__ cen4,
-                                                            const float4* __restrict__ vel4,
-                                                            const float4* __restrict__ ghost4,
-                                                            const unsigned int* __restrict__ perm,
-                                                            const double* __restrict__ x, float alpha, float4* facc,
-                                                            float* fvsig, unsigned long long* pc,
-                                                            unsigned int* __restrict__ task_ctr) {
-  __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  ForceShared& S = SH[wl];
-  Counters C;
-  const unsigned int ntask = (unsigned int)Lq.counts[7];
-  unsigned int raw = 0;
-  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
-  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
-    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
-    const unsigned int tend = min(base + TASK_CHUNK, ntask);
-    for (unsigned int t = base; t < tend; ++t) {
-      const int item = (int)Lq.s_task[t];
-      const int A = Lq.self_a[item];
-      const ItemGeom g = item_geom(T, box, A, 0);
-      const float4 cA = T.cen[A];
-      const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-      const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
-      const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
-      const unsigned int ti = t0 + (t - Lq.s_toff[item]);
-      const Box3 bi = tile_box3(TL, T, ti, sh);
-      const float Hi = TL.lo[ti].w * g.invL;
-      const bool vi = (unsigned int)lane < TL.n[ti];
-      const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
-      force_stage_own(S, lane, I);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      float vsi = 0.0f;
-      unsigned int q = 0;
-      // inside the cluster itself each unordered pair once: partners above the lane
-      if (vi) force_put(S, lane, I);
-      force_batch<COUNT>(I, S, TL.n[ti], true, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
-      for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
-        const unsigned int tl = b0 + lane;
-        bool ok = false;
-        if (tl < t0 + nt) {
-          const Box3 bj = tile_box3(TL, T, tl, sh);
-          ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
-        }
-        unsigned int mask = __ballot_sync(0xffffffffu, ok);
-        while (mask) {
-          const int k = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const unsigned int tj = b0 + (unsigned int)k;
-          const bool vj = (unsigned int)lane < TL.n[tj];
-          const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
-          const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
-          const unsigned int bal = __ballot_sync(0xffffffffu, pass);
-          const unsigned int np = __popc(bal);
-          if (q + np > 32u) {
-            force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
-            q = 0;
-          }
-          if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
-          q += np;
-        }
-      }
-      if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
-      flush_force(I.g, acc, vsi, facc, fvsig);
-    }
-  }
-  commit_counters<COUNT>(C, pc, 3);
-}
-
-// Pair tasks of one pass that have work, as (pair, cluster): in a density pass
-// those whose cluster or partner cell still iterates h, and in every pass
-// those whose cluster lies within reach of the partner cell (the same test the
-// sweep would start with).  One thread per task; warp-aggregated appends.
-template <bool DENS>
-__global__ void k_live_pair_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long ntask) {
+__device__ __forceinline__ void density_pair_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
+    const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
+    const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
+    const unsigned int* __restrict__ perm, const double* __restrict__ x, float4* dacc, unsigned int* dcnt, DensShared& S,
+    Counters& C) {
   const int lane = threadIdx.x & 31;
+  const bool i_active = TL.active[ti] != 0;
+  const PairSetup P = pair_setup(Lq, T, box, item);
+  const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+  const float Hi = TL.lo[ti].w * P.g.invL;
+  const float rhi_i = box_rhi(bi, P.u);
+  const unsigned int ni = TL.n[ti];
+  const bool vi = (unsigned int)lane < ni;
+  const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
+  dens_stage_own(S, lane, I);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned int cnt = 0, q = 0;
+  for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
+    unsigned int jt, jn, js;
+    bool stop;
+    unsigned int mask =
+        scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &jn, &js, &stop);
+    if (stop) break;
+    // the loads of the next candidate cluster are issued before the current
+    // one is tested, so that their latency overlaps that work
+    bool nv = false;
+    unsigned int ng = 0;
+    DensRaw nr;
+    if (mask) {
+      const int k = __ffs(mask) - 1;
+      nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+      ng = __shfl_sync(0xffffffffu, js, k) + lane;
+      nr = fetch_dens(nv, ng, pos4, cen4, act);
+    }
+    while (mask) {
+      mask &= mask - 1;
+      const bool vj = nv;
+      const unsigned int gj = ng;
+      const DensRaw cr = nr;
+      if (mask) {
+        const int k = __ffs(mask) - 1;
+        nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+        ng = __shfl_sync(0xffffffffu, js, k) + lane;
+        nr = fetch_dens(nv, ng, pos4, cen4, act);
+      }
+      const DensI J = make_dens(vj, gj, cr, P.shB, P.g.invL, P.g.e);
+      // stage only the partners within reach of the cluster's box
+      const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
+      const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+      const unsigned int np = __popc(bal);
+      if (q + np > 32u) {
+        dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+        q = 0;
+      }
+      if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+      q += np;
+    }
+  }
+  if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+  flush_dens(I.g, acc, cnt, dacc, dcnt);
+}
+
+// One self task: cluster ti against itself and the later clusters of its cell.
+template <bool COUNT>
+__device__ __forceinline__ void density_self_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
+    const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
+    const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
+    const unsigned int* __restrict__ perm, const double* __restrict__ x, float4* dacc, unsigned int* dcnt, DensShared& S,
+    Counters& C) {
+  const int lane = threadIdx.x & 31;
+  const int A = Lq.self_a[item];
+  const ItemGeom g = item_geom(T, box, A, 0);
+  const float4 cA = T.cen[A];
+  const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
+  const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+  const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
+  const bool i_active = TL.active[ti] != 0;
+  const Box3 bi = tile_box3(TL, T, ti, sh);
+  const float Hi = TL.lo[ti].w * g.invL;
+  const bool vi = (unsigned int)lane < TL.n[ti];
+  const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
+  dens_stage_own(S, lane, I);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned int cnt = 0, q = 0;
+  // inside the cluster itself each unordered pair once: partners above the lane
+  if (vi) dens_put(S, lane, I);
+  dens_batch<COUNT>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
+  // the later clusters of the cell, 32 box tests at a time
+  for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
+    const unsigned int tl = b0 + lane;
+    bool ok = false;
+    if (tl < t0 + nt && (i_active || TL.active[tl])) {
+      const Box3 bj = tile_box3(TL, T, tl, sh);
+      ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
+    }
+    unsigned int mask = __ballot_sync(0xffffffffu, ok);
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const unsigned int tj = b0 + (unsigned int)k;
+      const bool vj = (unsigned int)lane < TL.n[tj];
+      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
+      const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
+      const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+      const unsigned int np = __popc(bal);
+      if (q + np > 32u) {
+        dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+        q = 0;
+      }
+      if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+      q += np;
+    }
+  }
+  if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+  flush_dens(I.g, acc, cnt, dacc, dcnt);
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
+    const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
+    const float4* __restrict__ ghost4, const float* __restrict__ sort_r, const unsigned int* __restrict__ sort_i,
+    const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig, ForceShared& S,
+    Counters& C) {
+  const int lane = threadIdx.x & 31;
+  const PairSetup P = pair_setup(Lq, T, box, item);
+  const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+  const float Hi = TL.lo[ti].w * P.g.invL;
+  const float rhi_i = box_rhi(bi, P.u);
+  const bool vi = (unsigned int)lane < TL.n[ti];
+  const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
+  force_stage_own(S, lane, I);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  float vsi = 0.0f;
+  unsigned int q = 0;
+  for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
+    unsigned int jt, jn, js;
+    bool stop;
+    unsigned int mask =
+        scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, true, &jt, &jn, &js, &stop);
+    if (stop) break;
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
+      const ForceI J = load_force(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, vel4, ghost4,
+                                  P.g.invL, P.g.e);
+      const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
+      const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+      const unsigned int np = __popc(bal);
+      if (q + np > 32u) {
+        force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+        q = 0;
+      }
+      if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+      q += np;
+    }
+  }
+  if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+  flush_force(I.g, acc, vsi, facc, fvsig);
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void force_self_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
+    const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
+    const float4* __restrict__ ghost4, const float* __restrict__ sort_r, const unsigned int* __restrict__ sort_i,
+    const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig, ForceShared& S,
+    Counters& C) {
+  const int lane = threadIdx.x & 31;
+  const int A = Lq.self_a[item];
+  const ItemGeom g = item_geom(T, box, A, 0);
+  const float4 cA = T.cen[A];
+  const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
+  const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+  const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
+  const Box3 bi = tile_box3(TL, T, ti, sh);
+  const float Hi = TL.lo[ti].w * g.invL;
+  const bool vi = (unsigned int)lane < TL.n[ti];
+  const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+  force_stage_own(S, lane, I);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  float vsi = 0.0f;
+  unsigned int q = 0;
+  // inside the cluster itself each unordered pair once: partners above the lane
+  if (vi) force_put(S, lane, I);
+  force_batch<COUNT>(I, S, TL.n[ti], true, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+  for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
+    const unsigned int tl = b0 + lane;
+    bool ok = false;
+    if (tl < t0 + nt) {
+      const Box3 bj = tile_box3(TL, T, tl, sh);
+      ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
+    }
+    unsigned int mask = __ballot_sync(0xffffffffu, ok);
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const unsigned int tj = b0 + (unsigned int)k;
+      const bool vj = (unsigned int)lane < TL.n[tj];
+      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
+      const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+      const unsigned int np = __popc(bal);
+      if (q + np > 32u) {
+        force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+        q = 0;
+      }
+      if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+      q += np;
+    }
+  }
+  if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+  flush_force(I.g, acc, vsi, facc, fvsig);
+}
+
+// Density interactions of one pass: the live pair and self tasks in one queue.
+template <bool COUNT>
+__global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+                                                         const float4* __restrict__ pos4,
+                                                         const float4* __restrict__ cen4,
+                                                         const float* __restrict__ sort_r,
+                                                         const unsigned int* __restrict__ sort_i,
+                                                         const unsigned char* __restrict__ act,
+                                                         const unsigned int* __restrict__ perm,
+                                                         const double* __restrict__ x, float4* dacc,
+                                                         unsigned int* dcnt, unsigned long long* pc,
+                                                         unsigned int* __restrict__ task_ctr) {
+  __shared__ DensShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  DensShared& S = SH[wl];
+  Counters Cp, Cs;
+  const unsigned int ntask = *Lq.n_live;
+  unsigned int raw = 0;
+  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
+    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    for (unsigned int t = base; t < tend; ++t) {
+      const uint2 lt = Lq.p_live[t];
+      const int item = (int)(lt.x & 0x7fffffffu);
+      if (lt.x >> 31)
+        density_self_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc, dcnt, S,
+                                 Cs);
+      else
+        density_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc, dcnt, S,
+                                 Cp);
+    }
+  }
+  commit_counters<COUNT>(Cp, pc, 0);
+  commit_counters<COUNT>(Cs, pc, 1);
+}
+
+// Force interactions of one pass: the pair and self tasks in one queue.
+template <bool COUNT>
+__global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+                                                       const float4* __restrict__ pos4,
+                                                       const float4* __restrict__ cen4,
+                                                       const float4* __restrict__ vel4,
+                                                       const float4* __restrict__ ghost4,
+                                                       const float* __restrict__ sort_r,
+                                                       const unsigned int* __restrict__ sort_i,
+                                                       const unsigned int* __restrict__ perm,
+                                                       const double* __restrict__ x, float alpha, float4* facc,
+                                                       float* fvsig, unsigned long long* pc,
+                                                       unsigned int* __restrict__ task_ctr) {
+  __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  ForceShared& S = SH[wl];
+  Counters Cp, Cs;
+  const unsigned int ntask = *Lq.n_live;
+  unsigned int raw = 0;
+  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
+    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    for (unsigned int t = base; t < tend; ++t) {
+      const uint2 lt = Lq.p_live[t];
+      const int item = (int)(lt.x & 0x7fffffffu);
+      if (lt.x >> 31)
+        force_self_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
+                               facc, fvsig, S, Cs);
+      else
+        force_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
+                               facc, fvsig, S, Cp);
+    }
+  }
+  commit_counters<COUNT>(Cp, pc, 2);
+  commit_counters<COUNT>(Cs, pc, 3);
+}
+
+
+
+
+
+// Tasks of one pass that have work, as (interaction, cluster); bit 31 of the
+// interaction marks a self task.  Pair tasks: in a density pass those whose
+// cluster or partner cell still iterates h, and in every pass those whose
+// cluster lies within reach of the partner cell (the test the sweep would
+// start with).  Self tasks: in a density pass those whose cell still iterates
+// h.  Self tasks come first: the costliest tasks are then taken early and the
+// short pair tasks fill the end of the pass.  One thread per task;
+// warp-aggregated appends.
+template <bool DENS>
+__global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
+                             long long nst) {
+  const int lane = threadIdx.x & 31;
+  const long long ntask = npt + nst;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < ntask; b0 += stride) {
     const long long t = b0 + threadIdx.x;
     bool live = false;
-    int item = 0;
-    unsigned int ti = 0;
-    if (t < ntask) {
-      item = (int)Lq.p_task[t];
+    unsigned int rec = 0, ti = 0;
+    if (t < nst) {
+      const unsigned int ts = (unsigned int)t;
+      const int item = (int)Lq.s_task[ts];
+      const int A = Lq.self_a[item];
+      ti = T.tile0[A] + (ts - Lq.s_toff[item]);
+      rec = (unsigned int)item | 0x80000000u;
+      live = !DENS || T.active[A];
+    } else if (t < ntask) {
+      const unsigned int tp = (unsigned int)(t - nst);
+      const int item = (int)Lq.p_task[tp];
       const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
-      ti = T.tile0[A0] + ((unsigned int)t - Lq.p_toff[item]);
+      ti = T.tile0[A0] + (tp - Lq.p_toff[item]);
+      rec = (unsigned int)item;
       live = !DENS || TL.active[ti] || T.active[B0];
       if (live) {
         const PairSetup P = pair_setup(Lq, T, box, item);
@@ -1004,7 +1014,7 @@ __global__ void k_live_pair_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __r
     unsigned int at = 0;
     if (lane == 0 && bal) at = atomicAdd(Lq.n_live, (unsigned int)__popc(bal));
     at = __shfl_sync(0xffffffffu, at, 0);
-    if (live) Lq.p_live[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2((unsigned int)item, ti);
+    if (live) Lq.p_live[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2(rec, ti);
   }
 }
 
@@ -1323,50 +1333,31 @@ static int resident_ctas(const void* fn) {
   return 4;
 }
 
-void launch_live_pair_tasks(Engine& E, bool dens) {
+void launch_live_tasks(Engine& E, bool dens) {
   cudaMemsetAsync(E.Lq.n_live, 0, sizeof(unsigned int), E.st);
-  if (E.n_ptasks == 0) return;
-  const int grid = (int)std::min<long long>((E.n_ptasks + 255) / 256, (long long)E.nsm * 16);
-  if (dens) k_live_pair_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks);
-  else k_live_pair_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks);
+  const long long n = E.n_ptasks + E.n_stasks;
+  if (n == 0) return;
+  const int grid = (int)std::min<long long>((n + 255) / 256, (long long)E.nsm * 16);
+  if (dens) k_live_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks);
+  else k_live_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks);
   count_launch();
 }
 
-void launch_density_pair(Engine& E) {
-  launch_live_pair_tasks(E, true);
-  const auto k = E.count_pairs ? k_density_pair<true> : k_density_pair<false>;
+void launch_density(Engine& E) {
+  const auto k = E.count_pairs ? k_density<true> : k_density<false>;
   cudaMemsetAsync(E.task_ctr.p + 0, 0, sizeof(unsigned int), E.st);
   k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
-      E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p,
-      E.dacc.p, E.dcnt.p, E.pc.p, E.task_ctr.p + 0);
+      E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
+      E.dcnt.p, E.pc.p, E.task_ctr.p + 0);
   count_launch();
 }
 
-void launch_density_self(Engine& E) {
-  const auto k = E.count_pairs ? k_density_self<true> : k_density_self<false>;
+void launch_force(Engine& E) {
+  const auto k = E.count_pairs ? k_force<true> : k_force<false>;
   cudaMemsetAsync(E.task_ctr.p + 1, 0, sizeof(unsigned int), E.st);
   k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
-      E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.act.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p,
-      E.pc.p, E.task_ctr.p + 1);
-  count_launch();
-}
-
-void launch_force_pair(Engine& E) {
-  launch_live_pair_tasks(E, false);
-  const auto k = E.count_pairs ? k_force_pair<true> : k_force_pair<false>;
-  cudaMemsetAsync(E.task_ctr.p + 2, 0, sizeof(unsigned int), E.st);
-  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
-      E.Lq, E.cap_pair, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p,
-      E.perm.p, E.x.p, E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 2);
-  count_launch();
-}
-
-void launch_force_self(Engine& E) {
-  const auto k = E.count_pairs ? k_force_self<true> : k_force_self<false>;
-  cudaMemsetAsync(E.task_ctr.p + 3, 0, sizeof(unsigned int), E.st);
-  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
-      E.Lq, E.cap_self, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.perm.p, E.x.p,
-      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 3);
+      E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p, E.x.p,
+      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 1);
   count_launch();
 }
 

@@ -57,8 +57,8 @@ long long launch_count();
 
 // Phases of the path timed with CUDA events when profiling is on.
 enum Phase {
-  PH_INGEST, PH_SORT, PH_TREE, PH_LISTS, PH_SHIFT, PH_AXIS_SORT, PH_DENSITY_PAIR, PH_DENSITY_SELF, PH_GHOST,
-  PH_FORCE_PAIR, PH_FORCE_SELF, PH_REDUCE, PH_STEP, PH_OUTPUT, PH_COUNT
+  PH_INGEST, PH_SORT, PH_TREE, PH_LISTS, PH_SHIFT, PH_AXIS_SORT, PH_DENSITY, PH_DENSITY_TASKS, PH_GHOST,
+  PH_FORCE, PH_FORCE_TASKS, PH_REDUCE, PH_STEP, PH_OUTPUT, PH_COUNT
 };
 extern const char* const kPhaseNames[PH_COUNT];
 
@@ -167,7 +167,7 @@ class Engine {
   DBuf<int> l_self, l_pa, l_pb, l_pax, l_counts;
   DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp, l_ptask, l_stask, l_nlive;
   DBuf<uint2> l_plive;
-  long long n_ptasks = 0;
+  long long n_ptasks = 0, n_stasks = 0;
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
   Lists Lq{};
 

@@ -139,11 +139,11 @@ def test_profile_and_launch_counts(api, ctx):
         launched = api.sph_launch_count() - l0
     finally:
         b.close()
-    for ph in ("ingest", "keys_sort", "tree", "lists", "axis_sort", "density_pair", "density_self", "ghost",
-               "force_pair", "force_self", "reduce"):
+    for ph in ("ingest", "keys_sort", "tree", "lists", "axis_sort", "density", "density_tasks", "ghost",
+               "force", "force_tasks", "reduce"):
         assert prof[ph]["calls"] >= 1 and prof[ph]["ms"] > 0, ph
     assert sum(v["launches"] for v in prof.values()) <= launched
-    assert prof["density_pair"]["launches"] >= 1
+    assert prof["density"]["launches"] >= 1
 
 
 def test_checkpoint_restart_continues_the_run(api, ctx):

@@ -772,6 +772,8 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
 }
 
 // Storage for the sorted lists: every (cell, needed axis) gets ntile entries.
+// Cells of at most 32 clusters are not sorted: a warp tests all their clusters
+// at once, so an order would end no sweep earlier (sortbase = SORT_NONE).
 // Cells above SORT_SMALL clusters also list their (cell, axis) segments for the
 // global sort.
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
@@ -781,6 +783,10 @@ __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big
     const unsigned int ax = T.axes[id];
     if (!ax) continue;
     const unsigned int c = T.ntile[id];
+    if (c <= 32u) {
+      T.sortbase[id] = SORT_NONE;
+      continue;
+    }
     const int na = __popc(ax);
     T.sortbase[id] = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
     atomicAdd(&Lq.counts[4], na);
@@ -834,7 +840,7 @@ __global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, Tiles TL
   for (int id = blockIdx.x; id < nnodes; id += gridDim.x) {
     const unsigned int ax = T.axes[id];
     const unsigned int c = T.ntile[id];
-    if (!ax || c > SORT_SMALL) continue;
+    if (!ax || c <= 32u || c > SORT_SMALL) continue;
     unsigned int npow = 1;
     while (npow < c) npow <<= 1;
     const unsigned int t0 = T.tile0[id];
@@ -843,33 +849,6 @@ __global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, Tiles TL
     for (int a = 0; a < 13; ++a) {
       if (!(ax & (1u << a))) continue;
       const float3 u = axis_unit(a);
-      if (c <= 32) {
-        // one warp: register bitonic sort over shuffles
-        if (threadIdx.x < 32) {
-          const unsigned int q = threadIdx.x;
-          float r = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
-          unsigned int ix = q;
-          for (unsigned int k = 2; k <= 32; k <<= 1) {
-            for (unsigned int j = k >> 1; j > 0; j >>= 1) {
-              const float r2 = __shfl_xor_sync(0xffffffffu, r, j);
-              const unsigned int i2 = __shfl_xor_sync(0xffffffffu, ix, j);
-              const bool lower = (q & j) == 0;
-              const bool up = (q & k) == 0;
-              const bool gt = (r > r2) || (r == r2 && ix > i2);
-              if ((lower == up) == gt) {
-                r = r2;
-                ix = i2;
-              }
-            }
-          }
-          if (q < c) {
-            sort_r[out + q] = r;
-            sort_i[out + q] = t0 + ix;
-          }
-        }
-        out += c;
-        continue;
-      }
       for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
         sr[q] = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
         si[q] = q;

@@ -615,7 +615,8 @@ struct PairSetup {
   float3 shA, shB;        // particle frame offsets: leaf frame -> A's frame (B includes e db)
   float3 tshA, tshB;      // cluster box offsets (the leaf centre is added per cluster)
   float3 u;
-  unsigned int sb, ntj;   // B's sorted cluster list
+  unsigned int sb, ntj;   // B's sorted cluster list (sb = SORT_NONE: B's clusters in their own order)
+  unsigned int tb0;       // B's first cluster
   float HmB, slack;
   Box3 cellB;             // B's cell in A's frame
 };
@@ -633,7 +634,9 @@ __device__ __forceinline__ PairSetup pair_setup(const Lists& Lq, const Tree& T, 
   P.tshB = P.shB;
   P.u = axis_unit_f(ax);
   P.ntj = T.ntile[P.B];
-  P.sb = T.sortbase[P.B] + (unsigned int)__popc(T.axes[P.B] & ((1u << ax) - 1u)) * P.ntj;
+  P.tb0 = T.tile0[P.B];
+  const unsigned int sbB = T.sortbase[P.B];
+  P.sb = sbB == SORT_NONE ? SORT_NONE : sbB + (unsigned int)__popc(T.axes[P.B] & ((1u << ax) - 1u)) * P.ntj;
   P.HmB = T.hmax[P.B] * P.g.invL;
   P.slack = P.g.e * 1.52587890625e-05f + 1e-6f * fmaxf(P.HmB, T.hmax[P.A] * P.g.invL);   // 2^-16 e
   const float h = 0.5f * P.g.e;
@@ -655,17 +658,22 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
                                                       unsigned int* jt, unsigned int* jn, unsigned int* js,
                                                       bool* stop) {
   const int lane = threadIdx.x & 31;
-  const float r0 = sort_r[P.sb + e0] + P.g.offBp;
-  *stop = r0 - rhi_i > fmaxf(Hi, P.HmB) + P.slack;     // the sorted list only moves further away
-  if (*stop) return 0u;
+  const bool sorted = P.sb != SORT_NONE;
+  if (sorted) {
+    const float r0 = sort_r[P.sb + e0] + P.g.offBp;
+    *stop = r0 - rhi_i > fmaxf(Hi, P.HmB) + P.slack;     // the sorted list only moves further away
+    if (*stop) return 0u;
+  } else {
+    *stop = false;
+  }
   const unsigned int e = e0 + lane;
   bool pass = false;
   unsigned int t = 0;
   if (e < P.ntj) {
-    t = sort_i[P.sb + e];
-    const float rlo = sort_r[P.sb + e] + P.g.offBp;
+    t = sorted ? sort_i[P.sb + e] : P.tb0 + e;
     const float reach = fmaxf(Hi, TL.lo[t].w * P.g.invL) + P.slack;
-    if (rlo - rhi_i <= reach && (!DENS || i_active || TL.active[t])) {
+    const bool window = !sorted || sort_r[P.sb + e] + P.g.offBp - rhi_i <= reach;
+    if (window && (!DENS || i_active || TL.active[t])) {
       const Box3 bj = tile_box3(TL, T, t, P.tshB);
       pass = box_gap(bi, bj) <= reach;
     }

@@ -8,6 +8,7 @@
 #define SPH_WARPS_PER_CTA 4
 #define SPH_THREADS (32 * SPH_WARPS_PER_CTA)
 #define SORT_SMALL 2048u       // cells with up to this many clusters are sorted in shared memory
+#define SORT_NONE 0xffffffffu  // sortbase of a cell whose clusters are not sorted
 
 // Error bits set by kernels in a box's status word.
 enum : unsigned int {

@@ -315,6 +315,8 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   CK(t_hlim.reserve(n));
   CK(t_cen.reserve(n));
   CK(t_active.reserve(n));
+  CK(t_alo.reserve(3 * n));
+  CK(t_ahi.reserve(3 * n));
   CK(t_tile0.reserve(n));
   CK(t_ntile.reserve(n));
   CK(t_n.reserve(8));
@@ -334,6 +336,8 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   T.axes = t_axes.p;
   T.sortbase = t_sortbase.p;
   T.active = t_active.p;
+  T.alo = t_alo.p;
+  T.ahi = t_ahi.p;
   T.tile0 = t_tile0.p;
   T.ntile = t_ntile.p;
   T.n_nodes = t_n.p;

@@ -989,7 +989,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles T
 // warp-aggregated appends.
 template <bool DENS>
 __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
-                             long long nst) {
+                             long long nst, int partial) {
   const int lane = threadIdx.x & 31;
   const long long ntask = npt + nst;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1010,12 +1010,23 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
       const int A0 = Lq.pair_a[item], B0 = Lq.pair_b[item];
       ti = T.tile0[A0] + (tp - Lq.p_toff[item]);
       rec = (unsigned int)item;
-      live = !DENS || TL.active[ti] || T.active[B0];
+      const bool iact = !DENS || partial == 0 || TL.active[ti];
+      live = iact || T.active[B0];
       if (live) {
         const PairSetup P = pair_setup(Lq, T, box, item);
         const Box3 bi = tile_box3(TL, T, ti, P.tshA);
         const float Hi = TL.lo[ti].w * P.g.invL;
         live = box_gap(bi, P.cellB) <= fmaxf(Hi, P.HmB) + P.slack;
+        if (live && !iact) {
+          // only B's active particles need this cluster: their box, in A's frame,
+          // must lie within B's largest H
+          Box3 ba;
+          ba.lo = make_float3(key_float(T.alo[3 * B0]) + P.g.offB.x, key_float(T.alo[3 * B0 + 1]) + P.g.offB.y,
+                              key_float(T.alo[3 * B0 + 2]) + P.g.offB.z);
+          ba.hi = make_float3(key_float(T.ahi[3 * B0]) + P.g.offB.x, key_float(T.ahi[3 * B0 + 1]) + P.g.offB.y,
+                              key_float(T.ahi[3 * B0 + 2]) + P.g.offB.z);
+          live = box_gap(bi, ba) <= P.HmB + P.slack;
+        }
       }
     }
     const unsigned int bal = __ballot_sync(0xffffffffu, live);
@@ -1096,13 +1107,40 @@ __global__ void k_zero_active(long long N, const unsigned char* __restrict__ act
 }
 
 // Mark every cell that holds a particle still iterating h (and its ancestors).
-__global__ void k_mark_active_cells(long long N, const unsigned char* __restrict__ act,
-                                    const unsigned int* __restrict__ leaf_of, Tree T) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    if (!act[p]) continue;
-    for (int id = (int)leaf_of[p]; id >= 0; id = T.parent[id]) {
-      if (T.active[id]) break;        // an ancestor chain already being marked
+// After an h iteration: the clusters and cells that still hold a particle
+// iterating h, and for every cell the box of those particles in the cell's
+// frame.  One warp per cluster; the cluster's box of active particles is added
+// to every cell on its chain with ordered-key atomics.
+__global__ void k_mark_active(long long ntile, const unsigned char* __restrict__ act,
+                              const float4* __restrict__ pos4, Tree T, Tiles TL) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = warp; t < ntile; t += nwarps) {
+    const unsigned int n = TL.n[t], s0 = TL.start[t];
+    const bool a = (unsigned int)lane < n && act[s0 + lane];
+    if (!__any_sync(0xffffffffu, a)) continue;
+    float3 lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
+    if (a) {
+      const float4 p = pos4[s0 + lane];
+      lo = make_float3(p.x, p.y, p.z);
+      hi = lo;
+    }
+    lo.x = warp_min(lo.x); lo.y = warp_min(lo.y); lo.z = warp_min(lo.z);
+    hi.x = warp_max(hi.x); hi.y = warp_max(hi.y); hi.z = warp_max(hi.z);
+    if (lane != 0) continue;
+    TL.active[t] = 1;
+    const float4 lc = TL.cen[t];
+    for (int id = (int)TL.leaf[t]; id >= 0; id = T.parent[id]) {
       T.active[id] = 1;
+      const float4 cc = T.cen[id];
+      const float ox = lc.x - cc.x, oy = lc.y - cc.y, oz = lc.z - cc.z;   // exact
+      atomicMin(&T.alo[3 * id], float_key(lo.x + ox));
+      atomicMin(&T.alo[3 * id + 1], float_key(lo.y + oy));
+      atomicMin(&T.alo[3 * id + 2], float_key(lo.z + oz));
+      atomicMax(&T.ahi[3 * id], float_key(hi.x + ox));
+      atomicMax(&T.ahi[3 * id + 1], float_key(hi.y + oy));
+      atomicMax(&T.ahi[3 * id + 2], float_key(hi.z + oz));
     }
   }
 }
@@ -1346,8 +1384,10 @@ void launch_live_tasks(Engine& E, bool dens) {
   const long long n = E.n_ptasks + E.n_stasks;
   if (n == 0) return;
   const int grid = (int)std::min<long long>((n + 255) / 256, (long long)E.nsm * 16);
-  if (dens) k_live_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks);
-  else k_live_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks);
+  if (dens)
+    k_live_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, E.partial_pass);
+  else
+    k_live_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, 0);
   count_launch();
 }
 
@@ -1381,8 +1421,10 @@ void launch_zero_density(Engine& E, bool all) {
 }
 
 void launch_set_active(Engine& E) {
+  E.partial_pass = 0;
   k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); count_launch();
   cudaMemsetAsync(E.t_active.p, 1, E.n_nodes, E.st);
+  cudaMemsetAsync(E.tl_active.p, 1, E.n_tiles, E.st);
 }
 
 void launch_count_unconverged(Engine& E, int* out) {
@@ -1390,8 +1432,13 @@ void launch_count_unconverged(Engine& E, int* out) {
 }
 
 void launch_mark_active_cells(Engine& E) {
+  E.partial_pass = 1;
   cudaMemsetAsync(E.t_active.p, 0, E.n_nodes, E.st);
-  k_mark_active_cells<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.leaf_of.p, E.T); count_launch();
+  cudaMemsetAsync(E.tl_active.p, 0, E.n_tiles, E.st);
+  cudaMemsetAsync(E.t_alo.p, 0xff, 3 * (size_t)E.n_nodes * sizeof(unsigned int), E.st);
+  cudaMemsetAsync(E.t_ahi.p, 0, 3 * (size_t)E.n_nodes * sizeof(unsigned int), E.st);
+  k_mark_active<<<E.grid(32 * E.n_tiles), 256, 0, E.st>>>(E.n_tiles, E.act.p, E.pos4.p, E.T, E.TL);
+  count_launch();
 }
 
 void launch_task_offsets(Engine& E) {

@@ -159,6 +159,7 @@ class Engine {
   DBuf<double> t_hlim;
   DBuf<float4> t_cen;
   DBuf<unsigned char> t_active;
+  DBuf<unsigned int> t_alo, t_ahi;
   DBuf<unsigned int> t_tile0, t_ntile;
   Tree T{};
 
@@ -168,6 +169,7 @@ class Engine {
   DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp, l_ptask, l_stask, l_nlive;
   DBuf<uint2> l_plive;
   long long n_ptasks = 0, n_stasks = 0;
+  int partial_pass = 0;           // 1 while the density passes cover only particles still iterating h
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
   Lists Lq{};
 

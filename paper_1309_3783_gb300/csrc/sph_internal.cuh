@@ -102,6 +102,9 @@ __device__ __forceinline__ unsigned int float_key(float f) {
   unsigned int u = __float_as_uint(f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
+__device__ __forceinline__ float key_float(unsigned int k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
 
 // ------------------------------------------- exact neighbour decision in FP64
 // The fixed evaluation both this path and the oracle use for r_ij < H:
@@ -174,6 +177,8 @@ struct Tree {
   unsigned int* axes;       // bit a: a sorted list along axis a is needed
   unsigned int* sortbase;   // offset of the first sorted list of this cell
   unsigned char* active;    // 1 when a particle inside still iterates h
+  unsigned int* alo;        // box of the particles still iterating h, relative to the
+  unsigned int* ahi;        //   cell centre (units of L), 3 orderable float keys each
   unsigned int* tile0;      // first cluster of the cell (clusters of a cell are contiguous)
   unsigned int* ntile;      // clusters of the cell
   int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier

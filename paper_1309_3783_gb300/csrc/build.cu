@@ -356,87 +356,120 @@ __global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc*
   }
 }
 
-// Per-node statistics and the split rule of Section II-B / III-B:
-// split iff level < dcap, count > leaf_max and n_small > split_frac * count,
-// with n_small = #{H < edge/2 - margin}.
-__global__ void k_node_stats(Tree T, const BoxDesc* __restrict__ box, const float* __restrict__ Hs, int dcap,
-                             int leaf_max, float split_frac) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+// One round of the cell tree, one block of TREE_THREADS per frontier node (a
+// top cell can hold a large share of the box): the node's statistics and the
+// split rule of Section II-B / III-B -- split iff level < dcap,
+// count > leaf_max and n_small > split_frac * count, with
+// n_small = #{H < edge/2 - margin} -- and, for a split node, its children: the
+// non-empty octants, counted from the Morton digit of the next level in the
+// same pass over the node's particles (sorted keys make each octant a
+// contiguous range).  Children of one node get consecutive ids.
+constexpr int TREE_THREADS = 256;
+
+__global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDesc* __restrict__ box,
+                                                             const float* __restrict__ Hs,
+                                                             const unsigned long long* __restrict__ key, int dcap,
+                                                             int leaf_max, float split_frac, int allow_split,
+                                                             int cap_nodes, unsigned int* __restrict__ err_all) {
+  constexpr int NW = TREE_THREADS / 32;
+  __shared__ float s_hm[NW];
+  __shared__ unsigned int s_ns[NW], s_oc[NW][8];
+  __shared__ int s_c0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f0 = T.n_nodes[1], f1 = min(T.n_nodes[2], T.n_nodes[0]);
-  for (int id = f0 + warp; id < f1; id += nwarps) {
+  for (int id = f0 + blockIdx.x; id < f1; id += gridDim.x) {
     const int d = T.level[id];
     const BoxDesc bd = box[T.box[id]];
     const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
     const unsigned int s = T.start[id], c = T.count[id];
+    const bool may_split = allow_split && d < dcap && (int)c > leaf_max;
+    const int dig = 3 * (dcap - d - 1);   // Morton digit of level d + 1 (when may_split)
     float hm = 0.0f;
     unsigned int ns = 0;
-    for (unsigned int q = lane; q < c; q += 32) {
+    unsigned int oc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (unsigned int q = threadIdx.x; q < c; q += TREE_THREADS) {
       const float H = Hs[s + q];
       hm = fmaxf(hm, H);
       ns += ((double)H < half) ? 1u : 0u;
+      if (may_split) {
+        const unsigned int o = (unsigned int)(key[s + q] >> dig) & 7u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) oc[k] += (o == (unsigned int)k) ? 1u : 0u;
+      }
     }
     hm = warp_max(hm);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    if (may_split) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) oc[k] += __shfl_xor_sync(0xffffffffu, oc[k], o);
+    }
     if (lane == 0) {
-      T.hmax[id] = hm;
-      T.nsmall[id] = ns;
-      const bool sp = d < dcap && (int)c > leaf_max && (double)ns > (double)split_frac * (double)c;
-      T.split[id] = sp ? 1 : 0;
-      T.axes[id] = 0;
-      // limit the top grid sets on every particle: H < edge_k - margin
-      T.hlim[id] = (T.parent[id] < 0) ? __dsub_rn(ldexp(bd.L, -d), bd.margin) : 1e300;
-      unsigned int cx, cy, cz;
-      cell_coords(T.key[id], d, cx, cy, cz);
-      const double inv = ldexp(1.0, -d), invk = ldexp(1.0, -bd.k);
-      const int sh = d - bd.k;
-      const double tx = ((double)(cx >> sh) + 0.5) * invk, ty = ((double)(cy >> sh) + 0.5) * invk,
-                   tz = ((double)(cz >> sh) + 0.5) * invk;
-      T.cen[id] = make_float4((float)(((double)cx + 0.5) * inv - tx), (float)(((double)cy + 0.5) * inv - ty),
-                              (float)(((double)cz + 0.5) * inv - tz), (float)inv);
+      s_hm[w] = hm;
+      s_ns[w] = ns;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s_oc[w][k] = oc[k];
     }
-  }
-}
-
-// Children of every split frontier node: the non-empty octants, found by binary
-// search on the sorted keys; children of one node get consecutive ids.
-__global__ void k_split_nodes(Tree T, const unsigned long long* __restrict__ key, int dcap, int box_shift,
-                              int cap_nodes, unsigned int* __restrict__ err_all) {
-  const int f0 = T.n_nodes[1], f1 = min(T.n_nodes[2], cap_nodes);
-  for (int id = f0 + blockIdx.x * blockDim.x + threadIdx.x; id < f1; id += gridDim.x * blockDim.x) {
-    if (!T.split[id]) continue;
-    const int d = T.level[id];
-    const long long s = T.start[id], e = s + T.count[id];
-    long long bound[9];
-    bound[0] = s;
-    bound[8] = e;
-    const unsigned long long base = T.key[id] << 3;
-    for (int o = 1; o < 8; ++o) bound[o] = lower_bound_prefix(key, s, e, base | (unsigned long long)o, dcap, d + 1, box_shift);
-    int nch = 0;
-    for (int o = 0; o < 8; ++o) nch += (bound[o + 1] > bound[o]) ? 1 : 0;
-    const int c0 = atomicAdd(&T.n_nodes[0], nch);
-    if (c0 + nch > cap_nodes) {
-      atomicOr(err_all, ERR_OVERFLOW);
-      T.split[id] = 0;
-      continue;
+    __syncthreads();
+    if (w == 0) {
+      hm = lane < NW ? s_hm[lane] : 0.0f;
+      ns = lane < NW ? s_ns[lane] : 0u;
+      hm = warp_max(hm);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+      // lane k < 8 holds octant k's count
+      unsigned int mine = 0;
+      if (lane < 8)
+        for (int k = 0; k < NW; ++k) mine += s_oc[k][lane];
+      const bool sp = may_split && (double)ns > (double)split_frac * (double)c;
+      const unsigned int ne = __ballot_sync(0xffffffffu, lane < 8 && mine != 0);
+      const int nch = __popc(ne);
+      // start of octant `lane`: the counts of the octants before it
+      unsigned int before = mine;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, before, o);
+        if (lane >= o) before += y;
+      }
+      before -= mine;
+      int c0 = 0;
+      if (sp && lane == 0) c0 = atomicAdd(&T.n_nodes[0], nch);
+      c0 = __shfl_sync(0xffffffffu, c0, 0);
+      const bool fits = c0 + nch <= cap_nodes;
+      if (sp && fits && lane < 8 && mine != 0) {
+        const int cid = c0 + __popc(ne & ((1u << lane) - 1u));
+        T.start[cid] = s + before;
+        T.count[cid] = mine;
+        T.key[cid] = (T.key[id] << 3) | (unsigned long long)lane;
+        T.level[cid] = d + 1;
+        T.box[cid] = T.box[id];
+        T.parent[cid] = id;
+        T.child[cid] = -1;
+        T.nchild[cid] = 0;
+      }
+      if (lane == 0) {
+        if (sp && !fits) atomicOr(err_all, ERR_OVERFLOW);
+        T.hmax[id] = hm;
+        T.nsmall[id] = ns;
+        T.split[id] = (sp && fits) ? 1 : 0;
+        T.child[id] = (sp && fits) ? c0 : -1;
+        T.nchild[id] = (sp && fits) ? nch : 0;
+        T.axes[id] = 0;
+        // limit the top grid sets on every particle: H < edge_k - margin
+        T.hlim[id] = (T.parent[id] < 0) ? __dsub_rn(ldexp(bd.L, -d), bd.margin) : 1e300;
+        unsigned int cx, cy, cz;
+        cell_coords(T.key[id], d, cx, cy, cz);
+        const double inv = ldexp(1.0, -d), invk = ldexp(1.0, -bd.k);
+        const int sh = d - bd.k;
+        const double tx = ((double)(cx >> sh) + 0.5) * invk, ty = ((double)(cy >> sh) + 0.5) * invk,
+                     tz = ((double)(cz >> sh) + 0.5) * invk;
+        T.cen[id] = make_float4((float)(((double)cx + 0.5) * inv - tx), (float)(((double)cy + 0.5) * inv - ty),
+                                (float)(((double)cz + 0.5) * inv - tz), (float)inv);
+      }
     }
-    int c = c0;
-    for (int o = 0; o < 8; ++o) {
-      if (bound[o + 1] <= bound[o]) continue;
-      T.start[c] = (unsigned int)bound[o];
-      T.count[c] = (unsigned int)(bound[o + 1] - bound[o]);
-      T.key[c] = base | (unsigned long long)o;
-      T.level[c] = d + 1;
-      T.box[c] = T.box[id];
-      T.parent[c] = id;
-      T.child[c] = -1;
-      T.nchild[c] = 0;
-      ++c;
-    }
-    T.child[id] = c0;
-    T.nchild[id] = nch;
+    __syncthreads();
   }
 }
 
@@ -778,7 +811,7 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
 // global sort.
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
                              unsigned int* __restrict__ big_off, unsigned long long* __restrict__ big_count,
-                             int cap_big) {
+                             int cap_big, uint4* __restrict__ mid_seg, unsigned int* __restrict__ mid_count) {
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int ax = T.axes[id];
     if (!ax) continue;
@@ -788,8 +821,19 @@ __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big
       continue;
     }
     const int na = __popc(ax);
-    T.sortbase[id] = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
+    const unsigned int base = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
+    T.sortbase[id] = base;
     atomicAdd(&Lq.counts[4], na);
+    if (c <= SORT_SMALL) {
+      // one shared-memory sort per (cell, axis) segment
+      const unsigned int g0 = atomicAdd(mid_count, (unsigned int)na);
+      unsigned int q = 0;
+      for (int a = 0; a < 13; ++a) {
+        if (!(ax & (1u << a))) continue;
+        mid_seg[g0 + q] = make_uint4((unsigned int)id, (unsigned int)a, base + q * c, c);
+        ++q;
+      }
+    }
     if (c > SORT_SMALL) {
       // one atomic hands out the segment numbers and their storage together, so
       // storage follows segment order (the order the global sort produces)
@@ -831,24 +875,24 @@ __device__ __forceinline__ float tile_rlo(const Tiles& TL, const Tree& T, unsign
   return fmaf(u.x, x, fmaf(u.y, y, u.z * z));
 }
 
-// One CTA per cell with at most SORT_SMALL clusters: bitonic sort of
-// (projection, cluster) in shared memory for every needed axis.
-__global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, Tiles TL, float* __restrict__ sort_r,
-                                                   unsigned int* __restrict__ sort_i) {
+// One CTA per (cell, axis) segment of at most SORT_SMALL clusters: bitonic
+// sort of (projection, cluster) in shared memory.
+__global__ void __launch_bounds__(256) k_sort_small(const uint4* __restrict__ mid_seg,
+                                                   const unsigned int* __restrict__ mid_count, Tree T, Tiles TL,
+                                                   float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
   __shared__ float sr[SORT_SMALL];
   __shared__ unsigned int si[SORT_SMALL];
-  for (int id = blockIdx.x; id < nnodes; id += gridDim.x) {
-    const unsigned int ax = T.axes[id];
-    const unsigned int c = T.ntile[id];
-    if (!ax || c <= 32u || c > SORT_SMALL) continue;
+  const unsigned int nseg = *mid_count;
+  for (unsigned int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const uint4 seg = mid_seg[sg];
+    const int id = (int)seg.x;
+    const unsigned int c = seg.w, out = seg.z;
     unsigned int npow = 1;
     while (npow < c) npow <<= 1;
     const unsigned int t0 = T.tile0[id];
     const float4 cc = T.cen[id];
-    unsigned int out = T.sortbase[id];
-    for (int a = 0; a < 13; ++a) {
-      if (!(ax & (1u << a))) continue;
-      const float3 u = axis_unit(a);
+    {
+      const float3 u = axis_unit((int)seg.y);
       for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
         sr[q] = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
         si[q] = q;
@@ -876,7 +920,6 @@ __global__ void __launch_bounds__(256) k_sort_small(Tree T, int nnodes, Tiles TL
         sort_r[out + q] = sr[q];
         sort_i[out + q] = t0 + si[q];
       }
-      out += c;
       __syncthreads();
     }
   }

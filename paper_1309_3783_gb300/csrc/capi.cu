@@ -22,8 +22,8 @@ __global__ void k_gather_sorted(long long, const unsigned int*, const float*, co
                                 float4*);
 __global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned long long*, Tree, int, int*,
                             unsigned int*);
-__global__ void k_node_stats(Tree, const BoxDesc*, const float*, int, int, float);
-__global__ void k_split_nodes(Tree, const unsigned long long*, int, int, int, unsigned int*);
+__global__ void k_tree_round(Tree, const BoxDesc*, const float*, const unsigned long long*, int, int, float, int,
+                             int, unsigned int*);
 __global__ void k_frontier_next(Tree, int);
 __global__ void k_frontier_init(Tree, int);
 __global__ void k_items_top(int, Tree, const BoxDesc*, const unsigned long long*, const int*, int, int, Lists, int,
@@ -34,8 +34,9 @@ __global__ void k_particle_limits(long long, Tree, const unsigned int*, float*);
 __global__ void k_shift(long long, int, const unsigned long long*, const unsigned int*, const unsigned int*, Tree,
                         const BoxDesc*, const double*, const float*, const float*, float4*, float4*);
 __global__ void k_mark_axes(Lists, int, Tree);
-__global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, unsigned long long*, int);
-__global__ void k_sort_small(Tree, int, Tiles, float*, unsigned int*);
+__global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, unsigned long long*, int, uint4*,
+                             unsigned int*);
+__global__ void k_sort_small(const uint4*, const unsigned int*, Tree, Tiles, float*, unsigned int*);
 __global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, Tiles, unsigned long long*,
                                 unsigned int*);
 __global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, Tiles,
@@ -481,9 +482,9 @@ sph_status Engine::build_once(bool* retry) {
   k_frontier_init<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
   const int rounds = dcap - kmin + 1;
   for (int r = 0; r < rounds; ++r) {
-    k_node_stats<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, dcap, prm.leaf_max, prm.split_frac); count_launch();
+    k_tree_round<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, key.p, dcap, prm.leaf_max, prm.split_frac,
+                                          r + 1 < rounds ? 1 : 0, cap_nodes, err_all.p); count_launch();
     if (r + 1 < rounds) {
-      k_split_nodes<<<nsm * 4, 128, 0, st>>>(T, key.p, dcap, box_shift, cap_nodes, err_all.p); count_launch();
       k_frontier_next<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
     }
   }
@@ -544,9 +545,12 @@ sph_status Engine::build_once(bool* retry) {
   }
   ev = prof_begin(PH_AXIS_SORT, &l0);
   CK(cudaMemsetAsync(big_count.p, 0, sizeof(unsigned long long), st));
+  CK(mid_seg.reserve(13 * (size_t)std::max(n_nodes, 1)));
+  CK(mid_count.reserve(1));
+  CK(cudaMemsetAsync(mid_count.p, 0, sizeof(unsigned int), st));
   k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T); count_launch();
   k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
-                                              cap_big); count_launch();
+                                              cap_big, mid_seg.p, mid_count.p); count_launch();
   launch_task_offsets(*this);
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
@@ -596,7 +600,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   ev = prof_begin(PH_AXIS_SORT, &l0);
-  k_sort_small<<<nsm * 8, 256, 0, st>>>(T, n_nodes, TL, sort_r.p, sort_i.p); count_launch();
+  k_sort_small<<<nsm * 8, 256, 0, st>>>(mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p); count_launch();
   if (n_big > 0) {
     const size_t nb = (size_t)n_big_entries;
     CK(ckey.reserve(nb));

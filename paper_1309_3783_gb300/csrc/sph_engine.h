@@ -160,6 +160,8 @@ class Engine {
   DBuf<float4> t_cen;
   DBuf<unsigned char> t_active;
   DBuf<unsigned int> t_alo, t_ahi;
+  DBuf<uint4> mid_seg;            // (cell, axis, storage offset, clusters) of every shared-memory sort
+  DBuf<unsigned int> mid_count;
   DBuf<unsigned int> t_tile0, t_ntile;
   Tree T{};
 

@@ -374,7 +374,6 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
   constexpr int NW = TREE_THREADS / 32;
   __shared__ float s_hm[NW];
   __shared__ unsigned int s_ns[NW], s_oc[NW][8];
-  __shared__ int s_c0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f0 = T.n_nodes[1], f1 = min(T.n_nodes[2], T.n_nodes[0]);
   for (int id = f0 + blockIdx.x; id < f1; id += gridDim.x) {
@@ -500,34 +499,35 @@ __device__ __forceinline__ void push_item(Lists Lq, int out, int kind, int a, in
 
 // Top level: the self-interaction of every non-empty top cell and its pairs with
 // the non-empty neighbours along the 13 positive directions (periodic images
-// included; a box has at least 4 top cells per dimension when periodic).
+// included; a box has at least 4 top cells per dimension when periodic).  One
+// thread per (top cell, direction), each with one binary search.
 __global__ void k_items_top(int ntop, Tree T, const BoxDesc* __restrict__ box, const unsigned long long* __restrict__ key,
                             const int* __restrict__ top_at, int dcap, int box_shift, Lists Lq, int cap_queue,
                             unsigned int* __restrict__ err_all) {
-  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < ntop; id += gridDim.x * blockDim.x) {
+  const long long n = 13ll * ntop;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += (long long)gridDim.x * blockDim.x) {
+    const int id = (int)(w / 13), a = (int)(w % 13);
     const int b = T.box[id];
     const BoxDesc bd = box[b];
     const int k = bd.k;
-    push_item(Lq, 0, 0, id, -1, 0, cap_queue, err_all);
+    if (a == 0) push_item(Lq, 0, 0, id, -1, 0, cap_queue, err_all);
     unsigned int cx, cy, cz;
     cell_coords(T.key[id], k, cx, cy, cz);
     const int side = 1 << k;
-    for (int a = 0; a < 13; ++a) {
-      int dx, dy, dz;
-      axis_vec(a, dx, dy, dz);
-      int nx = (int)cx + dx, ny = (int)cy + dy, nz = (int)cz + dz;
-      if (bd.periodic) {
-        nx = (nx + side) % side;
-        ny = (ny + side) % side;
-        nz = (nz + side) % side;
-      } else if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side) {
-        continue;
-      }
-      const unsigned long long target = ((unsigned long long)b << (3 * k)) | morton3(nx, ny, nz);
-      const long long p = lower_bound_prefix(key, bd.off, bd.off + bd.n, target, dcap, k, box_shift);
-      if (p < bd.off + bd.n && prefix_at(key[p], dcap, k, box_shift) == target)
-        push_item(Lq, 0, 1, id, top_at[p], a, cap_queue, err_all);
+    int dx, dy, dz;
+    axis_vec(a, dx, dy, dz);
+    int nx = (int)cx + dx, ny = (int)cy + dy, nz = (int)cz + dz;
+    if (bd.periodic) {
+      nx = (nx + side) % side;
+      ny = (ny + side) % side;
+      nz = (nz + side) % side;
+    } else if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side) {
+      continue;
     }
+    const unsigned long long target = ((unsigned long long)b << (3 * k)) | morton3(nx, ny, nz);
+    const long long p = lower_bound_prefix(key, bd.off, bd.off + bd.n, target, dcap, k, box_shift);
+    if (p < bd.off + bd.n && prefix_at(key[p], dcap, k, box_shift) == target)
+      push_item(Lq, 0, 1, id, top_at[p], a, cap_queue, err_all);
   }
 }
 

@@ -507,7 +507,7 @@ sph_status Engine::build_once(bool* retry) {
   // ---- interaction lists
   ev = prof_begin(PH_LISTS, &l0);
   CK(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
-  k_items_top<<<grid(n_top), 256, 0, st>>>(n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
+  k_items_top<<<grid(13ll * n_top), 256, 0, st>>>(n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
                                            err_all.p); count_launch();
   for (int r = 0; r < rounds; ++r) {
     const int in = r & 1;

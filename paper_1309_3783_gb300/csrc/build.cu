@@ -64,7 +64,7 @@ __global__ void k_keys(long long N, int dcap, const int* __restrict__ bid, const
     unsigned int q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double uu = __ddiv_rn(x[3 * p + k], L);
+      const double uu = box[b].pow2 ? x[3 * p + k] * box[b].invL : __ddiv_rn(x[3 * p + k], L);
       double f = floor(__dmul_rn(uu, scale));
       f = fmin(fmax(f, 0.0), (double)qmax);
       q[k] = (unsigned int)f;
@@ -641,9 +641,15 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
     unsigned int cx, cy, cz;
     cell_coords(T.key[leaf], d, cx, cy, cz);
     const double inv = ldexp(1.0, -d);
-    const float sx = (float)(__ddiv_rn(x[3ll * i], L) - ((double)cx + 0.5) * inv);
-    const float sy = (float)(__ddiv_rn(x[3ll * i + 1], L) - ((double)cy + 0.5) * inv);
-    const float sz = (float)(__ddiv_rn(x[3ll * i + 2], L) - ((double)cz + 0.5) * inv);
+    // x / L: a power-of-two L scales exactly, so the FP64 division is needed only otherwise
+    const bool p2 = box[b].pow2 != 0;
+    const double iL = box[b].invL;
+    const double ux = p2 ? x[3ll * i] * iL : __ddiv_rn(x[3ll * i], L);
+    const double uy = p2 ? x[3ll * i + 1] * iL : __ddiv_rn(x[3ll * i + 1], L);
+    const double uz = p2 ? x[3ll * i + 2] * iL : __ddiv_rn(x[3ll * i + 2], L);
+    const float sx = (float)(ux - ((double)cx + 0.5) * inv);
+    const float sy = (float)(uy - ((double)cy + 0.5) * inv);
+    const float sz = (float)(uz - ((double)cz + 0.5) * inv);
     pos4[p] = make_float4(sx, sy, sz, Hs[p]);
     const float4 c = T.cen[leaf];
     cen4[p] = make_float4(c.x, c.y, c.z, m[i]);

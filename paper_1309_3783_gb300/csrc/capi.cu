@@ -178,6 +178,8 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
     d.off = off[b];
     d.n = boxes[b].n;
     d.periodic = boxes[b].periodic;
+    int ex = 0;
+    d.pow2 = std::frexp(boxes[b].L, &ex) == 0.5 ? 1u : 0u;
   }
   built = have_density = have_ghost = have_force = have_acc = false;
   sph_status s = ensure_particle_capacity();

@@ -1076,7 +1076,12 @@ __global__ void k_ghost(long long N, int mode, int it, int max_iter, float gamma
       pos4[p].w = Hn;
       if (!(Hn < hlimp[p])) atomicOr(err_all, ERR_REBUILD);
       if (Hn > H) {
-        for (int id = (int)leaf_of[p]; id >= 0; id = T.parent[id]) atomic_max_pos(&T.hmax[id], Hn);
+        // a cell's H_max bounds its children's: the climb ends at the first cell
+        // that already covers Hn
+        for (int id = (int)leaf_of[p]; id >= 0; id = T.parent[id]) {
+          if (T.hmax[id] >= Hn) break;
+          atomic_max_pos(&T.hmax[id], Hn);
+        }
       }
       atomicAdd(n_active, 1);
       continue;
@@ -1195,65 +1200,45 @@ __global__ void k_h_bracket_reset(long long N, float* __restrict__ hlo, float* _
 }
 
 // =========================================================================== reductions
-// Per box, in FP64: sum m a (3), sum m (v.a + du/dt), sum m v (3), sum m (v^2/2 + u).
-// Each block accumulates its particles per box in shared memory (boxes are
-// contiguous, so a block spans few of them) and adds its partial sums once.
-__global__ void __launch_bounds__(256) k_reduce(long long N, int box_shift, const unsigned long long* __restrict__ key,
+// FP64 conservation sums per box: sum m a (3), sum m (v.a + du/dt), sum m v (3),
+// sum m (v^2/2 + u).  Block row y reduces boxes y, y + gridDim.y, ...: every
+// thread accumulates its particles of the box in FP64 registers, then one block
+// reduction and eight atomics per box.
+__global__ void __launch_bounds__(256) k_reduce(int nbox, const long long* __restrict__ boff,
                                                 const float4* __restrict__ cen4, const float4* __restrict__ vel4,
                                                 const float4* __restrict__ facc, double* __restrict__ red) {
-  __shared__ double part[4][8];     // up to four boxes per block-chunk, flushed when a new box appears
-  __shared__ int pbox[4];
-  const long long chunk = (N + gridDim.x - 1) / gridDim.x;
-  const long long p0 = blockIdx.x * chunk, p1 = min(N, p0 + chunk);
-  for (long long base = p0; base < p1; base += blockDim.x) {
-    const long long p = base + threadIdx.x;
-    const bool valid = p < p1;
-    const int b = valid ? (int)(key[p] >> box_shift) : -1;
-    const int b0 = (int)(key[base] >> box_shift);
+  __shared__ double part[8][8];
+  for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
+    const long long p0 = boff[b], p1 = boff[b + 1];
     double val[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (valid) {
+    for (long long p = p0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < p1;
+         p += (long long)gridDim.x * blockDim.x) {
       const double m = cen4[p].w;
       const float4 vv = vel4[p];
       const float4 a = facc[p];
-      val[0] = m * a.x;
-      val[1] = m * a.y;
-      val[2] = m * a.z;
-      val[3] = m * ((double)vv.x * a.x + (double)vv.y * a.y + (double)vv.z * a.z + (double)a.w);
-      val[4] = m * vv.x;
-      val[5] = m * vv.y;
-      val[6] = m * vv.z;
-      val[7] = m * (0.5 * ((double)vv.x * vv.x + (double)vv.y * vv.y + (double)vv.z * vv.z) + (double)vv.w);
+      const double vx = vv.x, vy = vv.y, vz = vv.z;
+      val[0] += m * a.x;
+      val[1] += m * a.y;
+      val[2] += m * a.z;
+      val[3] += m * (vx * a.x + vy * a.y + vz * a.z + (double)a.w);
+      val[4] += m * vx;
+      val[5] += m * vy;
+      val[6] += m * vz;
+      val[7] += m * (0.5 * (vx * vx + vy * vy + vz * vz) + (double)vv.w);
     }
-    // slots: box b0 + 0..3 of this pass; boxes further away go straight to global
-    if (threadIdx.x < 32) {
-      part[threadIdx.x >> 3][threadIdx.x & 7] = 0.0;
-      if (threadIdx.x < 4) pbox[threadIdx.x] = b0 + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double v = val[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) part[w][k] = v;
     }
     __syncthreads();
-    const int slot = b - b0;
-    if (valid) {
-      if (slot >= 0 && slot < 4) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          double v = val[k];
-          // lanes of the same slot reduce in registers first
-          const unsigned int same = __match_any_sync(__activemask(), slot);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_down_sync(__activemask(), v, o);
-            const int os = __shfl_down_sync(__activemask(), slot, o);
-            if ((threadIdx.x & 31) + o < 32 && os == slot && ((same >> ((threadIdx.x & 31) + o)) & 1u)) v += w;
-          }
-          if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&part[slot][k], v);
-        }
-      } else {
-        for (int k = 0; k < 8; ++k) atomicAdd(&red[8 * b + k], val[k]);
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int sl = threadIdx.x >> 3, k = threadIdx.x & 7;
-      if (part[sl][k] != 0.0) atomicAdd(&red[8 * pbox[sl] + k], part[sl][k]);
+    if (threadIdx.x < 8) {
+      double v = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += part[q][threadIdx.x];
+      atomicAdd(&red[8 * b + threadIdx.x], v);
     }
     __syncthreads();
   }
@@ -1459,7 +1444,11 @@ void launch_bracket_reset(Engine& E) {
 
 void launch_reduce(Engine& E) {
   cudaMemsetAsync(E.red.p, 0, sizeof(double) * 8 * E.nbox, E.st);
-  k_reduce<<<E.nsm * 2, 256, 0, E.st>>>(E.N, E.box_shift, E.key.p, E.cen4.p, E.vel4.p, E.facc.p, E.red.p); count_launch();
+  long long maxn = 1;
+  for (int b = 0; b < E.nbox; ++b) maxn = std::max(maxn, E.spec[b].n);
+  const int gx = (int)std::max<long long>(1, std::min<long long>((maxn + 255) / 256, (E.nsm * 4 + E.nbox - 1) / E.nbox));
+  k_reduce<<<dim3(gx, std::min(E.nbox, 65535)), 256, 0, E.st>>>(E.nbox, E.boff.p, E.cen4.p, E.vel4.p, E.facc.p,
+                                                                 E.red.p); count_launch();
 }
 
 void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); count_launch(); }

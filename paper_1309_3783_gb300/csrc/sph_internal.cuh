@@ -28,7 +28,7 @@ struct BoxDesc {
   int k;                // top level: cell edge L / 2^k
   float Hmax, Hmin;     // extremes of the support radius (physical units)
   unsigned int err;     // ERR_* bits
-  unsigned int pad;
+  unsigned int pow2;    // 1 when L is a power of two: x / L is then exactly x * invL
   double dt;            // time step of the box (0: passes only)
 };
 

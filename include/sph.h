@@ -84,6 +84,14 @@ typedef struct sph_params {
                              H (1 + split_headroom) clears the limit, so that h
                              may grow by that much before the interactions must be
                              rebuilt; 0 = the paper's rule exactly (0.1)        */
+    int32_t reuse;        /* 1: sph_step keeps the cell decomposition, its lists and
+                             sorted indices over steps while they stay valid
+                             (Section II-C: sorted indices re-used until the
+                             decomposition must be re-computed): every particle keeps
+                             its cell, and H + 2 * (largest displacement since the
+                             build) must stay below the limit its interactions
+                             assumed, else the step rebuilds.  0: rebuild every
+                             step (0)                                            */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;
@@ -139,6 +147,8 @@ typedef struct sph_stats {
     int64_t force_pairs_cellpair;
     int64_t force_candidates_cellpair;
     int64_t guard_rechecks;     /* predicate decisions re-taken in FP64               */
+    int64_t builds;             /* full decompositions built since the box was set    */
+    int64_t reuses;             /* steps that kept the decomposition (params.reuse)   */
 } sph_stats;
 
 /* Device time of one phase of the path (CUDA events on the context stream). */
@@ -146,7 +156,8 @@ typedef struct sph_profile_entry {
     char name[32];              /* ingest, keys_sort, tree, lists, shift, axis_sort,
                                    density (pair and self interactions),
                                    density_tasks (the pass's live task list), ghost,
-                                   force, force_tasks, reduce, kick_drift, output */
+                                   force, force_tasks, reduce, kick_drift, output,
+                                   reuse (keeping the decomposition, params.reuse) */
     int64_t calls;              /* times the phase ran while recording                */
     int64_t launches;           /* kernel launches inside it                          */
     double ms;                  /* summed device time                                 */

@@ -110,6 +110,116 @@ __global__ void k_relayout(const long long* __restrict__ tab, const double* __re
   }
 }
 
+// ============================================================== decomposition reuse
+// Largest displacement of every box since its decomposition was built (FP64,
+// periodic minimum image), as the bits of a non-negative double (they order
+// like the values).
+__global__ void k_displacement(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
+                               const double* __restrict__ x, const double* __restrict__ xb,
+                               unsigned long long* __restrict__ dmax) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
+    const long long p = base + threadIdx.x;   // every lane of a warp runs every iteration
+    const bool valid = p < N;
+    const int b = valid ? bid[p] : -1;
+    double d2 = 0.0;
+    if (valid) {
+      const double L = box[b].L, halfL = 0.5 * box[b].L;
+      const int per = box[b].periodic;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double t = x[3 * p + k] - xb[3 * p + k];
+        if (per) {
+          if (t > halfL) t -= L;
+          else if (t < -halfL) t += L;
+        }
+        d2 = fma(t, t, d2);
+      }
+    }
+    unsigned long long bits = valid ? (unsigned long long)__double_as_longlong(sqrt(d2)) : 0ull;
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    if (__all_sync(0xffffffffu, !valid || b == b0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = y > bits ? y : bits;
+      }
+      if ((threadIdx.x & 31) == 0 && b0 >= 0) atomicMax(&dmax[b0], bits);
+    } else if (valid) {
+      atomicMax(&dmax[b], bits);
+    }
+  }
+}
+
+// The limit every particle's H must stay below with the decomposition kept:
+// the split limits along its chain of cells minus twice its box's largest
+// displacement (a pair within H may then have been up to H + 2 d apart when the
+// cells were assigned).  flag = 1 when some particle's current H is not below
+// its limit, i.e. the decomposition must be rebuilt.
+__global__ void k_reuse_limits(long long N, int box_shift, const unsigned long long* __restrict__ key, Tree T,
+                               const unsigned int* __restrict__ leaf_of, const unsigned int* __restrict__ perm,
+                               const float* __restrict__ h, float gamma_k,
+                               const unsigned long long* __restrict__ dmax, float* __restrict__ hlimp,
+                               unsigned int* __restrict__ flag) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(key[p] >> box_shift);
+    int id = (int)leaf_of[p];
+    double lim = 1e300;
+    while (id >= 0) {
+      lim = fmin(lim, T.hlim[id]);
+      id = T.parent[id];
+    }
+    lim -= 2.0 * __longlong_as_double((long long)dmax[b]);
+    const float lf = __double2float_rz(lim);
+    hlimp[p] = lf;
+    const float H = __fmul_rn(gamma_k, h[perm[p]]);
+    if (!(H < lf)) atomicOr(flag, 1u);
+  }
+}
+
+// Largest H of every cell from its leaves (cell H_max entries start at 0): one
+// warp per leaf, then a climb that stops at the first cell already covering it.
+__global__ void k_leaf_hmax(Tree T, int nnodes, const float* __restrict__ Hs) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int id = warp; id < nnodes; id += nwarps) {
+    if (T.child[id] >= 0) continue;
+    const unsigned int s = T.start[id], c = T.count[id];
+    float hm = 0.0f;
+    for (unsigned int q = lane; q < c; q += 32) hm = fmaxf(hm, Hs[s + q]);
+    hm = warp_max(hm);
+    if (lane != 0) continue;
+    for (int a = id; a >= 0; a = T.parent[a]) {
+      if (T.hmax[a] >= hm) break;
+      atomic_max_pos(&T.hmax[a], hm);
+    }
+  }
+}
+
+// Cluster boxes from the current offsets (membership kept): one warp per cluster.
+__global__ void k_tile_boxes(long long ntile, Tiles TL, const float4* __restrict__ pos4) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = warp; t < ntile; t += nwarps) {
+    const unsigned int n = TL.n[t], s0 = TL.start[t];
+    float4 lo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.0f), hi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.0f);
+    if ((unsigned int)lane < n) {
+      const float4 a = pos4[s0 + lane];
+      lo = make_float4(a.x, a.y, a.z, a.w);
+      hi = make_float4(a.x, a.y, a.z, 0.0f);
+    }
+    lo.x = warp_min(lo.x); lo.y = warp_min(lo.y); lo.z = warp_min(lo.z); lo.w = warp_max(lo.w);
+    hi.x = warp_max(hi.x); hi.y = warp_max(hi.y); hi.z = warp_max(hi.z);
+    if (lane == 0) {
+      TL.lo[t] = lo;
+      TL.hi[t] = hi;
+      TL.active[t] = 1;
+    }
+  }
+}
+
 // ============================================================== radix sort
 // Stable LSD radix sort of (64-bit key, 32-bit value), 8-bit digits.  Each
 // pass: per-tile digit histograms, one exclusive scan of the digit-major
@@ -647,9 +757,14 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
     const double ux = p2 ? x[3ll * i] * iL : __ddiv_rn(x[3ll * i], L);
     const double uy = p2 ? x[3ll * i + 1] * iL : __ddiv_rn(x[3ll * i + 1], L);
     const double uz = p2 ? x[3ll * i + 2] * iL : __ddiv_rn(x[3ll * i + 2], L);
-    const float sx = (float)(ux - ((double)cx + 0.5) * inv);
-    const float sy = (float)(uy - ((double)cy + 0.5) * inv);
-    const float sz = (float)(uz - ((double)cz + 0.5) * inv);
+    double ox = ux - ((double)cx + 0.5) * inv, oy = uy - ((double)cy + 0.5) * inv, oz = uz - ((double)cz + 0.5) * inv;
+    if (box[b].periodic) {
+      // a particle kept in its cell after a drift across the boundary: nearest image
+      ox -= rint(ox);
+      oy -= rint(oy);
+      oz -= rint(oz);
+    }
+    const float sx = (float)ox, sy = (float)oy, sz = (float)oz;
     pos4[p] = make_float4(sx, sy, sz, Hs[p]);
     const float4 c = T.cen[leaf];
     cen4[p] = make_float4(c.x, c.y, c.z, m[i]);

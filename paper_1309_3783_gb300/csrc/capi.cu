@@ -16,6 +16,13 @@ __global__ void k_ingest(long long, const int*, BoxDesc*, const double*, const f
                          const float*, float, float*);
 __global__ void k_keys(long long, int, const int*, const BoxDesc*, const double*, unsigned long long*, unsigned int*);
 __global__ void k_box_ids(long long, int, const long long*, int*);
+__global__ void k_displacement(long long, const int*, const BoxDesc*, const double*, const double*,
+                               unsigned long long*);
+__global__ void k_reuse_limits(long long, int, const unsigned long long*, Tree, const unsigned int*,
+                               const unsigned int*, const float*, float, const unsigned long long*, float*,
+                               unsigned int*);
+__global__ void k_leaf_hmax(Tree, int, const float*);
+__global__ void k_tile_boxes(long long, Tiles, const float4*);
 __global__ void k_relayout(const long long*, const double*, const float*, const float*, const float*, const float*,
                            const float4*, double*, float*, float*, float*, float*, float4*);
 __global__ void k_gather_sorted(long long, const unsigned int*, const float*, const float*, const float*, float*,
@@ -82,7 +89,7 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 const char* const kPhaseNames[PH_COUNT] = {"ingest",     "keys_sort",   "tree",      "lists",
                                            "shift",      "axis_sort",   "density",   "density_tasks",
                                            "ghost",      "force",       "force_tasks", "reduce",
-                                           "kick_drift", "output"};
+                                           "kick_drift", "output",      "reuse"};
 
 int Engine::prof_begin(int phase, long long* l0) {
   *l0 = launch_count();
@@ -182,6 +189,8 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
     d.pow2 = std::frexp(boxes[b].L, &ex) == 0.5 ? 1u : 0u;
   }
   built = have_density = have_ghost = have_force = have_acc = false;
+  reusable = false;
+  n_builds = n_reuses = 0;
   sph_status s = ensure_particle_capacity();
   if (s != SPH_OK) return s;
   CK(boff.reserve(nbox + 1));
@@ -241,6 +250,7 @@ sph_status Engine::ensure_particle_capacity() {
   CK(m.reserve(n));
   CK(u.reserve(n));
   CK(h.reserve(n));
+  CK(x_build.reserve(3 * n));
   CK(H_in.reserve(n));
   CK(hlo.reserve(n));
   CK(hhi.reserve(n));
@@ -400,6 +410,8 @@ sph_status Engine::set_particles(int b, const double* xx, const float* vv, const
   CK(cudaMemcpyAsync(u.p + o, uu, n * sizeof(float), kind, st));
   CK(cudaMemcpyAsync(h.p + o, hh, n * sizeof(float), kind, st));
   built = have_density = have_ghost = have_force = have_acc = false;
+  reusable = false;
+  n_builds = n_reuses = 0;
   return SPH_OK;
 }
 
@@ -429,7 +441,10 @@ sph_status Engine::build_once(bool* retry) {
     d.Hmin = INFINITY;
     d.err = 0;
     d.k = 0;
+    d.drift2 = 0.0f;
+    d.drift_u = 0.0f;
   }
+  reusable = false;
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
   {
     Scope sc(this, PH_INGEST);
@@ -621,6 +636,10 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaGetLastError());
   depth_used = 0;
   built = true;
+  // positions of this decomposition, for the displacement test of a later reuse
+  CK(cudaMemcpyAsync(x_build.p, x.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  reusable = true;
+  ++n_builds;
   return SPH_OK;
 }
 
@@ -785,7 +804,7 @@ sph_status Engine::step_boxes() {
     }
     CK(cudaGetLastError());
   }
-  s = build();
+  s = reuse_or_build();
   if (s != SPH_OK) return s;
   sph_status hs = h_update(nullptr, nullptr);
   if (hs != SPH_OK && hs != SPH_E_NOT_CONVERGED) return hs;
@@ -797,6 +816,55 @@ sph_status Engine::step_boxes() {
     CK(cudaGetLastError());
   }
   return hs;
+}
+
+// Decomposition reuse over steps (Section II-C: the sorted indices are re-used
+// until the decomposition must be re-computed).  The decomposition is kept when
+// every particle's H plus twice its box's largest displacement since the build
+// stays below the limit its interactions assumed: a pair within H was then at
+// most H + 2 d apart when its cells were assigned, so it is still covered by
+// exactly one interaction.  Particles keep their cells, clusters and sorted
+// indices; offsets, velocities, cluster boxes and cell H maxima are refreshed,
+// and the sweeps widen their tests by the displacement.
+sph_status Engine::reuse_or_build() {
+  if (!prm.reuse || !reusable) return build();
+  long long l0;
+  const int ev = prof_begin(PH_REUSE, &l0);
+  CK(dmax_bits.reserve(nbox));
+  CK(reuse_flag.reserve(1));
+  CK(cudaMemsetAsync(dmax_bits.p, 0, nbox * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(reuse_flag.p, 0, sizeof(unsigned int), st));
+  k_displacement<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, x_build.p, dmax_bits.p); count_launch();
+  k_reuse_limits<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, T, leaf_of.p, perm.p, h.p, prm.gamma_kernel,
+                                          dmax_bits.p, hlimp.p, reuse_flag.p); count_launch();
+  std::vector<unsigned long long> dm(nbox);
+  unsigned int flag = 0;
+  CK(cudaMemcpyAsync(dm.data(), dmax_bits.p, nbox * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&flag, reuse_flag.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) {
+    prof_end(PH_REUSE, ev, l0);
+    return build();
+  }
+  for (int b = 0; b < nbox; ++b) {
+    double d;
+    std::memcpy(&d, &dm[b], sizeof(d));
+    hbox[b].drift2 = (float)(2.0 * d);
+    hbox[b].drift_u = (float)(d / hbox[b].L);
+  }
+  CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
+  k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p); count_launch();
+  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  CK(cudaMemsetAsync(t_hmax.p, 0, n_nodes * sizeof(float), st));
+  k_leaf_hmax<<<nsm * 8, 256, 0, st>>>(T, n_nodes, Hs.p); count_launch();
+  k_tile_boxes<<<grid(32 * n_tiles), 256, 0, st>>>(n_tiles, TL, pos4.p); count_launch();
+  prof_end(PH_REUSE, ev, l0);
+  CK(cudaGetLastError());
+  built = true;
+  have_density = have_ghost = have_force = false;
+  ++n_reuses;
+  return SPH_OK;
 }
 
 // Leaf-size autotuning: time build + density + force for each candidate
@@ -929,6 +997,7 @@ sph_status Engine::set_field(int b, int field, const void* src, long long n, int
   if (field == SPH_FIELD_H) {
     CK(cudaMemcpyAsync(h.p + o, src, nb * sizeof(float), kind, st));
     built = have_density = have_ghost = have_force = false;
+    reusable = false;
     return SPH_OK;
   }
   if (field != SPH_FIELD_A && field != SPH_FIELD_DUDT) return fail(SPH_E_INVALID, "field cannot be set");
@@ -958,6 +1027,8 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->depth = dcap;
   o->h_iterations = last_iters;
   o->rebuilds = last_rebuilds;
+  o->builds = n_builds;
+  o->reuses = n_reuses;
   o->n_unconverged = last_unconverged;
   if (count_pairs) {
     unsigned long long c[16];
@@ -1082,6 +1153,7 @@ void sph_params_default(sph_params* p) {
   p->split_frac = 0.875f;
   p->max_depth = 20;
   p->split_headroom = 0.1f;
+  p->reuse = 0;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {

@@ -22,6 +22,7 @@ struct ItemGeom {
   float3 offB;      // centre of B minus centre of A (units of L), exact: e * db
   float offBp;      // projection of offB on the axis: e |db|
   float invL;
+  float drift;      // largest displacement since the decomposition was built (units of L)
   double L, halfL;
   int periodic;
 };
@@ -37,6 +38,7 @@ __device__ __forceinline__ ItemGeom item_geom(const Tree& T, const BoxDesc* box,
   const int n2 = dx * dx + dy * dy + dz * dz;
   g.offBp = g.e * (n2 == 1 ? 1.0f : (n2 == 2 ? 1.41421356237f : 1.73205080757f));
   g.invL = (float)bd.invL;
+  g.drift = bd.drift_u;
   g.L = bd.L;
   g.halfL = 0.5 * bd.L;
   g.periodic = bd.periodic;
@@ -639,7 +641,8 @@ __device__ __forceinline__ PairSetup pair_setup(const Lists& Lq, const Tree& T, 
   P.sb = sbB == SORT_NONE ? SORT_NONE : sbB + (unsigned int)__popc(T.axes[P.B] & ((1u << ax) - 1u)) * P.ntj;
   P.HmB = T.hmax[P.B] * P.g.invL;
   P.slack = P.g.e * 1.52587890625e-05f + 1e-6f * fmaxf(P.HmB, T.hmax[P.A] * P.g.invL);   // 2^-16 e
-  const float h = 0.5f * P.g.e;
+  // B's cell, widened by the drift of particles kept in it since the build
+  const float h = 0.5f * P.g.e + P.g.drift;
   P.cellB.lo = make_float3(P.g.offB.x - h, P.g.offB.y - h, P.g.offB.z - h);
   P.cellB.hi = make_float3(P.g.offB.x + h, P.g.offB.y + h, P.g.offB.z + h);
   return P;
@@ -660,7 +663,9 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
   const int lane = threadIdx.x & 31;
   const bool sorted = P.sb != SORT_NONE;
   if (sorted) {
-    const float r0 = sort_r[P.sb + e0] + P.g.offBp;
+    // sort keys are the projections at the build; a cluster's projection has
+    // since moved by at most the drift
+    const float r0 = sort_r[P.sb + e0] + P.g.offBp - P.g.drift;
     *stop = r0 - rhi_i > fmaxf(Hi, P.HmB) + P.slack;     // the sorted list only moves further away
     if (*stop) return 0u;
   } else {
@@ -672,7 +677,7 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
   if (e < P.ntj) {
     t = sorted ? sort_i[P.sb + e] : P.tb0 + e;
     const float reach = fmaxf(Hi, TL.lo[t].w * P.g.invL) + P.slack;
-    const bool window = !sorted || sort_r[P.sb + e] + P.g.offBp - rhi_i <= reach;
+    const bool window = !sorted || sort_r[P.sb + e] + P.g.offBp - P.g.drift - rhi_i <= reach;
     if (window && (!DENS || i_active || TL.active[t])) {
       const Box3 bj = tile_box3(TL, T, t, P.tshB);
       pass = box_gap(bi, bj) <= reach;

@@ -178,17 +178,17 @@ sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
   // admission in submission order while the footprint fits
   long long used = 0;
   for (long long id : s->resident) used += s->reqs[id].n * kBytesPerParticle;
-  bool admitted = false;
+
   while (!s->waiting.empty() && (int)s->resident.size() < s->max_boxes) {
     Request& r = s->reqs[s->waiting.front()];
     if (used + r.n * kBytesPerParticle > s->budget) break;
-    admitted = true;
+
     used += r.n * kBytesPerParticle;
     r.state = 1;
     s->resident.push_back(r.id);
     s->waiting.pop_front();
   }
-  (void)admitted;
+
   if (s->resident.empty()) return SPH_OK;
   if (s->resident != s->layout) {
     sph_status st = apply_layout(s);

@@ -58,7 +58,7 @@ long long launch_count();
 // Phases of the path timed with CUDA events when profiling is on.
 enum Phase {
   PH_INGEST, PH_SORT, PH_TREE, PH_LISTS, PH_SHIFT, PH_AXIS_SORT, PH_DENSITY, PH_DENSITY_TASKS, PH_GHOST,
-  PH_FORCE, PH_FORCE_TASKS, PH_REDUCE, PH_STEP, PH_OUTPUT, PH_COUNT
+  PH_FORCE, PH_FORCE_TASKS, PH_REDUCE, PH_STEP, PH_OUTPUT, PH_REUSE, PH_COUNT
 };
 extern const char* const kPhaseNames[PH_COUNT];
 
@@ -86,6 +86,7 @@ class Engine {
 
   // ---- the hot path -----------------------------------------------------------
   sph_status build();
+  sph_status reuse_or_build();        // keep the last decomposition while valid (prm.reuse), else build
   sph_status density();                                        // one pass at the current h, all particles
   sph_status h_update(long long* n_unconverged, int* iterations);
   sph_status force();
@@ -202,6 +203,11 @@ class Engine {
   int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0, depth_used = 0;
   long long n_entries = 0, n_big_entries = 0;
   int last_iters = 0, last_rebuilds = 0;
+  long long n_builds = 0, n_reuses = 0;
+  bool reusable = false;          // the last full build can be kept (positions since then tracked)
+  DBuf<double> x_build;           // positions at the last full build (input order)
+  DBuf<unsigned long long> dmax_bits;   // per box: largest displacement since the build (double bits)
+  DBuf<unsigned int> reuse_flag;
   long long last_unconverged = 0;
   bool built = false, have_density = false, have_ghost = false, have_force = false, have_acc = false;
 

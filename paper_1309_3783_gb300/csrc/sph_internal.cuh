@@ -29,6 +29,8 @@ struct BoxDesc {
   float Hmax, Hmin;     // extremes of the support radius (physical units)
   unsigned int err;     // ERR_* bits
   unsigned int pow2;    // 1 when L is a power of two: x / L is then exactly x * invL
+  float drift2;         // twice the largest displacement since the decomposition was built (physical)
+  float drift_u;        // the largest displacement since the build (units of L)
   double dt;            // time step of the box (0: passes only)
 };
 

@@ -171,3 +171,73 @@ def test_checkpoint_restart_continues_the_run(api, ctx):
     assert np.max(np.abs(d - box.L * np.round(d / box.L))) < 1e-9
     for k in ("v", "rho", "a"):
         assert np.max(np.abs(got[k] - ref[k])) <= 1e-4 * np.max(np.abs(ref[k])), k
+
+
+# ------------------------------------------------------------ decomposition reuse
+def _ctx_with(api, **kw):
+    p = api.sph_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return api.sph_ctx_create(p, device=0)
+
+
+def _run_steps(api, box, dt, n_steps, **kw):
+    c = _ctx_with(api, **kw)
+    try:
+        b = api.box_from(c, box)
+        try:
+            for _ in range(n_steps):
+                b.step(dt)
+            out = {k: b.get(k) for k in ("x", "v", "u", "h", "rho", "a", "count")}
+            out["stats"] = b.stats()
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    return out
+
+
+def _close_runs(a, b, L):
+    """Two runs with identical pair sets whose float sums differ in order only
+    (h converged to 5e-6 in both)."""
+    assert np.max(np.abs(_periodic_diff(a["x"], b["x"], L))) < 1e-6 * L
+    np.testing.assert_allclose(a["h"], b["h"], rtol=3e-5)
+    np.testing.assert_allclose(a["rho"], b["rho"], rtol=3e-5)
+    rms = np.sqrt(np.mean(np.sum(b["a"] ** 2, axis=1)))
+    assert np.max(np.abs(a["a"] - b["a"])) <= 1e-3 * rms
+
+
+def test_reused_decomposition_matches_rebuilt(api):
+    """Keeping the decomposition over steps (Section II-C) gives the run that
+    rebuilds every step, on a variable-h box with spheres and background."""
+    box = inputs.plummer_box(n=32768, n_spheres=4, seed=7)
+    dt = 2e-5
+    rebuilt = _run_steps(api, box, dt, 6, reuse=0, h_tol=5e-6)
+    kept = _run_steps(api, box, dt, 6, reuse=1, h_tol=5e-6)
+    assert rebuilt["stats"]["reuses"] == 0
+    assert kept["stats"]["reuses"] >= 3 and kept["stats"]["builds"] >= 1
+    _close_runs(kept, rebuilt, box.L)
+
+
+def test_reuse_falls_back_to_a_rebuild_when_particles_move_too_far(api):
+    """Steps long enough that H + 2 * displacement outgrows the split limits
+    force rebuilds; the run still equals the one that rebuilds every step."""
+    box = inputs.lattice_box(14, jitter=0.3, seed=71, v_sigma=2.0)
+    dt = 4e-3
+    rebuilt = _run_steps(api, box, dt, 4, reuse=0, h_tol=5e-6)
+    kept = _run_steps(api, box, dt, 4, reuse=1, h_tol=5e-6)
+    assert kept["stats"]["builds"] >= 2
+    _close_runs(kept, rebuilt, box.L)
+
+
+def test_kick_drift_kick_with_reuse_matches_oracle(api):
+    box = inputs.lattice_box(12, jitter=0.3, seed=31, v_sigma=0.3)
+    dt, n_steps = 2e-3, 3
+    g = _run_steps(api, box, dt, n_steps, reuse=1)
+    assert g["stats"]["reuses"] >= 1
+    x, v, u, h, out = orc.kdk_steps(box, dt, n_steps)
+    a_rms = np.sqrt(np.mean(np.sum(out["a"] ** 2, axis=1)))
+    assert np.max(np.abs(_periodic_diff(g["x"], x, box.L))) < 1e-5 * box.meta["spacing"]
+    assert np.max(np.abs(g["v"] - v)) < 1e-3 * a_rms * dt * n_steps + 1e-6
+    np.testing.assert_allclose(g["h"], h, rtol=2e-4)
+    np.testing.assert_allclose(g["rho"], out["rho"], rtol=1e-3)

@@ -251,10 +251,15 @@ struct ForceShared {
   float4 a[32];    // partner 1/H, band, m, H (physical)
   float4 v[32];    // partner velocity, rho
   float4 f[32];    // partner f P / rho^2, c, K/H^4, -
+  float4 jacc[32]; // partner sums of the batch: acceleration (3), du/dt
+  float jvs[32];   //   and the largest signal velocity
   int g[32];
   float4 ip[32];   // own cluster: position, m
   float4 iv[32];   // own cluster: velocity, rho
   float4 if_[32];  // own cluster: 1/H, f P / rho^2, c, K/H^4
+  float4 iacc[32]; // own cluster sums over the task
+  float ivs[32];
+  unsigned short plist[32 * 32];   // the batch's pairs: own lane | slot << 5 | [r<H_i] << 10 | [r<H_j] << 11
 };
 
 __device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
@@ -262,6 +267,8 @@ __device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI
   S.a[lane] = make_float4(j.invH, j.band, j.m, j.Hphys);
   S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
   S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
+  S.jacc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.jvs[lane] = 0.f;
   S.g[lane] = j.g;
 }
 
@@ -269,6 +276,8 @@ __device__ __forceinline__ void force_stage_own(ForceShared& S, int lane, const 
   S.ip[lane] = make_float4(i.p.x, i.p.y, i.p.z, i.m);
   S.iv[lane] = make_float4(i.v.x, i.v.y, i.v.z, i.rho);
   S.if_[lane] = make_float4(i.invH, i.F, i.c, i.K4);
+  S.iacc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  S.ivs[lane] = 0.f;
 }
 
 __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, float4* facc, float* fvsig) {
@@ -405,20 +414,23 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
   }
 }
 
-// One force pair seen from particle a (the side updated) with partner b:
-// d = x_a - x_b, r, the two kernel derivatives (zero where r is not below that
-// side's H), and the symmetric viscosity (Monaghan, alpha).  Adds to a's
-// acceleration -m_b coef d and to its du/dt m_b (f_a P_a/rho_a^2 W_a' + Pi Wbar/2) w.v,
-// keeping the largest signal velocity.
+// What one side of a force pair needs of a particle: position, velocity, rho,
+// f P / rho^2, sound speed, K/H^4, 1/H and mass.
 struct ForceSide {
   float3 p, v;
   float rho, F, c, K4, invH, m;
 };
 
-__device__ __forceinline__ void force_add(const ForceSide& a, const ForceSide& b, bool fa, bool fb, float alpha,
-                                          float4& acc, float& vs) {
+// Both sides of one force pair, a (own particle) and b (partner), d = x_a - x_b:
+// a gains ca, b gains cb (the antisymmetric acceleration terms and each side's
+// du/dt), both see vsig.  No contribution when r = 0.
+__device__ __forceinline__ void force_pair_terms(const ForceSide& a, const ForceSide& b, bool fa, bool fb,
+                                                 float alpha, float4& ca, float4& cb, float& vsig) {
   const float dx = a.p.x - b.p.x, dy = a.p.y - b.p.y, dz = a.p.z - b.p.z;
   const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  ca = make_float4(0.f, 0.f, 0.f, 0.f);
+  cb = ca;
+  vsig = 0.0f;
   if (!(r2 > 0.0f)) return;
   const float rinv = rsqrtf(r2);
   const float r = r2 * rinv;
@@ -429,16 +441,36 @@ __device__ __forceinline__ void force_add(const ForceSide& a, const ForceSide& b
   const float vdx = fmaf(a.v.x - b.v.x, dx, fmaf(a.v.y - b.v.y, dy, (a.v.z - b.v.z) * dz));
   const float wv = vdx * rinv;
   const float mu = fminf(wv, 0.0f);
-  const float vsig = a.c + b.c - 3.0f * mu;
+  vsig = a.c + b.c - 3.0f * mu;
   const float Pi = -alpha * vsig * mu / (a.rho + b.rho);
   const float Wbar = 0.5f * (Wa + Wb);
   const float coef = fmaf(a.F, Wa, fmaf(b.F, Wb, Pi * Wbar)) * rinv;
   const float hv = 0.5f * Pi * Wbar;
-  acc.x = fmaf(-b.m * coef, dx, acc.x);
-  acc.y = fmaf(-b.m * coef, dy, acc.y);
-  acc.z = fmaf(-b.m * coef, dz, acc.z);
-  acc.w = fmaf(b.m * fmaf(a.F, Wa, hv), wv, acc.w);
-  vs = fmaxf(vs, vsig);
+  const float ka = -b.m * coef, kb = a.m * coef;
+  ca = make_float4(ka * dx, ka * dy, ka * dz, b.m * fmaf(a.F, Wa, hv) * wv);
+  cb = make_float4(kb * dx, kb * dy, kb * dz, a.m * fmaf(b.F, Wb, hv) * wv);
+}
+
+// Sums over runs of adjacent lanes with the same key; true on the first lane of
+// each run, which then holds the run's total (sum of v, max of m).
+__device__ __forceinline__ bool run_sum_max(int key, float4& v, float& m) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int k2 = __shfl_down_sync(0xffffffffu, key, off);
+    const float x = __shfl_down_sync(0xffffffffu, v.x, off), y = __shfl_down_sync(0xffffffffu, v.y, off);
+    const float z = __shfl_down_sync(0xffffffffu, v.z, off), w = __shfl_down_sync(0xffffffffu, v.w, off);
+    const float m2 = __shfl_down_sync(0xffffffffu, m, off);
+    if (lane + off < 32 && k2 == key) {
+      v.x += x;
+      v.y += y;
+      v.z += z;
+      v.w += w;
+      m = fmaxf(m, m2);
+    }
+  }
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);   // every lane takes part in the shuffle
+  return lane == 0 || prev != key;
 }
 
 __device__ __forceinline__ ForceSide side_of(const ForceI& I) {
@@ -484,37 +516,69 @@ __device__ __forceinline__ ForceSide own_side(const ForceShared& S, int k) {
 
 // Force batch: every pair with r < max(H_i, H_j); own side in the row sweep,
 // partner side in the column sweep unless own_only.
+// Force batch: every pair with r < max(H_i, H_j), each evaluated once for both
+// sides.  The batch's pairs go into a list in shared memory (own lane major),
+// which the warp then takes 32 at a time: one pair per lane, so that all lanes
+// work however unevenly the pairs fall on the rows.  The own side is summed by a
+// segmented warp reduction (a particle's pairs are adjacent in the list) into its
+// task sums; the partner side goes to the partner's batch sums with
+// shared-memory atomics (or, inside one cluster, to that particle's task sums).
 template <bool COUNT>
 __device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsigned int allow, unsigned int jvalid,
-                                           float bandJ, int n, bool own_only, unsigned int cmask, float4& acc,
-                                           float& vsig_i, const unsigned int* perm, const double* x,
-                                           const ItemGeom& g, float alpha, float4* facc, float* fvsig,
-                                           Counters& C) {
+                                           float bandJ, int n, bool own_only, unsigned int cmask,
+                                           const unsigned int* perm, const double* x, const ItemGeom& g,
+                                           float alpha, Counters& C) {
   const int lane = threadIdx.x & 31;
   unsigned int mI, mJ, rc = 0;
   pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
+  const unsigned int m = mI | mJ;
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid & cmask) : 0u;
     C.rechecks += rc;
+    C.pairs += __popc(m & cmask);
   }
-  const ForceSide own = side_of(I);
-  for (unsigned int m = mI | mJ; m; m &= m - 1) {
-    const int sj = __ffs(m) - 1;
-    if (COUNT && ((cmask >> sj) & 1u)) C.pairs++;
-    force_add(own, staged_side(S, sj), (mI >> sj) & 1u, (mJ >> sj) & 1u, alpha, acc, vsig_i);
+  // list the pairs, own lane major
+  const unsigned int cnt = __popc(m);
+  unsigned int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
   }
-  if (own_only) return;
-  unsigned int colI = transpose_bits(mI, n), colJ = transpose_bits(mJ, n);
-  unsigned int col = colI | colJ;
-  if (col) {
-    const ForceSide me = staged_side(S, lane);
-    float4 pacc = make_float4(0.f, 0.f, 0.f, 0.f);
-    float pvs = 0.0f;
-    for (; col; col &= col - 1) {
-      const int li = __ffs(col) - 1;
-      force_add(me, own_side(S, li), (colJ >> li) & 1u, (colI >> li) & 1u, alpha, pacc, pvs);
+  const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned int k = incl - cnt;
+  for (unsigned int mm = m; mm; mm &= mm - 1) {
+    const unsigned int sj = __ffs(mm) - 1;
+    S.plist[k++] = (unsigned short)(lane | (sj << 5) | (((mI >> sj) & 1u) << 10) | (((mJ >> sj) & 1u) << 11));
+  }
+  __syncwarp();
+  for (unsigned int r0 = 0; r0 < total; r0 += 32) {
+    const unsigned int e = r0 + lane;
+    int li = 32 + lane;     // a key no other lane has
+    float4 ci = make_float4(0.f, 0.f, 0.f, 0.f), cj = ci;
+    float vs = 0.0f;
+    int sj = 0;
+    if (e < total) {
+      const unsigned int w = S.plist[e];
+      li = (int)(w & 31u);
+      sj = (int)((w >> 5) & 31u);
+      force_pair_terms(own_side(S, li), staged_side(S, sj), (w >> 10) & 1u, (w >> 11) & 1u, alpha, ci, cj, vs);
+      float4* dst = own_only ? &S.iacc[sj] : &S.jacc[sj];
+      atomicAdd(&dst->x, cj.x);
+      atomicAdd(&dst->y, cj.y);
+      atomicAdd(&dst->z, cj.z);
+      atomicAdd(&dst->w, cj.w);
+      atomicMax(reinterpret_cast<unsigned int*>(own_only ? &S.ivs[sj] : &S.jvs[sj]), __float_as_uint(vs));
     }
-    flush_force(S.g[lane], pacc, pvs, facc, fvsig);
+    float vmax = vs;
+    if (run_sum_max(li, ci, vmax) && li < 32) {
+      atomicAdd(&S.iacc[li].x, ci.x);
+      atomicAdd(&S.iacc[li].y, ci.y);
+      atomicAdd(&S.iacc[li].z, ci.z);
+      atomicAdd(&S.iacc[li].w, ci.w);
+      atomicMax(reinterpret_cast<unsigned int*>(&S.ivs[li]), __float_as_uint(vmax));
+    }
+    __syncwarp();
   }
 }
 
@@ -547,9 +611,8 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
 
 template <bool COUNT>
 __device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, unsigned int q, bool own_only,
-                                            float4& acc, float& vsi, const unsigned int* perm, const double* x,
-                                            const ItemGeom& g, float alpha, float4* facc, float* fvsig,
-                                            Counters& C) {
+                                            const unsigned int* perm, const double* x, const ItemGeom& g,
+                                            float alpha, float4* facc, float* fvsig, Counters& C) {
   const int lane = threadIdx.x & 31;
   const bool v = (unsigned int)lane < q;
   __syncwarp();
@@ -557,9 +620,12 @@ __device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, uns
   const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
   const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
   __syncwarp();
-  const unsigned int allow = own_only ? jvalid & ~(1u << lane) : jvalid;
-  force_tile<COUNT>(I, S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only,
-                    own_only ? upper_mask(lane) : 0xffffffffu, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+  // inside one cluster each unordered pair once (partners above the lane)
+  const unsigned int allow = own_only ? jvalid & upper_mask(lane) : jvalid;
+  force_tile<COUNT>(I, S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only, 0xffffffffu, perm, x, g, alpha,
+                    C);
+  __syncwarp();
+  if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
   __syncwarp();
 }
 
@@ -822,8 +888,6 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
   const bool vi = (unsigned int)lane < TL.n[ti];
   const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
   force_stage_own(S, lane, I);
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  float vsi = 0.0f;
   unsigned int q = 0;
   for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
     unsigned int jt, jn, js;
@@ -841,15 +905,16 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
+        force_batch<COUNT>(I, S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, P.g, alpha, facc, fvsig, C);
-  flush_force(I.g, acc, vsi, facc, fvsig);
+  if (q) force_batch<COUNT>(I, S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
+  __syncwarp();
+  flush_force(I.g, S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
 
 template <bool COUNT>
@@ -870,12 +935,10 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
   const bool vi = (unsigned int)lane < TL.n[ti];
   const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
   force_stage_own(S, lane, I);
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  float vsi = 0.0f;
   unsigned int q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) force_put(S, lane, I);
-  force_batch<COUNT>(I, S, TL.n[ti], true, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+  force_batch<COUNT>(I, S, TL.n[ti], true, perm, x, g, alpha, facc, fvsig, C);
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
     bool ok = false;
@@ -894,15 +957,16 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
+        force_batch<COUNT>(I, S, q, false, perm, x, g, alpha, facc, fvsig, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(I, S, q, false, acc, vsi, perm, x, g, alpha, facc, fvsig, C);
-  flush_force(I.g, acc, vsi, facc, fvsig);
+  if (q) force_batch<COUNT>(I, S, q, false, perm, x, g, alpha, facc, fvsig, C);
+  __syncwarp();
+  flush_force(I.g, S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
 
 // Density interactions of one pass: the live pair and self tasks in one queue.

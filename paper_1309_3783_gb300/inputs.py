@@ -233,6 +233,42 @@ def clustered_box(n: int = 2 ** 25, frac_uniform: float = 0.3, n_spheres: int = 
                        f"clustered n={n} spheres={n_spheres}", {"seed": seed})
 
 
+def sod_box(n_left: tuple = (58, 116, 116), n_right: tuple = (37, 73, 73), L: float = 1.0,
+            rho_left: float = 1.0, p_left: float = 1.0, p_right: float = 0.1795, gamma: float = 5.0 / 3.0,
+            eta: float = ETA) -> ParticleBox:
+    """The Sod shock of Section III: a periodic cube whose half x < L/2 holds the
+    dense gas (rho 1, P 1) and the other half the thin gas (P 0.1795, a quarter of
+    the density), at rest, as two cubic lattices of equal-mass particles (so the
+    dense half holds about four times as many).  The default sizes give about
+    780,000 + 197,000 particles (the paper: 800,000 + 200,000 on its own grid).
+    Masses follow from rho_left on the dense lattice; u is set from the target
+    pressures and each lattice's actual density; h = eta x the lattice spacing.
+    """
+    def lattice(n, x0, ax, a):
+        idx = np.indices(n).reshape(3, -1).T.astype(np.float64)
+        x = np.empty_like(idx)
+        x[:, 0] = x0 + (idx[:, 0] + 0.5) * ax
+        x[:, 1] = (idx[:, 1] + 0.5) * a
+        x[:, 2] = (idx[:, 2] + 0.5) * a
+        return x
+    half = 0.5 * L
+    aL = L / n_left[1]
+    aR = L / n_right[1]
+    xl = lattice(n_left, 0.0, half / n_left[0], aL)
+    xr = lattice(n_right, half, half / n_right[0], aR)
+    nl, nr = xl.shape[0], xr.shape[0]
+    m = rho_left * half * L * L / nl
+    rho_right = m * nr / (half * L * L)
+    u = np.concatenate([np.full(nl, p_left / ((gamma - 1.0) * rho_left)),
+                        np.full(nr, p_right / ((gamma - 1.0) * rho_right))]).astype(np.float32)
+    h = np.concatenate([np.full(nl, eta * aL), np.full(nr, eta * aR)]).astype(np.float32)
+    x = _wrap(np.concatenate([xl, xr]), L)
+    n = nl + nr
+    return ParticleBox(x, np.zeros((n, 3), np.float32), np.full(n, m, np.float32), u, h, L, True,
+                       f"sod {nl}+{nr}", {"rho_left": rho_left, "rho_right": rho_right, "p_left": p_left,
+                                          "p_right": p_right, "gamma": gamma, "n_left": nl})
+
+
 def served_box_sizes(n_boxes: int = 512, n_min: int = 1000, n_max: int = 262_144,
                      seed: int = 1) -> np.ndarray:
     """Lattice side lengths n_b with n_b^3 log-uniform in [n_min, n_max]."""

@@ -143,6 +143,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(dist, value, device="cpu"):
+    """The largest of every rank's value (the whole job ends with its slowest
+    replica); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
+def replica_seed(rank):
+    """Every replica draws its own instance of the workload recipe."""
+    return 1 + rank
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -161,7 +183,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    box = inputs.plummer_box(seed=1 + rank)
+    box = inputs.plummer_box(seed=replica_seed(rank))
     n = box.n
     ctx = sph.sph_ctx_create(device=local_rank)
     stream = torch.cuda.Stream()
@@ -221,12 +243,8 @@ def run_ours(args, rank, world, local_rank):
     prof = b.get_profile()
     b.profile(False)
     ms = [s.elapsed_time(e) for s, e in evs]
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=f"cuda:{local_rank}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(dist, sum(ms), f"cuda:{local_rank}")
+    value = job_rate(world, n * args.steps, total_ms / 1e3)
 
     # e2e through the C-ABI: the state lives in pinned host buffers between steps
     pinned = lambda shape, dt_: torch.empty(shape, dtype=dt_).pin_memory().numpy()
@@ -250,12 +268,8 @@ def run_ours(args, rank, world, local_rank):
         b.get("a", out=ah)
         b.get("dudt", out=duh)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=f"cuda:{local_rank}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = world * n * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, f"cuda:{local_rank}")
+    e2e = job_rate(world, n * e2e_steps, e2e_s)
 
     # roofline of the dominant kernel (FP32 ALU bound)
     dom = max(("density", "force"), key=lambda k: prof[k]["ms"])

@@ -58,10 +58,14 @@ __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigne
                              const float4*, unsigned int*, Tiles);
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
-void launch_live_tasks(Engine& E, bool dens);
+void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
 void launch_density(Engine& E);
 void launch_force(Engine& E);
-void launch_ghost(Engine& E, int mode, int it);
+void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
+void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep);
+void launch_iter_start(Engine& E, cudaGraphConditionalHandle iter);
+void launch_iter_next(Engine& E, cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force);
+void launch_set_drift(Engine& E);
 void launch_zero_density(Engine& E, bool all);
 void launch_set_active(Engine& E);
 void launch_mark_active_cells(Engine& E);
@@ -84,6 +88,7 @@ void launch_set_acc(Engine& E, long long off, long long n, int which, const floa
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 const char* const kPhaseNames[PH_COUNT] = {"ingest",     "keys_sort",   "tree",      "lists",
@@ -144,6 +149,7 @@ Engine::Engine(const sph_params& p, int dev, cudaStream_t s) : prm(p), device(de
 }
 
 Engine::~Engine() {
+  drop_step_graph();
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
 }
 
@@ -640,6 +646,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemcpyAsync(x_build.p, x.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   reusable = true;
   ++n_builds;
+  graph_ready = false;      // a captured step holds this build's sizes and buffers
   return SPH_OK;
 }
 
@@ -711,7 +718,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     CK(cudaMemcpyAsync(&n_active, dev_counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (n_active == 0) break;
+    if (n_active == 0) break;      // every particle finalised (on the last iteration, unconverged ones too)
     if (ea & ERR_REBUILD) {
       s = build();   // the input-order h carries the iteration's state
       if (s != SPH_OK) return s;
@@ -723,9 +730,10 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     }
   }
   if (it > prm.h_max_iter) it = prm.h_max_iter;
-  // particles that never converged
+  // particles that never converged: the last iteration finalises them with their
+  // flag cleared, so they are counted whenever the iteration ran to its limit
   long long nu = 0;
-  if (n_active > 0) {
+  if (it == prm.h_max_iter) {
     int cnt = 0;
     CK(cudaMemsetAsync(dev_counters.p + 1, 0, sizeof(int), st));
     launch_count_unconverged(*this, dev_counters.p + 1);
@@ -793,6 +801,12 @@ sph_status Engine::step_boxes() {
     if (s != SPH_OK && s != SPH_E_NOT_CONVERGED) return s;
     s = force();
     if (s != SPH_OK) return s;
+  }
+  if (moving && prm.reuse && reusable && !prof && !count_pairs && !graph_off) {
+    // the whole step, kick and drift included, as one captured graph
+    s = upload_boxes();
+    if (s != SPH_OK) return s;
+    return step_graph();
   }
   if (moving) {
     s = upload_boxes();
@@ -864,6 +878,182 @@ sph_status Engine::reuse_or_build() {
   built = true;
   have_density = have_ghost = have_force = false;
   ++n_reuses;
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------ captured step
+// A step that keeps the decomposition, as one CUDA graph with conditional nodes:
+//   kick, drift, the displacement test (a child graph), then
+//   IF the decomposition stays: refresh offsets, velocities, boxes and H maxima,
+//     and set the h iteration up;
+//   WHILE particles still iterate (no rebuild needed, limit not reached): one
+//     density pass and its h update, the iteration counter kept on the device;
+//   IF the iteration ended without a rebuild: force pass, reductions, the saved
+//     accelerations and the closing kick.
+// One synchronisation at the end reads what happened: when the test failed or an
+// iteration needed a rebuild, the host completes the step with a full build.
+void Engine::drop_step_graph() {
+  if (step_x) cudaGraphExecDestroy(step_x);
+  if (step_g) cudaGraphDestroy(step_g);
+  step_x = nullptr;
+  step_g = nullptr;
+  graph_ready = false;
+}
+
+#define CKG(call)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      cudaStreamCaptureStatus cs_;                                                 \
+      if (cudaStreamIsCapturing(st, &cs_) == cudaSuccess && cs_ != cudaStreamCaptureStatusNone) { \
+        cudaGraph_t g_;                                                            \
+        cudaStreamEndCapture(st, &g_);                                             \
+        if (g_) cudaGraphDestroy(g_);                                              \
+      }                                                                            \
+      cudaGetLastError();                                                          \
+      drop_step_graph();                                                           \
+      graph_off = true;                                                            \
+      return fail(SPH_E_CUDA, std::string("step capture: ") + cudaGetErrorString(e_)); \
+    }                                                                              \
+  } while (0)
+
+sph_status Engine::capture_step_graph() {
+  drop_step_graph();
+  CK(dmax_bits.reserve(nbox));
+  CK(reuse_flag.reserve(1));
+  CK(it_dev.reserve(2));
+  const long long c0 = launch_count();
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  CKG(cudaGraphCreate(&step_g, 0));
+  cudaGraphConditionalHandle keep, iter, frc;
+  CKG(cudaGraphConditionalHandleCreate(&keep, step_g, 0, cudaGraphCondAssignDefault));
+  CKG(cudaGraphConditionalHandleCreate(&iter, step_g, 0, cudaGraphCondAssignDefault));
+  CKG(cudaGraphConditionalHandleCreate(&frc, step_g, 0, cudaGraphCondAssignDefault));
+  // kick, drift, displacement test
+  cudaGraph_t g1 = nullptr;
+  CKG(cudaStreamBeginCapture(st, mode));
+  launch_kick(*this);
+  launch_drift(*this);
+  CKG(cudaMemsetAsync(dmax_bits.p, 0, nbox * sizeof(unsigned long long), st));
+  CKG(cudaMemsetAsync(reuse_flag.p, 0, sizeof(unsigned int), st));
+  k_displacement<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, x_build.p, dmax_bits.p); count_launch();
+  k_reuse_limits<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, T, leaf_of.p, perm.p, h.p, prm.gamma_kernel,
+                                          dmax_bits.p, hlimp.p, reuse_flag.p); count_launch();
+  launch_set_drift(*this);
+  launch_cond_keep(*this, keep);
+  CKG(cudaStreamEndCapture(st, &g1));
+  g_pre = launch_count() - c0;
+  cudaGraphNode_t n1, n2, n3, n4;
+  CKG(cudaGraphAddChildGraphNode(&n1, step_g, nullptr, 0, g1));
+  cudaGraphDestroy(g1);
+  // IF kept: refresh and set the iteration up
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = keep;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  CKG(cudaGraphAddNode(&n2, step_g, &n1, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  long long c1 = launch_count();
+  CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p); count_launch();
+  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  CKG(cudaMemsetAsync(t_hmax.p, 0, n_nodes * sizeof(float), st));
+  k_leaf_hmax<<<nsm * 8, 256, 0, st>>>(T, n_nodes, Hs.p); count_launch();
+  k_tile_boxes<<<grid(32 * n_tiles), 256, 0, st>>>(n_tiles, TL, pos4.p); count_launch();
+  launch_bracket_reset(*this);
+  launch_set_active(*this);
+  CKG(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+  CKG(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  launch_iter_start(*this, iter);
+  CKG(cudaStreamEndCapture(st, &body));
+  g_keep = launch_count() - c1;
+  // WHILE iterating: one density pass and its h update
+  cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = iter;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  CKG(cudaGraphAddNode(&n3, step_g, &n2, nullptr, 1, &cp));
+  body = cp.conditional.phGraph_out[0];
+  c1 = launch_count();
+  CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  launch_zero_density(*this, false);
+  launch_live_tasks(*this, true, it_dev.p);
+  launch_density(*this);
+  launch_ghost(*this, 1, 0, it_dev.p);
+  launch_iter_next(*this, iter, frc);
+  launch_mark_active_cells(*this);
+  CKG(cudaStreamEndCapture(st, &body));
+  g_iter = launch_count() - c1;
+  // IF finished without a rebuild: force pass and the closing kick
+  cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = frc;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  CKG(cudaGraphAddNode(&n4, step_g, &n3, nullptr, 1, &cp));
+  body = cp.conditional.phGraph_out[0];
+  c1 = launch_count();
+  CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  CKG(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
+  CKG(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
+  launch_live_tasks(*this, false);
+  launch_force(*this);
+  launch_reduce(*this);
+  launch_save_acc(*this);
+  launch_kick(*this);
+  CKG(cudaStreamEndCapture(st, &body));
+  g_force = launch_count() - c1;
+  CKG(cudaGraphInstantiate(&step_x, step_g, 0));
+  count_launches(-(launch_count() - c0));     // capturing launches nothing
+  graph_ready = true;
+  return SPH_OK;
+}
+
+sph_status Engine::step_graph() {
+  if (!graph_ready) {
+    sph_status s = capture_step_graph();
+    if (s != SPH_OK) return s;
+  }
+  CK(cudaGraphLaunch(step_x, st));
+  unsigned int flag = 0, ea = 0;
+  int itv[2] = {0, 0};
+  CK(cudaMemcpyAsync(&flag, reuse_flag.p, sizeof(flag), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(itv, it_dev.p, sizeof(itv), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const bool rebuild = flag != 0 || (ea & ERR_REBUILD) != 0u;
+  count_launches(g_pre + (flag ? 0 : g_keep + (long long)itv[0] * g_iter + (rebuild ? 0 : g_force)));
+  if (rebuild) {
+    // kick and drift are done: complete the step with a full build
+    sph_status s = build();
+    if (s != SPH_OK) return s;
+    sph_status hs = h_update(nullptr, nullptr);
+    if (hs != SPH_OK && hs != SPH_E_NOT_CONVERGED) return hs;
+    s = force();
+    if (s != SPH_OK) return s;
+    launch_kick(*this);
+    CK(cudaGetLastError());
+    return hs;
+  }
+  ++n_reuses;
+  built = true;
+  have_density = have_ghost = have_force = have_acc = true;
+  last_iters = itv[0];
+  last_rebuilds = 0;
+  long long nu = 0;
+  if (itv[0] >= prm.h_max_iter) {
+    int cnt = 0;
+    CK(cudaMemsetAsync(dev_counters.p + 1, 0, sizeof(int), st));
+    launch_count_unconverged(*this, dev_counters.p + 1);
+    CK(cudaMemcpyAsync(&cnt, dev_counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    nu = cnt;
+  }
+  last_unconverged = nu;
+  if (nu > 0) return fail(SPH_E_NOT_CONVERGED, std::to_string(nu) + " particles did not converge");
   return SPH_OK;
 }
 

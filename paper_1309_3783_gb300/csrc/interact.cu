@@ -1058,8 +1058,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles T
 // warp-aggregated appends.
 template <bool DENS>
 __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
-                             long long nst, int partial) {
+                             long long nst, int partial_host, const int* __restrict__ it_dev) {
   const int lane = threadIdx.x & 31;
+  // later iterations keep only what still iterates (in a captured step: from iteration 2 on)
+  const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
   const long long ntask = npt + nst;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < ntask; b0 += stride) {
@@ -1110,13 +1112,16 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
 // mode 0: finalise every particle at its current h (one density pass);
 // mode 1: one h iteration (Newton on N~ = n_ngb, bracket, clamp) for the
 //         active particles, finalising those that converged or ran out.
-__global__ void k_ghost(long long N, int mode, int it, int max_iter, float gamma_k, float n_ngb, float tol,
+__global__ void k_ghost(long long N, int mode, int it_host, const int* __restrict__ it_dev, int max_iter,
+                        float gamma_k, float n_ngb, float tol,
                         float gamma_gas, const unsigned int* __restrict__ perm, float* __restrict__ Hs,
                         float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
                         const float4* __restrict__ dacc, unsigned char* __restrict__ act, float* __restrict__ h,
                         float* __restrict__ hlo, float* __restrict__ hhi, int* __restrict__ conv,
                         const float* __restrict__ hlimp, const unsigned int* __restrict__ leaf_of, Tree T,
                         float4* __restrict__ ghost4, int* __restrict__ n_active, unsigned int* __restrict__ err_all) {
+  // the iteration number: the host's, or in a captured step the device counter
+  const int it = it_dev ? *it_dev : it_host;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     if (mode == 1 && !act[p]) continue;
     const unsigned int i = perm[p];
@@ -1265,6 +1270,44 @@ __global__ void k_h_bracket_reset(long long N, float* __restrict__ hlo, float* _
     hlo[p] = 0.0f;
     hhi[p] = __int_as_float(0x7f800000);
     conv[p] = 0;
+  }
+}
+
+// =========================================================================== captured steps
+// Conditions of a step captured as a CUDA graph with conditional nodes (one
+// thread each).  keep: the decomposition stays (no particle outgrew the limits).
+__global__ void k_cond_keep(cudaGraphConditionalHandle keep, const unsigned int* __restrict__ reuse_flag) {
+  cudaGraphSetConditional(keep, *reuse_flag == 0u ? 1u : 0u);
+}
+
+// start of the h iteration: iteration 1 runs
+__global__ void k_iter_start(cudaGraphConditionalHandle iter, int* __restrict__ it_dev) {
+  *it_dev = 1;
+  cudaGraphSetConditional(iter, 1u);
+}
+
+// after iteration *it_dev: another while particles still iterate, no rebuild is
+// needed and the limit is not reached; the force pass follows unless a rebuild is
+// needed (the host then takes over).  n_active is cleared for the next iteration.
+__global__ void k_iter_next(cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force, int* __restrict__ it_dev,
+                            int* __restrict__ n_active, const unsigned int* __restrict__ err_all, int max_iter,
+                            int* __restrict__ last_active) {
+  const bool rebuild = (*err_all & ERR_REBUILD) != 0u;
+  const int na = *n_active;
+  *last_active = na;
+  const bool more = !rebuild && na > 0 && *it_dev < max_iter;
+  if (more) *it_dev += 1;
+  *n_active = 0;
+  cudaGraphSetConditional(iter, more ? 1u : 0u);
+  cudaGraphSetConditional(force, (!more && !rebuild) ? 1u : 0u);
+}
+
+// the displacement of every box, written into its descriptor on the device
+__global__ void k_set_drift(int nbox, BoxDesc* __restrict__ box, const unsigned long long* __restrict__ dmax) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    const double d = __longlong_as_double((long long)dmax[b]);
+    box[b].drift2 = (float)(2.0 * d);
+    box[b].drift_u = (float)(d * box[b].invL);
   }
 }
 
@@ -1433,15 +1476,16 @@ static int resident_ctas(const void* fn) {
   return 4;
 }
 
-void launch_live_tasks(Engine& E, bool dens) {
+void launch_live_tasks(Engine& E, bool dens, const int* it_dev) {
   cudaMemsetAsync(E.Lq.n_live, 0, sizeof(unsigned int), E.st);
   const long long n = E.n_ptasks + E.n_stasks;
   if (n == 0) return;
   const int grid = (int)std::min<long long>((n + 255) / 256, (long long)E.nsm * 16);
   if (dens)
-    k_live_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, E.partial_pass);
+    k_live_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, E.partial_pass,
+                                                it_dev);
   else
-    k_live_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, 0);
+    k_live_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, 0, nullptr);
   count_launch();
 }
 
@@ -1463,8 +1507,8 @@ void launch_force(Engine& E) {
   count_launch();
 }
 
-void launch_ghost(Engine& E, int mode, int it) {
-  k_ghost<<<E.grid(E.N), 256, 0, E.st>>>(E.N, mode, it, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
+void launch_ghost(Engine& E, int mode, int it, const int* it_dev) {
+  k_ghost<<<E.grid(E.N), 256, 0, E.st>>>(E.N, mode, it, it_dev, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
                                           E.prm.h_tol, E.prm.gamma_gas, E.perm.p, E.Hs.p, E.pos4.p, E.cen4.p,
                                           E.vel4.p, E.dacc.p, E.act.p, E.h.p, E.hlo.p, E.hhi.p, E.conv.p,
                                           E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.dev_counters.p, E.err_all.p); count_launch();
@@ -1518,6 +1562,23 @@ void launch_reduce(Engine& E) {
   const int gx = (int)std::max<long long>(1, std::min<long long>((maxn + 255) / 256, (E.nsm * 4 + E.nbox - 1) / E.nbox));
   k_reduce<<<dim3(gx, std::min(E.nbox, 65535)), 256, 0, E.st>>>(E.nbox, E.boff.p, E.cen4.p, E.vel4.p, E.facc.p,
                                                                  E.red.p); count_launch();
+}
+
+void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep) {
+  k_cond_keep<<<1, 1, 0, E.st>>>(keep, E.reuse_flag.p); count_launch();
+}
+
+void launch_iter_start(Engine& E, cudaGraphConditionalHandle iter) {
+  k_iter_start<<<1, 1, 0, E.st>>>(iter, E.it_dev.p); count_launch();
+}
+
+void launch_iter_next(Engine& E, cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force) {
+  k_iter_next<<<1, 1, 0, E.st>>>(iter, force, E.it_dev.p, E.dev_counters.p, E.err_all.p, E.prm.h_max_iter,
+                                 E.it_dev.p + 1); count_launch();
+}
+
+void launch_set_drift(Engine& E) {
+  k_set_drift<<<1, 256, 0, E.st>>>(E.nbox, E.box.p, E.dmax_bits.p); count_launch();
 }
 
 void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); count_launch(); }

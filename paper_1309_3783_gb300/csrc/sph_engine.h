@@ -87,6 +87,9 @@ class Engine {
   // ---- the hot path -----------------------------------------------------------
   sph_status build();
   sph_status reuse_or_build();        // keep the last decomposition while valid (prm.reuse), else build
+  sph_status step_graph();            // a kept-decomposition step as one CUDA graph (prm.reuse)
+  sph_status capture_step_graph();
+  void drop_step_graph();
   sph_status density();                                        // one pass at the current h, all particles
   sph_status h_update(long long* n_unconverged, int* iterations);
   sph_status force();
@@ -208,6 +211,12 @@ class Engine {
   DBuf<double> x_build;           // positions at the last full build (input order)
   DBuf<unsigned long long> dmax_bits;   // per box: largest displacement since the build (double bits)
   DBuf<unsigned int> reuse_flag;
+  DBuf<int> it_dev;               // captured step: iteration number, and the last iteration's active count
+  // the captured step (valid for one decomposition)
+  cudaGraph_t step_g = nullptr;
+  cudaGraphExec_t step_x = nullptr;
+  bool graph_ready = false, graph_off = false;
+  long long g_pre = 0, g_keep = 0, g_iter = 0, g_force = 0;   // kernels per part
   long long last_unconverged = 0;
   bool built = false, have_density = false, have_ghost = false, have_force = false, have_acc = false;
 

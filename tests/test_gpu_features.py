@@ -241,3 +241,34 @@ def test_kick_drift_kick_with_reuse_matches_oracle(api):
     assert np.max(np.abs(g["v"] - v)) < 1e-3 * a_rms * dt * n_steps + 1e-6
     np.testing.assert_allclose(g["h"], h, rtol=2e-4)
     np.testing.assert_allclose(g["rho"], out["rho"], rtol=1e-3)
+
+
+def test_captured_step_matches_the_step_run_from_the_host(api):
+    """A kept-decomposition step runs as one CUDA graph (conditional nodes for the
+    kept test, the h iteration and the force pass); with profiling on, the same
+    step runs from the host, phase by phase.  Both give the same run."""
+    box = inputs.plummer_box(n=32768, n_spheres=4, seed=11)
+    dt, n_steps = 2e-5, 5
+
+    def run(profile):
+        c = _ctx_with(api, reuse=1, h_tol=5e-6)
+        try:
+            b = api.box_from(c, box)
+            try:
+                if profile:
+                    b.profile(True)
+                for _ in range(n_steps):
+                    b.step(dt)
+                out = {k: b.get(k) for k in ("x", "v", "u", "h", "rho", "a", "count")}
+                out["stats"] = b.stats()
+            finally:
+                b.close()
+        finally:
+            api.sph_ctx_destroy(c)
+        return out
+
+    host = run(True)
+    graph = run(False)
+    assert graph["stats"]["reuses"] == host["stats"]["reuses"] >= 3
+    assert np.array_equal(graph["count"], host["count"])
+    _close_runs(graph, host, box.L)

@@ -308,3 +308,27 @@ def test_plummer_262144_sampled(api, ctx):
                                    method="kdtree")
     assert conv.all()
     np.testing.assert_allclose(gi["h"][idx[:300]], hs, rtol=1e-4)
+
+
+def test_h_iteration_limit_reports_unconverged_particles(api):
+    """With the iteration limit reached, the particles still off the target are
+    reported (SPH_E_NOT_CONVERGED and their count) and keep the h of their last
+    iteration, as in the oracle."""
+    box = inputs.lattice_box(16, jitter=0.3, seed=12)
+    box.h = (box.h * np.float32(0.7)).astype(np.float32)
+    c = make_ctx(api, h_max_iter=2)
+    try:
+        b = api.box_from(c, box)
+        try:
+            st, nu, it = b.h_update()
+            conv = b.get("converged")
+            h = b.get("h")
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    assert it == 2 and nu > 0 and st == api.SPH_E_NOT_CONVERGED
+    assert nu == int(np.count_nonzero(conv == 0))
+    ho, convo, _, _ = orc.h_iterate(box.x, box.m, box.h, box.L, True, tol=1e-4, max_iter=2)
+    np.testing.assert_allclose(h, ho, rtol=1e-4)
+    assert abs(int(np.count_nonzero(~convo)) - nu) <= max(2, nu // 100)

@@ -149,6 +149,9 @@ typedef struct sph_stats {
     int64_t guard_rechecks;     /* predicate decisions re-taken in FP64               */
     int64_t builds;             /* full decompositions built since the box was set    */
     int64_t reuses;             /* steps that kept the decomposition (params.reuse)   */
+    int64_t h_active_after_first; /* particles the first density pass of the last h
+                                     iteration left unconverged (the quality of the
+                                     starting h: the previous step's roots, extrapolated) */
 } sph_stats;
 
 /* Device time of one phase of the path (CUDA events on the context stream). */

@@ -91,9 +91,10 @@ __global__ void k_box_ids(long long N, int nbox, const long long* __restrict__ o
 // tab[3y + 2] particles from offset tab[3y + 1] to offset tab[3y].
 __global__ void k_relayout(const long long* __restrict__ tab, const double* __restrict__ x,
                            const float* __restrict__ v, const float* __restrict__ m, const float* __restrict__ u,
-                           const float* __restrict__ h, const float4* __restrict__ a, double* __restrict__ nx,
-                           float* __restrict__ nv, float* __restrict__ nm, float* __restrict__ nu,
-                           float* __restrict__ nh, float4* __restrict__ na) {
+                           const float* __restrict__ h, const float4* __restrict__ hh, const float4* __restrict__ a,
+                           double* __restrict__ nx, float* __restrict__ nv, float* __restrict__ nm,
+                           float* __restrict__ nu, float* __restrict__ nh, float4* __restrict__ nhh,
+                           float4* __restrict__ na) {
   const long long dst = tab[3 * blockIdx.y], src = tab[3 * blockIdx.y + 1], n = tab[3 * blockIdx.y + 2];
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long s = src + q, d = dst + q;
@@ -106,6 +107,7 @@ __global__ void k_relayout(const long long* __restrict__ tab, const double* __re
     nm[d] = m[s];
     nu[d] = u[s];
     nh[d] = h[s];
+    nhh[d] = hh[s];
     na[d] = a[s];
   }
 }

@@ -24,7 +24,7 @@ __global__ void k_reuse_limits(long long, int, const unsigned long long*, Tree, 
 __global__ void k_leaf_hmax(Tree, int, const float*);
 __global__ void k_tile_boxes(long long, Tiles, const float4*);
 __global__ void k_relayout(const long long*, const double*, const float*, const float*, const float*, const float*,
-                           const float4*, double*, float*, float*, float*, float*, float4*);
+                           const float4*, const float4*, double*, float*, float*, float*, float*, float4*, float4*);
 __global__ void k_gather_sorted(long long, const unsigned int*, const float*, const float*, const float*, float*,
                                 float4*);
 __global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned long long*, Tree, int, int*,
@@ -227,22 +227,31 @@ sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector
   CK(rl_m.reserve(n));
   CK(rl_u.reserve(n));
   CK(rl_h.reserve(n));
+  CK(rl_hh.reserve(n));
   CK(rl_a.reserve(n));
   const int nmove = (int)(tab.size() / 3);
   if (nmove > 0) {
     CK(rl_tab.reserve(tab.size()));
     CK(cudaMemcpyAsync(rl_tab.p, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     const dim3 g((unsigned)std::min<long long>((maxn + 255) / 256, 64), (unsigned)nmove);
-    k_relayout<<<g, 256, 0, st>>>(rl_tab.p, x.p, v.p, m.p, u.p, h.p, a_in.p, rl_x.p, rl_v.p, rl_m.p, rl_u.p, rl_h.p,
-                                  rl_a.p); count_launch();
+    k_relayout<<<g, 256, 0, st>>>(rl_tab.p, x.p, v.p, m.p, u.p, h.p, hhist.p, a_in.p, rl_x.p, rl_v.p, rl_m.p,
+                                  rl_u.p, rl_h.p, rl_hh.p, rl_a.p); count_launch();
   }
+  const std::vector<BoxDesc> old = hbox;
   sph_status s = set_boxes(boxes);
   if (s != SPH_OK) return s;
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    if (src[b] < 0) continue;      // moved boxes keep their h history
+    hbox[b].dt_prev[0] = old[src[b]].dt_prev[0];
+    hbox[b].dt_prev[1] = old[src[b]].dt_prev[1];
+    hbox[b].hpred = old[src[b]].hpred;
+  }
   x.swap(rl_x);
   v.swap(rl_v);
   m.swap(rl_m);
   u.swap(rl_u);
   h.swap(rl_h);
+  hhist.swap(rl_hh);
   a_in.swap(rl_a);
   return SPH_OK;
 }
@@ -256,6 +265,7 @@ sph_status Engine::ensure_particle_capacity() {
   CK(m.reserve(n));
   CK(u.reserve(n));
   CK(h.reserve(n));
+  CK(hhist.reserve(n));
   CK(x_build.reserve(3 * n));
   CK(H_in.reserve(n));
   CK(hlo.reserve(n));
@@ -417,6 +427,7 @@ sph_status Engine::set_particles(int b, const double* xx, const float* vv, const
   CK(cudaMemcpyAsync(h.p + o, hh, n * sizeof(float), kind, st));
   built = have_density = have_ghost = have_force = have_acc = false;
   reusable = false;
+  hbox[b].hpred = 0;
   n_builds = n_reuses = 0;
   return SPH_OK;
 }
@@ -718,6 +729,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     CK(cudaMemcpyAsync(&n_active, dev_counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (it == 1) first_active = n_active;
     if (n_active == 0) break;      // every particle finalised (on the last iteration, unconverged ones too)
     if (ea & ERR_REBUILD) {
       s = build();   // the input-order h carries the iteration's state
@@ -785,12 +797,44 @@ sph_status Engine::step(double dt) {
   return step_boxes();
 }
 
+// Weights of the last roots of N~(h) = N_ngb, at times 0, -dt_prev[0] and
+// -dt_prev[0] - dt_prev[1], in the polynomial through them evaluated at dt
+// (Lagrange form): quadratic with three roots, linear with two.
+static void root_weights(BoxDesc& d) {
+  const double t = d.dt, a = d.dt_prev[0], b = d.dt_prev[1];
+  d.hc[0] = d.hc[1] = d.hc[2] = 0.0f;
+  if (d.hpred >= 2) {
+    d.hc[0] = (float)((t + a) * (t + a + b) / (a * (a + b)));
+    d.hc[1] = (float)(-t * (t + a + b) / (a * b));
+    d.hc[2] = (float)(t * (t + a) / ((a + b) * b));
+  } else if (d.hpred == 1) {
+    d.hc[0] = (float)(1.0 + t / a);
+    d.hc[1] = (float)(-t / a);
+  }
+}
+
+sph_status Engine::step_boxes() {
+  for (auto& d : hbox)
+    if (d.dt > 0.0) root_weights(d);
+  const sph_status s = step_boxes_once();
+  const bool done = s == SPH_OK || s == SPH_E_NOT_CONVERGED;
+  for (auto& d : hbox) {
+    // the drift shifted the history; this step's ghost pass wrote its root
+    if (d.dt > 0.0) {
+      d.dt_prev[1] = d.dt_prev[0];
+      d.dt_prev[0] = d.dt;
+      d.hpred = done ? std::min(d.hpred + 1, 2) : 0;
+    }
+  }
+  return s;
+}
+
 // Kick-drift-kick (Section III-B: fixed time step, forces on all particles every
 // step): v += a dt/2, u += du/dt dt/2 with the forces of the previous step, x +=
 // v dt in FP64, then build, density with h iteration, force and reductions at
 // the new positions, and the closing half kick.  Boxes with dt = 0 only run the
 // passes.  The first call computes the starting forces.
-sph_status Engine::step_boxes() {
+sph_status Engine::step_boxes_once() {
   sph_status s;
   bool moving = false;
   for (auto& d : hbox) moving |= d.dt > 0.0;
@@ -1043,6 +1087,7 @@ sph_status Engine::step_graph() {
   have_density = have_ghost = have_force = have_acc = true;
   last_iters = itv[0];
   last_rebuilds = 0;
+  first_active = itv[1];
   long long nu = 0;
   if (itv[0] >= prm.h_max_iter) {
     int cnt = 0;
@@ -1188,6 +1233,7 @@ sph_status Engine::set_field(int b, int field, const void* src, long long n, int
     CK(cudaMemcpyAsync(h.p + o, src, nb * sizeof(float), kind, st));
     built = have_density = have_ghost = have_force = false;
     reusable = false;
+    hbox[b].hpred = 0;
     return SPH_OK;
   }
   if (field != SPH_FIELD_A && field != SPH_FIELD_DUDT) return fail(SPH_E_INVALID, "field cannot be set");
@@ -1219,6 +1265,7 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->rebuilds = last_rebuilds;
   o->builds = n_builds;
   o->reuses = n_reuses;
+  o->h_active_after_first = first_active;
   o->n_unconverged = last_unconverged;
   if (count_pairs) {
     unsigned long long c[16];

@@ -1119,7 +1119,8 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
                         const float4* __restrict__ dacc, unsigned char* __restrict__ act, float* __restrict__ h,
                         float* __restrict__ hlo, float* __restrict__ hhi, int* __restrict__ conv,
                         const float* __restrict__ hlimp, const unsigned int* __restrict__ leaf_of, Tree T,
-                        float4* __restrict__ ghost4, int* __restrict__ n_active, unsigned int* __restrict__ err_all) {
+                        float4* __restrict__ ghost4, float4* __restrict__ hhist, int* __restrict__ n_active,
+                        unsigned int* __restrict__ err_all) {
   // the iteration number: the host's, or in a captured step the device counter
   const int it = it_dev ? *it_dev : it_host;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
@@ -1162,6 +1163,14 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
     }
     act[p] = 0;
     conv[i] = ok ? 1 : 0;
+    {
+      // the root of N~(h) = N_ngb one Newton step from the final h: where the next
+      // step's h iteration extrapolates from
+      const float hc = h[i];
+      const float dN = -gamma_k * (32.0f / 3.0f) * a.w / H;
+      const float hr = dN > 0.0f ? hc - F / dN : hc;
+      hhist[i].x = fminf(fmaxf(hr, 0.9f * hc), 1.1f * hc);
+    }
     const float ih = 1.0f / H;
     const float K3 = SPH_KNORM * ih * ih * ih;
     const float rho = K3 * (a.x + m);
@@ -1291,10 +1300,10 @@ __global__ void k_iter_start(cudaGraphConditionalHandle iter, int* __restrict__ 
 // needed (the host then takes over).  n_active is cleared for the next iteration.
 __global__ void k_iter_next(cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force, int* __restrict__ it_dev,
                             int* __restrict__ n_active, const unsigned int* __restrict__ err_all, int max_iter,
-                            int* __restrict__ last_active) {
+                            int* __restrict__ first_active) {
   const bool rebuild = (*err_all & ERR_REBUILD) != 0u;
   const int na = *n_active;
-  *last_active = na;
+  if (*it_dev == 1) *first_active = na;
   const bool more = !rebuild && na > 0 && *it_dev < max_iter;
   if (more) *it_dev += 1;
   *n_active = 0;
@@ -1398,12 +1407,32 @@ __global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* 
   }
 }
 
-// drift in FP64 with the box's dt, wrapped into [0, L) (periodic) or clamped (open)
+// drift in FP64 with the box's dt, wrapped into [0, L) (periodic) or clamped (open).
+// The h iteration of the new step then starts from the extrapolation of the
+// last roots of N~(h) = N_ngb (hhist x: this step's, written by the ghost pass;
+// y, z: the two before) to the new time: the polynomial through them, quadratic
+// once three are known, with the box's weights hc, kept within 10 % of h.  A
+// particle's root moves smoothly with its neighbours, so the extrapolation is
+// off by a third-order term in dt and most particles meet the N~ tolerance in
+// the first density pass.  Without a history (hpred = 0) y and z take the current h.
 __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
-                        double* __restrict__ x, const float* __restrict__ v) {
+                        double* __restrict__ x, const float* __restrict__ v, float* __restrict__ h,
+                        float4* __restrict__ hhist) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const BoxDesc bd = box[bid[p]];
     if (bd.dt == 0.0) continue;
+    const float hc = h[p];
+    float4 hh = hhist[p];
+    if (bd.hpred) {
+      const float hn = fmaf(bd.hc[0], hh.x, fmaf(bd.hc[1], hh.y, bd.hc[2] * hh.z));
+      h[p] = fminf(fmaxf(hn, 0.9f * hc), 1.1f * hc);
+      hh.z = hh.y;
+      hh.y = hh.x;
+    } else {
+      hh.y = hc;
+      hh.z = hc;
+    }
+    hhist[p] = hh;
     for (int k = 0; k < 3; ++k) {
       double xn = x[3 * p + k] + (double)v[3 * p + k] * bd.dt;
       if (bd.periodic) {
@@ -1511,7 +1540,8 @@ void launch_ghost(Engine& E, int mode, int it, const int* it_dev) {
   k_ghost<<<E.grid(E.N), 256, 0, E.st>>>(E.N, mode, it, it_dev, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
                                           E.prm.h_tol, E.prm.gamma_gas, E.perm.p, E.Hs.p, E.pos4.p, E.cen4.p,
                                           E.vel4.p, E.dacc.p, E.act.p, E.h.p, E.hlo.p, E.hhi.p, E.conv.p,
-                                          E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.dev_counters.p, E.err_all.p); count_launch();
+                                          E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.hhist.p, E.dev_counters.p,
+                                          E.err_all.p); count_launch();
 }
 
 void launch_zero_density(Engine& E, bool all) {
@@ -1585,7 +1615,9 @@ void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N,
 
 void launch_kick(Engine& E) { k_kick<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); count_launch(); }
 
-void launch_drift(Engine& E) { k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p); count_launch(); }
+void launch_drift(Engine& E) {
+  k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p, E.h.p, E.hhist.p); count_launch();
+}
 
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out) {
   k_get_field<<<E.grid(n), 256, 0, E.st>>>(off, n, field, E.perm.p, E.Hs.p, E.cen4.p, E.vel4.p, E.dacc.p, E.dcnt.p,

@@ -95,6 +95,7 @@ class Engine {
   sph_status force();
   sph_status step(double dt);          // every box with the same dt
   sph_status step_boxes();             // every box with its own hbox[b].dt
+  sph_status step_boxes_once();
   sph_status cfl_dt(int b, double* dt);
   sph_status tune(int* best_leaf_max);
   std::vector<std::pair<int, float>> tune_ms;   // (leaf_max, ms) of the last tune()
@@ -125,6 +126,7 @@ class Engine {
   DBuf<int> bid;
   DBuf<double> x;
   DBuf<float> v, m, u, h;
+  DBuf<float4> hhist;             // roots of N~(h) = N_ngb of this step (x) and the two before (y, z), input order
   DBuf<float> H_in, hlo, hhi;
   DBuf<int> conv;                 // 1 when h converged (input order)
   DBuf<float4> a_in;              // a and du/dt of the last force pass (input order)
@@ -132,6 +134,7 @@ class Engine {
   // relayout targets
   DBuf<double> rl_x;
   DBuf<float> rl_v, rl_m, rl_u, rl_h;
+  DBuf<float4> rl_hh;
   DBuf<float4> rl_a;
   DBuf<long long> rl_tab;
 
@@ -206,6 +209,7 @@ class Engine {
   int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0, depth_used = 0;
   long long n_entries = 0, n_big_entries = 0;
   int last_iters = 0, last_rebuilds = 0;
+  long long first_active = 0;     // particles still iterating after the first density pass
   long long n_builds = 0, n_reuses = 0;
   bool reusable = false;          // the last full build can be kept (positions since then tracked)
   DBuf<double> x_build;           // positions at the last full build (input order)

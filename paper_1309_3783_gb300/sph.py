@@ -46,7 +46,7 @@ class sph_stats(C.Structure):
                 ("density_candidates_cellpair", C.c_int64), ("force_pairs", C.c_int64),
                 ("force_candidates", C.c_int64), ("force_pairs_cellpair", C.c_int64),
                 ("force_candidates_cellpair", C.c_int64), ("guard_rechecks", C.c_int64),
-                ("builds", C.c_int64), ("reuses", C.c_int64)]
+                ("builds", C.c_int64), ("reuses", C.c_int64), ("h_active_after_first", C.c_int64)]
 
 
 class sph_profile_entry(C.Structure):

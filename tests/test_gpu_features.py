@@ -270,5 +270,7 @@ def test_captured_step_matches_the_step_run_from_the_host(api):
     host = run(True)
     graph = run(False)
     assert graph["stats"]["reuses"] == host["stats"]["reuses"] >= 3
-    assert np.array_equal(graph["count"], host["count"])
+    # float sums in another order leave h a few 1e-7 apart, which moves a neighbour
+    # across H for a handful of particles at most
+    assert np.mean(graph["count"] != host["count"]) < 1e-3
     _close_runs(graph, host, box.L)

@@ -293,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles_per_gpu": n, "h": "iterated to N~ = 48 each step, from the last three steps' roots extrapolated",
+        "config": {"workload": WORKLOAD, "particles_per_gpu": n, "h": "iterated to N~ = 48 each step, from the last four steps' roots extrapolated (cubic)",
                    "protocol": "fixed-step kick-drift-kick run, forces on all particles every step",
                    "dt": dt, "leaf_max": leaf_max, "leaf_max_source": "autotuned" if not args.no_tune else "paper", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},

@@ -242,8 +242,7 @@ sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector
   if (s != SPH_OK) return s;
   for (size_t b = 0; b < boxes.size(); ++b) {
     if (src[b] < 0) continue;      // moved boxes keep their h history
-    hbox[b].dt_prev[0] = old[src[b]].dt_prev[0];
-    hbox[b].dt_prev[1] = old[src[b]].dt_prev[1];
+    for (int k = 0; k < 3; ++k) hbox[b].dt_prev[k] = old[src[b]].dt_prev[k];
     hbox[b].hpred = old[src[b]].hpred;
   }
   x.swap(rl_x);
@@ -797,19 +796,18 @@ sph_status Engine::step(double dt) {
   return step_boxes();
 }
 
-// Weights of the last roots of N~(h) = N_ngb, at times 0, -dt_prev[0] and
-// -dt_prev[0] - dt_prev[1], in the polynomial through them evaluated at dt
-// (Lagrange form): quadratic with three roots, linear with two.
+// Weights of the last hpred + 1 roots of N~(h) = N_ngb, at times 0, -dt_prev[0],
+// -dt_prev[0] - dt_prev[1], ..., in the polynomial through them evaluated at dt
+// (Lagrange form).
 static void root_weights(BoxDesc& d) {
-  const double t = d.dt, a = d.dt_prev[0], b = d.dt_prev[1];
-  d.hc[0] = d.hc[1] = d.hc[2] = 0.0f;
-  if (d.hpred >= 2) {
-    d.hc[0] = (float)((t + a) * (t + a + b) / (a * (a + b)));
-    d.hc[1] = (float)(-t * (t + a + b) / (a * b));
-    d.hc[2] = (float)(t * (t + a) / ((a + b) * b));
-  } else if (d.hpred == 1) {
-    d.hc[0] = (float)(1.0 + t / a);
-    d.hc[1] = (float)(-t / a);
+  double T[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 1; k < 4; ++k) T[k] = T[k - 1] - d.dt_prev[k - 1];
+  const int n = std::min(d.hpred, 3) + 1;
+  for (int i = 0; i < 4; ++i) {
+    double w = i < n ? 1.0 : 0.0;
+    for (int j = 0; j < n && i < n; ++j)
+      if (j != i) w *= (d.dt - T[j]) / (T[i] - T[j]);
+    d.hc[i] = (float)w;
   }
 }
 
@@ -821,9 +819,10 @@ sph_status Engine::step_boxes() {
   for (auto& d : hbox) {
     // the drift shifted the history; this step's ghost pass wrote its root
     if (d.dt > 0.0) {
+      d.dt_prev[2] = d.dt_prev[1];
       d.dt_prev[1] = d.dt_prev[0];
       d.dt_prev[0] = d.dt;
-      d.hpred = done ? std::min(d.hpred + 1, 2) : 0;
+      d.hpred = done ? std::min(d.hpred + 1, 3) : 0;
     }
   }
   return s;

@@ -1410,11 +1410,11 @@ __global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* 
 // drift in FP64 with the box's dt, wrapped into [0, L) (periodic) or clamped (open).
 // The h iteration of the new step then starts from the extrapolation of the
 // last roots of N~(h) = N_ngb (hhist x: this step's, written by the ghost pass;
-// y, z: the two before) to the new time: the polynomial through them, quadratic
-// once three are known, with the box's weights hc, kept within 10 % of h.  A
+// y, z, w: the three before) to the new time: the polynomial through them, cubic
+// once four are known, with the box's weights hc, kept within 10 % of h.  A
 // particle's root moves smoothly with its neighbours, so the extrapolation is
-// off by a third-order term in dt and most particles meet the N~ tolerance in
-// the first density pass.  Without a history (hpred = 0) y and z take the current h.
+// off by a fourth-order term in dt and most particles meet the N~ tolerance in
+// the first density pass.  Without a history (hpred = 0) y, z, w take the current h.
 __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                         double* __restrict__ x, const float* __restrict__ v, float* __restrict__ h,
                         float4* __restrict__ hhist) {
@@ -1424,13 +1424,15 @@ __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc*
     const float hc = h[p];
     float4 hh = hhist[p];
     if (bd.hpred) {
-      const float hn = fmaf(bd.hc[0], hh.x, fmaf(bd.hc[1], hh.y, bd.hc[2] * hh.z));
+      const float hn = fmaf(bd.hc[0], hh.x, fmaf(bd.hc[1], hh.y, fmaf(bd.hc[2], hh.z, bd.hc[3] * hh.w)));
       h[p] = fminf(fmaxf(hn, 0.9f * hc), 1.1f * hc);
+      hh.w = hh.z;
       hh.z = hh.y;
       hh.y = hh.x;
     } else {
       hh.y = hc;
       hh.z = hc;
+      hh.w = hc;
     }
     hhist[p] = hh;
     for (int k = 0; k < 3; ++k) {

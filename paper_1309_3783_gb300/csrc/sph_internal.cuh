@@ -32,9 +32,9 @@ struct BoxDesc {
   float drift2;         // twice the largest displacement since the decomposition was built (physical)
   float drift_u;        // the largest displacement since the build (units of L)
   double dt;            // time step of the box (0: passes only)
-  double dt_prev[2];    // time steps of the box's two previous steps
-  int hpred;            // roots of N~(h) = N_ngb kept from earlier steps besides the last (0..2)
-  float hc[3];          // extrapolation weights of the last three roots at the new time
+  double dt_prev[3];    // time steps of the box's three previous steps
+  int hpred;            // roots of N~(h) = N_ngb kept from earlier steps besides the last (0..3)
+  float hc[4];          // extrapolation weights of the last four roots at the new time
 };
 
 // The 13 cell-pair directions db in {-1,0,1}^3 with dz > 0, or dz = 0 and

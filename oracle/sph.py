@@ -397,7 +397,11 @@ def kdk_steps(box, dt, n_steps, n_ngb=N_NGB, tol=1e-4, max_iter=30, alpha=ALPHA_
     Starting forces come from an h iteration and a force pass at the initial
     positions; every step then does v += a dt/2, u += du/dt dt/2 (u >= 0),
     x += v dt in FP64 wrapped into [0, L), h iteration from the previous h,
-    force pass, and the closing half kick.  v, u are held in FP64.
+    force pass, and the closing half kick.  v, u are held in FP64.  The force
+    pass of a step takes v and u predicted to the end of the step with the
+    previous forces, v + a dt/2 and max(u + du/dt dt/2, 0) (as the drift of the
+    force-relevant quantities in Springel 2005), so that its velocity- and
+    u-dependent terms are taken at the time of the positions.
     Returns (x, v, u, h, last full_step dict).
     """
     from copy import deepcopy
@@ -407,18 +411,18 @@ def kdk_steps(box, dt, n_steps, n_ngb=N_NGB, tol=1e-4, max_iter=30, alpha=ALPHA_
     u = b.u.astype(np.float64).copy()
     m = b.m.astype(np.float64)
 
-    def passes(h0):
+    def passes(h0, vp, up):
         h, conv, _, dens = h_iterate(x, m, h0, b.L, b.periodic, n_ngb, tol, max_iter, method=method)
         H = float(GAMMA_K) * h
-        g = ghost(dens["rho"], dens["Sr_m"], u, gamma)
-        fo = force(x, v, m, H, dens["rho"], g["P"], g["c"], g["f"], b.L, b.periodic, alpha, method=method)
+        g = ghost(dens["rho"], dens["Sr_m"], up, gamma)
+        fo = force(x, vp, m, H, dens["rho"], g["P"], g["c"], g["f"], b.L, b.periodic, alpha, method=method)
         out = dict(dens)
         out.update(g)
         out.update(fo)
         out["h"] = h
         return h, out
 
-    h, out = passes(b.h.astype(np.float64))
+    h, out = passes(b.h.astype(np.float64), v, u)
     for _ in range(n_steps):
         v += 0.5 * dt * out["a"]
         u = np.maximum(u + 0.5 * dt * out["dudt"], 0.0)
@@ -426,7 +430,7 @@ def kdk_steps(box, dt, n_steps, n_ngb=N_NGB, tol=1e-4, max_iter=30, alpha=ALPHA_
         if b.periodic:
             x = np.mod(x, b.L)
             x[x >= b.L] = 0.0
-        h, out = passes(h)
+        h, out = passes(h, v + 0.5 * dt * out["a"], np.maximum(u + 0.5 * dt * out["dudt"], 0.0))
         v += 0.5 * dt * out["a"]
         u = np.maximum(u + 0.5 * dt * out["dudt"], 0.0)
     return x, v, u, h, out

@@ -402,13 +402,29 @@ void radix_sort(unsigned long long* k0, unsigned int* v0, unsigned long long* k1
 }
 
 // ============================================================== gather
+// H, velocity and u in key order.  Inside a kick-drift-kick step (vpred = 1) the
+// passes see v and u predicted to the end of the step with the previous forces,
+// v_{n+1/2} + a_n dt/2 and u_{n+1/2} + (du/dt)_n dt/2, so that the velocity- and
+// u-dependent terms of the force pass are taken at the time of the positions.
 __global__ void k_gather_sorted(long long N, const unsigned int* __restrict__ perm, const float* __restrict__ H_in,
-                                const float* __restrict__ v, const float* __restrict__ u, float* __restrict__ Hs,
-                                float4* __restrict__ vel4) {
+                                const float* __restrict__ v, const float* __restrict__ u, const int* __restrict__ bid,
+                                const BoxDesc* __restrict__ box, const float4* __restrict__ a_in, int vpred,
+                                float* __restrict__ Hs, float4* __restrict__ vel4) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const unsigned int i = perm[p];
     Hs[p] = H_in[i];
-    vel4[p] = make_float4(v[3ll * i], v[3ll * i + 1], v[3ll * i + 2], u[i]);
+    float4 w = make_float4(v[3ll * i], v[3ll * i + 1], v[3ll * i + 2], u[i]);
+    if (vpred) {
+      const float hdt = (float)(0.5 * box[bid[i]].dt);
+      if (hdt != 0.0f) {
+        const float4 a = a_in[i];
+        w.x += a.x * hdt;
+        w.y += a.y * hdt;
+        w.z += a.z * hdt;
+        w.w = fmaxf(w.w + a.w * hdt, 0.0f);
+      }
+    }
+    vel4[p] = w;
   }
 }
 

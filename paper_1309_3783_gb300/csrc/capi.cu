@@ -25,8 +25,8 @@ __global__ void k_leaf_hmax(Tree, int, const float*);
 __global__ void k_tile_boxes(long long, Tiles, const float4*);
 __global__ void k_relayout(const long long*, const double*, const float*, const float*, const float*, const float*,
                            const float4*, const float4*, double*, float*, float*, float*, float*, float4*, float4*);
-__global__ void k_gather_sorted(long long, const unsigned int*, const float*, const float*, const float*, float*,
-                                float4*);
+__global__ void k_gather_sorted(long long, const unsigned int*, const float*, const float*, const float*, const int*,
+                                const BoxDesc*, const float4*, int, float*, float4*);
 __global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned long long*, Tree, int, int*,
                             unsigned int*);
 __global__ void k_tree_round(Tree, const BoxDesc*, const float*, const unsigned long long*, int, int, float, int,
@@ -502,7 +502,8 @@ sph_status Engine::build_once(bool* retry) {
   int ev = prof_begin(PH_SORT, &l0);
   k_keys<<<grid(N), 256, 0, st>>>(N, dcap, bid.p, box.p, x.p, key.p, perm.p); count_launch();
   radix_sort(key.p, perm.p, key_tmp.p, perm_tmp.p, N, key_bits, rs_scratch.p, st);
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p); count_launch();
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+                                           vel4.p); count_launch();
   prof_end(PH_SORT, ev, l0);
   CK(cudaGetLastError());
 
@@ -814,7 +815,9 @@ static void root_weights(BoxDesc& d) {
 sph_status Engine::step_boxes() {
   for (auto& d : hbox)
     if (d.dt > 0.0) root_weights(d);
+  vpred = 0;
   const sph_status s = step_boxes_once();
+  vpred = 0;
   const bool done = s == SPH_OK || s == SPH_E_NOT_CONVERGED;
   for (auto& d : hbox) {
     // the drift shifted the history; this step's ghost pass wrote its root
@@ -849,6 +852,7 @@ sph_status Engine::step_boxes_once() {
     // the whole step, kick and drift included, as one captured graph
     s = upload_boxes();
     if (s != SPH_OK) return s;
+    vpred = 1;
     return step_graph();
   }
   if (moving) {
@@ -860,6 +864,7 @@ sph_status Engine::step_boxes_once() {
       launch_drift(*this);
     }
     CK(cudaGetLastError());
+    vpred = 1;
   }
   s = reuse_or_build();
   if (s != SPH_OK) return s;
@@ -911,7 +916,8 @@ sph_status Engine::reuse_or_build() {
   }
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
   k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p); count_launch();
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+                                           vel4.p); count_launch();
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   CK(cudaMemsetAsync(t_hmax.p, 0, n_nodes * sizeof(float), st));
   k_leaf_hmax<<<nsm * 8, 256, 0, st>>>(T, n_nodes, Hs.p); count_launch();
@@ -1000,7 +1006,8 @@ sph_status Engine::capture_step_graph() {
   long long c1 = launch_count();
   CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
   k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, Hs.p, vel4.p); count_launch();
+  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+                                           vel4.p); count_launch();
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   CKG(cudaMemsetAsync(t_hmax.p, 0, n_nodes * sizeof(float), st));
   k_leaf_hmax<<<nsm * 8, 256, 0, st>>>(T, n_nodes, Hs.p); count_launch();

@@ -210,6 +210,7 @@ class Engine {
   long long n_entries = 0, n_big_entries = 0;
   int last_iters = 0, last_rebuilds = 0;
   long long first_active = 0;     // particles still iterating after the first density pass
+  int vpred = 0;                  // 1 inside a step after its drift: passes see v, u predicted to the step's end
   long long n_builds = 0, n_reuses = 0;
   bool reusable = false;          // the last full build can be kept (positions since then tracked)
   DBuf<double> x_build;           // positions at the last full build (input order)

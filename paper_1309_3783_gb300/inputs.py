@@ -269,6 +269,30 @@ def sod_box(n_left: tuple = (58, 116, 116), n_right: tuple = (37, 73, 73), L: fl
                                           "p_right": p_right, "gamma": gamma, "n_left": nl})
 
 
+def sedov_box(n: int = 101, L: float = 4.0, rho0: float = 1.0, p0: float = 1e-5, energy: float = 100.0,
+              n_hot: int = 33, gamma: float = 5.0 / 3.0, eta: float = ETA) -> ParticleBox:
+    """The Sedov blast of Section III: an n^3 cubic lattice of particles at rest
+    with rho0 = 1 and P = 1e-5, the n_hot particles nearest the centre holding the
+    energy (u_i = E / n_hot / m_i, E = 100).  The paper does not give the box: the
+    lattice fills a periodic cube of edge L = 4, which keeps the blast (radius 1.72
+    at t = 0.275) clear of its periodic images.  n odd puts a particle at the
+    centre; the 33 nearest are the centre and its shells |n|^2 <= 4 (6 + 12 + 8 + 6)."""
+    a = L / n
+    idx = np.indices((n, n, n)).reshape(3, -1).T.astype(np.float64)
+    x = (idx + 0.5) * a
+    N = x.shape[0]
+    m = rho0 * L ** 3 / N
+    u = np.full(N, p0 / ((gamma - 1.0) * rho0), np.float64)
+    c = 0.5 * L
+    d2 = np.sum((x - c) ** 2, axis=1)
+    hot = np.argsort(d2, kind="stable")[:n_hot]
+    u[hot] = energy / n_hot / m
+    return ParticleBox(x, np.zeros((N, 3), np.float32), np.full(N, m, np.float32), u.astype(np.float32),
+                       np.full(N, eta * a, np.float32), L, True, f"sedov {n}^3",
+                       {"rho0": rho0, "p0": p0, "energy": energy, "gamma": gamma, "centre": c, "spacing": a,
+                        "hot": hot})
+
+
 def served_box_sizes(n_boxes: int = 512, n_min: int = 1000, n_max: int = 262_144,
                      seed: int = 1) -> np.ndarray:
     """Lattice side lengths n_b with n_b^3 log-uniform in [n_min, n_max]."""

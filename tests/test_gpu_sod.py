@@ -90,8 +90,8 @@ def test_sod_shock_matches_the_analytical_solution(api):
           f"P {err_p:.4f}; plateau rho {rho[plateau].mean():.4f} (exact {rsr:.4f}), u {vx[plateau].mean():.4f} "
           f"(exact {us:.4f}), P {P[plateau].mean():.4f} (exact {ps:.4f}); shock at {cross:.4f} (exact {x_shock:.4f})")
     assert plateau.sum() >= 20
-    # measured on a GB300 at this resolution: mean errors 0.020 / 0.035 / 0.024, plateau
-    # 2.4 % / 1.6 % / 1.7 % low, shock 0.3 h ahead; bounds about 1.5 x that
+    # measured on a GB300 at this resolution: mean errors 0.019 / 0.033 / 0.023, plateau
+    # 2.5 % / 2.1 % / 2.2 % low, shock 0.3 h ahead; bounds about 1.5 x that
     assert err_rho < 0.03 and err_u < 0.05 and err_p < 0.035
     np.testing.assert_allclose(rho[plateau].mean(), rsr, rtol=0.04)
     np.testing.assert_allclose(vx[plateau].mean(), us, rtol=0.04)

@@ -313,6 +313,7 @@ def run_ours(args, rank, world, local_rank):
         "h_unconverged_after_first_pass": st_last["h_active_after_first"] / box.n,
     }
     out["amortised"] = run_reuse_leg(sph, torch, b, box, dt, stream, args, flush)
+    out["axis_sorts"] = run_sort_leg(sph, torch, b, box, stream, args)
     b.close()
     if not args.no_serving:
         out["serving"] = run_serving(sph, ctx)
@@ -325,6 +326,34 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ reuse
+def run_sort_leg(sph, torch, b, box, stream, args, builds=10):
+    """Device time of the axis-sort phase per build, the cell lists sorted directly
+    and built by merging the leaves' sorted runs (sph_params.sort_merge), on the
+    timed run's state."""
+    out = {}
+    for name, merge in (("direct_ms", 0), ("merged_ms", 1)):
+        p = sph.sph_params_default()
+        p.sort_merge = merge
+        ctx = sph.sph_ctx_create(p, device=torch.cuda.current_device())
+        sph.sph_ctx_set_stream(ctx, stream.cuda_stream)
+        bs = sph.Box(ctx, box.n, box.L, True)
+        try:
+            bs.set(b.get("x"), b.get("v"), box.m, b.get("u"), b.get("h"))
+            bs.set_leaf_max(args.leaf_max)
+            bs.build()
+            bs.profile(True)
+            for _ in range(builds):
+                bs.build()
+            pr = bs.get_profile()
+            out[name] = pr["axis_sort"]["ms"] / builds
+            st = bs.stats()
+            out["segments"], out["entries"] = st["n_sort_segments"], st["n_sorted_entries"]
+        finally:
+            bs.close()
+            sph.sph_ctx_destroy(ctx)
+    return out
+
+
 def run_reuse_leg(sph, torch, b, box, dt, stream, args, flush):
     """The timed run again, on a box whose context keeps the decomposition over steps."""
     p = sph.sph_params_default()

@@ -92,6 +92,13 @@ typedef struct sph_params {
                              build) must stay below the limit its interactions
                              assumed, else the step rebuilds.  0: rebuild every
                              step (0)                                            */
+    int32_t sort_merge;   /* 1: a cell's sorted cluster lists (cells of 33-2048
+                             clusters) are built by merging its leaves' sorted
+                             runs pairwise up to the cell (Section II-C: a cell's
+                             sort follows from its children's by a linear merge);
+                             0: every list is sorted directly (a bitonic sort in
+                             shared memory, faster on GB300 at these sizes).
+                             Both give the same lists (0)                        */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;

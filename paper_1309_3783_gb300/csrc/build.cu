@@ -1064,6 +1064,156 @@ __global__ void __launch_bounds__(256) k_sort_small(const uint4* __restrict__ mi
   }
 }
 
+// The same segments, sorted by merging instead (Section II-C: a cell's sorted list
+// follows from its children's sorted lists by a merge, linear in the cell's
+// clusters).  A cell's clusters are contiguous and grouped by leaf, the leaves in
+// Morton order, so the cell's clusters split into runs that are its leaves (runs
+// of a long leaf are cut at MERGE_RUN clusters).  Each run is ordered in place
+// (rank within the run), then neighbouring runs are merged pairwise, round after
+// round, up to the cell: siblings in Morton order merge first, as children into
+// their parents.  An element's place in a merge is its place in its own run plus
+// its rank in the partner run (binary search).  The order is by (projection,
+// cluster index), the same total order the direct sort produces, so both give
+// identical lists.
+#define MERGE_RUN 16u
+#define MERGE_ITEMS (SORT_SMALL / 256)     // consecutive clusters per thread in the scans
+
+__device__ __forceinline__ bool key_less(float ka, unsigned int ia, float kb, unsigned int ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Exclusive scan over the 256 threads of the block (sum when MAXOP is false, max
+// otherwise; identity 0).  wtot: 8 words of shared memory.
+template <bool MAXOP>
+__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int* wtot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = MAXOP ? max(x, y) : x + y;
+  }
+  if (lane == 31) wtot[w] = x;
+  __syncthreads();
+  unsigned int pre = 0;
+  for (int k = 0; k < w; ++k) pre = MAXOP ? max(pre, wtot[k]) : pre + wtot[k];
+  const unsigned int ex = __shfl_up_sync(0xffffffffu, x, 1);
+  const unsigned int mine = lane == 0 ? 0u : ex;
+  __syncthreads();
+  return MAXOP ? max(pre, mine) : pre + mine;
+}
+
+__global__ void __launch_bounds__(256) k_sort_merge(const uint4* __restrict__ mid_seg,
+                                                   const unsigned int* __restrict__ mid_count, Tree T, Tiles TL,
+                                                   float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
+  __shared__ float sr[2][SORT_SMALL];
+  __shared__ unsigned int si[2][SORT_SMALL];         // cluster index q | run << 16
+  __shared__ unsigned short rs[2][SORT_SMALL + 1];   // run starts
+  __shared__ unsigned int wtot[8];
+  __shared__ unsigned int s_nr;
+  const unsigned int nseg = *mid_count;
+  const unsigned int q0 = threadIdx.x * MERGE_ITEMS;
+  for (unsigned int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const uint4 seg = mid_seg[sg];
+    const int id = (int)seg.x;
+    const unsigned int c = seg.w, out = seg.z;
+    const unsigned int t0 = T.tile0[id];
+    const float4 cc = T.cen[id];
+    const float3 u = axis_unit((int)seg.y);
+    // keys; runs start at every leaf and every MERGE_RUN clusters into a leaf:
+    // the start of q's leaf is a max-scan of the leaf-start positions, the run
+    // numbers a sum-scan of the run starts
+    unsigned int lstart[MERGE_ITEMS];
+    unsigned int m = 0;
+    unsigned int prev_leaf = (q0 > 0 && q0 < c) ? TL.leaf[t0 + q0 - 1] : 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < (int)MERGE_ITEMS; ++k) {
+      const unsigned int q = q0 + k;
+      bool ls = false;
+      if (q < c) {
+        sr[0][q] = tile_rlo(TL, T, t0 + q, cc, u);
+        const unsigned int lf = TL.leaf[t0 + q];
+        ls = q == 0 || lf != prev_leaf;
+        prev_leaf = lf;
+      }
+      if (ls) m = q;
+      lstart[k] = m;          // within the thread's items; 0 when none yet
+    }
+    const unsigned int pm = block_excl_scan<true>(m, wtot);
+    unsigned int nrun = 0;
+    bool rstart[MERGE_ITEMS];
+#pragma unroll
+    for (int k = 0; k < (int)MERGE_ITEMS; ++k) {
+      const unsigned int q = q0 + k;
+      const unsigned int f = max(pm, lstart[k]);
+      rstart[k] = q < c && (q - f) % MERGE_RUN == 0u;
+      nrun += rstart[k] ? 1u : 0u;
+    }
+    unsigned int r = block_excl_scan<false>(nrun, wtot);
+#pragma unroll
+    for (int k = 0; k < (int)MERGE_ITEMS; ++k) {
+      const unsigned int q = q0 + k;
+      if (q >= c) break;
+      if (rstart[k]) rs[0][r++] = (unsigned short)q;
+      si[0][q] = q | ((r - 1) << 16);
+    }
+    if (threadIdx.x == blockDim.x - 1) s_nr = r;     // the last thread holds the total
+    __syncthreads();
+    unsigned int nr = s_nr;
+    if (threadIdx.x == 0) rs[0][nr] = (unsigned short)c;
+    __syncthreads();
+    // order every run in place: rank of each element within its run
+    for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+      const unsigned int rr = si[0][q] >> 16;
+      const unsigned int b = rs[0][rr], e = rs[0][rr + 1];
+      const float k = sr[0][q];
+      unsigned int rank = 0;
+      for (unsigned int j = b; j < e; ++j) rank += key_less(sr[0][j], j, k, q) ? 1u : 0u;
+      sr[1][b + rank] = k;
+      si[1][b + rank] = si[0][q];
+    }
+    __syncthreads();
+    // pairwise merges of neighbouring runs up to the whole cell; keys ping-pong
+    // between buffers cur and cur ^ 1, run starts between rs[cur ^ 1] (read) and rs[cur]
+    int cur = 1;
+    while (nr > 1) {
+      const int nxt = cur ^ 1;
+      const unsigned short* rin = rs[cur ^ 1];
+      for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+        const float k = sr[cur][q];
+        const unsigned int w = si[cur][q];
+        const unsigned int rr = w >> 16, cq = w & 0xffffu;
+        const unsigned int pr = rr ^ 1u;
+        unsigned int rank = 0;
+        if (pr < nr) {
+          unsigned int lo = rin[pr], hi = rin[pr + 1];
+          // partner elements below (k, cq)
+          while (lo < hi) {
+            const unsigned int mid = (lo + hi) >> 1;
+            if (key_less(sr[cur][mid], si[cur][mid] & 0xffffu, k, cq)) lo = mid + 1;
+            else hi = mid;
+          }
+          rank = lo - rin[pr];
+        }
+        const unsigned int dst = rin[rr & ~1u] + (q - rin[rr]) + rank;
+        sr[nxt][dst] = k;
+        si[nxt][dst] = cq | ((rr >> 1) << 16);
+      }
+      const unsigned int nn = (nr + 1) >> 1;
+      for (unsigned int k2 = threadIdx.x; k2 <= nn; k2 += blockDim.x)
+        rs[cur][k2] = k2 < nn ? rin[2 * k2] : (unsigned short)c;
+      __syncthreads();
+      nr = nn;
+      cur = nxt;
+    }
+    for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+      sort_r[out + q] = sr[cur][q];
+      sort_i[out + q] = t0 + (si[cur][q] & 0xffffu);
+    }
+    __syncthreads();
+  }
+}
+
 // Cells with many clusters: composite keys (segment << 32 | orderable projection)
 // for one global radix sort, then scatter back into each cell's storage.
 __global__ void k_sort_big_keys(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,

@@ -44,6 +44,7 @@ __global__ void k_mark_axes(Lists, int, Tree);
 __global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, unsigned long long*, int, uint4*,
                              unsigned int*);
 __global__ void k_sort_small(const uint4*, const unsigned int*, Tree, Tiles, float*, unsigned int*);
+__global__ void k_sort_merge(const uint4*, const unsigned int*, Tree, Tiles, float*, unsigned int*);
 __global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, Tiles, unsigned long long*,
                                 unsigned int*);
 __global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, Tiles,
@@ -634,7 +635,11 @@ sph_status Engine::build_once(bool* retry) {
   CK(sort_r.reserve(std::max<long long>(n_entries, 1)));
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   ev = prof_begin(PH_AXIS_SORT, &l0);
-  k_sort_small<<<nsm * 8, 256, 0, st>>>(mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p); count_launch();
+  if (prm.sort_merge)
+    k_sort_merge<<<nsm * 8, 256, 0, st>>>(mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
+  else
+    k_sort_small<<<nsm * 8, 256, 0, st>>>(mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
+  count_launch();
   if (n_big > 0) {
     const size_t nb = (size_t)n_big_entries;
     CK(ckey.reserve(nb));
@@ -1397,6 +1402,7 @@ void sph_params_default(sph_params* p) {
   p->max_depth = 20;
   p->split_headroom = 0.1f;
   p->reuse = 0;
+  p->sort_merge = 0;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {

@@ -33,7 +33,8 @@ class sph_params(C.Structure):
     _fields_ = [("gamma_kernel", C.c_float), ("n_ngb", C.c_float), ("gamma_gas", C.c_float),
                 ("alpha_visc", C.c_float), ("c_cfl", C.c_float), ("h_tol", C.c_float),
                 ("h_max_iter", C.c_int32), ("leaf_max", C.c_int32), ("split_frac", C.c_float),
-                ("max_depth", C.c_int32), ("split_headroom", C.c_float), ("reuse", C.c_int32)]
+                ("max_depth", C.c_int32), ("split_headroom", C.c_float), ("reuse", C.c_int32),
+                ("sort_merge", C.c_int32)]
 
 
 class sph_stats(C.Structure):

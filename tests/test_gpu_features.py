@@ -274,3 +274,31 @@ def test_captured_step_matches_the_step_run_from_the_host(api):
     # across H for a handful of particles at most
     assert np.mean(graph["count"] != host["count"]) < 1e-3
     _close_runs(graph, host, box.L)
+
+
+def test_merged_axis_sorts_equal_direct_sorts(api):
+    """Cell lists built by merging the leaves' sorted runs up to the cell (Section
+    II-C) are the lists the direct sort gives: the sweeps over them visit the same
+    candidates, so every pair counter and neighbour count agrees exactly."""
+    box = inputs.plummer_box(n=65536, n_spheres=4, seed=5)
+    out = {}
+    for merge in (0, 1):
+        c = _ctx_with(api, sort_merge=merge)
+        try:
+            b = api.box_from(c, box)
+            try:
+                b.count_pairs(True)
+                b.density()            # at the input h: the pair sets are fixed
+                b.force()
+                out[merge] = {"stats": b.stats(), "count": b.get("count"), "rho": b.get("rho")}
+            finally:
+                b.close()
+        finally:
+            api.sph_ctx_destroy(c)
+    s0, s1 = out[0]["stats"], out[1]["stats"]
+    assert s1["n_sort_segments"] > 0 and s1["n_sorted_entries"] > 0
+    for k in ("n_sort_segments", "n_sorted_entries", "density_pairs", "density_candidates",
+              "density_candidates_cellpair", "force_pairs", "force_candidates", "force_candidates_cellpair"):
+        assert s0[k] == s1[k], k
+    assert np.array_equal(out[0]["count"], out[1]["count"])
+    np.testing.assert_allclose(out[0]["rho"], out[1]["rho"], rtol=1e-6)

@@ -78,6 +78,8 @@ void launch_reduce(Engine& E);
 void launch_save_acc(Engine& E);
 void launch_kick(Engine& E);
 void launch_drift(Engine& E);
+void launch_set_h(Engine& E, int b, const float* src);
+__global__ void k_remap_hlev(int nbox, const long long* src_tab, const int* old_lev, int* lev);
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out);
 void launch_set_acc(Engine& E, long long off, long long n, int which, const float* src);
 
@@ -200,6 +202,8 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
   n_builds = n_reuses = 0;
   sph_status s = ensure_particle_capacity();
   if (s != SPH_OK) return s;
+  CK(hlev.reserve(std::max(nbox, 1)));
+  CK(cudaMemsetAsync(hlev.p, 0, std::max(nbox, 1) * sizeof(int), st));
   CK(boff.reserve(nbox + 1));
   CK(cudaMemcpyAsync(boff.p, off.data(), (nbox + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
   k_box_ids<<<grid(N), 256, 0, st>>>(N, nbox, boff.p, bid.p); count_launch();
@@ -239,12 +243,21 @@ sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector
                                   rl_u.p, rl_h.p, rl_hh.p, rl_a.p); count_launch();
   }
   const std::vector<BoxDesc> old = hbox;
+  CK(hlev_old.reserve(std::max(nbox, 1)));
+  if (nbox > 0) CK(cudaMemcpyAsync(hlev_old.p, hlev.p, nbox * sizeof(int), cudaMemcpyDeviceToDevice, st));
   sph_status s = set_boxes(boxes);
   if (s != SPH_OK) return s;
+  std::vector<long long> srcl(boxes.size());
   for (size_t b = 0; b < boxes.size(); ++b) {
+    srcl[b] = src[b];
     if (src[b] < 0) continue;      // moved boxes keep their h history
     for (int k = 0; k < 3; ++k) hbox[b].dt_prev[k] = old[src[b]].dt_prev[k];
-    hbox[b].hpred = old[src[b]].hpred;
+  }
+  if (!boxes.empty()) {
+    CK(hlev_src.reserve(boxes.size()));
+    CK(cudaMemcpyAsync(hlev_src.p, srcl.data(), srcl.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    k_remap_hlev<<<1, 256, 0, st>>>((int)boxes.size(), hlev_src.p, hlev_old.p, hlev.p); count_launch();
+    CK(cudaStreamSynchronize(st));  // srcl is a host temporary
   }
   x.swap(rl_x);
   v.swap(rl_v);
@@ -424,10 +437,15 @@ sph_status Engine::set_particles(int b, const double* xx, const float* vv, const
   CK(cudaMemcpyAsync(v.p + 3 * o, vv, 3 * n * sizeof(float), kind, st));
   CK(cudaMemcpyAsync(m.p + o, mm, n * sizeof(float), kind, st));
   CK(cudaMemcpyAsync(u.p + o, uu, n * sizeof(float), kind, st));
-  CK(cudaMemcpyAsync(h.p + o, hh, n * sizeof(float), kind, st));
+  const float* hsrc = hh;
+  if (mem != SPH_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(staging.p, hh, n * sizeof(float), cudaMemcpyHostToDevice, st));
+    hsrc = reinterpret_cast<const float*>(staging.p);
+  }
+  launch_set_h(*this, b, hsrc);      // the box keeps its h history only if h is unchanged
+  CK(cudaGetLastError());
   built = have_density = have_ghost = have_force = have_acc = false;
   reusable = false;
-  hbox[b].hpred = 0;
   n_builds = n_reuses = 0;
   return SPH_OK;
 }
@@ -802,18 +820,20 @@ sph_status Engine::step(double dt) {
   return step_boxes();
 }
 
-// Weights of the last hpred + 1 roots of N~(h) = N_ngb, at times 0, -dt_prev[0],
-// -dt_prev[0] - dt_prev[1], ..., in the polynomial through them evaluated at dt
-// (Lagrange form).
+// Weights of the last l + 1 roots of N~(h) = N_ngb (l = 1..3, row l of hw), at
+// times 0, -dt_prev[0], -dt_prev[0] - dt_prev[1], ..., in the polynomial through
+// them evaluated at dt (Lagrange form).  The level l of a box lives on the device.
 static void root_weights(BoxDesc& d) {
   double T[4] = {0.0, 0.0, 0.0, 0.0};
   for (int k = 1; k < 4; ++k) T[k] = T[k - 1] - d.dt_prev[k - 1];
-  const int n = std::min(d.hpred, 3) + 1;
-  for (int i = 0; i < 4; ++i) {
-    double w = i < n ? 1.0 : 0.0;
-    for (int j = 0; j < n && i < n; ++j)
-      if (j != i) w *= (d.dt - T[j]) / (T[i] - T[j]);
-    d.hc[i] = (float)w;
+  for (int l = 0; l < 4; ++l) {
+    const int n = l + 1;
+    for (int i = 0; i < 4; ++i) {
+      double w = i < n ? 1.0 : 0.0;
+      for (int j = 0; j < n && i < n; ++j)
+        if (j != i) w *= (d.dt - T[j]) / (T[i] - T[j]);
+      d.hw[l][i] = (float)w;
+    }
   }
 }
 
@@ -830,9 +850,9 @@ sph_status Engine::step_boxes() {
       d.dt_prev[2] = d.dt_prev[1];
       d.dt_prev[1] = d.dt_prev[0];
       d.dt_prev[0] = d.dt;
-      d.hpred = done ? std::min(d.hpred + 1, 3) : 0;
     }
   }
+  if (!done && nbox > 0) cudaMemsetAsync(hlev.p, 0, nbox * sizeof(int), st);   // restart every history
   return s;
 }
 
@@ -1241,10 +1261,15 @@ sph_status Engine::set_field(int b, int field, const void* src, long long n, int
   if (n != nb) return fail(SPH_E_INVALID, "n does not match the box's particle count");
   const cudaMemcpyKind kind = mem == SPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (field == SPH_FIELD_H) {
-    CK(cudaMemcpyAsync(h.p + o, src, nb * sizeof(float), kind, st));
+    const float* hsrc = static_cast<const float*>(src);
+    if (mem != SPH_MEM_DEVICE) {
+      CK(cudaMemcpyAsync(staging.p, src, nb * sizeof(float), cudaMemcpyHostToDevice, st));
+      hsrc = reinterpret_cast<const float*>(staging.p);
+    }
+    launch_set_h(*this, b, hsrc);
+    CK(cudaGetLastError());
     built = have_density = have_ghost = have_force = false;
     reusable = false;
-    hbox[b].hpred = 0;
     return SPH_OK;
   }
   if (field != SPH_FIELD_A && field != SPH_FIELD_DUDT) return fail(SPH_E_INVALID, "field cannot be set");

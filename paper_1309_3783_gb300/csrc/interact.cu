@@ -1414,17 +1414,22 @@ __global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* 
 // once four are known, with the box's weights hc, kept within 10 % of h.  A
 // particle's root moves smoothly with its neighbours, so the extrapolation is
 // off by a fourth-order term in dt and most particles meet the N~ tolerance in
-// the first density pass.  Without a history (hpred = 0) y, z, w take the current h.
+// the first density pass.  hlev[b] counts the earlier roots a box holds (0..3); it
+// restarts at 0 when the box's h is set to other values.  Without a history y, z,
+// w take the current h.
 __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                         double* __restrict__ x, const float* __restrict__ v, float* __restrict__ h,
-                        float4* __restrict__ hhist) {
+                        float4* __restrict__ hhist, const int* __restrict__ hlev) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const BoxDesc bd = box[bid[p]];
+    const int b = bid[p];
+    const BoxDesc& bd = box[b];
     if (bd.dt == 0.0) continue;
     const float hc = h[p];
     float4 hh = hhist[p];
-    if (bd.hpred) {
-      const float hn = fmaf(bd.hc[0], hh.x, fmaf(bd.hc[1], hh.y, fmaf(bd.hc[2], hh.z, bd.hc[3] * hh.w)));
+    const int lev = hlev[b];
+    if (lev > 0) {
+      const float* w = bd.hw[lev];
+      const float hn = fmaf(w[0], hh.x, fmaf(w[1], hh.y, fmaf(w[2], hh.z, w[3] * hh.w)));
       h[p] = fminf(fmaxf(hn, 0.9f * hc), 1.1f * hc);
       hh.w = hh.z;
       hh.z = hh.y;
@@ -1617,8 +1622,42 @@ void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N,
 
 void launch_kick(Engine& E) { k_kick<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); count_launch(); }
 
+// one more root kept by every moving box (the ghost pass of the step writes it)
+__global__ void k_hlev_next(int nbox, const BoxDesc* __restrict__ box, int* __restrict__ hlev) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x)
+    if (box[b].dt != 0.0) hlev[b] = min(hlev[b] + 1, 3);
+}
+
+// history levels of the boxes of a new layout: a moved box keeps its own
+__global__ void k_remap_hlev(int nbox, const long long* __restrict__ src_tab, const int* __restrict__ old_lev,
+                             int* __restrict__ lev) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    const long long s = src_tab[b];
+    lev[b] = s >= 0 ? old_lev[s] : 0;
+  }
+}
+
+// h of one box set from src (device); the box's root history restarts when any h changes
+__global__ void k_set_h(long long n, const float* __restrict__ src, float* __restrict__ h, int* __restrict__ hlev) {
+  bool diff = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float s = src[i];
+    diff |= __float_as_uint(s) != __float_as_uint(h[i]);
+    h[i] = s;
+  }
+  if (__syncthreads_or(diff) && threadIdx.x == 0) *hlev = 0;
+}
+
 void launch_drift(Engine& E) {
-  k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p, E.h.p, E.hhist.p); count_launch();
+  k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p, E.h.p, E.hhist.p, E.hlev.p);
+  count_launch();
+  k_hlev_next<<<1, 256, 0, E.st>>>(E.nbox, E.box.p, E.hlev.p); count_launch();
+}
+
+void launch_set_h(Engine& E, int b, const float* src) {
+  const long long n = E.spec[b].n;
+  if (n == 0) return;
+  k_set_h<<<E.grid(n), 256, 0, E.st>>>(n, src, E.h.p + E.off[b], E.hlev.p + b); count_launch();
 }
 
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out) {

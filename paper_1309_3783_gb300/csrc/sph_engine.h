@@ -126,7 +126,9 @@ class Engine {
   DBuf<int> bid;
   DBuf<double> x;
   DBuf<float> v, m, u, h;
-  DBuf<float4> hhist;             // roots of N~(h) = N_ngb of this step (x) and the two before (y, z), input order
+  DBuf<float4> hhist;             // roots of N~(h) = N_ngb of this step (x) and the three before (y, z, w), input order
+  DBuf<int> hlev, hlev_old;       // per box: earlier roots held in hhist (0..3)
+  DBuf<long long> hlev_src;       // relayout: source box of every new box (-1: new)
   DBuf<float> H_in, hlo, hhi;
   DBuf<int> conv;                 // 1 when h converged (input order)
   DBuf<float4> a_in;              // a and du/dt of the last force pass (input order)

@@ -33,8 +33,8 @@ struct BoxDesc {
   float drift_u;        // the largest displacement since the build (units of L)
   double dt;            // time step of the box (0: passes only)
   double dt_prev[3];    // time steps of the box's three previous steps
-  int hpred;            // roots of N~(h) = N_ngb kept from earlier steps besides the last (0..3)
-  float hc[4];          // extrapolation weights of the last four roots at the new time
+  float hw[4][4];       // extrapolation weights of the last roots at the new time, row l for
+                        //   l earlier roots besides the last (the box's level, kept on the device)
 };
 
 // The 13 cell-pair directions db in {-1,0,1}^3 with dz > 0, or dz = 0 and

@@ -53,8 +53,11 @@ def test_server_results_alone_and_in_the_mix(api):
     """Each served box ends in the state it reaches alone.
 
     Float atomics sum in a different order alone and in the mix, so h converged
-    to a tolerance tol may differ by up to ~tol between the two runs; a tight
-    tol (5e-6) makes both runs agree to rounding, and the bounds below follow.
+    to a tolerance tol may differ by up to ~tol between the two runs (a particle
+    whose extrapolated h lands at the tolerance's edge converges in the first pass
+    in one run and one Newton step later in the other); a tight tol (5e-6) keeps
+    both runs within the bounds below, and moves a neighbour across H for a
+    handful of particles at most.
     """
     p = api.sph_params_default()
     p.h_tol = 5e-6
@@ -81,7 +84,7 @@ def test_server_results_alone_and_in_the_mix(api):
             for k in ("x", "v", "u", "h", "rho", "a", "count"):
                 got = api.sph_server_get(srv, i, k, bx.n)
                 if k == "count":
-                    assert np.array_equal(got, ref[k])
+                    assert np.mean(got != ref[k]) < 2e-3
                 elif k == "x":
                     assert np.max(np.abs(_periodic_diff(got, ref[k], bx.L))) < 1e-9
                 else:
@@ -302,3 +305,41 @@ def test_merged_axis_sorts_equal_direct_sorts(api):
         assert s0[k] == s1[k], k
     assert np.array_equal(out[0]["count"], out[1]["count"])
     np.testing.assert_allclose(out[0]["rho"], out[1]["rho"], rtol=1e-6)
+
+
+def test_h_history_survives_a_round_trip_of_the_state(api):
+    """The h iteration of a step starts from the extrapolated roots of the earlier
+    steps.  Setting a box back to its own state (a host round trip) keeps that
+    history; setting other h values restarts it."""
+    box = inputs.plummer_box(n=32768, n_spheres=4, seed=9)
+    c = _ctx_with(api)
+    try:
+        b = api.box_from(c, box)
+        try:
+            b.h_update()
+            b.force()
+            dt = b.cfl_dt()
+            for _ in range(6):
+                b.step(dt)
+            kept = b.stats()["h_active_after_first"]
+            st = {k: b.get(k) for k in ("x", "v", "u", "h", "a", "dudt")}
+            b.set(st["x"], st["v"], box.m, st["u"], st["h"])
+            b.set_field("a", st["a"])
+            b.set_field("dudt", st["dudt"])
+            b.step(dt)
+            trip = b.stats()["h_active_after_first"]
+            st = {k: b.get(k) for k in ("x", "v", "u", "h", "a", "dudt")}
+            b.set(st["x"], st["v"], box.m, st["u"], (st["h"] * np.float32(1.01)).astype(np.float32))
+            b.set_field("a", st["a"])
+            b.set_field("dudt", st["dudt"])
+            b.step(dt)
+            fresh = b.stats()["h_active_after_first"]
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    print(f"first-pass unconverged: kept {kept}, after a round trip {trip}, after new h {fresh} of {box.n}")
+    # a few steps into the run (measured: 10 % kept, 11 % after the round trip, all
+    # particles after new h)
+    assert kept < 0.25 * box.n and trip < 1.5 * kept + 100
+    assert fresh > 0.9 * box.n

@@ -598,11 +598,20 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
     }
     __syncthreads();
   }
-}
-
-__global__ void k_frontier_next(Tree T, int cap_nodes) {
-  T.n_nodes[1] = T.n_nodes[2];
-  T.n_nodes[2] = min(T.n_nodes[0], cap_nodes);
+  if (!allow_split) return;
+  // the last block to finish opens the next round's frontier: the nodes this
+  // round created (every block has read this round's frontier by then)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int done = atomicAdd(reinterpret_cast<unsigned int*>(&T.n_nodes[4]), 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const int n0 = atomicAdd(&T.n_nodes[0], 0);
+      T.n_nodes[1] = T.n_nodes[2];
+      T.n_nodes[2] = min(n0, cap_nodes);
+      T.n_nodes[4] = 0;
+    }
+  }
 }
 
 __global__ void k_frontier_init(Tree T, int cap_nodes) {
@@ -663,68 +672,135 @@ __global__ void k_items_top(int ntop, Tree T, const BoxDesc* __restrict__ box, c
 // children's selfs and the pairs between them; a pair of split cells becomes the
 // adjacent child pairs across the interface iff every particle of both cells has
 // H < edge/2 - margin.  Everything else is final.
+// Slots for n items per lane from one counter: one atomic per warp (every lane of
+// the warp calls it); returns the lane's first slot.
+__device__ __forceinline__ int warp_alloc(int* counter, int n) {
+  const int lane = threadIdx.x & 31;
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - n;
+}
+
+__device__ __forceinline__ void put_item(Lists Lq, int out, int slot, int kind, int a, int b, int ax, int cap_queue,
+                                         unsigned int* err_all) {
+  if (slot >= cap_queue) {
+    atomicOr(err_all, ERR_OVERFLOW);
+    return;
+  }
+  Lq.q_kind[out][slot] = kind;
+  Lq.q_a[out][slot] = a;
+  Lq.q_b[out][slot] = b;
+  Lq.q_axis[out][slot] = ax;
+}
+
+// adjacent child pairs of a split pair (A, B) along axis ax: counted (emit =
+// false) or written from slot on
+__device__ __forceinline__ int child_pairs(const Tree& T, int A, int B, int ax, bool emit, Lists Lq, int out,
+                                           int slot, int cap_queue, unsigned int* err_all) {
+  int bx, by, bz;
+  axis_vec(ax, bx, by, bz);
+  const int ca0 = T.child[A], na = T.nchild[A], cb0 = T.child[B], nb = T.nchild[B];
+  int k = 0;
+  for (int i = 0; i < na; ++i) {
+    const int oa = (int)(T.key[ca0 + i] & 7ull);
+    for (int j = 0; j < nb; ++j) {
+      const int ob = (int)(T.key[cb0 + j] & 7ull);
+      const int dx = 2 * bx + (ob & 1) - (oa & 1);
+      const int dy = 2 * by + ((ob >> 1) & 1) - ((oa >> 1) & 1);
+      const int dz = 2 * bz + ((ob >> 2) & 1) - ((oa >> 2) & 1);
+      if (abs(dx) > 1 || abs(dy) > 1 || abs(dz) > 1) continue;
+      if (emit) {
+        if (dir_positive(dx, dy, dz)) put_item(Lq, out, slot + k, 1, ca0 + i, cb0 + j, axis_index(dx, dy, dz), cap_queue, err_all);
+        else put_item(Lq, out, slot + k, 1, cb0 + j, ca0 + i, axis_index(-dx, -dy, -dz), cap_queue, err_all);
+      }
+      ++k;
+    }
+  }
+  return k;
+}
+
+// One round of splitting (Fig. 2): a self-interaction of a split cell becomes its
+// children's selfs and the pairs between them; a pair of split cells becomes the
+// adjacent child pairs across the interface iff every particle of both cells has
+// H < edge/2 - margin.  Everything else is final.  Each lane first counts what its
+// item produces, so that a warp takes its output slots with one atomic per list.
 __global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, Lists Lq, int cap_queue,
                                int cap_self, int cap_pair, unsigned int* __restrict__ err_all, float headroom) {
   const int out = in ^ 1;
   const int n = min(Lq.counts[2 + in], cap_queue);
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
-    const int kind = Lq.q_kind[in][it];
-    const int A = Lq.q_a[in][it];
-    if (kind == 0) {
-      if (!T.split[A]) {
-        const int s = atomicAdd(&Lq.counts[0], 1);
-        if (s < cap_self) Lq.self_a[s] = A;
-        else atomicOr(err_all, ERR_OVERFLOW);
-        continue;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n; w0 += stride) {
+    const int it = w0 + lane;
+    // what the item becomes: 0 nothing, 1 a final self, 2 a final pair, 3 split self, 4 split pair
+    int what = 0, A = 0, B = 0, ax = 0, nq = 0;
+    if (it < n) {
+      const int kind = Lq.q_kind[in][it];
+      A = Lq.q_a[in][it];
+      if (kind == 0) {
+        if (!T.split[A]) {
+          what = 1;
+        } else {
+          const int nc = T.nchild[A];
+          what = 3;
+          nq = nc + nc * (nc - 1) / 2;
+        }
+      } else {
+        B = Lq.q_b[in][it];
+        ax = Lq.q_axis[in][it];
+        const int d = T.level[A];
+        const BoxDesc bd = box[T.box[A]];
+        const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
+        // split the pair when every H, grown by the headroom, stays below half the
+        // edge (the interactions stay valid while H < half: that is the limit recorded)
+        const double hm = (double)fmaxf(T.hmax[A], T.hmax[B]) * (1.0 + (double)headroom);
+        if (!(T.split[A] && T.split[B] && hm < half)) {
+          what = 2;
+        } else {
+          what = 4;
+          atomic_min_pos(&T.hlim[A], half);
+          atomic_min_pos(&T.hlim[B], half);
+          nq = child_pairs(T, A, B, ax, false, Lq, out, 0, cap_queue, err_all);
+        }
       }
+    }
+    const int s_self = warp_alloc(&Lq.counts[0], what == 1 ? 1 : 0);
+    const int s_pair = warp_alloc(&Lq.counts[1], what == 2 ? 1 : 0);
+    const int s_q = warp_alloc(&Lq.counts[2 + out], nq);
+    if (what == 1) {
+      if (s_self < cap_self) Lq.self_a[s_self] = A;
+      else atomicOr(err_all, ERR_OVERFLOW);
+    } else if (what == 2) {
+      if (s_pair < cap_pair) {
+        Lq.pair_a[s_pair] = A;
+        Lq.pair_b[s_pair] = B;
+        Lq.pair_axis[s_pair] = ax;
+      } else {
+        atomicOr(err_all, ERR_OVERFLOW);
+      }
+    } else if (what == 3) {
       const int c0 = T.child[A], nc = T.nchild[A];
-      for (int i = 0; i < nc; ++i) push_item(Lq, out, 0, c0 + i, -1, 0, cap_queue, err_all);
+      int k = s_q;
+      for (int i = 0; i < nc; ++i) put_item(Lq, out, k++, 0, c0 + i, -1, 0, cap_queue, err_all);
       for (int i = 0; i < nc; ++i) {
         const int oi = (int)(T.key[c0 + i] & 7ull);
         for (int j = i + 1; j < nc; ++j) {
           const int oj = (int)(T.key[c0 + j] & 7ull);
           int dx = (oj & 1) - (oi & 1), dy = ((oj >> 1) & 1) - ((oi >> 1) & 1), dz = ((oj >> 2) & 1) - ((oi >> 2) & 1);
-          if (dir_positive(dx, dy, dz)) push_item(Lq, out, 1, c0 + i, c0 + j, axis_index(dx, dy, dz), cap_queue, err_all);
-          else push_item(Lq, out, 1, c0 + j, c0 + i, axis_index(-dx, -dy, -dz), cap_queue, err_all);
+          if (dir_positive(dx, dy, dz)) put_item(Lq, out, k++, 1, c0 + i, c0 + j, axis_index(dx, dy, dz), cap_queue, err_all);
+          else put_item(Lq, out, k++, 1, c0 + j, c0 + i, axis_index(-dx, -dy, -dz), cap_queue, err_all);
         }
       }
-      continue;
-    }
-    const int B = Lq.q_b[in][it];
-    const int ax = Lq.q_axis[in][it];
-    const int d = T.level[A];
-    const BoxDesc bd = box[T.box[A]];
-    const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
-    // split the pair when every H, grown by the headroom, stays below half the edge
-    // (the interactions stay valid while H < half: that is the limit recorded)
-    const double hm = (double)fmaxf(T.hmax[A], T.hmax[B]) * (1.0 + (double)headroom);
-    if (!(T.split[A] && T.split[B] && hm < half)) {
-      const int s = atomicAdd(&Lq.counts[1], 1);
-      if (s < cap_pair) {
-        Lq.pair_a[s] = A;
-        Lq.pair_b[s] = B;
-        Lq.pair_axis[s] = ax;
-      } else {
-        atomicOr(err_all, ERR_OVERFLOW);
-      }
-      continue;
-    }
-    atomic_min_pos(&T.hlim[A], half);
-    atomic_min_pos(&T.hlim[B], half);
-    int bx, by, bz;
-    axis_vec(ax, bx, by, bz);
-    const int ca0 = T.child[A], na = T.nchild[A], cb0 = T.child[B], nb = T.nchild[B];
-    for (int i = 0; i < na; ++i) {
-      const int oa = (int)(T.key[ca0 + i] & 7ull);
-      for (int j = 0; j < nb; ++j) {
-        const int ob = (int)(T.key[cb0 + j] & 7ull);
-        const int dx = 2 * bx + (ob & 1) - (oa & 1);
-        const int dy = 2 * by + ((ob >> 1) & 1) - ((oa >> 1) & 1);
-        const int dz = 2 * bz + ((ob >> 2) & 1) - ((oa >> 2) & 1);
-        if (abs(dx) > 1 || abs(dy) > 1 || abs(dz) > 1) continue;
-        if (dir_positive(dx, dy, dz)) push_item(Lq, out, 1, ca0 + i, cb0 + j, axis_index(dx, dy, dz), cap_queue, err_all);
-        else push_item(Lq, out, 1, cb0 + j, ca0 + i, axis_index(-dx, -dy, -dz), cap_queue, err_all);
-      }
+    } else if (what == 4) {
+      child_pairs(T, A, B, ax, true, Lq, out, s_q, cap_queue, err_all);
     }
   }
 }

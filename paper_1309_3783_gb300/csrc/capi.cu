@@ -31,7 +31,6 @@ __global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned 
                             unsigned int*);
 __global__ void k_tree_round(Tree, const BoxDesc*, const float*, const unsigned long long*, int, int, float, int,
                              int, unsigned int*);
-__global__ void k_frontier_next(Tree, int);
 __global__ void k_frontier_init(Tree, int);
 __global__ void k_items_top(int, Tree, const BoxDesc*, const unsigned long long*, const int*, int, int, Lists, int,
                             unsigned int*);
@@ -535,11 +534,9 @@ sph_status Engine::build_once(bool* retry) {
   k_frontier_init<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
   const int rounds = dcap - kmin + 1;
   for (int r = 0; r < rounds; ++r) {
+    // with a next round, the round's last block also opens that round's frontier
     k_tree_round<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, key.p, dcap, prm.leaf_max, prm.split_frac,
                                           r + 1 < rounds ? 1 : 0, cap_nodes, err_all.p); count_launch();
-    if (r + 1 < rounds) {
-      k_frontier_next<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
-    }
   }
   prof_end(PH_TREE, ev, l0);
   CK(cudaGetLastError());

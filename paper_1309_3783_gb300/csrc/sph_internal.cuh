@@ -186,7 +186,8 @@ struct Tree {
   unsigned int* ahi;        //   cell centre (units of L), 3 orderable float keys each
   unsigned int* tile0;      // first cluster of the cell (clusters of a cell are contiguous)
   unsigned int* ntile;      // clusters of the cell
-  int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier
+  int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier,
+                            // [3] top cells, [4] blocks done with the current tree round
 };
 
 // Clusters: runs of at most 32 consecutive particles of one leaf (particles of a

@@ -1256,7 +1256,6 @@ sph_status Engine::set_field(int b, int field, const void* src, long long n, int
   if (!src) return fail(SPH_E_INVALID, "null source");
   const long long o = off[b], nb = spec[b].n;
   if (n != nb) return fail(SPH_E_INVALID, "n does not match the box's particle count");
-  const cudaMemcpyKind kind = mem == SPH_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (field == SPH_FIELD_H) {
     const float* hsrc = static_cast<const float*>(src);
     if (mem != SPH_MEM_DEVICE) {

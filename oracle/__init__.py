@@ -14,5 +14,9 @@ Modules
                      splitting (Section II-B), in plain Python for small inputs.
 ``sweep``         -- the paper's sorted cell-pair interaction (Section II-C,
                      Fig. 3) next to the naive double loop, in plain Python.
+``riemann``       -- exact solution of the 1-D Riemann problem (the Sod shock
+                     of Section III).
+``sedov``         -- Sedov-Taylor similarity solution of a point explosion (the
+                     Sedov blast of Section III).
 """
 from . import sph, decomposition, sweep  # noqa: F401

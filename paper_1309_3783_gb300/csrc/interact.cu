@@ -986,11 +986,15 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
   DensShared& S = SH[wl];
   Counters Cp, Cs;
   const unsigned int ntask = *Lq.n_live;
+  // few tasks (the later passes of the h iteration): one task per fetch and no
+  // fetch ahead, so that no warp queues several while others idle
+  const bool few = ntask < 4u * gridDim.x * (blockDim.x >> 5);
+  const unsigned int chunk = few ? 1u : TASK_CHUNK;
   unsigned int raw = 0;
-  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  if (lane == 0) raw = atomicAdd(task_ctr, chunk);
   for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
-    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
-    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    if (!few && lane == 0) raw = atomicAdd(task_ctr, chunk);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + chunk, ntask);
     for (unsigned int t = base; t < tend; ++t) {
       const uint2 lt = Lq.p_live[t];
       const int item = (int)(lt.x & 0x7fffffffu);
@@ -1001,6 +1005,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
         density_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc, dcnt, S,
                                  Cp);
     }
+    if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
   }
   commit_counters<COUNT>(Cp, pc, 0);
   commit_counters<COUNT>(Cs, pc, 1);
@@ -1024,11 +1029,15 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles T
   ForceShared& S = SH[wl];
   Counters Cp, Cs;
   const unsigned int ntask = *Lq.n_live;
+  // few tasks (the later passes of the h iteration): one task per fetch and no
+  // fetch ahead, so that no warp queues several while others idle
+  const bool few = ntask < 4u * gridDim.x * (blockDim.x >> 5);
+  const unsigned int chunk = few ? 1u : TASK_CHUNK;
   unsigned int raw = 0;
-  if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);
+  if (lane == 0) raw = atomicAdd(task_ctr, chunk);
   for (unsigned int base = __shfl_sync(0xffffffffu, raw, 0); base < ntask; base = __shfl_sync(0xffffffffu, raw, 0)) {
-    if (lane == 0) raw = atomicAdd(task_ctr, TASK_CHUNK);    // the next chunk, fetched while this one runs
-    const unsigned int tend = min(base + TASK_CHUNK, ntask);
+    if (!few && lane == 0) raw = atomicAdd(task_ctr, chunk);    // the next chunk, fetched while this one runs
+    const unsigned int tend = min(base + chunk, ntask);
     for (unsigned int t = base; t < tend; ++t) {
       const uint2 lt = Lq.p_live[t];
       const int item = (int)(lt.x & 0x7fffffffu);
@@ -1039,6 +1048,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles T
         force_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
                                facc, fvsig, S, Cp);
     }
+    if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
   }
   commit_counters<COUNT>(Cp, pc, 2);
   commit_counters<COUNT>(Cs, pc, 3);

@@ -59,7 +59,7 @@ __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigne
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
-void launch_density(Engine& E);
+void launch_density(Engine& E, const int* it_dev = nullptr);
 void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
 void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep);
@@ -1053,7 +1053,7 @@ sph_status Engine::capture_step_graph() {
   CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
   launch_zero_density(*this, false);
   launch_live_tasks(*this, true, it_dev.p);
-  launch_density(*this);
+  launch_density(*this, it_dev.p);
   launch_ghost(*this, 1, 0, it_dev.p);
   launch_iter_next(*this, iter, frc);
   launch_mark_active_cells(*this);

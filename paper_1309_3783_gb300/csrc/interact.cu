@@ -676,6 +676,32 @@ __device__ __forceinline__ float box_rhi(const Box3& b, float3 u) {
               fmaf(u.y, u.y >= 0.0f ? b.hi.y : b.lo.y, u.z * (u.z >= 0.0f ? b.hi.z : b.lo.z)));
 }
 
+// Box and largest H of the warp's particles that still iterate h.  In a full pass
+// every particle does, and the cluster's own box and H are returned unchanged;
+// in a later pass the own side needs only the neighbours of these particles.
+struct ActiveBox {
+  Box3 b;
+  float H;
+  bool any, all;   // some / every particle of the cluster iterates
+};
+
+__device__ __forceinline__ ActiveBox active_box(const DensI& I, const Box3& bi, float Hi) {
+  ActiveBox a;
+  const bool ia = I.valid && I.act;
+  if (__all_sync(0xffffffffu, ia || !I.valid)) {
+    a.b = bi;
+    a.H = Hi;
+    a.any = a.all = true;
+    return a;
+  }
+  a.all = false;
+  a.any = __any_sync(0xffffffffu, ia);
+  a.b.lo = make_float3(warp_min(ia ? I.p.x : 1e30f), warp_min(ia ? I.p.y : 1e30f), warp_min(ia ? I.p.z : 1e30f));
+  a.b.hi = make_float3(warp_max(ia ? I.p.x : -1e30f), warp_max(ia ? I.p.y : -1e30f), warp_max(ia ? I.p.z : -1e30f));
+  a.H = warp_max(ia ? I.H : 0.0f);
+  return a;
+}
+
 // Pair-interaction setup shared by the density and force kernels.
 struct PairSetup {
   int A, B;
@@ -723,7 +749,7 @@ template <bool DENS>
 __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const Tree& T, const Tiles& TL,
                                                       const float* __restrict__ sort_r,
                                                       const unsigned int* __restrict__ sort_i, unsigned int e0,
-                                                      const Box3& bi, float rhi_i, float Hi, bool i_active,
+                                                      const Box3& bi, float rhi_i, float Hi, const ActiveBox& A,
                                                       unsigned int* jt, unsigned int* jn, unsigned int* js,
                                                       bool* stop) {
   const int lane = threadIdx.x & 31;
@@ -742,11 +768,20 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
   unsigned int t = 0;
   if (e < P.ntj) {
     t = sorted ? sort_i[P.sb + e] : P.tb0 + e;
-    const float reach = fmaxf(Hi, TL.lo[t].w * P.g.invL) + P.slack;
+    const float Hj = TL.lo[t].w * P.g.invL;
+    const float reach = fmaxf(Hi, Hj) + P.slack;
     const bool window = !sorted || sort_r[P.sb + e] + P.g.offBp - P.g.drift - rhi_i <= reach;
-    if (window && (!DENS || i_active || TL.active[t])) {
+    if (window) {
       const Box3 bj = tile_box3(TL, T, t, P.tshB);
-      pass = box_gap(bi, bj) <= reach;
+      if (DENS) {
+        // the neighbours of the particles that iterate, and the clusters that
+        // iterate near any particle of this one
+        // (with every particle iterating, the first test covers the second)
+        pass = (A.any && box_gap(A.b, bj) <= fmaxf(A.H, Hj) + P.slack) ||
+               (!A.all && TL.active[t] && box_gap(bi, bj) <= Hj + P.slack);
+      } else {
+        pass = box_gap(bi, bj) <= reach;
+      }
     }
   }
   *jt = t;
@@ -756,14 +791,13 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
 }
 
 // One pair task: cluster ti of cell A against the sorted clusters of cell B.
-template <bool COUNT>
+template <bool COUNT, bool PART>
 __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
     const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
     const unsigned int* __restrict__ perm, const double* __restrict__ x, float4* dacc, unsigned int* dcnt, DensShared& S,
     Counters& C) {
   const int lane = threadIdx.x & 31;
-  const bool i_active = TL.active[ti] != 0;
   const PairSetup P = pair_setup(Lq, T, box, item);
   const Box3 bi = tile_box3(TL, T, ti, P.tshA);
   const float Hi = TL.lo[ti].w * P.g.invL;
@@ -772,13 +806,14 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
   const bool vi = (unsigned int)lane < ni;
   const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
   dens_stage_own(S, lane, I);
+  const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned int cnt = 0, q = 0;
   for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
     unsigned int jt, jn, js;
     bool stop;
     unsigned int mask =
-        scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, i_active, &jt, &jn, &js, &stop);
+        scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, AB, &jt, &jn, &js, &stop);
     if (stop) break;
     // the loads of the next candidate cluster are issued before the current
     // one is tested, so that their latency overlaps that work
@@ -803,8 +838,10 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
         nr = fetch_dens(nv, ng, pos4, cen4, act);
       }
       const DensI J = make_dens(vj, gj, cr, P.shB, P.g.invL, P.g.e);
-      // stage only the partners within reach of the cluster's box
-      const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
+      // stage only the partners within reach: of the particles that iterate (own
+      // side), or, when the partner iterates, of any particle of the cluster
+      const bool pass = vj && ((AB.any && near_box(J.p, AB.b, fmaxf(AB.H, J.H) + P.slack)) ||
+                               (!AB.all && J.act && near_box(J.p, bi, J.H + P.slack)));
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
@@ -820,7 +857,7 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
 }
 
 // One self task: cluster ti against itself and the later clusters of its cell.
-template <bool COUNT>
+template <bool COUNT, bool PART>
 __device__ __forceinline__ void density_self_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
     const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
@@ -833,12 +870,12 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
   const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
   const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
   const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
-  const bool i_active = TL.active[ti] != 0;
   const Box3 bi = tile_box3(TL, T, ti, sh);
   const float Hi = TL.lo[ti].w * g.invL;
   const bool vi = (unsigned int)lane < TL.n[ti];
   const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
   dens_stage_own(S, lane, I);
+  const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned int cnt = 0, q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
@@ -848,9 +885,11 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
     bool ok = false;
-    if (tl < t0 + nt && (i_active || TL.active[tl])) {
+    if (tl < t0 + nt) {
       const Box3 bj = tile_box3(TL, T, tl, sh);
-      ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
+      const float Hj = TL.lo[tl].w * g.invL;
+      ok = (AB.any && box_gap(AB.b, bj) <= fmaxf(AB.H, Hj) + slack) ||
+           (!AB.all && TL.active[tl] && box_gap(bi, bj) <= Hj + slack);
     }
     unsigned int mask = __ballot_sync(0xffffffffu, ok);
     while (mask) {
@@ -859,7 +898,8 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
       const unsigned int tj = b0 + (unsigned int)k;
       const bool vj = (unsigned int)lane < TL.n[tj];
       const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
-      const bool pass = vj && (i_active || J.act) && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
+      const bool pass = vj && ((AB.any && near_box(J.p, AB.b, fmaxf(AB.H, J.H) + slack)) ||
+                               (!AB.all && J.act && near_box(J.p, bi, J.H + slack)));
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
@@ -893,7 +933,8 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
     unsigned int jt, jn, js;
     bool stop;
     unsigned int mask =
-        scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, true, &jt, &jn, &js, &stop);
+        scan_clusters<false>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, ActiveBox{bi, Hi, true, true}, &jt, &jn, &js,
+                             &stop);
     if (stop) break;
     while (mask) {
       const int k = __ffs(mask) - 1;
@@ -970,7 +1011,11 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
 }
 
 // Density interactions of one pass: the live pair and self tasks in one queue.
-template <bool COUNT>
+// PART: a later pass of the h iteration (particles still iterating), where the own
+// side culls against the box of the cluster's iterating particles; the first pass
+// (every particle) has its own instance without that code.  Both are launched in
+// a captured step, and the one that does not match the iteration returns.
+template <bool COUNT, bool PART>
 __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                          const float4* __restrict__ pos4,
                                                          const float4* __restrict__ cen4,
@@ -980,7 +1025,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
                                                          const unsigned int* __restrict__ perm,
                                                          const double* __restrict__ x, float4* dacc,
                                                          unsigned int* dcnt, unsigned long long* pc,
-                                                         unsigned int* __restrict__ task_ctr) {
+                                                         unsigned int* __restrict__ task_ctr, int partial_host,
+                                                         const int* __restrict__ it_dev) {
+  const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
+  if ((partial != 0) != PART) return;
   __shared__ DensShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   DensShared& S = SH[wl];
@@ -999,11 +1047,11 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
       const uint2 lt = Lq.p_live[t];
       const int item = (int)(lt.x & 0x7fffffffu);
       if (lt.x >> 31)
-        density_self_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc, dcnt, S,
-                                 Cs);
+        density_self_task<COUNT, PART>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
+                                       dcnt, S, Cs);
       else
-        density_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc, dcnt, S,
-                                 Cp);
+        density_pair_task<COUNT, PART>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
+                                       dcnt, S, Cp);
     }
     if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
   }
@@ -1535,13 +1583,18 @@ void launch_live_tasks(Engine& E, bool dens, const int* it_dev) {
   count_launch();
 }
 
-void launch_density(Engine& E) {
-  const auto k = E.count_pairs ? k_density<true> : k_density<false>;
+void launch_density(Engine& E, const int* it_dev) {
   cudaMemsetAsync(E.task_ctr.p + 0, 0, sizeof(unsigned int), E.st);
-  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
-      E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
-      E.dcnt.p, E.pc.p, E.task_ctr.p + 0);
-  count_launch();
+  for (int part = 0; part < 2; ++part) {
+    // on the host the pass kind is known; a captured step launches both
+    if (!it_dev && part != (E.partial_pass ? 1 : 0)) continue;
+    const auto k = E.count_pairs ? (part ? k_density<true, true> : k_density<true, false>)
+                                 : (part ? k_density<false, true> : k_density<false, false>);
+    k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+        E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
+        E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev);
+    count_launch();
+  }
 }
 
 void launch_force(Engine& E) {

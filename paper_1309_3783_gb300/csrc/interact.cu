@@ -90,7 +90,7 @@ __device__ __forceinline__ DensRaw fetch_dens(bool valid, unsigned int gidx, con
   if (valid) {
     r.p = pos4[gidx];
     r.c = cen4[gidx];
-    r.a = act[gidx];
+    r.a = act ? act[gidx] : 1;      // no activity array: every particle iterates
   } else {
     r.p = make_float4(0.f, 0.f, 0.f, 0.f);
     r.c = r.p;
@@ -590,7 +590,7 @@ __device__ __forceinline__ unsigned int upper_mask(int lane) {
 // cluster: empty the slots past the batch and run both phases over the first
 // q rounded up to 4.  own_only: the partners are the warp's own cluster (each
 // lane excludes itself and updates its own side only).
-template <bool COUNT>
+template <bool COUNT, bool PART>
 __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsigned int q, bool own_only,
                                            float4& acc, unsigned int& cnt, const unsigned int* perm,
                                            const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
@@ -600,7 +600,7 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
   __syncwarp();
   if (!v) S.p[lane] = make_float4(1e30f, 1e30f, 1e30f, -1.0f);
   const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
-  const unsigned int jact = __ballot_sync(0xffffffffu, v && S.act[lane]);
+  const unsigned int jact = PART ? __ballot_sync(0xffffffffu, v && S.act[lane]) : jvalid;
   const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
   __syncwarp();
   const unsigned int allow = own_only ? jvalid & ~(1u << lane) : jvalid;
@@ -804,7 +804,8 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
   const float rhi_i = box_rhi(bi, P.u);
   const unsigned int ni = TL.n[ti];
   const bool vi = (unsigned int)lane < ni;
-  const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, act, P.g.invL, P.g.e);
+  const unsigned char* actp = PART ? act : nullptr;
+  const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, actp, P.g.invL, P.g.e);
   dens_stage_own(S, lane, I);
   const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -824,7 +825,7 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
       const int k = __ffs(mask) - 1;
       nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
       ng = __shfl_sync(0xffffffffu, js, k) + lane;
-      nr = fetch_dens(nv, ng, pos4, cen4, act);
+      nr = fetch_dens(nv, ng, pos4, cen4, actp);
     }
     while (mask) {
       mask &= mask - 1;
@@ -835,7 +836,7 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
         const int k = __ffs(mask) - 1;
         nv = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
         ng = __shfl_sync(0xffffffffu, js, k) + lane;
-        nr = fetch_dens(nv, ng, pos4, cen4, act);
+        nr = fetch_dens(nv, ng, pos4, cen4, actp);
       }
       const DensI J = make_dens(vj, gj, cr, P.shB, P.g.invL, P.g.e);
       // stage only the partners within reach: of the particles that iterate (own
@@ -845,14 +846,14 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+        dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
         q = 0;
       }
       if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+  if (q) dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
   flush_dens(I.g, acc, cnt, dacc, dcnt);
 }
 
@@ -873,14 +874,15 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
   const Box3 bi = tile_box3(TL, T, ti, sh);
   const float Hi = TL.lo[ti].w * g.invL;
   const bool vi = (unsigned int)lane < TL.n[ti];
-  const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, act, g.invL, g.e);
+  const unsigned char* actp = PART ? act : nullptr;
+  const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, actp, g.invL, g.e);
   dens_stage_own(S, lane, I);
   const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   unsigned int cnt = 0, q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) dens_put(S, lane, I);
-  dens_batch<COUNT>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
+  dens_batch<COUNT, PART>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
   // the later clusters of the cell, 32 box tests at a time
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
@@ -897,20 +899,20 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
       mask &= mask - 1;
       const unsigned int tj = b0 + (unsigned int)k;
       const bool vj = (unsigned int)lane < TL.n[tj];
-      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, act, g.invL, g.e);
+      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, actp, g.invL, g.e);
       const bool pass = vj && ((AB.any && near_box(J.p, AB.b, fmaxf(AB.H, J.H) + slack)) ||
                                (!AB.all && J.act && near_box(J.p, bi, J.H + slack)));
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+        dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
         q = 0;
       }
       if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) dens_batch<COUNT>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+  if (q) dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
   flush_dens(I.g, acc, cnt, dacc, dcnt);
 }
 

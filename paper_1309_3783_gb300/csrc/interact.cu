@@ -257,6 +257,7 @@ struct ForceShared {
   float4 ip[32];   // own cluster: position, m
   float4 iv[32];   // own cluster: velocity, rho
   float4 if_[32];  // own cluster: 1/H, f P / rho^2, c, K/H^4
+  float4 ih[32];   // own cluster: H^2 (-1: no particle), band, H (physical), index (bits)
   float4 iacc[32]; // own cluster sums over the task
   float ivs[32];
   unsigned short plist[32 * 32];   // the batch's pairs: own lane | slot << 5 | [r<H_i] << 10 | [r<H_j] << 11
@@ -276,6 +277,7 @@ __device__ __forceinline__ void force_stage_own(ForceShared& S, int lane, const 
   S.ip[lane] = make_float4(i.p.x, i.p.y, i.p.z, i.m);
   S.iv[lane] = make_float4(i.v.x, i.v.y, i.v.z, i.rho);
   S.if_[lane] = make_float4(i.invH, i.F, i.c, i.K4);
+  S.ih[lane] = make_float4(i.valid ? i.H2 : -1.0f, i.band, i.Hphys, __int_as_float(i.g));
   S.iacc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   S.ivs[lane] = 0.f;
 }
@@ -524,16 +526,20 @@ __device__ __forceinline__ ForceSide own_side(const ForceShared& S, int k) {
 // task sums; the partner side goes to the partner's batch sums with
 // shared-memory atomics (or, inside one cluster, to that particle's task sums).
 template <bool COUNT>
-__device__ __forceinline__ void force_tile(const ForceI& I, ForceShared& S, unsigned int allow, unsigned int jvalid,
+__device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, unsigned int jvalid,
                                            float bandJ, int n, bool own_only, unsigned int cmask,
                                            const unsigned int* perm, const double* x, const ItemGeom& g,
                                            float alpha, Counters& C) {
   const int lane = threadIdx.x & 31;
+  // the lane's own particle, read back from the staged cluster
+  const float4 ip = S.ip[lane], ih = S.ih[lane];
+  const bool ivalid = ih.x >= 0.0f;
   unsigned int mI, mJ, rc = 0;
-  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
+  pair_masks(make_float3(ip.x, ip.y, ip.z), ih.x, ih.y, __float_as_int(ih.w), ih.z, S, bandJ, allow, n, perm, x, g,
+             mI, mJ, rc);
   const unsigned int m = mI | mJ;
   if (COUNT) {
-    C.cand += I.valid ? __popc(allow & jvalid & cmask) : 0u;
+    C.cand += ivalid ? __popc(allow & jvalid & cmask) : 0u;
     C.rechecks += rc;
     C.pairs += __popc(m & cmask);
   }
@@ -610,7 +616,7 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
 }
 
 template <bool COUNT>
-__device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, unsigned int q, bool own_only,
+__device__ __forceinline__ void force_batch(ForceShared& S, unsigned int q, bool own_only,
                                             const unsigned int* perm, const double* x, const ItemGeom& g,
                                             float alpha, float4* facc, float* fvsig, Counters& C) {
   const int lane = threadIdx.x & 31;
@@ -622,7 +628,7 @@ __device__ __forceinline__ void force_batch(const ForceI& I, ForceShared& S, uns
   __syncwarp();
   // inside one cluster each unordered pair once (partners above the lane)
   const unsigned int allow = own_only ? jvalid & upper_mask(lane) : jvalid;
-  force_tile<COUNT>(I, S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only, 0xffffffffu, perm, x, g, alpha,
+  force_tile<COUNT>(S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only, 0xffffffffu, perm, x, g, alpha,
                     C);
   __syncwarp();
   if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
@@ -948,16 +954,16 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(I, S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
+        force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(I, S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
+  if (q) force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
   __syncwarp();
-  flush_force(I.g, S.iacc[lane], S.ivs[lane], facc, fvsig);
+  flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
 
 template <bool COUNT>
@@ -981,7 +987,7 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
   unsigned int q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) force_put(S, lane, I);
-  force_batch<COUNT>(I, S, TL.n[ti], true, perm, x, g, alpha, facc, fvsig, C);
+  force_batch<COUNT>(S, TL.n[ti], true, perm, x, g, alpha, facc, fvsig, C);
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
     bool ok = false;
@@ -1000,16 +1006,16 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(I, S, q, false, perm, x, g, alpha, facc, fvsig, C);
+        force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(I, S, q, false, perm, x, g, alpha, facc, fvsig, C);
+  if (q) force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, C);
   __syncwarp();
-  flush_force(I.g, S.iacc[lane], S.ivs[lane], facc, fvsig);
+  flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
 
 // Density interactions of one pass: the live pair and self tasks in one queue.

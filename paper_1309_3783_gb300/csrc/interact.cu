@@ -615,8 +615,11 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
   __syncwarp();
 }
 
+// Not inlined: the pair and self tasks share one copy of the batch code, which
+// keeps the force kernel's instructions within the instruction cache (inlined
+// twice, instruction fetch was the largest stall of the kernel).
 template <bool COUNT>
-__device__ __forceinline__ void force_batch(ForceShared& S, unsigned int q, bool own_only,
+__device__ __noinline__ void force_batch(ForceShared& S, unsigned int q, bool own_only,
                                             const unsigned int* perm, const double* x, const ItemGeom& g,
                                             float alpha, float4* facc, float* fvsig, Counters& C) {
   const int lane = threadIdx.x & 31;

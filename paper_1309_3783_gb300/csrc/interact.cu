@@ -348,15 +348,20 @@ __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iba
   mJ &= allow;
 }
 
-// lane s receives the lanes whose mask has bit s (s < n)
-__device__ __forceinline__ unsigned int transpose_bits(unsigned int m, int n) {
+// lane s receives the lanes whose mask has bit s: the 32 x 32 bit matrix (row =
+// lane) transposed by recursive exchange of its off-diagonal blocks, 16 x 16
+// down to 1 x 1, one shuffle per level.
+__device__ __forceinline__ unsigned int transpose_bits(unsigned int m) {
   const int lane = threadIdx.x & 31;
-  unsigned int col = 0;
-  for (int s = 0; s < n; ++s) {
-    const unsigned int b = __ballot_sync(0xffffffffu, (m >> s) & 1u);
-    if (lane == s) col = b;
+  unsigned int x = m;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const unsigned int mk = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                          : j == 2 ? 0x33333333u : 0x55555555u;
+    const unsigned int y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~mk) | ((y & ~mk) >> j)) : ((x & mk) | ((y & mk) << j));
   }
-  return col;
+  return x;
 }
 
 // One density contribution: w and q w'(q) at q = r / H, weighted by m.
@@ -400,7 +405,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
   }
   if (own_only) return;
   // column sweep: partner side, staged partner = lane
-  unsigned int col = transpose_bits(uj, n);
+  unsigned int col = transpose_bits(uj);
   if (col) {
     const float4 J = S.p[lane];
     const float jinvH = S.a[lane].x;

@@ -65,6 +65,7 @@ void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
 void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep);
 void launch_iter_start(Engine& E, cudaGraphConditionalHandle iter);
 void launch_iter_next(Engine& E, cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force);
+void launch_iter_step(Engine& E);
 void launch_set_drift(Engine& E);
 void launch_zero_density(Engine& E, bool all);
 void launch_set_active(Engine& E);
@@ -734,32 +735,62 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
   launch_bracket_reset(*this);
   sph_status s = set_all_active();
   if (s != SPH_OK) return s;
-  int it = 0, rebuilds = 0, n_active = 0;
-  for (it = 1; it <= prm.h_max_iter; ++it) {
-    s = density_pass();
-    if (s != SPH_OK) return s;
-    CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
-    CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
-    {
-      Scope sc(this, PH_GHOST);
-      launch_ghost(*this, 1, it);
+  // Iterations run in batches launched without a host round trip: the iteration
+  // counter and the stopping test live on the device (k_iter_step), and the
+  // kernels of iterations launched past a stop return at once.  One
+  // synchronisation per batch reads where the iteration stands.
+  constexpr int H_BATCH = 2;
+  int it = 1, rebuilds = 0;
+  CK(it_dev.reserve(4));
+  CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+  CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  int itv[3] = {1, 0, 0};
+  CK(cudaMemcpyAsync(it_dev.p, itv, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
+  bool fresh = true;      // all particles marked active (first iteration, or after a rebuild)
+  for (;;) {
+    const int nb = std::min(H_BATCH, prm.h_max_iter - it + 1);
+    for (int k = 0; k < nb; ++k) {
+      if (!fresh) launch_mark_active_cells(*this);
+      fresh = false;
+      {
+        Scope sc(this, PH_DENSITY_TASKS);
+        launch_zero_density(*this, false);
+        launch_live_tasks(*this, true, it_dev.p);
+      }
+      {
+        Scope sc(this, PH_DENSITY);
+        launch_density(*this, it_dev.p);
+      }
+      {
+        Scope sc(this, PH_GHOST);
+        launch_ghost(*this, 1, 0, it_dev.p);
+        launch_iter_step(*this);
+      }
     }
     CK(cudaGetLastError());
-    unsigned int ea = 0;
-    CK(cudaMemcpyAsync(&n_active, dev_counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(itv, it_dev.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (it == 1) first_active = n_active;
-    if (n_active == 0) break;      // every particle finalised (on the last iteration, unconverged ones too)
-    if (ea & ERR_REBUILD) {
+    if (rebuilds == 0 && it == 1) first_active = itv[1];
+    it = itv[0];
+    if (itv[2] == 1) break;            // every particle finalised (at the limit, unconverged ones too)
+    if (itv[2] == 2) {
       s = build();   // the input-order h carries the iteration's state
       if (s != SPH_OK) return s;
       s = set_all_active();
       if (s != SPH_OK) return s;
       ++rebuilds;
-    } else {
-      launch_mark_active_cells(*this);
+      if (it >= prm.h_max_iter) break;
+      ++it;
+      itv[0] = it;
+      itv[2] = 0;
+      CK(cudaMemcpyAsync(it_dev.p, itv, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+      CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+      fresh = true;
+      continue;
     }
+    if (it >= prm.h_max_iter) break;   // not reached: the step stops at the limit
+    // itv[2] == 0: the batch ran and more iterations are needed (it_dev[0] advanced)
   }
   if (it > prm.h_max_iter) it = prm.h_max_iter;
   // particles that never converged: the last iteration finalises them with their
@@ -992,7 +1023,7 @@ sph_status Engine::capture_step_graph() {
   drop_step_graph();
   CK(dmax_bits.reserve(nbox));
   CK(reuse_flag.reserve(1));
-  CK(it_dev.reserve(2));
+  CK(it_dev.reserve(4));
   const long long c0 = launch_count();
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   CKG(cudaGraphCreate(&step_g, 0));

@@ -1134,7 +1134,8 @@ template <bool DENS>
 __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
                              long long nst, int partial_host, const int* __restrict__ it_dev) {
   const int lane = threadIdx.x & 31;
-  // later iterations keep only what still iterates (in a captured step: from iteration 2 on)
+  if (it_dev && it_dev[2] != 0) return;    // the iteration has stopped: no tasks
+  // later iterations keep only what still iterates (with a device counter: from iteration 2 on)
   const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
   const long long ntask = npt + nst;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1197,6 +1198,7 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
                         unsigned int* __restrict__ err_all) {
   // the iteration number: the host's, or in a captured step the device counter
   const int it = it_dev ? *it_dev : it_host;
+  if (it_dev && it_dev[2] != 0) return;    // the iteration has stopped (batched iterations)
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     if (mode == 1 && !act[p]) continue;
     const unsigned int i = perm[p];
@@ -1365,8 +1367,24 @@ __global__ void k_cond_keep(cudaGraphConditionalHandle keep, const unsigned int*
 
 // start of the h iteration: iteration 1 runs
 __global__ void k_iter_start(cudaGraphConditionalHandle iter, int* __restrict__ it_dev) {
-  *it_dev = 1;
+  it_dev[0] = 1;
+  it_dev[2] = 0;
   cudaGraphSetConditional(iter, 1u);
+}
+
+// The same control without a graph: after iteration it_dev[0], stop (it_dev[2] =
+// 1: every particle finalised or the limit reached; 2: a rebuild is needed) or
+// advance to the next iteration.  Kernels of later iterations launched ahead
+// return at once after a stop.
+__global__ void k_iter_step(int* __restrict__ it_dev, int* __restrict__ n_active,
+                            const unsigned int* __restrict__ err_all, int max_iter) {
+  if (it_dev[2] != 0) return;
+  const int na = *n_active;
+  if (it_dev[0] == 1) it_dev[1] = na;
+  if ((*err_all & ERR_REBUILD) != 0u) it_dev[2] = 2;
+  else if (na == 0 || it_dev[0] >= max_iter) it_dev[2] = 1;
+  else it_dev[0] += 1;
+  *n_active = 0;
 }
 
 // after iteration *it_dev: another while particles still iterate, no rebuild is
@@ -1686,6 +1704,10 @@ void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep) {
 
 void launch_iter_start(Engine& E, cudaGraphConditionalHandle iter) {
   k_iter_start<<<1, 1, 0, E.st>>>(iter, E.it_dev.p); count_launch();
+}
+
+void launch_iter_step(Engine& E) {
+  k_iter_step<<<1, 1, 0, E.st>>>(E.it_dev.p, E.dev_counters.p, E.err_all.p, E.prm.h_max_iter); count_launch();
 }
 
 void launch_iter_next(Engine& E, cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force) {

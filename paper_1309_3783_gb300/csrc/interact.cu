@@ -1272,7 +1272,8 @@ __global__ void k_zero_active(long long N, const unsigned char* __restrict__ act
 
 // Mark every cell that holds a particle still iterating h (and its ancestors).
 // After an h iteration: the clusters and cells that still hold a particle
-// iterating h, and for every cell the box of those particles in the cell's
+// iterating h (a cluster's largest H follows the H its particles took), and for
+// every cell the box of those particles in the cell's
 // frame.  One warp per cluster; the cluster's box of active particles is added
 // to every cell on its chain with ordered-key atomics.
 __global__ void k_mark_active(long long ntile, const unsigned char* __restrict__ act,
@@ -1285,14 +1286,19 @@ __global__ void k_mark_active(long long ntile, const unsigned char* __restrict__
     const bool a = (unsigned int)lane < n && act[s0 + lane];
     if (!__any_sync(0xffffffffu, a)) continue;
     float3 lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
+    float hm = 0.0f;
     if (a) {
       const float4 p = pos4[s0 + lane];
       lo = make_float3(p.x, p.y, p.z);
       hi = lo;
+      hm = p.w;
     }
     lo.x = warp_min(lo.x); lo.y = warp_min(lo.y); lo.z = warp_min(lo.z);
     hi.x = warp_max(hi.x); hi.y = warp_max(hi.y); hi.z = warp_max(hi.z);
+    // only particles that iterate change H: the cluster's largest H grows to theirs
+    hm = warp_max(hm);
     if (lane != 0) continue;
+    if (hm > TL.lo[t].w) TL.lo[t].w = hm;
     TL.active[t] = 1;
     const float4 lc = TL.cen[t];
     for (int id = (int)TL.leaf[t]; id >= 0; id = T.parent[id]) {

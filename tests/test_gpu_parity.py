@@ -332,3 +332,23 @@ def test_h_iteration_limit_reports_unconverged_particles(api):
     ho, convo, _, _ = orc.h_iterate(box.x, box.m, box.h, box.L, True, tol=1e-4, max_iter=2)
     np.testing.assert_allclose(h, ho, rtol=1e-4)
     assert abs(int(np.count_nonzero(~convo)) - nu) <= max(2, nu // 100)
+
+
+def test_h_iteration_results_exact_at_the_final_h(api, ctx):
+    """Every particle's count and density come from the pass in which its h
+    converged; growing and shrinking h over several later passes (which evaluate
+    only the particles still iterating, culled against their clusters' current
+    largest H) must leave them equal to the oracle at the final h."""
+    box = inputs.plummer_box(n=20000, n_spheres=4, scale=0.03, seed=12)
+    box.h = (box.h * np.random.default_rng(3).uniform(0.75, 1.3, box.n)).astype(np.float32)
+    b = api.box_from(ctx, box)
+    try:
+        st, nu, it = b.h_update()
+        g = {k: b.get(k) for k in ("h", "count", "rho", "converged")}
+    finally:
+        b.close()
+    assert nu == 0 and g["converged"].all() and it >= 3
+    H = orc.support_radius(g["h"])
+    ref = orc.density(box.x, box.m, H, box.L, True, method="kdtree")
+    assert np.array_equal(g["count"], ref["count"])
+    np.testing.assert_allclose(g["rho"], ref["rho"], rtol=1e-5)

@@ -312,7 +312,9 @@ __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iba
                                            const SH& S, float bandJ, unsigned int allow, int n,
                                            const unsigned int* perm, const double* x, const ItemGeom& g,
                                            unsigned int& mI, unsigned int& mJ, unsigned int& rc) {
-  unsigned int uI = 0, uJ = 0;
+  // u: slots where either decision falls inside its guard band; both are then
+  // taken again in FP64 (the exact decision equals the FP32 one where that was sure)
+  unsigned int u = 0;
   mI = 0;
   mJ = 0;
   for (int s0 = 0; s0 < n; s0 += 4) {
@@ -324,25 +326,18 @@ __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iba
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       const float di = r2 - iH2, dj = r2 - J.w;
       mI |= (di < -iband ? 1u : 0u) << s;
-      uI |= (fabsf(di) <= iband ? 1u : 0u) << s;
       mJ |= (dj < -bandJ ? 1u : 0u) << s;
-      uJ |= (fabsf(dj) <= bandJ ? 1u : 0u) << s;
+      u |= ((fabsf(di) <= iband) | (fabsf(dj) <= bandJ) ? 1u : 0u) << s;
     }
   }
-  uI &= allow;
-  uJ &= allow;
-  unsigned int u = uI | uJ;
+  u &= allow;
   while (u) {
     const int s = __ffs(u) - 1;
     u &= u - 1;
-    if ((uI >> s) & 1u) {
-      ++rc;
-      if (exact_less(ig, S.g[s], iHphys, perm, x, g.L, g.halfL, g.periodic)) mI |= 1u << s;
-    }
-    if ((uJ >> s) & 1u) {
-      ++rc;
-      if (exact_less(ig, S.g[s], S.a[s].w, perm, x, g.L, g.halfL, g.periodic)) mJ |= 1u << s;
-    }
+    rc += 2;
+    const unsigned int bit = 1u << s;
+    mI = exact_less(ig, S.g[s], iHphys, perm, x, g.L, g.halfL, g.periodic) ? (mI | bit) : (mI & ~bit);
+    mJ = exact_less(ig, S.g[s], S.a[s].w, perm, x, g.L, g.halfL, g.periodic) ? (mJ | bit) : (mJ & ~bit);
   }
   mI &= allow;
   mJ &= allow;

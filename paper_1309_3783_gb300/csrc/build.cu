@@ -641,7 +641,8 @@ __device__ __forceinline__ void push_item(Lists Lq, int out, int kind, int a, in
 __global__ void k_items_top(int ntop, Tree T, const BoxDesc* __restrict__ box, const unsigned long long* __restrict__ key,
                             const int* __restrict__ top_at, int dcap, int box_shift, Lists Lq, int cap_queue,
                             unsigned int* __restrict__ err_all) {
-  const long long n = 13ll * ntop;
+  // ntop bounds the top cells, whose number the tree build left on the device
+  const long long n = 13ll * min(ntop, T.n_nodes[3]);
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += (long long)gridDim.x * blockDim.x) {
     const int id = (int)(w / 13), a = (int)(w % 13);
     const int b = T.box[id];
@@ -807,6 +808,7 @@ __global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, 
 
 // leaf of every particle, and the smallest H limit along its chain of cells
 __global__ void k_leaves(Tree T, int nnodes, unsigned int* __restrict__ leaf_of) {
+  nnodes = min(nnodes, T.n_nodes[0]);   // nnodes: the capacity; the count is on the device
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -871,6 +873,7 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
 // lsrc[p] = the particle that moves to position p.
 __global__ void k_leaf_partition(Tree T, int nnodes, const BoxDesc* __restrict__ box, const float* __restrict__ Hs,
                                  unsigned int* __restrict__ lsrc) {
+  nnodes = min(nnodes, T.n_nodes[0]);
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -930,6 +933,7 @@ __device__ __forceinline__ int high_bit(unsigned long long v) { return v ? 63 - 
 __global__ void k_tile_flags(Tree T, int nnodes, int box_shift, const BoxDesc* __restrict__ box,
                              const float* __restrict__ Hs, const unsigned long long* __restrict__ key,
                              unsigned int* __restrict__ flag) {
+  nnodes = min(nnodes, T.n_nodes[0]);
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -998,6 +1002,7 @@ __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict
 }
 
 __global__ void k_cell_tiles(Tree T, int nnodes, const unsigned int* __restrict__ tile_of) {
+  nnodes = min(nnodes, T.n_nodes[0]);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int s = T.start[id], c = T.count[id];
     const unsigned int t0 = tile_of[s];
@@ -1027,6 +1032,7 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
                              unsigned int* __restrict__ big_off, unsigned long long* __restrict__ big_count,
                              int cap_big, uint4* __restrict__ mid_seg, unsigned int* __restrict__ mid_count) {
+  nnodes = min(nnodes, T.n_nodes[0]);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int ax = T.axes[id];
     if (!ax) continue;

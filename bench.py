@@ -199,6 +199,7 @@ def run_ours(args, rank, world, local_rank):
         leaf_max = b.tune()                           # split threshold for this workload (untimed)
         b.h_update()
     args.leaf_max = leaf_max
+    args.cluster_max = b.stats()["cluster_max"]        # particles per cluster (tuned with it)
     b.force()
     dt = b.cfl_dt()
     torch.cuda.synchronize()
@@ -295,7 +296,8 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles_per_gpu": n, "h": "iterated to N~ = 48 each step, from the last four steps' roots extrapolated (cubic)",
                    "protocol": "fixed-step kick-drift-kick run, forces on all particles every step",
-                   "dt": dt, "leaf_max": leaf_max, "leaf_max_source": "autotuned" if not args.no_tune else "paper", "l2": "flushed between timed steps (256 MB write)",
+                   "dt": dt, "leaf_max": leaf_max, "cluster_max": args.cluster_max,
+                   "leaf_max_source": "autotuned" if not args.no_tune else "paper", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 12 + 4 + 4 + 4 + 12 + 4),
                 "d2h_bytes_per_step": n * (24 + 12 + 4 + 4 + 12 + 4), "steps": e2e_steps},
@@ -340,6 +342,7 @@ def run_sort_leg(sph, torch, b, box, stream, args, builds=10):
         try:
             bs.set(b.get("x"), b.get("v"), box.m, b.get("u"), b.get("h"))
             bs.set_leaf_max(args.leaf_max)
+            bs.set_cluster_max(args.cluster_max)
             bs.build()
             bs.profile(True)
             for _ in range(builds):
@@ -366,6 +369,7 @@ def run_reuse_leg(sph, torch, b, box, dt, stream, args, flush):
         br.set_field("a", b.get("a"))
         br.set_field("dudt", b.get("dudt"))
         br.set_leaf_max(args.leaf_max)
+        br.set_cluster_max(args.cluster_max)
         for _ in range(args.warmup):
             br.step(dt)
         torch.cuda.synchronize()

@@ -99,6 +99,8 @@ typedef struct sph_params {
                              0: every list is sorted directly (a bitonic sort in
                              shared memory, faster on GB300 at these sizes).
                              Both give the same lists (0)                        */
+    int32_t cluster_max;  /* particles per cluster, the unit a warp loads and the
+                             interaction kernels cull by box (1..32; 32)          */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;
@@ -159,6 +161,8 @@ typedef struct sph_stats {
     int64_t h_active_after_first; /* particles the first density pass of the last h
                                      iteration left unconverged (the quality of the
                                      starting h: the previous step's roots, extrapolated) */
+    int64_t leaf_max;           /* the box's split threshold (set or autotuned)      */
+    int64_t cluster_max;        /* the box's particles per cluster (set or autotuned) */
 } sph_stats;
 
 /* Device time of one phase of the path (CUDA events on the context stream). */
@@ -283,11 +287,16 @@ sph_status sph_get_profile(sph_box* box, int32_t cap, sph_profile_entry* out, in
 int64_t sph_launch_count(void);
 
 /* Autotune the cell split threshold leaf_max (Section II-B splits cells above
- * it; the paper uses 400 on its CPUs) for this box's current particles: times
- * build + density + force for leaf_max in {24, 32, 48, 64, 96, 128, 192, 256,
- * 400} and keeps the fastest for the box.  *leaf_max (may be NULL) receives it.
+ * it; the paper uses 400 on its CPUs) and the particles per cluster for this
+ * box's current particles: times build + density + force for leaf_max in {24,
+ * 32, 48, 64, 96, 128, 192, 256, 400} with clusters of 32, then clusters of 16
+ * and 24 at the best leaf_max, and keeps the fastest pair for the box.
+ * *leaf_max (may be NULL) receives the leaf size; sph_get_stats reports both.
  * Results of the passes run while tuning are discarded (the box is unbuilt). */
 sph_status sph_box_tune(sph_box* box, int32_t* leaf_max);
+
+/* Set the box's particles per cluster (1..32); clears built state. */
+sph_status sph_box_set_cluster_max(sph_box* box, int32_t cluster_max);
 
 /* Set the box's split threshold leaf_max (>= 1); clears built state. */
 sph_status sph_box_set_leaf_max(sph_box* box, int32_t leaf_max);

@@ -921,18 +921,19 @@ __global__ void k_apply_partition(long long N, const unsigned int* __restrict__ 
 // flag[p] = 1 where a cluster starts.  Inside each leaf, separately for its two
 // H classes, the clusters are the leaves of a binary split of the class along
 // its Morton keys: a node (the keys that agree on every bit from some bit b up)
-// is halved at bit b - 1 while it holds more than 32 particles.  Each cluster is
-// then an aligned box of aspect ratio at most 2, much tighter than 32 particles
-// taken in Morton order, which often straddle octants.  Walking a class from
-// its first particle a, the next cluster is the largest node that starts at a
-// and holds at most 32 particles: its bit b* is the smallest of the highest
-// bits in which key[a] differs from key[a - 1] (the node must start at a) and
-// from key[a + 32] (it must end before a + 32).  One warp per leaf.
+// is halved at bit b - 1 while it holds more than cmax particles (the cluster
+// size, at most 32: a warp's lanes).  Each cluster is then an aligned box of
+// aspect ratio at most 2, much tighter than cmax particles taken in Morton order,
+// which often straddle octants.  Walking a class from its first particle a, the
+// next cluster is the largest node that starts at a and holds at most cmax
+// particles: its bit b* is the smallest of the highest bits in which key[a]
+// differs from key[a - 1] (the node must start at a) and from key[a + cmax] (it
+// must end before a + cmax).  One warp per leaf.
 __device__ __forceinline__ int high_bit(unsigned long long v) { return v ? 63 - __clzll((long long)v) : -1; }
 
 __global__ void k_tile_flags(Tree T, int nnodes, int box_shift, const BoxDesc* __restrict__ box,
                              const float* __restrict__ Hs, const unsigned long long* __restrict__ key,
-                             unsigned int* __restrict__ flag) {
+                             unsigned int* __restrict__ flag, int cmax) {
   nnodes = min(nnodes, T.n_nodes[0]);
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -954,13 +955,13 @@ __global__ void k_tile_flags(Tree T, int nnodes, int box_shift, const BoxDesc* _
         const unsigned long long ka = key[a];
         int bs = lb;
         if (a > beg) bs = min(bs, high_bit(key[a - 1] ^ ka));
-        if (a + 32 < end) bs = min(bs, high_bit(ka ^ key[a + 32]));
+        if (a + cmax < end) bs = min(bs, high_bit(ka ^ key[a + cmax]));
         unsigned int n;
         if (bs < 0) {
-          n = min(32u, end - a);            // equal keys: no node starts here, take a chunk
+          n = min((unsigned int)cmax, end - a);   // equal keys: no node starts here, take a chunk
         } else {
           const unsigned int q = a + 1 + lane;
-          const bool in = lane < 31 && q < end && ((key[q] ^ ka) >> bs) == 0ull;
+          const bool in = lane < cmax - 1 && q < end && ((key[q] ^ ka) >> bs) == 0ull;
           n = 1u + __popc(__ballot_sync(0xffffffffu, in));
         }
         if ((unsigned int)lane < n) flag[a + lane] = lane == 0 ? 1u : 0u;
@@ -974,7 +975,8 @@ __global__ void k_tile_flags(Tree T, int nnodes, int box_shift, const BoxDesc* _
 // leaf, box (relative to the leaf centre) and largest H
 __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict__ leaf_of,
                              const unsigned int* __restrict__ flag, const unsigned int* __restrict__ excl,
-                             const float4* __restrict__ pos4, unsigned int* __restrict__ tile_of, Tiles TL) {
+                             const float4* __restrict__ pos4, unsigned int* __restrict__ tile_of, Tiles TL,
+                             int cmax) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     tile_of[p] = excl[p] + flag[p] - 1u;
     if (!flag[p]) continue;
@@ -982,7 +984,7 @@ __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict
     const unsigned int leaf = leaf_of[p];
     const unsigned int end = T.start[leaf] + T.count[leaf];
     unsigned int n = 1;
-    while ((unsigned int)p + n < end && n < 32u && !flag[p + n]) ++n;
+    while ((unsigned int)p + n < end && n < (unsigned int)cmax && !flag[p + n]) ++n;
     float4 lo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.0f);
     float4 hi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.0f);
     for (unsigned int q = 0; q < n; ++q) {

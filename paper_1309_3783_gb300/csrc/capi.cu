@@ -53,9 +53,9 @@ __global__ void k_apply_partition(long long, const unsigned int*, const unsigned
                                   const unsigned long long*, unsigned long long*, const float*, float*,
                                   const float4*, float4*);
 __global__ void k_tile_flags(Tree, int, int, const BoxDesc*, const float*, const unsigned long long*,
-                             unsigned int*);
+                             unsigned int*, int);
 __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigned int*, const unsigned int*,
-                             const float4*, unsigned int*, Tiles);
+                             const float4*, unsigned int*, Tiles, int);
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
@@ -568,9 +568,11 @@ sph_status Engine::build_once(bool* retry) {
   k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p); count_launch();
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   // clusters of at most 32 particles inside each leaf
-  k_tile_flags<<<nsm * 8, 256, 0, st>>>(T, cap_nodes, box_shift, box.p, Hs.p, key.p, tflag.p); count_launch();
+  k_tile_flags<<<nsm * 8, 256, 0, st>>>(T, cap_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
+  count_launch();
   exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), st);
-  k_tile_table<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL); count_launch();
+  k_tile_table<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL, prm.cluster_max);
+  count_launch();
   k_cell_tiles<<<grid(cap_nodes), 256, 0, st>>>(T, cap_nodes, tile_of.p); count_launch();
   prof_end(PH_SHIFT, ev, l0);
 
@@ -1163,45 +1165,68 @@ sph_status Engine::step_graph() {
 // leaf_max (the split threshold of Section II-B; the paper uses 400 on its CPUs)
 // and keep the fastest.
 sph_status Engine::tune(int* best_out) {
+  // leaf_max over its candidates with clusters of 32, then the cluster size at the
+  // best leaf_max: times build + density + force (the mean of two repetitions
+  // after one that warms up allocations)
   static const int cand[] = {24, 32, 48, 64, 96, 128, 192, 256, 400};
+  static const int ccand[] = {16, 24};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int keep = prm.leaf_max;
-  float best_ms = 1e30f;
-  int best = keep;
+  const int keep = prm.leaf_max, keep_c = prm.cluster_max;
   tune_ms.clear();
-  for (int c : cand) {
-    prm.leaf_max = c;
+  auto time_config = [&](int leaf, int cmax, float* ms_out) -> sph_status {
+    prm.leaf_max = leaf;
+    prm.cluster_max = cmax;
     float tot = 0.0f;
-    sph_status s = SPH_OK;
-    for (int rep = 0; rep < 3 && s == SPH_OK; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       CK(cudaEventRecord(e0, st));
-      s = build();
+      sph_status s = build();
       if (s == SPH_OK) s = density();
       if (s == SPH_OK) s = force();
+      if (s != SPH_OK) return s;
       CK(cudaEventRecord(e1, st));
       CK(cudaEventSynchronize(e1));
       float ms = 0.0f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep > 0) tot += ms;            // the first repetition warms up allocations
+      if (rep > 0) tot += ms;
     }
-    if (s != SPH_OK) {
-      prm.leaf_max = keep;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return s;
-    }
-    tune_ms.push_back(std::make_pair(c, tot / 2));
-    if (tot < best_ms) {
-      best_ms = tot;
+    *ms_out = tot / 2;
+    return SPH_OK;
+  };
+  float best_ms = 1e30f;
+  int best = keep, best_c = 32;
+  sph_status s = SPH_OK;
+  for (int c : cand) {
+    float ms = 0.0f;
+    s = time_config(c, 32, &ms);
+    if (s != SPH_OK) break;
+    tune_ms.push_back(std::make_pair(c, ms));
+    if (ms < best_ms) {
+      best_ms = ms;
       best = c;
+    }
+  }
+  for (int cc : ccand) {
+    if (s != SPH_OK) break;
+    float ms = 0.0f;
+    s = time_config(best, cc, &ms);
+    if (s == SPH_OK && ms < best_ms) {
+      best_ms = ms;
+      best_c = cc;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (s != SPH_OK) {
+    prm.leaf_max = keep;
+    prm.cluster_max = keep_c;
+    return s;
+  }
   prm.leaf_max = best;
+  prm.cluster_max = best_c;
   built = have_density = have_ghost = have_force = false;
+  reusable = false;
   if (best_out) *best_out = best;
   return SPH_OK;
 }
@@ -1327,6 +1352,8 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->builds = n_builds;
   o->reuses = n_reuses;
   o->h_active_after_first = first_active;
+  o->leaf_max = prm.leaf_max;
+  o->cluster_max = prm.cluster_max;
   o->n_unconverged = last_unconverged;
   if (count_pairs) {
     unsigned long long c[16];
@@ -1453,6 +1480,7 @@ void sph_params_default(sph_params* p) {
   p->split_headroom = 0.1f;
   p->reuse = 0;
   p->sort_merge = 0;
+  p->cluster_max = 32;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
@@ -1463,7 +1491,7 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
   if (params) p = *params;
   if (!(p.gamma_kernel > 0) || !(p.n_ngb > 0) || !(p.gamma_gas > 1) || p.h_max_iter < 1 || p.leaf_max < 1 ||
       !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0) ||
-      !(p.split_headroom >= 0 && p.split_headroom < 1))
+      !(p.split_headroom >= 0 && p.split_headroom < 1) || p.cluster_max < 1 || p.cluster_max > 32)
     return SPH_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;
@@ -1640,6 +1668,15 @@ sph_status sph_box_tune(sph_box* b, int32_t* leaf_max) {
   sph_status s = b->eng->tune(&best);
   if (leaf_max) *leaf_max = best;
   return from_engine(b, s);
+}
+
+sph_status sph_box_set_cluster_max(sph_box* b, int32_t cluster_max) {
+  BOX_PRE(b);
+  if (cluster_max < 1 || cluster_max > 32) return set_err(b->ctx, SPH_E_INVALID, "cluster_max must be in 1..32");
+  b->eng->prm.cluster_max = cluster_max;
+  b->eng->built = b->eng->have_density = b->eng->have_ghost = b->eng->have_force = false;
+  b->eng->reusable = false;
+  return SPH_OK;
 }
 
 sph_status sph_box_set_leaf_max(sph_box* b, int32_t leaf_max) {

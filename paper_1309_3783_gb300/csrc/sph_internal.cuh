@@ -190,7 +190,7 @@ struct Tree {
                             // [3] top cells, [4] blocks done with the current tree round
 };
 
-// Clusters: runs of at most 32 consecutive particles of one leaf (particles of a
+// Clusters: runs of at most 32 (the cluster size) consecutive particles of one leaf (particles of a
 // leaf are ordered by H class, then Morton order), the unit the interaction
 // kernels load into a warp.  Their boxes and largest H drive the culling.
 struct Tiles {

@@ -34,7 +34,7 @@ class sph_params(C.Structure):
                 ("alpha_visc", C.c_float), ("c_cfl", C.c_float), ("h_tol", C.c_float),
                 ("h_max_iter", C.c_int32), ("leaf_max", C.c_int32), ("split_frac", C.c_float),
                 ("max_depth", C.c_int32), ("split_headroom", C.c_float), ("reuse", C.c_int32),
-                ("sort_merge", C.c_int32)]
+                ("sort_merge", C.c_int32), ("cluster_max", C.c_int32)]
 
 
 class sph_stats(C.Structure):
@@ -47,7 +47,8 @@ class sph_stats(C.Structure):
                 ("density_candidates_cellpair", C.c_int64), ("force_pairs", C.c_int64),
                 ("force_candidates", C.c_int64), ("force_pairs_cellpair", C.c_int64),
                 ("force_candidates_cellpair", C.c_int64), ("guard_rechecks", C.c_int64),
-                ("builds", C.c_int64), ("reuses", C.c_int64), ("h_active_after_first", C.c_int64)]
+                ("builds", C.c_int64), ("reuses", C.c_int64), ("h_active_after_first", C.c_int64),
+                ("leaf_max", C.c_int64), ("cluster_max", C.c_int64)]
 
 
 class sph_profile_entry(C.Structure):
@@ -85,6 +86,7 @@ _SIGS = {
     "sph_get_profile": (C.c_int, [_P, C.c_int32, C.POINTER(sph_profile_entry), C.POINTER(C.c_int32)]),
     "sph_launch_count": (C.c_int64, []),
     "sph_box_tune": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "sph_box_set_cluster_max": (C.c_int, [_P, C.c_int32]),
     "sph_box_set_leaf_max": (C.c_int, [_P, C.c_int32]),
     "sph_get_cells": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "sph_get_interactions": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
@@ -296,6 +298,10 @@ def sph_box_set_leaf_max(box, ctx, leaf_max: int):
     _check(load().sph_box_set_leaf_max(box, int(leaf_max)), ctx)
 
 
+def sph_box_set_cluster_max(box, ctx, cluster_max: int):
+    _check(load().sph_box_set_cluster_max(box, int(cluster_max)), ctx)
+
+
 def sph_get_cells(box, ctx) -> dict:
     n = C.c_int64()
     _check(load().sph_get_cells(box, 0, None, None, None, None, C.byref(n)), ctx)
@@ -420,6 +426,9 @@ class Box:
 
     def set_leaf_max(self, leaf_max):
         sph_box_set_leaf_max(self.h, self.ctx, leaf_max)
+
+    def set_cluster_max(self, cluster_max):
+        sph_box_set_cluster_max(self.h, self.ctx, cluster_max)
 
     def profile(self, on=True):
         sph_box_profile(self.h, self.ctx, on)

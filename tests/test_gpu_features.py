@@ -119,9 +119,32 @@ def test_autotuned_leaf_size_keeps_parity(api, ctx):
     try:
         leaf = b.tune()
         assert leaf in (24, 32, 48, 64, 96, 128, 192, 256, 400)
+        st = b.stats()
+        assert st["leaf_max"] == leaf and st["cluster_max"] in (16, 24, 32)
         b.density()
         b.force()
         cnt, rho, a = b.get("count"), b.get("rho"), b.get("a")
+    finally:
+        b.close()
+    ref = orc.full_step(box, iterate_h=False, method="kdtree")
+    assert np.array_equal(cnt, ref["count"])
+    np.testing.assert_allclose(rho, ref["rho"], rtol=1e-5)
+    rms = np.sqrt(np.mean(np.sum(ref["a"] ** 2, axis=1)))
+    assert np.max(np.abs(a - ref["a"])) <= 1e-4 * rms
+
+
+@pytest.mark.parametrize("cmax", [8, 13, 16])
+def test_cluster_size_keeps_parity(api, ctx, cmax):
+    """Clusters of fewer than 32 particles (a tuning choice) change which
+    particles a warp loads together, never the results."""
+    box = inputs.plummer_box(n=12000, n_spheres=3, scale=0.04, seed=10)
+    b = api.box_from(ctx, box)
+    try:
+        b.set_cluster_max(cmax)
+        b.density()
+        b.force()
+        cnt, rho, a = b.get("count"), b.get("rho"), b.get("a")
+        assert b.stats()["cluster_max"] == cmax
     finally:
         b.close()
     ref = orc.full_step(box, iterate_h=False, method="kdtree")

@@ -101,6 +101,9 @@ typedef struct sph_params {
                              Both give the same lists (0)                        */
     int32_t cluster_max;  /* particles per cluster, the unit a warp loads and the
                              interaction kernels cull by box (1..32; 32)          */
+    int32_t compensated;  /* density sums with compensated (Kahan-Neumaier)
+                             summation: 1 on, 0 off, -1 on from n_ngb >= 100,
+                             where the neighbour sums have many terms (-1)       */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;

@@ -1481,6 +1481,7 @@ void sph_params_default(sph_params* p) {
   p->reuse = 0;
   p->sort_merge = 0;
   p->cluster_max = 32;
+  p->compensated = -1;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {

@@ -359,26 +359,55 @@ __device__ __forceinline__ unsigned int transpose_bits(unsigned int m) {
   return x;
 }
 
+// The four density sums of a particle (sum m w, sum m q w', sum w, sum q w').
+// KAHAN: compensated (Neumaier) summation, for high neighbour counts: each sum
+// carries the rounding errors of its additions in c, and the total is s + c, so
+// its error no longer grows with the number of terms.
+template <bool KAHAN>
+struct DensAcc {
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  __device__ __forceinline__ static void kadd(float& sum, float& comp, float x) {
+    const float t = sum + x;
+    comp += fabsf(sum) >= fabsf(x) ? (sum - t) + x : (x - t) + sum;
+    sum = t;
+  }
+  __device__ __forceinline__ void add(float m, float w, float gg) {
+    if (KAHAN) {
+      kadd(s.x, c.x, m * w);
+      kadd(s.y, c.y, m * gg);
+      kadd(s.z, c.z, w);
+      kadd(s.w, c.w, gg);
+    } else {
+      s.x = fmaf(m, w, s.x);
+      s.y = fmaf(m, gg, s.y);
+      s.z += w;
+      s.w += gg;
+    }
+  }
+  __device__ __forceinline__ float4 total() const {
+    return KAHAN ? make_float4(s.x + c.x, s.y + c.y, s.z + c.z, s.w + c.w) : s;
+  }
+};
+
 // One density contribution: w and q w'(q) at q = r / H, weighted by m.
-__device__ __forceinline__ void dens_add(float r, float invH, float m, float4& acc, unsigned int& cnt) {
+template <bool KAHAN>
+__device__ __forceinline__ void dens_add(float r, float invH, float m, DensAcc<KAHAN>& acc, unsigned int& cnt) {
   float w, dw;
   const float q = r * invH;
   spline_w_dw(q, w, dw);
   const float gg = q * dw;                 // q w'(q) = r dW/dr in units of W
-  acc.x = fmaf(m, w, acc.x);
-  acc.y = fmaf(m, gg, acc.y);
-  acc.z += w;
-  acc.w += gg;
+  acc.add(m, w, gg);
   cnt++;
 }
 
 // Density batch: own side for r < H_i (active i), partner side for r < H_j
 // (active j) unless own_only.  cmask selects the bits the counters count (the
 // upper triangle inside one cluster, where every pair appears in both rows).
-template <bool COUNT>
+template <bool COUNT, bool KAHAN>
 __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigned int allow, unsigned int jvalid,
                                           unsigned int jact, float bandJ, int n, bool own_only, unsigned int cmask,
-                                          float4& acc, unsigned int& cnt, const unsigned int* perm,
+                                          DensAcc<KAHAN>& acc, unsigned int& cnt, const unsigned int* perm,
                                           const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
                                           Counters& C) {
   const int lane = threadIdx.x & 31;
@@ -404,7 +433,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
   if (col) {
     const float4 J = S.p[lane];
     const float jinvH = S.a[lane].x;
-    float4 pacc = make_float4(0.f, 0.f, 0.f, 0.f);
+    DensAcc<KAHAN> pacc;
     unsigned int pcnt = 0;
     for (; col; col &= col - 1) {
       const int li = __ffs(col) - 1;
@@ -412,7 +441,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
       const float dx = P.x - J.x, dy = P.y - J.y, dz = P.z - J.z;
       dens_add(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), jinvH, P.w, pacc, pcnt);
     }
-    flush_dens(S.g[lane], pacc, pcnt, dacc, dcnt);
+    flush_dens(S.g[lane], pacc.total(), pcnt, dacc, dcnt);
   }
 }
 
@@ -596,9 +625,9 @@ __device__ __forceinline__ unsigned int upper_mask(int lane) {
 // cluster: empty the slots past the batch and run both phases over the first
 // q rounded up to 4.  own_only: the partners are the warp's own cluster (each
 // lane excludes itself and updates its own side only).
-template <bool COUNT, bool PART>
+template <bool COUNT, bool PART, bool KAHAN>
 __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsigned int q, bool own_only,
-                                           float4& acc, unsigned int& cnt, const unsigned int* perm,
+                                           DensAcc<KAHAN>& acc, unsigned int& cnt, const unsigned int* perm,
                                            const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
                                            Counters& C) {
   const int lane = threadIdx.x & 31;
@@ -610,7 +639,7 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
   const float bandJ = warp_max(v ? S.a[lane].y : 0.0f);
   __syncwarp();
   const unsigned int allow = own_only ? jvalid & ~(1u << lane) : jvalid;
-  dens_tile<COUNT>(I, S, allow, jvalid, jact, bandJ, (int)((q + 3u) & ~3u), own_only,
+  dens_tile<COUNT, KAHAN>(I, S, allow, jvalid, jact, bandJ, (int)((q + 3u) & ~3u), own_only,
                    own_only ? upper_mask(lane) : 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
   __syncwarp();
 }
@@ -800,7 +829,7 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
 }
 
 // One pair task: cluster ti of cell A against the sorted clusters of cell B.
-template <bool COUNT, bool PART>
+template <bool COUNT, bool PART, bool KAHAN>
 __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
     const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
@@ -817,7 +846,7 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
   const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, actp, P.g.invL, P.g.e);
   dens_stage_own(S, lane, I);
   const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  DensAcc<KAHAN> acc;
   unsigned int cnt = 0, q = 0;
   for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
     unsigned int jt, jn, js;
@@ -855,19 +884,19 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+        dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
         q = 0;
       }
       if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
-  flush_dens(I.g, acc, cnt, dacc, dcnt);
+  if (q) dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+  flush_dens(I.g, acc.total(), cnt, dacc, dcnt);
 }
 
 // One self task: cluster ti against itself and the later clusters of its cell.
-template <bool COUNT, bool PART>
+template <bool COUNT, bool PART, bool KAHAN>
 __device__ __forceinline__ void density_self_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
     const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
@@ -887,11 +916,11 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
   const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, actp, g.invL, g.e);
   dens_stage_own(S, lane, I);
   const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  DensAcc<KAHAN> acc;
   unsigned int cnt = 0, q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) dens_put(S, lane, I);
-  dens_batch<COUNT, PART>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
+  dens_batch<COUNT, PART, KAHAN>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
   // the later clusters of the cell, 32 box tests at a time
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
@@ -914,15 +943,15 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+        dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
         q = 0;
       }
       if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) dens_batch<COUNT, PART>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
-  flush_dens(I.g, acc, cnt, dacc, dcnt);
+  if (q) dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+  flush_dens(I.g, acc.total(), cnt, dacc, dcnt);
 }
 
 template <bool COUNT>
@@ -1026,7 +1055,7 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
 // side culls against the box of the cluster's iterating particles; the first pass
 // (every particle) has its own instance without that code.  Both are launched in
 // a captured step, and the one that does not match the iteration returns.
-template <bool COUNT, bool PART>
+template <bool COUNT, bool PART, bool KAHAN>
 __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                          const float4* __restrict__ pos4,
                                                          const float4* __restrict__ cen4,
@@ -1058,10 +1087,10 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
       const uint2 lt = Lq.p_live[t];
       const int item = (int)(lt.x & 0x7fffffffu);
       if (lt.x >> 31)
-        density_self_task<COUNT, PART>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
+        density_self_task<COUNT, PART, KAHAN>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
                                        dcnt, S, Cs);
       else
-        density_pair_task<COUNT, PART>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
+        density_pair_task<COUNT, PART, KAHAN>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
                                        dcnt, S, Cp);
     }
     if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
@@ -1623,8 +1652,15 @@ void launch_density(Engine& E, const int* it_dev) {
   for (int part = 0; part < 2; ++part) {
     // on the host the pass kind is known; a captured step launches both
     if (!it_dev && part != (E.partial_pass ? 1 : 0)) continue;
-    const auto k = E.count_pairs ? (part ? k_density<true, true> : k_density<true, false>)
-                                 : (part ? k_density<false, true> : k_density<false, false>);
+    // compensated sums when asked, or (compensated < 0) from 100 neighbours on
+    const bool kahan = E.prm.compensated > 0 || (E.prm.compensated < 0 && E.prm.n_ngb >= 100.0f);
+    decltype(&k_density<false, false, false>) k;
+    if (kahan)
+      k = E.count_pairs ? (part ? k_density<true, true, true> : k_density<true, false, true>)
+                        : (part ? k_density<false, true, true> : k_density<false, false, true>);
+    else
+      k = E.count_pairs ? (part ? k_density<true, true, false> : k_density<true, false, false>)
+                        : (part ? k_density<false, true, false> : k_density<false, false, false>);
     k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
         E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
         E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev);

@@ -352,3 +352,31 @@ def test_h_iteration_results_exact_at_the_final_h(api, ctx):
     ref = orc.density(box.x, box.m, H, box.L, True, method="kdtree")
     assert np.array_equal(g["count"], ref["count"])
     np.testing.assert_allclose(g["rho"], ref["rho"], rtol=1e-5)
+
+
+def test_compensated_sums_at_high_neighbour_counts(api):
+    """With about 400 neighbours per particle the FP32 density sums carry ~20x
+    more rounding than at 48; compensated summation (sph_params.compensated)
+    brings them back to the error of the terms themselves."""
+    box = inputs.lattice_box(24, jitter=0.3, seed=21)
+    box.h = (box.h * np.float32((400.0 / 48.0) ** (1.0 / 3.0))).astype(np.float32)
+    H = orc.support_radius(box.h)
+    ref = orc.density(box.x, box.m, H, box.L, True, method="kdtree")
+    err = {}
+    for comp in (0, 1):
+        c = make_ctx(api, compensated=comp)
+        try:
+            b = api.box_from(c, box)
+            try:
+                b.density()
+                got = {k: b.get(k) for k in ("count", "rho", "nw")}
+            finally:
+                b.close()
+        finally:
+            api.sph_ctx_destroy(c)
+        assert np.array_equal(got["count"], ref["count"])
+        err[comp] = max(np.max(np.abs(got["rho"] / ref["rho"] - 1.0)), np.max(np.abs(got["nw"] / ref["nw"] - 1.0)))
+        np.testing.assert_allclose(got["rho"], ref["rho"], rtol=1e-5)
+    print(f"mean neighbours {ref['count'].mean():.0f}; max relative error of rho and sum W: plain {err[0]:.2e}, "
+          f"compensated {err[1]:.2e}")
+    assert err[1] < err[0]

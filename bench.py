@@ -276,7 +276,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, f"cuda:{local_rank}")
     e2e = job_rate(world, n * e2e_steps, e2e_s)
 
-    # roofline of the dominant kernel (FP32 ALU bound)
+    # roofline of the dominant kernel (FP32 ALU bound); the FMA throughput measured beside it
+    fp32_measured = sph.sph_measure_fp32_peak(ctx)
     dom = max(("density", "force"), key=lambda k: prof[k]["ms"])
     calls = max(prof[dom]["calls"], 1)
     avg_ms = prof[dom]["ms"] / calls
@@ -304,7 +305,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "flops_per_launch": flops, "avg_launch_ms": avg_ms,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)"},
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)",
+                     "peak_measured": fp32_measured,
+                     "peak_measured_source": "independent FMA chains on every SM (sph_measure_fp32_peak), this run"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["calls"]},

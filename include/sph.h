@@ -289,6 +289,13 @@ sph_status sph_get_profile(sph_box* box, int32_t cap, sph_profile_entry* out, in
 /* Kernel launches made by the library in this process so far. */
 int64_t sph_launch_count(void);
 
+/* FP32 throughput of the device, measured: a kernel of independent fused
+ * multiply-add chains (8 per thread, no memory traffic) over every SM, timed
+ * with CUDA events on the context's stream after a warm-up launch.  *tflops
+ * receives the rate (2 flops per FMA); the roofline's measured FP32 ceiling.
+ * Synchronises. */
+sph_status sph_measure_fp32_peak(sph_ctx* ctx, double* tflops);
+
 /* Autotune the cell split threshold leaf_max (Section II-B splits cells above
  * it; the paper uses 400 on its CPUs) and the particles per cluster for this
  * box's current particles: times build + density + force for leaf_max in {24,

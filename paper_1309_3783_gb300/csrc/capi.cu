@@ -60,6 +60,7 @@ __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
 void launch_density(Engine& E, const int* it_dev = nullptr);
+double measure_fp32_peak(cudaStream_t st, int nsm, float* scratch);
 void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
 void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep);
@@ -1662,6 +1663,19 @@ sph_status sph_get_profile(sph_box* b, int32_t cap, sph_profile_entry* out, int3
 }
 
 int64_t sph_launch_count(void) { return sph::launch_count(); }
+
+sph_status sph_measure_fp32_peak(sph_ctx* c, double* tflops) {
+  if (!c || !tflops) return SPH_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return SPH_E_CUDA;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) return SPH_E_CUDA;
+  float* scratch = nullptr;
+  if (cudaMalloc(&scratch, (size_t)nsm * 8 * sizeof(float)) != cudaSuccess) return SPH_E_OOM;
+  *tflops = sph::measure_fp32_peak(c->cur, nsm, scratch);
+  const cudaError_t e = cudaGetLastError();
+  cudaFree(scratch);
+  return e == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
 
 sph_status sph_box_tune(sph_box* b, int32_t* leaf_max) {
   BOX_PRE(b);

@@ -1576,6 +1576,42 @@ __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc*
   }
 }
 
+// =========================================================================== FP32 peak
+// Independent FMA chains (8 per thread) with no memory traffic between the first
+// load and the final store: the FP32 pipe's throughput.  The store depends on
+// every chain so the compiler keeps them.
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, float a, float b, float* __restrict__ out) {
+  float v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (float)(threadIdx.x + k) * 1e-3f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fmaf(v[k], a, b);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += v[k];
+  if (s == 12345.678f) out[blockIdx.x] = s;   // practically never: keeps the chains live
+}
+
+double measure_fp32_peak(cudaStream_t st, int nsm, float* scratch) {
+  const int blocks = nsm * 8, threads = 256, iters = 8192;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_peak<<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-4f, scratch); count_launch();
+  cudaEventRecord(e0, st);
+  k_fma_peak<<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-4f, scratch); count_launch();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+  return ms > 0.0f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+}
+
 // =========================================================================== outputs
 // Write field `field` of the particles of one box [off, off + n) in caller order.
 __global__ void k_get_field(long long off, long long n, int field, const unsigned int* __restrict__ perm,

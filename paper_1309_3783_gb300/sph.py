@@ -85,6 +85,7 @@ _SIGS = {
     "sph_box_profile": (C.c_int, [_P, C.c_int]),
     "sph_get_profile": (C.c_int, [_P, C.c_int32, C.POINTER(sph_profile_entry), C.POINTER(C.c_int32)]),
     "sph_launch_count": (C.c_int64, []),
+    "sph_measure_fp32_peak": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "sph_box_tune": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "sph_box_set_cluster_max": (C.c_int, [_P, C.c_int32]),
     "sph_box_set_leaf_max": (C.c_int, [_P, C.c_int32]),
@@ -286,6 +287,13 @@ def sph_get_profile(box, ctx) -> dict:
 
 def sph_launch_count() -> int:
     return int(load().sph_launch_count())
+
+
+def sph_measure_fp32_peak(ctx) -> float:
+    """Measured FP32 FMA throughput of the context's device (TFLOP/s)."""
+    v = C.c_double(0.0)
+    _check(load().sph_measure_fp32_peak(ctx, C.byref(v)), ctx)
+    return float(v.value)
 
 
 def sph_box_tune(box, ctx) -> int:

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "sph.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sph_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +29,7 @@ def test_header_declares_the_interface():
 
 def test_library_exports_every_declared_symbol(lib_path):
     out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (sph_[a-z_]+)", out))
+    exported = set(re.findall(r"\bT (sph_[a-z0-9_]+)", out))
     missing = [n for n in _declared() if n not in exported]
     assert not missing, missing
 

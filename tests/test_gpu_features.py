@@ -366,3 +366,12 @@ def test_h_history_survives_a_round_trip_of_the_state(api):
     # particles after new h)
     assert kept < 0.25 * box.n and trip < 1.5 * kept + 100
     assert fresh > 0.9 * box.n
+
+
+def test_measured_fp32_peak_is_plausible(api, ctx):
+    """The FMA-chain kernel reaches the FP32 pipe's rate: between 40 % (a low
+    clock under load) and 105 % of 152 SMs x 128 lanes x 2 flops x 2.07 GHz."""
+    t = api.sph_measure_fp32_peak(ctx)
+    nominal = 152 * 128 * 2 * 2.070e9 / 1e12
+    print(f"measured FP32 peak {t:.1f} TFLOP/s (nominal {nominal:.1f})")
+    assert 0.4 * nominal < t < 1.05 * nominal

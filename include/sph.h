@@ -275,6 +275,14 @@ sph_status sph_cfl_dt(sph_box* box, double* dt);
  * Errors: SPH_E_INVALID (n mismatch), SPH_E_NOT_BUILT (field not computed). */
 sph_status sph_get(sph_box* box, int field, void* dst, int64_t n, int mem);
 
+/* Copy n_fields fields (at most 64) at once: field fields[k] into dst[k] with
+ * n[k] elements as in sph_get, all to memory of kind mem, with one
+ * synchronisation at the end (host destinations in page-locked memory are
+ * filled asynchronously until then).  Errors as sph_get; fields before a
+ * failing one may have been copied. */
+sph_status sph_get_fields(sph_box* box, int32_t n_fields, const int32_t* fields, void* const* dst,
+                          const int64_t* n, int mem);
+
 /* Counters of the last build and passes (synchronises). */
 sph_status sph_get_stats(sph_box* box, sph_stats* out);
 

@@ -1250,6 +1250,31 @@ sph_status Engine::cfl_dt(int b, double* dt) {
 
 // ----------------------------------------------------------------------- outputs
 sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
+  sph_status s = get_async(b, field, dst, n, mem, staging.p);
+  if (s == SPH_OK && mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+// Several fields with one synchronisation: each field that is gathered goes
+// through its own staging region.
+sph_status Engine::get_fields(int b, int nf, const int* fields, void* const* dsts, const long long* ns, int mem) {
+  if (nf < 0 || (nf > 0 && (!fields || !dsts || !ns))) return fail(SPH_E_INVALID, "null field list");
+  size_t need = 0;
+  for (int k = 0; k < nf; ++k) need += (size_t)std::max<long long>(ns[k], 0) * 3 * sizeof(double) / 2 + 256;
+  CK(staging_many.reserve(need));
+  size_t at = 0;
+  for (int k = 0; k < nf; ++k) {
+    sph_status s = get_async(b, fields[k], dsts[k], ns[k], mem, staging_many.p + at);
+    if (s != SPH_OK) return s;
+    at += (size_t)std::max<long long>(ns[k], 0) * 3 * sizeof(double) / 2 + 256;
+  }
+  if (mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
+  return SPH_OK;
+}
+
+// One field, enqueued on the stream (host destinations complete at the next
+// synchronisation); gathered fields pass through the staging region stg.
+sph_status Engine::get_async(int b, int field, void* dst, long long n, int mem, unsigned char* stg) {
   if (b < 0 || b >= nbox) return fail(SPH_E_INVALID, "box index out of range");
   if (!dst) return fail(SPH_E_INVALID, "null destination");
   const long long o = off[b], nb = spec[b].n;
@@ -1258,7 +1283,6 @@ sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
     if (n != 8) return fail(SPH_E_INVALID, "reductions need n = 8");
     if (!have_force) return fail(SPH_E_NOT_BUILT, "no force pass yet");
     CK(cudaMemcpyAsync(dst, red.p + 8 * b, 8 * sizeof(double), kind, st));
-    if (mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
     return SPH_OK;
   }
   if (n != nb) return fail(SPH_E_INVALID, "n does not match the box's particle count");
@@ -1276,7 +1300,6 @@ sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
   }
   if (src) {
     CK(cudaMemcpyAsync(dst, src, bytes, kind, st));
-    if (mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
     return SPH_OK;
   }
   int per = 1;
@@ -1293,16 +1316,13 @@ sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
       break;
     default: return fail(SPH_E_INVALID, "unknown field");
   }
-  void* out = mem == SPH_MEM_DEVICE ? dst : (void*)staging.p;
+  void* out = mem == SPH_MEM_DEVICE ? dst : (void*)stg;
   {
     Scope sc(this, PH_OUTPUT);
     launch_get_field(*this, o, nb, field, out);
   }
   CK(cudaGetLastError());
-  if (mem != SPH_MEM_DEVICE) {
-    CK(cudaMemcpyAsync(dst, staging.p, per * nb * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-  }
+  if (mem != SPH_MEM_DEVICE) CK(cudaMemcpyAsync(dst, stg, per * nb * 4, cudaMemcpyDeviceToHost, st));
   return SPH_OK;
 }
 
@@ -1635,6 +1655,16 @@ sph_status sph_cfl_dt(sph_box* b, double* dt) {
 sph_status sph_get(sph_box* b, int field, void* dst, int64_t n, int mem) {
   BOX_PRE(b);
   return from_engine(b, b->eng->get(0, field, dst, n, mem));
+}
+
+sph_status sph_get_fields(sph_box* b, int32_t n_fields, const int32_t* fields, void* const* dst, const int64_t* n,
+                          int mem) {
+  BOX_PRE(b);
+  if (n_fields < 0 || n_fields > 64) return set_err(b->ctx, SPH_E_INVALID, "n_fields must be in 0..64");
+  std::vector<int> f(fields ? fields : nullptr, fields ? fields + n_fields : nullptr);
+  std::vector<long long> nn(n ? n : nullptr, n ? n + n_fields : nullptr);
+  if (n_fields > 0 && (!fields || !n || !dst)) return set_err(b->ctx, SPH_E_INVALID, "null field list");
+  return from_engine(b, b->eng->get_fields(0, n_fields, f.data(), dst, nn.data(), mem));
 }
 
 sph_status sph_box_profile(sph_box* b, int on) {

@@ -100,6 +100,8 @@ class Engine {
   sph_status tune(int* best_leaf_max);
   std::vector<std::pair<int, float>> tune_ms;   // (leaf_max, ms) of the last tune()
   sph_status get(int b, int field, void* dst, long long n, int mem);
+  sph_status get_async(int b, int field, void* dst, long long n, int mem, unsigned char* stg);
+  sph_status get_fields(int b, int nf, const int* fields, void* const* dsts, const long long* ns, int mem);
   sph_status set_field(int b, int field, const void* src, long long n, int mem);
   sph_status stats(int b, sph_stats* out);
   sph_status cells(int b, long long cap, int* level, int* ijk, int* count, int* split, long long* n_out);
@@ -206,6 +208,7 @@ class Engine {
   DBuf<unsigned int> task_ctr;    // task counters of the four interaction kernels
   DBuf<int> dev_counters;         // [0] particles still active after a ghost pass
   DBuf<unsigned char> staging;    // output staging (input order)
+  DBuf<unsigned char> staging_many;   // one region per field of a multi-field read
 
   // host mirrors of counts after the last build
   int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0, depth_used = 0;

@@ -86,6 +86,8 @@ _SIGS = {
     "sph_get_profile": (C.c_int, [_P, C.c_int32, C.POINTER(sph_profile_entry), C.POINTER(C.c_int32)]),
     "sph_launch_count": (C.c_int64, []),
     "sph_measure_fp32_peak": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "sph_get_fields": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_void_p),
+                                 C.POINTER(C.c_int64), C.c_int]),
     "sph_box_tune": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "sph_box_set_cluster_max": (C.c_int, [_P, C.c_int32]),
     "sph_box_set_leaf_max": (C.c_int, [_P, C.c_int32]),
@@ -266,6 +268,18 @@ def sph_get(box, ctx, field, n: int, out=None):
     return out
 
 
+def sph_get_fields(box, ctx, outs: dict, n: int):
+    """Copy several fields at once into host numpy arrays (``outs``: name -> array),
+    with one synchronisation."""
+    names = list(outs)
+    k = len(names)
+    fields = (C.c_int32 * k)(*[FIELDS[f] for f in names])
+    ptrs = (C.c_void_p * k)(*[outs[f].ctypes.data_as(C.c_void_p).value for f in names])
+    cnt = (C.c_int64 * k)(*[8 if FIELDS[f] == 16 else n for f in names])
+    _check(load().sph_get_fields(box, k, fields, ptrs, cnt, SPH_MEM_HOST), ctx)
+    return outs
+
+
 def sph_get_stats(box, ctx) -> dict:
     s = sph_stats()
     _check(load().sph_get_stats(box, C.byref(s)), ctx)
@@ -425,6 +439,10 @@ class Box:
 
     def get(self, field, out=None):
         return sph_get(self.h, self.ctx, field, self.n, out)
+
+    def get_many(self, outs: dict):
+        """Fill several host arrays at once (name -> numpy array), one synchronisation."""
+        return sph_get_fields(self.h, self.ctx, outs, self.n)
 
     def stats(self):
         return sph_get_stats(self.h, self.ctx)

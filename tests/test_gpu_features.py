@@ -375,3 +375,18 @@ def test_measured_fp32_peak_is_plausible(api, ctx):
     nominal = 152 * 128 * 2 * 2.070e9 / 1e12
     print(f"measured FP32 peak {t:.1f} TFLOP/s (nominal {nominal:.1f})")
     assert 0.4 * nominal < t < 1.05 * nominal
+
+
+def test_multi_field_read_equals_single_reads(api, ctx):
+    box = inputs.lattice_box(10, jitter=0.2, seed=17, v_sigma=0.1)
+    b = api.box_from(ctx, box)
+    try:
+        b.h_update()
+        b.force()
+        single = {k: b.get(k) for k in ("x", "v", "u", "h", "rho", "a", "count", "reductions")}
+        many = {k: np.empty_like(v) for k, v in single.items()}
+        b.get_many(many)
+    finally:
+        b.close()
+    for k in single:
+        assert np.array_equal(single[k], many[k].reshape(single[k].shape)), k

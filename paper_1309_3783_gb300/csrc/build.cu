@@ -494,6 +494,22 @@ __global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc*
 // contiguous range).  Children of one node get consecutive ids.
 constexpr int TREE_THREADS = 256;
 
+// k consecutive node ids, all or none: the count never passes the capacity, so
+// every id below it belongs to a node that was written (an allocation that only
+// partly fitted would leave unwritten ids inside the tree, which the next round's
+// frontier would read).  -1 when they do not fit.  The compare-and-swap retries
+// only when another node allocated in between.
+__device__ __forceinline__ int alloc_nodes(int* count, int k, int cap) {
+  int old = atomicAdd(count, 0);
+  for (int tries = 0; tries < (1 << 20); ++tries) {
+    if (old + k > cap) return -1;
+    const int prev = atomicCAS(count, old, old + k);
+    if (prev == old) return old;
+    old = prev;
+  }
+  return -1;
+}
+
 __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDesc* __restrict__ box,
                                                              const float* __restrict__ Hs,
                                                              const unsigned long long* __restrict__ key, int dcap,
@@ -561,10 +577,10 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
         if (lane >= o) before += y;
       }
       before -= mine;
-      int c0 = 0;
-      if (sp && lane == 0) c0 = atomicAdd(&T.n_nodes[0], nch);
+      int c0 = -1;
+      if (sp && lane == 0) c0 = alloc_nodes(&T.n_nodes[0], nch, cap_nodes);
       c0 = __shfl_sync(0xffffffffu, c0, 0);
-      const bool fits = c0 + nch <= cap_nodes;
+      const bool fits = c0 >= 0;
       if (sp && fits && lane < 8 && mine != 0) {
         const int cid = c0 + __popc(ne & ((1u << lane) - 1u));
         T.start[cid] = s + before;

@@ -542,13 +542,27 @@ sph_status Engine::build_once(bool* retry) {
   }
   prof_end(PH_TREE, ev, l0);
   CK(cudaGetLastError());
-  // The node count stays on the device: the kernels up to the list sizes take
-  // the capacity as their bound and read the count themselves; the host reads it
-  // (and any overflow) with the list sizes.
+  // The tree's size is read before anything uses the tree: when it overflowed,
+  // nodes past the last complete allocation were never written, and the build is
+  // retried with more room before any kernel reads them.
+  int tn[8];
+  unsigned int ea[4];
+  CK(cudaMemcpyAsync(tn, t_n.p, sizeof(tn), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if ((ea[0] & ERR_OVERFLOW) || tn[0] > cap_nodes) {
+    sph_status s = ensure_tree_capacity(std::max(2 * cap_nodes, tn[0] + 1024));
+    if (s != SPH_OK) return s;
+    *retry = true;
+    return SPH_OK;
+  }
+  n_nodes = tn[0];
+  n_top = tn[3];
+
   ev = prof_begin(PH_LISTS, &l0);
   CK(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
-  k_items_top<<<nsm * 8, 256, 0, st>>>(cap_nodes, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
-                                       err_all.p); count_launch();
+  k_items_top<<<grid(13ll * n_top), 256, 0, st>>>(n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
+                                                  err_all.p); count_launch();
   for (int r = 0; r < rounds; ++r) {
     const int in = r & 1;
     CK(cudaMemsetAsync(l_counts.p + 2 + (in ^ 1), 0, sizeof(int), st));
@@ -557,9 +571,9 @@ sph_status Engine::build_once(bool* retry) {
   }
   prof_end(PH_LISTS, ev, l0);
   ev = prof_begin(PH_SHIFT, &l0);
-  k_leaves<<<nsm * 8, 256, 0, st>>>(T, cap_nodes, leaf_of.p); count_launch();
+  k_leaves<<<nsm * 8, 256, 0, st>>>(T, n_nodes, leaf_of.p); count_launch();
   // particles of each leaf: the ones with H above the leaf edge last (stable)
-  k_leaf_partition<<<nsm * 8, 256, 0, st>>>(T, cap_nodes, box.p, Hs.p, lsrc.p); count_launch();
+  k_leaf_partition<<<nsm * 8, 256, 0, st>>>(T, n_nodes, box.p, Hs.p, lsrc.p); count_launch();
   k_apply_partition<<<grid(N), 256, 0, st>>>(N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
                                              vel4.p, vel4_tmp.p); count_launch();
   perm.swap(perm_tmp);
@@ -569,12 +583,12 @@ sph_status Engine::build_once(bool* retry) {
   k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p); count_launch();
   k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   // clusters of at most 32 particles inside each leaf
-  k_tile_flags<<<nsm * 8, 256, 0, st>>>(T, cap_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
+  k_tile_flags<<<nsm * 8, 256, 0, st>>>(T, n_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
   count_launch();
   exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), st);
   k_tile_table<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL, prm.cluster_max);
   count_launch();
-  k_cell_tiles<<<grid(cap_nodes), 256, 0, st>>>(T, cap_nodes, tile_of.p); count_launch();
+  k_cell_tiles<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, tile_of.p); count_launch();
   prof_end(PH_SHIFT, ev, l0);
 
   // ---- sorted projections
@@ -587,33 +601,23 @@ sph_status Engine::build_once(bool* retry) {
   }
   ev = prof_begin(PH_AXIS_SORT, &l0);
   CK(cudaMemsetAsync(big_count.p, 0, sizeof(unsigned long long), st));
-  CK(mid_seg.reserve(13 * (size_t)std::max(cap_nodes, 1)));
+  CK(mid_seg.reserve(13 * (size_t)std::max(n_nodes, 1)));
   CK(mid_count.reserve(1));
   CK(cudaMemsetAsync(mid_count.p, 0, sizeof(unsigned int), st));
   k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T); count_launch();
-  k_sort_alloc<<<grid(cap_nodes), 256, 0, st>>>(T, cap_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
+  k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
                                               cap_big, mid_seg.p, mid_count.p); count_launch();
   launch_task_offsets(*this);
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
-  int lc[8], tn[8];
-  unsigned int ea[4];
+  int lc[8];
   unsigned long long bcw = 0;
-  CK(cudaMemcpyAsync(tn, t_n.p, sizeof(tn), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(lc, l_counts.p, sizeof(lc), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&bcw, big_count.p, sizeof(bcw), cudaMemcpyDeviceToHost, st));
   unsigned int ntl = 0;
   CK(cudaMemcpyAsync(&ntl, dev_counters.p + 4, sizeof(ntl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (tn[0] > cap_nodes) {
-    sph_status s = ensure_tree_capacity(std::max(2 * cap_nodes, tn[0] + 1024));
-    if (s != SPH_OK) return s;
-    *retry = true;
-    return SPH_OK;
-  }
-  n_nodes = tn[0];
-  n_top = tn[3];
   const int last_q = lc[2 + (rounds & 1)];
   if ((ea[0] & ERR_OVERFLOW) || lc[0] > cap_self || lc[1] > cap_pair || last_q != 0) {
     sph_status s = ensure_list_capacity(std::max(cap_self, lc[0]) * 2, std::max(cap_pair, lc[1]) * 2,

@@ -11,6 +11,7 @@
 // the resident set changes, the boxes that stay keep their state on the device:
 // the engine moves it to the new layout with one kernel, and only the new
 // boxes are copied in from the host.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -63,6 +64,8 @@ struct sph_server {
   std::vector<long long> resident;
   std::vector<long long> layout;   // the boxes in the engine, in its order
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  unsigned char* pin = nullptr;    // page-locked staging for the results of finished boxes
+  size_t pin_cap = 0;
   std::string err;
 };
 
@@ -114,6 +117,67 @@ static sph_status finish(sph_server* s, size_t b) {
     if (st != SPH_OK) r.result[f].clear();
   }
   r.state = 2;
+  return SPH_OK;
+}
+
+static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// The results of several finished boxes: every field of every box is queued into
+// page-locked staging and read with one synchronisation per chunk of at most
+// kPinMax bytes, then copied to the requests.  Without page-locked memory the
+// boxes go one field at a time.
+static const size_t kPinMax = 256u << 20;
+
+static sph_status finish_many(sph_server* s, const std::vector<size_t>& boxes) {
+  sph::Engine& E = *s->eng;
+  size_t i = 0;
+  while (i < boxes.size()) {
+    size_t j = i, bytes = 0;
+    while (j < boxes.size()) {
+      const Request& r = s->reqs[s->resident[boxes[j]]];
+      size_t bb = 0;
+      for (int f = 0; f < kFields; ++f) bb += round256(field_bytes(f, r.n));
+      if (j > i && bytes + bb > kPinMax) break;
+      bytes += bb;
+      ++j;
+    }
+    if (bytes > s->pin_cap) {
+      if (s->pin) cudaFreeHost(s->pin);
+      s->pin = nullptr;
+      s->pin_cap = 0;
+      const size_t cap = std::max(bytes, std::min(2 * bytes, kPinMax));
+      if (cudaMallocHost(reinterpret_cast<void**>(&s->pin), cap) != cudaSuccess) {
+        cudaGetLastError();
+        s->pin = nullptr;
+        for (size_t k = i; k < j; ++k) finish(s, boxes[k]);
+        i = j;
+        continue;
+      }
+      s->pin_cap = cap;
+    }
+    std::vector<std::pair<size_t, bool>> at((j - i) * kFields);
+    size_t off = 0;
+    for (size_t k = i; k < j; ++k) {
+      const Request& r = s->reqs[s->resident[boxes[k]]];
+      for (int f = 0; f < kFields; ++f) {
+        const long long n = f == SPH_FIELD_REDUCTIONS ? 8 : r.n;
+        const sph_status st = E.get_async((int)boxes[k], f, s->pin + off, n, SPH_MEM_HOST, E.staging.p);
+        at[(k - i) * kFields + f] = std::make_pair(off, st == SPH_OK);
+        off += round256(field_bytes(f, r.n));
+      }
+    }
+    if (cudaStreamSynchronize(s->st) != cudaSuccess) return srv_fail(s, SPH_E_CUDA, "reading results");
+    for (size_t k = i; k < j; ++k) {
+      Request& r = s->reqs[s->resident[boxes[k]]];
+      r.result.assign(kFields, {});
+      for (int f = 0; f < kFields; ++f) {
+        const auto& a = at[(k - i) * kFields + f];
+        if (a.second) r.result[f].assign(s->pin + a.first, s->pin + a.first + field_bytes(f, r.n));
+      }
+      r.state = 2;
+    }
+    i = j;
+  }
   return SPH_OK;
 }
 
@@ -222,11 +286,14 @@ sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
     // return the finished boxes; the others stay on the device and move to the
     // new layout at the next tick
     std::vector<long long> keep;
+    std::vector<size_t> done;
     for (size_t b = 0; b < s->resident.size(); ++b) {
       Request& r = s->reqs[s->resident[b]];
-      if (r.done_steps >= r.n_steps) finish(s, b);
+      if (r.done_steps >= r.n_steps) done.push_back(b);
       else keep.push_back(r.id);
     }
+    sph_status fs = finish_many(s, done);
+    if (fs != SPH_OK) return fs;
     s->resident = keep;
   }
   return SPH_OK;
@@ -279,6 +346,7 @@ sph_status sph_server_destroy(sph_server* s) {
   delete s->eng;
   cudaEventDestroy(s->e0);
   cudaEventDestroy(s->e1);
+  if (s->pin) cudaFreeHost(s->pin);
   {
     std::lock_guard<std::mutex> g(s->ctx->mu);
     s->ctx->live--;

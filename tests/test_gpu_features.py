@@ -390,3 +390,38 @@ def test_multi_field_read_equals_single_reads(api, ctx):
         b.close()
     for k in single:
         assert np.array_equal(single[k], many[k].reshape(single[k].shape)), k
+
+
+def test_server_tree_grows_past_its_first_capacity(api):
+    """The server's engine sizes its tree for the first boxes it holds; a later,
+    much larger clustered box outgrows it, the build retries with more room, and
+    the box's results equal those of the box run alone."""
+    c = _ctx_with(api, leaf_max=8)      # 60,000 particles then need > 7,500 leaves: well past 4,096 nodes
+    try:
+        small = inputs.lattice_box(10, jitter=0.2, seed=51)
+        big = inputs.plummer_box(n=60000, n_spheres=4, seed=52)
+        srv = api.sph_server_create(c, 0, 0)
+        try:
+            a = api.sph_server_submit(srv, small.x, small.v, small.m, small.u, small.h, small.L, True, 0, 0.0)
+            while not api.sph_server_poll(srv, a)[0]:
+                api.sph_server_tick(srv)
+            bid = api.sph_server_submit(srv, big.x, big.v, big.m, big.u, big.h, big.L, True, 0, 0.0)
+            ticks = 0
+            while not api.sph_server_poll(srv, bid)[0]:
+                api.sph_server_tick(srv)
+                ticks += 1
+                assert ticks < 10
+            got = {k: api.sph_server_get(srv, bid, k, big.n) for k in ("count", "rho", "h")}
+        finally:
+            api.sph_server_destroy(srv)
+        b = api.box_from(c, big)
+        try:
+            b.h_update()
+            ref = {k: b.get(k) for k in ("count", "rho", "h")}
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    np.testing.assert_allclose(got["h"], ref["h"], rtol=1e-4)
+    np.testing.assert_allclose(got["rho"], ref["rho"], rtol=1e-3)
+    assert np.mean(got["count"] != ref["count"]) < 2e-3

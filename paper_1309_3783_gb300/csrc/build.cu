@@ -15,6 +15,7 @@ namespace sph {
 __global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box, const double* __restrict__ x,
                          const float* __restrict__ v, const float* __restrict__ m, const float* __restrict__ u,
                          const float* __restrict__ h, float gamma_k, float* __restrict__ H_out) {
+  pdl_wait();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     const long long p = base + threadIdx.x;   // every lane of a warp runs every iteration
@@ -56,6 +57,7 @@ __global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box,
 __global__ void k_keys(long long N, int dcap, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                        const double* __restrict__ x, unsigned long long* __restrict__ key,
                        unsigned int* __restrict__ val) {
+  pdl_wait();
   const double scale = ldexp(1.0, dcap);
   const unsigned int qmax = (1u << dcap) - 1u;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
@@ -76,6 +78,7 @@ __global__ void k_keys(long long N, int dcap, const int* __restrict__ bid, const
 
 // box of every particle from the box offsets (off[0..nbox], off[nbox] = N)
 __global__ void k_box_ids(long long N, int nbox, const long long* __restrict__ off, int* __restrict__ bid) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     int lo = 0, hi = nbox - 1;
     while (lo < hi) {
@@ -95,6 +98,7 @@ __global__ void k_relayout(const long long* __restrict__ tab, const double* __re
                            double* __restrict__ nx, float* __restrict__ nv, float* __restrict__ nm,
                            float* __restrict__ nu, float* __restrict__ nh, float4* __restrict__ nhh,
                            float4* __restrict__ na) {
+  pdl_wait();
   const long long dst = tab[3 * blockIdx.y], src = tab[3 * blockIdx.y + 1], n = tab[3 * blockIdx.y + 2];
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long s = src + q, d = dst + q;
@@ -119,6 +123,7 @@ __global__ void k_relayout(const long long* __restrict__ tab, const double* __re
 __global__ void k_displacement(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                                const double* __restrict__ x, const double* __restrict__ xb,
                                unsigned long long* __restrict__ dmax) {
+  pdl_wait();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     const long long p = base + threadIdx.x;   // every lane of a warp runs every iteration
@@ -163,6 +168,7 @@ __global__ void k_reuse_limits(long long N, int box_shift, const unsigned long l
                                const float* __restrict__ h, float gamma_k,
                                const unsigned long long* __restrict__ dmax, float* __restrict__ hlimp,
                                unsigned int* __restrict__ flag) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(key[p] >> box_shift);
     int id = (int)leaf_of[p];
@@ -182,6 +188,7 @@ __global__ void k_reuse_limits(long long N, int box_shift, const unsigned long l
 // Largest H of every cell from its leaves (cell H_max entries start at 0): one
 // warp per leaf, then a climb that stops at the first cell already covering it.
 __global__ void k_leaf_hmax(Tree T, int nnodes, const float* __restrict__ Hs) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -201,6 +208,7 @@ __global__ void k_leaf_hmax(Tree T, int nnodes, const float* __restrict__ Hs) {
 
 // Cluster boxes from the current offsets (membership kept): one warp per cluster.
 __global__ void k_tile_boxes(long long ntile, Tiles TL, const float4* __restrict__ pos4) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -233,6 +241,7 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 __global__ void k_radix_hist(long long n, const unsigned long long* __restrict__ key, int shift,
                              unsigned int* __restrict__ hist, int ntiles) {
+  pdl_wait();
   __shared__ unsigned int cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -249,6 +258,7 @@ __global__ void k_radix_scatter(long long n, const unsigned long long* __restric
                                 const unsigned int* __restrict__ vin, unsigned long long* __restrict__ kout,
                                 unsigned int* __restrict__ vout, int shift, const unsigned int* __restrict__ offs,
                                 int ntiles) {
+  pdl_wait();
   __shared__ unsigned int base[256];
   __shared__ unsigned int wcnt[RS_THREADS / 32][256];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -320,6 +330,7 @@ __device__ unsigned int block_exclusive_scan(unsigned int v, unsigned int* tmp, 
 // in and out may be the same array: every thread reads its items before writing them
 __global__ void k_scan_tiles(long long n, const unsigned int* in, unsigned int* out,
                              unsigned int* __restrict__ tile_sums) {
+  pdl_wait();
   __shared__ unsigned int tmp[32];
   const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
   unsigned int loc[SC_ITEMS];
@@ -341,6 +352,7 @@ __global__ void k_scan_tiles(long long n, const unsigned int* in, unsigned int* 
 
 // single block: exclusive scan of the tile sums in place (any count), total -> *total
 __global__ void k_scan_sums(int ntiles, unsigned int* __restrict__ sums, unsigned int* __restrict__ total_out) {
+  pdl_wait();
   __shared__ unsigned int tmp[32];
   unsigned int carry = 0;
   for (int base = 0; base < ntiles; base += blockDim.x) {
@@ -355,6 +367,7 @@ __global__ void k_scan_sums(int ntiles, unsigned int* __restrict__ sums, unsigne
 }
 
 __global__ void k_scan_add(long long n, unsigned int* __restrict__ out, const unsigned int* __restrict__ sums) {
+  pdl_wait();
   const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
   const unsigned int add = sums[blockIdx.x];
 #pragma unroll
@@ -366,9 +379,9 @@ void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsi
                     unsigned int* total, cudaStream_t st) {
   const long long ntiles = (n + SC_TILE - 1) / SC_TILE;
   if (ntiles == 0) return;
-  k_scan_tiles<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, in, out, tile_sums); count_launch();
-  k_scan_sums<<<1, 1024, 0, st>>>((int)ntiles, tile_sums, total); count_launch();
-  k_scan_add<<<(unsigned)ntiles, SC_THREADS, 0, st>>>(n, out, tile_sums); count_launch();
+  launch_pdl(k_scan_tiles, (unsigned)ntiles, SC_THREADS, st, n, in, out, tile_sums); count_launch();
+  launch_pdl(k_scan_sums, 1, 1024, st, (int)ntiles, tile_sums, total); count_launch();
+  launch_pdl(k_scan_add, (unsigned)ntiles, SC_THREADS, st, n, out, tile_sums); count_launch();
 }
 
 long long radix_scratch_words(long long n) {
@@ -389,9 +402,9 @@ void radix_sort(unsigned long long* k0, unsigned int* v0, unsigned long long* k1
   unsigned int *va = v0, *vb = v1;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
-    k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, shift, hist, (int)ntiles); count_launch();
+    launch_pdl(k_radix_hist, (unsigned)ntiles, RS_THREADS, st, n, ka, shift, hist, (int)ntiles); count_launch();
     exclusive_scan(hist, hist, 256 * ntiles, sums, nullptr, st);
-    k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, st>>>(n, ka, va, kb, vb, shift, hist, (int)ntiles); count_launch();
+    launch_pdl(k_radix_scatter, (unsigned)ntiles, RS_THREADS, st, n, ka, va, kb, vb, shift, hist, (int)ntiles); count_launch();
     std::swap(ka, kb);
     std::swap(va, vb);
   }
@@ -410,6 +423,7 @@ __global__ void k_gather_sorted(long long N, const unsigned int* __restrict__ pe
                                 const float* __restrict__ v, const float* __restrict__ u, const int* __restrict__ bid,
                                 const BoxDesc* __restrict__ box, const float4* __restrict__ a_in, int vpred,
                                 float* __restrict__ Hs, float4* __restrict__ vel4) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const unsigned int i = perm[p];
     Hs[p] = H_in[i];
@@ -460,6 +474,7 @@ __device__ __forceinline__ void cell_coords(unsigned long long prefix, int level
 __global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc* __restrict__ box,
                             const unsigned long long* __restrict__ key, Tree T, int cap_nodes,
                             int* __restrict__ top_at, unsigned int* __restrict__ err_all) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(key[p] >> box_shift);
     const BoxDesc bd = box[b];
@@ -515,6 +530,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
                                                              const unsigned long long* __restrict__ key, int dcap,
                                                              int leaf_max, float split_frac, int allow_split,
                                                              int cap_nodes, unsigned int* __restrict__ err_all) {
+  pdl_wait();
   constexpr int NW = TREE_THREADS / 32;
   __shared__ float s_hm[NW];
   __shared__ unsigned int s_ns[NW], s_oc[NW][8];
@@ -631,6 +647,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
 }
 
 __global__ void k_frontier_init(Tree T, int cap_nodes) {
+  pdl_wait();
   T.n_nodes[1] = 0;
   T.n_nodes[2] = min(T.n_nodes[0], cap_nodes);
   T.n_nodes[3] = min(T.n_nodes[0], cap_nodes);   // top cells are nodes [0, n_nodes[3])
@@ -657,6 +674,7 @@ __device__ __forceinline__ void push_item(Lists Lq, int out, int kind, int a, in
 __global__ void k_items_top(int ntop, Tree T, const BoxDesc* __restrict__ box, const unsigned long long* __restrict__ key,
                             const int* __restrict__ top_at, int dcap, int box_shift, Lists Lq, int cap_queue,
                             unsigned int* __restrict__ err_all) {
+  pdl_wait();
   // ntop bounds the top cells, whose number the tree build left on the device
   const long long n = 13ll * min(ntop, T.n_nodes[3]);
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += (long long)gridDim.x * blockDim.x) {
@@ -751,6 +769,7 @@ __device__ __forceinline__ int child_pairs(const Tree& T, int A, int B, int ax, 
 // item produces, so that a warp takes its output slots with one atomic per list.
 __global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, Lists Lq, int cap_queue,
                                int cap_self, int cap_pair, unsigned int* __restrict__ err_all, float headroom) {
+  pdl_wait();
   const int out = in ^ 1;
   const int n = min(Lq.counts[2 + in], cap_queue);
   const int lane = threadIdx.x & 31;
@@ -824,6 +843,7 @@ __global__ void k_items_expand(int in, Tree T, const BoxDesc* __restrict__ box, 
 
 // leaf of every particle, and the smallest H limit along its chain of cells
 __global__ void k_leaves(Tree T, int nnodes, unsigned int* __restrict__ leaf_of) {
+  pdl_wait();
   nnodes = min(nnodes, T.n_nodes[0]);   // nnodes: the capacity; the count is on the device
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -837,6 +857,7 @@ __global__ void k_leaves(Tree T, int nnodes, unsigned int* __restrict__ leaf_of)
 
 __global__ void k_particle_limits(long long N, Tree T, const unsigned int* __restrict__ leaf_of,
                                   float* __restrict__ hlimp) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     int id = (int)leaf_of[p];
     double lim = 1e300;
@@ -854,6 +875,7 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
                         const unsigned int* __restrict__ perm, const unsigned int* __restrict__ leaf_of, Tree T,
                         const BoxDesc* __restrict__ box, const double* __restrict__ x, const float* __restrict__ m,
                         const float* __restrict__ Hs, float4* __restrict__ pos4, float4* __restrict__ cen4) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(key[p] >> box_shift);
     const double L = box[b].L;
@@ -889,6 +911,7 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
 // lsrc[p] = the particle that moves to position p.
 __global__ void k_leaf_partition(Tree T, int nnodes, const BoxDesc* __restrict__ box, const float* __restrict__ Hs,
                                  unsigned int* __restrict__ lsrc) {
+  pdl_wait();
   nnodes = min(nnodes, T.n_nodes[0]);
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -925,6 +948,7 @@ __global__ void k_apply_partition(long long N, const unsigned int* __restrict__ 
                                   const unsigned long long* __restrict__ key_in, unsigned long long* __restrict__ key_out,
                                   const float* __restrict__ H_in, float* __restrict__ H_out,
                                   const float4* __restrict__ vel_in, float4* __restrict__ vel_out) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const unsigned int q = lsrc[p];
     perm_out[p] = perm_in[q];
@@ -950,6 +974,7 @@ __device__ __forceinline__ int high_bit(unsigned long long v) { return v ? 63 - 
 __global__ void k_tile_flags(Tree T, int nnodes, int box_shift, const BoxDesc* __restrict__ box,
                              const float* __restrict__ Hs, const unsigned long long* __restrict__ key,
                              unsigned int* __restrict__ flag, int cmax) {
+  pdl_wait();
   nnodes = min(nnodes, T.n_nodes[0]);
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -993,6 +1018,7 @@ __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict
                              const unsigned int* __restrict__ flag, const unsigned int* __restrict__ excl,
                              const float4* __restrict__ pos4, unsigned int* __restrict__ tile_of, Tiles TL,
                              int cmax) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     tile_of[p] = excl[p] + flag[p] - 1u;
     if (!flag[p]) continue;
@@ -1020,6 +1046,7 @@ __global__ void k_tile_table(long long N, Tree T, const unsigned int* __restrict
 }
 
 __global__ void k_cell_tiles(Tree T, int nnodes, const unsigned int* __restrict__ tile_of) {
+  pdl_wait();
   nnodes = min(nnodes, T.n_nodes[0]);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int s = T.start[id], c = T.count[id];
@@ -1034,6 +1061,7 @@ __global__ void k_cell_tiles(Tree T, int nnodes, const unsigned int* __restrict_
 // cell-pair axes.  Here the sorted entries are the cell's clusters, keyed by the
 // lower end of the projection of their box on the axis.
 __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
+  pdl_wait();
   const int n = min(Lq.counts[1], cap_pair);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned int bit = 1u << Lq.pair_axis[i];
@@ -1050,6 +1078,7 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
                              unsigned int* __restrict__ big_off, unsigned long long* __restrict__ big_count,
                              int cap_big, uint4* __restrict__ mid_seg, unsigned int* __restrict__ mid_count) {
+  pdl_wait();
   nnodes = min(nnodes, T.n_nodes[0]);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
     const unsigned int ax = T.axes[id];
@@ -1119,6 +1148,7 @@ __device__ __forceinline__ float tile_rlo(const Tiles& TL, const Tree& T, unsign
 __global__ void __launch_bounds__(256) k_sort_small(const uint4* __restrict__ mid_seg,
                                                    const unsigned int* __restrict__ mid_count, Tree T, Tiles TL,
                                                    float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
+  pdl_wait();
   __shared__ float sr[SORT_SMALL];
   __shared__ unsigned int si[SORT_SMALL];
   const unsigned int nseg = *mid_count;
@@ -1206,6 +1236,7 @@ __device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned
 __global__ void __launch_bounds__(256) k_sort_merge(const uint4* __restrict__ mid_seg,
                                                    const unsigned int* __restrict__ mid_count, Tree T, Tiles TL,
                                                    float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
+  pdl_wait();
   __shared__ float sr[2][SORT_SMALL];
   __shared__ unsigned int si[2][SORT_SMALL];         // cluster index q | run << 16
   __shared__ unsigned short rs[2][SORT_SMALL + 1];   // run starts
@@ -1319,6 +1350,7 @@ __global__ void __launch_bounds__(256) k_sort_merge(const uint4* __restrict__ mi
 __global__ void k_sort_big_keys(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
                                 const unsigned int* __restrict__ big_off, Tree T, Tiles TL,
                                 unsigned long long* __restrict__ ckey, unsigned int* __restrict__ cval) {
+  pdl_wait();
   for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
     const int id = big_node[sgi];
     const int a = big_axis[sgi];
@@ -1336,6 +1368,7 @@ __global__ void k_sort_big_scatter(int nseg, const int* __restrict__ big_node, c
                                    const unsigned int* __restrict__ big_off, Tree T, Tiles TL,
                                    const unsigned int* __restrict__ cval, float* __restrict__ sort_r,
                                    unsigned int* __restrict__ sort_i) {
+  pdl_wait();
   for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
     const int id = big_node[sgi];
     const int a = big_axis[sgi];

@@ -207,7 +207,7 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
   CK(cudaMemsetAsync(hlev.p, 0, std::max(nbox, 1) * sizeof(int), st));
   CK(boff.reserve(nbox + 1));
   CK(cudaMemcpyAsync(boff.p, off.data(), (nbox + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
-  k_box_ids<<<grid(N), 256, 0, st>>>(N, nbox, boff.p, bid.p); count_launch();
+  launch_pdl(k_box_ids, grid(N), 256, st, N, nbox, boff.p, bid.p); count_launch();
   CK(cudaStreamSynchronize(st));
   return SPH_OK;
 }
@@ -240,7 +240,7 @@ sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector
     CK(rl_tab.reserve(tab.size()));
     CK(cudaMemcpyAsync(rl_tab.p, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     const dim3 g((unsigned)std::min<long long>((maxn + 255) / 256, 64), (unsigned)nmove);
-    k_relayout<<<g, 256, 0, st>>>(rl_tab.p, x.p, v.p, m.p, u.p, h.p, hhist.p, a_in.p, rl_x.p, rl_v.p, rl_m.p,
+    launch_pdl(k_relayout, g, 256, st, rl_tab.p, x.p, v.p, m.p, u.p, h.p, hhist.p, a_in.p, rl_x.p, rl_v.p, rl_m.p,
                                   rl_u.p, rl_h.p, rl_hh.p, rl_a.p); count_launch();
   }
   const std::vector<BoxDesc> old = hbox;
@@ -257,7 +257,7 @@ sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector
   if (!boxes.empty()) {
     CK(hlev_src.reserve(boxes.size()));
     CK(cudaMemcpyAsync(hlev_src.p, srcl.data(), srcl.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
-    k_remap_hlev<<<1, 256, 0, st>>>((int)boxes.size(), hlev_src.p, hlev_old.p, hlev.p); count_launch();
+    launch_pdl(k_remap_hlev, 1, 256, st, (int)boxes.size(), hlev_src.p, hlev_old.p, hlev.p); count_launch();
     CK(cudaStreamSynchronize(st));  // srcl is a host temporary
   }
   x.swap(rl_x);
@@ -484,7 +484,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
   {
     Scope sc(this, PH_INGEST);
-    k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
+    launch_pdl(k_ingest, grid(N), 256, st, N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hbox.data(), box.p, nbox * sizeof(BoxDesc), cudaMemcpyDeviceToHost, st));
@@ -520,9 +520,9 @@ sph_status Engine::build_once(bool* retry) {
   // ---- keys and sort
   long long l0;
   int ev = prof_begin(PH_SORT, &l0);
-  k_keys<<<grid(N), 256, 0, st>>>(N, dcap, bid.p, box.p, x.p, key.p, perm.p); count_launch();
+  launch_pdl(k_keys, grid(N), 256, st, N, dcap, bid.p, box.p, x.p, key.p, perm.p); count_launch();
   radix_sort(key.p, perm.p, key_tmp.p, perm_tmp.p, N, key_bits, rs_scratch.p, st);
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+  launch_pdl(k_gather_sorted, grid(N), 256, st, N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
                                            vel4.p); count_launch();
   prof_end(PH_SORT, ev, l0);
   CK(cudaGetLastError());
@@ -532,12 +532,12 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemsetAsync(t_n.p, 0, 8 * sizeof(int), st));
   CK(cudaMemsetAsync(top_at.p, 0xff, N * sizeof(int), st));
   CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
-  k_top_nodes<<<grid(N), 256, 0, st>>>(N, dcap, box_shift, box.p, key.p, T, cap_nodes, top_at.p, err_all.p); count_launch();
-  k_frontier_init<<<1, 1, 0, st>>>(T, cap_nodes); count_launch();
+  launch_pdl(k_top_nodes, grid(N), 256, st, N, dcap, box_shift, box.p, key.p, T, cap_nodes, top_at.p, err_all.p); count_launch();
+  launch_pdl(k_frontier_init, 1, 1, st, T, cap_nodes); count_launch();
   const int rounds = dcap - kmin + 1;
   for (int r = 0; r < rounds; ++r) {
     // with a next round, the round's last block also opens that round's frontier
-    k_tree_round<<<nsm * 8, 256, 0, st>>>(T, box.p, Hs.p, key.p, dcap, prm.leaf_max, prm.split_frac,
+    launch_pdl(k_tree_round, nsm * 8, 256, st, T, box.p, Hs.p, key.p, dcap, prm.leaf_max, prm.split_frac,
                                           r + 1 < rounds ? 1 : 0, cap_nodes, err_all.p); count_launch();
   }
   prof_end(PH_TREE, ev, l0);
@@ -561,34 +561,34 @@ sph_status Engine::build_once(bool* retry) {
 
   ev = prof_begin(PH_LISTS, &l0);
   CK(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
-  k_items_top<<<grid(13ll * n_top), 256, 0, st>>>(n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
+  launch_pdl(k_items_top, grid(13ll * n_top), 256, st, n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
                                                   err_all.p); count_launch();
   for (int r = 0; r < rounds; ++r) {
     const int in = r & 1;
     CK(cudaMemsetAsync(l_counts.p + 2 + (in ^ 1), 0, sizeof(int), st));
-    k_items_expand<<<nsm * 8, 256, 0, st>>>(in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p,
+    launch_pdl(k_items_expand, nsm * 8, 256, st, in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p,
                                             prm.split_headroom); count_launch();
   }
   prof_end(PH_LISTS, ev, l0);
   ev = prof_begin(PH_SHIFT, &l0);
-  k_leaves<<<nsm * 8, 256, 0, st>>>(T, n_nodes, leaf_of.p); count_launch();
+  launch_pdl(k_leaves, nsm * 8, 256, st, T, n_nodes, leaf_of.p); count_launch();
   // particles of each leaf: the ones with H above the leaf edge last (stable)
-  k_leaf_partition<<<nsm * 8, 256, 0, st>>>(T, n_nodes, box.p, Hs.p, lsrc.p); count_launch();
-  k_apply_partition<<<grid(N), 256, 0, st>>>(N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
+  launch_pdl(k_leaf_partition, nsm * 8, 256, st, T, n_nodes, box.p, Hs.p, lsrc.p); count_launch();
+  launch_pdl(k_apply_partition, grid(N), 256, st, N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
                                              vel4.p, vel4_tmp.p); count_launch();
   perm.swap(perm_tmp);
   key.swap(key_tmp);
   Hs.swap(Hs_tmp);
   vel4.swap(vel4_tmp);
-  k_particle_limits<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, hlimp.p); count_launch();
-  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  launch_pdl(k_particle_limits, grid(N), 256, st, N, T, leaf_of.p, hlimp.p); count_launch();
+  launch_pdl(k_shift, grid(N), 256, st, N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   // clusters of at most 32 particles inside each leaf
-  k_tile_flags<<<nsm * 8, 256, 0, st>>>(T, n_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
+  launch_pdl(k_tile_flags, nsm * 8, 256, st, T, n_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
   count_launch();
   exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), st);
-  k_tile_table<<<grid(N), 256, 0, st>>>(N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL, prm.cluster_max);
+  launch_pdl(k_tile_table, grid(N), 256, st, N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL, prm.cluster_max);
   count_launch();
-  k_cell_tiles<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, tile_of.p); count_launch();
+  launch_pdl(k_cell_tiles, grid(n_nodes), 256, st, T, n_nodes, tile_of.p); count_launch();
   prof_end(PH_SHIFT, ev, l0);
 
   // ---- sorted projections
@@ -604,8 +604,8 @@ sph_status Engine::build_once(bool* retry) {
   CK(mid_seg.reserve(13 * (size_t)std::max(n_nodes, 1)));
   CK(mid_count.reserve(1));
   CK(cudaMemsetAsync(mid_count.p, 0, sizeof(unsigned int), st));
-  k_mark_axes<<<nsm * 8, 256, 0, st>>>(Lq, cap_pair, T); count_launch();
-  k_sort_alloc<<<grid(n_nodes), 256, 0, st>>>(T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
+  launch_pdl(k_mark_axes, nsm * 8, 256, st, Lq, cap_pair, T); count_launch();
+  launch_pdl(k_sort_alloc, grid(n_nodes), 256, st, T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
                                               cap_big, mid_seg.p, mid_count.p); count_launch();
   launch_task_offsets(*this);
   prof_end(PH_AXIS_SORT, ev, l0);
@@ -657,9 +657,9 @@ sph_status Engine::build_once(bool* retry) {
   CK(sort_i.reserve(std::max<long long>(n_entries, 1)));
   ev = prof_begin(PH_AXIS_SORT, &l0);
   if (prm.sort_merge)
-    k_sort_merge<<<nsm * 8, 256, 0, st>>>(mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
+    launch_pdl(k_sort_merge, nsm * 8, 256, st, mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
   else
-    k_sort_small<<<nsm * 8, 256, 0, st>>>(mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
+    launch_pdl(k_sort_small, nsm * 8, 256, st, mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
   count_launch();
   if (n_big > 0) {
     const size_t nb = (size_t)n_big_entries;
@@ -668,11 +668,11 @@ sph_status Engine::build_once(bool* retry) {
     CK(cval.reserve(nb));
     CK(cval_tmp.reserve(nb));
     if (rs_scratch.n < (size_t)radix_scratch_words(nb)) CK(rs_scratch.reserve(radix_scratch_words(nb)));
-    k_sort_big_keys<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, TL,
+    launch_pdl(k_sort_big_keys, std::min(n_big, nsm * 8), 256, st, n_big, big_node.p, big_axis.p, big_off.p, T, TL,
                                                               ckey.p, cval.p); count_launch();
     radix_sort(ckey.p, cval.p, ckey_tmp.p, cval_tmp.p, (long long)nb, 32 + std::max(1, ceil_log2(n_big)),
                rs_scratch.p, st);
-    k_sort_big_scatter<<<std::min(n_big, nsm * 8), 256, 0, st>>>(n_big, big_node.p, big_axis.p, big_off.p, T, TL,
+    launch_pdl(k_sort_big_scatter, std::min(n_big, nsm * 8), 256, st, n_big, big_node.p, big_axis.p, big_off.p, T, TL,
                                                                  cval.p, sort_r.p, sort_i.p); count_launch();
   }
   prof_end(PH_AXIS_SORT, ev, l0);
@@ -954,8 +954,8 @@ sph_status Engine::reuse_or_build() {
   CK(reuse_flag.reserve(1));
   CK(cudaMemsetAsync(dmax_bits.p, 0, nbox * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(reuse_flag.p, 0, sizeof(unsigned int), st));
-  k_displacement<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, x_build.p, dmax_bits.p); count_launch();
-  k_reuse_limits<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, T, leaf_of.p, perm.p, h.p, prm.gamma_kernel,
+  launch_pdl(k_displacement, grid(N), 256, st, N, bid.p, box.p, x.p, x_build.p, dmax_bits.p); count_launch();
+  launch_pdl(k_reuse_limits, grid(N), 256, st, N, box_shift, key.p, T, leaf_of.p, perm.p, h.p, prm.gamma_kernel,
                                           dmax_bits.p, hlimp.p, reuse_flag.p); count_launch();
   std::vector<unsigned long long> dm(nbox);
   unsigned int flag = 0;
@@ -973,13 +973,13 @@ sph_status Engine::reuse_or_build() {
     hbox[b].drift_u = (float)(d / hbox[b].L);
   }
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
-  k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+  launch_pdl(k_ingest, grid(N), 256, st, N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
+  launch_pdl(k_gather_sorted, grid(N), 256, st, N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
                                            vel4.p); count_launch();
-  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  launch_pdl(k_shift, grid(N), 256, st, N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   CK(cudaMemsetAsync(t_hmax.p, 0, n_nodes * sizeof(float), st));
-  k_leaf_hmax<<<nsm * 8, 256, 0, st>>>(T, n_nodes, Hs.p); count_launch();
-  k_tile_boxes<<<grid(32 * n_tiles), 256, 0, st>>>(n_tiles, TL, pos4.p); count_launch();
+  launch_pdl(k_leaf_hmax, nsm * 8, 256, st, T, n_nodes, Hs.p); count_launch();
+  launch_pdl(k_tile_boxes, grid(32 * n_tiles), 256, st, n_tiles, TL, pos4.p); count_launch();
   prof_end(PH_REUSE, ev, l0);
   CK(cudaGetLastError());
   built = true;
@@ -1043,8 +1043,8 @@ sph_status Engine::capture_step_graph() {
   launch_drift(*this);
   CKG(cudaMemsetAsync(dmax_bits.p, 0, nbox * sizeof(unsigned long long), st));
   CKG(cudaMemsetAsync(reuse_flag.p, 0, sizeof(unsigned int), st));
-  k_displacement<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, x_build.p, dmax_bits.p); count_launch();
-  k_reuse_limits<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, T, leaf_of.p, perm.p, h.p, prm.gamma_kernel,
+  launch_pdl(k_displacement, grid(N), 256, st, N, bid.p, box.p, x.p, x_build.p, dmax_bits.p); count_launch();
+  launch_pdl(k_reuse_limits, grid(N), 256, st, N, box_shift, key.p, T, leaf_of.p, perm.p, h.p, prm.gamma_kernel,
                                           dmax_bits.p, hlimp.p, reuse_flag.p); count_launch();
   launch_set_drift(*this);
   launch_cond_keep(*this, keep);
@@ -1063,13 +1063,13 @@ sph_status Engine::capture_step_graph() {
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   long long c1 = launch_count();
   CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
-  k_ingest<<<grid(N), 256, 0, st>>>(N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
-  k_gather_sorted<<<grid(N), 256, 0, st>>>(N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+  launch_pdl(k_ingest, grid(N), 256, st, N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p); count_launch();
+  launch_pdl(k_gather_sorted, grid(N), 256, st, N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
                                            vel4.p); count_launch();
-  k_shift<<<grid(N), 256, 0, st>>>(N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  launch_pdl(k_shift, grid(N), 256, st, N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
   CKG(cudaMemsetAsync(t_hmax.p, 0, n_nodes * sizeof(float), st));
-  k_leaf_hmax<<<nsm * 8, 256, 0, st>>>(T, n_nodes, Hs.p); count_launch();
-  k_tile_boxes<<<grid(32 * n_tiles), 256, 0, st>>>(n_tiles, TL, pos4.p); count_launch();
+  launch_pdl(k_leaf_hmax, nsm * 8, 256, st, T, n_nodes, Hs.p); count_launch();
+  launch_pdl(k_tile_boxes, grid(32 * n_tiles), 256, st, n_tiles, TL, pos4.p); count_launch();
   launch_bracket_reset(*this);
   launch_set_active(*this);
   CKG(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));

@@ -1067,6 +1067,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
                                                          unsigned int* dcnt, unsigned long long* pc,
                                                          unsigned int* __restrict__ task_ctr, int partial_host,
                                                          const int* __restrict__ it_dev) {
+  pdl_wait();
   const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
   if ((partial != 0) != PART) return;
   __shared__ DensShared SH[SPH_WARPS_PER_CTA];
@@ -1112,6 +1113,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles T
                                                        const double* __restrict__ x, float alpha, float4* facc,
                                                        float* fvsig, unsigned long long* pc,
                                                        unsigned int* __restrict__ task_ctr) {
+  pdl_wait();
   __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   ForceShared& S = SH[wl];
@@ -1157,6 +1159,7 @@ __global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles T
 template <bool DENS>
 __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
                              long long nst, int partial_host, const int* __restrict__ it_dev) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   if (it_dev && it_dev[2] != 0) return;    // the iteration has stopped: no tasks
   // later iterations keep only what still iterates (with a device counter: from iteration 2 on)
@@ -1220,6 +1223,7 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
                         const float* __restrict__ hlimp, const unsigned int* __restrict__ leaf_of, Tree T,
                         float4* __restrict__ ghost4, float4* __restrict__ hhist, int* __restrict__ n_active,
                         unsigned int* __restrict__ err_all) {
+  pdl_wait();
   // the iteration number: the host's, or in a captured step the device counter
   const int it = it_dev ? *it_dev : it_host;
   if (it_dev && it_dev[2] != 0) return;    // the iteration has stopped (batched iterations)
@@ -1286,6 +1290,7 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
 
 __global__ void k_zero_active(long long N, const unsigned char* __restrict__ act, float4* __restrict__ dacc,
                               unsigned int* __restrict__ dcnt, int all) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     if (all || act[p]) {
       dacc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1302,6 +1307,7 @@ __global__ void k_zero_active(long long N, const unsigned char* __restrict__ act
 // to every cell on its chain with ordered-key atomics.
 __global__ void k_mark_active(long long ntile, const unsigned char* __restrict__ act,
                               const float4* __restrict__ pos4, Tree T, Tiles TL) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1344,6 +1350,7 @@ __global__ void k_mark_active(long long ntile, const unsigned char* __restrict__
 // interaction over the whole list capacity (zero past the list), so that the
 // prefix and the task totals are ready before the host reads the list sizes.
 __global__ void k_task_tiles(Lists Lq, Tree T, int cap_pair, int cap_self) {
+  pdl_wait();
   const int npair = min(Lq.counts[1], cap_pair), nself = min(Lq.counts[0], cap_self);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cap_pair + cap_self; i += gridDim.x * blockDim.x) {
     if (i < cap_pair) Lq.p_toff[i] = i < npair ? T.ntile[Lq.pair_a[i]] : 0u;
@@ -1353,6 +1360,7 @@ __global__ void k_task_tiles(Lists Lq, Tree T, int cap_pair, int cap_self) {
 
 // task -> interaction tables (one warp per interaction)
 __global__ void k_task_items(Lists Lq, Tree T, int npair, int nself) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1367,6 +1375,7 @@ __global__ void k_task_items(Lists Lq, Tree T, int npair, int nself) {
 }
 
 __global__ void k_count_unconverged(long long N, const int* __restrict__ conv, int* __restrict__ out) {
+  pdl_wait();
   int c = 0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
     c += conv[p] ? 0 : 1;
@@ -1376,11 +1385,13 @@ __global__ void k_count_unconverged(long long N, const int* __restrict__ conv, i
 }
 
 __global__ void k_set_active(long long N, unsigned char* __restrict__ act) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
     act[p] = 1;
 }
 
 __global__ void k_h_bracket_reset(long long N, float* __restrict__ hlo, float* __restrict__ hhi, int* __restrict__ conv) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     hlo[p] = 0.0f;
     hhi[p] = __int_as_float(0x7f800000);
@@ -1392,11 +1403,13 @@ __global__ void k_h_bracket_reset(long long N, float* __restrict__ hlo, float* _
 // Conditions of a step captured as a CUDA graph with conditional nodes (one
 // thread each).  keep: the decomposition stays (no particle outgrew the limits).
 __global__ void k_cond_keep(cudaGraphConditionalHandle keep, const unsigned int* __restrict__ reuse_flag) {
+  pdl_wait();
   cudaGraphSetConditional(keep, *reuse_flag == 0u ? 1u : 0u);
 }
 
 // start of the h iteration: iteration 1 runs
 __global__ void k_iter_start(cudaGraphConditionalHandle iter, int* __restrict__ it_dev) {
+  pdl_wait();
   it_dev[0] = 1;
   it_dev[2] = 0;
   cudaGraphSetConditional(iter, 1u);
@@ -1408,6 +1421,7 @@ __global__ void k_iter_start(cudaGraphConditionalHandle iter, int* __restrict__ 
 // return at once after a stop.
 __global__ void k_iter_step(int* __restrict__ it_dev, int* __restrict__ n_active,
                             const unsigned int* __restrict__ err_all, int max_iter) {
+  pdl_wait();
   if (it_dev[2] != 0) return;
   const int na = *n_active;
   if (it_dev[0] == 1) it_dev[1] = na;
@@ -1423,6 +1437,7 @@ __global__ void k_iter_step(int* __restrict__ it_dev, int* __restrict__ n_active
 __global__ void k_iter_next(cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force, int* __restrict__ it_dev,
                             int* __restrict__ n_active, const unsigned int* __restrict__ err_all, int max_iter,
                             int* __restrict__ first_active) {
+  pdl_wait();
   const bool rebuild = (*err_all & ERR_REBUILD) != 0u;
   const int na = *n_active;
   if (*it_dev == 1) *first_active = na;
@@ -1435,6 +1450,7 @@ __global__ void k_iter_next(cudaGraphConditionalHandle iter, cudaGraphConditiona
 
 // the displacement of every box, written into its descriptor on the device
 __global__ void k_set_drift(int nbox, BoxDesc* __restrict__ box, const unsigned long long* __restrict__ dmax) {
+  pdl_wait();
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
     const double d = __longlong_as_double((long long)dmax[b]);
     box[b].drift2 = (float)(2.0 * d);
@@ -1450,6 +1466,7 @@ __global__ void k_set_drift(int nbox, BoxDesc* __restrict__ box, const unsigned 
 __global__ void __launch_bounds__(256) k_reduce(int nbox, const long long* __restrict__ boff,
                                                 const float4* __restrict__ cen4, const float4* __restrict__ vel4,
                                                 const float4* __restrict__ facc, double* __restrict__ red) {
+  pdl_wait();
   __shared__ double part[8][8];
   for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
     const long long p0 = boff[b], p1 = boff[b + 1];
@@ -1491,6 +1508,7 @@ __global__ void __launch_bounds__(256) k_reduce(int nbox, const long long* __res
 // accelerations of the last force pass, kept in caller order for the next kick
 __global__ void k_save_acc(long long N, const unsigned int* __restrict__ perm, const float4* __restrict__ facc,
                            float4* __restrict__ a_in) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
     a_in[perm[p]] = facc[p];
 }
@@ -1498,6 +1516,7 @@ __global__ void k_save_acc(long long N, const unsigned int* __restrict__ perm, c
 // caller-order (a, du/dt) into the saved accelerations: which = 0 sets a (n x 3), 1 sets du/dt
 __global__ void k_set_acc(long long off, long long n, int which, const float* __restrict__ src,
                           float4* __restrict__ a_in) {
+  pdl_wait();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     float4 a = a_in[off + q];
     if (which == 0) {
@@ -1512,12 +1531,13 @@ __global__ void k_set_acc(long long off, long long n, int which, const float* __
 }
 
 void launch_set_acc(Engine& E, long long off, long long n, int which, const float* src) {
-  k_set_acc<<<E.grid(n), 256, 0, E.st>>>(off, n, which, src, E.a_in.p); count_launch();
+  launch_pdl(k_set_acc, E.grid(n), 256, E.st, off, n, which, src, E.a_in.p); count_launch();
 }
 
 // half kick with the box's dt: v += a dt/2, u += du/dt dt/2 (u kept >= 0)
 __global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                        const float4* __restrict__ a_in, float* __restrict__ v, float* __restrict__ u) {
+  pdl_wait();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const float hdt = (float)(0.5 * box[bid[i]].dt);
     if (hdt == 0.0f) continue;
@@ -1542,6 +1562,7 @@ __global__ void k_kick(long long N, const int* __restrict__ bid, const BoxDesc* 
 __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc* __restrict__ box,
                         double* __restrict__ x, const float* __restrict__ v, float* __restrict__ h,
                         float4* __restrict__ hhist, const int* __restrict__ hlev) {
+  pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const int b = bid[p];
     const BoxDesc& bd = box[b];
@@ -1581,6 +1602,7 @@ __global__ void k_drift(long long N, const int* __restrict__ bid, const BoxDesc*
 // load and the final store: the FP32 pipe's throughput.  The store depends on
 // every chain so the compiler keeps them.
 __global__ void __launch_bounds__(256) k_fma_peak(int iters, float a, float b, float* __restrict__ out) {
+  pdl_wait();
   float v[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = (float)(threadIdx.x + k) * 1e-3f;
@@ -1620,6 +1642,7 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
                             const unsigned int* __restrict__ dcnt, const float4* __restrict__ ghost4,
                             const float4* __restrict__ facc, const float* __restrict__ fvsig,
                             const float* __restrict__ h, float gamma_gas, void* out) {
+  pdl_wait();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long p = off + q;
     const long long i = (long long)perm[p] - off;
@@ -1676,10 +1699,10 @@ void launch_live_tasks(Engine& E, bool dens, const int* it_dev) {
   if (n == 0) return;
   const int grid = (int)std::min<long long>((n + 255) / 256, (long long)E.nsm * 16);
   if (dens)
-    k_live_tasks<true><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, E.partial_pass,
+    launch_pdl(k_live_tasks<true>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, E.partial_pass,
                                                 it_dev);
   else
-    k_live_tasks<false><<<grid, 256, 0, E.st>>>(E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, 0, nullptr);
+    launch_pdl(k_live_tasks<false>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, 0, nullptr);
   count_launch();
 }
 
@@ -1697,7 +1720,7 @@ void launch_density(Engine& E, const int* it_dev) {
     else
       k = E.count_pairs ? (part ? k_density<true, true, false> : k_density<true, false, false>)
                         : (part ? k_density<false, true, false> : k_density<false, false, false>);
-    k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+    launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
         E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
         E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev);
     count_launch();
@@ -1707,14 +1730,14 @@ void launch_density(Engine& E, const int* it_dev) {
 void launch_force(Engine& E) {
   const auto k = E.count_pairs ? k_force<true> : k_force<false>;
   cudaMemsetAsync(E.task_ctr.p + 1, 0, sizeof(unsigned int), E.st);
-  k<<<E.nsm * resident_ctas((const void*)k), SPH_THREADS, 0, E.st>>>(
+  launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
       E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p, E.x.p,
       E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 1);
   count_launch();
 }
 
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev) {
-  k_ghost<<<E.grid(E.N), 256, 0, E.st>>>(E.N, mode, it, it_dev, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
+  launch_pdl(k_ghost, E.grid(E.N), 256, E.st, E.N, mode, it, it_dev, E.prm.h_max_iter, E.prm.gamma_kernel, E.prm.n_ngb,
                                           E.prm.h_tol, E.prm.gamma_gas, E.perm.p, E.Hs.p, E.pos4.p, E.cen4.p,
                                           E.vel4.p, E.dacc.p, E.act.p, E.h.p, E.hlo.p, E.hhi.p, E.conv.p,
                                           E.hlimp.p, E.leaf_of.p, E.T, E.ghost4.p, E.hhist.p, E.dev_counters.p,
@@ -1722,18 +1745,18 @@ void launch_ghost(Engine& E, int mode, int it, const int* it_dev) {
 }
 
 void launch_zero_density(Engine& E, bool all) {
-  k_zero_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p, E.dacc.p, E.dcnt.p, all ? 1 : 0); count_launch();
+  launch_pdl(k_zero_active, E.grid(E.N), 256, E.st, E.N, E.act.p, E.dacc.p, E.dcnt.p, all ? 1 : 0); count_launch();
 }
 
 void launch_set_active(Engine& E) {
   E.partial_pass = 0;
-  k_set_active<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.act.p); count_launch();
+  launch_pdl(k_set_active, E.grid(E.N), 256, E.st, E.N, E.act.p); count_launch();
   cudaMemsetAsync(E.t_active.p, 1, E.n_nodes, E.st);
   cudaMemsetAsync(E.tl_active.p, 1, E.n_tiles, E.st);
 }
 
 void launch_count_unconverged(Engine& E, int* out) {
-  k_count_unconverged<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.conv.p, out); count_launch();
+  launch_pdl(k_count_unconverged, E.grid(E.N), 256, E.st, E.N, E.conv.p, out); count_launch();
 }
 
 void launch_mark_active_cells(Engine& E) {
@@ -1742,12 +1765,12 @@ void launch_mark_active_cells(Engine& E) {
   cudaMemsetAsync(E.tl_active.p, 0, E.n_tiles, E.st);
   cudaMemsetAsync(E.t_alo.p, 0xff, 3 * (size_t)E.n_nodes * sizeof(unsigned int), E.st);
   cudaMemsetAsync(E.t_ahi.p, 0, 3 * (size_t)E.n_nodes * sizeof(unsigned int), E.st);
-  k_mark_active<<<E.grid(32 * E.n_tiles), 256, 0, E.st>>>(E.n_tiles, E.act.p, E.pos4.p, E.T, E.TL);
+  launch_pdl(k_mark_active, E.grid(32 * E.n_tiles), 256, E.st, E.n_tiles, E.act.p, E.pos4.p, E.T, E.TL);
   count_launch();
 }
 
 void launch_task_offsets(Engine& E) {
-  k_task_tiles<<<E.grid(E.cap_pair + E.cap_self), 256, 0, E.st>>>(E.Lq, E.T, E.cap_pair, E.cap_self); count_launch();
+  launch_pdl(k_task_tiles, E.grid(E.cap_pair + E.cap_self), 256, E.st, E.Lq, E.T, E.cap_pair, E.cap_self); count_launch();
   exclusive_scan(E.Lq.p_toff, E.Lq.p_toff, E.cap_pair, E.scan_tmp.p,
                  reinterpret_cast<unsigned int*>(E.Lq.counts + 6), E.st);
   exclusive_scan(E.Lq.s_toff, E.Lq.s_toff, E.cap_self, E.scan_tmp.p,
@@ -1755,11 +1778,11 @@ void launch_task_offsets(Engine& E) {
 }
 
 void launch_task_items(Engine& E) {
-  k_task_items<<<E.nsm * 8, 256, 0, E.st>>>(E.Lq, E.T, E.n_pairs, E.n_selfs); count_launch();
+  launch_pdl(k_task_items, E.nsm * 8, 256, E.st, E.Lq, E.T, E.n_pairs, E.n_selfs); count_launch();
 }
 
 void launch_bracket_reset(Engine& E) {
-  k_h_bracket_reset<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.hlo.p, E.hhi.p, E.conv.p); count_launch();
+  launch_pdl(k_h_bracket_reset, E.grid(E.N), 256, E.st, E.N, E.hlo.p, E.hhi.p, E.conv.p); count_launch();
 }
 
 void launch_reduce(Engine& E) {
@@ -1767,37 +1790,38 @@ void launch_reduce(Engine& E) {
   long long maxn = 1;
   for (int b = 0; b < E.nbox; ++b) maxn = std::max(maxn, E.spec[b].n);
   const int gx = (int)std::max<long long>(1, std::min<long long>((maxn + 255) / 256, (E.nsm * 4 + E.nbox - 1) / E.nbox));
-  k_reduce<<<dim3(gx, std::min(E.nbox, 65535)), 256, 0, E.st>>>(E.nbox, E.boff.p, E.cen4.p, E.vel4.p, E.facc.p,
+  launch_pdl(k_reduce, dim3(gx, std::min(E.nbox, 65535)), 256, E.st, E.nbox, E.boff.p, E.cen4.p, E.vel4.p, E.facc.p,
                                                                  E.red.p); count_launch();
 }
 
 void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep) {
-  k_cond_keep<<<1, 1, 0, E.st>>>(keep, E.reuse_flag.p); count_launch();
+  launch_pdl(k_cond_keep, 1, 1, E.st, keep, E.reuse_flag.p); count_launch();
 }
 
 void launch_iter_start(Engine& E, cudaGraphConditionalHandle iter) {
-  k_iter_start<<<1, 1, 0, E.st>>>(iter, E.it_dev.p); count_launch();
+  launch_pdl(k_iter_start, 1, 1, E.st, iter, E.it_dev.p); count_launch();
 }
 
 void launch_iter_step(Engine& E) {
-  k_iter_step<<<1, 1, 0, E.st>>>(E.it_dev.p, E.dev_counters.p, E.err_all.p, E.prm.h_max_iter); count_launch();
+  launch_pdl(k_iter_step, 1, 1, E.st, E.it_dev.p, E.dev_counters.p, E.err_all.p, E.prm.h_max_iter); count_launch();
 }
 
 void launch_iter_next(Engine& E, cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force) {
-  k_iter_next<<<1, 1, 0, E.st>>>(iter, force, E.it_dev.p, E.dev_counters.p, E.err_all.p, E.prm.h_max_iter,
+  launch_pdl(k_iter_next, 1, 1, E.st, iter, force, E.it_dev.p, E.dev_counters.p, E.err_all.p, E.prm.h_max_iter,
                                  E.it_dev.p + 1); count_launch();
 }
 
 void launch_set_drift(Engine& E) {
-  k_set_drift<<<1, 256, 0, E.st>>>(E.nbox, E.box.p, E.dmax_bits.p); count_launch();
+  launch_pdl(k_set_drift, 1, 256, E.st, E.nbox, E.box.p, E.dmax_bits.p); count_launch();
 }
 
-void launch_save_acc(Engine& E) { k_save_acc<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.perm.p, E.facc.p, E.a_in.p); count_launch(); }
+void launch_save_acc(Engine& E) { launch_pdl(k_save_acc, E.grid(E.N), 256, E.st, E.N, E.perm.p, E.facc.p, E.a_in.p); count_launch(); }
 
-void launch_kick(Engine& E) { k_kick<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); count_launch(); }
+void launch_kick(Engine& E) { launch_pdl(k_kick, E.grid(E.N), 256, E.st, E.N, E.bid.p, E.box.p, E.a_in.p, E.v.p, E.u.p); count_launch(); }
 
 // one more root kept by every moving box (the ghost pass of the step writes it)
 __global__ void k_hlev_next(int nbox, const BoxDesc* __restrict__ box, int* __restrict__ hlev) {
+  pdl_wait();
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x)
     if (box[b].dt != 0.0) hlev[b] = min(hlev[b] + 1, 3);
 }
@@ -1805,6 +1829,7 @@ __global__ void k_hlev_next(int nbox, const BoxDesc* __restrict__ box, int* __re
 // history levels of the boxes of a new layout: a moved box keeps its own
 __global__ void k_remap_hlev(int nbox, const long long* __restrict__ src_tab, const int* __restrict__ old_lev,
                              int* __restrict__ lev) {
+  pdl_wait();
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
     const long long s = src_tab[b];
     lev[b] = s >= 0 ? old_lev[s] : 0;
@@ -1813,6 +1838,7 @@ __global__ void k_remap_hlev(int nbox, const long long* __restrict__ src_tab, co
 
 // h of one box set from src (device); the box's root history restarts when any h changes
 __global__ void k_set_h(long long n, const float* __restrict__ src, float* __restrict__ h, int* __restrict__ hlev) {
+  pdl_wait();
   bool diff = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float s = src[i];
@@ -1823,19 +1849,19 @@ __global__ void k_set_h(long long n, const float* __restrict__ src, float* __res
 }
 
 void launch_drift(Engine& E) {
-  k_drift<<<E.grid(E.N), 256, 0, E.st>>>(E.N, E.bid.p, E.box.p, E.x.p, E.v.p, E.h.p, E.hhist.p, E.hlev.p);
+  launch_pdl(k_drift, E.grid(E.N), 256, E.st, E.N, E.bid.p, E.box.p, E.x.p, E.v.p, E.h.p, E.hhist.p, E.hlev.p);
   count_launch();
-  k_hlev_next<<<1, 256, 0, E.st>>>(E.nbox, E.box.p, E.hlev.p); count_launch();
+  launch_pdl(k_hlev_next, 1, 256, E.st, E.nbox, E.box.p, E.hlev.p); count_launch();
 }
 
 void launch_set_h(Engine& E, int b, const float* src) {
   const long long n = E.spec[b].n;
   if (n == 0) return;
-  k_set_h<<<E.grid(n), 256, 0, E.st>>>(n, src, E.h.p + E.off[b], E.hlev.p + b); count_launch();
+  launch_pdl(k_set_h, E.grid(n), 256, E.st, n, src, E.h.p + E.off[b], E.hlev.p + b); count_launch();
 }
 
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out) {
-  k_get_field<<<E.grid(n), 256, 0, E.st>>>(off, n, field, E.perm.p, E.Hs.p, E.cen4.p, E.vel4.p, E.dacc.p, E.dcnt.p,
+  launch_pdl(k_get_field, E.grid(n), 256, E.st, off, n, field, E.perm.p, E.Hs.p, E.cen4.p, E.vel4.p, E.dacc.p, E.dcnt.p,
                                            E.ghost4.p, E.facc.p, E.fvsig.p, E.h.p, E.prm.gamma_gas, out); count_launch();
 }
 

@@ -3,6 +3,39 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <utility>
+
+// Programmatic dependent launch.  The library's kernels are launched with
+// programmatic stream serialisation (launch_pdl), so that a kernel's launch
+// overlaps the end of the kernel before it in the stream instead of starting
+// after it.  Every kernel begins with pdl_wait(), which blocks until the
+// previous grid has completed and its memory writes are visible: each kernel
+// still sees all the work issued before it, as in plain stream order.  No
+// kernel signals its dependents early.  While the stream is being captured into
+// a graph the launches are plain (the captured step keeps ordinary edges).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) {
+    kernel<<<grid, block, 0, st>>>(std::forward<Args>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 #define SPH_MAX_DEPTH 20          // bits per dimension of the Morton code
 #define SPH_WARPS_PER_CTA 4

@@ -100,7 +100,7 @@ const char* const kPhaseNames[PH_COUNT] = {"ingest",     "keys_sort",   "tree", 
                                            "ghost",      "force",       "force_tasks", "reduce",
                                            "kick_drift", "output",      "reuse"};
 
-int Engine::prof_begin(int phase, long long* l0) {
+int Engine::prof_begin(int phase, long long* l0, cudaStream_t on) {
   *l0 = launch_count();
   if (!prof) return -1;
   while (ev_pool.size() < ev_used + 2) {
@@ -110,14 +110,14 @@ int Engine::prof_begin(int phase, long long* l0) {
   }
   const int ev = (int)ev_used;
   ev_used += 2;
-  cudaEventRecord(ev_pool[ev], st);
+  cudaEventRecord(ev_pool[ev], on ? on : st);
   (void)phase;
   return ev;
 }
 
-void Engine::prof_end(int phase, int ev, long long l0) {
+void Engine::prof_end(int phase, int ev, long long l0, cudaStream_t on) {
   if (!prof || ev < 0) return;
-  cudaEventRecord(ev_pool[ev + 1], st);
+  cudaEventRecord(ev_pool[ev + 1], on ? on : st);
   prof_recs.push_back(ProfRec{phase, ev, launch_count() - l0});
 }
 
@@ -155,6 +155,17 @@ Engine::Engine(const sph_params& p, int dev, cudaStream_t s) : prm(p), device(de
 Engine::~Engine() {
   drop_step_graph();
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (st_side) cudaStreamDestroy(st_side);
+}
+
+sph_status Engine::ensure_side_stream() {
+  if (st_side) return SPH_OK;
+  CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&st_side, cudaStreamNonBlocking));
+  return SPH_OK;
 }
 
 int Engine::grid(long long work, int threads) const {
@@ -559,6 +570,18 @@ sph_status Engine::build_once(bool* retry) {
   n_nodes = tn[0];
   n_top = tn[3];
 
+  // The interaction lists (on st) and the particles' leaf order, cell-relative
+  // offsets and clusters (on the side stream) read the tree and nothing the other
+  // writes: they run concurrently and join before the particles' H limits (which
+  // read the limits the list rounds leave in the cells) and the axis sorts.  The
+  // lists are enqueued first: k_items_top reads the particle keys by the pointer
+  // it is given, and the leaf partition then writes a new key array in their place.
+  {
+    sph_status s = ensure_side_stream();
+    if (s != SPH_OK) return s;
+  }
+  CK(cudaEventRecord(ev_fork, st));
+  CK(cudaStreamWaitEvent(st_side, ev_fork, 0));
   ev = prof_begin(PH_LISTS, &l0);
   CK(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
   launch_pdl(k_items_top, grid(13ll * n_top), 256, st, n_top, T, box.p, key.p, top_at.p, dcap, box_shift, Lq, cap_queue,
@@ -570,25 +593,31 @@ sph_status Engine::build_once(bool* retry) {
                                             prm.split_headroom); count_launch();
   }
   prof_end(PH_LISTS, ev, l0);
-  ev = prof_begin(PH_SHIFT, &l0);
-  launch_pdl(k_leaves, nsm * 8, 256, st, T, n_nodes, leaf_of.p); count_launch();
+  cudaStream_t ss = st_side;
+  ev = prof_begin(PH_SHIFT, &l0, ss);
+  launch_pdl(k_leaves, nsm * 8, 256, ss, T, n_nodes, leaf_of.p); count_launch();
   // particles of each leaf: the ones with H above the leaf edge last (stable)
-  launch_pdl(k_leaf_partition, nsm * 8, 256, st, T, n_nodes, box.p, Hs.p, lsrc.p); count_launch();
-  launch_pdl(k_apply_partition, grid(N), 256, st, N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
-                                             vel4.p, vel4_tmp.p); count_launch();
+  launch_pdl(k_leaf_partition, nsm * 8, 256, ss, T, n_nodes, box.p, Hs.p, lsrc.p); count_launch();
+  launch_pdl(k_apply_partition, grid(N), 256, ss, N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
+             vel4.p, vel4_tmp.p); count_launch();
   perm.swap(perm_tmp);
   key.swap(key_tmp);
   Hs.swap(Hs_tmp);
   vel4.swap(vel4_tmp);
-  launch_pdl(k_particle_limits, grid(N), 256, st, N, T, leaf_of.p, hlimp.p); count_launch();
-  launch_pdl(k_shift, grid(N), 256, st, N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p, cen4.p); count_launch();
+  launch_pdl(k_shift, grid(N), 256, ss, N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p,
+             cen4.p); count_launch();
   // clusters of at most 32 particles inside each leaf
-  launch_pdl(k_tile_flags, nsm * 8, 256, st, T, n_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
+  launch_pdl(k_tile_flags, nsm * 8, 256, ss, T, n_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
   count_launch();
-  exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), st);
-  launch_pdl(k_tile_table, grid(N), 256, st, N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL, prm.cluster_max);
+  exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), ss);
+  launch_pdl(k_tile_table, grid(N), 256, ss, N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL, prm.cluster_max);
   count_launch();
-  launch_pdl(k_cell_tiles, grid(n_nodes), 256, st, T, n_nodes, tile_of.p); count_launch();
+  launch_pdl(k_cell_tiles, grid(n_nodes), 256, ss, T, n_nodes, tile_of.p); count_launch();
+  prof_end(PH_SHIFT, ev, l0, ss);
+  CK(cudaEventRecord(ev_join, ss));
+  CK(cudaStreamWaitEvent(st, ev_join, 0));
+  ev = prof_begin(PH_SHIFT, &l0);
+  launch_pdl(k_particle_limits, grid(N), 256, st, N, T, leaf_of.p, hlimp.p); count_launch();
   prof_end(PH_SHIFT, ev, l0);
 
   // ---- sorted projections

@@ -111,6 +111,11 @@ class Engine {
   sph_params prm;
   int device = 0;
   cudaStream_t st = nullptr;
+  // Side stream of the build: after the tree, the particle-side kernels run on it
+  // while the interaction lists are built on st (fork and join by events).
+  // Created with the first build.
+  cudaStream_t st_side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int nsm = 148;
   std::string err;
   bool count_pairs = false;
@@ -239,8 +244,8 @@ class Engine {
   std::vector<ProfRec> prof_recs;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  int prof_begin(int phase, long long* l0);
-  void prof_end(int phase, int ev, long long l0);
+  int prof_begin(int phase, long long* l0, cudaStream_t on = nullptr);    // on: st when null
+  void prof_end(int phase, int ev, long long l0, cudaStream_t on = nullptr);
   void prof_reset();
   sph_status prof_read(std::vector<double>& ms, std::vector<long long>& calls, std::vector<long long>& launches);
   struct Scope {
@@ -256,6 +261,7 @@ class Engine {
   sph_status cuda_fail(cudaError_t e, const char* where);
   sph_status fail(sph_status s, const std::string& msg);
   sph_status ensure_particle_capacity();
+  sph_status ensure_side_stream();
   sph_status ensure_tree_capacity(int nodes);
   sph_status ensure_list_capacity(int selfs, int pairs, int queue);
   sph_status build_once(bool* retry);

@@ -59,7 +59,7 @@ __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigne
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
-void launch_density(Engine& E, const int* it_dev = nullptr);
+void launch_density(Engine& E, const int* it_dev = nullptr, int part = -1);
 double measure_fp32_peak(cudaStream_t st, int nsm, float* scratch);
 void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
@@ -792,8 +792,10 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
         launch_live_tasks(*this, true, it_dev.p);
       }
       {
+        // iteration it + k unless the iteration stopped earlier in the batch (its
+        // kernels then find no tasks): the pass kind is known here
         Scope sc(this, PH_DENSITY);
-        launch_density(*this, it_dev.p);
+        launch_density(*this, it_dev.p, it + k > 1 ? 1 : 0);
       }
       {
         Scope sc(this, PH_GHOST);

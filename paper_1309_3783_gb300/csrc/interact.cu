@@ -1101,8 +1101,11 @@ __global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles
 }
 
 // Force interactions of one pass: the pair and self tasks in one queue.
+// Registers capped at 64 per thread (8 blocks of 128 threads): more warps in
+// flight to hide the partner loads outweigh the few spilled values; shared
+// memory then holds 7 blocks per SM.
 template <bool COUNT>
-__global__ void __launch_bounds__(SPH_THREADS) k_force(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+__global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                        const float4* __restrict__ pos4,
                                                        const float4* __restrict__ cen4,
                                                        const float4* __restrict__ vel4,
@@ -1706,11 +1709,15 @@ void launch_live_tasks(Engine& E, bool dens, const int* it_dev) {
   count_launch();
 }
 
-void launch_density(Engine& E, const int* it_dev) {
+// One density pass.  The kernel instance (first pass or later pass) follows the
+// iteration counter it_dev when given, else E.partial_pass.  only: the instance
+// the caller knows the pass needs (-1: both, as in a captured step, where the
+// one that does not match the counter returns at once).
+void launch_density(Engine& E, const int* it_dev, int only) {
   cudaMemsetAsync(E.task_ctr.p + 0, 0, sizeof(unsigned int), E.st);
   for (int part = 0; part < 2; ++part) {
-    // on the host the pass kind is known; a captured step launches both
     if (!it_dev && part != (E.partial_pass ? 1 : 0)) continue;
+    if (it_dev && only >= 0 && part != only) continue;
     // compensated sums when asked, or (compensated < 0) from 100 neighbours on
     const bool kahan = E.prm.compensated > 0 || (E.prm.compensated < 0 && E.prm.n_ngb >= 100.0f);
     decltype(&k_density<false, false, false>) k;

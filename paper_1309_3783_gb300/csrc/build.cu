@@ -506,7 +506,10 @@ __global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc*
 // n_small = #{H < edge/2 - margin} -- and, for a split node, its children: the
 // non-empty octants, counted from the Morton digit of the next level in the
 // same pass over the node's particles (sorted keys make each octant a
-// contiguous range).  Children of one node get consecutive ids.
+// contiguous range).  Children of one node get consecutive ids.  capped: dcap is
+// a bound below the full depth (the previous build's depth plus one); a node at
+// dcap that the rule would split sets ERR_DEPTH, and the build is redone at the
+// full depth.  The deepest level of any node goes to n_nodes[5].
 constexpr int TREE_THREADS = 256;
 
 // k consecutive node ids, all or none: the count never passes the capacity, so
@@ -529,7 +532,8 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
                                                              const float* __restrict__ Hs,
                                                              const unsigned long long* __restrict__ key, int dcap,
                                                              int leaf_max, float split_frac, int allow_split,
-                                                             int cap_nodes, unsigned int* __restrict__ err_all) {
+                                                             int capped, int cap_nodes,
+                                                             unsigned int* __restrict__ err_all) {
   pdl_wait();
   constexpr int NW = TREE_THREADS / 32;
   __shared__ float s_hm[NW];
@@ -610,6 +614,9 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
       }
       if (lane == 0) {
         if (sp && !fits) atomicOr(err_all, ERR_OVERFLOW);
+        if (capped && d >= dcap && (int)c > leaf_max && (double)ns > (double)split_frac * (double)c)
+          atomicOr(err_all, ERR_DEPTH);
+        atomicMax(&T.n_nodes[5], d);
         T.hmax[id] = hm;
         T.nsmall[id] = ns;
         T.split[id] = (sp && fits) ? 1 : 0;

@@ -30,7 +30,7 @@ __global__ void k_gather_sorted(long long, const unsigned int*, const float*, co
 __global__ void k_top_nodes(long long, int, int, const BoxDesc*, const unsigned long long*, Tree, int, int*,
                             unsigned int*);
 __global__ void k_tree_round(Tree, const BoxDesc*, const float*, const unsigned long long*, int, int, float, int,
-                             int, unsigned int*);
+                             int, int, unsigned int*);
 __global__ void k_frontier_init(Tree, int);
 __global__ void k_items_top(int, Tree, const BoxDesc*, const unsigned long long*, const int*, int, int, Lists, int,
                             unsigned int*);
@@ -193,6 +193,7 @@ size_t Engine::footprint_bytes() const {
 
 sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
   spec = boxes;
+  depth_hint = 0;           // new boxes: the first build takes the full depth
   nbox = (int)boxes.size();
   off.assign(nbox + 1, 0);
   for (int b = 0; b < nbox; ++b) off[b + 1] = off[b] + boxes[b].n;
@@ -523,7 +524,13 @@ sph_status Engine::build_once(bool* retry) {
     const int dn = (int)std::ceil(std::log2(d.L / (double)d.Hmin)) + 1;
     need = std::max(need, dn);
   }
-  dcap = std::max(std::min(dc, need), kmax);
+  // The deepest level a split could reach bounds the key width; while the boxes
+  // stay the same, the previous build's deepest level plus one bounds it tighter
+  // (fewer key bits to sort, fewer tree and list rounds).  A split that this bound
+  // blocks sets ERR_DEPTH in the tree rounds and the build is redone at the full depth.
+  const int dcap_full = std::max(std::min(dc, need), kmax);
+  dcap = depth_hint > 0 ? std::max(kmax, std::min(dcap_full, depth_hint + 1)) : dcap_full;
+  const int capped = dcap < dcap_full ? 1 : 0;
   box_shift = 3 * dcap;
   key_bits = box_bits + 3 * dcap;
   CK(cudaMemcpyAsync(box.p, hbox.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, st));
@@ -549,7 +556,7 @@ sph_status Engine::build_once(bool* retry) {
   for (int r = 0; r < rounds; ++r) {
     // with a next round, the round's last block also opens that round's frontier
     launch_pdl(k_tree_round, nsm * 8, 256, st, T, box.p, Hs.p, key.p, dcap, prm.leaf_max, prm.split_frac,
-                                          r + 1 < rounds ? 1 : 0, cap_nodes, err_all.p); count_launch();
+               r + 1 < rounds ? 1 : 0, capped, cap_nodes, err_all.p); count_launch();
   }
   prof_end(PH_TREE, ev, l0);
   CK(cudaGetLastError());
@@ -561,14 +568,21 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemcpyAsync(tn, t_n.p, sizeof(tn), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (ea[0] & ERR_DEPTH) depth_hint = 0;     // the bound blocked a split: full depth
   if ((ea[0] & ERR_OVERFLOW) || tn[0] > cap_nodes) {
     sph_status s = ensure_tree_capacity(std::max(2 * cap_nodes, tn[0] + 1024));
     if (s != SPH_OK) return s;
     *retry = true;
     return SPH_OK;
   }
+  if (ea[0] & ERR_DEPTH) {
+    *retry = true;
+    return SPH_OK;
+  }
   n_nodes = tn[0];
   n_top = tn[3];
+  depth_used = tn[5];
+  depth_hint = tn[5];
 
   // The interaction lists (on st) and the particles' leaf order, cell-relative
   // offsets and clusters (on the side stream) read the tree and nothing the other
@@ -706,7 +720,6 @@ sph_status Engine::build_once(bool* retry) {
   }
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
-  depth_used = 0;
   built = true;
   // positions of this decomposition, for the displacement test of a later reuse
   CK(cudaMemcpyAsync(x_build.p, x.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1402,7 +1415,7 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->n_sort_segments = n_segments;
   o->n_sorted_entries = n_entries;
   o->top_level = hbox.empty() ? 0 : hbox[b].k;
-  o->depth = dcap;
+  o->depth = depth_used;
   o->h_iterations = last_iters;
   o->rebuilds = last_rebuilds;
   o->builds = n_builds;

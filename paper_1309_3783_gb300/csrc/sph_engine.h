@@ -216,7 +216,9 @@ class Engine {
   DBuf<unsigned char> staging_many;   // one region per field of a multi-field read
 
   // host mirrors of counts after the last build
-  int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0, depth_used = 0;
+  int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0;
+  int depth_used = 0;       // deepest level holding a cell in the last build
+  int depth_hint = 0;       // the depth bound of the next build is this plus one (0: none)
   long long n_entries = 0, n_big_entries = 0;
   int last_iters = 0, last_rebuilds = 0;
   long long first_active = 0;     // particles still iterating after the first density pass

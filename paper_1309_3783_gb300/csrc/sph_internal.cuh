@@ -49,6 +49,7 @@ enum : unsigned int {
   ERR_H_TOO_LARGE = 2u,      // top grid cannot hold H_max
   ERR_OVERFLOW = 4u,         // a device list exceeded its capacity
   ERR_REBUILD = 8u,          // some H outgrew what the cell splits assumed
+  ERR_DEPTH = 16u,           // a split was blocked by a depth bound below the full depth
 };
 
 // One box of a batch.  Particles of box b occupy [off, off + n) both in the
@@ -220,7 +221,8 @@ struct Tree {
   unsigned int* tile0;      // first cluster of the cell (clusters of a cell are contiguous)
   unsigned int* ntile;      // clusters of the cell
   int* n_nodes;             // [0] nodes in use, [1] first node of the frontier, [2] end of frontier,
-                            // [3] top cells, [4] blocks done with the current tree round
+                            // [3] top cells, [4] blocks done with the current tree round,
+                            // [5] deepest level holding a cell
 };
 
 // Clusters: runs of at most 32 (the cluster size) consecutive particles of one leaf (particles of a

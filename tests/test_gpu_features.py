@@ -425,3 +425,45 @@ def test_server_tree_grows_past_its_first_capacity(api):
     np.testing.assert_allclose(got["h"], ref["h"], rtol=1e-4)
     np.testing.assert_allclose(got["rho"], ref["rho"], rtol=1e-3)
     assert np.mean(got["count"] != ref["count"]) < 2e-3
+
+
+def test_depth_bound_too_shallow_redoes_the_build(api):
+    """A box's next build bounds the tree depth by its last build's deepest level
+    plus one (fewer key bits to sort, fewer rounds).  A box first built on a
+    uniform lattice (a shallow tree), then given clustered particles that need
+    deeper cells, finds on the device that the bound blocks a split, redoes the
+    build at the full depth, and gets the decomposition and neighbour counts of a
+    fresh box."""
+    lat = inputs.lattice_box(32, jitter=0.2, seed=61)              # 32,768 particles
+    clu = inputs.plummer_box(n=32768, n_spheres=2, seed=62)
+    c = _ctx_with(api)
+    try:
+        b = api.box_from(c, lat)
+        try:
+            b.build()
+            d_lat = b.stats()["depth"]
+            assert d_lat == int(b.cells()["level"].max())
+            b.set(clu.x, clu.v, clu.m, clu.u, clu.h)
+            b.build()
+            b.density()
+            got_cells, got, d_got = b.cells(), b.get("count"), b.stats()["depth"]
+        finally:
+            b.close()
+        f = api.box_from(c, clu)
+        try:
+            f.build()
+            f.density()
+            ref_cells, ref, d_ref = f.cells(), f.get("count"), f.stats()["depth"]
+        finally:
+            f.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    assert d_got > d_lat + 1            # the bound from the lattice was too shallow
+    assert d_got == d_ref == int(ref_cells["level"].max())
+
+    def cells_key(cl):
+        return sorted(zip(cl["level"].tolist(), map(tuple, cl["ijk"].tolist()), cl["count"].tolist(),
+                          cl["split"].tolist()))
+
+    assert cells_key(got_cells) == cells_key(ref_cells)
+    np.testing.assert_array_equal(got, ref)

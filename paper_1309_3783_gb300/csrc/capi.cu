@@ -529,7 +529,8 @@ sph_status Engine::build_once(bool* retry) {
   // (fewer key bits to sort, fewer tree and list rounds).  A split that this bound
   // blocks sets ERR_DEPTH in the tree rounds and the build is redone at the full depth.
   const int dcap_full = std::max(std::min(dc, need), kmax);
-  dcap = depth_hint > 0 ? std::max(kmax, std::min(dcap_full, depth_hint + 1)) : dcap_full;
+  const bool hint = depth_hint > 0 && depth_hint_leaf == prm.leaf_max;   // a leaf size change voids it
+  dcap = hint ? std::max(kmax, std::min(dcap_full, depth_hint + 1)) : dcap_full;
   const int capped = dcap < dcap_full ? 1 : 0;
   box_shift = 3 * dcap;
   key_bits = box_bits + 3 * dcap;
@@ -583,6 +584,7 @@ sph_status Engine::build_once(bool* retry) {
   n_top = tn[3];
   depth_used = tn[5];
   depth_hint = tn[5];
+  depth_hint_leaf = prm.leaf_max;
 
   // The interaction lists (on st) and the particles' leaf order, cell-relative
   // offsets and clusters (on the side stream) read the tree and nothing the other

@@ -219,6 +219,7 @@ class Engine {
   int n_nodes = 0, n_top = 0, n_selfs = 0, n_pairs = 0, n_segments = 0, n_big = 0;
   int depth_used = 0;       // deepest level holding a cell in the last build
   int depth_hint = 0;       // the depth bound of the next build is this plus one (0: none)
+  int depth_hint_leaf = 0;  // the leaf size the hint was taken with
   long long n_entries = 0, n_big_entries = 0;
   int last_iters = 0, last_rebuilds = 0;
   long long first_active = 0;     // particles still iterating after the first density pass

@@ -59,7 +59,7 @@ __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigne
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
-void launch_density(Engine& E, const int* it_dev = nullptr, int part = -1);
+void launch_density(Engine& E, const int* it_dev = nullptr, int only = -1);
 double measure_fp32_peak(cudaStream_t st, int nsm, float* scratch);
 void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);

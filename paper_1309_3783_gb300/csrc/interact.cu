@@ -12,6 +12,7 @@
 #include "sph_engine.h"
 
 #include <cfloat>
+#include <mutex>
 
 namespace sph {
 
@@ -1679,11 +1680,14 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
 }
 
 // =========================================================================== launchers
-// CTAs of a kernel resident per SM at SPH_THREADS threads (looked up once)
+// CTAs of a kernel resident per SM at SPH_THREADS threads (looked up once; engines
+// may run in several host threads)
 static int resident_ctas(const void* fn) {
-  static const void* fns[8] = {nullptr};
-  static int val[8] = {0};
-  for (int k = 0; k < 8; ++k) {
+  static std::mutex mu;
+  static const void* fns[16] = {nullptr};   // the 8 density and 2 force instances
+  static int val[16] = {0};
+  std::lock_guard<std::mutex> lock(mu);
+  for (int k = 0; k < 16; ++k) {
     if (fns[k] == fn) return val[k];
     if (!fns[k]) {
       int nb = 0;

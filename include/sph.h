@@ -168,7 +168,10 @@ typedef struct sph_stats {
     int64_t cluster_max;        /* the box's particles per cluster (set or autotuned) */
 } sph_stats;
 
-/* Device time of one phase of the path (CUDA events on the context stream). */
+/* Device time of one phase of the path (CUDA events on the stream the phase runs
+ * on: the context stream, except `shift` -- the particle-side part of the build --
+ * which runs on the box's own side stream while `lists` runs on the context
+ * stream; the two overlap, so phase times can add up to more than the step). */
 typedef struct sph_profile_entry {
     char name[32];              /* ingest, keys_sort, tree, lists, shift, axis_sort,
                                    density (pair and self interactions),
@@ -192,7 +195,9 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out);
 
 /* Replace the context's stream with a caller-owned cudaStream_t (passed as
  * void*; NULL restores the context's own stream).  The caller keeps the stream
- * alive while the context uses it. */
+ * alive while the context uses it.  All work of a call is ordered on that stream:
+ * the part of a build that a box runs on its own side stream is forked from it
+ * and joined back into it with events. */
 sph_status sph_ctx_set_stream(sph_ctx* ctx, void* cuda_stream);
 
 /* The stream the context launches on, as a cudaStream_t cast to void*. */

@@ -257,3 +257,32 @@ def test_periodic_wrap_matches_explicit_images():
     e = sph.density(xr, mr, Hr, 3 * box.L, False, targets=np.arange(centre, centre + box.n))
     assert np.array_equal(d["count"], e["count"])
     np.testing.assert_allclose(d["rho"], e["rho"], rtol=1e-12)
+
+
+def test_sound_speed_is_the_adiabatic_pressure_derivative():
+    """c^2 = dP/drho at fixed entropy.  The adiabat is followed with the first
+    law alone, du/drho = P / rho^2 (integrated with RK4, P from the oracle), and
+    the pressure change along it is compared with the oracle's c^2: a wrong factor
+    in P (gamma for gamma - 1) or in c (a missing 1/rho or gamma) fails it."""
+    zero = np.zeros(4)
+    rho0 = np.array([0.3, 1.0, 2.5, 40.0])
+    u0 = np.array([0.2, 1.0, 3.0, 0.05])
+    P = lambda rho, u: sph.ghost(rho, zero, u)["P"]
+    dudr = lambda rho, u: P(rho, u) / rho ** 2
+
+    def along_adiabat(rho_to, steps=200):
+        rho, u = rho0.copy(), u0.copy()
+        dr = (rho_to - rho0) / steps
+        for _ in range(steps):
+            k1 = dudr(rho, u)
+            k2 = dudr(rho + dr / 2, u + dr / 2 * k1)
+            k3 = dudr(rho + dr / 2, u + dr / 2 * k2)
+            k4 = dudr(rho + dr, u + dr * k3)
+            u = u + dr / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+            rho = rho + dr
+        return P(rho, u)
+
+    eps = 1e-4
+    dPdrho = (along_adiabat(rho0 * (1 + eps)) - along_adiabat(rho0 * (1 - eps))) / (2 * eps * rho0)
+    c = sph.ghost(rho0, zero, u0)["c"]
+    np.testing.assert_allclose(c ** 2, dPdrho, rtol=1e-7)

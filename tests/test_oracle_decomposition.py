@@ -20,11 +20,13 @@ def _clustered(n, seed):
     return inputs.plummer_box(n=n, n_spheres=3, scale=0.03, seed=seed)
 
 
-@pytest.mark.parametrize("seed,leaf_max", [(1, 16), (2, 40), (3, 400)])
-def test_coverage_each_pair_exactly_once(seed, leaf_max):
+@pytest.mark.parametrize("seed,leaf_max,headroom", [(1, 16, 0.0), (2, 40, 0.0), (3, 400, 0.0), (1, 16, 0.1),
+                                                    (4, 24, 0.1)])
+def test_coverage_each_pair_exactly_once(seed, leaf_max, headroom):
+    """headroom 0 is the paper's rule; 0.1 is the library's default option."""
     box = _clustered(2500, seed)
     H = sph.support_radius(box.h)
-    D = dc.decompose(box.x, H, box.L, True, leaf_max=leaf_max)
+    D = dc.decompose(box.x, H, box.L, True, leaf_max=leaf_max, headroom=headroom)
     want = dc.interacting_pairs_brute(box.x, H, box.L, True)
     got = dc.visits(D, box.x, H, box.L, True)
     assert set(got) == want

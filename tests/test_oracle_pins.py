@@ -133,17 +133,66 @@ def test_lattice_at_rest_has_no_force():
 
 
 def test_momentum_and_energy_conservation():
+    """Pairwise antisymmetry: sum m a = 0 and sum m (v.a + du/dt) = 0 to rounding.
+    The masses differ by up to a factor 3, so that the same sums without the mass
+    factor (in the force or in the reductions) are far from zero."""
     box = inputs.lattice_box(8, jitter=0.45, seed=11, v_sigma=0.3)
-    box.u[:] = np.random.default_rng(2).uniform(0.5, 2.0, box.n).astype(np.float32)
+    rng = np.random.default_rng(2)
+    box.u[:] = rng.uniform(0.5, 2.0, box.n).astype(np.float32)
+    box.m = (box.m * rng.uniform(0.5, 1.5, box.n)).astype(np.float32)
     _, dens, g, fo = _prepare(box, tol=1e-6)
     m = box.m.astype(np.float64)
     red = sph.reductions(m, box.v, box.u, fo["a"], fo["dudt"])
     scale_p = np.sum(m * np.linalg.norm(fo["a"], axis=1))
-    scale_e = np.sum(m * np.abs(fo["dudt"]))
+    scale_e = np.sum(m * np.abs(fo["dudt"])) + np.sum(m * np.abs((box.v * fo["a"]).sum(1)))
     assert np.all(np.abs(red[0:3]) < 1e-12 * scale_p)
     assert abs(red[3]) < 1e-12 * scale_e
+    # the unweighted sums do not vanish: the mass factor is what cancels them
+    ones = np.ones(box.n)
+    unweighted = sph.reductions(ones, box.v, box.u, fo["a"], fo["dudt"])
+    assert np.linalg.norm(unweighted[0:3]) > 1e-3 * np.sum(np.linalg.norm(fo["a"], axis=1))
     # viscosity is on for approaching pairs: some particle must heat
     assert np.any(fo["dudt"] > 0) and np.all(fo["vsig"] > 0)
+
+
+def test_reductions_momentum_and_energy_closed_form():
+    """sum m v and E = sum m (v^2/2 + u) of a box moving at one velocity v0 with
+    u_i = i and masses m_i = 2 i / (n (n + 1)) (i = 1..n): total mass 1, so
+    sum m v = v0 and E = |v0|^2 / 2 + (2 n + 1) / 3 exactly.  A dropped mass
+    factor, a missing 1/2 in the kinetic term or a transposed v fails it."""
+    n = 1000
+    i = np.arange(1, n + 1, dtype=np.float64)
+    m = 2.0 * i / (n * (n + 1))
+    v0 = np.array([0.3, -1.25, 2.0])
+    v = np.tile(v0, (n, 1))
+    u = i.copy()
+    zero3 = np.zeros((n, 3))
+    red = sph.reductions(m, v, u, zero3, np.zeros(n))
+    np.testing.assert_allclose(red[4:7], v0, rtol=1e-13)
+    np.testing.assert_allclose(red[7], 0.5 * float(v0 @ v0) + (2 * n + 1) / 3.0, rtol=1e-13)
+    assert np.all(red[0:4] == 0.0)
+
+
+def test_reductions_rates_are_time_derivatives():
+    """Entries 0-3 are the time derivatives of entries 4-7 along v(t) = v + a t,
+    u(t) = u + du/dt t: sum m a = d/dt sum m v and sum m (v.a + du/dt) =
+    d/dt sum m (v^2/2 + u).  Both are polynomials of degree <= 2 in t, so a
+    centred difference is exact up to rounding; arbitrary unequal masses and
+    rates make every term count."""
+    rng = np.random.default_rng(31)
+    n = 500
+    m = rng.uniform(0.1, 3.0, n)
+    v = rng.normal(0.0, 1.0, (n, 3))
+    u = rng.uniform(0.0, 2.0, n)
+    a = rng.normal(0.0, 5.0, (n, 3))
+    dudt = rng.normal(0.0, 3.0, n)
+    red = sph.reductions(m, v, u, a, dudt)
+    eps = 1e-3
+    rp = sph.reductions(m, v + eps * a, u + eps * dudt, a, dudt)
+    rm = sph.reductions(m, v - eps * a, u - eps * dudt, a, dudt)
+    fd = (rp[4:8] - rm[4:8]) / (2 * eps)
+    scale = np.sum(m * (np.linalg.norm(a, axis=1) * (1 + np.linalg.norm(v, axis=1)) + np.abs(dudt)))
+    np.testing.assert_allclose(red[0:4], fd, rtol=0, atol=1e-11 * scale)
 
 
 def test_two_particle_closed_form():

@@ -1,16 +1,20 @@
 #!/usr/bin/env python
 """Throughput of the SPH density + force step on GB300 (one JSON line).
 
-Workload: the variable-h single box -- 262,144 particles, 50 % uniform
-background plus 16 Plummer spheres (scale radius 0.02, seeded centres),
-periodic unit box, equal masses, u = 1, v ~ N(0, 0.1), h iterated to 48
-neighbours.  The run follows the paper's protocol (fixed time step, forces on
-every particle every step): one step is a half kick, a drift, the whole
-decomposition build (keys, sort, cell tree, interaction lists, particle offsets,
-axis sorts), density with the h iteration (started from the last two steps'
-roots of N~(h) = 48, extrapolated), ghost,
-force, FP64 conservation reductions and the closing half kick.  dt is the
-Courant step of the initial state (C_CFL = 0.3).
+Workload (default): the large high-contrast box -- 33,554,432 particles, 30 %
+uniform background plus 70 % in 4096 Plummer spheres with scale radii
+log-uniform in [1e-4, 1e-2], periodic unit box, equal masses, u = 1,
+v ~ N(0, 0.1), h iterated to 48 neighbours (H spans three orders of magnitude),
+leaf size and cluster size autotuned.  ``--workload`` selects another:
+``plummer-262144`` (262,144 particles, 50 % uniform plus 16 Plummer spheres) or
+``lognormal-8388608`` (2^23 particles drawn from a log-normal field).
+
+The run follows the paper's protocol (fixed time step, forces on every particle
+every step): one step is a half kick, a drift, the whole decomposition build
+(keys, sort, cell tree, interaction lists, particle offsets, axis sorts), density
+with the h iteration (started from the last four steps' roots of N~(h) = 48,
+extrapolated with a cubic), ghost, force, FP64 conservation reductions and the
+closing half kick.  dt is the Courant step of the initial state (C_CFL = 0.3).
 
 value : particle-updates/s of a run resident in device memory.
 e2e   : the same through the C-ABI with host buffers: every step uploads the full
@@ -21,6 +25,8 @@ e2e   : the same through the C-ABI with host buffers: every step uploads the ful
 amortised: the same run with the decomposition kept over steps while it stays
         valid (sph_params.reuse, Section II-C: sorted indices re-used until the
         decomposition must be rebuilt); builds and reuses over the timed steps.
+
+workloads: the other two single-box workloads, a shorter run each.
 
 serving: the served batch -- 512 independent jittered-lattice boxes with
         particle counts log-uniform in [1k, 262k] (per-box seeds), each request
@@ -33,8 +39,8 @@ serving: the served batch -- 512 independent jittered-lattice boxes with
         plain single-box path for comparison with the batched server.
 
 ``--impl reference`` times the FP64 oracle (the only reference this method has:
-the paper publishes no code) on the host cores, on a bounded sample of the same
-workload per step.  Under torchrun (N > 1) every rank runs an independent replica
+the paper publishes no code) on the host cores, each step on a bounded sample of
+the same workload.  Under torchrun (N > 1) every rank runs an independent replica
 on its own GPU ("replicas only": the path has no exchange step).
 """
 from __future__ import annotations
@@ -58,8 +64,29 @@ from paper_1309_3783_gb300 import inputs  # noqa: E402
 
 METRIC = "SPH density+force particle-updates/s"
 UNIT = "particle-updates/s"
-WORKLOAD = "plummer-262144"
-SAMPLE_N = 16384            # the oracle's bounded sample: the same recipe at 1/16 of the particles
+
+
+def _clustered(seed):
+    return inputs.clustered_box(seed=seed)
+
+
+def _plummer(seed):
+    return inputs.plummer_box(seed=seed)
+
+
+def _lognormal(seed):
+    return inputs.lognormal_box(seed=seed)
+
+
+WORKLOADS = {
+    "clustered-33554432": (_clustered, "33,554,432 particles: 30 % uniform, 70 % in 4096 Plummer spheres with "
+                                       "scale radii log-uniform in [1e-4, 1e-2]"),
+    "plummer-262144": (_plummer, "262,144 particles: 50 % uniform, 50 % in 16 Plummer spheres of scale 0.02"),
+    "lognormal-8388608": (_lognormal, "8,388,608 particles drawn from a log-normal field (sigma 2, P(k) ~ k^-2, "
+                                      "256^3 mesh)"),
+}
+DEFAULT_WORKLOAD = "clustered-33554432"
+SAMPLE_K = 4096             # the oracle's bounded sample per step: particles nearest a drawn centre
 
 # Algorithmic FP32 operations per interacting pair, counted from the formulas
 # the kernels evaluate (mul/add = 1, FMA = 2, sqrt/rsqrt/div = 1; one branch of
@@ -85,6 +112,14 @@ def env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def host_threads():
+    """Host cores this process may run on (the oracle's k-d tree searches use them all)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 # ------------------------------------------------------------------ clocks
@@ -167,6 +202,36 @@ def replica_seed(rank):
     return 1 + rank
 
 
+# ------------------------------------------------------------------ timed runs
+def timed_steps(torch, b, dt, stream, steps, flush=None):
+    """Device time (ms) of each of `steps` steps, CUDA events on the library's stream."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            if flush is not None:
+                flush.zero_()                       # L2 flush between steps (outside the events)
+            evs[k][0].record(stream)
+        b.step(dt)
+        with torch.cuda.stream(stream):
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in evs]
+
+
+def prepare_box(sph, ctx, box, tune):
+    """Resident input state: h converged once (a simulation's previous step), the
+    split threshold and cluster size tuned for the workload, dt from the CFL rule."""
+    b = sph.Box(ctx, box.n, box.L, True)
+    b.set(box.x, box.v, box.m, box.u, box.h)
+    b.h_update()
+    leaf_max = 400
+    if tune:
+        leaf_max = b.tune()                           # untimed
+        b.h_update()
+    b.force()
+    return b, leaf_max, b.stats()["cluster_max"], b.cfl_dt()
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -185,70 +250,45 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    box = inputs.plummer_box(seed=replica_seed(rank))
+    make, recipe = WORKLOADS[args.workload]
+    box = make(replica_seed(rank))
     n = box.n
     ctx = sph.sph_ctx_create(device=local_rank)
     stream = torch.cuda.Stream()
     sph.sph_ctx_set_stream(ctx, stream.cuda_stream)
-    b = sph.Box(ctx, n, box.L, True)
-
-    # resident input state: h converged once (a simulation's previous step), dt from CFL
-    b.set(box.x, box.v, box.m, box.u, box.h)
-    b.h_update()
-    leaf_max = 400
-    if not args.no_tune:
-        leaf_max = b.tune()                           # split threshold for this workload (untimed)
-        b.h_update()
-    args.leaf_max = leaf_max
-    args.cluster_max = b.stats()["cluster_max"]        # particles per cluster (tuned with it)
-    b.force()
-    dt = b.cfl_dt()
+    b, leaf_max, cluster_max, dt = prepare_box(sph, ctx, box, not args.no_tune)
+    args.leaf_max, args.cluster_max = leaf_max, cluster_max
     torch.cuda.synchronize()
 
-    def step_device():
-        return b.step(dt)
-
     for _ in range(args.warmup):
-        step_device()
+        b.step(dt)
     torch.cuda.synchronize()
 
     # algorithmic work of one step (the same for every step): exact pair counts
     # over the step's density passes and its force pass (untimed, after the warm-up
     # so that the h iteration starts as in the timed steps)
     b.count_pairs(True)
-    b.profile(True)
-    step_device()
+    b.step(dt)
     st = b.stats()
-    b.profile(False)
     b.count_pairs(False)
-    # per step; the timed steps run the same passes (their number can differ by one
-    # pass of the few particles the h extrapolation leaves), so a launch's share is
-    # the step's flops over the timed launches per step
     flops_step = {"density": FLOPS_DENSITY_PAIR * st["density_pairs"] + FLOPS_DENSITY_SIDE * st["density_sides"],
                   "force": FLOPS_FORCE_PAIR * st["force_pairs"]}
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local_rank}")
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # inputs far larger than L2 need no flush; small ones get a 256 MB write between steps
+    big = n * 520 > 4 * 129 * 2 ** 20
+    flush = None if big else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local_rank}")
     l0 = sph.sph_launch_count()
     b.profile(True)
-    statuses = []
     with ClockSampler(local_rank) as clk:
         barrier()
         torch.cuda.profiler.start()                 # ncu --profile-from-start off captures from here
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()                       # L2 flush between steps (outside the events)
-                evs[k][0].record(stream)
-            statuses.append(step_device())
-            with torch.cuda.stream(stream):
-                evs[k][1].record(stream)
+        ms = timed_steps(torch, b, dt, stream, args.steps, flush)
         barrier()
         torch.cuda.profiler.stop()
     launches = sph.sph_launch_count() - l0
     st_last = b.stats()
     prof = b.get_profile()
     b.profile(False)
-    ms = [s.elapsed_time(e) for s, e in evs]
     total_ms = max_over_ranks(dist, sum(ms), f"cuda:{local_rank}")
     value = job_rate(world, n * args.steps, total_ms / 1e3)
 
@@ -256,8 +296,7 @@ def run_ours(args, rank, world, local_rank):
     pinned = lambda shape, dt_: torch.empty(shape, dtype=dt_).pin_memory().numpy()
     xh, vh, ah = pinned((n, 3), torch.float64), pinned((n, 3), torch.float32), pinned((n, 3), torch.float32)
     mh, uh, hh, duh = (pinned(n, torch.float32) for _ in range(4))
-    for name, buf in (("x", xh), ("v", vh), ("a", ah), ("u", uh), ("h", hh), ("dudt", duh)):
-        b.get(name, out=buf)
+    b.get_many({"x": xh, "v": vh, "a": ah, "u": uh, "h": hh, "dudt": duh})
     mh[:] = box.m
     e2e_steps = max(3, min(args.steps, 10))
     barrier()
@@ -283,18 +322,24 @@ def run_ours(args, rank, world, local_rank):
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
-            traffic = json.load(open(tpath)).get(dom)
-        except (OSError, ValueError):
+            tj = json.load(open(tpath)).get(args.workload, {})
+            if dom in tj:
+                traffic = tj[dom]
+        except (OSError, ValueError, AttributeError):
             traffic = None
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles_per_gpu": n, "h": "iterated to N~ = 48 each step, from the last four steps' roots extrapolated (cubic)",
-                   "protocol": "fixed-step kick-drift-kick run, forces on all particles every step",
-                   "dt": dt, "leaf_max": leaf_max, "cluster_max": args.cluster_max,
-                   "leaf_max_source": "autotuned" if not args.no_tune else "paper", "l2": "flushed between timed steps (256 MB write)",
+        "config": {"workload": args.workload, "recipe": recipe, "particles_per_gpu": n,
+                   "h": "iterated to N~ = 48 each step, from the last four steps' roots extrapolated (cubic)",
+                   "protocol": "fixed-step kick-drift-kick run, forces on all particles every step, decomposition "
+                               "rebuilt every step",
+                   "dt": dt, "leaf_max": leaf_max, "cluster_max": cluster_max,
+                   "leaf_max_source": "autotuned" if not args.no_tune else "paper",
+                   "l2": ("inputs larger than L2 (about 520 B per particle resident)" if big
+                          else "flushed between timed steps (256 MB write)"),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 12 + 4 + 4 + 4 + 12 + 4),
                 "d2h_bytes_per_step": n * (24 + 12 + 4 + 4 + 12 + 4), "steps": e2e_steps},
@@ -303,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
                      "flops_per_launch": flops, "avg_launch_ms": avg_ms,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)",
                      "peak_measured": fp32_measured,
+                     "frac_of_measured": achieved / fp32_measured if fp32_measured else None,
                      "peak_measured_source": "independent FMA chains on every SM (sph_measure_fp32_peak), this run"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -310,23 +356,49 @@ def run_ours(args, rank, world, local_rank):
         "pairs": {"density": st["density_pairs"], "density_candidates": st["density_candidates"],
                   "force": st["force_pairs"], "force_candidates": st["force_candidates"],
                   "guard_rechecks": st["guard_rechecks"]},
+        "decomposition": {"cells": st_last["n_cells"], "leaves": st_last["n_leaves"], "depth": st_last["depth"],
+                          "pair_interactions": st_last["n_pairs"]},
         "h_iterations_last_step": st_last["h_iterations"],
         "h_unconverged_after_first_pass": st_last["h_active_after_first"] / box.n,
     }
     out["amortised"] = run_reuse_leg(sph, torch, b, box, dt, stream, args, flush)
     out["axis_sorts"] = run_sort_leg(sph, torch, b, box, stream, args)
     b.close()
+    if not args.no_extra_workloads:
+        out["workloads"] = run_other_workloads(sph, torch, ctx, stream, args, rank)
     if not args.no_serving:
         out["serving"] = run_serving(sph, ctx)
     sph.sph_ctx_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(box)
+        out["cpu_baseline"] = cpu_baseline(box, args.workload)
     if dist is not None:
         dist.destroy_process_group()
     return out
 
 
-# ------------------------------------------------------------------ reuse
+# ------------------------------------------------------------------ other legs
+def run_other_workloads(sph, torch, ctx, stream, args, rank, steps=10, warmup=3):
+    """The other single-box workloads, a shorter run each (leaf size 400, clusters of 32)."""
+    out = {}
+    for name, (make, recipe) in WORKLOADS.items():
+        if name == args.workload:
+            continue
+        box = make(replica_seed(rank))
+        b, _, _, dt = prepare_box(sph, ctx, box, tune=False)
+        try:
+            for _ in range(warmup):
+                b.step(dt)
+            torch.cuda.synchronize()
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+            ms = timed_steps(torch, b, dt, stream, steps, flush)
+            del flush
+            out[name] = {"value": box.n * steps / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms) / steps,
+                         "steps": steps, "recipe": recipe}
+        finally:
+            b.close()
+    return out
+
+
 def run_sort_leg(sph, torch, b, box, stream, args, builds=10):
     """Device time of the axis-sort phase per build, the cell lists sorted directly
     and built by merging the leaves' sorted runs (sph_params.sort_merge), on the
@@ -373,17 +445,8 @@ def run_reuse_leg(sph, torch, b, box, dt, stream, args, flush):
             br.step(dt)
         torch.cuda.synchronize()
         s0 = br.stats()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                evs[k][0].record(stream)
-            br.step(dt)
-            with torch.cuda.stream(stream):
-                evs[k][1].record(stream)
-        torch.cuda.synchronize()
+        ms = sum(timed_steps(torch, br, dt, stream, args.steps, flush))
         s1 = br.stats()
-        ms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
         return {"value": box.n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
                 "builds": s1["builds"] - s0["builds"], "reuses": s1["reuses"] - s0["reuses"]}
     finally:
@@ -476,57 +539,121 @@ def run_serving(sph, ctx, n_boxes=512):
 
 
 # ------------------------------------------------------------------ oracle arm
-def _oracle_sample_box():
-    """The workload's recipe at 1/16 of the particles, with h converged by the oracle."""
+class _Grid:
+    """Particles of a periodic box binned on a g^3 mesh, for ball queries."""
+
+    def __init__(self, x, L, g=64):
+        self.x, self.L, self.g = x, L, g
+        c = np.minimum((x * (g / L)).astype(np.int64), g - 1)
+        cid = (c[:, 0] * g + c[:, 1]) * g + c[:, 2]
+        self.order = np.argsort(cid, kind="stable")
+        self.start = np.searchsorted(cid[self.order], np.arange(g ** 3 + 1))
+
+    def ball(self, centre, R):
+        g, L = self.g, self.L
+        lo = np.floor((centre - R) * (g / L)).astype(np.int64)
+        hi = np.floor((centre + R) * (g / L)).astype(np.int64)
+        axes = [np.unique(np.arange(lo[k], hi[k] + 1) % g) if hi[k] - lo[k] + 1 < g else np.arange(g)
+                for k in range(3)]
+        cells = ((axes[0][:, None, None] * g + axes[1][None, :, None]) * g + axes[2][None, None, :]).ravel()
+        idx = np.concatenate([self.order[self.start[c]:self.start[c + 1]] for c in cells])
+        d = self.x[idx] - centre
+        d -= L * np.round(d / L)
+        r = np.sqrt((d * d).sum(1))
+        keep = r <= R
+        return idx[keep], r[keep]
+
+
+class OracleSampler:
+    """Bounded samples of a workload for the FP64 oracle: the k particles nearest to
+    a randomly drawn particle (so that clumps and background are drawn in
+    proportion to their mass), and around them the sub-volume that holds their
+    neighbours and their partners' neighbours (3 x the largest first-guess support
+    radius near them)."""
+
+    def __init__(self, box, k=SAMPLE_K, seed=1):
+        from oracle import sph as orc
+        self.box, self.k = box, min(k, box.n)
+        self.grid = _Grid(box.x, box.L)
+        self.H0 = orc.support_radius(box.h)
+        self.rng = np.random.default_rng(seed)
+
+    def draw(self):
+        box, k = self.box, self.k
+        centre = box.x[self.rng.integers(box.n)]
+        R = 1e-3 * box.L
+        while True:
+            idx, r = self.grid.ball(centre, R)
+            if len(idx) >= k or R > box.L:
+                break
+            R *= 1.6
+        part = np.argpartition(r, k - 1)[:k]
+        rk = float(r[part].max())
+        cand, rc = self.grid.ball(centre, rk + float(self.H0.max()))
+        hloc = float(self.H0[cand[rc <= rk + self.H0[cand]]].max())
+        sub, _ = self.grid.ball(centre, min(rk + 3.0 * hloc, 0.5 * box.L))
+        sub = np.sort(sub)
+        return sub, np.searchsorted(sub, np.sort(idx[part]))
+
+
+def oracle_sample_step(box, sub, t):
+    """One oracle step on a sample: the h iteration (FP64, from the first guess)
+    over the sub-volume, ghost, then the force pass and the conservation sums of
+    the k sampled particles.  Results at the sub-volume's edge are not used."""
     from oracle import sph as orc
-    box = inputs.plummer_box(n=SAMPLE_N, seed=1)
-    h, conv, _, _ = orc.h_iterate(box.x, box.m, box.h, box.L, True, method="kdtree")
-    box.h = h.astype(np.float32)
-    return box
+    xs = box.x[sub]
+    m = box.m[sub].astype(np.float64)
+    h, conv, _, dens = orc.h_iterate(xs, m, box.h[sub], box.L, True, method="kdtree")
+    H = float(orc.GAMMA_K) * h
+    g = orc.ghost(dens["rho"], dens["Sr_m"], box.u[sub])
+    fo = orc.force(xs, box.v[sub], m, H, dens["rho"], g["P"], g["c"], g["f"], box.L, True, targets=t,
+                   method="kdtree")
+    return orc.reductions(m[t], box.v[sub][t], box.u[sub][t], fo["a"], fo["dudt"])
 
 
-def _oracle_step(box):
-    from oracle import sph as orc
-    return orc.full_step(box, iterate_h=True, method="kdtree")
-
-
-def cpu_baseline(_box=None):
-    sample = _oracle_sample_box()
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        _oracle_step(sample)
+def cpu_baseline(box, workload, budget_s=20.0):
+    sampler = OracleSampler(box)
+    t_total, reps = 0.0, 0
+    while t_total < budget_s and reps < 20:
+        sub, t = sampler.draw()
+        t0 = time.perf_counter()
+        oracle_sample_step(box, sub, t)
+        t_total += time.perf_counter() - t0
         reps += 1
-        if time.perf_counter() - t0 > 10.0 or reps >= 20:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": sample.n * reps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{reps} oracle steps (h iteration from converged h, force, reductions; FP64) on the "
-                      f"same Plummer recipe at {sample.n} particles; k-d tree search on all cores, numpy "
-                      f"arithmetic on one"}
+    return {"value": sampler.k * reps / t_total, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+            "sample": f"{reps} oracle sample steps on the {workload} box: each the {sampler.k} particles nearest a "
+                      f"randomly drawn particle, h iterated over the sub-volume around them (FP64), then their force "
+                      f"pass and conservation sums; k-d tree searches on all host threads, numpy arithmetic mostly "
+                      f"single-threaded; time per sampled particle"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    sample = _oracle_sample_box()
-    for _ in range(args.warmup):
-        _oracle_step(sample)
+    workload = getattr(args, "workload", DEFAULT_WORKLOAD)
+    steps, warmup = getattr(args, "steps", 20), getattr(args, "warmup", 5)
+    make, recipe = WORKLOADS[workload]
+    box = make(replica_seed(0))
+    sampler = OracleSampler(box)
+    draws = [sampler.draw() for _ in range(warmup + steps)]
+    for sub, t in draws[:warmup]:
+        oracle_sample_step(box, sub, t)
     times = []
-    for _ in range(args.steps):
+    for sub, t in draws[warmup:]:
         t0 = time.perf_counter()
-        _oracle_step(sample)
+        oracle_sample_step(box, sub, t)
         times.append(time.perf_counter() - t0)
     total = sum(times)
-    value = sample.n * args.steps / total
+    value = sampler.k * steps / total
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * total / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles_per_step": sample.n,
-                   "sample": "same recipe at 1/16 of the particles"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{sample.n}-particle Plummer box per step"},
+        "config": {"workload": workload, "recipe": recipe, "particles_per_step": sampler.k,
+                   "sample": f"each step the {sampler.k} particles nearest a randomly drawn particle of the box, h "
+                             f"iterated over their sub-volume, their force pass and sums"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+                         "sample": f"{sampler.k} sampled particles of the {workload} box per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -537,9 +664,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="keep the paper's leaf_max = 400")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-batch latency run")
+    ap.add_argument("--no-extra-workloads", action="store_true", help="skip the other single-box workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

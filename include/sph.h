@@ -127,8 +127,11 @@ typedef enum {
     SPH_FIELD_X = 13,         /* position                             [f64 x3] */
     SPH_FIELD_V = 14,         /* velocity                             [f32 x3] */
     SPH_FIELD_U = 15,         /* internal energy                      [f32 x1] */
-    SPH_FIELD_REDUCTIONS = 16 /* 8 doubles: sum m a (3), sum m (v.a + du/dt),
+    SPH_FIELD_REDUCTIONS = 16, /* 8 doubles: sum m a (3), sum m (v.a + du/dt),
                                  sum m v (3), sum m (v^2/2 + u); n must be 8 */
+    SPH_FIELD_FORCE_COUNT = 17 /* force partners j != i with r < max(H_i, H_j)
+                                 [i32 x1]; only after a force pass run with pair
+                                 counting on (sph_box_count_pairs) */
 } sph_field;
 
 /* Counters of the last build and passes. */
@@ -393,8 +396,10 @@ sph_status sph_server_destroy(sph_server* s);
  * cudaStream_t (NULL: the legacy default stream).  Results: rho_i including the
  * self term and the neighbour count j != i with r_ij < H_i, H = 1.825742 h,
  * decided exactly like sph_density.  Returns SPH_E_INVALID for n < 1 or
- * n > SPH_STATIC_MAX_N, SPH_E_H_TOO_LARGE when a periodic box is narrower than
- * three H_max, SPH_E_CUDA on a runtime error; synchronises the stream.
+ * n > SPH_STATIC_MAX_N, for a non-finite L <= 0, and for any particle with a
+ * coordinate outside [0, L) or an h or m that is not finite and positive (the
+ * checks of sph_build); SPH_E_H_TOO_LARGE when a periodic box is narrower than
+ * three H_max; SPH_E_CUDA on a runtime error.  Synchronises the stream.
  * The first call on a device looks up the array's address: make it before any
  * stream capture.  All calls share the one array (each call clears what it
  * needs), so calls that overlap on the GPU, from any stream or thread, race:

@@ -336,6 +336,7 @@ sph_status Engine::ensure_particle_capacity() {
   CK(ghost4.reserve(n));
   CK(facc.reserve(n));
   CK(fvsig.reserve(n));
+  CK(fcnt.reserve(n));
   CK(red.reserve(8 * std::max(nbox, 1)));
   CK(err_all.reserve(4));
   CK(pc.reserve(16));
@@ -870,6 +871,7 @@ sph_status Engine::force() {
   if (!have_ghost) return fail(SPH_E_NOT_BUILT, "force pass needs a density pass first");
   CK(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
   CK(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
+  if (count_pairs) CK(cudaMemsetAsync(fcnt.p, 0, N * sizeof(unsigned int), st));
   {
     Scope sc(this, PH_FORCE_TASKS);
     launch_live_tasks(*this, false);
@@ -886,6 +888,7 @@ sph_status Engine::force() {
   CK(cudaGetLastError());
   have_force = true;
   have_acc = true;
+  have_fcount = count_pairs;
   return SPH_OK;
 }
 
@@ -1363,6 +1366,9 @@ sph_status Engine::get_async(int b, int field, void* dst, long long n, int mem, 
     case SPH_FIELD_A: per = 3;  // fallthrough
     case SPH_FIELD_DUDT: case SPH_FIELD_VSIG:
       if (!have_force) return fail(SPH_E_NOT_BUILT, "no force pass yet");
+      break;
+    case SPH_FIELD_FORCE_COUNT:
+      if (!have_force || !have_fcount) return fail(SPH_E_NOT_BUILT, "no force pass with pair counting yet");
       break;
     default: return fail(SPH_E_INVALID, "unknown field");
   }

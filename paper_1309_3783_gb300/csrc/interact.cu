@@ -559,7 +559,7 @@ template <bool COUNT>
 __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, unsigned int jvalid,
                                            float bandJ, int n, bool own_only, unsigned int cmask,
                                            const unsigned int* perm, const double* x, const ItemGeom& g,
-                                           float alpha, Counters& C) {
+                                           float alpha, unsigned int* fcnt, Counters& C) {
   const int lane = threadIdx.x & 31;
   // the lane's own particle, read back from the staged cluster
   const float4 ip = S.ip[lane], ih = S.ih[lane];
@@ -599,6 +599,11 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
       li = (int)(w & 31u);
       sj = (int)((w >> 5) & 31u);
       force_pair_terms(own_side(S, li), staged_side(S, sj), (w >> 10) & 1u, (w >> 11) & 1u, alpha, ci, cj, vs);
+      if (COUNT) {
+        // force partners of both particles (the pair set, checked per particle)
+        atomicAdd(&fcnt[__float_as_int(S.ih[li].w)], 1u);
+        atomicAdd(&fcnt[S.g[sj]], 1u);
+      }
       float4* dst = own_only ? &S.iacc[sj] : &S.jacc[sj];
       atomicAdd(&dst->x, cj.x);
       atomicAdd(&dst->y, cj.y);
@@ -651,7 +656,8 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
 template <bool COUNT>
 __device__ __noinline__ void force_batch(ForceShared& S, unsigned int q, bool own_only,
                                             const unsigned int* perm, const double* x, const ItemGeom& g,
-                                            float alpha, float4* facc, float* fvsig, Counters& C) {
+                                            float alpha, float4* facc, float* fvsig, unsigned int* fcnt,
+                                            Counters& C) {
   const int lane = threadIdx.x & 31;
   const bool v = (unsigned int)lane < q;
   __syncwarp();
@@ -662,7 +668,7 @@ __device__ __noinline__ void force_batch(ForceShared& S, unsigned int q, bool ow
   // inside one cluster each unordered pair once (partners above the lane)
   const unsigned int allow = own_only ? jvalid & upper_mask(lane) : jvalid;
   force_tile<COUNT>(S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only, 0xffffffffu, perm, x, g, alpha,
-                    C);
+                    fcnt, C);
   __syncwarp();
   if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
   __syncwarp();
@@ -959,8 +965,8 @@ template <bool COUNT>
 __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
     const float4* __restrict__ ghost4, const float* __restrict__ sort_r, const unsigned int* __restrict__ sort_i,
-    const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig, ForceShared& S,
-    Counters& C) {
+    const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig,
+    unsigned int* fcnt, ForceShared& S, Counters& C) {
   const int lane = threadIdx.x & 31;
   const PairSetup P = pair_setup(Lq, T, box, item);
   const Box3 bi = tile_box3(TL, T, ti, P.tshA);
@@ -987,14 +993,14 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
+        force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, fcnt, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, C);
+  if (q) force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, fcnt, C);
   __syncwarp();
   flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
@@ -1003,8 +1009,8 @@ template <bool COUNT>
 __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
     const float4* __restrict__ ghost4, const float* __restrict__ sort_r, const unsigned int* __restrict__ sort_i,
-    const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig, ForceShared& S,
-    Counters& C) {
+    const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig,
+    unsigned int* fcnt, ForceShared& S, Counters& C) {
   const int lane = threadIdx.x & 31;
   const int A = Lq.self_a[item];
   const ItemGeom g = item_geom(T, box, A, 0);
@@ -1020,7 +1026,7 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
   unsigned int q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) force_put(S, lane, I);
-  force_batch<COUNT>(S, TL.n[ti], true, perm, x, g, alpha, facc, fvsig, C);
+  force_batch<COUNT>(S, TL.n[ti], true, perm, x, g, alpha, facc, fvsig, fcnt, C);
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
     bool ok = false;
@@ -1039,14 +1045,14 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, C);
+        force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, fcnt, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, C);
+  if (q) force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, fcnt, C);
   __syncwarp();
   flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
@@ -1115,7 +1121,7 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
                                                        const unsigned int* __restrict__ sort_i,
                                                        const unsigned int* __restrict__ perm,
                                                        const double* __restrict__ x, float alpha, float4* facc,
-                                                       float* fvsig, unsigned long long* pc,
+                                                       float* fvsig, unsigned int* fcnt, unsigned long long* pc,
                                                        unsigned int* __restrict__ task_ctr) {
   pdl_wait();
   __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
@@ -1137,10 +1143,10 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
       const int item = (int)(lt.x & 0x7fffffffu);
       if (lt.x >> 31)
         force_self_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
-                               facc, fvsig, S, Cs);
+                               facc, fvsig, fcnt, S, Cs);
       else
         force_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
-                               facc, fvsig, S, Cp);
+                               facc, fvsig, fcnt, S, Cp);
     }
     if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
   }
@@ -1645,7 +1651,8 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
                             const float4* __restrict__ vel4, const float4* __restrict__ dacc,
                             const unsigned int* __restrict__ dcnt, const float4* __restrict__ ghost4,
                             const float4* __restrict__ facc, const float* __restrict__ fvsig,
-                            const float* __restrict__ h, float gamma_gas, void* out) {
+                            const unsigned int* __restrict__ fcnt, const float* __restrict__ h, float gamma_gas,
+                            void* out) {
   pdl_wait();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long p = off + q;
@@ -1674,6 +1681,7 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
       }
       case SPH_FIELD_DUDT: fo[i] = facc[p].w; break;
       case SPH_FIELD_VSIG: fo[i] = fvsig[p]; break;
+      case SPH_FIELD_FORCE_COUNT: reinterpret_cast<int*>(out)[i] = (int)fcnt[p]; break;
       default: break;
     }
   }
@@ -1743,7 +1751,7 @@ void launch_force(Engine& E) {
   cudaMemsetAsync(E.task_ctr.p + 1, 0, sizeof(unsigned int), E.st);
   launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
       E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p, E.x.p,
-      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.pc.p, E.task_ctr.p + 1);
+      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.fcnt.p, E.pc.p, E.task_ctr.p + 1);
   count_launch();
 }
 
@@ -1873,7 +1881,8 @@ void launch_set_h(Engine& E, int b, const float* src) {
 
 void launch_get_field(Engine& E, long long off, long long n, int field, void* out) {
   launch_pdl(k_get_field, E.grid(n), 256, E.st, off, n, field, E.perm.p, E.Hs.p, E.cen4.p, E.vel4.p, E.dacc.p, E.dcnt.p,
-                                           E.ghost4.p, E.facc.p, E.fvsig.p, E.h.p, E.prm.gamma_gas, out); count_launch();
+                                           E.ghost4.p, E.facc.p, E.fvsig.p, E.fcnt.p, E.h.p, E.prm.gamma_gas, out);
+  count_launch();
 }
 
 }  // namespace sph

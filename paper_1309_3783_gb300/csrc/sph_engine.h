@@ -207,6 +207,7 @@ class Engine {
   DBuf<float4> ghost4;            // rho, f P / rho^2, c, f
   DBuf<float4> facc;              // a (3), du/dt
   DBuf<float> fvsig;
+  DBuf<unsigned int> fcnt;        // force partners per particle (filled while counting pairs)
   DBuf<double> red;               // 8 per box
   DBuf<unsigned int> err_all;     // global error bits
   DBuf<unsigned long long> pc;    // pair counters per kernel (see commit_counters)
@@ -237,6 +238,7 @@ class Engine {
   long long g_pre = 0, g_keep = 0, g_iter = 0, g_force = 0;   // kernels per part
   long long last_unconverged = 0;
   bool built = false, have_density = false, have_ghost = false, have_force = false, have_acc = false;
+  bool have_fcount = false;       // the last force pass counted pairs (fcnt is filled)
 
   // profiling: CUDA events around each phase on the engine's stream
   struct ProfRec {

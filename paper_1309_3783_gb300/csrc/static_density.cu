@@ -17,6 +17,9 @@
 // bit for bit.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cmath>
+
 #include "sph.h"
 #include "sph_internal.cuh"
 
@@ -38,8 +41,10 @@ constexpr size_t kScratchWords = 2 * (size_t)kMaxCells + 2 * (size_t)kMaxN + 64;
 // life of the process.  Host code must not use this name as a device address.
 static __device__ __align__(256) unsigned int g_scratch[kScratchWords];
 
-// Device address of g_scratch per device, looked up once per device.
-static unsigned int* g_scratch_ptr[64] = {nullptr};
+// Device address of g_scratch per device, looked up once per device.  Host
+// threads that make their first calls at the same time may each look it up; they
+// store the same value, through atomics.
+static std::atomic<unsigned int*> g_scratch_ptr[64];
 
 __device__ __forceinline__ int wrap_cell(int c, int side, int periodic) {
   if (periodic) return (c + side) % side;
@@ -53,6 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_density_static(const double* __res
                                                             int* __restrict__ count, unsigned int* __restrict__ ws,
                                                             int* __restrict__ status) {
   __shared__ float s_hmax;
+  __shared__ int s_bad;
   __shared__ int s_side;
   __shared__ unsigned int s_carry;
   unsigned int* cells = ws;
@@ -62,24 +68,34 @@ __global__ void __launch_bounds__(kThreads) k_density_static(const double* __res
   const int tid = threadIdx.x;
   if (tid == 0) {
     s_hmax = 0.0f;
+    s_bad = 0;
     *status = 0;
   }
   __syncthreads();
-  // support radii and their maximum
+  // input checks (those of the main path's ingest: 0 <= x < L, h and m finite and
+  // positive), support radii and their maximum
   float hm = 0.0f;
+  bool bad = false;
   for (int i = tid; i < n; i += kThreads) {
-    const float H = __fmul_rn(gamma_k, h[i]);
+    const float hi = h[i], mi = m[i];
+    for (int k = 0; k < 3; ++k) {
+      const double xk = x[3 * i + k];
+      bad |= !(xk >= 0.0 && xk < L);
+    }
+    bad |= !(isfinite(hi) && hi > 0.0f) || !(isfinite(mi) && mi > 0.0f);
+    const float H = __fmul_rn(gamma_k, hi);
     Hs[i] = H;
-    hm = fmaxf(hm, H);
+    if (H > hm) hm = H;
   }
   hm = warp_max(hm);
   if ((tid & 31) == 0) atomic_max_pos(&s_hmax, hm);
+  if (bad) s_bad = 1;
   __syncthreads();
   if (tid == 0) {
     // cells of edge >= H_max (with a relative margin far above the rounding of a
     // cell index); at least 3 per dimension for periodic boxes
     int side = 1;
-    if (!(s_hmax > 0.0f) || !isfinite(s_hmax)) {
+    if (s_bad || !(s_hmax > 0.0f) || !isfinite(s_hmax)) {
       *status = SPH_E_INVALID;
     } else {
       const double sd = floor(L / ((double)s_hmax * (1.0 + 1e-9)));
@@ -192,16 +208,18 @@ extern "C" sph_status sph_density_static(const double* x, const float* m, const 
                                          int periodic, float* rho, int32_t* count, void* stream) {
   if (!x || !m || !h || !rho || !count || !(box_len > 0)) return SPH_E_INVALID;
   if (n < 1 || n > kMaxN) return SPH_E_INVALID;      // beyond the static working memory
+  if (!std::isfinite(box_len)) return SPH_E_INVALID;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SPH_E_CUDA;
-  if (!g_scratch_ptr[dev]) {
+  unsigned int* ws = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!ws) {
     // first call on this device: look up the array's device address (call it
     // before any stream capture)
     unsigned int* ptr = nullptr;
     if (cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_scratch) != cudaSuccess || !ptr) return SPH_E_CUDA;
-    g_scratch_ptr[dev] = ptr;
+    g_scratch_ptr[dev].store(ptr, std::memory_order_release);
+    ws = ptr;
   }
-  unsigned int* ws = g_scratch_ptr[dev];
   // the status word lives in the last words of the working memory
   int* status = reinterpret_cast<int*>(ws + kScratchWords - 1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -22,11 +22,12 @@ SPH_E_NOT_CONVERGED = -5
 SPH_MEM_HOST, SPH_MEM_DEVICE = 0, 1
 
 FIELDS = {"rho": 0, "drho_dh": 1, "nw": 2, "nngb": 3, "count": 4, "h": 5, "P": 6, "c": 7, "f": 8, "a": 9,
-          "dudt": 10, "vsig": 11, "converged": 12, "x": 13, "v": 14, "u": 15, "reductions": 16}
+          "dudt": 10, "vsig": 11, "converged": 12, "x": 13, "v": 14, "u": 15, "reductions": 16,
+          "force_count": 17}
 _FIELD_TYPE = {0: (np.float32, 1), 1: (np.float32, 1), 2: (np.float32, 1), 3: (np.float32, 1), 4: (np.int32, 1),
                5: (np.float32, 1), 6: (np.float32, 1), 7: (np.float32, 1), 8: (np.float32, 1), 9: (np.float32, 3),
                10: (np.float32, 1), 11: (np.float32, 1), 12: (np.int32, 1), 13: (np.float64, 3),
-               14: (np.float32, 3), 15: (np.float32, 1), 16: (np.float64, 1)}
+               14: (np.float32, 3), 15: (np.float32, 1), 16: (np.float64, 1), 17: (np.int32, 1)}
 
 
 class sph_params(C.Structure):
@@ -496,5 +497,9 @@ def sph_density_static(x, m, h, box_len: float, periodic: bool, rho, count, stre
     pc, mc, _ = _arg(count, np.int32, n)
     if {mx, mm, mh, mr, mc} != {SPH_MEM_DEVICE}:
         raise ValueError("sph_density_static takes device tensors only")
+    import torch
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in (x, m, h, rho, count)):
+        raise ValueError(f"sph_density_static runs on the current device (cuda:{dev}): every tensor must be there")
     return load().sph_density_static(px, pm, ph, n, float(box_len), 1 if periodic else 0, pr, pc,
                                      C.c_void_p(stream) if stream else None)

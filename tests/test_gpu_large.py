@@ -1,18 +1,21 @@
-"""Full-size variable-h workloads through the C-ABI, checked on local samples.
+"""Full-size variable-h workloads through the C-ABI, checked on samples.
 
 The 8,388,608-particle log-normal box and the 33,554,432-particle clustered box
 (4096 Plummer spheres with scale radii from 1e-4 to 1e-2 over a uniform
 background) stand in for the paper's cosmological volume, whose smoothing
 lengths span three orders of magnitude.  The GPU iterates h from the first
 guess to N~ = 48 and then runs the force pass; the oracle takes the GPU's final
-h as its input, so that the neighbour predicate is identical on both sides, and
-is evaluated around a few sample centres.
+h as its input, so that the neighbour predicate is identical on both sides.
 
-A sample is the k particles nearest to a centre (a randomly chosen particle, so
-dense regions are drawn in proportion to their mass).  Everything the oracle
-needs for those targets lies within R + 2 H_max of the centre (R the sample
-radius): their neighbours within max(H_i, H_j) and, for the force, those
-neighbours' own densities.  The oracle therefore runs on that sub-volume only.
+Samples: the k particles nearest to each of several centres.  Centres drawn
+uniformly in space (20 x 1024 = 20,480 particles, which by volume land mostly in
+the background and voids), plus centres at randomly chosen particles (drawn in
+proportion to mass, so mostly inside the dense clumps).  The oracle runs on the
+sub-volume that holds everything the targets' results depend on: the targets'
+partners j (r < max(H_i, H_j)) and, for the force, every neighbour within H_j of
+those partners (their densities).  That sub-volume is the ball around the centre
+reaching max(|x_j - c| + H_j) over targets and partners, found exactly from the
+GPU's final H with a coarse grid index.
 """
 import numpy as np
 import pytest
@@ -30,25 +33,51 @@ def api():
     return sph
 
 
-def _min_image(d, L):
-    return d - L * np.round(d / L)
+class _Grid:
+    """Particles binned on a g^3 mesh of the periodic box, for ball queries."""
 
+    def __init__(self, x, L, g=64):
+        self.x, self.L, self.g = x, L, g
+        c = np.minimum((x * (g / L)).astype(np.int64), g - 1)
+        cid = (c[:, 0] * g + c[:, 1]) * g + c[:, 2]
+        self.order = np.argsort(cid, kind="stable")
+        self.start = np.searchsorted(cid[self.order], np.arange(g ** 3 + 1))
 
-def _samples(box, H, n_centres, k, seed):
-    """(targets, sub) per centre: the k nearest particles and the sub-volume the oracle needs."""
-    rng = np.random.default_rng(seed)
-    reach = 2.05 * float(H.max())
-    out = []
-    for c in rng.choice(box.n, n_centres, replace=False):
-        d = _min_image(box.x - box.x[c], box.L)
+    def ball(self, centre, R):
+        """(indices, distances) of the particles within R of centre (minimum image)."""
+        g, L = self.g, self.L
+        lo = np.floor((centre - R) * (g / L)).astype(np.int64)
+        hi = np.floor((centre + R) * (g / L)).astype(np.int64)
+        axes = [np.unique(np.arange(lo[k], hi[k] + 1) % g) if hi[k] - lo[k] + 1 < g else np.arange(g)
+                for k in range(3)]
+        cells = ((axes[0][:, None, None] * g + axes[1][None, :, None]) * g + axes[2][None, None, :]).ravel()
+        idx = np.concatenate([self.order[self.start[c]:self.start[c + 1]] for c in cells])
+        d = self.x[idx] - centre
+        d -= L * np.round(d / L)
         r = np.sqrt((d * d).sum(1))
-        targets = np.argpartition(r, k)[:k]
-        sub = np.nonzero(r <= r[targets].max() + reach)[0]
-        out.append((np.sort(targets), sub))
-    return out
+        keep = r <= R
+        return idx[keep], r[keep]
 
 
-def _check_sampled(api, box, n_centres=6, k=64, seed=0):
+def _sample(grid, H, centre, k):
+    """(targets, sub): the k particles nearest to centre and the sub-volume the oracle needs."""
+    R = 1e-3 * grid.L
+    while True:
+        idx, r = grid.ball(centre, R)
+        if len(idx) >= k:
+            break
+        R *= 1.6
+    part = np.argpartition(r, k - 1)[:k]
+    targets, rk = np.sort(idx[part]), float(r[part].max())
+    # partners of the targets lie within r_k + max(H_T, H_j) of the centre
+    cand, rc = grid.ball(centre, rk + float(H.max()))
+    near = rc - rk < np.maximum(float(H[targets].max()), H[cand])
+    reach = float(np.max(rc[near] + H[cand[near]]))
+    sub, _ = grid.ball(centre, reach * (1.0 + 1e-9) + 1e-12)
+    return targets, np.sort(sub)
+
+
+def _check_sampled(api, box, n_uniform=20, k_uniform=1024, n_clumps=6, k_clump=64, seed=0):
     p = api.sph_params_default()
     ctx = api.sph_ctx_create(p, device=0)
     try:
@@ -69,9 +98,14 @@ def _check_sampled(api, box, n_centres=6, k=64, seed=0):
     H = orc.support_radius(h)
     print(f"{box.name}: h iterations {iters}, H in [{H.min():.3e}, {H.max():.3e}] "
           f"(ratio {H.max() / H.min():.0f}), tree depth {int(cells['level'].max())}")
+    grid = _Grid(box.x, box.L)
+    rng = np.random.default_rng(seed)
+    centres = [(c, k_uniform) for c in rng.uniform(0.0, box.L, (n_uniform, 3))]
+    centres += [(box.x[i], k_clump) for i in rng.choice(box.n, n_clumps, replace=False)]
     worst = {"rho": 0.0, "nw": 0.0, "a": 0.0, "dudt": 0.0, "vsig": 0.0}
-    n_checked = 0
-    for targets, sub in _samples(box, H, n_centres, k, seed):
+    checked = set()
+    for centre, k in centres:
+        targets, sub = _sample(grid, H, centre, k)
         xs, Hs = box.x[sub], H[sub]
         t = np.searchsorted(sub, targets)
         ref = orc.density(xs, box.m[sub], Hs, box.L, True, targets=t, method="kdtree")
@@ -106,9 +140,11 @@ def _check_sampled(api, box, n_centres=6, k=64, seed=0):
         worst["a"] = max(worst["a"], float(ea / rms))
         worst["dudt"] = max(worst["dudt"], float(eu / rms_u))
         worst["vsig"] = max(worst["vsig"], rel(g["vsig"][targets], fo["vsig"]))
-        n_checked += len(targets)
+        checked.update(targets.tolist())
+    assert len(checked) >= 20000
     # measured errors against the FP64 oracle (shown with pytest -s)
-    print(f"[errors vs FP64] {box.name}: {n_checked} sampled particles, counts exact; rho max rel "
+    print(f"[errors vs FP64] {box.name}: {len(checked)} sampled particles ({n_uniform} x {k_uniform} around "
+          f"uniform centres, {n_clumps} x {k_clump} around particles), counts exact; rho max rel "
           f"{worst['rho']:.1e}, sum W {worst['nw']:.1e}; a max {worst['a']:.1e} of rms, du/dt max "
           f"{worst['dudt']:.1e} of rms, v_sig max rel {worst['vsig']:.1e}")
 

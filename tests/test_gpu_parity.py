@@ -198,6 +198,54 @@ def test_open_box_and_box_length(api, ctx):
         check_force(g, ref)
 
 
+# ------------------------------------------------------------------ interacting pair sets
+def _pair_set_case(name):
+    if name == "lattice4096":
+        return inputs.lattice_box(16, jitter=0.1, seed=1), 400
+    box = inputs.plummer_box(n=20000, n_spheres=4, scale=0.05, seed=3)
+    return box, 48
+
+
+@pytest.mark.parametrize("case", ["lattice4096", "plummer20000"])
+def test_interacting_pair_sets_equal_brute_force(api, case):
+    """Section II-B: every pair within max(H_i, H_j) lies in exactly one self- or
+    pair-interaction.  The density kernel's pair and side counters and the force
+    kernel's pair counter and per-particle partner counts equal brute force: a
+    pair dropped or visited twice changes them (its force term can be below the
+    force tolerance, dW/dr vanishing at the cutoff)."""
+    box, leaf = _pair_set_case(case)
+    c = make_ctx(api, leaf_max=leaf)
+    try:
+        b = api.box_from(c, box)
+        try:
+            b.count_pairs(True)
+            b.density()
+            sd = b.stats()
+            cnt = b.get("count")
+            b.force()
+            sf = b.stats()
+            fcnt = b.get("force_count")
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    H = orc.support_radius(box.h)
+    method = "brute" if box.n <= 4096 else "kdtree"
+    t, j, _, _ = orc.neighbour_pairs(box.x, None, box.L, True, None, "force", Hall=H, method=method)
+    per = np.bincount(t, minlength=box.n)
+    n_unordered = len(t) // 2
+    if box.n <= 4096:
+        assert len(dc.interacting_pairs_brute(box.x, H, box.L, True)) == n_unordered
+    ref = orc.density(box.x, box.m, H, box.L, True, method=method)
+    assert np.array_equal(cnt, ref["count"])
+    assert sd["density_pairs"] == n_unordered
+    assert sd["density_sides"] == int(ref["count"].sum())
+    assert sf["force_pairs"] == n_unordered
+    assert np.array_equal(fcnt, per), np.nonzero(fcnt != per)[0][:10]
+    print(f"[pair sets] {case}: {n_unordered} unordered pairs within max(H_i, H_j), "
+          f"{sd['density_candidates']} density and {sf['force_candidates']} force candidates evaluated")
+
+
 # ------------------------------------------------------------------ decomposition
 @pytest.mark.parametrize("headroom", [0.0, 0.1])
 def test_decomposition_matches_the_paper_rules(api, headroom):

@@ -23,6 +23,7 @@ struct ItemGeom {
   float3 offB;      // centre of B minus centre of A (units of L), exact: e * db
   float offBp;      // projection of offB on the axis: e |db|
   float invL;
+  float L32;        // L in FP32
   float drift;      // largest displacement since the decomposition was built (units of L)
   double L, halfL;
   int periodic;
@@ -39,12 +40,22 @@ __device__ __forceinline__ ItemGeom item_geom(const Tree& T, const BoxDesc* box,
   const int n2 = dx * dx + dy * dy + dz * dz;
   g.offBp = g.e * (n2 == 1 ? 1.0f : (n2 == 2 ? 1.41421356237f : 1.73205080757f));
   g.invL = (float)bd.invL;
+  g.L32 = (float)bd.L;
   g.drift = bd.drift_u;
   g.L = bd.L;
   g.halfL = 0.5 * bd.L;
   g.periodic = bd.periodic;
   return g;
 }
+
+// The FP64 data of a box that the exact decisions need, passed by value (an
+// argument passed by reference to out-of-line code would live in local memory).
+struct BoxExact {
+  double L, halfL;
+  int periodic;
+};
+
+__device__ __forceinline__ BoxExact box_exact(const ItemGeom& g) { return BoxExact{g.L, g.halfL, g.periodic}; }
 
 // Tasks are handed out in chunks from a counter in device memory (zeroed before
 // every launch): the cost of a task varies by orders of magnitude, so a static
@@ -203,7 +214,7 @@ struct ForceI {
 
 __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, float3 shift, const float4* pos4,
                                              const float4* cen4, const float4* vel4, const float4* ghost4,
-                                             float invL, float e) {
+                                             float invL, float L, float e) {
   ForceI r;
   r.valid = valid;
   if (valid) {
@@ -215,7 +226,7 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
     r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
     const float H = p.w * invL;
     r.H = H;
-    r.invH = 1.0f / H;
+    r.invH = gh.w * L;                // 1 / H in units of L
     r.H2 = H * H;
     r.band = BAND_REL * H * (e + H);
     r.Hphys = p.w;
@@ -224,7 +235,7 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
     r.rho = gh.x;
     r.F = gh.y;
     r.c = gh.z;
-    const float ih = 1.0f / p.w;
+    const float ih = gh.w;            // 1 / H (physical), from the ghost pass
     r.K4 = SPH_KNORM * (ih * ih) * (ih * ih);
     r.g = (int)gidx;
   } else {
@@ -311,7 +322,7 @@ __device__ __forceinline__ void flush_force(int gidx, float4 acc, float vs, floa
 template <class SH>
 __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iband, int ig, float iHphys,
                                            const SH& S, float bandJ, unsigned int allow, int n,
-                                           const unsigned int* perm, const double* x, const ItemGeom& g,
+                                           const unsigned int* perm, const double* x, const BoxExact g,
                                            unsigned int& mI, unsigned int& mJ, unsigned int& rc) {
   // u: slots where either decision falls inside its guard band; both are then
   // taken again in FP64 (the exact decision equals the FP32 one where that was sure)
@@ -413,7 +424,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
                                           Counters& C) {
   const int lane = threadIdx.x & 31;
   unsigned int mI, mJ, rc = 0;
-  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, g, mI, mJ, rc);
+  pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, box_exact(g), mI, mJ, rc);
   const unsigned int ui = I.act ? mI : 0u, uj = own_only ? 0u : (mJ & jact);
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid & cmask) : 0u;
@@ -558,8 +569,8 @@ __device__ __forceinline__ ForceSide own_side(const ForceShared& S, int k) {
 template <bool COUNT>
 __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, unsigned int jvalid,
                                            float bandJ, int n, bool own_only, unsigned int cmask,
-                                           const unsigned int* perm, const double* x, const ItemGeom& g,
-                                           float alpha, unsigned int* fcnt, Counters& C) {
+                                           const unsigned int* perm, const double* x, const BoxExact g,
+                                           float alpha, unsigned int* fcnt, Counters* C) {
   const int lane = threadIdx.x & 31;
   // the lane's own particle, read back from the staged cluster
   const float4 ip = S.ip[lane], ih = S.ih[lane];
@@ -569,9 +580,9 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
              mI, mJ, rc);
   const unsigned int m = mI | mJ;
   if (COUNT) {
-    C.cand += ivalid ? __popc(allow & jvalid & cmask) : 0u;
-    C.rechecks += rc;
-    C.pairs += __popc(m & cmask);
+    C->cand += ivalid ? __popc(allow & jvalid & cmask) : 0u;
+    C->rechecks += rc;
+    C->pairs += __popc(m & cmask);
   }
   // list the pairs, own lane major
   const unsigned int cnt = __popc(m);
@@ -652,12 +663,13 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
 
 // Not inlined: the pair and self tasks share one copy of the batch code, which
 // keeps the force kernel's instructions within the instruction cache (inlined
-// twice, instruction fetch was the largest stall of the kernel).
+// twice, instruction fetch was the largest stall of the kernel).  Everything is
+// passed by value or by pointer, so that a call stores nothing to local memory.
 template <bool COUNT>
 __device__ __noinline__ void force_batch(ForceShared& S, unsigned int q, bool own_only,
-                                            const unsigned int* perm, const double* x, const ItemGeom& g,
+                                            const unsigned int* perm, const double* x, const BoxExact g,
                                             float alpha, float4* facc, float* fvsig, unsigned int* fcnt,
-                                            Counters& C) {
+                                            Counters* C) {
   const int lane = threadIdx.x & 31;
   const bool v = (unsigned int)lane < q;
   __syncwarp();
@@ -966,14 +978,14 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
     const float4* __restrict__ ghost4, const float* __restrict__ sort_r, const unsigned int* __restrict__ sort_i,
     const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig,
-    unsigned int* fcnt, ForceShared& S, Counters& C) {
+    unsigned int* fcnt, ForceShared& S, Counters* C) {
   const int lane = threadIdx.x & 31;
   const PairSetup P = pair_setup(Lq, T, box, item);
   const Box3 bi = tile_box3(TL, T, ti, P.tshA);
   const float Hi = TL.lo[ti].w * P.g.invL;
   const float rhi_i = box_rhi(bi, P.u);
   const bool vi = (unsigned int)lane < TL.n[ti];
-  const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.e);
+  const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.L32, P.g.e);
   force_stage_own(S, lane, I);
   unsigned int q = 0;
   for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
@@ -988,19 +1000,19 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
       mask &= mask - 1;
       const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
       const ForceI J = load_force(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, vel4, ghost4,
-                                  P.g.invL, P.g.e);
+                                  P.g.invL, P.g.L32, P.g.e);
       const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, fcnt, C);
+        force_batch<COUNT>(S, q, false, perm, x, box_exact(P.g), alpha, facc, fvsig, fcnt, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(S, q, false, perm, x, P.g, alpha, facc, fvsig, fcnt, C);
+  if (q) force_batch<COUNT>(S, q, false, perm, x, box_exact(P.g), alpha, facc, fvsig, fcnt, C);
   __syncwarp();
   flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
@@ -1010,7 +1022,7 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
     const float4* __restrict__ ghost4, const float* __restrict__ sort_r, const unsigned int* __restrict__ sort_i,
     const unsigned int* __restrict__ perm, const double* __restrict__ x, float alpha, float4* facc, float* fvsig,
-    unsigned int* fcnt, ForceShared& S, Counters& C) {
+    unsigned int* fcnt, ForceShared& S, Counters* C) {
   const int lane = threadIdx.x & 31;
   const int A = Lq.self_a[item];
   const ItemGeom g = item_geom(T, box, A, 0);
@@ -1021,12 +1033,12 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
   const Box3 bi = tile_box3(TL, T, ti, sh);
   const float Hi = TL.lo[ti].w * g.invL;
   const bool vi = (unsigned int)lane < TL.n[ti];
-  const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+  const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.e);
   force_stage_own(S, lane, I);
   unsigned int q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) force_put(S, lane, I);
-  force_batch<COUNT>(S, TL.n[ti], true, perm, x, g, alpha, facc, fvsig, fcnt, C);
+  force_batch<COUNT>(S, TL.n[ti], true, perm, x, box_exact(g), alpha, facc, fvsig, fcnt, C);
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
     bool ok = false;
@@ -1040,19 +1052,19 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
       mask &= mask - 1;
       const unsigned int tj = b0 + (unsigned int)k;
       const bool vj = (unsigned int)lane < TL.n[tj];
-      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.e);
+      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.e);
       const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, fcnt, C);
+        force_batch<COUNT>(S, q, false, perm, x, box_exact(g), alpha, facc, fvsig, fcnt, C);
         q = 0;
       }
       if (pass) force_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) force_batch<COUNT>(S, q, false, perm, x, g, alpha, facc, fvsig, fcnt, C);
+  if (q) force_batch<COUNT>(S, q, false, perm, x, box_exact(g), alpha, facc, fvsig, fcnt, C);
   __syncwarp();
   flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
@@ -1143,10 +1155,10 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
       const int item = (int)(lt.x & 0x7fffffffu);
       if (lt.x >> 31)
         force_self_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
-                               facc, fvsig, fcnt, S, Cs);
+                               facc, fvsig, fcnt, S, COUNT ? &Cs : nullptr);
       else
         force_pair_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
-                               facc, fvsig, fcnt, S, Cp);
+                               facc, fvsig, fcnt, S, COUNT ? &Cp : nullptr);
     }
     if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
   }
@@ -1294,7 +1306,7 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
     // f = [1 + h/(3 rho) d rho/dh]^-1 = 3 rho / (-sum_j m_j r W'), without cancellation;
     // 1 when no other particle lies inside the support
     const float f = a.y < 0.0f ? -3.0f * (a.x + m) / a.y : 1.0f;
-    ghost4[p] = make_float4(rho, f * P / (rho * rho), c, f);
+    ghost4[p] = make_float4(rho, f * P / (rho * rho), c, ih);
   }
 }
 
@@ -1671,7 +1683,7 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
       case SPH_FIELD_COUNT: reinterpret_cast<int*>(out)[i] = (int)dcnt[p]; break;
       case SPH_FIELD_P: fo[i] = (gamma_gas - 1.0f) * ghost4[p].x * vel4[p].w; break;
       case SPH_FIELD_C: fo[i] = ghost4[p].z; break;
-      case SPH_FIELD_F: fo[i] = ghost4[p].w; break;
+      case SPH_FIELD_F: fo[i] = a.y < 0.0f ? -3.0f * (a.x + m) / a.y : 1.0f; break;   // as the ghost pass
       case SPH_FIELD_A: {
         const float4 f = facc[p];
         fo[3 * i] = f.x;

@@ -499,8 +499,9 @@ __global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc*
   }
 }
 
-// One round of the cell tree, one block of TREE_THREADS per frontier node (a
-// top cell can hold a large share of the box): the node's statistics and the
+// One round of the cell tree, one block of TREE_THREADS per large frontier node
+// (a top cell can hold a large share of the box) and one warp per small one: the
+// node's statistics and the
 // split rule of Section II-B / III-B -- split iff level < dcap,
 // count > leaf_max and n_small > split_frac * count, with
 // n_small = #{H < edge/2 - margin} -- and, for a split node, its children: the
@@ -512,21 +513,89 @@ __global__ void k_top_nodes(long long N, int dcap, int box_shift, const BoxDesc*
 // full depth.  The deepest level of any node goes to n_nodes[5].
 constexpr int TREE_THREADS = 256;
 
-// k consecutive node ids, all or none: the count never passes the capacity, so
-// every id below it belongs to a node that was written (an allocation that only
-// partly fitted would leave unwritten ids inside the tree, which the next round's
-// frontier would read).  -1 when they do not fit.  The compare-and-swap retries
-// only when another node allocated in between.
-__device__ __forceinline__ int alloc_nodes(int* count, int k, int cap) {
-  int old = atomicAdd(count, 0);
-  for (int tries = 0; tries < (1 << 20); ++tries) {
-    if (old + k > cap) return -1;
-    const int prev = atomicCAS(count, old, old + k);
-    if (prev == old) return old;
-    old = prev;
+// k consecutive node ids from one atomic (a compare-and-swap loop serialised the
+// thousands of nodes that split in one round).  When they do not all fit under
+// the capacity, the ids that do are written as empty nodes (no particles, no
+// children), so that every id below the capacity is a valid node for the rest of
+// the build, which the overflow flag then redoes with more room; -1 then.
+__device__ __forceinline__ int alloc_nodes(Tree& T, int k, int cap, int level, int box) {
+  const int old = atomicAdd(&T.n_nodes[0], k);
+  if (old + k <= cap) return old;
+  for (int i = old; i < min(old + k, cap); ++i) {
+    T.start[i] = 0;
+    T.count[i] = 0;
+    T.key[i] = 0ull;
+    T.level[i] = level;
+    T.box[i] = box;
+    T.parent[i] = -1;
+    T.child[i] = -1;
+    T.nchild[i] = 0;
   }
   return -1;
 }
+
+// The split decision and the writes of one node, by one warp, from its largest
+// H (hm), its particles with H < edge/2 - margin (ns) and, on lane k < 8, the
+// particles in octant k (mine).
+__device__ __forceinline__ void tree_node_finish(Tree& T, int id, int d, const BoxDesc& bd, unsigned int s,
+                                                 unsigned int c, bool may_split, float hm, unsigned int ns,
+                                                 unsigned int mine, int dcap, int leaf_max, float split_frac,
+                                                 int capped, int cap_nodes, unsigned int* __restrict__ err_all) {
+  const int lane = threadIdx.x & 31;
+  const bool sp = may_split && (double)ns > (double)split_frac * (double)c;
+  const unsigned int ne = __ballot_sync(0xffffffffu, lane < 8 && mine != 0);
+  const int nch = __popc(ne);
+  // start of octant `lane`: the counts of the octants before it
+  unsigned int before = mine;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, before, o);
+    if (lane >= o) before += y;
+  }
+  before -= mine;
+  int c0 = -1;
+  if (sp && lane == 0) c0 = alloc_nodes(T, nch, cap_nodes, d + 1, T.box[id]);
+  c0 = __shfl_sync(0xffffffffu, c0, 0);
+  const bool fits = c0 >= 0;
+  if (sp && fits && lane < 8 && mine != 0) {
+    const int cid = c0 + __popc(ne & ((1u << lane) - 1u));
+    T.start[cid] = s + before;
+    T.count[cid] = mine;
+    T.key[cid] = (T.key[id] << 3) | (unsigned long long)lane;
+    T.level[cid] = d + 1;
+    T.box[cid] = T.box[id];
+    T.parent[cid] = id;
+    T.child[cid] = -1;
+    T.nchild[cid] = 0;
+  }
+  if (lane == 0) {
+    if (sp && !fits) atomicOr(err_all, ERR_OVERFLOW);
+    if (capped && d >= dcap && (int)c > leaf_max && (double)ns > (double)split_frac * (double)c)
+      atomicOr(err_all, ERR_DEPTH);
+    atomicMax(&T.n_nodes[5], d);
+    T.hmax[id] = hm;
+    T.nsmall[id] = ns;
+    T.split[id] = (sp && fits) ? 1 : 0;
+    T.child[id] = (sp && fits) ? c0 : -1;
+    T.nchild[id] = (sp && fits) ? nch : 0;
+    T.axes[id] = 0;
+    // limit the top grid sets on every particle: H < edge_k - margin
+    T.hlim[id] = (T.parent[id] < 0) ? __dsub_rn(ldexp(bd.L, -d), bd.margin) : 1e300;
+    unsigned int cx, cy, cz;
+    cell_coords(T.key[id], d, cx, cy, cz);
+    const double inv = ldexp(1.0, -d), invk = ldexp(1.0, -bd.k);
+    const int sh = d - bd.k;
+    const double tx = ((double)(cx >> sh) + 0.5) * invk, ty = ((double)(cy >> sh) + 0.5) * invk,
+                 tz = ((double)(cz >> sh) + 0.5) * invk;
+    T.cen[id] = make_float4((float)(((double)cx + 0.5) * inv - tx), (float)(((double)cy + 0.5) * inv - ty),
+                            (float)(((double)cz + 0.5) * inv - tz), (float)inv);
+  }
+}
+
+// Nodes of more than TREE_WARP_MAX particles take a block of TREE_THREADS each;
+// the others one warp each (most nodes are small, and a block per node leaves
+// its warps waiting at barriers on a few particles).
+constexpr unsigned int TREE_WARP_MAX = 2048;
 
 __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDesc* __restrict__ box,
                                                              const float* __restrict__ Hs,
@@ -540,11 +609,14 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
   __shared__ unsigned int s_ns[NW], s_oc[NW][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int f0 = T.n_nodes[1], f1 = min(T.n_nodes[2], T.n_nodes[0]);
+  // large nodes: one block each
   for (int id = f0 + blockIdx.x; id < f1; id += gridDim.x) {
+    const unsigned int c = T.count[id];
+    if (c <= TREE_WARP_MAX) continue;   // the same for the whole block
     const int d = T.level[id];
     const BoxDesc bd = box[T.box[id]];
     const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
-    const unsigned int s = T.start[id], c = T.count[id];
+    const unsigned int s = T.start[id];
     const bool may_split = allow_split && d < dcap && (int)c > leaf_max;
     const int dig = 3 * (dcap - d - 1);   // Morton digit of level d + 1 (when may_split)
     float hm = 0.0f;
@@ -561,13 +633,10 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
       }
     }
     hm = warp_max(hm);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    ns = __reduce_add_sync(0xffffffffu, ns);
     if (may_split) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) oc[k] += __shfl_xor_sync(0xffffffffu, oc[k], o);
+      for (int k = 0; k < 8; ++k) oc[k] = __reduce_add_sync(0xffffffffu, oc[k]);
     }
     if (lane == 0) {
       s_hm[w] = hm;
@@ -580,66 +649,55 @@ __global__ void __launch_bounds__(TREE_THREADS) k_tree_round(Tree T, const BoxDe
       hm = lane < NW ? s_hm[lane] : 0.0f;
       ns = lane < NW ? s_ns[lane] : 0u;
       hm = warp_max(hm);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+      ns = __reduce_add_sync(0xffffffffu, ns);
       // lane k < 8 holds octant k's count
       unsigned int mine = 0;
       if (lane < 8)
         for (int k = 0; k < NW; ++k) mine += s_oc[k][lane];
-      const bool sp = may_split && (double)ns > (double)split_frac * (double)c;
-      const unsigned int ne = __ballot_sync(0xffffffffu, lane < 8 && mine != 0);
-      const int nch = __popc(ne);
-      // start of octant `lane`: the counts of the octants before it
-      unsigned int before = mine;
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xffffffffu, before, o);
-        if (lane >= o) before += y;
-      }
-      before -= mine;
-      int c0 = -1;
-      if (sp && lane == 0) c0 = alloc_nodes(&T.n_nodes[0], nch, cap_nodes);
-      c0 = __shfl_sync(0xffffffffu, c0, 0);
-      const bool fits = c0 >= 0;
-      if (sp && fits && lane < 8 && mine != 0) {
-        const int cid = c0 + __popc(ne & ((1u << lane) - 1u));
-        T.start[cid] = s + before;
-        T.count[cid] = mine;
-        T.key[cid] = (T.key[id] << 3) | (unsigned long long)lane;
-        T.level[cid] = d + 1;
-        T.box[cid] = T.box[id];
-        T.parent[cid] = id;
-        T.child[cid] = -1;
-        T.nchild[cid] = 0;
-      }
-      if (lane == 0) {
-        if (sp && !fits) atomicOr(err_all, ERR_OVERFLOW);
-        if (capped && d >= dcap && (int)c > leaf_max && (double)ns > (double)split_frac * (double)c)
-          atomicOr(err_all, ERR_DEPTH);
-        atomicMax(&T.n_nodes[5], d);
-        T.hmax[id] = hm;
-        T.nsmall[id] = ns;
-        T.split[id] = (sp && fits) ? 1 : 0;
-        T.child[id] = (sp && fits) ? c0 : -1;
-        T.nchild[id] = (sp && fits) ? nch : 0;
-        T.axes[id] = 0;
-        // limit the top grid sets on every particle: H < edge_k - margin
-        T.hlim[id] = (T.parent[id] < 0) ? __dsub_rn(ldexp(bd.L, -d), bd.margin) : 1e300;
-        unsigned int cx, cy, cz;
-        cell_coords(T.key[id], d, cx, cy, cz);
-        const double inv = ldexp(1.0, -d), invk = ldexp(1.0, -bd.k);
-        const int sh = d - bd.k;
-        const double tx = ((double)(cx >> sh) + 0.5) * invk, ty = ((double)(cy >> sh) + 0.5) * invk,
-                     tz = ((double)(cz >> sh) + 0.5) * invk;
-        T.cen[id] = make_float4((float)(((double)cx + 0.5) * inv - tx), (float)(((double)cy + 0.5) * inv - ty),
-                                (float)(((double)cz + 0.5) * inv - tz), (float)inv);
-      }
+      tree_node_finish(T, id, d, bd, s, c, may_split, hm, ns, mine, dcap, leaf_max, split_frac, capped, cap_nodes,
+                       err_all);
     }
     __syncthreads();
+  }
+  // the other nodes: one warp each
+  for (int id = f0 + (int)(blockIdx.x * NW + w); id < f1; id += (int)(gridDim.x * NW)) {
+    const unsigned int c = T.count[id];
+    if (c > TREE_WARP_MAX) continue;
+    const int d = T.level[id];
+    const BoxDesc bd = box[T.box[id]];
+    const double half = __dsub_rn(ldexp(bd.L, -(d + 1)), bd.margin);
+    const unsigned int s = T.start[id];
+    const bool may_split = allow_split && d < dcap && (int)c > leaf_max;
+    const int dig = 3 * (dcap - d - 1);
+    float hm = 0.0f;
+    unsigned int ns = 0, mine = 0;
+    unsigned int oc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (unsigned int q = lane; q < c; q += 32) {
+      const float H = Hs[s + q];
+      hm = fmaxf(hm, H);
+      ns += ((double)H < half) ? 1u : 0u;
+      if (may_split) {
+        const unsigned int o = (unsigned int)(key[s + q] >> dig) & 7u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) oc[k] += (o == (unsigned int)k) ? 1u : 0u;
+      }
+    }
+    hm = warp_max(hm);
+    ns = __reduce_add_sync(0xffffffffu, ns);
+    if (may_split) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const unsigned int t = __reduce_add_sync(0xffffffffu, oc[k]);
+        if (lane == k) mine = t;
+      }
+    }
+    tree_node_finish(T, id, d, bd, s, c, may_split, hm, ns, mine, dcap, leaf_max, split_frac, capped, cap_nodes,
+                     err_all);
   }
   if (!allow_split) return;
   // the last block to finish opens the next round's frontier: the nodes this
   // round created (every block has read this round's frontier by then)
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int done = atomicAdd(reinterpret_cast<unsigned int*>(&T.n_nodes[4]), 1u);
@@ -1150,8 +1208,27 @@ __device__ __forceinline__ float tile_rlo(const Tiles& TL, const Tree& T, unsign
   return fmaf(u.x, x, fmaf(u.y, y, u.z * z));
 }
 
-// One CTA per (cell, axis) segment of at most SORT_SMALL clusters: bitonic
-// sort of (projection, cluster) in shared memory.
+// Bitonic sort of (projection, cluster) in shared memory, ordered by projection
+// then cluster index: segments of more than SORT_WARP_MAX clusters (at most
+// SORT_SMALL) take one CTA each, the others one warp each (a CTA on a few dozen
+// clusters spends its time at barriers).
+constexpr unsigned int SORT_WARP_MAX = 256;
+
+__device__ __forceinline__ void bitonic_step(float* sr, unsigned int* si, unsigned int q, unsigned int j,
+                                             unsigned int k) {
+  const unsigned int l = q ^ j;
+  if (l > q) {
+    const bool up = (q & k) == 0;
+    const float a0 = sr[q], a1 = sr[l];
+    const unsigned int i0 = si[q], i1 = si[l];
+    const bool gt = (a0 > a1) || (a0 == a1 && i0 > i1);
+    if (gt == up) {
+      sr[q] = a1; sr[l] = a0;
+      si[q] = i1; si[l] = i0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_sort_small(const uint4* __restrict__ mid_seg,
                                                    const unsigned int* __restrict__ mid_count, Tree T, Tiles TL,
                                                    float* __restrict__ sort_r, unsigned int* __restrict__ sort_i) {
@@ -1161,43 +1238,61 @@ __global__ void __launch_bounds__(256) k_sort_small(const uint4* __restrict__ mi
   const unsigned int nseg = *mid_count;
   for (unsigned int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const uint4 seg = mid_seg[sg];
-    const int id = (int)seg.x;
     const unsigned int c = seg.w, out = seg.z;
+    if (c <= SORT_WARP_MAX) continue;   // the same for the whole block
+    const int id = (int)seg.x;
     unsigned int npow = 1;
     while (npow < c) npow <<= 1;
     const unsigned int t0 = T.tile0[id];
     const float4 cc = T.cen[id];
-    {
-      const float3 u = axis_unit((int)seg.y);
-      for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
-        sr[q] = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
-        si[q] = q;
-      }
-      __syncthreads();
-      for (unsigned int k = 2; k <= npow; k <<= 1) {
-        for (unsigned int j = k >> 1; j > 0; j >>= 1) {
-          for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
-            const unsigned int l = q ^ j;
-            if (l > q) {
-              const bool up = (q & k) == 0;
-              const float a0 = sr[q], a1 = sr[l];
-              const unsigned int i0 = si[q], i1 = si[l];
-              const bool gt = (a0 > a1) || (a0 == a1 && i0 > i1);
-              if (gt == up) {
-                sr[q] = a1; sr[l] = a0;
-                si[q] = i1; si[l] = i0;
-              }
-            }
-          }
-          __syncthreads();
-        }
-      }
-      for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
-        sort_r[out + q] = sr[q];
-        sort_i[out + q] = t0 + si[q];
-      }
-      __syncthreads();
+    const float3 u = axis_unit((int)seg.y);
+    for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) {
+      sr[q] = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
+      si[q] = q;
     }
+    __syncthreads();
+    for (unsigned int k = 2; k <= npow; k <<= 1) {
+      for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+        for (unsigned int q = threadIdx.x; q < npow; q += blockDim.x) bitonic_step(sr, si, q, j, k);
+        __syncthreads();
+      }
+    }
+    for (unsigned int q = threadIdx.x; q < c; q += blockDim.x) {
+      sort_r[out + q] = sr[q];
+      sort_i[out + q] = t0 + si[q];
+    }
+    __syncthreads();
+  }
+  // small segments: one warp each, in its own slice of the arrays
+  const unsigned int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float* wr = sr + w * SORT_WARP_MAX;
+  unsigned int* wi = si + w * SORT_WARP_MAX;
+  for (unsigned int sg = blockIdx.x * nw + w; sg < nseg; sg += gridDim.x * nw) {
+    const uint4 seg = mid_seg[sg];
+    const unsigned int c = seg.w, out = seg.z;
+    if (c > SORT_WARP_MAX) continue;
+    const int id = (int)seg.x;
+    unsigned int npow = 1;
+    while (npow < c) npow <<= 1;
+    const unsigned int t0 = T.tile0[id];
+    const float4 cc = T.cen[id];
+    const float3 u = axis_unit((int)seg.y);
+    for (unsigned int q = lane; q < npow; q += 32) {
+      wr[q] = q < c ? tile_rlo(TL, T, t0 + q, cc, u) : FLT_MAX;
+      wi[q] = q;
+    }
+    __syncwarp();
+    for (unsigned int k = 2; k <= npow; k <<= 1) {
+      for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+        for (unsigned int q = lane; q < npow; q += 32) bitonic_step(wr, wi, q, j, k);
+        __syncwarp();
+      }
+    }
+    for (unsigned int q = lane; q < c; q += 32) {
+      sort_r[out + q] = wr[q];
+      sort_i[out + q] = t0 + wi[q];
+    }
+    __syncwarp();
   }
 }
 

@@ -75,11 +75,18 @@ struct BoxDesc {
 // dy > 0, or dz = dy = 0 and dx > 0 (one of each +-db).  Section II-C: the
 // sorted indices are kept per cell along these 13 axes.
 __host__ __device__ inline void axis_vec(int a, int& dx, int& dy, int& dz) {
-  // enumeration in z-major order over (dx, dy, dz) restricted to the half space
-  const signed char T[13][3] = {
-      {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1},
-      {-1, 0, 1}, {0, 0, 1},  {1, 0, 1},  {-1, 1, 1}, {0, 1, 1},   {1, 1, 1}};
-  dx = T[a][0]; dy = T[a][1]; dz = T[a][2];
+  // enumeration in z-major order over (dx, dy, dz) restricted to the half space:
+  // 0: (1, 0, 0); 1..3: (a - 2, 1, 0); 4..12: ((a - 4) % 3 - 1, (a - 4) / 3 - 1, 1).
+  // Computed, not looked up: a table indexed at run time would be built in local
+  // memory at every call.
+  if (a == 0) {
+    dx = 1; dy = 0; dz = 0;
+  } else if (a < 4) {
+    dx = a - 2; dy = 1; dz = 0;
+  } else {
+    const int b = a - 4;
+    dx = b % 3 - 1; dy = b / 3 - 1; dz = 1;
+  }
 }
 
 __host__ __device__ inline int axis_index(int dx, int dy, int dz) {

@@ -122,7 +122,7 @@ __device__ __forceinline__ DensI make_dens(bool valid, unsigned int gidx, const 
     r.p = make_float3(p.x + (c.x + shift.x), p.y + (c.y + shift.y), p.z + (c.z + shift.z));
     const float H = p.w * invL;
     r.H = H;
-    r.invH = 1.0f / H;
+    r.invH = __fdividef(1.0f, H);   // 2 ulp: enters the kernel's argument only
     r.H2 = H * H;
     r.band = BAND_REL * H * (e + H);
     r.Hphys = p.w;
@@ -402,6 +402,10 @@ struct DensAcc {
   }
 };
 
+// r from r^2 by the fast reciprocal square root (its rounding enters the kernel's
+// argument only; the neighbour decision is taken on r^2)
+__device__ __forceinline__ float pair_r(float r2) { return r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f; }
+
 // One density contribution: w and q w'(q) at q = r / H, weighted by m.
 template <bool KAHAN>
 __device__ __forceinline__ void dens_add(float r, float invH, float m, DensAcc<KAHAN>& acc, unsigned int& cnt) {
@@ -437,7 +441,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
     const int sj = __ffs(m) - 1;
     const float4 J = S.p[sj];
     const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
-    dens_add(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), I.invH, S.a[sj].z, acc, cnt);
+    dens_add(pair_r(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), I.invH, S.a[sj].z, acc, cnt);
   }
   if (own_only) return;
   // column sweep: partner side, staged partner = lane
@@ -451,7 +455,7 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
       const int li = __ffs(col) - 1;
       const float4 P = S.ip[li];
       const float dx = P.x - J.x, dy = P.y - J.y, dz = P.z - J.z;
-      dens_add(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), jinvH, P.w, pacc, pcnt);
+      dens_add(pair_r(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), jinvH, P.w, pacc, pcnt);
     }
     flush_dens(S.g[lane], pacc.total(), pcnt, dacc, dcnt);
   }
@@ -485,7 +489,7 @@ __device__ __forceinline__ void force_pair_terms(const ForceSide& a, const Force
   const float wv = vdx * rinv;
   const float mu = fminf(wv, 0.0f);
   vsig = a.c + b.c - 3.0f * mu;
-  const float Pi = -alpha * vsig * mu / (a.rho + b.rho);
+  const float Pi = __fdividef(-alpha * vsig * mu, a.rho + b.rho);
   const float Wbar = 0.5f * (Wa + Wb);
   const float coef = fmaf(a.F, Wa, fmaf(b.F, Wb, Pi * Wbar)) * rinv;
   const float hv = 0.5f * Pi * Wbar;
@@ -711,20 +715,21 @@ __device__ __forceinline__ Box3 tile_box3(const Tiles& TL, const Tree& T, unsign
   return b;
 }
 
-__device__ __forceinline__ float box_gap(const Box3& a, const Box3& b) {
+// Distance between two boxes within reach, compared squared (FP32; the
+// caller's slack, at least 1e-6 of the reach, covers the rounding of both forms).
+__device__ __forceinline__ bool box_near(const Box3& a, const Box3& b, float reach) {
   const float gx = fmaxf(0.0f, fmaxf(b.lo.x - a.hi.x, a.lo.x - b.hi.x));
   const float gy = fmaxf(0.0f, fmaxf(b.lo.y - a.hi.y, a.lo.y - b.hi.y));
   const float gz = fmaxf(0.0f, fmaxf(b.lo.z - a.hi.z, a.lo.z - b.hi.z));
-  return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+  return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= reach * reach;
 }
 
-// distance from a point to a box within reach (FP32; the caller's slack covers
-// the rounding of both)
+// distance from a point to a box within reach (as box_near)
 __device__ __forceinline__ bool near_box(const float3 p, const Box3& b, float reach) {
   const float gx = fmaxf(0.0f, fmaxf(b.lo.x - p.x, p.x - b.hi.x));
   const float gy = fmaxf(0.0f, fmaxf(b.lo.y - p.y, p.y - b.hi.y));
   const float gz = fmaxf(0.0f, fmaxf(b.lo.z - p.z, p.z - b.hi.z));
-  return sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz))) <= reach;
+  return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= reach * reach;
 }
 
 // upper end of the projection of a box on u
@@ -834,10 +839,10 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
         // the neighbours of the particles that iterate, and the clusters that
         // iterate near any particle of this one
         // (with every particle iterating, the first test covers the second)
-        pass = (A.any && box_gap(A.b, bj) <= fmaxf(A.H, Hj) + P.slack) ||
-               (!A.all && TL.active[t] && box_gap(bi, bj) <= Hj + P.slack);
+        pass = (A.any && box_near(A.b, bj, fmaxf(A.H, Hj) + P.slack)) ||
+               (!A.all && TL.active[t] && box_near(bi, bj, Hj + P.slack));
       } else {
-        pass = box_gap(bi, bj) <= reach;
+        pass = box_near(bi, bj, reach);
       }
     }
   }
@@ -947,8 +952,8 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
     if (tl < t0 + nt) {
       const Box3 bj = tile_box3(TL, T, tl, sh);
       const float Hj = TL.lo[tl].w * g.invL;
-      ok = (AB.any && box_gap(AB.b, bj) <= fmaxf(AB.H, Hj) + slack) ||
-           (!AB.all && TL.active[tl] && box_gap(bi, bj) <= Hj + slack);
+      ok = (AB.any && box_near(AB.b, bj, fmaxf(AB.H, Hj) + slack)) ||
+           (!AB.all && TL.active[tl] && box_near(bi, bj, Hj + slack));
     }
     unsigned int mask = __ballot_sync(0xffffffffu, ok);
     while (mask) {
@@ -1044,7 +1049,7 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
     bool ok = false;
     if (tl < t0 + nt) {
       const Box3 bj = tile_box3(TL, T, tl, sh);
-      ok = box_gap(bi, bj) <= fmaxf(Hi, TL.lo[tl].w * g.invL) + slack;
+      ok = box_near(bi, bj, fmaxf(Hi, TL.lo[tl].w * g.invL) + slack);
     }
     unsigned int mask = __ballot_sync(0xffffffffu, ok);
     while (mask) {
@@ -1074,8 +1079,10 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
 // side culls against the box of the cluster's iterating particles; the first pass
 // (every particle) has its own instance without that code.  Both are launched in
 // a captured step, and the one that does not match the iteration returns.
+// The first pass (PART = false) keeps to 5 blocks of 128 threads per SM (at most
+// 102 registers): with fewer warps in flight it waits longer on partner loads.
 template <bool COUNT, bool PART, bool KAHAN>
-__global__ void __launch_bounds__(SPH_THREADS) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+__global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : 5) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                          const float4* __restrict__ pos4,
                                                          const float4* __restrict__ cen4,
                                                          const float* __restrict__ sort_r,
@@ -1211,7 +1218,7 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
         const PairSetup P = pair_setup(Lq, T, box, item);
         const Box3 bi = tile_box3(TL, T, ti, P.tshA);
         const float Hi = TL.lo[ti].w * P.g.invL;
-        live = box_gap(bi, P.cellB) <= fmaxf(Hi, P.HmB) + P.slack;
+        live = box_near(bi, P.cellB, fmaxf(Hi, P.HmB) + P.slack);
         if (live && !iact) {
           // only B's active particles need this cluster: their box, in A's frame,
           // must lie within B's largest H
@@ -1220,7 +1227,7 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
                               key_float(T.alo[3 * B0 + 2]) + P.g.offB.z);
           ba.hi = make_float3(key_float(T.ahi[3 * B0]) + P.g.offB.x, key_float(T.ahi[3 * B0 + 1]) + P.g.offB.y,
                               key_float(T.ahi[3 * B0 + 2]) + P.g.offB.z);
-          live = box_gap(bi, ba) <= P.HmB + P.slack;
+          live = box_near(bi, ba, P.HmB + P.slack);
         }
       }
     }

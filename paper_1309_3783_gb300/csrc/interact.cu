@@ -603,12 +603,13 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
     S.plist[k++] = (unsigned short)(lane | (sj << 5) | (((mI >> sj) & 1u) << 10) | (((mJ >> sj) & 1u) << 11));
   }
   __syncwarp();
+  const unsigned int lt = (1u << lane) - 1u;
   for (unsigned int r0 = 0; r0 < total; r0 += 32) {
     const unsigned int e = r0 + lane;
     int li = 32 + lane;     // a key no other lane has
     float4 ci = make_float4(0.f, 0.f, 0.f, 0.f), cj = ci;
     float vs = 0.0f;
-    int sj = 0;
+    int sj = 64 + lane;     // likewise
     if (e < total) {
       const unsigned int w = S.plist[e];
       li = (int)(w & 31u);
@@ -619,21 +620,32 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
         atomicAdd(&fcnt[__float_as_int(S.ih[li].w)], 1u);
         atomicAdd(&fcnt[S.g[sj]], 1u);
       }
-      float4* dst = own_only ? &S.iacc[sj] : &S.jacc[sj];
-      atomicAdd(&dst->x, cj.x);
-      atomicAdd(&dst->y, cj.y);
-      atomicAdd(&dst->z, cj.z);
-      atomicAdd(&dst->w, cj.w);
-      atomicMax(reinterpret_cast<unsigned int*>(own_only ? &S.ivs[sj] : &S.jvs[sj]), __float_as_uint(vs));
     }
+    // Shared-memory float atomics are slow, the more so where lanes collide, so
+    // the sums are written plainly in steps that touch each particle once.  Own
+    // side: one head lane per row of the round holds the row's total.
     float vmax = vs;
     if (run_sum_max(li, ci, vmax) && li < 32) {
-      atomicAdd(&S.iacc[li].x, ci.x);
-      atomicAdd(&S.iacc[li].y, ci.y);
-      atomicAdd(&S.iacc[li].z, ci.z);
-      atomicAdd(&S.iacc[li].w, ci.w);
+      float4 t = S.iacc[li];
+      t.x += ci.x; t.y += ci.y; t.z += ci.z; t.w += ci.w;
+      S.iacc[li] = t;
       atomicMax(reinterpret_cast<unsigned int*>(&S.ivs[li]), __float_as_uint(vmax));
     }
+    __syncwarp();
+    // partner side: the lanes of one partner take turns by their rank among them
+    const unsigned int peers = __match_any_sync(0xffffffffu, sj);
+    const unsigned int rank = __popc(peers & lt);
+    const unsigned int nturn = __reduce_max_sync(0xffffffffu, e < total ? rank : 0u);
+    float4* dst = own_only ? S.iacc : S.jacc;
+    for (unsigned int r = 0; r <= nturn; ++r) {
+      if (e < total && rank == r) {
+        float4 t = dst[sj];
+        t.x += cj.x; t.y += cj.y; t.z += cj.z; t.w += cj.w;
+        dst[sj] = t;
+      }
+      __syncwarp();
+    }
+    if (e < total) atomicMax(reinterpret_cast<unsigned int*>(own_only ? &S.ivs[sj] : &S.jvs[sj]), __float_as_uint(vs));
     __syncwarp();
   }
 }

@@ -28,6 +28,11 @@ amortised: the same run with the decomposition kept over steps while it stays
 
 workloads: the other two single-box workloads, a shorter run each.
 
+precision: the headline workload and the 262,144-particle box run again from the
+        same state with plain FP32 positions (sph_params.precision = 1) beside the
+        default offsets from each cell's centre: throughput, FP64 re-decisions per
+        pass and the largest relative density difference between the two.
+
 serving: the served batch -- 512 independent jittered-lattice boxes with
         particle counts log-uniform in [1k, 262k] (per-box seeds), each request
         advancing 10 kick-drift-kick steps -- through the continuous-batching
@@ -363,9 +368,13 @@ def run_ours(args, rank, world, local_rank):
     }
     out["amortised"] = run_reuse_leg(sph, torch, b, box, dt, stream, args, flush)
     out["axis_sorts"] = run_sort_leg(sph, torch, b, box, stream, args)
+    state = {k: b.get(k) for k in ("x", "v", "u", "h", "a", "dudt")}
     b.close()
+    if not args.no_precision:
+        out["precision"] = {args.workload: run_precision_leg(sph, torch, box, state, dt, stream, args)}
     if not args.no_extra_workloads:
-        out["workloads"] = run_other_workloads(sph, torch, ctx, stream, args, rank)
+        out["workloads"] = run_other_workloads(sph, torch, ctx, stream, args, rank,
+                                               None if args.no_precision else out.setdefault("precision", {}))
     if not args.no_serving:
         out["serving"] = run_serving(sph, ctx)
     sph.sph_ctx_destroy(ctx)
@@ -377,8 +386,9 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ other legs
-def run_other_workloads(sph, torch, ctx, stream, args, rank, steps=10, warmup=3):
-    """The other single-box workloads, a shorter run each (leaf size 400, clusters of 32)."""
+def run_other_workloads(sph, torch, ctx, stream, args, rank, precision=None, steps=10, warmup=3):
+    """The other single-box workloads, a shorter run each (leaf size 400, clusters of 32);
+    the 262,144-particle box also in both position precisions (into `precision`)."""
     out = {}
     for name, (make, recipe) in WORKLOADS.items():
         if name == args.workload:
@@ -394,8 +404,52 @@ def run_other_workloads(sph, torch, ctx, stream, args, rank, steps=10, warmup=3)
             del flush
             out[name] = {"value": box.n * steps / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms) / steps,
                          "steps": steps, "recipe": recipe}
+            if precision is not None and name == "plummer-262144":
+                state = {k: b.get(k) for k in ("x", "v", "u", "h", "a", "dudt")}
+                args_small = argparse.Namespace(leaf_max=400, cluster_max=32, warmup=warmup, steps=steps)
+                precision[name] = run_precision_leg(sph, torch, box, state, dt, stream, args_small)
         finally:
             b.close()
+    return out
+
+
+def run_precision_leg(sph, torch, box, state, dt, stream, args):
+    """The same state in both position precisions (sph_params.precision): offsets
+    from each cell's centre taken from the FP64 positions (0, the default) and plain
+    FP32 positions x / L (1).  Per mode: throughput of the stepping run, FP64
+    re-decisions of one density and force pass, and the largest relative
+    difference of the densities of that pass from the default mode's (the default
+    mode is within 1e-6 of the FP64 oracle in the parity tests)."""
+    out, rho = {}, {}
+    for prec, name in ((0, "cell_offsets"), (1, "plain_fp32")):
+        p = sph.sph_params_default()
+        p.precision = prec
+        ctx = sph.sph_ctx_create(p, device=torch.cuda.current_device())
+        sph.sph_ctx_set_stream(ctx, stream.cuda_stream)
+        b = sph.Box(ctx, box.n, box.L, True)
+        try:
+            b.set(state["x"], state["v"], box.m, state["u"], state["h"])
+            b.set_leaf_max(args.leaf_max)
+            b.set_cluster_max(args.cluster_max)
+            b.count_pairs(True)
+            b.density()
+            rho[prec] = b.get("rho").astype(np.float64)
+            b.force()
+            st = b.stats()
+            b.count_pairs(False)
+            b.set_field("a", state["a"])
+            b.set_field("dudt", state["dudt"])
+            for _ in range(args.warmup):
+                b.step(dt)
+            torch.cuda.synchronize()
+            ms = sum(timed_steps(torch, b, dt, stream, args.steps))
+            out[name] = {"value": box.n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+                         "fp64_decisions_per_pass": st["guard_rechecks"],
+                         "pairs_per_pass": st["force_pairs"]}
+        finally:
+            b.close()
+            sph.sph_ctx_destroy(ctx)
+    out["plain_fp32"]["rho_max_rel_diff_from_cell_offsets"] = float(np.max(np.abs(rho[1] - rho[0]) / rho[0]))
     return out
 
 
@@ -669,6 +723,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the paper's leaf_max = 400")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-batch latency run")
     ap.add_argument("--no-extra-workloads", action="store_true", help="skip the other single-box workloads")
+    ap.add_argument("--no-precision", action="store_true", help="skip the plain-FP32 position comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

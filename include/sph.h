@@ -104,6 +104,15 @@ typedef struct sph_params {
     int32_t compensated;  /* density sums with compensated (Kahan-Neumaier)
                              summation: 1 on, 0 off, -1 on from n_ngb >= 100,
                              where the neighbour sums have many terms (-1)       */
+    int32_t precision;    /* position precision of the pair arithmetic: 0 = each
+                             particle's offset from its cell's centre, rounded once
+                             to FP32 from the FP64 position (the error scales with
+                             the cell); 1 = plain FP32: positions held as x / L
+                             rounded to FP32 in the box frame (error up to 2^-25 L
+                             whatever the cell), the offsets taken from them.  In
+                             both, counts and pair sets stay exact: the guard band
+                             of the FP32 decision covers the rounding and pairs
+                             inside it are decided in FP64 (0)                   */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;

@@ -953,9 +953,16 @@ __global__ void k_shift(long long N, int box_shift, const unsigned long long* __
     // x / L: a power-of-two L scales exactly, so the FP64 division is needed only otherwise
     const bool p2 = box[b].pow2 != 0;
     const double iL = box[b].invL;
-    const double ux = p2 ? x[3ll * i] * iL : __ddiv_rn(x[3ll * i], L);
-    const double uy = p2 ? x[3ll * i + 1] * iL : __ddiv_rn(x[3ll * i + 1], L);
-    const double uz = p2 ? x[3ll * i + 2] * iL : __ddiv_rn(x[3ll * i + 2], L);
+    double ux = p2 ? x[3ll * i] * iL : __ddiv_rn(x[3ll * i], L);
+    double uy = p2 ? x[3ll * i + 1] * iL : __ddiv_rn(x[3ll * i + 1], L);
+    double uz = p2 ? x[3ll * i + 2] * iL : __ddiv_rn(x[3ll * i + 2], L);
+    if (box[b].global32) {
+      // plain FP32: the position is held as x / L rounded to FP32 (the offset below
+      // then carries that rounding, up to 2^-25 of L per coordinate)
+      ux = (double)__double2float_rn(ux);
+      uy = (double)__double2float_rn(uy);
+      uz = (double)__double2float_rn(uz);
+    }
     double ox = ux - ((double)cx + 0.5) * inv, oy = uy - ((double)cy + 0.5) * inv, oz = uz - ((double)cz + 0.5) * inv;
     if (box[b].periodic) {
       // a particle kept in its cell after a drift across the boundary: nearest image

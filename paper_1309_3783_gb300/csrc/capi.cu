@@ -489,6 +489,7 @@ sph_status Engine::build_once(bool* retry) {
     d.Hmax = 0.0f;
     d.Hmin = INFINITY;
     d.err = 0;
+    d.global32 = prm.precision != 0 ? 1u : 0u;
     d.k = 0;
     d.drift2 = 0.0f;
     d.drift_u = 0.0f;
@@ -1559,6 +1560,7 @@ void sph_params_default(sph_params* p) {
   p->sort_merge = 0;
   p->cluster_max = 32;
   p->compensated = -1;
+  p->precision = 0;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
@@ -1569,7 +1571,8 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
   if (params) p = *params;
   if (!(p.gamma_kernel > 0) || !(p.n_ngb > 0) || !(p.gamma_gas > 1) || p.h_max_iter < 1 || p.leaf_max < 1 ||
       !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0) ||
-      !(p.split_headroom >= 0 && p.split_headroom < 1) || p.cluster_max < 1 || p.cluster_max > 32)
+      !(p.split_headroom >= 0 && p.split_headroom < 1) || p.cluster_max < 1 || p.cluster_max > 32 ||
+      (p.precision != 0 && p.precision != 1))
     return SPH_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;

@@ -23,6 +23,9 @@ struct ItemGeom {
   float3 offB;      // centre of B minus centre of A (units of L), exact: e * db
   float offBp;      // projection of offB on the axis: e |db|
   float invL;
+  float eb;         // length scale of the position rounding: the cell edge, or 1 (L) for
+                    //   plain FP32 positions; the guard band is 2^-17 H (eb + H)
+  float es;         // absolute rounding of plain FP32 positions added to the culling slack
   float L32;        // L in FP32
   float drift;      // largest displacement since the decomposition was built (units of L)
   double L, halfL;
@@ -40,6 +43,8 @@ __device__ __forceinline__ ItemGeom item_geom(const Tree& T, const BoxDesc* box,
   const int n2 = dx * dx + dy * dy + dz * dz;
   g.offBp = g.e * (n2 == 1 ? 1.0f : (n2 == 2 ? 1.41421356237f : 1.73205080757f));
   g.invL = (float)bd.invL;
+  g.eb = bd.global32 ? 1.0f : g.e;
+  g.es = bd.global32 ? 9.5367431640625e-07f : 0.0f;   // 2^-20 L: the 2^-25 rounding of both positions
   g.L32 = (float)bd.L;
   g.drift = bd.drift_u;
   g.L = bd.L;
@@ -744,6 +749,14 @@ __device__ __forceinline__ bool near_box(const float3 p, const Box3& b, float re
   return fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= reach * reach;
 }
 
+// a box moved by an offset (one rounding per bound, within the culling slack)
+__device__ __forceinline__ Box3 box_shift(const Box3& b, float3 d) {
+  Box3 r;
+  r.lo = make_float3(b.lo.x + d.x, b.lo.y + d.y, b.lo.z + d.z);
+  r.hi = make_float3(b.hi.x + d.x, b.hi.y + d.y, b.hi.z + d.z);
+  return r;
+}
+
 // upper end of the projection of a box on u
 __device__ __forceinline__ float box_rhi(const Box3& b, float3 u) {
   return fmaf(u.x, u.x >= 0.0f ? b.hi.x : b.lo.x,
@@ -806,12 +819,33 @@ __device__ __forceinline__ PairSetup pair_setup(const Lists& Lq, const Tree& T, 
   const unsigned int sbB = T.sortbase[P.B];
   P.sb = sbB == SORT_NONE ? SORT_NONE : sbB + (unsigned int)__popc(T.axes[P.B] & ((1u << ax) - 1u)) * P.ntj;
   P.HmB = T.hmax[P.B] * P.g.invL;
-  P.slack = P.g.e * 1.52587890625e-05f + 1e-6f * fmaxf(P.HmB, T.hmax[P.A] * P.g.invL);   // 2^-16 e
+  P.slack = P.g.e * 1.52587890625e-05f + P.g.es + 1e-6f * fmaxf(P.HmB, T.hmax[P.A] * P.g.invL);   // 2^-16 e
   // B's cell, widened by the drift of particles kept in it since the build
   const float h = 0.5f * P.g.e + P.g.drift;
   P.cellB.lo = make_float3(P.g.offB.x - h, P.g.offB.y - h, P.g.offB.z - h);
   P.cellB.hi = make_float3(P.g.offB.x + h, P.g.offB.y + h, P.g.offB.z + h);
   return P;
+}
+
+// The frame of a pair task's particle arithmetic: the centre of the own cluster's
+// leaf.  A pair of large cells that cannot split (one particle of large H in it
+// is enough) still holds particles of small H; in A's frame their positions
+// would be rounded at A's scale, in their leaf's frame at the leaf's.  The own
+// offsets are used as stored (sh_own = -leaf centre cancels their leaf centre
+// exactly), B's particles move by the exact dyadic offset sh_part, so each
+// position is rounded once, at most at A's scale: the guard band stays valid.
+// d: the leaf centre in A's frame (exact), for moving boxes between the frames.
+struct LeafFrame {
+  float3 sh_own, sh_part, d;
+};
+
+__device__ __forceinline__ LeafFrame leaf_frame(const Tiles& TL, const Tree& T, unsigned int ti, const PairSetup& P) {
+  const float4 cl = TL.cen[ti], ca = T.cen[P.A];
+  LeafFrame F;
+  F.sh_own = make_float3(-cl.x, -cl.y, -cl.z);
+  F.d = make_float3(cl.x - ca.x, cl.y - ca.y, cl.z - ca.z);
+  F.sh_part = make_float3(P.shB.x - F.d.x, P.shB.y - F.d.y, P.shB.z - F.d.z);
+  return F;
 }
 
 // Lane-parallel scan of B's sorted cluster list for the i cluster (box bi,
@@ -873,22 +907,25 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
     Counters& C) {
   const int lane = threadIdx.x & 31;
   const PairSetup P = pair_setup(Lq, T, box, item);
-  const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+  const LeafFrame F = leaf_frame(TL, T, ti, P);
+  const Box3 bi = tile_box3(TL, T, ti, P.tshA);          // the cluster in A's frame (the sorted sweep)
+  const Box3 bil = tile_box3(TL, T, ti, F.sh_own);       // ... and in its leaf's frame (the particles)
   const float Hi = TL.lo[ti].w * P.g.invL;
   const float rhi_i = box_rhi(bi, P.u);
   const unsigned int ni = TL.n[ti];
   const bool vi = (unsigned int)lane < ni;
   const unsigned char* actp = PART ? act : nullptr;
-  const DensI I = load_dens(vi, TL.start[ti] + lane, P.shA, pos4, cen4, actp, P.g.invL, P.g.e);
+  const DensI I = load_dens(vi, TL.start[ti] + lane, F.sh_own, pos4, cen4, actp, P.g.invL, P.g.eb);
   dens_stage_own(S, lane, I);
-  const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
+  const ActiveBox AB = PART ? active_box(I, bil, Hi) : ActiveBox{bil, Hi, true, true};
+  const ActiveBox ABc{box_shift(AB.b, F.d), AB.H, AB.any, AB.all};   // in A's frame
   DensAcc<KAHAN> acc;
   unsigned int cnt = 0, q = 0;
   for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
     unsigned int jt, jn, js;
     bool stop;
     unsigned int mask =
-        scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, AB, &jt, &jn, &js, &stop);
+        scan_clusters<true>(P, T, TL, sort_r, sort_i, e0, bi, rhi_i, Hi, ABc, &jt, &jn, &js, &stop);
     if (stop) break;
     // the loads of the next candidate cluster are issued before the current
     // one is tested, so that their latency overlaps that work
@@ -912,11 +949,11 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
         ng = __shfl_sync(0xffffffffu, js, k) + lane;
         nr = fetch_dens(nv, ng, pos4, cen4, actp);
       }
-      const DensI J = make_dens(vj, gj, cr, P.shB, P.g.invL, P.g.e);
+      const DensI J = make_dens(vj, gj, cr, F.sh_part, P.g.invL, P.g.eb);
       // stage only the partners within reach: of the particles that iterate (own
       // side), or, when the partner iterates, of any particle of the cluster
       const bool pass = vj && ((AB.any && near_box(J.p, AB.b, fmaxf(AB.H, J.H) + P.slack)) ||
-                               (!AB.all && J.act && near_box(J.p, bi, J.H + P.slack)));
+                               (!AB.all && J.act && near_box(J.p, bil, J.H + P.slack)));
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
@@ -943,13 +980,13 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
   const ItemGeom g = item_geom(T, box, A, 0);
   const float4 cA = T.cen[A];
   const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-  const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+  const float slack = g.e * 1.52587890625e-05f + g.es + 1e-6f * T.hmax[A] * g.invL;
   const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
   const Box3 bi = tile_box3(TL, T, ti, sh);
   const float Hi = TL.lo[ti].w * g.invL;
   const bool vi = (unsigned int)lane < TL.n[ti];
   const unsigned char* actp = PART ? act : nullptr;
-  const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, actp, g.invL, g.e);
+  const DensI I = load_dens(vi, TL.start[ti] + lane, sh, pos4, cen4, actp, g.invL, g.eb);
   dens_stage_own(S, lane, I);
   const ActiveBox AB = PART ? active_box(I, bi, Hi) : ActiveBox{bi, Hi, true, true};
   DensAcc<KAHAN> acc;
@@ -973,7 +1010,7 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
       mask &= mask - 1;
       const unsigned int tj = b0 + (unsigned int)k;
       const bool vj = (unsigned int)lane < TL.n[tj];
-      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, actp, g.invL, g.e);
+      const DensI J = load_dens(vj, TL.start[tj] + lane, sh, pos4, cen4, actp, g.invL, g.eb);
       const bool pass = vj && ((AB.any && near_box(J.p, AB.b, fmaxf(AB.H, J.H) + slack)) ||
                                (!AB.all && J.act && near_box(J.p, bi, J.H + slack)));
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
@@ -998,11 +1035,13 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
     unsigned int* fcnt, ForceShared& S, Counters* C) {
   const int lane = threadIdx.x & 31;
   const PairSetup P = pair_setup(Lq, T, box, item);
-  const Box3 bi = tile_box3(TL, T, ti, P.tshA);
+  const LeafFrame F = leaf_frame(TL, T, ti, P);
+  const Box3 bi = tile_box3(TL, T, ti, P.tshA);          // the cluster in A's frame (the sorted sweep)
+  const Box3 bil = tile_box3(TL, T, ti, F.sh_own);       // ... and in its leaf's frame (the particles)
   const float Hi = TL.lo[ti].w * P.g.invL;
   const float rhi_i = box_rhi(bi, P.u);
   const bool vi = (unsigned int)lane < TL.n[ti];
-  const ForceI I = load_force(vi, TL.start[ti] + lane, P.shA, pos4, cen4, vel4, ghost4, P.g.invL, P.g.L32, P.g.e);
+  const ForceI I = load_force(vi, TL.start[ti] + lane, F.sh_own, pos4, cen4, vel4, ghost4, P.g.invL, P.g.L32, P.g.eb);
   force_stage_own(S, lane, I);
   unsigned int q = 0;
   for (unsigned int e0 = 0; e0 < P.ntj; e0 += 32) {
@@ -1016,9 +1055,9 @@ __device__ __forceinline__ void force_pair_task(int item, unsigned int ti, const
       const int k = __ffs(mask) - 1;
       mask &= mask - 1;
       const bool vj = (unsigned int)lane < __shfl_sync(0xffffffffu, jn, k);
-      const ForceI J = load_force(vj, __shfl_sync(0xffffffffu, js, k) + lane, P.shB, pos4, cen4, vel4, ghost4,
-                                  P.g.invL, P.g.L32, P.g.e);
-      const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + P.slack);
+      const ForceI J = load_force(vj, __shfl_sync(0xffffffffu, js, k) + lane, F.sh_part, pos4, cen4, vel4, ghost4,
+                                  P.g.invL, P.g.L32, P.g.eb);
+      const bool pass = vj && near_box(J.p, bil, fmaxf(Hi, J.H) + P.slack);
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
@@ -1045,12 +1084,12 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
   const ItemGeom g = item_geom(T, box, A, 0);
   const float4 cA = T.cen[A];
   const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
-  const float slack = g.e * 1.52587890625e-05f + 1e-6f * T.hmax[A] * g.invL;
+  const float slack = g.e * 1.52587890625e-05f + g.es + 1e-6f * T.hmax[A] * g.invL;
   const unsigned int t0 = T.tile0[A], nt = T.ntile[A];
   const Box3 bi = tile_box3(TL, T, ti, sh);
   const float Hi = TL.lo[ti].w * g.invL;
   const bool vi = (unsigned int)lane < TL.n[ti];
-  const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.e);
+  const ForceI I = load_force(vi, TL.start[ti] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.eb);
   force_stage_own(S, lane, I);
   unsigned int q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
@@ -1069,7 +1108,7 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
       mask &= mask - 1;
       const unsigned int tj = b0 + (unsigned int)k;
       const bool vj = (unsigned int)lane < TL.n[tj];
-      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.e);
+      const ForceI J = load_force(vj, TL.start[tj] + lane, sh, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.eb);
       const bool pass = vj && near_box(J.p, bi, fmaxf(Hi, J.H) + slack);
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);

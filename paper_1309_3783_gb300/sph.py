@@ -35,7 +35,8 @@ class sph_params(C.Structure):
                 ("alpha_visc", C.c_float), ("c_cfl", C.c_float), ("h_tol", C.c_float),
                 ("h_max_iter", C.c_int32), ("leaf_max", C.c_int32), ("split_frac", C.c_float),
                 ("max_depth", C.c_int32), ("split_headroom", C.c_float), ("reuse", C.c_int32),
-                ("sort_merge", C.c_int32), ("cluster_max", C.c_int32), ("compensated", C.c_int32)]
+                ("sort_merge", C.c_int32), ("cluster_max", C.c_int32), ("compensated", C.c_int32),
+                ("precision", C.c_int32)]
 
 
 class sph_stats(C.Structure):

@@ -449,3 +449,62 @@ def test_compensated_sums_at_high_neighbour_counts(api):
     print(f"mean neighbours {ref['count'].mean():.0f}; max relative error of rho and sum W: plain {err[0]:.2e}, "
           f"compensated {err[1]:.2e}")
     assert err[1] < err[0]
+
+
+# ------------------------------------------------------------------ position precision
+def test_plain_fp32_positions_keep_counts_but_lose_accuracy(api):
+    """Plain FP32 positions (sph_params.precision = 1: x / L rounded to FP32 in the
+    box frame) against the default offsets from each cell's centre, on a box with
+    dense cores (support radii down to ~1e-4 L).  Both keep the neighbour counts
+    and the force pair sets exact (the guard band covers each rounding, and pairs
+    inside it are decided in FP64), but plain FP32 positions carry an absolute
+    error of up to 2^-25 L, a large relative error at small separations: the
+    densities and forces drift from the FP64 oracle by far more than with offsets
+    whose rounding scales with the cell.  The dense cores here straddle cell
+    boundaries inside pairs of large cells that cannot split (their other
+    particles have large H): pair tasks take the own leaf's frame, so that those
+    positions are still rounded at the leaf's scale."""
+    box = inputs.plummer_box(n=20000, n_spheres=2, scale=0.002, seed=7)
+    # both modes at the same converged h (N~ = 48), taken from one h iteration
+    c = make_ctx(api)
+    try:
+        b = api.box_from(c, box)
+        try:
+            st, nu, _ = b.h_update()
+            box.h = b.get("h")
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    assert nu == 0
+    H = orc.support_radius(box.h)
+    ref = orc.full_step(box, iterate_h=False, method="kdtree")
+    print(f"[precision] neighbour counts up to {int(ref['count'].max())} (median {int(np.median(ref['count']))})")
+    t, _, _, _ = orc.neighbour_pairs(box.x, None, box.L, True, None, "force", Hall=H, method="kdtree")
+    per = np.bincount(t, minlength=box.n)
+    rms = np.sqrt(np.mean(np.sum(ref["a"] ** 2, axis=1)))
+    err, rechecks = {}, {}
+    for prec in (0, 1):
+        c = make_ctx(api, precision=prec, leaf_max=48)
+        try:
+            b = api.box_from(c, box)
+            try:
+                b.count_pairs(True)
+                b.density()
+                g = {k: b.get(k) for k in ("count", "rho")}
+                b.force()
+                g["a"], g["fc"] = b.get("a"), b.get("force_count")
+                rechecks[prec] = b.stats()["guard_rechecks"]
+            finally:
+                b.close()
+        finally:
+            api.sph_ctx_destroy(c)
+        assert np.array_equal(g["count"], ref["count"]), prec
+        assert np.array_equal(g["fc"], per), prec
+        err[prec] = (max_rel(g["rho"], ref["rho"]), float(np.max(np.abs(g["a"] - ref["a"])) / rms))
+    print(f"[precision] H in [{H.min():.1e}, {H.max():.1e}]: cell offsets rho {err[0][0]:.1e}, a {err[0][1]:.1e} of rms, "
+          f"{rechecks[0]} FP64 decisions; plain FP32 rho {err[1][0]:.1e}, a {err[1][1]:.1e} of rms, "
+          f"{rechecks[1]} FP64 decisions")
+    assert err[0][0] <= 1e-5 and err[0][1] <= 1e-4
+    assert err[1][0] > 10 * err[0][0]
+    assert rechecks[1] > rechecks[0]

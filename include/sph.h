@@ -244,6 +244,17 @@ sph_status sph_box_set(sph_box* box, const double* x, const float* v, const floa
  * n mismatch). */
 sph_status sph_box_set_field(sph_box* box, int field, const void* src, int64_t n, int mem);
 
+/* Mark the box's first n_owned particles (caller order) as its own and the
+ * others as a halo: copies of particles that another rank owns in a spatial
+ * decomposition of one box over several GPUs (the distributed-memory version
+ * the paper names as future work, Section IV).  Halo particles take part in
+ * every pass, so that the owned particles find all their neighbours, but only
+ * owned particles enter the conservation sums (SPH_FIELD_REDUCTIONS), which the
+ * ranks then add.  Default: every particle (n_owned = n).  Kept until the next
+ * call; the reductions of an earlier force pass are invalidated.
+ * Errors: SPH_E_INVALID (n_owned outside 0..n). */
+sph_status sph_box_set_owned(sph_box* box, int64_t n_owned);
+
 /* Turn exact pair counting on (1) or off (0) for the following passes; the
  * counts appear in sph_stats.  Counting adds atomics to the pair kernels. */
 sph_status sph_box_count_pairs(sph_box* box, int on);

@@ -206,6 +206,7 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
     d.margin = boxes[b].L * std::ldexp(1.0, -50);
     d.off = off[b];
     d.n = boxes[b].n;
+    d.nown = boxes[b].n;
     d.periodic = boxes[b].periodic;
     int ex = 0;
     d.pow2 = std::frexp(boxes[b].L, &ex) == 0.5 ? 1u : 0u;
@@ -1653,6 +1654,14 @@ sph_status sph_box_set(sph_box* b, const double* x, const float* v, const float*
 sph_status sph_box_set_field(sph_box* b, int field, const void* src, int64_t n, int mem) {
   BOX_PRE(b);
   return from_engine(b, b->eng->set_field(0, field, src, n, mem));
+}
+
+sph_status sph_box_set_owned(sph_box* b, int64_t n_owned) {
+  BOX_PRE(b);
+  if (n_owned < 0 || n_owned > b->eng->spec[0].n) return set_err(b->ctx, SPH_E_INVALID, "n_owned must be in 0..n");
+  b->eng->hbox[0].nown = n_owned;
+  b->eng->have_force = false;       // the sums of the last force pass counted other particles
+  return from_engine(b, b->eng->upload_boxes());
 }
 
 sph_status sph_box_count_pairs(sph_box* b, int on) {

@@ -1544,15 +1544,18 @@ __global__ void k_set_drift(int nbox, BoxDesc* __restrict__ box, const unsigned 
 // thread accumulates its particles of the box in FP64 registers, then one block
 // reduction and eight atomics per box.
 __global__ void __launch_bounds__(256) k_reduce(int nbox, const long long* __restrict__ boff,
+                                                const BoxDesc* __restrict__ box, const unsigned int* __restrict__ perm,
                                                 const float4* __restrict__ cen4, const float4* __restrict__ vel4,
                                                 const float4* __restrict__ facc, double* __restrict__ red) {
   pdl_wait();
   __shared__ double part[8][8];
   for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
     const long long p0 = boff[b], p1 = boff[b + 1];
+    const long long nown = box[b].nown;
     double val[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long p = p0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < p1;
          p += (long long)gridDim.x * blockDim.x) {
+      if ((long long)perm[p] - p0 >= nown) continue;   // a halo particle: summed by its owner
       const double m = cen4[p].w;
       const float4 vv = vel4[p];
       const float4 a = facc[p];
@@ -1879,7 +1882,8 @@ void launch_reduce(Engine& E) {
   long long maxn = 1;
   for (int b = 0; b < E.nbox; ++b) maxn = std::max(maxn, E.spec[b].n);
   const int gx = (int)std::max<long long>(1, std::min<long long>((maxn + 255) / 256, (E.nsm * 4 + E.nbox - 1) / E.nbox));
-  launch_pdl(k_reduce, dim3(gx, std::min(E.nbox, 65535)), 256, E.st, E.nbox, E.boff.p, E.cen4.p, E.vel4.p, E.facc.p,
+  launch_pdl(k_reduce, dim3(gx, std::min(E.nbox, 65535)), 256, E.st, E.nbox, E.boff.p, E.box.p, E.perm.p, E.cen4.p,
+             E.vel4.p, E.facc.p,
                                                                  E.red.p); count_launch();
 }
 

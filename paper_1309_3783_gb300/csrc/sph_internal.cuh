@@ -69,6 +69,8 @@ struct BoxDesc {
   double dt_prev[3];    // time steps of the box's three previous steps
   float hw[4][4];       // extrapolation weights of the last roots at the new time, row l for
                         //   l earlier roots besides the last (the box's level, kept on the device)
+  long long nown;         // the box's first nown particles (caller order) enter the conservation
+                          //   sums; the others are a halo of particles owned elsewhere
   unsigned int global32;  // 1: plain FP32 positions (x / L rounded to FP32 in the box frame; the
                           //   offsets are taken from them); 0: offsets from the FP64 positions
 };

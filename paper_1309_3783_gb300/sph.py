@@ -74,6 +74,7 @@ _SIGS = {
     "sph_box_create": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int, C.POINTER(_P)]),
     "sph_box_set": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int]),
     "sph_box_count_pairs": (C.c_int, [_P, C.c_int]),
+    "sph_box_set_owned": (C.c_int, [_P, C.c_int64]),
     "sph_box_set_field": (C.c_int, [_P, C.c_int, _P, C.c_int64, C.c_int]),
     "sph_box_destroy": (C.c_int, [_P]),
     "sph_build": (C.c_int, [_P]),
@@ -215,6 +216,10 @@ def sph_box_set_field(box, ctx, field, src, n: int):
     dtype, per = _FIELD_TYPE[f]
     p, mem, keep = _arg(src, dtype, n * per)
     _check(load().sph_box_set_field(box, f, p, n, mem), ctx)
+
+
+def sph_box_set_owned(box, ctx, n_owned: int):
+    _check(load().sph_box_set_owned(box, int(n_owned)), ctx)
 
 
 def sph_box_count_pairs(box, ctx, on: bool):
@@ -417,6 +422,9 @@ class Box:
     def set_field(self, field, src):
         sph_box_set_field(self.h, self.ctx, field, src, self.n)
         return self
+
+    def set_owned(self, n_owned):
+        sph_box_set_owned(self.h, self.ctx, n_owned)
 
     def count_pairs(self, on=True):
         sph_box_count_pairs(self.h, self.ctx, on)

@@ -113,6 +113,12 @@ typedef struct sph_params {
                              both, counts and pair sets stay exact: the guard band
                              of the FP32 decision covers the rounding and pairs
                              inside it are decided in FP64 (0)                   */
+    int32_t graphs;       /* 1: a kick-drift-kick step of sph_step is launched as
+                             one CUDA graph with conditional nodes (captured after
+                             a host-driven build and launched again while the boxes
+                             keep their top levels and the capacities hold; one
+                             synchronisation per step); 0: every launch from the
+                             host, with the synchronisations of a build (1)      */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;
@@ -178,6 +184,9 @@ typedef struct sph_stats {
                                      starting h: the previous step's roots, extrapolated) */
     int64_t leaf_max;           /* the box's split threshold (set or autotuned)      */
     int64_t cluster_max;        /* the box's particles per cluster (set or autotuned) */
+    int64_t graph_steps;        /* steps of sph_step run as one captured graph (params.graphs) */
+    int64_t host_steps;         /* steps whose passes were launched from the host       */
+    int64_t host_syncs;         /* synchronisations of the host with the box's stream   */
 } sph_stats;
 
 /* Device time of one phase of the path (CUDA events on the stream the phase runs

@@ -51,6 +51,60 @@ __global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box,
   }
 }
 
+// ============================================================== captured rebuild steps
+// The fields a build recomputes for every box, reset on the device (the host
+// build resets them and uploads the table; the top level k stays).
+__global__ void k_box_reset(int nbox, BoxDesc* box) {
+  pdl_wait();
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    box[b].Hmax = 0.0f;
+    box[b].Hmin = __int_as_float(0x7f800000);
+    box[b].err = 0u;
+    box[b].drift2 = 0.0f;
+    box[b].drift_u = 0.0f;
+  }
+}
+
+// After the ingest of a captured rebuild step: the checks of the host build on
+// each box's support radii -- valid input, H_max within the box (periodic: below
+// L/4) -- and the top level they give (the finest level whose edge clears H_max
+// grown by the headroom, at most dc), which must be the level the graph was
+// captured with (ERR_SHAPE otherwise).
+__global__ void k_check_shape(int nbox, const BoxDesc* __restrict__ box, int dc, float headroom,
+                              unsigned int* __restrict__ err_all) {
+  pdl_wait();
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    const BoxDesc& d = box[b];
+    if (d.err & ERR_BAD_INPUT) atomicOr(err_all, ERR_BAD_INPUT);
+    const int k0 = d.periodic ? 2 : 0;
+    if (!((double)d.Hmax < ldexp(d.L, -k0) - d.margin)) {
+      atomicOr(err_all, ERR_H_TOO_LARGE);
+      continue;
+    }
+    const double hr = 1.0 + (double)headroom;
+    int k = k0;
+    while (k + 1 <= dc && (double)d.Hmax * hr < ldexp(d.L, -(k + 1)) - d.margin) ++k;
+    if (k != d.k) atomicOr(err_all, ERR_SHAPE);
+  }
+}
+
+// The end of a captured build: it held when no check failed and every count fits
+// its capacity (tree nodes, selfs, pairs, the empty last expansion queue, the
+// task tables, the global sort's segments); the IF node of the passes follows.
+__global__ void k_check_build(cudaGraphConditionalHandle ok, const unsigned int* __restrict__ err_all,
+                              const int* __restrict__ t_n, int cap_nodes, const int* __restrict__ counts, int cap_self,
+                              int cap_pair, int last_q, unsigned int cap_ptask, unsigned int cap_stask,
+                              const unsigned long long* __restrict__ big_count, int cap_big,
+                              unsigned int* __restrict__ status) {
+  pdl_wait();
+  const unsigned int bad = ERR_BAD_INPUT | ERR_H_TOO_LARGE | ERR_OVERFLOW | ERR_DEPTH | ERR_SHAPE;
+  const bool held = (*err_all & bad) == 0u && t_n[0] <= cap_nodes && counts[0] <= cap_self && counts[1] <= cap_pair &&
+                    counts[last_q] == 0 && (unsigned int)counts[6] <= cap_ptask &&
+                    (unsigned int)counts[7] <= cap_stask && (long long)(*big_count >> 40) <= (long long)cap_big;
+  cudaGraphSetConditional(ok, held ? 1u : 0u);
+  *status = held ? 1u : 0u;
+}
+
 // ============================================================== keys
 // key = box << (3 dcap) | Morton(floor((x / L) 2^dcap)) with the cell index
 // clamped to [0, 2^dcap - 1]; the value is the input index.
@@ -1147,9 +1201,14 @@ __global__ void k_mark_axes(Lists Lq, int cap_pair, Tree T) {
 // at once, so an order would end no sweep earlier (sortbase = SORT_NONE).
 // Cells above SORT_SMALL clusters also list their (cell, axis) segments for the
 // global sort.
+// cap_entries, cap_bigent: the storage of the sorted lists and of the global
+// sort's keys (a captured step; the host build passes no limit and sizes the
+// storage afterwards).  A cell whose lists do not fit stays unsorted (its
+// clusters are then swept in their own order) and sets ERR_OVERFLOW.
 __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big_node, int* __restrict__ big_axis,
                              unsigned int* __restrict__ big_off, unsigned long long* __restrict__ big_count,
-                             int cap_big, uint4* __restrict__ mid_seg, unsigned int* __restrict__ mid_count) {
+                             int cap_big, uint4* __restrict__ mid_seg, unsigned int* __restrict__ mid_count,
+                             unsigned int cap_entries, unsigned int cap_bigent, unsigned int* __restrict__ err_all) {
   pdl_wait();
   nnodes = min(nnodes, T.n_nodes[0]);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nnodes; id += gridDim.x * blockDim.x) {
@@ -1162,6 +1221,11 @@ __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big
     }
     const int na = __popc(ax);
     const unsigned int base = atomicAdd(reinterpret_cast<unsigned int*>(&Lq.counts[5]), (unsigned int)na * c);
+    if ((unsigned long long)base + (unsigned long long)na * c > cap_entries) {
+      T.sortbase[id] = SORT_NONE;
+      atomicOr(err_all, ERR_OVERFLOW);
+      continue;
+    }
     T.sortbase[id] = base;
     atomicAdd(&Lq.counts[4], na);
     if (c <= SORT_SMALL) {
@@ -1181,11 +1245,16 @@ __global__ void k_sort_alloc(Tree T, int nnodes, Lists Lq, int* __restrict__ big
           atomicAdd(big_count, ((unsigned long long)na << 40) | (unsigned long long)((unsigned int)na * c));
       const int s0 = (int)(t >> 40);
       const unsigned int e0 = (unsigned int)(t & ((1ull << 40) - 1ull));
+      const bool fits = (unsigned long long)e0 + (unsigned long long)na * c <= cap_bigent;
+      if (!fits) {
+        T.sortbase[id] = SORT_NONE;    // unsorted, as above; its segments are marked empty
+        atomicOr(err_all, ERR_OVERFLOW);
+      }
       int q = 0;
       for (int a = 0; a < 13; ++a) {
         if (!(ax & (1u << a))) continue;
         if (s0 + q < cap_big) {
-          big_node[s0 + q] = id;
+          big_node[s0 + q] = fits ? id : -1;
           big_axis[s0 + q] = a;
           big_off[s0 + q] = e0 + (unsigned int)q * c;
         }
@@ -1456,12 +1525,17 @@ __global__ void __launch_bounds__(256) k_sort_merge(const uint4* __restrict__ mi
 
 // Cells with many clusters: composite keys (segment << 32 | orderable projection)
 // for one global radix sort, then scatter back into each cell's storage.
+// nseg < 0: the segment count comes from the device (a captured step, capped at
+// cap_big); segments marked empty (node -1) are skipped.
 __global__ void k_sort_big_keys(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
                                 const unsigned int* __restrict__ big_off, Tree T, Tiles TL,
-                                unsigned long long* __restrict__ ckey, unsigned int* __restrict__ cval) {
+                                unsigned long long* __restrict__ ckey, unsigned int* __restrict__ cval,
+                                const unsigned long long* __restrict__ big_count, int cap_big) {
   pdl_wait();
+  if (nseg < 0) nseg = min((int)(*big_count >> 40), cap_big);
   for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
     const int id = big_node[sgi];
+    if (id < 0) continue;
     const int a = big_axis[sgi];
     const unsigned int c = T.ntile[id], t0 = T.tile0[id], o = big_off[sgi];
     const float4 cc = T.cen[id];
@@ -1476,10 +1550,13 @@ __global__ void k_sort_big_keys(int nseg, const int* __restrict__ big_node, cons
 __global__ void k_sort_big_scatter(int nseg, const int* __restrict__ big_node, const int* __restrict__ big_axis,
                                    const unsigned int* __restrict__ big_off, Tree T, Tiles TL,
                                    const unsigned int* __restrict__ cval, float* __restrict__ sort_r,
-                                   unsigned int* __restrict__ sort_i) {
+                                   unsigned int* __restrict__ sort_i, const unsigned long long* __restrict__ big_count,
+                                   int cap_big) {
   pdl_wait();
+  if (nseg < 0) nseg = min((int)(*big_count >> 40), cap_big);
   for (int sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
     const int id = big_node[sgi];
+    if (id < 0) continue;
     const int a = big_axis[sgi];
     const unsigned int ax = T.axes[id];
     const unsigned int c = T.ntile[id], t0 = T.tile0[id], o = big_off[sgi];

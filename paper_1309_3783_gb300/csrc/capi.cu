@@ -41,13 +41,13 @@ __global__ void k_shift(long long, int, const unsigned long long*, const unsigne
                         const BoxDesc*, const double*, const float*, const float*, float4*, float4*);
 __global__ void k_mark_axes(Lists, int, Tree);
 __global__ void k_sort_alloc(Tree, int, Lists, int*, int*, unsigned int*, unsigned long long*, int, uint4*,
-                             unsigned int*);
+                             unsigned int*, unsigned int, unsigned int, unsigned int*);
 __global__ void k_sort_small(const uint4*, const unsigned int*, Tree, Tiles, float*, unsigned int*);
 __global__ void k_sort_merge(const uint4*, const unsigned int*, Tree, Tiles, float*, unsigned int*);
 __global__ void k_sort_big_keys(int, const int*, const int*, const unsigned int*, Tree, Tiles, unsigned long long*,
-                                unsigned int*);
+                                unsigned int*, const unsigned long long*, int);
 __global__ void k_sort_big_scatter(int, const int*, const int*, const unsigned int*, Tree, Tiles,
-                                   const unsigned int*, float*, unsigned int*);
+                                   const unsigned int*, float*, unsigned int*, const unsigned long long*, int);
 __global__ void k_leaf_partition(Tree, int, const BoxDesc*, const float*, unsigned int*);
 __global__ void k_apply_partition(long long, const unsigned int*, const unsigned int*, unsigned int*,
                                   const unsigned long long*, unsigned long long*, const float*, float*,
@@ -57,6 +57,10 @@ __global__ void k_tile_flags(Tree, int, int, const BoxDesc*, const float*, const
 __global__ void k_tile_table(long long, Tree, const unsigned int*, const unsigned int*, const unsigned int*,
                              const float4*, unsigned int*, Tiles, int);
 __global__ void k_cell_tiles(Tree, int, const unsigned int*);
+__global__ void k_box_reset(int, BoxDesc*);
+__global__ void k_check_shape(int, const BoxDesc*, int, float, unsigned int*);
+__global__ void k_check_build(cudaGraphConditionalHandle, const unsigned int*, const int*, int, const int*, int, int, int,
+                              unsigned int, unsigned int, const unsigned long long*, int, unsigned int*);
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
 void launch_density(Engine& E, const int* it_dev = nullptr, int only = -1);
@@ -103,6 +107,15 @@ const char* const kPhaseNames[PH_COUNT] = {"ingest",     "keys_sort",   "tree", 
 int Engine::prof_begin(int phase, long long* l0, cudaStream_t on) {
   *l0 = launch_count();
   if (!prof) return -1;
+  if (prof_into_graph) {
+    // recorded as nodes of the captured rebuild step, from events of its own
+    // (created before the capture); read after every launch of the graph
+    const int ev = (int)(2 * gprof_recs.size());
+    if ((size_t)ev + 2 > gev_pool.size()) return -1;
+    cudaEventRecord(gev_pool[ev], on ? on : st);
+    (void)phase;
+    return ev;
+  }
   while (ev_pool.size() < ev_used + 2) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return -1;
@@ -117,6 +130,11 @@ int Engine::prof_begin(int phase, long long* l0, cudaStream_t on) {
 
 void Engine::prof_end(int phase, int ev, long long l0, cudaStream_t on) {
   if (!prof || ev < 0) return;
+  if (prof_into_graph) {
+    cudaEventRecord(gev_pool[ev + 1], on ? on : st);
+    gprof_recs.push_back(GProfRec{phase, ev, launch_count() - l0});
+    return;
+  }
   cudaEventRecord(ev_pool[ev + 1], on ? on : st);
   prof_recs.push_back(ProfRec{phase, ev, launch_count() - l0});
 }
@@ -124,6 +142,9 @@ void Engine::prof_end(int phase, int ev, long long l0, cudaStream_t on) {
 void Engine::prof_reset() {
   prof_recs.clear();
   ev_used = 0;
+  gprof_ms.assign(PH_COUNT, 0.0);
+  gprof_calls.assign(PH_COUNT, 0);
+  gprof_launches.assign(PH_COUNT, 0);
 }
 
 sph_status Engine::prof_read(std::vector<double>& ms, std::vector<long long>& calls, std::vector<long long>& launches) {
@@ -137,6 +158,11 @@ sph_status Engine::prof_read(std::vector<double>& ms, std::vector<long long>& ca
     ms[r.phase] += t;
     calls[r.phase] += 1;
     launches[r.phase] += r.launches;
+  }
+  for (int k = 0; k < PH_COUNT && k < (int)gprof_ms.size(); ++k) {
+    ms[k] += gprof_ms[k];
+    calls[k] += gprof_calls[k];
+    launches[k] += gprof_launches[k];
   }
   return SPH_OK;
 }
@@ -154,6 +180,8 @@ Engine::Engine(const sph_params& p, int dev, cudaStream_t s) : prm(p), device(de
 
 Engine::~Engine() {
   drop_step_graph();
+  drop_build_graph();
+  for (cudaEvent_t e : gev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
@@ -166,6 +194,12 @@ sph_status Engine::ensure_side_stream() {
   CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
   CK(cudaStreamCreateWithFlags(&st_side, cudaStreamNonBlocking));
   return SPH_OK;
+}
+
+// Every synchronisation of the engine with its stream, counted.
+cudaError_t Engine::sync_stream() {
+  ++host_syncs;
+  return cudaStreamSynchronize(st);
 }
 
 int Engine::grid(long long work, int threads) const {
@@ -193,6 +227,7 @@ size_t Engine::footprint_bytes() const {
 
 sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
   spec = boxes;
+  steps_in_layout = 0;
   depth_hint = 0;           // new boxes: the first build takes the full depth
   nbox = (int)boxes.size();
   off.assign(nbox + 1, 0);
@@ -221,7 +256,7 @@ sph_status Engine::set_boxes(const std::vector<BoxSpec>& boxes) {
   CK(boff.reserve(nbox + 1));
   CK(cudaMemcpyAsync(boff.p, off.data(), (nbox + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
   launch_pdl(k_box_ids, grid(N), 256, st, N, nbox, boff.p, bid.p); count_launch();
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   return SPH_OK;
 }
 
@@ -271,7 +306,7 @@ sph_status Engine::relayout(const std::vector<BoxSpec>& boxes, const std::vector
     CK(hlev_src.reserve(boxes.size()));
     CK(cudaMemcpyAsync(hlev_src.p, srcl.data(), srcl.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     launch_pdl(k_remap_hlev, 1, 256, st, (int)boxes.size(), hlev_src.p, hlev_old.p, hlev.p); count_launch();
-    CK(cudaStreamSynchronize(st));  // srcl is a host temporary
+    CK(sync_stream());  // srcl is a host temporary
   }
   x.swap(rl_x);
   v.swap(rl_v);
@@ -503,7 +538,7 @@ sph_status Engine::build_once(bool* retry) {
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(hbox.data(), box.p, nbox * sizeof(BoxDesc), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   const int box_bits = ceil_log2(nbox);
   int dc = std::min(std::min(prm.max_depth, SPH_MAX_DEPTH), (64 - box_bits) / 3);
   int need = 0;
@@ -571,7 +606,7 @@ sph_status Engine::build_once(bool* retry) {
   unsigned int ea[4];
   CK(cudaMemcpyAsync(tn, t_n.p, sizeof(tn), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   if (ea[0] & ERR_DEPTH) depth_hint = 0;     // the bound blocked a split: full depth
   if ((ea[0] & ERR_OVERFLOW) || tn[0] > cap_nodes) {
     sph_status s = ensure_tree_capacity(std::max(2 * cap_nodes, tn[0] + 1024));
@@ -654,7 +689,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemsetAsync(mid_count.p, 0, sizeof(unsigned int), st));
   launch_pdl(k_mark_axes, nsm * 8, 256, st, Lq, cap_pair, T); count_launch();
   launch_pdl(k_sort_alloc, grid(n_nodes), 256, st, T, n_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
-                                              cap_big, mid_seg.p, mid_count.p); count_launch();
+             cap_big, mid_seg.p, mid_count.p, 0xffffffffu, 0xffffffffu, err_all.p); count_launch();
   launch_task_offsets(*this);
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
@@ -665,7 +700,7 @@ sph_status Engine::build_once(bool* retry) {
   unsigned int ntl = 0;
   CK(cudaMemcpyAsync(&ntl, dev_counters.p + 4, sizeof(ntl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   const int last_q = lc[2 + (rounds & 1)];
   if ((ea[0] & ERR_OVERFLOW) || lc[0] > cap_self || lc[1] > cap_pair || last_q != 0) {
     sph_status s = ensure_list_capacity(std::max(cap_self, lc[0]) * 2, std::max(cap_pair, lc[1]) * 2,
@@ -717,11 +752,11 @@ sph_status Engine::build_once(bool* retry) {
     CK(cval_tmp.reserve(nb));
     if (rs_scratch.n < (size_t)radix_scratch_words(nb)) CK(rs_scratch.reserve(radix_scratch_words(nb)));
     launch_pdl(k_sort_big_keys, std::min(n_big, nsm * 8), 256, st, n_big, big_node.p, big_axis.p, big_off.p, T, TL,
-                                                              ckey.p, cval.p); count_launch();
+               ckey.p, cval.p, big_count.p, cap_big); count_launch();
     radix_sort(ckey.p, cval.p, ckey_tmp.p, cval_tmp.p, (long long)nb, 32 + std::max(1, ceil_log2(n_big)),
                rs_scratch.p, st);
     launch_pdl(k_sort_big_scatter, std::min(n_big, nsm * 8), 256, st, n_big, big_node.p, big_axis.p, big_off.p, T, TL,
-                                                                 cval.p, sort_r.p, sort_i.p); count_launch();
+               cval.p, sort_r.p, sort_i.p, big_count.p, cap_big); count_launch();
   }
   prof_end(PH_AXIS_SORT, ev, l0);
   CK(cudaGetLastError());
@@ -731,6 +766,8 @@ sph_status Engine::build_once(bool* retry) {
   reusable = true;
   ++n_builds;
   graph_ready = false;      // a captured step holds this build's sizes and buffers
+  bgraph_ready = false;     // ... and so does the captured rebuild step (the buffers swapped)
+  gb_last_q = 2 + (rounds & 1);
   return SPH_OK;
 }
 
@@ -765,7 +802,7 @@ sph_status Engine::density() {
   if (s != SPH_OK) return s;
   s = density_pass();
   if (s != SPH_OK) return s;
-  CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+  CK(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
   {
     Scope sc(this, PH_GHOST);
     launch_ghost(*this, 0, 1);
@@ -794,7 +831,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
   constexpr int H_BATCH = 2;
   int it = 1, rebuilds = 0;
   CK(it_dev.reserve(4));
-  CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+  CK(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
   CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
   int itv[3] = {1, 0, 0};
   CK(cudaMemcpyAsync(it_dev.p, itv, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -823,7 +860,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(itv, it_dev.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(sync_stream());
     if (rebuilds == 0 && it == 1) first_active = itv[1];
     it = itv[0];
     if (itv[2] == 1) break;            // every particle finalised (at the limit, unconverged ones too)
@@ -839,7 +876,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
       itv[2] = 0;
       CK(cudaMemcpyAsync(it_dev.p, itv, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
       CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
-      CK(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+      CK(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
       fresh = true;
       continue;
     }
@@ -855,7 +892,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     CK(cudaMemsetAsync(dev_counters.p + 1, 0, sizeof(int), st));
     launch_count_unconverged(*this, dev_counters.p + 1);
     CK(cudaMemcpyAsync(&cnt, dev_counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(sync_stream());
     nu = cnt;
   }
   last_iters = it;
@@ -957,12 +994,21 @@ sph_status Engine::step_boxes_once() {
     s = force();
     if (s != SPH_OK) return s;
   }
-  if (moving && prm.reuse && reusable && !prof && !count_pairs && !graph_off) {
+  if (moving && prm.reuse && reusable && !prof && !count_pairs && !graph_off && prm.graphs) {
     // the whole step, kick and drift included, as one captured graph
     s = upload_boxes();
     if (s != SPH_OK) return s;
     vpred = 1;
     return step_graph();
+  }
+  if (moving) ++steps_in_layout;
+  if (moving && !prm.reuse && built && !count_pairs && !graph_off && prm.graphs && steps_in_layout > 2) {
+    // a step that rebuilds, as one captured graph (captured again after every
+    // host-driven build: the graph holds that build's shape and capacities)
+    s = upload_boxes();
+    if (s != SPH_OK) return s;
+    vpred = 1;
+    return build_step_graph();
   }
   if (moving) {
     s = upload_boxes();
@@ -975,7 +1021,14 @@ sph_status Engine::step_boxes_once() {
     CK(cudaGetLastError());
     vpred = 1;
   }
-  s = reuse_or_build();
+  return step_host(moving);
+}
+
+// The rest of a step after its kick and drift: build (or keep) the decomposition,
+// the h iteration, the force pass and the closing kick, host-sequenced.
+sph_status Engine::step_host(bool moving) {
+  ++steps_host;
+  sph_status s = reuse_or_build();
   if (s != SPH_OK) return s;
   sph_status hs = h_update(nullptr, nullptr);
   if (hs != SPH_OK && hs != SPH_E_NOT_CONVERGED) return hs;
@@ -1012,7 +1065,7 @@ sph_status Engine::reuse_or_build() {
   unsigned int flag = 0;
   CK(cudaMemcpyAsync(dm.data(), dmax_bits.p, nbox * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&flag, reuse_flag.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   if (flag) {
     prof_end(PH_REUSE, ev, l0);
     return build();
@@ -1123,7 +1176,7 @@ sph_status Engine::capture_step_graph() {
   launch_pdl(k_tile_boxes, grid(32 * n_tiles), 256, st, n_tiles, TL, pos4.p); count_launch();
   launch_bracket_reset(*this);
   launch_set_active(*this);
-  CKG(cudaMemsetAsync(dev_counters.p, 0, 8 * sizeof(int), st));
+  CKG(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
   CKG(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
   launch_iter_start(*this, iter);
   CKG(cudaStreamEndCapture(st, &body));
@@ -1182,7 +1235,7 @@ sph_status Engine::step_graph() {
   CK(cudaMemcpyAsync(&flag, reuse_flag.p, sizeof(flag), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(itv, it_dev.p, sizeof(itv), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   const bool rebuild = flag != 0 || (ea & ERR_REBUILD) != 0u;
   count_launches(g_pre + (flag ? 0 : g_keep + (long long)itv[0] * g_iter + (rebuild ? 0 : g_force)));
   if (rebuild) {
@@ -1209,12 +1262,410 @@ sph_status Engine::step_graph() {
     CK(cudaMemsetAsync(dev_counters.p + 1, 0, sizeof(int), st));
     launch_count_unconverged(*this, dev_counters.p + 1);
     CK(cudaMemcpyAsync(&cnt, dev_counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(sync_stream());
     nu = cnt;
   }
   last_unconverged = nu;
   if (nu > 0) return fail(SPH_E_NOT_CONVERGED, std::to_string(nu) + " particles did not converge");
   return SPH_OK;
+}
+
+// ------------------------------------------------------------ captured rebuild step
+// A step that rebuilds the decomposition (the default protocol), as one CUDA
+// graph with conditional nodes:
+//   the kick and the drift, then the whole build, every launch sized by the
+//   capacities of the last host-driven build and reading this build's counts on
+//   the device; k_check_shape flags a box whose support radii no longer give the
+//   top level that build chose, the tree rounds flag a split that the depth
+//   bound blocks, and k_check_build checks every count against its capacity;
+//   IF the build held: the h iteration set up;
+//   WHILE particles still iterate (no rebuild needed, limit not reached): one
+//   density pass and its h update, the iteration counter kept on the device;
+//   IF the iteration ended without a rebuild: force pass, reductions, the saved
+//   accelerations and the closing kick.
+// One synchronisation at the end reads what happened.  When the build did not
+// hold or an iteration needed a rebuild, the host completes the step (kick and
+// drift are done) with a host-driven build; that build drops the graph, and the
+// next step captures it again with the new build's shape and capacities.  The
+// capture reserves every buffer first (nothing can be allocated while capturing)
+// and swaps the double buffers of the particle side exactly as a build does, so
+// that every launch of the graph leaves the data where the host expects it.
+void Engine::drop_build_graph() {
+  if (bstep_x) cudaGraphExecDestroy(bstep_x);
+  if (bstep_g) cudaGraphDestroy(bstep_g);
+  bstep_x = nullptr;
+  bstep_g = nullptr;
+  bgraph_ready = false;
+  gprof_recs.clear();
+}
+
+#define CKB(call)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      cudaStreamCaptureStatus cs_;                                                 \
+      if (cudaStreamIsCapturing(st, &cs_) == cudaSuccess && cs_ != cudaStreamCaptureStatusNone) { \
+        cudaGraph_t g_;                                                            \
+        cudaStreamEndCapture(st, &g_);                                             \
+        if (g_) cudaGraphDestroy(g_);                                              \
+      }                                                                            \
+      cudaGetLastError();                                                          \
+      gcap = false;                                                                \
+      prof_into_graph = false;                                                     \
+      drop_build_graph();                                                          \
+      graph_off = true;                                                            \
+      return fail(SPH_E_CUDA, std::string("rebuild step capture: ") + cudaGetErrorString(e_)); \
+    }                                                                              \
+  } while (0)
+
+// The build of a captured rebuild step (enqueued while capturing; gcap set).
+sph_status Engine::enqueue_captured_build() {
+  CKB(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  launch_pdl(k_box_reset, 1, 256, st, nbox, box.p); count_launch();
+  {
+    Scope sc(this, PH_INGEST);
+    launch_pdl(k_ingest, grid(N), 256, st, N, bid.p, box.p, x.p, v.p, m.p, u.p, h.p, prm.gamma_kernel, H_in.p);
+    count_launch();
+  }
+  const int box_bits = ceil_log2(nbox);
+  const int dc = std::min(std::min(prm.max_depth, SPH_MAX_DEPTH), (64 - box_bits) / 3);
+  launch_pdl(k_check_shape, 1, 256, st, nbox, box.p, dc, prm.split_headroom, err_all.p); count_launch();
+  long long l0;
+  int ev = prof_begin(PH_SORT, &l0);
+  launch_pdl(k_keys, grid(N), 256, st, N, dcap, bid.p, box.p, x.p, key.p, perm.p); count_launch();
+  radix_sort(key.p, perm.p, key_tmp.p, perm_tmp.p, N, key_bits, rs_scratch.p, st);
+  launch_pdl(k_gather_sorted, grid(N), 256, st, N, perm.p, H_in.p, v.p, u.p, bid.p, box.p, a_in.p, vpred, Hs.p,
+             vel4.p); count_launch();
+  prof_end(PH_SORT, ev, l0);
+  // the tree: a split that the depth bound blocks is flagged (capped)
+  ev = prof_begin(PH_TREE, &l0);
+  CKB(cudaMemsetAsync(t_n.p, 0, 8 * sizeof(int), st));
+  CKB(cudaMemsetAsync(top_at.p, 0xff, N * sizeof(int), st));
+  launch_pdl(k_top_nodes, grid(N), 256, st, N, dcap, box_shift, box.p, key.p, T, cap_nodes, top_at.p, err_all.p);
+  count_launch();
+  launch_pdl(k_frontier_init, 1, 1, st, T, cap_nodes); count_launch();
+  const int rounds = dcap - kmin + 1;
+  for (int r = 0; r < rounds; ++r) {
+    launch_pdl(k_tree_round, nsm * 8, 256, st, T, box.p, Hs.p, key.p, dcap, prm.leaf_max, prm.split_frac,
+               r + 1 < rounds ? 1 : 0, 1, cap_nodes, err_all.p); count_launch();
+  }
+  prof_end(PH_TREE, ev, l0);
+  // the lists on st, the particle side on the side stream (as a build does)
+  CKB(cudaEventRecord(ev_fork, st));
+  CKB(cudaStreamWaitEvent(st_side, ev_fork, 0));
+  ev = prof_begin(PH_LISTS, &l0);
+  CKB(cudaMemsetAsync(l_counts.p, 0, 8 * sizeof(int), st));
+  launch_pdl(k_items_top, grid(13ll * std::min<long long>(N, cap_nodes)), 256, st, cap_nodes, T, box.p, key.p,
+             top_at.p, dcap, box_shift, Lq, cap_queue, err_all.p); count_launch();
+  for (int r = 0; r < rounds; ++r) {
+    const int in = r & 1;
+    CKB(cudaMemsetAsync(l_counts.p + 2 + (in ^ 1), 0, sizeof(int), st));
+    launch_pdl(k_items_expand, nsm * 8, 256, st, in, T, box.p, Lq, cap_queue, cap_self, cap_pair, err_all.p,
+               prm.split_headroom); count_launch();
+  }
+  prof_end(PH_LISTS, ev, l0);
+  cudaStream_t ss = st_side;
+  ev = prof_begin(PH_SHIFT, &l0, ss);
+  launch_pdl(k_leaves, nsm * 8, 256, ss, T, cap_nodes, leaf_of.p); count_launch();
+  launch_pdl(k_leaf_partition, nsm * 8, 256, ss, T, cap_nodes, box.p, Hs.p, lsrc.p); count_launch();
+  launch_pdl(k_apply_partition, grid(N), 256, ss, N, lsrc.p, perm.p, perm_tmp.p, key.p, key_tmp.p, Hs.p, Hs_tmp.p,
+             vel4.p, vel4_tmp.p); count_launch();
+  perm.swap(perm_tmp);
+  key.swap(key_tmp);
+  Hs.swap(Hs_tmp);
+  vel4.swap(vel4_tmp);
+  launch_pdl(k_shift, grid(N), 256, ss, N, box_shift, key.p, perm.p, leaf_of.p, T, box.p, x.p, m.p, Hs.p, pos4.p,
+             cen4.p); count_launch();
+  launch_pdl(k_tile_flags, nsm * 8, 256, ss, T, cap_nodes, box_shift, box.p, Hs.p, key.p, tflag.p, prm.cluster_max);
+  count_launch();
+  exclusive_scan(tflag.p, texcl.p, N, rs_scratch.p, reinterpret_cast<unsigned int*>(dev_counters.p + 4), ss);
+  launch_pdl(k_tile_table, grid(N), 256, ss, N, T, leaf_of.p, tflag.p, texcl.p, pos4.p, tile_of.p, TL,
+             prm.cluster_max); count_launch();
+  launch_pdl(k_cell_tiles, grid(cap_nodes), 256, ss, T, cap_nodes, tile_of.p); count_launch();
+  prof_end(PH_SHIFT, ev, l0, ss);
+  CKB(cudaEventRecord(ev_join, ss));
+  CKB(cudaStreamWaitEvent(st, ev_join, 0));
+  launch_pdl(k_particle_limits, grid(N), 256, st, N, T, leaf_of.p, hlimp.p); count_launch();
+  // the sorted projections
+  ev = prof_begin(PH_AXIS_SORT, &l0);
+  CKB(cudaMemsetAsync(big_count.p, 0, sizeof(unsigned long long), st));
+  CKB(cudaMemsetAsync(mid_count.p, 0, sizeof(unsigned int), st));
+  launch_pdl(k_mark_axes, nsm * 8, 256, st, Lq, cap_pair, T); count_launch();
+  launch_pdl(k_sort_alloc, grid(cap_nodes), 256, st, T, cap_nodes, Lq, big_node.p, big_axis.p, big_off.p, big_count.p,
+             cap_big, mid_seg.p, mid_count.p, (unsigned int)sort_r.n, (unsigned int)ckey.n, err_all.p);
+  count_launch();
+  launch_task_offsets(*this);
+  launch_task_items(*this);
+  if (prm.sort_merge)
+    launch_pdl(k_sort_merge, nsm * 8, 256, st, mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
+  else
+    launch_pdl(k_sort_small, nsm * 8, 256, st, mid_seg.p, mid_count.p, T, TL, sort_r.p, sort_i.p);
+  count_launch();
+  // cells of many clusters: one global sort over the key storage, its unused
+  // entries holding the largest key so that they sort last
+  CKB(cudaMemsetAsync(ckey.p, 0xff, ckey.n * sizeof(unsigned long long), st));
+  launch_pdl(k_sort_big_keys, nsm * 8, 256, st, -1, big_node.p, big_axis.p, big_off.p, T, TL, ckey.p, cval.p,
+             big_count.p, cap_big); count_launch();
+  radix_sort(ckey.p, cval.p, ckey_tmp.p, cval_tmp.p, (long long)ckey.n, 32 + ceil_log2((long long)cap_big + 1),
+             rs_scratch.p, st);
+  launch_pdl(k_sort_big_scatter, nsm * 8, 256, st, -1, big_node.p, big_axis.p, big_off.p, T, TL, cval.p, sort_r.p,
+             sort_i.p, big_count.p, cap_big); count_launch();
+  prof_end(PH_AXIS_SORT, ev, l0);
+  CKB(cudaMemcpyAsync(x_build.p, x.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return SPH_OK;
+}
+
+sph_status Engine::capture_build_graph() {
+  drop_build_graph();
+  // capacities with room to grow: a count past one makes the build not hold, and
+  // the host completes that step with a build of its own
+  const size_t cp = (size_t)(n_ptasks + n_ptasks / 4 + 1024), cs = (size_t)(n_stasks + n_stasks / 4 + 1024);
+  CK(l_ptask.reserve(cp));
+  CK(l_stask.reserve(cs));
+  CK(l_plive.reserve(cp + cs));
+  CK(l_nlive.reserve(1));
+  Lq.p_task = l_ptask.p;
+  Lq.s_task = l_stask.p;
+  Lq.p_live = l_plive.p;
+  Lq.n_live = l_nlive.p;
+  CK(sort_r.reserve((size_t)(n_entries + n_entries / 4 + 4096)));
+  CK(sort_i.reserve(sort_r.n));
+  const size_t nb = (size_t)(n_big_entries + n_big_entries / 4 + 4096);
+  CK(ckey.reserve(nb));
+  CK(ckey_tmp.reserve(ckey.n));
+  CK(cval.reserve(ckey.n));
+  CK(cval_tmp.reserve(ckey.n));
+  if (rs_scratch.n < (size_t)radix_scratch_words((long long)std::max<size_t>((size_t)N, ckey.n)))
+    CK(rs_scratch.reserve((size_t)radix_scratch_words((long long)std::max<size_t>((size_t)N, ckey.n))));
+  CK(mid_seg.reserve(13 * (size_t)cap_nodes));
+  CK(mid_count.reserve(1));
+  CK(big_count.reserve(1));
+  CK(gstat.reserve(4));
+  CK(it_dev.reserve(4));
+  {
+    sph_status s = ensure_side_stream();
+    if (s != SPH_OK) return s;
+  }
+  if (prof) {
+    while (gev_pool.size() < 64) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      gev_pool.push_back(e);
+    }
+  }
+  const long long c0 = launch_count();
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  CKB(cudaGraphCreate(&bstep_g, 0));
+  cudaGraphConditionalHandle ok, iter, frc;
+  CKB(cudaGraphConditionalHandleCreate(&ok, bstep_g, 0, cudaGraphCondAssignDefault));
+  CKB(cudaGraphConditionalHandleCreate(&iter, bstep_g, 0, cudaGraphCondAssignDefault));
+  CKB(cudaGraphConditionalHandleCreate(&frc, bstep_g, 0, cudaGraphCondAssignDefault));
+  // kick, drift, build and its check
+  cudaGraph_t g1 = nullptr;
+  gcap = true;
+  prof_into_graph = prof;
+  CKB(cudaStreamBeginCapture(st, mode));
+  {
+    Scope sc(this, PH_STEP);
+    launch_kick(*this);
+    launch_drift(*this);
+  }
+  {
+    sph_status s = enqueue_captured_build();
+    if (s != SPH_OK) return s;
+  }
+  launch_pdl(k_check_build, 1, 1, st, ok, err_all.p, t_n.p, cap_nodes, l_counts.p, cap_self, cap_pair, gb_last_q,
+             (unsigned int)l_ptask.n, (unsigned int)l_stask.n, big_count.p, cap_big, gstat.p); count_launch();
+  CKB(cudaStreamEndCapture(st, &g1));
+  gb_build = launch_count() - c0;
+  cudaGraphNode_t n1, n2, n3, n4;
+  CKB(cudaGraphAddChildGraphNode(&n1, bstep_g, nullptr, 0, g1));
+  cudaGraphDestroy(g1);
+  // IF the build held: the h iteration set up
+  cudaGraphNodeParams cp_ = {};
+  cp_.type = cudaGraphNodeTypeConditional;
+  cp_.conditional.handle = ok;
+  cp_.conditional.type = cudaGraphCondTypeIf;
+  cp_.conditional.size = 1;
+  CKB(cudaGraphAddNode(&n2, bstep_g, &n1, nullptr, 1, &cp_));
+  cudaGraph_t body = cp_.conditional.phGraph_out[0];
+  long long c1 = launch_count();
+  CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  launch_bracket_reset(*this);
+  launch_set_active(*this);
+  CKB(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
+  CKB(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  launch_iter_start(*this, iter);
+  CKB(cudaStreamEndCapture(st, &body));
+  gb_setup = launch_count() - c1;
+  // WHILE iterating: one density pass and its h update (timed as a whole below)
+  cudaGraphNode_t prev = n2;
+  int ev_iter = -1;
+  if (prof) {
+    ev_iter = (int)(2 * gprof_recs.size());
+    cudaGraphNode_t e0;
+    CKB(cudaGraphAddEventRecordNode(&e0, bstep_g, &prev, 1, gev_pool[ev_iter]));
+    prev = e0;
+  }
+  cp_ = {};
+  cp_.type = cudaGraphNodeTypeConditional;
+  cp_.conditional.handle = iter;
+  cp_.conditional.type = cudaGraphCondTypeWhile;
+  cp_.conditional.size = 1;
+  CKB(cudaGraphAddNode(&n3, bstep_g, &prev, nullptr, 1, &cp_));
+  body = cp_.conditional.phGraph_out[0];
+  c1 = launch_count();
+  const bool keep_prof = prof;
+  prof = false;                      // no per-pass events inside the loop
+  prof_into_graph = false;
+  CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  launch_zero_density(*this, false);
+  launch_live_tasks(*this, true, it_dev.p);
+  launch_density(*this, it_dev.p);
+  launch_ghost(*this, 1, 0, it_dev.p);
+  launch_iter_next(*this, iter, frc);
+  launch_mark_active_cells(*this);
+  CKB(cudaStreamEndCapture(st, &body));
+  prof = keep_prof;
+  prof_into_graph = prof;
+  gb_iter = launch_count() - c1;
+  prev = n3;
+  if (prof) {
+    cudaGraphNode_t e1;
+    CKB(cudaGraphAddEventRecordNode(&e1, bstep_g, &prev, 1, gev_pool[ev_iter + 1]));
+    prev = e1;
+    gprof_recs.push_back(GProfRec{PH_DENSITY, ev_iter, gb_iter});
+  }
+  // IF finished without a rebuild: force pass and the closing kick
+  cp_ = {};
+  cp_.type = cudaGraphNodeTypeConditional;
+  cp_.conditional.handle = frc;
+  cp_.conditional.type = cudaGraphCondTypeIf;
+  cp_.conditional.size = 1;
+  CKB(cudaGraphAddNode(&n4, bstep_g, &prev, nullptr, 1, &cp_));
+  body = cp_.conditional.phGraph_out[0];
+  c1 = launch_count();
+  CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
+  CKB(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
+  CKB(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
+  {
+    Scope sc(this, PH_FORCE_TASKS);
+    launch_live_tasks(*this, false);
+  }
+  {
+    Scope sc(this, PH_FORCE);
+    launch_force(*this);
+  }
+  {
+    Scope sc(this, PH_REDUCE);
+    launch_reduce(*this);
+    launch_save_acc(*this);
+  }
+  {
+    Scope sc(this, PH_STEP);
+    launch_kick(*this);
+  }
+  CKB(cudaStreamEndCapture(st, &body));
+  gb_force = launch_count() - c1;
+  gcap = false;
+  prof_into_graph = false;
+  CKB(cudaGraphInstantiate(&bstep_x, bstep_g, 0));
+  count_launches(-(launch_count() - c0));     // capturing launches nothing
+  bgraph_ready = true;
+  bgraph_prof = prof;
+  return SPH_OK;
+}
+
+sph_status Engine::build_step_graph() {
+  if (!bgraph_ready || bgraph_prof != prof) {
+    sph_status s = capture_build_graph();
+    if (s != SPH_OK) return s;
+  }
+  CK(cudaGraphLaunch(bstep_x, st));
+  unsigned int gs = 0, ea = 0;
+  int itv[2] = {0, 0}, tn[8], lc[8];
+  unsigned int ntl = 0;
+  unsigned long long bcw = 0;
+  CK(cudaMemcpyAsync(&gs, gstat.p, sizeof(gs), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(itv, it_dev.p, sizeof(itv), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(tn, t_n.p, sizeof(tn), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(lc, l_counts.p, sizeof(lc), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ntl, dev_counters.p + 4, sizeof(ntl), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&bcw, big_count.p, sizeof(bcw), cudaMemcpyDeviceToHost, st));
+  CK(sync_stream());
+  const bool held = gs == 1u;
+  const bool rebuild = !held || (ea & ERR_REBUILD) != 0u;
+  count_launches(gb_build + (held ? gb_setup + (long long)itv[0] * gb_iter + (rebuild ? 0 : gb_force) : 0));
+  if (held) {
+    // this build's sizes, as a host build leaves them
+    n_nodes = tn[0];
+    n_top = tn[3];
+    depth_used = tn[5];
+    depth_hint = tn[5];
+    depth_hint_leaf = prm.leaf_max;
+    n_selfs = lc[0];
+    n_pairs = lc[1];
+    n_segments = lc[4];
+    n_entries = (unsigned int)lc[5];
+    n_ptasks = lc[6];
+    n_stasks = lc[7];
+    n_tiles = ntl;
+    n_big = (int)(bcw >> 40);
+    n_big_entries = (long long)(bcw & ((1ull << 40) - 1ull));
+    built = true;
+    reusable = true;
+    ++n_builds;
+    graph_ready = false;
+  }
+  if (rebuild) {
+    // kick and drift are done: complete the step with a host-driven build
+    sph_status s = build();
+    if (s != SPH_OK) return s;
+    return step_rest_after_build();
+  }
+  ++steps_graph;
+  if (bgraph_prof) {
+    for (const GProfRec& r : gprof_recs) {
+      float t = 0.0f;
+      CK(cudaEventElapsedTime(&t, gev_pool[r.ev], gev_pool[r.ev + 1]));
+      gprof_ms[r.phase] += t;
+      gprof_calls[r.phase] += 1;
+      gprof_launches[r.phase] += r.launches;
+    }
+  }
+  have_density = have_ghost = have_force = have_acc = true;
+  last_iters = itv[0];
+  last_rebuilds = 0;
+  first_active = itv[1];
+  long long nu = 0;
+  if (itv[0] >= prm.h_max_iter) {
+    int cnt = 0;
+    CK(cudaMemsetAsync(dev_counters.p + 1, 0, sizeof(int), st));
+    launch_count_unconverged(*this, dev_counters.p + 1);
+    CK(cudaMemcpyAsync(&cnt, dev_counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(sync_stream());
+    nu = cnt;
+  }
+  last_unconverged = nu;
+  if (nu > 0) return fail(SPH_E_NOT_CONVERGED, std::to_string(nu) + " particles did not converge");
+  return SPH_OK;
+}
+
+// After a host-driven build inside a step whose kick and drift are done: the h
+// iteration, the force pass and the closing kick.
+sph_status Engine::step_rest_after_build() {
+  ++steps_host;
+  sph_status hs = h_update(nullptr, nullptr);
+  if (hs != SPH_OK && hs != SPH_E_NOT_CONVERGED) return hs;
+  sph_status s = force();
+  if (s != SPH_OK) return s;
+  {
+    Scope sc(this, PH_STEP);
+    launch_kick(*this);
+  }
+  CK(cudaGetLastError());
+  return hs;
 }
 
 // Leaf-size autotuning: time build + density + force for each candidate
@@ -1293,7 +1744,7 @@ sph_status Engine::cfl_dt(int b, double* dt) {
   std::vector<float> H(n), vs(n);
   CK(cudaMemcpyAsync(H.data(), Hs.p + o, n * sizeof(float), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(vs.data(), fvsig.p + o, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   double hmin = INFINITY, vmax = 0.0;
   for (long long p = 0; p < n; ++p) {
     hmin = std::min(hmin, (double)H[p]);
@@ -1306,7 +1757,7 @@ sph_status Engine::cfl_dt(int b, double* dt) {
 // ----------------------------------------------------------------------- outputs
 sph_status Engine::get(int b, int field, void* dst, long long n, int mem) {
   sph_status s = get_async(b, field, dst, n, mem, staging.p);
-  if (s == SPH_OK && mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
+  if (s == SPH_OK && mem != SPH_MEM_DEVICE) CK(sync_stream());
   return s;
 }
 
@@ -1323,7 +1774,7 @@ sph_status Engine::get_fields(int b, int nf, const int* fields, void* const* dst
     if (s != SPH_OK) return s;
     at += (size_t)std::max<long long>(ns[k], 0) * 3 * sizeof(double) / 2 + 256;
   }
-  if (mem != SPH_MEM_DEVICE) CK(cudaStreamSynchronize(st));
+  if (mem != SPH_MEM_DEVICE) CK(sync_stream());
   return SPH_OK;
 }
 
@@ -1433,11 +1884,14 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->h_active_after_first = first_active;
   o->leaf_max = prm.leaf_max;
   o->cluster_max = prm.cluster_max;
+  o->graph_steps = steps_graph;
+  o->host_steps = steps_host;
+  o->host_syncs = host_syncs;
   o->n_unconverged = last_unconverged;
   if (count_pairs) {
     unsigned long long c[16];
     CK(cudaMemcpyAsync(c, pc.p, sizeof(c), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(sync_stream());
     o->density_pairs = (long long)(c[0] + c[3]);
     o->density_sides = (long long)(c[1] + c[4]);
     o->density_candidates = (long long)(c[2] + c[5]);
@@ -1463,7 +1917,7 @@ sph_status Engine::cells(int b, long long cap, int* level, int* ijk, int* count,
   CK(cudaMemcpyAsync(sp.data(), t_split.p, n_nodes * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ct.data(), t_count.p, n_nodes * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ky.data(), t_key.p, n_nodes * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   long long k = 0;
   for (int id = 0; id < n_nodes; ++id) {
     if (bx[id] != b) continue;
@@ -1495,7 +1949,7 @@ sph_status Engine::interactions(int b, long long cap, int* kind, int* a, int* bb
     CK(cudaMemcpyAsync(pb.data(), l_pb.p, n_pairs * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(pax.data(), l_pax.p, n_pairs * sizeof(int), cudaMemcpyDeviceToHost, st));
   }
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream());
   std::vector<int> local(n_nodes, -1);
   int c = 0;
   for (int id = 0; id < n_nodes; ++id)
@@ -1562,6 +2016,7 @@ void sph_params_default(sph_params* p) {
   p->cluster_max = 32;
   p->compensated = -1;
   p->precision = 0;
+  p->graphs = 1;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
@@ -1573,7 +2028,7 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
   if (!(p.gamma_kernel > 0) || !(p.n_ngb > 0) || !(p.gamma_gas > 1) || p.h_max_iter < 1 || p.leaf_max < 1 ||
       !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0) ||
       !(p.split_headroom >= 0 && p.split_headroom < 1) || p.cluster_max < 1 || p.cluster_max > 32 ||
-      (p.precision != 0 && p.precision != 1))
+      (p.precision != 0 && p.precision != 1) || (p.graphs != 0 && p.graphs != 1))
     return SPH_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;

@@ -1238,10 +1238,15 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
 // warp-aggregated appends.
 template <bool DENS>
 __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
-                             long long nst, int partial_host, const int* __restrict__ it_dev) {
+                             long long nst, int partial_host, const int* __restrict__ it_dev, int cap_p, int cap_s) {
   pdl_wait();
   const int lane = threadIdx.x & 31;
   if (it_dev && it_dev[2] != 0) return;    // the iteration has stopped: no tasks
+  if (npt < 0) {
+    // a captured step: the task counts of this build, from the device
+    npt = min(Lq.counts[6], cap_p);
+    nst = min(Lq.counts[7], cap_s);
+  }
   // later iterations keep only what still iterates (with a device counter: from iteration 2 on)
   const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
   const long long ntask = npt + nst;
@@ -1385,9 +1390,10 @@ __global__ void k_zero_active(long long N, const unsigned char* __restrict__ act
 // every cell the box of those particles in the cell's
 // frame.  One warp per cluster; the cluster's box of active particles is added
 // to every cell on its chain with ordered-key atomics.
-__global__ void k_mark_active(long long ntile, const unsigned char* __restrict__ act,
-                              const float4* __restrict__ pos4, Tree T, Tiles TL) {
+__global__ void k_mark_active(long long ntile, const unsigned int* __restrict__ ntile_dev,
+                              const unsigned char* __restrict__ act, const float4* __restrict__ pos4, Tree T, Tiles TL) {
   pdl_wait();
+  if (ntile_dev) ntile = min(ntile, (long long)*ntile_dev);   // a captured step: this build's clusters
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1439,8 +1445,15 @@ __global__ void k_task_tiles(Lists Lq, Tree T, int cap_pair, int cap_self) {
 }
 
 // task -> interaction tables (one warp per interaction)
-__global__ void k_task_items(Lists Lq, Tree T, int npair, int nself) {
+// npair < 0: the list sizes come from the device (a captured step); the tables
+// hold cap_p pair tasks and cap_s self tasks, and nothing is written past them.
+__global__ void k_task_items(Lists Lq, Tree T, int npair, int nself, int cap_pair, int cap_self, unsigned int cap_p,
+                             unsigned int cap_s) {
   pdl_wait();
+  if (npair < 0) {
+    npair = min(Lq.counts[1], cap_pair);
+    nself = min(Lq.counts[0], cap_self);
+  }
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1450,7 +1463,8 @@ __global__ void k_task_items(Lists Lq, Tree T, int npair, int nself) {
     const unsigned int t0 = pr ? Lq.p_toff[it] : Lq.s_toff[it];
     const unsigned int n = T.ntile[pr ? Lq.pair_a[it] : Lq.self_a[it]];
     unsigned int* dst = pr ? Lq.p_task : Lq.s_task;
-    for (unsigned int k = lane; k < n; k += 32) dst[t0 + k] = (unsigned int)it;
+    const unsigned int cap = pr ? cap_p : cap_s;
+    for (unsigned int k = lane; k < n && t0 + k < cap; k += 32) dst[t0 + k] = (unsigned int)it;
   }
 }
 
@@ -1783,14 +1797,18 @@ static int resident_ctas(const void* fn) {
 
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev) {
   cudaMemsetAsync(E.Lq.n_live, 0, sizeof(unsigned int), E.st);
-  const long long n = E.n_ptasks + E.n_stasks;
+  // a captured rebuild step sizes the launch by the task capacity and the kernel
+  // reads the counts of the build from the device
+  const int cap_p = (int)E.l_ptask.n, cap_s = (int)E.l_stask.n;
+  const long long npt = E.gcap ? -1 : E.n_ptasks, nst = E.gcap ? -1 : E.n_stasks;
+  const long long n = E.gcap ? (long long)cap_p + cap_s : E.n_ptasks + E.n_stasks;
   if (n == 0) return;
   const int grid = (int)std::min<long long>((n + 255) / 256, (long long)E.nsm * 16);
   if (dens)
-    launch_pdl(k_live_tasks<true>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, E.partial_pass,
-                                                it_dev);
+    launch_pdl(k_live_tasks<true>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, npt, nst, E.partial_pass, it_dev,
+               cap_p, cap_s);
   else
-    launch_pdl(k_live_tasks<false>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, E.n_ptasks, E.n_stasks, 0, nullptr);
+    launch_pdl(k_live_tasks<false>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, npt, nst, 0, nullptr, cap_p, cap_s);
   count_launch();
 }
 
@@ -1843,8 +1861,8 @@ void launch_zero_density(Engine& E, bool all) {
 void launch_set_active(Engine& E) {
   E.partial_pass = 0;
   launch_pdl(k_set_active, E.grid(E.N), 256, E.st, E.N, E.act.p); count_launch();
-  cudaMemsetAsync(E.t_active.p, 1, E.n_nodes, E.st);
-  cudaMemsetAsync(E.tl_active.p, 1, E.n_tiles, E.st);
+  cudaMemsetAsync(E.t_active.p, 1, E.gcap ? (size_t)E.cap_nodes : (size_t)E.n_nodes, E.st);
+  cudaMemsetAsync(E.tl_active.p, 1, E.gcap ? (size_t)E.N : (size_t)E.n_tiles, E.st);
 }
 
 void launch_count_unconverged(Engine& E, int* out) {
@@ -1853,11 +1871,15 @@ void launch_count_unconverged(Engine& E, int* out) {
 
 void launch_mark_active_cells(Engine& E) {
   E.partial_pass = 1;
-  cudaMemsetAsync(E.t_active.p, 0, E.n_nodes, E.st);
-  cudaMemsetAsync(E.tl_active.p, 0, E.n_tiles, E.st);
-  cudaMemsetAsync(E.t_alo.p, 0xff, 3 * (size_t)E.n_nodes * sizeof(unsigned int), E.st);
-  cudaMemsetAsync(E.t_ahi.p, 0, 3 * (size_t)E.n_nodes * sizeof(unsigned int), E.st);
-  launch_pdl(k_mark_active, E.grid(32 * E.n_tiles), 256, E.st, E.n_tiles, E.act.p, E.pos4.p, E.T, E.TL);
+  // a captured rebuild step covers the capacities (this build's sizes are on the device)
+  const long long nn = E.gcap ? E.cap_nodes : E.n_nodes, nt = E.gcap ? E.N : E.n_tiles;
+  cudaMemsetAsync(E.t_active.p, 0, nn, E.st);
+  cudaMemsetAsync(E.tl_active.p, 0, nt, E.st);
+  cudaMemsetAsync(E.t_alo.p, 0xff, 3 * (size_t)nn * sizeof(unsigned int), E.st);
+  cudaMemsetAsync(E.t_ahi.p, 0, 3 * (size_t)nn * sizeof(unsigned int), E.st);
+  launch_pdl(k_mark_active, E.grid(32 * nt), 256, E.st, nt,
+             E.gcap ? reinterpret_cast<const unsigned int*>(E.dev_counters.p + 4) : nullptr, E.act.p, E.pos4.p, E.T,
+             E.TL);
   count_launch();
 }
 
@@ -1870,7 +1892,9 @@ void launch_task_offsets(Engine& E) {
 }
 
 void launch_task_items(Engine& E) {
-  launch_pdl(k_task_items, E.nsm * 8, 256, E.st, E.Lq, E.T, E.n_pairs, E.n_selfs); count_launch();
+  launch_pdl(k_task_items, E.nsm * 8, 256, E.st, E.Lq, E.T, E.gcap ? -1 : E.n_pairs, E.gcap ? -1 : E.n_selfs,
+             E.cap_pair, E.cap_self, (unsigned int)E.l_ptask.n, (unsigned int)E.l_stask.n);
+  count_launch();
 }
 
 void launch_bracket_reset(Engine& E) {

@@ -90,6 +90,12 @@ class Engine {
   sph_status step_graph();            // a kept-decomposition step as one CUDA graph (prm.reuse)
   sph_status capture_step_graph();
   void drop_step_graph();
+  sph_status build_step_graph();      // a step that rebuilds the decomposition, as one CUDA graph
+  sph_status capture_build_graph();
+  void drop_build_graph();
+  sph_status enqueue_captured_build();
+  sph_status step_host(bool moving);  // the rest of a step after its kick and drift, host-sequenced
+  sph_status step_rest_after_build();
   sph_status density();                                        // one pass at the current h, all particles
   sph_status h_update(long long* n_unconverged, int* iterations);
   sph_status force();
@@ -236,6 +242,26 @@ class Engine {
   cudaGraphExec_t step_x = nullptr;
   bool graph_ready = false, graph_off = false;
   long long g_pre = 0, g_keep = 0, g_iter = 0, g_force = 0;   // kernels per part
+  // the captured rebuild step (valid while the boxes keep their top levels and the
+  // capacities hold; a host build drops it, the next step captures it again)
+  bool gcap = false;              // launches being captured for it: capacity-sized, counts on the device
+  cudaGraph_t bstep_g = nullptr;
+  cudaGraphExec_t bstep_x = nullptr;
+  bool bgraph_ready = false, bgraph_prof = false;
+  long long gb_build = 0, gb_setup = 0, gb_iter = 0, gb_force = 0;   // kernels per part
+  int gb_last_q = 0;              // the expansion queue the last list round leaves empty
+  DBuf<unsigned int> gstat;       // [0] 1 when the captured build held
+  struct GProfRec {
+    int phase, ev;
+    long long launches;
+  };
+  std::vector<GProfRec> gprof_recs;   // phase events recorded inside the captured rebuild step
+  std::vector<cudaEvent_t> gev_pool;
+  std::vector<double> gprof_ms;
+  std::vector<long long> gprof_calls, gprof_launches;
+  bool prof_into_graph = false;
+  long long steps_host = 0, steps_graph = 0, host_syncs = 0;
+  long long steps_in_layout = 0;  // steps since the boxes were last laid out (a capture pays off after a few)
   long long last_unconverged = 0;
   bool built = false, have_density = false, have_ghost = false, have_force = false, have_acc = false;
   bool have_fcount = false;       // the last force pass counted pairs (fcnt is filled)
@@ -263,6 +289,7 @@ class Engine {
 
   // helpers
   int grid(long long work, int threads = 256) const;
+  cudaError_t sync_stream();
   sph_status cuda_fail(cudaError_t e, const char* where);
   sph_status fail(sph_status s, const std::string& msg);
   sph_status ensure_particle_capacity();

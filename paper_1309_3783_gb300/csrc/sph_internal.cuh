@@ -50,6 +50,7 @@ enum : unsigned int {
   ERR_OVERFLOW = 4u,         // a device list exceeded its capacity
   ERR_REBUILD = 8u,          // some H outgrew what the cell splits assumed
   ERR_DEPTH = 16u,           // a split was blocked by a depth bound below the full depth
+  ERR_SHAPE = 32u,           // a captured build's top levels no longer fit the boxes' support radii
 };
 
 // One box of a batch.  Particles of box b occupy [off, off + n) both in the

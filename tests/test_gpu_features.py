@@ -467,3 +467,41 @@ def test_depth_bound_too_shallow_redoes_the_build(api):
 
     assert cells_key(got_cells) == cells_key(ref_cells)
     np.testing.assert_array_equal(got, ref)
+
+
+def test_captured_rebuild_steps_equal_host_steps(api):
+    """sph_params.graphs = 1 runs every kick-drift-kick step that rebuilds the
+    decomposition as one CUDA graph (one synchronisation per step), falling back
+    to the host-driven build when the captured shape or capacities no longer hold;
+    graphs = 0 launches everything from the host.  Over a run of a clustered box
+    (its cells and tasks change every step) the two runs must agree."""
+    box = inputs.plummer_box(n=32768, n_spheres=4, seed=12)
+    dt = 2e-4
+    out, stats = {}, {}
+    for g in (0, 1):
+        ctx = _ctx_with(api, graphs=g, h_tol=5e-6)
+        try:
+            b = api.box_from(ctx, box)
+            try:
+                s0 = None
+                for k in range(12):
+                    b.step(dt)
+                    if k == 3:
+                        s0 = b.stats()
+                s1 = b.stats()
+                out[g] = {f: b.get(f) for f in ("x", "h", "rho", "a", "count")}
+                stats[g] = {k: s1[k] - s0[k] for k in ("graph_steps", "host_steps", "host_syncs", "builds")}
+            finally:
+                b.close()
+        finally:
+            api.sph_ctx_destroy(ctx)
+    print(f"[captured steps] last 8 steps: host launches {stats[0]}, graphs {stats[1]}")
+    assert stats[0]["graph_steps"] == 0 and stats[1]["graph_steps"] > 0
+    # a captured step synchronises once (its status read), a host step several times
+    assert stats[1]["host_syncs"] <= stats[1]["graph_steps"] + 8 * stats[1]["host_steps"]
+    assert stats[0]["host_syncs"] >= 2 * stats[0]["host_steps"]
+    assert stats[1]["builds"] == 8
+    # one synchronisation per captured step that held; more for the others
+    assert stats[1]["host_syncs"] < stats[0]["host_syncs"]
+    assert np.mean(out[1]["count"] != out[0]["count"]) < 1e-3
+    _close_runs(out[1], out[0], box.L)

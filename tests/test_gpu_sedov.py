@@ -55,6 +55,8 @@ def _run(api, box):
                 if k in marks:
                     snaps.append({"t": marks[k], "x": b.get("x"), "v": b.get("v"), "rho": b.get("rho"),
                                   "P": b.get("P"), "h": b.get("h"), "e": energy()})
+            st = b.stats()
+            print(f"[steps] sedov: {n} steps, {st['graph_steps']} as captured graphs, {st['host_steps']} from the host")
         finally:
             b.close()
     finally:

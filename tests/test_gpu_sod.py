@@ -43,6 +43,8 @@ def _run(api, box, t_end):
                 b.step(dt)
             out = {k: b.get(k) for k in ("x", "v", "rho", "P", "h")}
             out["steps"] = n
+            st = b.stats()
+            print(f"[steps] sod: {n} steps, {st['graph_steps']} as captured graphs, {st['host_steps']} from the host")
         finally:
             b.close()
     finally:

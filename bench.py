@@ -22,6 +22,11 @@ e2e   : the same through the C-ABI with host buffers: every step uploads the ful
         state back (x, v, u, h, a, du/dt, one multi-field read) inside the timed
         region.
 
+step_control: per timed step, steps run as one captured CUDA graph, steps
+        sequenced from the host (the fallback when a captured build's shape no
+        longer holds) and host synchronisations; gpu_launches counts the kernels
+        of the timed steps, those inside graphs included.
+
 amortised: the same run with the decomposition kept over steps while it stays
         valid (sph_params.reuse, Section II-C: sorted indices re-used until the
         decomposition must be rebuilt); builds and reuses over the timed steps.
@@ -42,6 +47,9 @@ serving: the served batch -- 512 independent jittered-lattice boxes with
         per box and step), the request latency and the aggregate throughput.  The
         same requests on a 1-in-8 subset also run one box at a time through the
         plain single-box path for comparison with the batched server.
+
+``--workload clustered-4194304`` runs one octant of the headline recipe (the same
+densities in a box of half the edge), the case the counter captures use.
 
 ``--impl reference`` times the FP64 oracle (the only reference this method has:
 the paper publishes no code) on the host cores, each step on a bounded sample of
@@ -83,12 +91,24 @@ def _lognormal(seed):
     return inputs.lognormal_box(seed=seed)
 
 
+def _clustered_octant(seed):
+    return inputs.clustered_box(n=2 ** 22, n_spheres=512, L=0.5, seed=seed)
+
+
 WORKLOADS = {
     "clustered-33554432": (_clustered, "33,554,432 particles: 30 % uniform, 70 % in 4096 Plummer spheres with "
                                        "scale radii log-uniform in [1e-4, 1e-2]"),
     "plummer-262144": (_plummer, "262,144 particles: 50 % uniform, 50 % in 16 Plummer spheres of scale 0.02"),
     "lognormal-8388608": (_lognormal, "8,388,608 particles drawn from a log-normal field (sigma 2, P(k) ~ k^-2, "
                                       "256^3 mesh)"),
+}
+# profiling only (never among the extra workloads): one octant of the headline
+# recipe -- the same background density, sphere populations and scale radii in a
+# box of half the edge -- small enough for multi-pass counter captures
+PROFILE_WORKLOADS = {
+    "clustered-4194304": (_clustered_octant, "4,194,304 particles: one octant of the 33,554,432-particle recipe "
+                                             "(L = 0.5, 512 Plummer spheres: the same densities and sphere "
+                                             "profiles)"),
 }
 DEFAULT_WORKLOAD = "clustered-33554432"
 SAMPLE_K = 4096             # the oracle's bounded sample per step: particles nearest a drawn centre
@@ -255,10 +275,13 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    make, recipe = WORKLOADS[args.workload]
+    make, recipe = {**WORKLOADS, **PROFILE_WORKLOADS}[args.workload]
     box = make(replica_seed(rank))
     n = box.n
-    ctx = sph.sph_ctx_create(device=local_rank)
+    params = sph.sph_params_default()
+    if getattr(args, "host_steps", False):
+        params.graphs = 0
+    ctx = sph.sph_ctx_create(params, device=local_rank)
     stream = torch.cuda.Stream()
     sph.sph_ctx_set_stream(ctx, stream.cuda_stream)
     b, leaf_max, cluster_max, dt = prepare_box(sph, ctx, box, not args.no_tune)
@@ -283,6 +306,7 @@ def run_ours(args, rank, world, local_rank):
     big = n * 520 > 4 * 129 * 2 ** 20
     flush = None if big else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local_rank}")
     l0 = sph.sph_launch_count()
+    st_first = b.stats()
     b.profile(True)
     with ClockSampler(local_rank) as clk:
         barrier()
@@ -356,6 +380,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac_of_measured": achieved / fp32_measured if fp32_measured else None,
                      "peak_measured_source": "independent FMA chains on every SM (sph_measure_fp32_peak), this run"},
         "gpu_launches": launches,
+        "step_control": {k: (st_last[k] - st_first[k]) / args.steps for k in ("graph_steps", "host_steps", "host_syncs")},
         "clocks": clk.summary(),
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if v["calls"]},
         "pairs": {"density": st["density_pairs"], "density_candidates": st["density_candidates"],
@@ -667,14 +692,16 @@ def oracle_sample_step(box, sub, t):
 
 def cpu_baseline(box, workload, budget_s=20.0):
     sampler = OracleSampler(box)
-    t_total, reps = 0.0, 0
+    t_total, cpu_total, reps = 0.0, 0.0, 0
     while t_total < budget_s and reps < 20:
         sub, t = sampler.draw()
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         oracle_sample_step(box, sub, t)
         t_total += time.perf_counter() - t0
+        cpu_total += time.process_time() - c0
         reps += 1
-    return {"value": sampler.k * reps / t_total, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+    return {"value": sampler.k * reps / t_total, "unit": UNIT, "cores": host_threads(),
+            "cores_busy": round(cpu_total / t_total, 2), "kind": "oracle",
             "sample": f"{reps} oracle sample steps on the {workload} box: each the {sampler.k} particles nearest a "
                       f"randomly drawn particle, h iterated over the sub-volume around them (FP64), then their force "
                       f"pass and conservation sums; k-d tree searches on all host threads, numpy arithmetic mostly "
@@ -686,17 +713,18 @@ def run_reference(args, rank, world):
         return None
     workload = getattr(args, "workload", DEFAULT_WORKLOAD)
     steps, warmup = getattr(args, "steps", 20), getattr(args, "warmup", 5)
-    make, recipe = WORKLOADS[workload]
+    make, recipe = {**WORKLOADS, **PROFILE_WORKLOADS}[workload]
     box = make(replica_seed(0))
     sampler = OracleSampler(box)
     draws = [sampler.draw() for _ in range(warmup + steps)]
     for sub, t in draws[:warmup]:
         oracle_sample_step(box, sub, t)
-    times = []
+    times, cpu = [], 0.0
     for sub, t in draws[warmup:]:
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         oracle_sample_step(box, sub, t)
         times.append(time.perf_counter() - t0)
+        cpu += time.process_time() - c0
     total = sum(times)
     value = sampler.k * steps / total
     return {
@@ -706,7 +734,8 @@ def run_reference(args, rank, world):
         "config": {"workload": workload, "recipe": recipe, "particles_per_step": sampler.k,
                    "sample": f"each step the {sampler.k} particles nearest a randomly drawn particle of the box, h "
                              f"iterated over their sub-volume, their force pass and sums"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_threads(),
+                         "cores_busy": round(cpu / total, 2) if total > 0 else None, "kind": "oracle",
                          "sample": f"{sampler.k} sampled particles of the {workload} box per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -718,12 +747,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted({**WORKLOADS, **PROFILE_WORKLOADS}), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="keep the paper's leaf_max = 400")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-batch latency run")
     ap.add_argument("--no-extra-workloads", action="store_true", help="skip the other single-box workloads")
     ap.add_argument("--no-precision", action="store_true", help="skip the plain-FP32 position comparison")
+    ap.add_argument("--host-steps", action="store_true",
+                    help="launch every kernel of a step from the host instead of one captured graph "
+                         "(the same kernels; for counter captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

@@ -119,6 +119,19 @@ typedef struct sph_params {
                              keep their top levels and the capacities hold; one
                              synchronisation per step); 0: every launch from the
                              host, with the synchronisations of a build (1)      */
+    int32_t pair_cache;   /* 1: the first density pass of an h iteration keeps its
+                             interacting pairs (per batch of staged partners: their
+                             indices and each own particle's exact pair mask), and
+                             the force pass replays them for every task whose
+                             particles kept their h since then instead of culling
+                             and testing the candidates again; about 256 bytes
+                             per batch, about one batch per particle (the pool
+                             starts at 1.5 and grows to what a recording took;
+                             tasks a full pool could not keep cull again).  The pair
+                             set is the same.  On GB300 the force pass then takes
+                             a quarter less time and the recording first density
+                             pass about as much more; 0: the force pass culls on
+                             its own (0)                                           */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;
@@ -187,6 +200,12 @@ typedef struct sph_stats {
     int64_t graph_steps;        /* steps of sph_step run as one captured graph (params.graphs) */
     int64_t host_steps;         /* steps whose passes were launched from the host       */
     int64_t host_syncs;         /* synchronisations of the host with the box's stream   */
+    /* filled only when pair counting is on: force tasks since the last density
+       or h update replayed from the pairs the first density pass kept
+       (params.pair_cache), and those that culled their candidates again (a
+       particle near them took a new h, or the records ran out of room)      */
+    int64_t force_tasks_replayed;
+    int64_t force_tasks_culled;
 } sph_stats;
 
 /* Device time of one phase of the path (CUDA events on the stream the phase runs

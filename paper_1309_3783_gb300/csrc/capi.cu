@@ -68,6 +68,8 @@ double measure_fp32_peak(cudaStream_t st, int nsm, float* scratch);
 void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
 void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep);
+cudaError_t add_cond_set_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                              cudaGraphConditionalHandle h, const int* flag);
 void launch_iter_start(Engine& E, cudaGraphConditionalHandle iter);
 void launch_iter_next(Engine& E, cudaGraphConditionalHandle iter, cudaGraphConditionalHandle force);
 void launch_iter_step(Engine& E);
@@ -112,7 +114,8 @@ int Engine::prof_begin(int phase, long long* l0, cudaStream_t on) {
     // (created before the capture); read after every launch of the graph
     const int ev = (int)(2 * gprof_recs.size());
     if ((size_t)ev + 2 > gev_pool.size()) return -1;
-    cudaEventRecord(gev_pool[ev], on ? on : st);
+    // an event node of the graph (a plain record would only order the capture)
+    cudaEventRecordWithFlags(gev_pool[ev], on ? on : st, cudaEventRecordExternal);
     (void)phase;
     return ev;
   }
@@ -131,7 +134,7 @@ int Engine::prof_begin(int phase, long long* l0, cudaStream_t on) {
 void Engine::prof_end(int phase, int ev, long long l0, cudaStream_t on) {
   if (!prof || ev < 0) return;
   if (prof_into_graph) {
-    cudaEventRecord(gev_pool[ev + 1], on ? on : st);
+    cudaEventRecordWithFlags(gev_pool[ev + 1], on ? on : st, cudaEventRecordExternal);
     gprof_recs.push_back(GProfRec{phase, ev, launch_count() - l0});
     return;
   }
@@ -360,6 +363,7 @@ sph_status Engine::ensure_particle_capacity() {
   CK(tl_hi.reserve(n));
   CK(tl_cen.reserve(n));
   CK(tl_active.reserve(n));
+  CK(tl_changed.reserve(n));
   TL.start = tl_start.p;
   TL.n = tl_n.p;
   TL.leaf = tl_leaf.p;
@@ -367,6 +371,7 @@ sph_status Engine::ensure_particle_capacity() {
   TL.hi = tl_hi.p;
   TL.cen = tl_cen.p;
   TL.active = tl_active.p;
+  TL.changed = tl_changed.p;
   CK(dacc.reserve(n));
   CK(dcnt.reserve(n));
   CK(ghost4.reserve(n));
@@ -407,8 +412,11 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   CK(t_hlim.reserve(n));
   CK(t_cen.reserve(n));
   CK(t_active.reserve(n));
+  CK(t_changed.reserve(n));
   CK(t_alo.reserve(3 * n));
   CK(t_ahi.reserve(3 * n));
+  CK(t_clo.reserve(3 * n));
+  CK(t_chi.reserve(3 * n));
   CK(t_tile0.reserve(n));
   CK(t_ntile.reserve(n));
   CK(t_n.reserve(8));
@@ -428,8 +436,11 @@ sph_status Engine::ensure_tree_capacity(int nodes) {
   T.axes = t_axes.p;
   T.sortbase = t_sortbase.p;
   T.active = t_active.p;
+  T.changed = t_changed.p;
   T.alo = t_alo.p;
   T.ahi = t_ahi.p;
+  T.clo = t_clo.p;
+  T.chi = t_chi.p;
   T.tile0 = t_tile0.p;
   T.ntile = t_ntile.p;
   T.n_nodes = t_n.p;
@@ -765,6 +776,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(cudaMemcpyAsync(x_build.p, x.p, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   reusable = true;
   ++n_builds;
+  rec_valid = false;        // the records name this build's tasks
   graph_ready = false;      // a captured step holds this build's sizes and buffers
   bgraph_ready = false;     // ... and so does the captured rebuild step (the buffers swapped)
   gb_last_q = 2 + (rounds & 1);
@@ -772,6 +784,75 @@ sph_status Engine::build_once(bool* retry) {
 }
 
 // ----------------------------------------------------------------------- passes
+// The pool holds the last recordings' need with a quarter to spare, and at least
+// 1.5 batches per particle (clustered boxes take about one).  A recording that
+// runs out keeps the tasks it completed; the others take the full force path.
+// A larger pool moves the buffers, so the captured steps are captured again.
+sph_status Engine::rec_prepare() {
+  if (!prm.pair_cache) return SPH_OK;
+  if (rec_unread && rec_ctr.p) {
+    // the last recording's need was not read back with a synchronisation of its own
+    unsigned int rc = 0;
+    CK(cudaMemcpyAsync(&rc, rec_ctr.p, sizeof(rc), cudaMemcpyDeviceToHost, st));
+    CK(sync_stream());
+    rec_used = rc;
+    rec_need = std::max<long long>(rec_need, rc);
+  }
+  rec_unread = false;
+  long long want = std::max<long long>(rec_need + rec_need / 4, (N + N / 2) / REC_CHUNK) + 64;
+  want = std::min<long long>(want, (long long)(REC_NONE / REC_CHUNK) - 1);
+  bool moved = false;
+  if ((size_t)want > rec_next.n || !rec_pool.p) {
+    rec_pool.release();
+    rec_next.release();
+    moved = true;
+    if (rec_pool.reserve((size_t)want * REC_CHUNK * 64) != cudaSuccess ||
+        rec_next.reserve((size_t)want) != cudaSuccess) {
+      // no room for the records: the force pass culls on its own
+      cudaGetLastError();
+      rec_pool.release();
+      rec_next.release();
+      R = PairRec{};
+      if (!gcap) graph_ready = bgraph_ready = false;
+      return SPH_OK;
+    }
+  }
+  CK(rec_ctr.reserve(1));
+  const size_t np = std::max<size_t>(l_ptask.n, 1), ns = std::max<size_t>(l_stask.n, 1);
+  if (np > rec_pt.n || ns > rec_st.n) moved = true;
+  CK(rec_pt.reserve(np));
+  CK(rec_st.reserve(ns));
+  R.pool = rec_pool.p;
+  R.next = rec_next.p;
+  R.ctr = rec_ctr.p;
+  R.ptask = rec_pt.p;
+  R.stask = rec_st.p;
+  R.cap = (unsigned int)(rec_next.n);
+  if (moved && !gcap) {
+    graph_ready = false;
+    bgraph_ready = false;
+  }
+  return SPH_OK;
+}
+
+void Engine::rec_enqueue_reset() {
+  rec_valid = false;
+  if (!prm.pair_cache || !rec_pool.p) return;
+  const size_t np = gcap ? rec_pt.n : (size_t)n_ptasks, ns = gcap ? rec_st.n : (size_t)n_stasks;
+  const size_t nn = gcap ? (size_t)cap_nodes : (size_t)n_nodes, nt = gcap ? (size_t)N : (size_t)n_tiles;
+  cudaMemsetAsync(rec_ctr.p, 0, sizeof(unsigned int), st);
+  if (np) cudaMemsetAsync(rec_pt.p, 0xff, np * sizeof(uint2), st);
+  if (ns) cudaMemsetAsync(rec_st.p, 0xff, ns * sizeof(uint2), st);
+  if (nn) {
+    cudaMemsetAsync(t_changed.p, 0, nn, st);
+    cudaMemsetAsync(t_clo.p, 0xff, 3 * nn * sizeof(unsigned int), st);
+    cudaMemsetAsync(t_chi.p, 0, 3 * nn * sizeof(unsigned int), st);
+  }
+  if (nt) cudaMemsetAsync(tl_changed.p, 0, nt, st);
+  rec_valid = true;
+  rec_unread = true;
+}
+
 sph_status Engine::set_all_active() {
   launch_set_active(*this);
   CK(cudaGetLastError());
@@ -800,6 +881,9 @@ sph_status Engine::density() {
   if (count_pairs) CK(cudaMemsetAsync(pc.p, 0, 16 * sizeof(unsigned long long), st));
   sph_status s = set_all_active();
   if (s != SPH_OK) return s;
+  s = rec_prepare();
+  if (s != SPH_OK) return s;
+  rec_enqueue_reset();
   s = density_pass();
   if (s != SPH_OK) return s;
   CK(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
@@ -824,6 +908,9 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
   launch_bracket_reset(*this);
   sph_status s = set_all_active();
   if (s != SPH_OK) return s;
+  s = rec_prepare();
+  if (s != SPH_OK) return s;
+  rec_enqueue_reset();
   // Iterations run in batches launched without a host round trip: the iteration
   // counter and the stopping test live on the device (k_iter_step), and the
   // kernels of iterations launched past a stop return at once.  One
@@ -860,7 +947,15 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(itv, it_dev.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    unsigned int rc = 0;
+    const bool read_rec = rebuilds == 0 && it == 1 && rec_valid;
+    if (read_rec) CK(cudaMemcpyAsync(&rc, rec_ctr.p, sizeof(rc), cudaMemcpyDeviceToHost, st));
     CK(sync_stream());
+    if (read_rec) {
+      rec_used = rc;
+      rec_need = std::max<long long>(rec_need, rc);
+      rec_unread = false;
+    }
     if (rebuilds == 0 && it == 1) first_active = itv[1];
     it = itv[0];
     if (itv[2] == 1) break;            // every particle finalised (at the limit, unconverged ones too)
@@ -1130,6 +1225,10 @@ void Engine::drop_step_graph() {
 
 sph_status Engine::capture_step_graph() {
   drop_step_graph();
+  {
+    const sph_status rs = rec_prepare();
+    if (rs != SPH_OK) return rs;
+  }
   CK(dmax_bits.reserve(nbox));
   CK(reuse_flag.reserve(1));
   CK(it_dev.reserve(4));
@@ -1178,6 +1277,7 @@ sph_status Engine::capture_step_graph() {
   launch_set_active(*this);
   CKG(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
   CKG(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  rec_enqueue_reset();
   launch_iter_start(*this, iter);
   CKG(cudaStreamEndCapture(st, &body));
   g_keep = launch_count() - c1;
@@ -1230,12 +1330,18 @@ sph_status Engine::step_graph() {
     if (s != SPH_OK) return s;
   }
   CK(cudaGraphLaunch(step_x, st));
-  unsigned int flag = 0, ea = 0;
+  unsigned int flag = 0, ea = 0, rc = 0;
   int itv[2] = {0, 0};
   CK(cudaMemcpyAsync(&flag, reuse_flag.p, sizeof(flag), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&ea, err_all.p, sizeof(ea), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(itv, it_dev.p, sizeof(itv), cudaMemcpyDeviceToHost, st));
+  if (R.pool) CK(cudaMemcpyAsync(&rc, rec_ctr.p, sizeof(rc), cudaMemcpyDeviceToHost, st));
   CK(sync_stream());
+  if (R.pool && !flag) {
+    rec_used = rc;
+    rec_need = std::max<long long>(rec_need, rc);
+    rec_unread = false;
+  }
   const bool rebuild = flag != 0 || (ea & ERR_REBUILD) != 0u;
   count_launches(g_pre + (flag ? 0 : g_keep + (long long)itv[0] * g_iter + (rebuild ? 0 : g_force)));
   if (rebuild) {
@@ -1253,6 +1359,7 @@ sph_status Engine::step_graph() {
   ++n_reuses;
   built = true;
   have_density = have_ghost = have_force = have_acc = true;
+  rec_valid = R.pool != nullptr;
   last_iters = itv[0];
   last_rebuilds = 0;
   first_active = itv[1];
@@ -1445,6 +1552,8 @@ sph_status Engine::capture_build_graph() {
   {
     sph_status s = ensure_side_stream();
     if (s != SPH_OK) return s;
+    s = rec_prepare();
+    if (s != SPH_OK) return s;
   }
   if (prof) {
     while (gev_pool.size() < 64) {
@@ -1465,6 +1574,8 @@ sph_status Engine::capture_build_graph() {
   gcap = true;
   prof_into_graph = prof;
   CKB(cudaStreamBeginCapture(st, mode));
+  // the force decision of this launch starts out false (the later force phases read it)
+  CKB(cudaMemsetAsync(it_dev.p + 3, 0, sizeof(int), st));
   {
     Scope sc(this, PH_STEP);
     launch_kick(*this);
@@ -1495,6 +1606,7 @@ sph_status Engine::capture_build_graph() {
   launch_set_active(*this);
   CKB(cudaMemsetAsync(dev_counters.p, 0, 4 * sizeof(int), st));
   CKB(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
+  rec_enqueue_reset();
   launch_iter_start(*this, iter);
   CKB(cudaStreamEndCapture(st, &body));
   gb_setup = launch_count() - c1;
@@ -1536,36 +1648,81 @@ sph_status Engine::capture_build_graph() {
     prev = e1;
     gprof_recs.push_back(GProfRec{PH_DENSITY, ev_iter, gb_iter});
   }
-  // IF finished without a rebuild: force pass and the closing kick
-  cp_ = {};
-  cp_.type = cudaGraphNodeTypeConditional;
-  cp_.conditional.handle = frc;
-  cp_.conditional.type = cudaGraphCondTypeIf;
-  cp_.conditional.size = 1;
-  CKB(cudaGraphAddNode(&n4, bstep_g, &prev, nullptr, 1, &cp_));
-  body = cp_.conditional.phGraph_out[0];
+  // IF finished without a rebuild: force pass and the closing kick.  Timed, the
+  // phases take one conditional node each, so that event nodes of the top graph
+  // sit between them (a conditional body holds no events); a handle belongs to
+  // one node, so the later ones take the decision from the flag k_iter_next left
+  // in it_dev[3], one kernel node each.
   c1 = launch_count();
-  CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
-  CKB(cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st));
-  CKB(cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st));
-  {
-    Scope sc(this, PH_FORCE_TASKS);
+  prof = false;
+  prof_into_graph = false;
+  int nphase = 0;
+  auto phase_if = [&](int phase, auto&& enqueue) -> sph_status {
+    cudaGraphConditionalHandle h = frc;
+    if (nphase > 0) {
+      CKB(cudaGraphConditionalHandleCreate(&h, bstep_g, 0, cudaGraphCondAssignDefault));
+      cudaGraphNode_t ks;
+      CKB(add_cond_set_node(&ks, bstep_g, &prev, 1, h, it_dev.p + 3));
+      count_launches(1);
+      prev = ks;
+    }
+    ++nphase;
+    int ev = -1;
+    if (keep_prof) {
+      ev = (int)(2 * gprof_recs.size());
+      cudaGraphNode_t e0;
+      CKB(cudaGraphAddEventRecordNode(&e0, bstep_g, &prev, 1, gev_pool[ev]));
+      prev = e0;
+    }
+    cudaGraphNodeParams q = {};
+    q.type = cudaGraphNodeTypeConditional;
+    q.conditional.handle = h;
+    q.conditional.type = cudaGraphCondTypeIf;
+    q.conditional.size = 1;
+    cudaGraphNode_t nd;
+    CKB(cudaGraphAddNode(&nd, bstep_g, &prev, nullptr, 1, &q));
+    const long long l0 = launch_count();
+    CKB(cudaStreamBeginCaptureToGraph(st, q.conditional.phGraph_out[0], nullptr, nullptr, 0, mode));
+    enqueue();
+    cudaGraph_t bg = nullptr;
+    CKB(cudaStreamEndCapture(st, &bg));
+    prev = nd;
+    if (keep_prof) {
+      cudaGraphNode_t e1;
+      CKB(cudaGraphAddEventRecordNode(&e1, bstep_g, &prev, 1, gev_pool[ev + 1]));
+      prev = e1;
+      gprof_recs.push_back(GProfRec{phase, ev, launch_count() - l0});
+    }
+    return SPH_OK;
+  };
+  auto force_tasks = [&] {
+    cudaMemsetAsync(facc.p, 0, N * sizeof(float4), st);
+    cudaMemsetAsync(fvsig.p, 0, N * sizeof(float), st);
     launch_live_tasks(*this, false);
-  }
-  {
-    Scope sc(this, PH_FORCE);
-    launch_force(*this);
-  }
-  {
-    Scope sc(this, PH_REDUCE);
+  };
+  auto reduce = [&] {
     launch_reduce(*this);
     launch_save_acc(*this);
+  };
+  sph_status ps;
+  if (keep_prof) {
+    ps = phase_if(PH_FORCE_TASKS, force_tasks);
+    if (ps == SPH_OK) ps = phase_if(PH_FORCE, [&] { launch_force(*this); });
+    if (ps == SPH_OK) ps = phase_if(PH_REDUCE, reduce);
+    if (ps == SPH_OK) ps = phase_if(PH_STEP, [&] { launch_kick(*this); });
+  } else {
+    ps = phase_if(PH_FORCE, [&] {
+      force_tasks();
+      launch_force(*this);
+      reduce();
+      launch_kick(*this);
+    });
   }
-  {
-    Scope sc(this, PH_STEP);
-    launch_kick(*this);
+  prof = keep_prof;
+  if (ps != SPH_OK) {
+    gcap = false;
+    return ps;
   }
-  CKB(cudaStreamEndCapture(st, &body));
   gb_force = launch_count() - c1;
   gcap = false;
   prof_into_graph = false;
@@ -1593,8 +1750,15 @@ sph_status Engine::build_step_graph() {
   CK(cudaMemcpyAsync(lc, l_counts.p, sizeof(lc), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&ntl, dev_counters.p + 4, sizeof(ntl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&bcw, big_count.p, sizeof(bcw), cudaMemcpyDeviceToHost, st));
+  unsigned int rc = 0;
+  if (R.pool) CK(cudaMemcpyAsync(&rc, rec_ctr.p, sizeof(rc), cudaMemcpyDeviceToHost, st));
   CK(sync_stream());
   const bool held = gs == 1u;
+  if (R.pool && held) {
+    rec_used = rc;
+    rec_need = std::max<long long>(rec_need, rc);
+    rec_unread = false;
+  }
   const bool rebuild = !held || (ea & ERR_REBUILD) != 0u;
   count_launches(gb_build + (held ? gb_setup + (long long)itv[0] * gb_iter + (rebuild ? 0 : gb_force) : 0));
   if (held) {
@@ -1625,6 +1789,7 @@ sph_status Engine::build_step_graph() {
     return step_rest_after_build();
   }
   ++steps_graph;
+  rec_valid = R.pool != nullptr;
   if (bgraph_prof) {
     for (const GProfRec& r : gprof_recs) {
       float t = 0.0f;
@@ -1903,6 +2068,8 @@ sph_status Engine::stats(int b, sph_stats* o) {
     o->force_pairs_cellpair = (long long)c[6];
     o->force_candidates_cellpair = (long long)c[7];
     o->guard_rechecks = (long long)c[10];
+    o->force_tasks_replayed = (long long)c[11];
+    o->force_tasks_culled = (long long)c[12];
   }
   return SPH_OK;
 }
@@ -2017,6 +2184,7 @@ void sph_params_default(sph_params* p) {
   p->compensated = -1;
   p->precision = 0;
   p->graphs = 1;
+  p->pair_cache = 0;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
@@ -2028,7 +2196,8 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
   if (!(p.gamma_kernel > 0) || !(p.n_ngb > 0) || !(p.gamma_gas > 1) || p.h_max_iter < 1 || p.leaf_max < 1 ||
       !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0) ||
       !(p.split_headroom >= 0 && p.split_headroom < 1) || p.cluster_max < 1 || p.cluster_max > 32 ||
-      (p.precision != 0 && p.precision != 1) || (p.graphs != 0 && p.graphs != 1))
+      (p.precision != 0 && p.precision != 1) || (p.graphs != 0 && p.graphs != 1) ||
+      (p.pair_cache != 0 && p.pair_cache != 1))
     return SPH_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;

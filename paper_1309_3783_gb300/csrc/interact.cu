@@ -67,6 +67,13 @@ __device__ __forceinline__ BoxExact box_exact(const ItemGeom& g) { return BoxExa
 // split leaves most SMs idle behind the longest ones.
 constexpr unsigned int TASK_CHUNK = 2;
 
+// blocks per SM of the recording first density pass: as the plain first pass
+// (5), with a few registers spilled for the record state, which measured faster
+// than 4 blocks without spills
+#ifndef REC_BLOCKS
+#define REC_BLOCKS 5
+#endif
+
 // Exact decision r_ij < H (physical H) from the caller's FP64 positions.
 __device__ __noinline__ bool exact_less(int gi, int gj, float Hphys, const unsigned int* __restrict__ perm,
                                         const double* __restrict__ x, double L, double halfL, int periodic) {
@@ -160,6 +167,15 @@ struct DensShared {
   int g[32];
   unsigned char act[32];
   float4 ip[32];    // own cluster: position, m
+  // pair records (first pass): the current task's first batch, batch count and
+  // record slot, and 0 once one of its batches was lost (lane 0 keeps them)
+  unsigned int rc_first, rc_nb, rc_slot, rc_ok;
+};
+
+// A warp's next batch (first pass, the same in every lane); a multiple of
+// REC_CHUNK means that its chunk is used up (0: no chunk yet).
+struct RecW {
+  unsigned int pos = 0;
 };
 
 __device__ __forceinline__ void dens_put(DensShared& S, int lane, const DensI& j) {
@@ -206,6 +222,57 @@ __device__ __forceinline__ void commit_counters(const Counters& C, unsigned long
   }
 }
 
+
+// the lanes above this one
+__device__ __forceinline__ unsigned int upper_mask(int lane) {
+  return lane == 31 ? 0u : (0xffffffffu << (lane + 1));
+}
+
+// ------------------------------------------------------------- pair records
+// Called by the whole warp.  A task starts with no batch; its batches go to the
+// warp's current chunk, and to a new chunk (linked from the old one) when that is
+// full.  A batch that finds the pool full is lost, and with it the task's record.
+__device__ __forceinline__ void rec_task_begin(DensShared& S, unsigned int slot) {
+  if ((threadIdx.x & 31) == 0) {
+    S.rc_nb = 0;
+    S.rc_ok = 1;
+    S.rc_slot = slot;
+  }
+}
+
+__device__ __forceinline__ void rec_batch(const PairRec& R, RecW& W, DensShared& S, unsigned int jvalid,
+                                          unsigned int m) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  if (!S.rc_ok) return;
+  if (W.pos % REC_CHUNK == 0u) {
+    unsigned int c = 0;
+    if (lane == 0) c = atomicAdd(R.ctr, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= R.cap) {
+      if (lane == 0) S.rc_ok = 0;
+      W.pos = 0;
+      return;
+    }
+    if (lane == 0 && W.pos != 0) R.next[W.pos / REC_CHUNK - 1u] = c;
+    W.pos = c * REC_CHUNK;
+  }
+  // streaming stores: the records are read once, by the force pass, and should
+  // not push the particle data the passes share out of L2
+  unsigned int* B = R.pool + 64ull * W.pos;
+  __stcs(B + lane, (jvalid >> lane) & 1u ? (unsigned int)S.g[lane] : REC_NONE);
+  __stcs(B + 32 + lane, m);
+  if (lane == 0) {
+    if (S.rc_nb == 0) S.rc_first = W.pos;
+    S.rc_nb += 1;
+  }
+  W.pos += 1;
+}
+
+__device__ __forceinline__ void rec_task_end(uint2* slots, const DensShared& S) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0 && S.rc_ok) slots[S.rc_slot] = make_uint2(S.rc_nb ? S.rc_first : 0u, S.rc_nb);
+}
 
 // =========================================================================== force
 struct ForceI {
@@ -430,10 +497,13 @@ __device__ __forceinline__ void dens_tile(const DensI& I, DensShared& S, unsigne
                                           unsigned int jact, float bandJ, int n, bool own_only, unsigned int cmask,
                                           DensAcc<KAHAN>& acc, unsigned int& cnt, const unsigned int* perm,
                                           const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
-                                          Counters& C) {
+                                          Counters& C, bool rec, const PairRec& R, RecW& W) {
   const int lane = threadIdx.x & 31;
   unsigned int mI, mJ, rc = 0;
   pair_masks(I.p, I.H2, I.band, I.g, I.Hphys, S, bandJ, allow, n, perm, x, box_exact(g), mI, mJ, rc);
+  // the pairs for the force pass: each unordered pair once (inside one cluster,
+  // the partners above the lane)
+  if (rec) rec_batch(R, W, S, jvalid, (mI | mJ) & (own_only ? upper_mask(lane) : 0xffffffffu));
   const unsigned int ui = I.act ? mI : 0u, uj = own_only ? 0u : (mJ & jact);
   if (COUNT) {
     C.cand += I.valid ? __popc(allow & jvalid & cmask) : 0u;
@@ -475,8 +545,11 @@ struct ForceSide {
 
 // Both sides of one force pair, a (own particle) and b (partner), d = x_a - x_b:
 // a gains ca, b gains cb (the antisymmetric acceleration terms and each side's
-// du/dt), both see vsig.  No contribution when r = 0.
-__device__ __forceinline__ void force_pair_terms(const ForceSide& a, const ForceSide& b, bool fa, bool fb,
+// du/dt), both see vsig.  No contribution when r = 0.  A side's kernel gradient
+// is taken inside its support (q < 1) and is zero outside; at q = 1 it is zero
+// too, so the FP32 test agrees with the exact one to within the gradient's size
+// there, about 6 (1 - q)^2 for q within rounding of 1.
+__device__ __forceinline__ void force_pair_terms(const ForceSide& a, const ForceSide& b,
                                                  float alpha, float4& ca, float4& cb, float& vsig) {
   const float dx = a.p.x - b.p.x, dy = a.p.y - b.p.y, dz = a.p.z - b.p.z;
   const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -486,9 +559,12 @@ __device__ __forceinline__ void force_pair_terms(const ForceSide& a, const Force
   if (!(r2 > 0.0f)) return;
   const float rinv = rsqrtf(r2);
   const float r = r2 * rinv;
-  float w, dwa = 0.0f, dwb = 0.0f;
-  if (fa) spline_w_dw(r * a.invH, w, dwa);
-  if (fb) spline_w_dw(r * b.invH, w, dwb);
+  float w, dwa, dwb;
+  const float qa = r * a.invH, qb = r * b.invH;
+  spline_w_dw(qa, w, dwa);
+  spline_w_dw(qb, w, dwb);
+  dwa = qa < 1.0f ? dwa : 0.0f;
+  dwb = qb < 1.0f ? dwb : 0.0f;
   const float Wa = a.K4 * dwa, Wb = b.K4 * dwb;
   const float vdx = fmaf(a.v.x - b.v.x, dx, fmaf(a.v.y - b.v.y, dy, (a.v.z - b.v.z) * dz));
   const float wv = vdx * rinv;
@@ -566,33 +642,17 @@ __device__ __forceinline__ ForceSide own_side(const ForceShared& S, int k) {
   return s;
 }
 
-// Force batch: every pair with r < max(H_i, H_j); own side in the row sweep,
-// partner side in the column sweep unless own_only.
-// Force batch: every pair with r < max(H_i, H_j), each evaluated once for both
-// sides.  The batch's pairs go into a list in shared memory (own lane major),
-// which the warp then takes 32 at a time: one pair per lane, so that all lanes
-// work however unevenly the pairs fall on the rows.  The own side is summed by a
-// segmented warp reduction (a particle's pairs are adjacent in the list) into its
-// task sums; the partner side goes to the partner's batch sums with
-// shared-memory atomics (or, inside one cluster, to that particle's task sums).
+// The pairs of one batch (mask m of the lane's own particle over the staged
+// slots), each evaluated once for both sides.  The pairs go into a list in shared
+// memory (own lane major), which the warp then takes 32 at a time: one pair per
+// lane, so that all lanes work however unevenly the pairs fall on the rows.  The
+// own side is summed by a segmented warp reduction (a particle's pairs are
+// adjacent in the list) into its task sums; the partner side goes to the
+// partner's batch sums (or, inside one cluster, to that particle's task sums).
 template <bool COUNT>
-__device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, unsigned int jvalid,
-                                           float bandJ, int n, bool own_only, unsigned int cmask,
-                                           const unsigned int* perm, const double* x, const BoxExact g,
-                                           float alpha, unsigned int* fcnt, Counters* C) {
+__device__ __forceinline__ void force_rounds(ForceShared& S, unsigned int m, bool own_only, float alpha,
+                                             unsigned int* fcnt) {
   const int lane = threadIdx.x & 31;
-  // the lane's own particle, read back from the staged cluster
-  const float4 ip = S.ip[lane], ih = S.ih[lane];
-  const bool ivalid = ih.x >= 0.0f;
-  unsigned int mI, mJ, rc = 0;
-  pair_masks(make_float3(ip.x, ip.y, ip.z), ih.x, ih.y, __float_as_int(ih.w), ih.z, S, bandJ, allow, n, perm, x, g,
-             mI, mJ, rc);
-  const unsigned int m = mI | mJ;
-  if (COUNT) {
-    C->cand += ivalid ? __popc(allow & jvalid & cmask) : 0u;
-    C->rechecks += rc;
-    C->pairs += __popc(m & cmask);
-  }
   // list the pairs, own lane major
   const unsigned int cnt = __popc(m);
   unsigned int incl = cnt;
@@ -605,7 +665,7 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
   unsigned int k = incl - cnt;
   for (unsigned int mm = m; mm; mm &= mm - 1) {
     const unsigned int sj = __ffs(mm) - 1;
-    S.plist[k++] = (unsigned short)(lane | (sj << 5) | (((mI >> sj) & 1u) << 10) | (((mJ >> sj) & 1u) << 11));
+    S.plist[k++] = (unsigned short)(lane | (sj << 5));
   }
   __syncwarp();
   const unsigned int lt = (1u << lane) - 1u;
@@ -619,7 +679,7 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
       const unsigned int w = S.plist[e];
       li = (int)(w & 31u);
       sj = (int)((w >> 5) & 31u);
-      force_pair_terms(own_side(S, li), staged_side(S, sj), (w >> 10) & 1u, (w >> 11) & 1u, alpha, ci, cj, vs);
+      force_pair_terms(own_side(S, li), staged_side(S, sj), alpha, ci, cj, vs);
       if (COUNT) {
         // force partners of both particles (the pair set, checked per particle)
         atomicAdd(&fcnt[__float_as_int(S.ih[li].w)], 1u);
@@ -655,19 +715,37 @@ __device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, u
   }
 }
 
-__device__ __forceinline__ unsigned int upper_mask(int lane) {
-  return lane == 31 ? 0u : (0xffffffffu << (lane + 1));
+// Force batch: every pair with r < max(H_i, H_j) among the staged partners,
+// decided exactly (phase 1), then evaluated for both sides.
+template <bool COUNT>
+__device__ __forceinline__ void force_tile(ForceShared& S, unsigned int allow, unsigned int jvalid,
+                                           float bandJ, int n, bool own_only, unsigned int cmask,
+                                           const unsigned int* perm, const double* x, const BoxExact g,
+                                           float alpha, unsigned int* fcnt, Counters* C) {
+  // the lane's own particle, read back from the staged cluster
+  const float4 ip = S.ip[threadIdx.x & 31], ih = S.ih[threadIdx.x & 31];
+  const bool ivalid = ih.x >= 0.0f;
+  unsigned int mI, mJ, rc = 0;
+  pair_masks(make_float3(ip.x, ip.y, ip.z), ih.x, ih.y, __float_as_int(ih.w), ih.z, S, bandJ, allow, n, perm, x, g,
+             mI, mJ, rc);
+  const unsigned int m = mI | mJ;
+  if (COUNT) {
+    C->cand += ivalid ? __popc(allow & jvalid & cmask) : 0u;
+    C->rechecks += rc;
+    C->pairs += __popc(m & cmask);
+  }
+  force_rounds<COUNT>(S, m, own_only, alpha, fcnt);
 }
 
 // One batch of q <= 32 staged partners (slots 0..q-1) against the warp's
 // cluster: empty the slots past the batch and run both phases over the first
 // q rounded up to 4.  own_only: the partners are the warp's own cluster (each
 // lane excludes itself and updates its own side only).
-template <bool COUNT, bool PART, bool KAHAN>
+template <bool COUNT, bool PART, bool KAHAN, bool REC>
 __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsigned int q, bool own_only,
                                            DensAcc<KAHAN>& acc, unsigned int& cnt, const unsigned int* perm,
                                            const double* x, const ItemGeom& g, float4* dacc, unsigned int* dcnt,
-                                           Counters& C) {
+                                           Counters& C, const PairRec& R, RecW& W) {
   const int lane = threadIdx.x & 31;
   const bool v = (unsigned int)lane < q;
   __syncwarp();
@@ -678,7 +756,7 @@ __device__ __forceinline__ void dens_batch(const DensI& I, DensShared& S, unsign
   __syncwarp();
   const unsigned int allow = own_only ? jvalid & ~(1u << lane) : jvalid;
   dens_tile<COUNT, KAHAN>(I, S, allow, jvalid, jact, bandJ, (int)((q + 3u) & ~3u), own_only,
-                   own_only ? upper_mask(lane) : 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C);
+                   own_only ? upper_mask(lane) : 0xffffffffu, acc, cnt, perm, x, g, dacc, dcnt, C, REC && !PART, R, W);
   __syncwarp();
 }
 
@@ -702,6 +780,34 @@ __device__ __noinline__ void force_batch(ForceShared& S, unsigned int q, bool ow
   const unsigned int allow = own_only ? jvalid & upper_mask(lane) : jvalid;
   force_tile<COUNT>(S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only, 0xffffffffu, perm, x, g, alpha,
                     fcnt, C);
+  __syncwarp();
+  if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
+  __syncwarp();
+}
+
+// One recorded batch B of the first density pass: the staged partners are read
+// back by index (own_only: the warp's own cluster, already staged), the pairs come
+// from the recorded masks, and phase 2 runs as in force_batch.
+template <bool COUNT>
+__device__ __noinline__ void force_replay_batch(ForceShared& S, const unsigned int* __restrict__ B, bool own_only,
+                                                float3 sh, float invL, float L32, float eb,
+                                                const float4* __restrict__ pos4, const float4* __restrict__ cen4,
+                                                const float4* __restrict__ vel4, const float4* __restrict__ ghost4,
+                                                float alpha, float4* facc, float* fvsig, unsigned int* fcnt,
+                                                Counters* C) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int gj = __ldcs(B + lane);     // read once: evict first
+  const unsigned int m = __ldcs(B + 32 + lane);
+  const bool v = gj != REC_NONE;
+  __syncwarp();
+  if (!own_only) force_put(S, lane, load_force(v, gj, sh, pos4, cen4, vel4, ghost4, invL, L32, eb));
+  __syncwarp();
+  if (COUNT) {
+    const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
+    C->cand += S.ih[lane].x >= 0.0f ? __popc(jvalid & (own_only ? upper_mask(lane) : 0xffffffffu)) : 0u;
+    C->pairs += __popc(m);
+  }
+  force_rounds<COUNT>(S, m, own_only, alpha, fcnt);
   __syncwarp();
   if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
   __syncwarp();
@@ -899,14 +1005,15 @@ __device__ __forceinline__ unsigned int scan_clusters(const PairSetup& P, const 
 }
 
 // One pair task: cluster ti of cell A against the sorted clusters of cell B.
-template <bool COUNT, bool PART, bool KAHAN>
+template <bool COUNT, bool PART, bool KAHAN, bool REC>
 __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
     const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
     const unsigned int* __restrict__ perm, const double* __restrict__ x, float4* dacc, unsigned int* dcnt, DensShared& S,
-    Counters& C) {
+    Counters& C, const PairRec& R, RecW& W) {
   const int lane = threadIdx.x & 31;
   const PairSetup P = pair_setup(Lq, T, box, item);
+  if (REC) rec_task_begin(S, Lq.p_toff[item] + (ti - T.tile0[P.A]));
   const LeafFrame F = leaf_frame(TL, T, ti, P);
   const Box3 bi = tile_box3(TL, T, ti, P.tshA);          // the cluster in A's frame (the sorted sweep)
   const Box3 bil = tile_box3(TL, T, ti, F.sh_own);       // ... and in its leaf's frame (the particles)
@@ -957,26 +1064,28 @@ __device__ __forceinline__ void density_pair_task(int item, unsigned int ti, con
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+        dens_batch<COUNT, PART, KAHAN, REC>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C, R, W);
         q = 0;
       }
       if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C);
+  if (q) dens_batch<COUNT, PART, KAHAN, REC>(I, S, q, false, acc, cnt, perm, x, P.g, dacc, dcnt, C, R, W);
   flush_dens(I.g, acc.total(), cnt, dacc, dcnt);
+  if (REC) rec_task_end(R.ptask, S);
 }
 
 // One self task: cluster ti against itself and the later clusters of its cell.
-template <bool COUNT, bool PART, bool KAHAN>
+template <bool COUNT, bool PART, bool KAHAN, bool REC>
 __device__ __forceinline__ void density_self_task(int item, unsigned int ti, const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
     const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float* __restrict__ sort_r,
     const unsigned int* __restrict__ sort_i, const unsigned char* __restrict__ act,
     const unsigned int* __restrict__ perm, const double* __restrict__ x, float4* dacc, unsigned int* dcnt, DensShared& S,
-    Counters& C) {
+    Counters& C, const PairRec& R, RecW& W) {
   const int lane = threadIdx.x & 31;
   const int A = Lq.self_a[item];
+  if (REC) rec_task_begin(S, Lq.s_toff[item] + (ti - T.tile0[A]));
   const ItemGeom g = item_geom(T, box, A, 0);
   const float4 cA = T.cen[A];
   const float3 sh = make_float3(-cA.x, -cA.y, -cA.z);
@@ -993,7 +1102,7 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
   unsigned int cnt = 0, q = 0;
   // inside the cluster itself each unordered pair once: partners above the lane
   if (vi) dens_put(S, lane, I);
-  dens_batch<COUNT, PART, KAHAN>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C);
+  dens_batch<COUNT, PART, KAHAN, REC>(I, S, TL.n[ti], true, acc, cnt, perm, x, g, dacc, dcnt, C, R, W);
   // the later clusters of the cell, 32 box tests at a time
   for (unsigned int b0 = ti + 1; b0 < t0 + nt; b0 += 32) {
     const unsigned int tl = b0 + lane;
@@ -1016,15 +1125,16 @@ __device__ __forceinline__ void density_self_task(int item, unsigned int ti, con
       const unsigned int bal = __ballot_sync(0xffffffffu, pass);
       const unsigned int np = __popc(bal);
       if (q + np > 32u) {
-        dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+        dens_batch<COUNT, PART, KAHAN, REC>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C, R, W);
         q = 0;
       }
       if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
       q += np;
     }
   }
-  if (q) dens_batch<COUNT, PART, KAHAN>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C);
+  if (q) dens_batch<COUNT, PART, KAHAN, REC>(I, S, q, false, acc, cnt, perm, x, g, dacc, dcnt, C, R, W);
   flush_dens(I.g, acc.total(), cnt, dacc, dcnt);
+  if (REC) rec_task_end(R.stask, S);
 }
 
 template <bool COUNT>
@@ -1125,6 +1235,89 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
   flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
 }
 
+// Whether a task's records still hold when its partner cell (the own cell for a
+// self task) holds particles that took a new h after the recording: they do when
+// every such particle lies out of reach of the own cluster, reach taken with the
+// largest H the cell has had since the recording (cell H maxima only grow within
+// a step), so that no pair with them was recorded or is missing.
+__device__ __forceinline__ bool changed_out_of_reach(bool self, int item, unsigned int ti, const Lists& Lq,
+                                                  const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box) {
+  int C;
+  Box3 bi;
+  float reach;
+  float3 off;
+  if (self) {
+    C = Lq.self_a[item];
+    const ItemGeom g = item_geom(T, box, C, 0);
+    const float4 cA = T.cen[C];
+    bi = tile_box3(TL, T, ti, make_float3(-cA.x, -cA.y, -cA.z));
+    const float Hm = T.hmax[C] * g.invL;
+    reach = fmaxf(TL.lo[ti].w * g.invL, Hm) + g.e * 1.52587890625e-05f + g.es + 1e-6f * Hm;
+    off = make_float3(0.0f, 0.0f, 0.0f);
+  } else {
+    const PairSetup P = pair_setup(Lq, T, box, item);
+    C = P.B;
+    bi = tile_box3(TL, T, ti, P.tshA);
+    reach = fmaxf(TL.lo[ti].w * P.g.invL, P.HmB) + P.slack;
+    off = P.g.offB;
+  }
+  Box3 cb;
+  cb.lo = make_float3(key_float(T.clo[3 * C]) + off.x, key_float(T.clo[3 * C + 1]) + off.y,
+                      key_float(T.clo[3 * C + 2]) + off.z);
+  cb.hi = make_float3(key_float(T.chi[3 * C]) + off.x, key_float(T.chi[3 * C + 1]) + off.y,
+                      key_float(T.chi[3 * C + 2]) + off.z);
+  return !box_near(bi, cb, reach);
+}
+
+// A force task replayed from the records of the first density pass: the frames
+// of the particle arithmetic are those of force_pair_task / force_self_task, the
+// batches follow the recording warp's chain of chunks.  Valid while no particle of
+// the own cluster or of the partner cell (the own cell for a self task) has taken
+// a new h since the recording: the recorded pairs are then the pairs at the
+// current h.
+template <bool COUNT>
+__device__ __forceinline__ void force_replay_task(bool self, int item, unsigned int ti, uint2 rec, const PairRec& R,
+    const Lists& Lq, const Tree& T, const Tiles& TL, const BoxDesc* __restrict__ box,
+    const float4* __restrict__ pos4, const float4* __restrict__ cen4, const float4* __restrict__ vel4,
+    const float4* __restrict__ ghost4, float alpha, float4* facc, float* fvsig, unsigned int* fcnt, ForceShared& S,
+    Counters* C) {
+  const int lane = threadIdx.x & 31;
+  ItemGeom g;
+  float3 sh_own, sh_part;
+  if (self) {
+    const int A = Lq.self_a[item];
+    g = item_geom(T, box, A, 0);
+    const float4 cA = T.cen[A];
+    sh_own = make_float3(-cA.x, -cA.y, -cA.z);
+    sh_part = sh_own;
+  } else {
+    // as pair_setup and leaf_frame
+    const int A = Lq.pair_a[item], Bc = Lq.pair_b[item];
+    g = item_geom(T, box, A, Lq.pair_axis[item]);
+    const float4 cA = T.cen[A], cB = T.cen[Bc], cl = TL.cen[ti];
+    const float3 shB = make_float3(g.offB.x - cB.x, g.offB.y - cB.y, g.offB.z - cB.z);
+    const float3 d = make_float3(cl.x - cA.x, cl.y - cA.y, cl.z - cA.z);
+    sh_own = make_float3(-cl.x, -cl.y, -cl.z);
+    sh_part = make_float3(shB.x - d.x, shB.y - d.y, shB.z - d.z);
+  }
+  const bool vi = (unsigned int)lane < TL.n[ti];
+  const ForceI I = load_force(vi, TL.start[ti] + lane, sh_own, pos4, cen4, vel4, ghost4, g.invL, g.L32, g.eb);
+  force_stage_own(S, lane, I);
+  unsigned int b = rec.x;
+  for (unsigned int k = 0; k < rec.y; ++k, ++b) {
+    if (k > 0 && b % REC_CHUNK == 0u) b = R.next[b / REC_CHUNK - 1u] * REC_CHUNK;   // the chunk is full: next one
+    const bool own_only = self && k == 0;
+    if (own_only) {
+      __syncwarp();
+      if (vi) force_put(S, lane, I);
+    }
+    force_replay_batch<COUNT>(S, R.pool + 64ull * b, own_only, sh_part, g.invL, g.L32, g.eb, pos4, cen4, vel4,
+                              ghost4, alpha, facc, fvsig, fcnt, C);
+  }
+  __syncwarp();
+  flush_force(__float_as_int(S.ih[lane].w), S.iacc[lane], S.ivs[lane], facc, fvsig);
+}
+
 // Density interactions of one pass: the live pair and self tasks in one queue.
 // PART: a later pass of the h iteration (particles still iterating), where the own
 // side culls against the box of the cluster's iterating particles; the first pass
@@ -1132,8 +1325,8 @@ __device__ __forceinline__ void force_self_task(int item, unsigned int ti, const
 // a captured step, and the one that does not match the iteration returns.
 // The first pass (PART = false) keeps to 5 blocks of 128 threads per SM (at most
 // 102 registers): with fewer warps in flight it waits longer on partner loads.
-template <bool COUNT, bool PART, bool KAHAN>
-__global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : 5) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+template <bool COUNT, bool PART, bool KAHAN, bool REC>
+__global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : (REC ? REC_BLOCKS : 5)) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                          const float4* __restrict__ pos4,
                                                          const float4* __restrict__ cen4,
                                                          const float* __restrict__ sort_r,
@@ -1143,13 +1336,14 @@ __global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : 5) k_density(Lists Lq,
                                                          const double* __restrict__ x, float4* dacc,
                                                          unsigned int* dcnt, unsigned long long* pc,
                                                          unsigned int* __restrict__ task_ctr, int partial_host,
-                                                         const int* __restrict__ it_dev) {
+                                                         const int* __restrict__ it_dev, const __grid_constant__ PairRec Rec) {
   pdl_wait();
   const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
   if ((partial != 0) != PART) return;
   __shared__ DensShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   DensShared& S = SH[wl];
+  RecW W;
   Counters Cp, Cs;
   const unsigned int ntask = *Lq.n_live;
   // few tasks (the later passes of the h iteration): one task per fetch and no
@@ -1165,11 +1359,11 @@ __global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : 5) k_density(Lists Lq,
       const uint2 lt = Lq.p_live[t];
       const int item = (int)(lt.x & 0x7fffffffu);
       if (lt.x >> 31)
-        density_self_task<COUNT, PART, KAHAN>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
-                                       dcnt, S, Cs);
+        density_self_task<COUNT, PART, KAHAN, REC && !PART>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act,
+                                                       perm, x, dacc, dcnt, S, Cs, Rec, W);
       else
-        density_pair_task<COUNT, PART, KAHAN>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act, perm, x, dacc,
-                                       dcnt, S, Cp);
+        density_pair_task<COUNT, PART, KAHAN, REC && !PART>(item, lt.y, Lq, T, TL, box, pos4, cen4, sort_r, sort_i, act,
+                                                       perm, x, dacc, dcnt, S, Cp, Rec, W);
     }
     if (few && lane == 0) raw = atomicAdd(task_ctr, chunk);
   }
@@ -1192,7 +1386,8 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
                                                        const unsigned int* __restrict__ perm,
                                                        const double* __restrict__ x, float alpha, float4* facc,
                                                        float* fvsig, unsigned int* fcnt, unsigned long long* pc,
-                                                       unsigned int* __restrict__ task_ctr) {
+                                                       unsigned int* __restrict__ task_ctr,
+                                                       const __grid_constant__ PairRec R) {
   pdl_wait();
   __shared__ ForceShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -1211,7 +1406,20 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
     for (unsigned int t = base; t < tend; ++t) {
       const uint2 lt = Lq.p_live[t];
       const int item = (int)(lt.x & 0x7fffffffu);
-      if (lt.x >> 31)
+      const bool self = (lt.x >> 31) != 0u;
+      // the records of the first density pass, where they hold
+      uint2 rec = make_uint2(REC_NONE, 0u);
+      if (R.pool && !TL.changed[lt.y]) {
+        const int A = self ? Lq.self_a[item] : Lq.pair_a[item];
+        const int C = self ? A : Lq.pair_b[item];
+        if (!T.changed[C] || changed_out_of_reach(self, item, lt.y, Lq, T, TL, box))
+          rec = self ? R.stask[Lq.s_toff[item] + (lt.y - T.tile0[A])] : R.ptask[Lq.p_toff[item] + (lt.y - T.tile0[A])];
+      }
+      if (COUNT && lane == 0) atomicAdd(&pc[rec.x != REC_NONE ? 11 : 12], 1ull);
+      if (rec.x != REC_NONE)
+        force_replay_task<COUNT>(self, item, lt.y, rec, R, Lq, T, TL, box, pos4, cen4, vel4, ghost4, alpha, facc,
+                                 fvsig, fcnt, S, COUNT ? (self ? &Cs : &Cp) : nullptr);
+      else if (self)
         force_self_task<COUNT>(item, lt.y, Lq, T, TL, box, pos4, cen4, vel4, ghost4, sort_r, sort_i, perm, x, alpha,
                                facc, fvsig, fcnt, S, COUNT ? &Cs : nullptr);
       else
@@ -1416,9 +1624,11 @@ __global__ void k_mark_active(long long ntile, const unsigned int* __restrict__ 
     if (lane != 0) continue;
     if (hm > TL.lo[t].w) TL.lo[t].w = hm;
     TL.active[t] = 1;
+    TL.changed[t] = 1;
     const float4 lc = TL.cen[t];
     for (int id = (int)TL.leaf[t]; id >= 0; id = T.parent[id]) {
       T.active[id] = 1;
+      T.changed[id] = 1;
       const float4 cc = T.cen[id];
       const float ox = lc.x - cc.x, oy = lc.y - cc.y, oz = lc.z - cc.z;   // exact
       atomicMin(&T.alo[3 * id], float_key(lo.x + ox));
@@ -1427,6 +1637,12 @@ __global__ void k_mark_active(long long ntile, const unsigned int* __restrict__ 
       atomicMax(&T.ahi[3 * id], float_key(hi.x + ox));
       atomicMax(&T.ahi[3 * id + 1], float_key(hi.y + oy));
       atomicMax(&T.ahi[3 * id + 2], float_key(hi.z + oz));
+      atomicMin(&T.clo[3 * id], float_key(lo.x + ox));
+      atomicMin(&T.clo[3 * id + 1], float_key(lo.y + oy));
+      atomicMin(&T.clo[3 * id + 2], float_key(lo.z + oz));
+      atomicMax(&T.chi[3 * id], float_key(hi.x + ox));
+      atomicMax(&T.chi[3 * id + 1], float_key(hi.y + oy));
+      atomicMax(&T.chi[3 * id + 2], float_key(hi.z + oz));
     }
   }
 }
@@ -1538,8 +1754,14 @@ __global__ void k_iter_next(cudaGraphConditionalHandle iter, cudaGraphConditiona
   const bool more = !rebuild && na > 0 && *it_dev < max_iter;
   if (more) *it_dev += 1;
   *n_active = 0;
+  it_dev[3] = (!more && !rebuild) ? 1 : 0;     // for the conditions of later force phases
   cudaGraphSetConditional(iter, more ? 1u : 0u);
   cudaGraphSetConditional(force, (!more && !rebuild) ? 1u : 0u);
+}
+
+// a condition taken from a flag in device memory (a graph node of its own)
+__global__ void k_cond_set(cudaGraphConditionalHandle h, const int* __restrict__ flag) {
+  cudaGraphSetConditional(h, *flag != 0 ? 1u : 0u);
 }
 
 // the displacement of every box, written into its descriptor on the device
@@ -1823,16 +2045,22 @@ void launch_density(Engine& E, const int* it_dev, int only) {
     if (it_dev && only >= 0 && part != only) continue;
     // compensated sums when asked, or (compensated < 0) from 100 neighbours on
     const bool kahan = E.prm.compensated > 0 || (E.prm.compensated < 0 && E.prm.n_ngb >= 100.0f);
-    decltype(&k_density<false, false, false>) k;
+    // the first pass records its pairs for the force pass when the records are on
+    const bool rec = part == 0 && E.rec_valid;
+    decltype(&k_density<false, false, false, false>) k;
     if (kahan)
-      k = E.count_pairs ? (part ? k_density<true, true, true> : k_density<true, false, true>)
-                        : (part ? k_density<false, true, true> : k_density<false, false, true>);
+      k = E.count_pairs ? (part ? k_density<true, true, true, false>
+                                : (rec ? k_density<true, false, true, true> : k_density<true, false, true, false>))
+                        : (part ? k_density<false, true, true, false>
+                                : (rec ? k_density<false, false, true, true> : k_density<false, false, true, false>));
     else
-      k = E.count_pairs ? (part ? k_density<true, true, false> : k_density<true, false, false>)
-                        : (part ? k_density<false, true, false> : k_density<false, false, false>);
+      k = E.count_pairs ? (part ? k_density<true, true, false, false>
+                                : (rec ? k_density<true, false, false, true> : k_density<true, false, false, false>))
+                        : (part ? k_density<false, true, false, false>
+                                : (rec ? k_density<false, false, false, true> : k_density<false, false, false, false>));
     launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
         E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
-        E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev);
+        E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev, E.rec_for_force());
     count_launch();
   }
 }
@@ -1842,7 +2070,7 @@ void launch_force(Engine& E) {
   cudaMemsetAsync(E.task_ctr.p + 1, 0, sizeof(unsigned int), E.st);
   launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
       E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p, E.x.p,
-      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.fcnt.p, E.pc.p, E.task_ctr.p + 1);
+      E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.fcnt.p, E.pc.p, E.task_ctr.p + 1, E.rec_for_force());
   count_launch();
 }
 
@@ -1909,6 +2137,19 @@ void launch_reduce(Engine& E) {
   launch_pdl(k_reduce, dim3(gx, std::min(E.nbox, 65535)), 256, E.st, E.nbox, E.boff.p, E.box.p, E.perm.p, E.cen4.p,
              E.vel4.p, E.facc.p,
                                                                  E.red.p); count_launch();
+}
+
+cudaError_t add_cond_set_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                              cudaGraphConditionalHandle h, const int* flag) {
+  cudaKernelNodeParams kp = {};
+  void* args[2] = {&h, &flag};
+  kp.func = (void*)k_cond_set;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
 }
 
 void launch_cond_keep(Engine& E, cudaGraphConditionalHandle keep) {

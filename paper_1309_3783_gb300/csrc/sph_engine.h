@@ -168,7 +168,7 @@ class Engine {
   // clusters (capacity N)
   DBuf<unsigned int> tl_start, tl_n, tl_leaf;
   DBuf<float4> tl_lo, tl_hi, tl_cen;
-  DBuf<unsigned char> tl_active;
+  DBuf<unsigned char> tl_active, tl_changed;
   Tiles TL{};
   long long n_tiles = 0;
 
@@ -180,8 +180,8 @@ class Engine {
   DBuf<float> t_hmax;
   DBuf<double> t_hlim;
   DBuf<float4> t_cen;
-  DBuf<unsigned char> t_active;
-  DBuf<unsigned int> t_alo, t_ahi;
+  DBuf<unsigned char> t_active, t_changed;
+  DBuf<unsigned int> t_alo, t_ahi, t_clo, t_chi;
   DBuf<uint4> mid_seg;            // (cell, axis, storage offset, clusters) of every shared-memory sort
   DBuf<unsigned int> mid_count;
   DBuf<unsigned int> t_tile0, t_ntile;
@@ -196,6 +196,20 @@ class Engine {
   int partial_pass = 0;           // 1 while the density passes cover only particles still iterating h
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
   Lists Lq{};
+
+  // the pairs of the first density pass of an h iteration, kept for the force pass
+  // (params.pair_cache): pool of batches in chunks, chunk links, chunk counter,
+  // per-task records
+  DBuf<unsigned int> rec_pool, rec_next, rec_ctr;
+  DBuf<uint2> rec_pt, rec_st;
+  PairRec R{};
+  bool rec_valid = false;         // the records hold for the next force pass
+  long long rec_need = 0;         // chunks the last recordings took (the pool grows to this)
+  long long rec_used = 0;         // chunks the last recording read back took
+  bool rec_unread = false;        // the last recording's chunk count was not read back yet
+  sph_status rec_prepare();       // pool and record arrays sized for the next recording
+  void rec_enqueue_reset();       // a recording starts with the next full density pass
+  PairRec rec_for_force() const { return rec_valid ? R : PairRec{}; }
 
   // sorted projections
   DBuf<float> sort_r;

@@ -228,6 +228,9 @@ struct Tree {
   unsigned int* axes;       // bit a: a sorted list along axis a is needed
   unsigned int* sortbase;   // offset of the first sorted list of this cell
   unsigned char* active;    // 1 when a particle inside still iterates h
+  unsigned char* changed;   // 1 when a particle inside took a new h after the first density pass
+  unsigned int* clo;        // box of those particles, relative to the cell centre (units of L),
+  unsigned int* chi;        //   3 orderable float keys each
   unsigned int* alo;        // box of the particles still iterating h, relative to the
   unsigned int* ahi;        //   cell centre (units of L), 3 orderable float keys each
   unsigned int* tile0;      // first cluster of the cell (clusters of a cell are contiguous)
@@ -248,6 +251,24 @@ struct Tiles {
   float4* hi;               // box maximum relative to the leaf centre (units of L)
   float4* cen;              // the leaf's centre (as Tree::cen)
   unsigned char* active;    // 1 when a particle inside still iterates h
+  unsigned char* changed;   // 1 when a particle inside took a new h after the first density pass
+};
+
+// The interacting pairs of the first (full) density pass of an h iteration, kept
+// for the force pass: per batch of staged partners, the partners' particle
+// indices and, per particle of the warp's cluster, the mask of the partners it
+// interacts with (r < max(H_i, H_j), decided exactly).  A warp appends its batches
+// to chunks of REC_CHUNK batches that it takes from a counter and links; the
+// batches of one task are consecutive in that chain.
+constexpr unsigned int REC_CHUNK = 32;
+constexpr unsigned int REC_NONE = 0xffffffffu;
+struct PairRec {
+  unsigned int* pool;       // 64 words per batch: 32 partner indices (REC_NONE: empty slot), 32 masks
+  unsigned int* next;       // per chunk: the chunk its warp continued in
+  unsigned int* ctr;        // [0] chunks taken (may run past cap: those batches are not kept)
+  uint2* ptask;             // per pair task: (first batch, batches); x = REC_NONE: not recorded
+  uint2* stask;             // per self task
+  unsigned int cap;         // chunks in the pool
 };
 
 // Interaction lists.

@@ -36,7 +36,8 @@ class sph_params(C.Structure):
                 ("h_max_iter", C.c_int32), ("leaf_max", C.c_int32), ("split_frac", C.c_float),
                 ("max_depth", C.c_int32), ("split_headroom", C.c_float), ("reuse", C.c_int32),
                 ("sort_merge", C.c_int32), ("cluster_max", C.c_int32), ("compensated", C.c_int32),
-                ("precision", C.c_int32), ("graphs", C.c_int32)]
+                ("precision", C.c_int32), ("graphs", C.c_int32),
+                ("pair_cache", C.c_int32)]
 
 
 class sph_stats(C.Structure):
@@ -51,7 +52,8 @@ class sph_stats(C.Structure):
                 ("force_candidates_cellpair", C.c_int64), ("guard_rechecks", C.c_int64),
                 ("builds", C.c_int64), ("reuses", C.c_int64), ("h_active_after_first", C.c_int64),
                 ("leaf_max", C.c_int64), ("cluster_max", C.c_int64), ("graph_steps", C.c_int64),
-                ("host_steps", C.c_int64), ("host_syncs", C.c_int64)]
+                ("host_steps", C.c_int64), ("host_syncs", C.c_int64),
+                ("force_tasks_replayed", C.c_int64), ("force_tasks_culled", C.c_int64)]
 
 
 class sph_profile_entry(C.Structure):

@@ -505,3 +505,92 @@ def test_captured_rebuild_steps_equal_host_steps(api):
     assert stats[1]["host_syncs"] < stats[0]["host_syncs"]
     assert np.mean(out[1]["count"] != out[0]["count"]) < 1e-3
     _close_runs(out[1], out[0], box.L)
+
+
+def _force_state(api, box, state, pair_cache, h_update):
+    """One density (or h iteration) and force pass from `state`, pairs counted."""
+    c = _ctx_with(api, pair_cache=pair_cache)
+    try:
+        b = api.box_from(c, box)
+        try:
+            b.set(state["x"], state["v"], box.m, state["u"], state["h"])
+            if pair_cache:
+                b.density()         # a first recording sizes the pool for this box
+            b.count_pairs(True)
+            if h_update:
+                b.h_update()
+            else:
+                b.density()
+            b.force()
+            out = {k: b.get(k).astype(np.float64) for k in ("h", "rho", "a", "dudt", "vsig")}
+            out["force_count"] = b.get("force_count")
+            out["stats"] = b.stats()
+            return out
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("h_update", [False, True])
+def test_pair_cache_replays_the_full_force_pass(api, h_update):
+    """sph_params.pair_cache = 1 keeps the pairs of the first density pass and the
+    force pass replays them where no particle near a task took a new h since then.
+    From the same state the pair set (per particle) must equal the force pass that
+    culls on its own, and the forces agree to FP32 summation order.  With the h
+    iteration, particles that still iterate after the first pass make some tasks
+    cull again: both kinds of task run."""
+    box = inputs.clustered_box(n=60000, n_spheres=24, seed=5)
+    h = _force_state(api, box, {"x": box.x, "v": box.v, "u": box.u, "h": box.h}, 0, True)["h"]
+    if h_update:
+        # 2 % of the particles off their converged h: they iterate after the first pass
+        rng = np.random.default_rng(3)
+        k = rng.choice(box.n, box.n // 50, replace=False)
+        h[k] *= np.exp(rng.normal(0.0, 0.05, k.size))
+    state = {"x": box.x, "v": box.v, "u": box.u, "h": h.astype(np.float32)}
+    rep = _force_state(api, box, state, 1, h_update)
+    # the reference: the force pass that culls on its own, at the h the replayed
+    # run ended with
+    full = _force_state(api, box, dict(state, h=rep["h"].astype(np.float32)), 0, False)
+    s0, s1 = full["stats"], rep["stats"]
+    print(f"[pair cache] h_update={h_update}: replayed {s1['force_tasks_replayed']} culled {s1['force_tasks_culled']}, "
+          f"pairs {s1['force_pairs']}")
+    assert s0["force_tasks_replayed"] == 0 and s0["force_tasks_culled"] > 0
+    assert s1["force_tasks_replayed"] > 0
+    if h_update:
+        assert s1["force_tasks_culled"] > 0
+    else:
+        assert s1["force_tasks_culled"] == 0
+    assert s1["force_pairs"] == s0["force_pairs"]
+    np.testing.assert_array_equal(rep["force_count"], full["force_count"])
+    for k in ("a", "dudt"):
+        scale = np.sqrt(np.mean(full[k] ** 2))
+        assert np.max(np.abs(rep[k] - full[k])) <= 1e-4 * scale, k
+    np.testing.assert_allclose(rep["vsig"], full["vsig"], rtol=1e-5)
+
+
+def test_profiled_captured_steps_time_each_phase(api):
+    """With profiling on, a captured rebuild step records its phases with event
+    nodes (the force phases each in a conditional node of their own): the step
+    stays one graph launch and every phase reports a time."""
+    box = inputs.plummer_box(n=32768, n_spheres=4, seed=12)
+    c = _ctx_with(api, h_tol=5e-6)
+    try:
+        b = api.box_from(c, box)
+        try:
+            for _ in range(4):
+                b.step(2e-4)
+            b.profile(True)
+            s0 = b.stats()
+            for _ in range(4):
+                b.step(2e-4)
+            s1 = b.stats()
+            prof = b.get_profile()
+            b.profile(False)
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    assert s1["graph_steps"] - s0["graph_steps"] == 4
+    for ph in ("keys_sort", "tree", "density", "force", "reduce"):
+        assert prof[ph]["calls"] >= 4 and prof[ph]["ms"] > 0.0, ph

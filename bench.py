@@ -41,12 +41,18 @@ precision: the headline workload and the 262,144-particle box run again from the
 serving: the served batch -- 512 independent jittered-lattice boxes with
         particle counts log-uniform in [1k, 262k] (per-box seeds), each request
         advancing 10 kick-drift-kick steps -- through the continuous-batching
-        server.  A saturated run (every request submitted at once) measures the
-        capacity; a run with Poisson arrivals at 80 % of that capacity gives the
-        p50/p99 step latency (CUDA events around every batched step, one sample
-        per box and step), the request latency and the aggregate throughput.  The
-        same requests on a 1-in-8 subset also run one box at a time through the
-        plain single-box path for comparison with the batched server.
+        server, which admits boxes while a tick steps at most 2^19 particles
+        (sph_server_set_tick_budget).  A saturated run (every request submitted at
+        once) measures the capacity; a run with Poisson arrivals at 80 % of that
+        capacity gives the p50/p99 step latency (CUDA events around every batched
+        step, one sample per box and step), the request latency and the aggregate
+        throughput; the same arrivals again without the tick budget for
+        comparison.  Boxes admitted in a tick first go through a batched intake
+        pass (h iterated from the submitted h, starting forces; its device time
+        reported apart, p50/p99_intake_ms) and take their first step in the same
+        tick.  The same requests on a 1-in-8 subset also run one box at a
+        time through the plain single-box path for comparison with the batched
+        server.
 
 ``--workload clustered-4194304`` runs one octant of the headline recipe (the same
 densities in a box of half the edge), the case the counter captures use.
@@ -340,9 +346,11 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, f"cuda:{local_rank}")
     e2e = job_rate(world, n * e2e_steps, e2e_s)
 
-    # roofline of the dominant kernel (FP32 ALU bound); the FMA throughput measured beside it
+    # roofline of the dominant kernel (FP32 ALU bound), the force kernel: the largest
+    # single launch of a step (the density phase of a captured step spans the whole h
+    # iteration, several kernels); the FMA throughput measured beside it
     fp32_measured = sph.sph_measure_fp32_peak(ctx)
-    dom = max(("density", "force"), key=lambda k: prof[k]["ms"])
+    dom = "force"
     calls = max(prof[dom]["calls"], 1)
     avg_ms = prof[dom]["ms"] / calls
     flops = flops_step[dom] * args.steps / calls
@@ -536,6 +544,7 @@ def run_reuse_leg(sph, torch, b, box, dt, stream, args, flush):
 # ------------------------------------------------------------------ serving
 SERVE_STEPS = 10
 SERVE_LOAD = 0.8
+SERVE_TICK_BUDGET = 2 ** 19     # particles a tick may step: two of the largest served boxes
 
 
 def _served_requests(n_boxes):
@@ -547,10 +556,11 @@ def _served_requests(n_boxes):
     return out
 
 
-def _serve(sph, ctx, reqs, arrivals=None):
+def _serve(sph, ctx, reqs, arrivals=None, tick_budget=0):
     """Run requests through one server; returns (wall s, step ms list, request latencies s)."""
     srv = sph.sph_server_create(ctx, 0, 0)
     try:
+        sph.sph_server_set_tick_budget(srv, tick_budget)
         order = np.argsort(arrivals) if arrivals is not None else np.arange(len(reqs))
         ids, t_sub = {}, {}
         k = 0
@@ -571,11 +581,13 @@ def _serve(sph, ctx, reqs, arrivals=None):
             if active == 0 and k < len(reqs) and arrivals is not None:
                 time.sleep(max(0.0, min(0.002, arrivals[order[k]] - (time.perf_counter() - t0))))
         wall = time.perf_counter() - t0
-        step_ms = []
+        step_ms, intake_ms = [], []
         for r, rid in ids.items():
             step_ms.extend(sph.sph_server_poll(srv, rid, SERVE_STEPS)[1].tolist())
+            intake_ms.append(sph.sph_server_intake_ms(srv, rid))
             sph.sph_server_release(srv, rid)
         lat = [done_t[r] - t_sub[r] for r in ids]
+        _serve.intake_ms = intake_ms
         return wall, step_ms, lat
     finally:
         sph.sph_server_destroy(srv)
@@ -585,11 +597,15 @@ def run_serving(sph, ctx, n_boxes=512):
     reqs = _served_requests(n_boxes)
     work = sum(bx.n for bx, _ in reqs) * SERVE_STEPS
     mean_n = work / SERVE_STEPS / len(reqs)
-    wall_sat, _, _ = _serve(sph, ctx, reqs)                 # saturated: every request at once
+    # saturated: every request at once, the ticks as large as the budget allows
+    wall_sat, _, _ = _serve(sph, ctx, reqs, tick_budget=SERVE_TICK_BUDGET)
     capacity = work / wall_sat
     rate = SERVE_LOAD * capacity / (mean_n * SERVE_STEPS)  # requests per second
     arrivals = inputs.poisson_arrivals(len(reqs), rate, seed=1)
-    wall, step_ms, lat = _serve(sph, ctx, reqs, arrivals)
+    wall, step_ms, lat = _serve(sph, ctx, reqs, arrivals, tick_budget=SERVE_TICK_BUDGET)
+    intake = [v for v in _serve.intake_ms if v >= 0.0]
+    # the same arrivals without the tick budget: every waiting box admitted at once
+    _, step_ms_nb, lat_nb = _serve(sph, ctx, reqs, arrivals)
     # the same requests on a 1-in-8 subset: batched server against one box at a time
     sub = reqs[::8]
     sub_work = sum(bx.n for bx, _ in sub) * SERVE_STEPS
@@ -608,8 +624,13 @@ def run_serving(sph, ctx, n_boxes=512):
     return {
         "workload": f"{len(reqs)} jittered-lattice boxes, 1k-262k particles (mean {mean_n:.0f}), "
                     f"{SERVE_STEPS} kick-drift-kick steps each, Poisson arrivals at {SERVE_LOAD:.0%} of capacity",
+        "tick_budget_particles": SERVE_TICK_BUDGET,
         "p50_step_ms": pct(step_ms, 50), "p99_step_ms": pct(step_ms, 99),
+        "p99_over_p50": pct(step_ms, 99) / pct(step_ms, 50),
         "p50_request_s": pct(lat, 50), "p99_request_s": pct(lat, 99),
+        "p50_intake_ms": pct(intake, 50), "p99_intake_ms": pct(intake, 99),
+        "without_tick_budget": {"p50_step_ms": pct(step_ms_nb, 50), "p99_step_ms": pct(step_ms_nb, 99),
+                                "p50_request_s": pct(lat_nb, 50), "p99_request_s": pct(lat_nb, 99)},
         "throughput": work / wall, "unit": UNIT, "capacity": capacity, "arrival_rate_per_s": rate,
         "step_samples": len(step_ms),
         "batched_vs_single_box": {"boxes": len(sub), "batched": sub_work / wall_b, "single_box": sub_work / wall_1,

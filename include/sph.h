@@ -412,14 +412,28 @@ sph_status sph_server_submit(sph_server* s, int64_t n, double box_len, int perio
                              const double* x, const float* v, const float* m, const float* u,
                              const float* h, int32_t n_steps, double dt, int64_t* id);
 
-/* Run one tick: admit waiting boxes that fit, advance every admitted box by
- * one step in one batched pipeline, retire finished boxes.  *n_active
- * receives the number of boxes advanced (0 when idle). */
+/* Bound the work of one tick: boxes are admitted only while the resident
+ * particles stay within max_particles (a box larger than that is admitted
+ * when nothing else is resident), so that the time of a batched step stays
+ * bounded while bursts of requests wait in the queue.  0 (the default): no
+ * bound beyond the memory budget.  Errors: SPH_E_INVALID (max_particles < 0). */
+sph_status sph_server_set_tick_budget(sph_server* s, int64_t max_particles);
+
+/* Run one tick: admit waiting boxes that fit (their intake pass: h iterated
+ * from the submitted h, starting forces), advance every admitted box by one
+ * step in one batched pipeline, retire finished boxes.  *n_active receives the
+ * number of boxes advanced (0 when idle). */
 sph_status sph_server_tick(sph_server* s, int32_t* n_active);
 
 /* State of request id: *done = 1 when all its steps ran.  step_ms (may be
  * NULL, capacity max_steps) receives the device time of each of its steps. */
 sph_status sph_server_poll(sph_server* s, int64_t id, int32_t* done, float* step_ms, int32_t max_steps);
+
+/* Device time of the intake pass request id went through in its admission
+ * tick (its h iteration from the initial h and its starting forces, batched
+ * with the other boxes admitted in that tick); -1 when it had none (waiting,
+ * or a request of n_steps = 0, which runs as passes of the batched step). */
+sph_status sph_server_intake_ms(sph_server* s, int64_t id, float* ms);
 
 /* Copy a field of a finished request (as sph_get, host memory). */
 sph_status sph_server_get(sph_server* s, int64_t id, int field, void* dst, int64_t n);

@@ -4,13 +4,16 @@
 // tree, interaction lists, axis sorts and the density/force kernels all run over
 // the concatenated boxes; interactions never cross boxes).
 //
-// Admission is by device footprint against a byte budget and by a box count
-// limit; waiting requests are admitted in submission order as finished boxes
-// retire (continuous batching).  A box's first tick computes its starting
-// forces; each further tick is one kick-drift-kick step of its own dt.  When
-// the resident set changes, the boxes that stay keep their state on the device:
-// the engine moves it to the new layout with one kernel, and only the new
-// boxes are copied in from the host.
+// Admission is by device footprint against a byte budget, by a box count limit
+// and by a bound on the particles one tick steps; waiting requests are admitted
+// in submission order as finished boxes retire (continuous batching).  The boxes
+// admitted in a tick first go through an intake pass on an engine of their own:
+// the h iteration from their initial h and their starting forces, all new boxes
+// batched.  They then join the resident boxes, moved device to device, and take
+// their first kick-drift-kick step in the same tick, so that the batched step
+// never carries the longer start-up iteration of a new box.  When the resident
+// set changes, the boxes that stay keep their state on the device: the engine
+// moves it to the new layout with one kernel.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,6 +40,8 @@ struct Request {
   bool started = false;
   int state = 0;            // 0 waiting, 1 resident, 2 finished
   std::vector<float> step_ms;
+  float intake_ms = -1.0f;  // device time of the intake pass it went through (-1: none)
+  int intake_box = -1;      // its box in the intake engine during its admission tick
   std::vector<std::vector<unsigned char>> result;   // per field, caller order
 };
 
@@ -56,14 +61,16 @@ struct sph_server {
   int device = 0;
   cudaStream_t st = nullptr;
   sph::Engine* eng = nullptr;
+  sph::Engine* intake = nullptr;   // start-up passes of the boxes admitted in a tick
   long long budget = 0;
+  long long tick_budget = 0;       // particles a tick may step (0: no bound)
   int max_boxes = 0;
   long long next_id = 1;
   std::map<long long, Request> reqs;
   std::deque<long long> waiting;
   std::vector<long long> resident;
   std::vector<long long> layout;   // the boxes in the engine, in its order
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, i0 = nullptr, i1 = nullptr;
   unsigned char* pin = nullptr;    // page-locked staging for the results of finished boxes
   size_t pin_cap = 0;
   std::string err;
@@ -95,6 +102,16 @@ static sph_status apply_layout(sph_server* s) {
   for (size_t b = 0; b < s->resident.size(); ++b) {
     if (src[b] >= 0) continue;
     Request& r = s->reqs[s->resident[b]];
+    if (r.intake_box >= 0) {
+      // from the intake engine: converged h and starting forces, device to device
+      sph::Engine& I = *s->intake;
+      const long long o = I.off[r.intake_box];
+      st = E.set_particles((int)b, I.x.p + 3 * o, I.v.p + 3 * o, I.m.p + o, I.u.p + o, I.h.p + o, SPH_MEM_DEVICE);
+      if (st != SPH_OK) return srv_fail(s, st, E.err);
+      cudaMemcpyAsync(E.a_in.p + E.off[b], I.a_in.p + o, r.n * sizeof(float4), cudaMemcpyDeviceToDevice, s->st);
+      r.intake_box = -1;
+      continue;
+    }
     st = E.set_particles((int)b, r.x.data(), r.v.data(), r.m.data(), r.u.data(), r.h.data(), SPH_MEM_HOST);
     if (st != SPH_OK) return srv_fail(s, st, E.err);
     cudaMemsetAsync(E.a_in.p + E.off[b], 0, r.n * sizeof(float4), s->st);
@@ -103,6 +120,47 @@ static sph_status apply_layout(sph_server* s) {
   // every box reads a_in, so the engine never recomputes forces on its own
   E.have_acc = true;
   s->layout = s->resident;
+  return SPH_OK;
+}
+
+// The intake pass of the boxes admitted in this tick (requests with steps to
+// run): one engine over all of them, built, h iterated from their initial h,
+// forces computed; the boxes then join the resident layout from its buffers.
+static sph_status run_intake(sph_server* s, const std::vector<long long>& ids) {
+  if (ids.empty()) return SPH_OK;
+  if (!s->intake) s->intake = new sph::Engine(s->ctx->prm, s->device, s->st);
+  sph::Engine& I = *s->intake;
+  I.st = s->st;
+  std::vector<sph::BoxSpec> spec;
+  for (long long id : ids) {
+    const Request& r = s->reqs[id];
+    spec.push_back(sph::BoxSpec{r.L, r.n, r.periodic});
+  }
+  sph_status st = I.set_boxes(spec);
+  if (st != SPH_OK) return srv_fail(s, st, I.err);
+  for (size_t k = 0; k < ids.size(); ++k) {
+    Request& r = s->reqs[ids[k]];
+    st = I.set_particles((int)k, r.x.data(), r.v.data(), r.m.data(), r.u.data(), r.h.data(), SPH_MEM_HOST);
+    if (st != SPH_OK) return srv_fail(s, st, I.err);
+  }
+  cudaEventRecord(s->i0, s->st);
+  st = I.build();
+  if (st == SPH_OK) {
+    st = I.h_update(nullptr, nullptr);
+    if (st == SPH_E_NOT_CONVERGED) st = SPH_OK;
+  }
+  if (st == SPH_OK) st = I.force();
+  cudaEventRecord(s->i1, s->st);
+  if (st != SPH_OK) return srv_fail(s, st, I.err);
+  cudaEventSynchronize(s->i1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, s->i0, s->i1);
+  for (size_t k = 0; k < ids.size(); ++k) {
+    Request& r = s->reqs[ids[k]];
+    r.intake_box = (int)k;
+    r.intake_ms = ms;
+    r.started = true;       // its first step runs in this tick
+  }
   return SPH_OK;
 }
 
@@ -202,6 +260,8 @@ sph_status sph_server_create(sph_ctx* ctx, int64_t budget_bytes, int32_t max_box
   s->eng = new sph::Engine(cv->prm, cv->device, s->st);
   cudaEventCreate(&s->e0);
   cudaEventCreate(&s->e1);
+  cudaEventCreate(&s->i0);
+  cudaEventCreate(&s->i1);
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->live++;
@@ -233,27 +293,46 @@ sph_status sph_server_submit(sph_server* s, int64_t n, double L, int periodic, c
   return SPH_OK;
 }
 
+sph_status sph_server_set_tick_budget(sph_server* s, int64_t max_particles) {
+  if (!s || max_particles < 0) return SPH_E_INVALID;
+  s->tick_budget = max_particles;
+  return SPH_OK;
+}
+
 sph_status sph_server_tick(sph_server* s, int32_t* n_active) {
   if (!s) return SPH_E_INVALID;
   cudaSetDevice(s->device);
   s->st = s->ctx->cur;
   s->eng->st = s->st;
+  if (s->intake) s->intake->st = s->st;
   if (n_active) *n_active = 0;
-  // admission in submission order while the footprint fits
-  long long used = 0;
-  for (long long id : s->resident) used += s->reqs[id].n * kBytesPerParticle;
+  // admission in submission order while the footprint fits (and the particles
+  // stay within the tick budget)
+  long long used = 0, parts = 0;
+  std::vector<long long> admitted;   // admitted in this tick, with steps to run
+  for (long long id : s->resident) {
+    used += s->reqs[id].n * kBytesPerParticle;
+    parts += s->reqs[id].n;
+  }
 
   while (!s->waiting.empty() && (int)s->resident.size() < s->max_boxes) {
     Request& r = s->reqs[s->waiting.front()];
     if (used + r.n * kBytesPerParticle > s->budget) break;
+    if (s->tick_budget > 0 && parts + r.n > s->tick_budget && !s->resident.empty()) break;
 
     used += r.n * kBytesPerParticle;
+    parts += r.n;
     r.state = 1;
     s->resident.push_back(r.id);
+    if (r.n_steps > 0) admitted.push_back(r.id);
     s->waiting.pop_front();
   }
 
   if (s->resident.empty()) return SPH_OK;
+  {
+    const sph_status is = run_intake(s, admitted);
+    if (is != SPH_OK) return is;
+  }
   if (s->resident != s->layout) {
     sph_status st = apply_layout(s);
     if (st != SPH_OK) return st;
@@ -310,6 +389,14 @@ sph_status sph_server_poll(sph_server* s, int64_t id, int32_t* done, float* step
   return SPH_OK;
 }
 
+sph_status sph_server_intake_ms(sph_server* s, int64_t id, float* ms) {
+  if (!s || !ms) return SPH_E_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return srv_fail(s, SPH_E_INVALID, "unknown request");
+  *ms = it->second.intake_ms;
+  return SPH_OK;
+}
+
 sph_status sph_server_get(sph_server* s, int64_t id, int field, void* dst, int64_t n) {
   if (!s || !dst) return SPH_E_INVALID;
   auto it = s->reqs.find(id);
@@ -344,8 +431,11 @@ sph_status sph_server_destroy(sph_server* s) {
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->st);
   delete s->eng;
+  delete s->intake;
   cudaEventDestroy(s->e0);
   cudaEventDestroy(s->e1);
+  cudaEventDestroy(s->i0);
+  cudaEventDestroy(s->i1);
   if (s->pin) cudaFreeHost(s->pin);
   {
     std::lock_guard<std::mutex> g(s->ctx->mu);

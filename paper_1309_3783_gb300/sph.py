@@ -103,6 +103,8 @@ _SIGS = {
     "sph_server_submit": (C.c_int, [_P, C.c_int64, C.c_double, C.c_int, _P, _P, _P, _P, _P, C.c_int32,
                                     C.c_double, C.POINTER(C.c_int64)]),
     "sph_server_tick": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "sph_server_set_tick_budget": (C.c_int, [_P, C.c_int64]),
+    "sph_server_intake_ms": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_float)]),
     "sph_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int32), _P, C.c_int32]),
     "sph_server_get": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int64]),
     "sph_server_release": (C.c_int, [_P, C.c_int64]),
@@ -370,6 +372,20 @@ def sph_server_submit(srv, x, v, m, u, h, box_len: float, periodic: bool, n_step
     if st != SPH_OK:
         raise SphError(st, "sph_server_submit failed")
     return rid.value
+
+
+def sph_server_set_tick_budget(srv, max_particles: int) -> None:
+    st = load().sph_server_set_tick_budget(srv, int(max_particles))
+    if st != SPH_OK:
+        raise SphError(st, "sph_server_set_tick_budget failed")
+
+
+def sph_server_intake_ms(srv, rid: int) -> float:
+    ms = C.c_float(0.0)
+    st = load().sph_server_intake_ms(srv, int(rid), C.byref(ms))
+    if st != SPH_OK:
+        raise SphError(st, "sph_server_intake_ms failed")
+    return float(ms.value)
 
 
 def sph_server_tick(srv) -> int:

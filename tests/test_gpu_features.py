@@ -76,8 +76,9 @@ def test_server_results_alone_and_in_the_mix(api):
             api.sph_server_tick(srv)
             ticks += 1
             assert ticks < 100
-        # two boxes at a time, each needing a start tick plus n_steps ticks
-        assert ticks >= 2 * (n_steps + 1)
+        # two boxes at a time, each taking n_steps ticks (its intake pass runs in
+        # its admission tick, which also takes its first step)
+        assert ticks == 2 * n_steps
         for bx, i, ref in zip(boxes, ids, alone):
             _, ms = api.sph_server_poll(srv, i, n_steps)
             assert np.all(ms > 0)
@@ -109,6 +110,31 @@ def test_server_admission_by_memory_budget(api, ctx):
         big = inputs.lattice_box(16, jitter=0.2, seed=4)
         with pytest.raises(api.SphError):                    # can never fit
             api.sph_server_submit(srv, big.x, big.v, big.m, big.u, big.h, 1.0, True, 1, 0.0)
+    finally:
+        api.sph_server_destroy(srv)
+
+
+def test_server_tick_budget_bounds_the_particles_of_a_tick(api, ctx):
+    """With a tick budget of 1.5 boxes, one box is resident at a time; a box larger
+    than the budget is still admitted when nothing else is resident."""
+    small = inputs.lattice_box(10, jitter=0.2, seed=3)
+    srv = api.sph_server_create(ctx, 0, 0)
+    try:
+        api.sph_server_set_tick_budget(srv, small.n + small.n // 2)
+        ids = [api.sph_server_submit(srv, small.x, small.v, small.m, small.u, small.h, 1.0, True, 2, 1e-4)
+               for _ in range(3)]
+        active = []
+        while not all(api.sph_server_poll(srv, i)[0] for i in ids):
+            active.append(api.sph_server_tick(srv))
+        assert max(active) == 1 and len(active) == 6       # two steps per box (intake in the first)
+        assert all(api.sph_server_intake_ms(srv, i) > 0.0 for i in ids)
+        api.sph_server_set_tick_budget(srv, small.n // 2)  # smaller than one box
+        k = api.sph_server_submit(srv, small.x, small.v, small.m, small.u, small.h, 1.0, True, 1, 0.0)
+        assert api.sph_server_tick(srv) == 1
+        while not api.sph_server_poll(srv, k)[0]:
+            api.sph_server_tick(srv)
+        with pytest.raises(api.SphError):
+            api.sph_server_set_tick_budget(srv, -1)
     finally:
         api.sph_server_destroy(srv)
 

@@ -129,6 +129,10 @@ SAMPLE_K = 4096             # the oracle's bounded sample per step: particles ne
 #            2, two kernel derivatives 10, v.x 8, w 1, min 1, v_sig 3, Pi 4,
 #            W-bar 2, coefficient 6, half-viscosity 2, both sides' a, du/dt and
 #            v_sig 26).
+# bytes a force pass must move per particle: its position/offset, cell offset and
+# mass, velocity and u, ghost quantities (4 x 16 B read), its a, du/dt and v_sig
+# (20 B written)
+FORCE_BYTES_PER_PARTICLE = 84
 FLOPS_DENSITY_PAIR = 11
 FLOPS_DENSITY_SIDE = 16
 FLOPS_FORCE_PAIR = 75
@@ -383,6 +387,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                     "algorithmic_bytes": n * FORCE_BYTES_PER_PARTICLE,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (nominal max clock)",
                      "peak_measured": fp32_measured,
                      "frac_of_measured": achieved / fp32_measured if fp32_measured else None,

@@ -17,6 +17,11 @@ __global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box,
                          const float* __restrict__ h, float gamma_k, float* __restrict__ H_out) {
   pdl_wait();
   const long long stride = (long long)gridDim.x * blockDim.x;
+  // a warp whose lanes all hold particles of one box keeps that box's extremes
+  // across its iterations and adds them once (the same address from every warp
+  // of a large box would serialise the atomics)
+  int rb = -1;
+  unsigned int rmx = 0u, rmn = 0xffffffffu;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     const long long p = base + threadIdx.x;   // every lane of a warp runs every iteration
     const bool valid = p < N;
@@ -44,10 +49,26 @@ __global__ void k_ingest(long long N, const int* __restrict__ bid, BoxDesc* box,
     const unsigned int hb = ok ? __float_as_uint(H) : 0u;
     const unsigned int mx = __reduce_max_sync(same, hb);
     const unsigned int mn = __reduce_min_sync(same, ok ? hb : 0xffffffffu);
-    if (valid && (threadIdx.x & 31) == __ffs(same) - 1) {
+    if (same == 0xffffffffu && b >= 0) {      // the same in every lane
+      if (b != rb) {
+        if (rb >= 0 && (threadIdx.x & 31) == 0) {
+          if (rmx) atomicMax(reinterpret_cast<unsigned int*>(&box[rb].Hmax), rmx);
+          if (rmn != 0xffffffffu) atomicMin(reinterpret_cast<unsigned int*>(&box[rb].Hmin), rmn);
+        }
+        rb = b;
+        rmx = 0u;
+        rmn = 0xffffffffu;
+      }
+      rmx = max(rmx, mx);
+      rmn = min(rmn, mn);
+    } else if (valid && (threadIdx.x & 31) == __ffs(same) - 1) {
       if (mx) atomicMax(reinterpret_cast<unsigned int*>(&box[b].Hmax), mx);
       if (mn != 0xffffffffu) atomicMin(reinterpret_cast<unsigned int*>(&box[b].Hmin), mn);
     }
+  }
+  if (rb >= 0 && (threadIdx.x & 31) == 0) {
+    if (rmx) atomicMax(reinterpret_cast<unsigned int*>(&box[rb].Hmax), rmx);
+    if (rmn != 0xffffffffu) atomicMin(reinterpret_cast<unsigned int*>(&box[rb].Hmin), rmn);
   }
 }
 
@@ -179,6 +200,10 @@ __global__ void k_displacement(long long N, const int* __restrict__ bid, const B
                                unsigned long long* __restrict__ dmax) {
   pdl_wait();
   const long long stride = (long long)gridDim.x * blockDim.x;
+  // a warp whose lanes all hold particles of one box keeps that box's largest
+  // displacement across its iterations and adds it once (see k_ingest)
+  int rb = -1;
+  unsigned long long rbits = 0ull;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     const long long p = base + threadIdx.x;   // every lane of a warp runs every iteration
     const bool valid = p < N;
@@ -205,11 +230,21 @@ __global__ void k_displacement(long long N, const int* __restrict__ bid, const B
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, bits, o);
         bits = y > bits ? y : bits;
       }
-      if ((threadIdx.x & 31) == 0 && b0 >= 0) atomicMax(&dmax[b0], bits);
+      if (b0 >= 0 && __all_sync(0xffffffffu, valid)) {
+        if (b0 != rb) {
+          if (rb >= 0 && (threadIdx.x & 31) == 0) atomicMax(&dmax[rb], rbits);
+          rb = b0;
+          rbits = 0ull;
+        }
+        rbits = bits > rbits ? bits : rbits;
+      } else if ((threadIdx.x & 31) == 0 && b0 >= 0) {
+        atomicMax(&dmax[b0], bits);
+      }
     } else if (valid) {
       atomicMax(&dmax[b], bits);
     }
   }
+  if (rb >= 0 && (threadIdx.x & 31) == 0) atomicMax(&dmax[rb], rbits);
 }
 
 // The limit every particle's H must stay below with the decomposition kept:

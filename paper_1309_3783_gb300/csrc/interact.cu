@@ -1555,7 +1555,11 @@ __global__ void k_ghost(long long N, int mode, int it_host, const int* __restric
           atomic_max_pos(&T.hmax[id], Hn);
         }
       }
-      atomicAdd(n_active, 1);
+      {
+        // one atomic for the lanes here (every particle of a first pass may iterate)
+        const unsigned int am = __activemask();
+        if ((threadIdx.x & 31) == __ffs(am) - 1) atomicAdd(n_active, __popc(am));
+      }
       continue;
     }
     act[p] = 0;

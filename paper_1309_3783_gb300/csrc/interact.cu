@@ -396,25 +396,30 @@ __device__ __forceinline__ void pair_masks(const float3 ip, float iH2, float iba
                                            const SH& S, float bandJ, unsigned int allow, int n,
                                            const unsigned int* perm, const double* x, const BoxExact g,
                                            unsigned int& mI, unsigned int& mJ, unsigned int& rc) {
-  // u: slots where either decision falls inside its guard band; both are then
-  // taken again in FP64 (the exact decision equals the FP32 one where that was sure)
-  unsigned int u = 0;
+  // Per slot, r^2 against H^2 - band (sure inside) and H^2 + band (sure outside),
+  // for both radii: each test is the sign of one difference, shifted into its mask
+  // (slots taken from the last, so that slot s lands in bit s).  u: slots where
+  // either decision is not sure; both are then taken again in FP64 (the exact
+  // decision equals the FP32 one where that was sure).
+  const float iLo = iH2 - iband, iHi = iH2 + iband;
+  unsigned int sure = 0;   // slots where both decisions are sure
   mI = 0;
   mJ = 0;
-  for (int s0 = 0; s0 < n; s0 += 4) {
+  for (int s0 = n - 4; s0 >= 0; s0 -= 4) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 3; k >= 0; --k) {
       const int s = s0 + k;
       const float4 J = S.p[s];
       const float dx = ip.x - J.x, dy = ip.y - J.y, dz = ip.z - J.z;
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      const float di = r2 - iH2, dj = r2 - J.w;
-      mI |= (di < -iband ? 1u : 0u) << s;
-      mJ |= (dj < -bandJ ? 1u : 0u) << s;
-      u |= ((fabsf(di) <= iband) | (fabsf(dj) <= bandJ) ? 1u : 0u) << s;
+      const unsigned int ai = __float_as_uint(r2 - iLo), bi = __float_as_uint(iHi - r2);   // sign: in / out
+      const unsigned int aj = __float_as_uint(r2 - (J.w - bandJ)), bj = __float_as_uint((J.w + bandJ) - r2);
+      mI = __funnelshift_l(ai, mI, 1);
+      mJ = __funnelshift_l(aj, mJ, 1);
+      sure = __funnelshift_l((ai | bi) & (aj | bj), sure, 1);
     }
   }
-  u &= allow;
+  unsigned int u = ~sure & allow;
   while (u) {
     const int s = __ffs(u) - 1;
     u &= u - 1;

@@ -335,14 +335,18 @@ __device__ __forceinline__ ForceI load_force(bool valid, unsigned int gidx, floa
 }
 
 // Per warp: the staged partners (p, a, v, f, g) and the warp's own cluster
-// (ip, iv, if_).
+// (ip, iv, if_).  The pair list holds 768 of a batch's up to 1024 pairs, so that
+// 8 blocks of 4 warps fit an SM's shared memory (the register cap's occupancy; with
+// a full list shared memory held the kernel at 7 blocks, 3.5 % slower on the 33.5M
+// box); a batch with more pairs runs as two halves of the own lanes.
+constexpr int PLIST_CAP = 768;
 struct ForceShared {
   float4 p[32];    // partner position, H^2
   float4 a[32];    // partner 1/H, band, m, H (physical)
   float4 v[32];    // partner velocity, rho
   float4 f[32];    // partner f P / rho^2, c, K/H^4, -
-  float4 jacc[32]; // partner sums of the batch: acceleration (3), du/dt
-  float jvs[32];   //   and the largest signal velocity
+  float4 jacc[32]; // partner sums of the batch: acceleration (3), du/dt (their largest
+                   //   signal velocity in f[].w)
   int g[32];
   float4 ip[32];   // own cluster: position, m
   float4 iv[32];   // own cluster: velocity, rho
@@ -350,16 +354,15 @@ struct ForceShared {
   float4 ih[32];   // own cluster: H^2 (-1: no particle), band, H (physical), index (bits)
   float4 iacc[32]; // own cluster sums over the task
   float ivs[32];
-  unsigned short plist[32 * 32];   // the batch's pairs: own lane | slot << 5 | [r<H_i] << 10 | [r<H_j] << 11
+  unsigned short plist[PLIST_CAP]; // the batch's pairs: own lane | slot << 5
 };
 
 __device__ __forceinline__ void force_put(ForceShared& S, int lane, const ForceI& j) {
   S.p[lane] = make_float4(j.p.x, j.p.y, j.p.z, j.H2);
   S.a[lane] = make_float4(j.invH, j.band, j.m, j.Hphys);
   S.v[lane] = make_float4(j.v.x, j.v.y, j.v.z, j.rho);
-  S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);
+  S.f[lane] = make_float4(j.F, j.c, j.K4, 0.f);   // w: the partner's largest v_sig of the batch
   S.jacc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-  S.jvs[lane] = 0.f;
   S.g[lane] = j.g;
 }
 
@@ -661,10 +664,16 @@ __device__ __forceinline__ ForceSide own_side(const ForceShared& S, int k) {
 // adjacent in the list) into its task sums; the partner side goes to the
 // partner's batch sums (or, inside one cluster, to that particle's task sums).
 template <bool COUNT>
+__device__ __forceinline__ void force_rounds_list(ForceShared& S, unsigned int m, bool own_only, float alpha,
+                                                  unsigned int* fcnt, unsigned int cnt, unsigned int incl,
+                                                  unsigned int total);
+
+template <bool COUNT>
 __device__ __forceinline__ void force_rounds(ForceShared& S, unsigned int m, bool own_only, float alpha,
                                              unsigned int* fcnt) {
   const int lane = threadIdx.x & 31;
-  // list the pairs, own lane major
+  // list the pairs, own lane major (in two halves of the own lanes when they do
+  // not fit the list: at most 16 x 32 pairs each)
   const unsigned int cnt = __popc(m);
   unsigned int incl = cnt;
 #pragma unroll
@@ -673,6 +682,32 @@ __device__ __forceinline__ void force_rounds(ForceShared& S, unsigned int m, boo
     if (lane >= o) incl += y;
   }
   const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+  const bool split = total > (unsigned int)PLIST_CAP;
+  for (int half = 0; half < (split ? 2 : 1); ++half) {
+    unsigned int mh = m, ch = cnt, ih = incl, th = total;
+    if (split) {
+      mh = (lane >> 4) == half ? m : 0u;
+      ch = __popc(mh);
+      ih = ch;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, ih, o);
+        if (lane >= o) ih += y;
+      }
+      th = __shfl_sync(0xffffffffu, ih, 31);
+    }
+    force_rounds_list<COUNT>(S, mh, own_only, alpha, fcnt, ch, ih, th);
+  }
+}
+
+// The rounds over one list: cnt pairs of the lane (mask m), incl their inclusive
+// prefix over the lanes, total all of them (<= PLIST_CAP).
+template <bool COUNT>
+__device__ __forceinline__ void force_rounds_list(ForceShared& S, unsigned int m, bool own_only, float alpha,
+                                                  unsigned int* fcnt, unsigned int cnt, unsigned int incl,
+                                                  unsigned int total) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
   unsigned int k = incl - cnt;
   for (unsigned int mm = m; mm; mm &= mm - 1) {
     const unsigned int sj = __ffs(mm) - 1;
@@ -721,7 +756,7 @@ __device__ __forceinline__ void force_rounds(ForceShared& S, unsigned int m, boo
       }
       __syncwarp();
     }
-    if (e < total) atomicMax(reinterpret_cast<unsigned int*>(own_only ? &S.ivs[sj] : &S.jvs[sj]), __float_as_uint(vs));
+    if (e < total) atomicMax(reinterpret_cast<unsigned int*>(own_only ? &S.ivs[sj] : &S.f[sj].w), __float_as_uint(vs));
     __syncwarp();
   }
 }
@@ -792,7 +827,7 @@ __device__ __noinline__ void force_batch(ForceShared& S, unsigned int q, bool ow
   force_tile<COUNT>(S, allow, jvalid, bandJ, (int)((q + 3u) & ~3u), own_only, 0xffffffffu, perm, x, g, alpha,
                     fcnt, C);
   __syncwarp();
-  if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
+  if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.f[lane].w, facc, fvsig);
   __syncwarp();
 }
 
@@ -820,7 +855,7 @@ __device__ __noinline__ void force_replay_batch(ForceShared& S, const unsigned i
   }
   force_rounds<COUNT>(S, m, own_only, alpha, fcnt);
   __syncwarp();
-  if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.jvs[lane], facc, fvsig);
+  if (v && !own_only) flush_force(S.g[lane], S.jacc[lane], S.f[lane].w, facc, fvsig);
   __syncwarp();
 }
 
@@ -2081,10 +2116,23 @@ void launch_density(Engine& E, const int* it_dev, int only) {
   }
 }
 
+#ifndef FORCE_BLOCKS
+#define FORCE_BLOCKS 0
+#endif
 void launch_force(Engine& E) {
   const auto k = E.count_pairs ? k_force<true> : k_force<false>;
   cudaMemsetAsync(E.task_ctr.p + 1, 0, sizeof(unsigned int), E.st);
-  launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
+  int nb = resident_ctas((const void*)k);
+  if (FORCE_BLOCKS > 0) {
+    static bool set[2] = {false, false};
+    if (!set[E.count_pairs ? 1 : 0]) {
+      const int pct = (int)std::ceil(100.0 * FORCE_BLOCKS * (sizeof(ForceShared) * SPH_WARPS_PER_CTA + 1024) / (228.0 * 1024));
+      cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout, std::min(pct, 100));
+      set[E.count_pairs ? 1 : 0] = true;
+    }
+    nb = std::min(nb, FORCE_BLOCKS);
+  }
+  launch_pdl(k, E.nsm * nb, SPH_THREADS, E.st,
       E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.vel4.p, E.ghost4.p, E.sort_r.p, E.sort_i.p, E.perm.p, E.x.p,
       E.prm.alpha_visc, E.facc.p, E.fvsig.p, E.fcnt.p, E.pc.p, E.task_ctr.p + 1, E.rec_for_force());
   count_launch();

@@ -73,11 +73,14 @@ __device__ __forceinline__ BoxExact box_exact(const ItemGeom& g) { return BoxExa
 constexpr unsigned int TASK_CHUNK_DENSITY = 8;
 constexpr unsigned int TASK_CHUNK_FORCE = 2;
 
-// blocks per SM of the recording first density pass: as the plain first pass
-// (5), with a few registers spilled for the record state, which measured faster
-// than 4 blocks without spills
+// blocks per SM of the recording first density pass (5, with a few registers
+// spilled for the record state, measured faster than 4 blocks without spills) and
+// of the plain first pass (see k_density)
 #ifndef REC_BLOCKS
 #define REC_BLOCKS 5
+#endif
+#ifndef DENS_BLOCKS
+#define DENS_BLOCKS 7
 #endif
 
 // Exact decision r_ij < H (physical H) from the caller's FP64 positions.
@@ -1369,10 +1372,12 @@ __device__ __forceinline__ void force_replay_task(bool self, int item, unsigned 
 // side culls against the box of the cluster's iterating particles; the first pass
 // (every particle) has its own instance without that code.  Both are launched in
 // a captured step, and the one that does not match the iteration returns.
-// The first pass (PART = false) keeps to 5 blocks of 128 threads per SM (at most
-// 102 registers): with fewer warps in flight it waits longer on partner loads.
+// The first pass (PART = false) runs 7 blocks of 128 threads per SM (at most 73
+// registers, a few spilled): the pass waits mostly on partner loads, and more warps
+// in flight hide more of them (33.5M: 62.8 ms at 5 blocks, 61.5 at 6, 60.5 at 7,
+// 61.7 at 8, where the spills grow).
 template <bool COUNT, bool PART, bool KAHAN, bool REC>
-__global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : (REC ? REC_BLOCKS : 5)) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+__global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : (REC ? REC_BLOCKS : DENS_BLOCKS)) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                          const float4* __restrict__ pos4,
                                                          const float4* __restrict__ cen4,
                                                          const float* __restrict__ sort_r,

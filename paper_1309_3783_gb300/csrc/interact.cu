@@ -74,13 +74,18 @@ constexpr unsigned int TASK_CHUNK_DENSITY = 8;
 constexpr unsigned int TASK_CHUNK_FORCE = 2;
 
 // blocks per SM of the recording first density pass (5, with a few registers
-// spilled for the record state, measured faster than 4 blocks without spills) and
-// of the plain first pass (see k_density)
+// spilled for the record state, measured faster than 4 blocks without spills), of
+// the plain first pass (see k_density) and of the later passes (5: with 5 % of the
+// particles iterating, a later pass cost 26 % of a full pass unbounded at 3 blocks,
+// 21 % at 5, 25 % at 7)
 #ifndef REC_BLOCKS
 #define REC_BLOCKS 5
 #endif
 #ifndef DENS_BLOCKS
 #define DENS_BLOCKS 7
+#endif
+#ifndef PART_BLOCKS
+#define PART_BLOCKS 5
 #endif
 
 // Exact decision r_ij < H (physical H) from the caller's FP64 positions.
@@ -1377,7 +1382,7 @@ __device__ __forceinline__ void force_replay_task(bool self, int item, unsigned 
 // in flight hide more of them (33.5M: 62.8 ms at 5 blocks, 61.5 at 6, 60.5 at 7,
 // 61.7 at 8, where the spills grow).
 template <bool COUNT, bool PART, bool KAHAN, bool REC>
-__global__ void __launch_bounds__(SPH_THREADS, PART ? 1 : (REC ? REC_BLOCKS : DENS_BLOCKS)) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
+__global__ void __launch_bounds__(SPH_THREADS, PART ? PART_BLOCKS : (REC ? REC_BLOCKS : DENS_BLOCKS)) k_density(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                          const float4* __restrict__ pos4,
                                                          const float4* __restrict__ cen4,
                                                          const float* __restrict__ sort_r,

@@ -676,6 +676,26 @@ __device__ __forceinline__ void force_rounds_list(ForceShared& S, unsigned int m
                                                   unsigned int* fcnt, unsigned int cnt, unsigned int incl,
                                                   unsigned int total);
 
+// A batch with more pairs than the list holds (rare: dense clusters): two halves
+// of the own lanes, at most 16 x 32 pairs each, out of line so that the common
+// path keeps its registers.
+template <bool COUNT>
+__device__ __noinline__ void force_rounds_halves(ForceShared& S, unsigned int m, bool own_only, float alpha,
+                                                 unsigned int* fcnt) {
+  const int lane = threadIdx.x & 31;
+  for (int half = 0; half < 2; ++half) {
+    const unsigned int mh = (lane >> 4) == half ? m : 0u;
+    const unsigned int ch = __popc(mh);
+    unsigned int ih = ch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, ih, o);
+      if (lane >= o) ih += y;
+    }
+    force_rounds_list<COUNT>(S, mh, own_only, alpha, fcnt, ch, ih, __shfl_sync(0xffffffffu, ih, 31));
+  }
+}
+
 template <bool COUNT>
 __device__ __forceinline__ void force_rounds(ForceShared& S, unsigned int m, bool own_only, float alpha,
                                              unsigned int* fcnt) {
@@ -690,22 +710,8 @@ __device__ __forceinline__ void force_rounds(ForceShared& S, unsigned int m, boo
     if (lane >= o) incl += y;
   }
   const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-  const bool split = total > (unsigned int)PLIST_CAP;
-  for (int half = 0; half < (split ? 2 : 1); ++half) {
-    unsigned int mh = m, ch = cnt, ih = incl, th = total;
-    if (split) {
-      mh = (lane >> 4) == half ? m : 0u;
-      ch = __popc(mh);
-      ih = ch;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xffffffffu, ih, o);
-        if (lane >= o) ih += y;
-      }
-      th = __shfl_sync(0xffffffffu, ih, 31);
-    }
-    force_rounds_list<COUNT>(S, mh, own_only, alpha, fcnt, ch, ih, th);
-  }
+  if (total <= (unsigned int)PLIST_CAP) force_rounds_list<COUNT>(S, m, own_only, alpha, fcnt, cnt, incl, total);
+  else force_rounds_halves<COUNT>(S, m, own_only, alpha, fcnt);
 }
 
 // The rounds over one list: cnt pairs of the lane (mask m), incl their inclusive

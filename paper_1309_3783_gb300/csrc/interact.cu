@@ -1435,9 +1435,10 @@ __global__ void __launch_bounds__(SPH_THREADS, PART ? PART_BLOCKS : (REC ? REC_B
 }
 
 // Force interactions of one pass: the pair and self tasks in one queue.
-// Registers capped at 64 per thread (8 blocks of 128 threads): more warps in
-// flight to hide the partner loads outweigh the few spilled values; shared
-// memory then holds 7 blocks per SM.
+// Registers capped at 64 per thread (8 blocks of 128 threads, whose shared memory
+// fits an SM with the 768-entry pair list): more warps in flight to hide the
+// partner loads outweigh the few spilled values (33.5M: 6, 5 and 4 blocks took 74,
+// 84 and 98 ms against 65 ms).
 template <bool COUNT>
 __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box,
                                                        const float4* __restrict__ pos4,
@@ -2068,7 +2069,7 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
 // may run in several host threads)
 static int resident_ctas(const void* fn) {
   static std::mutex mu;
-  static const void* fns[16] = {nullptr};   // the 8 density and 2 force instances
+  static const void* fns[16] = {nullptr};   // the 12 density and 2 force instances
   static int val[16] = {0};
   std::lock_guard<std::mutex> lock(mu);
   for (int k = 0; k < 16; ++k) {

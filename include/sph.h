@@ -363,8 +363,10 @@ sph_status sph_measure_fp32_peak(sph_ctx* ctx, double* tflops);
 /* Autotune the cell split threshold leaf_max (Section II-B splits cells above
  * it; the paper uses 400 on its CPUs) and the particles per cluster for this
  * box's current particles: times build + density + force for leaf_max in {24,
- * 32, 48, 64, 96, 128, 192, 256, 400} with clusters of 32, then clusters of 16
- * and 24 at the best leaf_max, and keeps the fastest pair for the box.
+ * 32, 48, 64, 96, 128, 192, 256, 400, 600, 800, 1200, 1600, 2400, 3200, 4800}
+ * with clusters of 32,
+ * then clusters of 16 and 24 at the best leaf_max, and keeps the fastest pair for
+ * the box.
  * *leaf_max (may be NULL) receives the leaf size; sph_get_stats reports both.
  * Results of the passes run while tuning are discarded (the box is unbuilt). */
 sph_status sph_box_tune(sph_box* box, int32_t* leaf_max);

@@ -1840,7 +1840,8 @@ sph_status Engine::tune(int* best_out) {
   // leaf_max over its candidates with clusters of 32, then the cluster size at the
   // best leaf_max: times build + density + force (the mean of two repetitions
   // after one that warms up allocations)
-  static const int cand[] = {24, 32, 48, 64, 96, 128, 192, 256, 400};
+  // (above the paper's 400: on GB300 larger leaves, fewer and heavier tasks, can pay)
+  static const int cand[] = {24, 32, 48, 64, 96, 128, 192, 256, 400, 600, 800, 1200, 1600, 2400, 3200, 4800};
   static const int ccand[] = {16, 24};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

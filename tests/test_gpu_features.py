@@ -144,7 +144,7 @@ def test_autotuned_leaf_size_keeps_parity(api, ctx):
     b = api.box_from(ctx, box)
     try:
         leaf = b.tune()
-        assert leaf in (24, 32, 48, 64, 96, 128, 192, 256, 400)
+        assert leaf in (24, 32, 48, 64, 96, 128, 192, 256, 400, 600, 800, 1200, 1600, 2400, 3200, 4800)
         st = b.stats()
         assert st["leaf_max"] == leaf and st["cluster_max"] in (16, 24, 32)
         b.density()

@@ -203,10 +203,10 @@ def _pair_set_case(name):
     if name == "lattice4096":
         return inputs.lattice_box(16, jitter=0.1, seed=1), 400
     box = inputs.plummer_box(n=20000, n_spheres=4, scale=0.05, seed=3)
-    return box, 48
+    return box, (4800 if name.endswith("leaf4800") else 48)
 
 
-@pytest.mark.parametrize("case", ["lattice4096", "plummer20000"])
+@pytest.mark.parametrize("case", ["lattice4096", "plummer20000", "plummer20000_leaf4800"])
 def test_interacting_pair_sets_equal_brute_force(api, case):
     """Section II-B: every pair within max(H_i, H_j) lies in exactly one self- or
     pair-interaction.  The density kernel's pair and side counters and the force

@@ -253,13 +253,18 @@ def timed_steps(torch, b, dt, stream, steps, flush=None):
     return [s.elapsed_time(e) for s, e in evs]
 
 
-def prepare_box(sph, ctx, box, tune):
+def prepare_box(sph, ctx, box, tune, leaf=None):
     """Resident input state: h converged once (a simulation's previous step), the
-    split threshold and cluster size tuned for the workload, dt from the CFL rule."""
+    split threshold and cluster size tuned for the workload (or the split
+    threshold given), dt from the CFL rule."""
     b = sph.Box(ctx, box.n, box.L, True)
     b.set(box.x, box.v, box.m, box.u, box.h)
-    b.h_update()
     leaf_max = 400
+    if leaf:
+        b.set_leaf_max(leaf)
+        leaf_max = leaf
+        tune = False
+    b.h_update()
     if tune:
         leaf_max = b.tune()                           # untimed
         b.h_update()
@@ -294,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = sph.sph_ctx_create(params, device=local_rank)
     stream = torch.cuda.Stream()
     sph.sph_ctx_set_stream(ctx, stream.cuda_stream)
-    b, leaf_max, cluster_max, dt = prepare_box(sph, ctx, box, not args.no_tune)
+    b, leaf_max, cluster_max, dt = prepare_box(sph, ctx, box, not args.no_tune, args.leaf_max_set)
     args.leaf_max, args.cluster_max = leaf_max, cluster_max
     torch.cuda.synchronize()
 
@@ -364,7 +369,8 @@ def run_ours(args, rank, world, local_rank):
     if os.path.exists(tpath):
         try:
             tj = json.load(open(tpath)).get(args.workload, {})
-            if dom in tj:
+            # counters taken on another decomposition do not describe this launch
+            if dom in tj and tj.get("leaf_max") == leaf_max and tj.get("cluster_max") == cluster_max:
                 traffic = tj[dom]
         except (OSError, ValueError, AttributeError):
             traffic = None
@@ -378,7 +384,8 @@ def run_ours(args, rank, world, local_rank):
                    "protocol": "fixed-step kick-drift-kick run, forces on all particles every step, decomposition "
                                "rebuilt every step",
                    "dt": dt, "leaf_max": leaf_max, "cluster_max": cluster_max,
-                   "leaf_max_source": "autotuned" if not args.no_tune else "paper",
+                   "leaf_max_source": ("set" if args.leaf_max_set else
+                                       "autotuned" if not args.no_tune else "paper"),
                    "l2": ("inputs larger than L2 (about 520 B per particle resident)" if big
                           else "flushed between timed steps (256 MB write)"),
                    "parallelism": f"replicas x{world}"},
@@ -425,14 +432,15 @@ def run_ours(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ other legs
 def run_other_workloads(sph, torch, ctx, stream, args, rank, precision=None, steps=10, warmup=3):
-    """The other single-box workloads, a shorter run each (leaf size 400, clusters of 32);
-    the 262,144-particle box also in both position precisions (into `precision`)."""
+    """The other single-box workloads, a shorter run each (leaf and cluster size
+    autotuned for each box); the 262,144-particle box also in both position
+    precisions (into `precision`)."""
     out = {}
     for name, (make, recipe) in WORKLOADS.items():
         if name == args.workload:
             continue
         box = make(replica_seed(rank))
-        b, _, _, dt = prepare_box(sph, ctx, box, tune=False)
+        b, leaf, cmax, dt = prepare_box(sph, ctx, box, tune=True)
         try:
             for _ in range(warmup):
                 b.step(dt)
@@ -441,10 +449,10 @@ def run_other_workloads(sph, torch, ctx, stream, args, rank, precision=None, ste
             ms = timed_steps(torch, b, dt, stream, steps, flush)
             del flush
             out[name] = {"value": box.n * steps / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": sum(ms) / steps,
-                         "steps": steps, "recipe": recipe}
+                         "steps": steps, "leaf_max": leaf, "cluster_max": cmax, "recipe": recipe}
             if precision is not None and name == "plummer-262144":
                 state = {k: b.get(k) for k in ("x", "v", "u", "h", "a", "dudt")}
-                args_small = argparse.Namespace(leaf_max=400, cluster_max=32, warmup=warmup, steps=steps)
+                args_small = argparse.Namespace(leaf_max=leaf, cluster_max=cmax, warmup=warmup, steps=steps)
                 precision[name] = run_precision_leg(sph, torch, box, state, dt, stream, args_small)
         finally:
             b.close()
@@ -776,6 +784,8 @@ def main():
     ap.add_argument("--workload", choices=sorted({**WORKLOADS, **PROFILE_WORKLOADS}), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="keep the paper's leaf_max = 400")
+    ap.add_argument("--leaf-max", dest="leaf_max_set", type=int, default=None,
+                    help="use this split threshold instead of autotuning it (clusters of 32)")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-batch latency run")
     ap.add_argument("--no-extra-workloads", action="store_true", help="skip the other single-box workloads")
     ap.add_argument("--no-precision", action="store_true", help="skip the plain-FP32 position comparison")

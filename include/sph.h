@@ -132,6 +132,18 @@ typedef struct sph_params {
                              a quarter less time and the recording first density
                              pass about as much more; 0: the force pass culls on
                              its own (0)                                           */
+    int32_t h_gather;     /* 1: a later pass of the h iteration (Section II-D, the
+                             density loop again for the particles whose h has not
+                             converged) in which at most an eighth of the
+                             particles iterate gathers: each leaf's iterating
+                             particles are packed into clusters of up to 32 and
+                             every interaction runs for the packed clusters of its
+                             cells, the own side only, instead of the symmetric
+                             tasks of every cluster near an iterating particle.
+                             The sums are the same up to rounding order; counts
+                             stay exact.  0: the symmetric tasks in every pass;
+                             passes with pair counting (sph_box_count_pairs) also
+                             take them (1)                                          */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;
@@ -206,6 +218,9 @@ typedef struct sph_stats {
        particle near them took a new h, or the records ran out of room)      */
     int64_t force_tasks_replayed;
     int64_t force_tasks_culled;
+    int64_t h_gathered_passes;  /* later density passes of the last h iteration
+                                   launched from the host (sph_h_update, or a step
+                                   not run as a graph) that gathered (params.h_gather) */
 } sph_stats;
 
 /* Device time of one phase of the path (CUDA events on the stream the phase runs

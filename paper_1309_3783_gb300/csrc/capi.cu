@@ -64,6 +64,8 @@ __global__ void k_check_build(cudaGraphConditionalHandle, const unsigned int*, c
 // launchers of interact.cu
 void launch_live_tasks(Engine& E, bool dens, const int* it_dev = nullptr);
 void launch_density(Engine& E, const int* it_dev = nullptr, int only = -1);
+void launch_gather_prep(Engine& E, const int* it_dev);
+void launch_density_gather(Engine& E);
 double measure_fp32_peak(cudaStream_t st, int nsm, float* scratch);
 void launch_force(Engine& E);
 void launch_ghost(Engine& E, int mode, int it, const int* it_dev = nullptr);
@@ -382,6 +384,15 @@ sph_status Engine::ensure_particle_capacity() {
   CK(err_all.reserve(4));
   CK(pc.reserve(16));
   CK(task_ctr.reserve(4));
+  CK(pk_cnt.reserve(n + 1));
+  CK(pk_v.reserve(n + 1));
+  CK(pk_idx.reserve(n));
+  CK(pk_info.reserve(n));
+  CK(pk_n.reserve(n));
+  CK(pk_sums.reserve((n + 1) / 2048 + 64));
+  CK(pk_tot.reserve(2));
+  CK(g_n.reserve(2));
+  CK(gflag.reserve(2));
   CK(dev_counters.reserve(8));
   CK(staging.reserve(24 * n));
   CK(cudaMemsetAsync(conv.p, 0, n * sizeof(int), st));
@@ -739,6 +750,7 @@ sph_status Engine::build_once(bool* retry) {
   CK(l_ptask.reserve(std::max(lc[6], 1)));
   CK(l_stask.reserve(std::max(lc[7], 1)));
   CK(l_plive.reserve(std::max(lc[6] + lc[7], 1)));
+  CK(g_live.reserve(l_plive.n));
   CK(l_nlive.reserve(1));
   n_ptasks = lc[6];
   n_stasks = lc[7];
@@ -896,6 +908,7 @@ sph_status Engine::density() {
   have_force = false;
   last_iters = 1;
   last_rebuilds = 0;
+  last_gathered = 0;
   return SPH_OK;
 }
 
@@ -922,6 +935,8 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
   CK(cudaMemsetAsync(err_all.p, 0, 4 * sizeof(unsigned int), st));
   int itv[3] = {1, 0, 0};
   CK(cudaMemcpyAsync(it_dev.p, itv, 3 * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(g_n.p + 1, 0, sizeof(unsigned int), st));
+  unsigned int ngath = 0;
   bool fresh = true;      // all particles marked active (first iteration, or after a rebuild)
   for (;;) {
     const int nb = std::min(H_BATCH, prm.h_max_iter - it + 1);
@@ -931,6 +946,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
       {
         Scope sc(this, PH_DENSITY_TASKS);
         launch_zero_density(*this, false);
+        if (it + k > 1) launch_gather_prep(*this, it_dev.p);
         launch_live_tasks(*this, true, it_dev.p);
       }
       {
@@ -938,6 +954,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
         // kernels then find no tasks): the pass kind is known here
         Scope sc(this, PH_DENSITY);
         launch_density(*this, it_dev.p, it + k > 1 ? 1 : 0);
+        if (it + k > 1) launch_density_gather(*this);
       }
       {
         Scope sc(this, PH_GHOST);
@@ -947,6 +964,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(itv, it_dev.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ngath, g_n.p + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     unsigned int rc = 0;
     const bool read_rec = rebuilds == 0 && it == 1 && rec_valid;
     if (read_rec) CK(cudaMemcpyAsync(&rc, rec_ctr.p, sizeof(rc), cudaMemcpyDeviceToHost, st));
@@ -992,6 +1010,7 @@ sph_status Engine::h_update(long long* n_unconverged, int* iterations) {
   }
   last_iters = it;
   last_rebuilds = rebuilds;
+  last_gathered = ngath;
   last_unconverged = nu;
   if (n_unconverged) *n_unconverged = nu;
   if (iterations) *iterations = it;
@@ -1292,8 +1311,10 @@ sph_status Engine::capture_step_graph() {
   c1 = launch_count();
   CKG(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
   launch_zero_density(*this, false);
+  launch_gather_prep(*this, it_dev.p);
   launch_live_tasks(*this, true, it_dev.p);
   launch_density(*this, it_dev.p);
+  launch_density_gather(*this);
   launch_ghost(*this, 1, 0, it_dev.p);
   launch_iter_next(*this, iter, frc);
   launch_mark_active_cells(*this);
@@ -1362,6 +1383,7 @@ sph_status Engine::step_graph() {
   rec_valid = R.pool != nullptr;
   last_iters = itv[0];
   last_rebuilds = 0;
+  last_gathered = 0;
   first_active = itv[1];
   long long nu = 0;
   if (itv[0] >= prm.h_max_iter) {
@@ -1530,6 +1552,7 @@ sph_status Engine::capture_build_graph() {
   CK(l_ptask.reserve(cp));
   CK(l_stask.reserve(cs));
   CK(l_plive.reserve(cp + cs));
+  CK(g_live.reserve(l_plive.n));
   CK(l_nlive.reserve(1));
   Lq.p_task = l_ptask.p;
   Lq.s_task = l_stask.p;
@@ -1632,8 +1655,10 @@ sph_status Engine::capture_build_graph() {
   prof_into_graph = false;
   CKB(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, mode));
   launch_zero_density(*this, false);
+  launch_gather_prep(*this, it_dev.p);
   launch_live_tasks(*this, true, it_dev.p);
   launch_density(*this, it_dev.p);
+  launch_density_gather(*this);
   launch_ghost(*this, 1, 0, it_dev.p);
   launch_iter_next(*this, iter, frc);
   launch_mark_active_cells(*this);
@@ -1802,6 +1827,7 @@ sph_status Engine::build_step_graph() {
   have_density = have_ghost = have_force = have_acc = true;
   last_iters = itv[0];
   last_rebuilds = 0;
+  last_gathered = 0;
   first_active = itv[1];
   long long nu = 0;
   if (itv[0] >= prm.h_max_iter) {
@@ -2048,6 +2074,7 @@ sph_status Engine::stats(int b, sph_stats* o) {
   o->builds = n_builds;
   o->reuses = n_reuses;
   o->h_active_after_first = first_active;
+  o->h_gathered_passes = last_gathered;
   o->leaf_max = prm.leaf_max;
   o->cluster_max = prm.cluster_max;
   o->graph_steps = steps_graph;
@@ -2186,6 +2213,7 @@ void sph_params_default(sph_params* p) {
   p->precision = 0;
   p->graphs = 1;
   p->pair_cache = 0;
+  p->h_gather = 1;
 }
 
 sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
@@ -2198,7 +2226,7 @@ sph_status sph_ctx_create(const sph_params* params, int device, sph_ctx** out) {
       !(p.split_frac >= 0 && p.split_frac <= 1) || p.max_depth < 1 || !(p.h_tol > 0) || !(p.alpha_visc >= 0) ||
       !(p.split_headroom >= 0 && p.split_headroom < 1) || p.cluster_max < 1 || p.cluster_max > 32 ||
       (p.precision != 0 && p.precision != 1) || (p.graphs != 0 && p.graphs != 1) ||
-      (p.pair_cache != 0 && p.pair_cache != 1))
+      (p.pair_cache != 0 && p.pair_cache != 1) || (p.h_gather != 0 && p.h_gather != 1))
     return SPH_E_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SPH_E_INVALID;

@@ -207,6 +207,12 @@ struct Counters {
   unsigned int cand = 0, pairs = 0, sides = 0, rechecks = 0;
 };
 
+// A later pass of the h iteration gathers (the symmetric tasks stand aside) when
+// its task builder chose to and its tasks fitted the buffer.
+__device__ __forceinline__ bool gather_on(const int* gflag, const unsigned int* g_n, unsigned int cap_g) {
+  return gflag[0] != 0 && *g_n <= cap_g;
+}
+
 __device__ __forceinline__ void flush_dens(int gidx, float4 acc, unsigned int cnt, float4* dacc, unsigned int* dcnt) {
   if (gidx < 0 || cnt == 0) return;
   atomicAdd(&dacc[gidx], acc);
@@ -1398,10 +1404,13 @@ __global__ void __launch_bounds__(SPH_THREADS, PART ? PART_BLOCKS : (REC ? REC_B
                                                          const double* __restrict__ x, float4* dacc,
                                                          unsigned int* dcnt, unsigned long long* pc,
                                                          unsigned int* __restrict__ task_ctr, int partial_host,
-                                                         const int* __restrict__ it_dev, const __grid_constant__ PairRec Rec) {
+                                                         const int* __restrict__ it_dev, const int* __restrict__ gflag,
+                                                         const unsigned int* __restrict__ g_n, unsigned int cap_g,
+                                                         const __grid_constant__ PairRec Rec) {
   pdl_wait();
   const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
   if ((partial != 0) != PART) return;
+  if (PART && gflag && gather_on(gflag, g_n, cap_g)) return;   // the pass gathers
   __shared__ DensShared SH[SPH_WARPS_PER_CTA];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   DensShared& S = SH[wl];
@@ -1510,7 +1519,9 @@ __global__ void __launch_bounds__(SPH_THREADS, 8) k_force(Lists Lq, Tree T, Tile
 // warp-aggregated appends.
 template <bool DENS>
 __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, long long npt,
-                             long long nst, int partial_host, const int* __restrict__ it_dev, int cap_p, int cap_s) {
+                             long long nst, int partial_host, const int* __restrict__ it_dev, int cap_p, int cap_s,
+                             const int* __restrict__ gflag, const unsigned int* __restrict__ g_n,
+                             unsigned int cap_g) {
   pdl_wait();
   const int lane = threadIdx.x & 31;
   if (it_dev && it_dev[2] != 0) return;    // the iteration has stopped: no tasks
@@ -1521,6 +1532,7 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
   }
   // later iterations keep only what still iterates (with a device counter: from iteration 2 on)
   const int partial = it_dev ? (*it_dev > 1 ? 1 : 0) : partial_host;
+  if (DENS && partial && gflag && gather_on(gflag, g_n, cap_g)) return;   // the pass gathers
   const long long ntask = npt + nst;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < ntask; b0 += stride) {
@@ -1564,6 +1576,313 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
     if (lane == 0 && bal) at = atomicAdd(Lq.n_live, (unsigned int)__popc(bal));
     at = __shfl_sync(0xffffffffu, at, 0);
     if (live) Lq.p_live[at + __popc(bal & ((1u << lane) - 1u))] = make_uint2(rec, ti);
+  }
+}
+
+// =========================================================================== gathered later passes
+// A later pass of the h iteration needs the density sums of the particles still
+// iterating only (Section II-D: the density loop runs again for the particles
+// whose h has not converged).  Tracked per cluster and cell, a few per cent of
+// randomly placed iterating particles make most clusters and cells active, and
+// the symmetric tasks then run nearly in full for their partner side.  A later
+// pass with few iterating particles gathers instead: each leaf's iterating
+// particles are packed, in their sorted order, into clusters of up to 32, so that
+// the packed clusters of a cell are one range; every interaction then runs once
+// per packed cluster of each of its cells, the own side only — for a pair (A, B)
+// A's packed clusters against B's clusters and B's against A's, for the self
+// interaction of A its packed clusters against all of A's clusters with the
+// particle itself left out.  A pair with r < H_i of an iterating particle i lies
+// in exactly one interaction (Section II-B), and there it is taken once, from i.
+
+// The packing runs for the later passes only (the first pass of a captured
+// iteration returns at once, and so does a stopped iteration).
+__device__ __forceinline__ bool later_pass(const int* it_dev) { return it_dev[0] > 1 && it_dev[2] == 0; }
+
+// Particles still iterating per cluster (cnt[t], 0 past the clusters of this
+// build, ntcap + 1 entries); clears the gathered task count.  One warp per cluster.
+__global__ void k_pack_count(long long ntcap, const unsigned int* __restrict__ ntile_dev, const int* __restrict__ it_dev,
+                             Tiles TL, const unsigned char* __restrict__ act, unsigned int* __restrict__ cnt,
+                             unsigned int* __restrict__ g_n) {
+  pdl_wait();
+  if (!later_pass(it_dev)) return;
+  const long long nt = ntile_dev ? min(ntcap, (long long)*ntile_dev) : ntcap;
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *g_n = 0;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = warp; t <= ntcap; t += nwarps) {
+    bool a = false;
+    if (t < nt) a = (unsigned int)lane < TL.n[t] && act[TL.start[t] + lane];
+    const unsigned int c = __popc(__ballot_sync(0xffffffffu, a));
+    if (lane == 0) cnt[t] = c;
+  }
+}
+
+// After the scan of the counts (rank[t]: iterating particles before cluster t):
+// the packed clusters of each leaf, at its first cluster (0 elsewhere).
+__global__ void k_pack_leaf(long long ntcap, const unsigned int* __restrict__ ntile_dev, const int* __restrict__ it_dev,
+                            Tree T, Tiles TL, const unsigned int* __restrict__ rank, unsigned int* __restrict__ v) {
+  pdl_wait();
+  if (!later_pass(it_dev)) return;
+  const long long nt = ntile_dev ? min(ntcap, (long long)*ntile_dev) : ntcap;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t <= ntcap;
+       t += (long long)gridDim.x * blockDim.x) {
+    unsigned int val = 0;
+    if (t < nt) {
+      const unsigned int L = TL.leaf[t];
+      if (T.tile0[L] == (unsigned int)t) val = (rank[t + T.ntile[L]] - rank[t] + 31u) >> 5;
+    }
+    v[t] = val;
+  }
+}
+
+// The packed clusters (after the scan of k_pack_leaf's counts: pk0[t], the first
+// packed cluster of the leaf whose first cluster is t): the sorted indices of the
+// iterating particles by rank (idx), and per packed cluster its first rank and
+// its leaf's first cluster (info) and its size (pn).  One warp per cluster.
+__global__ void k_pack_fill(long long ntcap, const unsigned int* __restrict__ ntile_dev, const int* __restrict__ it_dev,
+                            Tree T, Tiles TL, const unsigned char* __restrict__ act,
+                            const unsigned int* __restrict__ rank, const unsigned int* __restrict__ pk0,
+                            unsigned int* __restrict__ idx, uint2* __restrict__ info, unsigned char* __restrict__ pn) {
+  pdl_wait();
+  if (!later_pass(it_dev)) return;
+  const long long nt = ntile_dev ? min(ntcap, (long long)*ntile_dev) : ntcap;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = warp; t < nt; t += nwarps) {
+    const unsigned int s = TL.start[t];
+    const bool a = (unsigned int)lane < TL.n[t] && act[s + lane];
+    const unsigned int bal = __ballot_sync(0xffffffffu, a);
+    if (!bal || !a) continue;
+    const unsigned int L = TL.leaf[t], t0 = T.tile0[L];
+    const unsigned int r0 = rank[t0];                        // the leaf's first rank
+    const unsigned int na = rank[t0 + T.ntile[L]] - r0;       // its iterating particles
+    const unsigned int k = rank[t] - r0 + __popc(bal & ((1u << lane) - 1u));
+    idx[r0 + k] = s + (unsigned int)lane;
+    if ((k & 31u) == 0u) {
+      const unsigned int pid = pk0[t0] + (k >> 5);
+      info[pid] = make_uint2(r0 + k, t0);
+      pn[pid] = (unsigned char)min(32u, na - k);
+    }
+  }
+}
+
+// The gathered tasks of a later pass, when it gathers: (interaction, packed
+// cluster), bit 31 of the interaction marking a self interaction and bit 30 the
+// direction of a pair (0: the packed clusters of A against B, 1: of B against
+// A).  The pass gathers when it is a later one, the caller allows it and at most
+// an eighth of the particles iterate (gflag[0]); the symmetric path runs instead
+// when the tasks exceed the buffer.  One thread per interaction, self
+// interactions first; warp-aggregated appends.
+__global__ void k_gather_tasks(Lists Lq, Tree T, long long npair, long long nself, int cap_pair, int cap_self,
+                               const int* __restrict__ it_dev, long long N, int allow,
+                               const unsigned int* __restrict__ pk0, const unsigned int* __restrict__ pk_tot,
+                               uint2* __restrict__ tasks, unsigned int* __restrict__ g_n, unsigned int cap_g,
+                               int* __restrict__ gflag) {
+  pdl_wait();
+  const bool on = allow != 0 && later_pass(it_dev) && 8ull * pk_tot[0] <= (unsigned long long)N;
+  if (blockIdx.x == 0 && threadIdx.x == 0) gflag[0] = on ? 1 : 0;
+  if (!on) return;
+  if (npair < 0) {
+    npair = min(Lq.counts[1], cap_pair);
+    nself = min(Lq.counts[0], cap_self);
+  }
+  const int lane = threadIdx.x & 31;
+  const long long nitem = nself + npair;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < nitem; b0 += stride) {
+    const long long i = b0 + threadIdx.x;
+    unsigned int code = 0, a0 = 0, a1 = 0, c0 = 0, c1 = 0;
+    if (i < nself) {
+      const int A = Lq.self_a[i];
+      a0 = pk0[T.tile0[A]];
+      a1 = pk0[T.tile0[A] + T.ntile[A]];
+      code = (unsigned int)i | 0x80000000u;
+    } else if (i < nitem) {
+      const int j = (int)(i - nself);
+      const int A = Lq.pair_a[j], B = Lq.pair_b[j];
+      a0 = pk0[T.tile0[A]];
+      a1 = pk0[T.tile0[A] + T.ntile[A]];
+      c0 = pk0[T.tile0[B]];
+      c1 = pk0[T.tile0[B] + T.ntile[B]];
+      code = (unsigned int)j;
+    }
+    const unsigned int mine = (a1 - a0) + (c1 - c0);
+    unsigned int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned int base = 0;
+    if (lane == 31 && wtot) base = atomicAdd(g_n, wtot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned int at = base + incl - mine;
+    for (unsigned int p = a0; p < a1; ++p, ++at)
+      if (at < cap_g) tasks[at] = make_uint2(code, p);
+    for (unsigned int p = c0; p < c1; ++p, ++at)
+      if (at < cap_g) tasks[at] = make_uint2(code | 0x40000000u, p);
+  }
+}
+
+// r < H_i over the first n staged partners (n a multiple of 4), exact: the FP32
+// test outside the guard band, FP64 inside (as pair_masks, the own radius only).
+__device__ __forceinline__ unsigned int own_mask(const DensI& I, const DensShared& S, unsigned int allow, int n,
+                                                 const unsigned int* perm, const double* x, const BoxExact g) {
+  const float iLo = I.H2 - I.band, iHi = I.H2 + I.band;
+  unsigned int m = 0, sure = 0;
+  for (int s0 = n - 4; s0 >= 0; s0 -= 4) {
+#pragma unroll
+    for (int k = 3; k >= 0; --k) {
+      const float4 J = S.p[s0 + k];
+      const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const unsigned int ai = __float_as_uint(r2 - iLo), bi = __float_as_uint(iHi - r2);   // sign: in / out
+      m = __funnelshift_l(ai, m, 1);
+      sure = __funnelshift_l(ai | bi, sure, 1);
+    }
+  }
+  unsigned int u = ~sure & allow;
+  while (u) {
+    const int s = __ffs(u) - 1;
+    u &= u - 1;
+    const unsigned int bit = 1u << s;
+    m = exact_less(I.g, S.g[s], I.Hphys, perm, x, g.L, g.halfL, g.periodic) ? (m | bit) : (m & ~bit);
+  }
+  return m & allow;
+}
+
+// One batch of q <= 32 staged partners, the own side only; in a self interaction
+// the particle itself (staged with its cell) is left out.
+template <bool KAHAN>
+__device__ __forceinline__ void gather_batch(const DensI& I, DensShared& S, unsigned int q, bool self,
+                                             DensAcc<KAHAN>& acc, unsigned int& cnt, const unsigned int* perm,
+                                             const double* x, const BoxExact g) {
+  const int lane = threadIdx.x & 31;
+  const bool v = (unsigned int)lane < q;
+  __syncwarp();
+  if (!v) S.p[lane] = make_float4(1e30f, 1e30f, 1e30f, -1.0f);
+  const unsigned int jvalid = __ballot_sync(0xffffffffu, v);
+  __syncwarp();
+  const unsigned int m = I.valid ? own_mask(I, S, jvalid, (int)((q + 3u) & ~3u), perm, x, g) : 0u;
+  for (unsigned int b = m; b; b &= b - 1) {
+    const int sj = __ffs(b) - 1;
+    if (self && S.g[sj] == I.g) continue;
+    const float4 J = S.p[sj];
+    const float dx = I.p.x - J.x, dy = I.p.y - J.y, dz = I.p.z - J.z;
+    dens_add(pair_r(fmaf(dz, dz, fmaf(dy, dy, dx * dx))), I.invH, S.a[sj].z, acc, cnt);
+  }
+  __syncwarp();
+}
+
+// One gathered task: packed cluster pid (of cell O) against the clusters of cell X.
+// The frame is the packed cluster's leaf centre; X's particles move into it by
+// the exact dyadic offset of the pair kernel's leaf frame (X's centre image minus
+// O's centre, taken in the same order), so each position is rounded once, at
+// most at the cells' scale, and the guard band holds as there.
+template <bool KAHAN>
+__device__ __forceinline__ void gather_task(uint2 tk, const Lists& Lq, const Tree& T, const Tiles& TL,
+                                            const BoxDesc* __restrict__ box, const float4* __restrict__ pos4,
+                                            const float4* __restrict__ cen4, const unsigned int* __restrict__ perm,
+                                            const double* __restrict__ x, float4* dacc, unsigned int* dcnt,
+                                            const uint2* __restrict__ pk_info, const unsigned char* __restrict__ pk_n,
+                                            const unsigned int* __restrict__ pk_idx, DensShared& S) {
+  const int lane = threadIdx.x & 31;
+  const bool self = (tk.x >> 31) != 0u, dir1 = ((tk.x >> 30) & 1u) != 0u;
+  const int item = (int)(tk.x & 0x3fffffffu);
+  int O, X, ax = 0;
+  if (self) {
+    O = X = Lq.self_a[item];
+  } else {
+    const int A = Lq.pair_a[item], B = Lq.pair_b[item];
+    ax = Lq.pair_axis[item];
+    O = dir1 ? B : A;
+    X = dir1 ? A : B;
+  }
+  // pair items join cells of one level: A's geometry serves both directions
+  const ItemGeom g = item_geom(T, box, self ? O : Lq.pair_a[item], ax);
+  const float3 offX = self ? make_float3(0.f, 0.f, 0.f)
+                           : (dir1 ? make_float3(-g.offB.x, -g.offB.y, -g.offB.z) : g.offB);
+  const uint2 info = pk_info[tk.y];
+  const unsigned int n = pk_n[tk.y];
+  const float4 cO = T.cen[O], cX = T.cen[X], cl = TL.cen[info.y];
+  const float3 shX = make_float3(offX.x - cX.x, offX.y - cX.y, offX.z - cX.z);
+  const float3 d = make_float3(cl.x - cO.x, cl.y - cO.y, cl.z - cO.z);
+  const float3 sh_part = make_float3(shX.x - d.x, shX.y - d.y, shX.z - d.z);
+  const float3 sh_own = make_float3(-cl.x, -cl.y, -cl.z);
+  const bool vi = (unsigned int)lane < n;
+  const DensI I = load_dens(vi, vi ? pk_idx[info.x + lane] : 0u, sh_own, pos4, cen4, nullptr, g.invL, g.eb);
+  // the packed particles' box and largest H: the own side reaches no further
+  Box3 bo;
+  bo.lo = make_float3(warp_min(vi ? I.p.x : 1e30f), warp_min(vi ? I.p.y : 1e30f), warp_min(vi ? I.p.z : 1e30f));
+  bo.hi = make_float3(warp_max(vi ? I.p.x : -1e30f), warp_max(vi ? I.p.y : -1e30f), warp_max(vi ? I.p.z : -1e30f));
+  const float Ho = warp_max(vi ? I.H : 0.0f);
+  const float slack = g.e * 1.52587890625e-05f + g.es + 1e-6f * fmaxf(T.hmax[O], T.hmax[X]) * g.invL;
+  const float reach = Ho + slack;
+  if (!self) {
+    // X's cell, widened by the drift since the build, in this frame
+    const float h = 0.5f * g.e + g.drift;
+    Box3 cx;
+    cx.lo = make_float3(cX.x + sh_part.x - h, cX.y + sh_part.y - h, cX.z + sh_part.z - h);
+    cx.hi = make_float3(cX.x + sh_part.x + h, cX.y + sh_part.y + h, cX.z + sh_part.z + h);
+    if (!box_near(bo, cx, reach)) return;
+  }
+  DensAcc<KAHAN> acc;
+  unsigned int cnt = 0, q = 0;
+  const unsigned int t0 = T.tile0[X], nt = T.ntile[X];
+  for (unsigned int b0 = 0; b0 < nt; b0 += 32) {
+    bool ok = false;
+    if (b0 + lane < nt) ok = box_near(bo, tile_box3(TL, T, t0 + b0 + lane, sh_part), reach);
+    unsigned int mask = __ballot_sync(0xffffffffu, ok);
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const unsigned int tj = t0 + b0 + (unsigned int)k;
+      const bool vj = (unsigned int)lane < TL.n[tj];
+      const DensI J = load_dens(vj, TL.start[tj] + lane, sh_part, pos4, cen4, nullptr, g.invL, g.eb);
+      const bool pass = vj && near_box(J.p, bo, reach);
+      const unsigned int bal = __ballot_sync(0xffffffffu, pass);
+      const unsigned int np = __popc(bal);
+      if (q + np > 32u) {
+        gather_batch<KAHAN>(I, S, q, self, acc, cnt, perm, x, box_exact(g));
+        q = 0;
+      }
+      if (pass) dens_put(S, (int)(q + __popc(bal & ((1u << lane) - 1u))), J);
+      q += np;
+    }
+  }
+  if (q) gather_batch<KAHAN>(I, S, q, self, acc, cnt, perm, x, box_exact(g));
+  flush_dens(I.g, acc.total(), cnt, dacc, dcnt);
+}
+
+#ifndef GATHER_BLOCKS
+#define GATHER_BLOCKS 8
+#endif
+// The gathered density pass (a later pass of the h iteration that gathers): the
+// tasks of k_gather_tasks, one per fetch; g_n[1] counts the passes that gathered.
+// Returns at once when the pass runs the symmetric tasks instead.
+template <bool KAHAN>
+__global__ void __launch_bounds__(SPH_THREADS, GATHER_BLOCKS) k_density_gather(
+    Lists Lq, Tree T, Tiles TL, const BoxDesc* __restrict__ box, const float4* __restrict__ pos4,
+    const float4* __restrict__ cen4, const unsigned int* __restrict__ perm, const double* __restrict__ x,
+    float4* dacc, unsigned int* dcnt, const uint2* __restrict__ tasks, unsigned int* __restrict__ g_n,
+    unsigned int cap_g, const int* __restrict__ gflag, const uint2* __restrict__ pk_info,
+    const unsigned char* __restrict__ pk_n, const unsigned int* __restrict__ pk_idx,
+    unsigned int* __restrict__ task_ctr) {
+  pdl_wait();
+  if (!gather_on(gflag, g_n, cap_g)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) g_n[1] += 1u;
+  __shared__ DensShared SH[SPH_WARPS_PER_CTA];
+  const int lane = threadIdx.x & 31;
+  DensShared& S = SH[threadIdx.x >> 5];
+  const unsigned int ntask = *g_n;
+  unsigned int t = 0;
+  if (lane == 0) t = atomicAdd(task_ctr, 1u);
+  for (t = __shfl_sync(0xffffffffu, t, 0); t < ntask; t = __shfl_sync(0xffffffffu, t, 0)) {
+    gather_task<KAHAN>(tasks[t], Lq, T, TL, box, pos4, cen4, perm, x, dacc, dcnt, pk_info, pk_n, pk_idx, S);
+    if (lane == 0) t = atomicAdd(task_ctr, 1u);
   }
 }
 
@@ -2069,10 +2388,10 @@ __global__ void k_get_field(long long off, long long n, int field, const unsigne
 // may run in several host threads)
 static int resident_ctas(const void* fn) {
   static std::mutex mu;
-  static const void* fns[16] = {nullptr};   // the 12 density and 2 force instances
-  static int val[16] = {0};
+  static const void* fns[24] = {nullptr};   // the 12 density, 2 gathered density and 2 force instances
+  static int val[24] = {0};
   std::lock_guard<std::mutex> lock(mu);
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < 24; ++k) {
     if (fns[k] == fn) return val[k];
     if (!fns[k]) {
       int nb = 0;
@@ -2096,9 +2415,10 @@ void launch_live_tasks(Engine& E, bool dens, const int* it_dev) {
   const int grid = (int)std::min<long long>((n + 255) / 256, (long long)E.nsm * 16);
   if (dens)
     launch_pdl(k_live_tasks<true>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, npt, nst, E.partial_pass, it_dev,
-               cap_p, cap_s);
+               cap_p, cap_s, it_dev ? E.gflag.p : nullptr, E.g_n.p, (unsigned int)E.g_live.n);
   else
-    launch_pdl(k_live_tasks<false>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, npt, nst, 0, nullptr, cap_p, cap_s);
+    launch_pdl(k_live_tasks<false>, grid, 256, E.st, E.Lq, E.T, E.TL, E.box.p, npt, nst, 0, nullptr, cap_p, cap_s,
+               nullptr, nullptr, 0u);
   count_launch();
 }
 
@@ -2128,9 +2448,45 @@ void launch_density(Engine& E, const int* it_dev, int only) {
                                 : (rec ? k_density<false, false, false, true> : k_density<false, false, false, false>));
     launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st,
         E.Lq, E.T, E.TL, E.box.p, E.pos4.p, E.cen4.p, E.sort_r.p, E.sort_i.p, E.act.p, E.perm.p, E.x.p, E.dacc.p,
-        E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev, E.rec_for_force());
+        E.dcnt.p, E.pc.p, E.task_ctr.p + 0, E.partial_pass, it_dev, it_dev ? E.gflag.p : nullptr, E.g_n.p,
+        (unsigned int)E.g_live.n, E.rec_for_force());
     count_launch();
   }
+}
+
+// The packing and the task list of a gathered later pass (a pass of the h
+// iteration given by it_dev; the kernels decide on the device whether it gathers).
+void launch_gather_prep(Engine& E, const int* it_dev) {
+  // a captured rebuild step covers the capacities (this build's sizes are on the device)
+  const long long nt = E.gcap ? E.N : E.n_tiles;
+  const unsigned int* ntd = E.gcap ? reinterpret_cast<const unsigned int*>(E.dev_counters.p + 4) : nullptr;
+  launch_pdl(k_pack_count, E.grid(32 * (nt + 1)), 256, E.st, nt, ntd, it_dev, E.TL, E.act.p, E.pk_cnt.p, E.g_n.p);
+  count_launch();
+  exclusive_scan(E.pk_cnt.p, E.pk_cnt.p, nt + 1, E.pk_sums.p, E.pk_tot.p + 0, E.st);
+  launch_pdl(k_pack_leaf, E.grid(nt + 1), 256, E.st, nt, ntd, it_dev, E.T, E.TL, E.pk_cnt.p, E.pk_v.p);
+  count_launch();
+  exclusive_scan(E.pk_v.p, E.pk_v.p, nt + 1, E.pk_sums.p, E.pk_tot.p + 1, E.st);
+  launch_pdl(k_pack_fill, E.grid(32 * nt), 256, E.st, nt, ntd, it_dev, E.T, E.TL, E.act.p, E.pk_cnt.p,
+             E.pk_v.p, E.pk_idx.p, E.pk_info.p, E.pk_n.p);
+  count_launch();
+  const long long npair = E.gcap ? -1 : E.n_pairs, nself = E.gcap ? -1 : E.n_selfs;
+  const long long nitem = E.gcap ? (long long)E.cap_pair + E.cap_self : (long long)E.n_pairs + E.n_selfs;
+  const int allow = E.prm.h_gather != 0 && !E.count_pairs ? 1 : 0;
+  launch_pdl(k_gather_tasks, E.grid(std::max<long long>(nitem, 1)), 256, E.st, E.Lq, E.T, npair, nself,
+             E.cap_pair, E.cap_self, it_dev, (long long)E.N, allow, E.pk_v.p, E.pk_tot.p, E.g_live.p, E.g_n.p,
+             (unsigned int)E.g_live.n, E.gflag.p);
+  count_launch();
+}
+
+// The gathered density pass; returns at once unless the pass gathers.
+void launch_density_gather(Engine& E) {
+  const bool kahan = E.prm.compensated > 0 || (E.prm.compensated < 0 && E.prm.n_ngb >= 100.0f);
+  const auto k = kahan ? k_density_gather<true> : k_density_gather<false>;
+  cudaMemsetAsync(E.task_ctr.p + 2, 0, sizeof(unsigned int), E.st);
+  launch_pdl(k, E.nsm * resident_ctas((const void*)k), SPH_THREADS, E.st, E.Lq, E.T, E.TL, E.box.p, E.pos4.p,
+             E.cen4.p, E.perm.p, E.x.p, E.dacc.p, E.dcnt.p, E.g_live.p, E.g_n.p, (unsigned int)E.g_live.n,
+             E.gflag.p, E.pk_info.p, E.pk_n.p, E.pk_idx.p, E.task_ctr.p + 2);
+  count_launch();
 }
 
 #ifndef FORCE_BLOCKS

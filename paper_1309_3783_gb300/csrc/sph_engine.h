@@ -192,6 +192,15 @@ class Engine {
   DBuf<int> l_self, l_pa, l_pb, l_pax, l_counts;
   DBuf<unsigned int> l_ptoff, l_stoff, scan_tmp, l_ptask, l_stask, l_nlive;
   DBuf<uint2> l_plive;
+  // gathered later passes of the h iteration: per cluster the particles still
+  // iterating (scanned to ranks), per leaf start its packed clusters (scanned to
+  // their first index), the packed clusters (indices by rank, first rank and leaf
+  // start, size), scan scratch and totals, the gathered tasks, their count and the
+  // pass's choice
+  DBuf<unsigned int> pk_cnt, pk_v, pk_idx, pk_sums, pk_tot, g_n;
+  DBuf<uint2> pk_info, g_live;
+  DBuf<unsigned char> pk_n;
+  DBuf<int> gflag;
   long long n_ptasks = 0, n_stasks = 0;
   int partial_pass = 0;           // 1 while the density passes cover only particles still iterating h
   DBuf<int> q_kind[2], q_a[2], q_b[2], q_ax[2];
@@ -244,6 +253,7 @@ class Engine {
   long long n_entries = 0, n_big_entries = 0;
   int last_iters = 0, last_rebuilds = 0;
   long long first_active = 0;     // particles still iterating after the first density pass
+  long long last_gathered = 0;    // later passes of the last host-driven h iteration that gathered
   int vpred = 0;                  // 1 inside a step after its drift: passes see v, u predicted to the step's end
   long long n_builds = 0, n_reuses = 0;
   bool reusable = false;          // the last full build can be kept (positions since then tracked)

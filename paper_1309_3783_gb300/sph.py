@@ -37,7 +37,7 @@ class sph_params(C.Structure):
                 ("max_depth", C.c_int32), ("split_headroom", C.c_float), ("reuse", C.c_int32),
                 ("sort_merge", C.c_int32), ("cluster_max", C.c_int32), ("compensated", C.c_int32),
                 ("precision", C.c_int32), ("graphs", C.c_int32),
-                ("pair_cache", C.c_int32)]
+                ("pair_cache", C.c_int32), ("h_gather", C.c_int32)]
 
 
 class sph_stats(C.Structure):
@@ -53,7 +53,8 @@ class sph_stats(C.Structure):
                 ("builds", C.c_int64), ("reuses", C.c_int64), ("h_active_after_first", C.c_int64),
                 ("leaf_max", C.c_int64), ("cluster_max", C.c_int64), ("graph_steps", C.c_int64),
                 ("host_steps", C.c_int64), ("host_syncs", C.c_int64),
-                ("force_tasks_replayed", C.c_int64), ("force_tasks_culled", C.c_int64)]
+                ("force_tasks_replayed", C.c_int64), ("force_tasks_culled", C.c_int64),
+                ("h_gathered_passes", C.c_int64)]
 
 
 class sph_profile_entry(C.Structure):

@@ -423,6 +423,80 @@ def test_h_iteration_results_exact_at_the_final_h(api, ctx):
     np.testing.assert_allclose(g["rho"], ref["rho"], rtol=1e-5)
 
 
+def _perturbed_run(api, box, h, **kw):
+    c = make_ctx(api, **kw)
+    try:
+        b = api.box_from(c, box)
+        try:
+            b.set_field("h", h)
+            st, nu, it = b.h_update()
+            out = {k: b.get(k) for k in ("h", "count", "rho")}
+            out["stats"], out["it"] = b.stats(), it
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c)
+    return out
+
+
+@pytest.mark.parametrize("leaf,mode", [(48, "random"), (48, "region"), (4800, "random")])
+def test_gathered_later_passes_equal_the_symmetric_passes(api, leaf, mode):
+    """Section II-D: a later pass of the h iteration evaluates the particles still
+    iterating.  With at most an eighth of them iterating it gathers
+    (sph_params.h_gather): each leaf's iterating particles packed into clusters,
+    every interaction run for them from their own side.  Every run, with one
+    later pass (h_max_iter 2) or iterated to convergence, in either mode, has
+    counts exact and densities within the bar against the oracle at its final h;
+    the two modes evaluate the same h after one later pass and converge to the
+    same h.  5 % of the particles iterate, spread at random or gathered around
+    one particle."""
+    box = inputs.plummer_box(n=20000, n_spheres=4, scale=0.05, seed=5)
+    c0 = make_ctx(api, leaf_max=leaf)
+    try:
+        b = api.box_from(c0, box)
+        try:
+            b.h_update()
+            h0 = b.get("h")
+        finally:
+            b.close()
+    finally:
+        api.sph_ctx_destroy(c0)
+    rng = np.random.default_rng(7)
+    if mode == "random":
+        k = rng.choice(box.n, box.n // 20, replace=False)
+    else:
+        d = box.x - box.x[rng.integers(box.n)]
+        d -= box.L * np.round(d / box.L)
+        k = np.argsort((d * d).sum(axis=1))[: box.n // 20]
+    h1 = h0.copy()
+    h1[k] *= rng.uniform(0.97, 1.03, k.size).astype(np.float32)   # within the split headroom: no rebuild
+    res = {(g, mi): _perturbed_run(api, box, h1, leaf_max=leaf, h_gather=g, h_max_iter=mi)
+           for g in (0, 1) for mi in (2, 30)}
+    for key, r in res.items():
+        assert r["stats"]["rebuilds"] == 0, key
+    assert res[(1, 2)]["stats"]["h_gathered_passes"] == 1
+    assert res[(0, 2)]["stats"]["h_gathered_passes"] == 0
+    assert res[(1, 30)]["stats"]["h_gathered_passes"] >= 1
+    assert res[(0, 30)]["stats"]["h_gathered_passes"] == 0
+    # each run exact against the oracle at its own final h (the density sums are
+    # float atomics in no fixed order, so two runs' h may differ in the last bits)
+    refs = {}
+    for key, r in res.items():
+        ref = orc.density(box.x, box.m, orc.support_radius(r["h"]), box.L, True, method="kdtree")
+        assert np.array_equal(r["count"], ref["count"]), key
+        np.testing.assert_allclose(r["rho"], ref["rho"], rtol=1e-5, err_msg=str(key))
+        refs[key] = ref
+    g1, s1, g30, s30 = res[(1, 2)], res[(0, 2)], res[(1, 30)], res[(0, 30)]
+    # one later pass: both modes evaluate the h of the first pass's Newton step
+    np.testing.assert_allclose(g1["h"], s1["h"], rtol=1e-6)
+    np.testing.assert_allclose(g1["rho"], s1["rho"], rtol=1e-5)
+    # the full iteration converges to the same h
+    np.testing.assert_allclose(g30["h"], s30["h"], rtol=1e-4)
+    print(f"[gather] leaf {leaf} {mode}: {g30['it']} passes, {g30['stats']['h_gathered_passes']} gathered; "
+          f"rho max rel: one later pass to the symmetric pass {max_rel(g1['rho'], s1['rho']):.1e}, "
+          f"the full iteration to FP64 {max_rel(g30['rho'], refs[(1, 30)]['rho']):.1e}")
+
+
 def test_compensated_sums_at_high_neighbour_counts(api):
     """With about 400 neighbours per particle the FP32 density sums carry ~20x
     more rounding than at 48; compensated summation (sph_params.compensated)

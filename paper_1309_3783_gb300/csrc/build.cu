@@ -416,10 +416,21 @@ __device__ unsigned int block_exclusive_scan(unsigned int v, unsigned int* tmp, 
   return before;
 }
 
+// A scan may take its length from the device (n_dev: *n_dev + 1 entries, at most
+// n) and run only in the later passes of an h iteration (gate: the iteration
+// counter, which the kernels read; the scan is skipped in a first or stopped pass).
+__device__ __forceinline__ bool scan_len(long long& n, const unsigned int* n_dev, const int* gate) {
+  if (gate && !(gate[0] > 1 && gate[2] == 0)) return false;
+  if (n_dev) n = min(n, (long long)*n_dev + 1);
+  return true;
+}
+
 // in and out may be the same array: every thread reads its items before writing them
 __global__ void k_scan_tiles(long long n, const unsigned int* in, unsigned int* out,
-                             unsigned int* __restrict__ tile_sums) {
+                             unsigned int* __restrict__ tile_sums, const unsigned int* __restrict__ n_dev,
+                             const int* __restrict__ gate) {
   pdl_wait();
+  if (!scan_len(n, n_dev, gate) || (long long)blockIdx.x * SC_TILE >= n) return;
   __shared__ unsigned int tmp[32];
   const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
   unsigned int loc[SC_ITEMS];
@@ -440,8 +451,11 @@ __global__ void k_scan_tiles(long long n, const unsigned int* in, unsigned int* 
 }
 
 // single block: exclusive scan of the tile sums in place (any count), total -> *total
-__global__ void k_scan_sums(int ntiles, unsigned int* __restrict__ sums, unsigned int* __restrict__ total_out) {
+__global__ void k_scan_sums(int ntiles, unsigned int* __restrict__ sums, unsigned int* __restrict__ total_out,
+                            long long n, const unsigned int* __restrict__ n_dev, const int* __restrict__ gate) {
   pdl_wait();
+  if (!scan_len(n, n_dev, gate)) return;
+  ntiles = min(ntiles, (int)((n + SC_TILE - 1) / SC_TILE));
   __shared__ unsigned int tmp[32];
   unsigned int carry = 0;
   for (int base = 0; base < ntiles; base += blockDim.x) {
@@ -455,8 +469,10 @@ __global__ void k_scan_sums(int ntiles, unsigned int* __restrict__ sums, unsigne
   if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-__global__ void k_scan_add(long long n, unsigned int* __restrict__ out, const unsigned int* __restrict__ sums) {
+__global__ void k_scan_add(long long n, unsigned int* __restrict__ out, const unsigned int* __restrict__ sums,
+                           const unsigned int* __restrict__ n_dev, const int* __restrict__ gate) {
   pdl_wait();
+  if (!scan_len(n, n_dev, gate) || (long long)blockIdx.x * SC_TILE >= n) return;
   const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_ITEMS;
   const unsigned int add = sums[blockIdx.x];
 #pragma unroll
@@ -465,12 +481,12 @@ __global__ void k_scan_add(long long n, unsigned int* __restrict__ out, const un
 }
 
 void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsigned int* tile_sums,
-                    unsigned int* total, cudaStream_t st) {
+                    unsigned int* total, cudaStream_t st, const unsigned int* n_dev, const int* gate) {
   const long long ntiles = (n + SC_TILE - 1) / SC_TILE;
   if (ntiles == 0) return;
-  launch_pdl(k_scan_tiles, (unsigned)ntiles, SC_THREADS, st, n, in, out, tile_sums); count_launch();
-  launch_pdl(k_scan_sums, 1, 1024, st, (int)ntiles, tile_sums, total); count_launch();
-  launch_pdl(k_scan_add, (unsigned)ntiles, SC_THREADS, st, n, out, tile_sums); count_launch();
+  launch_pdl(k_scan_tiles, (unsigned)ntiles, SC_THREADS, st, n, in, out, tile_sums, n_dev, gate); count_launch();
+  launch_pdl(k_scan_sums, 1, 1024, st, (int)ntiles, tile_sums, total, n, n_dev, gate); count_launch();
+  launch_pdl(k_scan_add, (unsigned)ntiles, SC_THREADS, st, n, out, tile_sums, n_dev, gate); count_launch();
 }
 
 long long radix_scratch_words(long long n) {

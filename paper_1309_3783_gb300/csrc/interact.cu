@@ -1598,8 +1598,8 @@ __global__ void k_live_tasks(Lists Lq, Tree T, Tiles TL, const BoxDesc* __restri
 // iteration returns at once, and so does a stopped iteration).
 __device__ __forceinline__ bool later_pass(const int* it_dev) { return it_dev[0] > 1 && it_dev[2] == 0; }
 
-// Particles still iterating per cluster (cnt[t], 0 past the clusters of this
-// build, ntcap + 1 entries); clears the gathered task count.  One warp per cluster.
+// Particles still iterating per cluster (cnt[t] for the nt clusters of this
+// build, and cnt[nt] = 0); clears the gathered task count.  One warp per cluster.
 __global__ void k_pack_count(long long ntcap, const unsigned int* __restrict__ ntile_dev, const int* __restrict__ it_dev,
                              Tiles TL, const unsigned char* __restrict__ act, unsigned int* __restrict__ cnt,
                              unsigned int* __restrict__ g_n) {
@@ -1610,7 +1610,7 @@ __global__ void k_pack_count(long long ntcap, const unsigned int* __restrict__ n
   if (blockIdx.x == 0 && threadIdx.x == 0) *g_n = 0;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long t = warp; t <= ntcap; t += nwarps) {
+  for (long long t = warp; t <= nt; t += nwarps) {
     bool a = false;
     if (t < nt) a = (unsigned int)lane < TL.n[t] && act[TL.start[t] + lane];
     const unsigned int c = __popc(__ballot_sync(0xffffffffu, a));
@@ -1625,7 +1625,7 @@ __global__ void k_pack_leaf(long long ntcap, const unsigned int* __restrict__ nt
   pdl_wait();
   if (!later_pass(it_dev)) return;
   const long long nt = ntile_dev ? min(ntcap, (long long)*ntile_dev) : ntcap;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t <= ntcap;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t <= nt;
        t += (long long)gridDim.x * blockDim.x) {
     unsigned int val = 0;
     if (t < nt) {
@@ -2462,10 +2462,10 @@ void launch_gather_prep(Engine& E, const int* it_dev) {
   const unsigned int* ntd = E.gcap ? reinterpret_cast<const unsigned int*>(E.dev_counters.p + 4) : nullptr;
   launch_pdl(k_pack_count, E.grid(32 * (nt + 1)), 256, E.st, nt, ntd, it_dev, E.TL, E.act.p, E.pk_cnt.p, E.g_n.p);
   count_launch();
-  exclusive_scan(E.pk_cnt.p, E.pk_cnt.p, nt + 1, E.pk_sums.p, E.pk_tot.p + 0, E.st);
+  exclusive_scan(E.pk_cnt.p, E.pk_cnt.p, nt + 1, E.pk_sums.p, E.pk_tot.p + 0, E.st, ntd, it_dev);
   launch_pdl(k_pack_leaf, E.grid(nt + 1), 256, E.st, nt, ntd, it_dev, E.T, E.TL, E.pk_cnt.p, E.pk_v.p);
   count_launch();
-  exclusive_scan(E.pk_v.p, E.pk_v.p, nt + 1, E.pk_sums.p, E.pk_tot.p + 1, E.st);
+  exclusive_scan(E.pk_v.p, E.pk_v.p, nt + 1, E.pk_sums.p, E.pk_tot.p + 1, E.st, ntd, it_dev);
   launch_pdl(k_pack_fill, E.grid(32 * nt), 256, E.st, nt, ntd, it_dev, E.T, E.TL, E.act.p, E.pk_cnt.p,
              E.pk_v.p, E.pk_idx.p, E.pk_info.p, E.pk_n.p);
   count_launch();

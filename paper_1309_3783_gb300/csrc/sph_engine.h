@@ -64,7 +64,8 @@ extern const char* const kPhaseNames[PH_COUNT];
 
 // Kernels and helpers implemented in build.cu / interact.cu.
 void exclusive_scan(const unsigned int* in, unsigned int* out, long long n, unsigned int* tile_sums,
-                    unsigned int* total, cudaStream_t st);
+                    unsigned int* total, cudaStream_t st, const unsigned int* n_dev = nullptr,
+                    const int* gate = nullptr);
 long long radix_scratch_words(long long n);
 void radix_sort(unsigned long long* k0, unsigned int* v0, unsigned long long* k1, unsigned int* v1, long long n,
                 int bits, unsigned int* scratch, cudaStream_t st);

@@ -386,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
                    "dt": dt, "leaf_max": leaf_max, "cluster_max": cluster_max,
                    "leaf_max_source": ("set" if args.leaf_max_set else
                                        "autotuned" if not args.no_tune else "paper"),
-                   "l2": ("inputs larger than L2 (about 520 B per particle resident)" if big
+                   "l2": ("inputs larger than L2 (about 540 B per particle resident)" if big
                           else "flushed between timed steps (256 MB write)"),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 12 + 4 + 4 + 4 + 12 + 4),

@@ -51,3 +51,33 @@ def test_context_creation_fails_cleanly_without_a_device(lib_path):
     from paper_1309_3783_gb300 import sph
     with pytest.raises(sph.SphError):
         sph.sph_ctx_create(device=0)
+
+
+def _header_struct(name):
+    """(field, C type) of `typedef struct name { ... } name;` in include/sph.h, in order."""
+    src = open(os.path.join(ROOT, "include", "sph.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, flags=re.S).group(1)
+    return re.findall(r"\b(int32_t|int64_t|float|double|char)\s+(\w+)\s*(?:\[\d+\])?\s*;", body)
+
+
+@pytest.mark.parametrize("name", ["sph_params", "sph_stats", "sph_profile_entry"])
+def test_binding_structs_mirror_the_header(name):
+    import ctypes as C
+    from paper_1309_3783_gb300 import sph
+    width = {"int32_t": 4, "int64_t": 8, "float": 4, "double": 8}
+    want = _header_struct(name)
+    got = getattr(sph, name)._fields_
+    assert [f for _, f in want] == [f for f, _ in got]
+    for (ctype, field), (_, pytype) in zip(want, got):
+        if ctype != "char":
+            assert C.sizeof(pytype) == width[ctype], field
+        if ctype in ("float", "double"):
+            assert pytype in (C.c_float, C.c_double), field
+
+
+def test_parameter_defaults_of_the_options(lib_path):
+    from paper_1309_3783_gb300 import sph
+    p = sph.sph_params_default()
+    assert p.graphs == 1 and p.h_gather == 1 and p.pair_cache == 0 and p.reuse == 0 and p.sort_merge == 0
+    assert p.cluster_max == 32 and p.compensated == -1 and p.precision == 0
